@@ -1,0 +1,300 @@
+"""Seeded synthetic inputs for the chi0 / Sternheimer path (Gamma point, cubic cell).
+
+This module stands in for the ground-state DFT run that precedes a response
+calculation (the paper takes psi_i, eps_i from Quantum ESPRESSO, Sec. 3 and
+Fig. "workflow").  It draws random numbers (well positions, perturbation
+coefficients) from seeded PCG64 generators, lays out the model potential and
+projectors on the plane-wave spheres, and diagonalises the model Kohn-Sham
+Hamiltonian densely on the host to give the occupied states.  It contains none
+of the response method's arithmetic (no Sternheimer solve, no P_c, no density
+response) and is shared by the tests, the benchmark and the library's users as
+the source of inputs only.
+
+Conventions (Hartree atomic units):
+  * cubic cell of side L, volume Omega = L^3, reciprocal unit b = 2 pi / L;
+  * G = b (h, k, l); wavefunction sphere 0.5 |G|^2 <= ecut, density sphere
+    0.5 |G|^2 <= 4 ecut;
+  * canonical order of a sphere: ascending h^2+k^2+l^2, ties broken by the
+    Miller triple (h, k, l) compared lexicographically as signed integers;
+  * plane-wave coefficients are dimensionless: f(r) = sum_G f(G) e^{iGr} for
+    potentials and densities, psi(r) = Omega^{-1/2} sum_G psi(G) e^{iGr} with
+    sum_G |psi(G)|^2 = 1 for orbitals.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+import scipy.linalg
+
+__all__ = [
+    "Config", "CONFIGS", "System", "miller_sphere", "make_system",
+    "perturbations", "gauss_legendre_omega", "real_basis_map",
+]
+
+
+@dataclasses.dataclass(frozen=True)
+class Config:
+    """One synthetic workload (a Gaussian-well model insulator at Gamma)."""
+    name: str
+    L: float                  # cubic cell side [bohr]
+    ecut: float               # wavefunction cutoff [Ha]
+    grid: int                 # FFT points per axis
+    n_wells: int              # Gaussian wells, positions uniform in the cell
+    well_seed: int
+    n_v: int                  # doubly occupied states
+    n_pert: int = 8
+    pert_seed: int = 2
+    well_depth: float = 2.0   # D_w [Ha]
+    well_width: float = 1.0   # w [bohr]
+    kb: bool = False          # one s + three p Gaussian KB projectors per atom
+    kb_width: float = 0.8     # w_p [bohr]
+    kb_d_s: float = 1.0       # D_s [Ha]
+    kb_d_p: float = 0.5       # D_p [Ha]
+    min_gap: float = 0.01     # reseed (seed + 1) while HOMO-LUMO gap < this [Ha]
+
+
+CONFIGS = {
+    # 24^3 grid, ~500 plane waves, 4 wells, N_v = 4, 8 perturbations.
+    "chi0_L10_24": Config("chi0_L10_24", L=10.0, ecut=5.0, grid=24, n_wells=4,
+                          well_seed=1, n_v=4, n_pert=8, pert_seed=2),
+    # 48^3 grid, ~4k plane waves, 32 wells, N_v = 64, PDEP block of 64.
+    # Seeds 3-8 give HOMO-LUMO gaps below 0.01 Ha; the reseeding rule lands on 9.
+    "pdep_L16_48": Config("pdep_L16_48", L=16.0, ecut=7.75, grid=48, n_wells=32,
+                          well_seed=9, n_v=64, n_pert=64, pert_seed=5),
+    # 96^3 grid, ~30k plane waves, 64 atoms with wells + KB projectors, N_v = 256.
+    "kb_L24_96": Config("kb_L24_96", L=24.0, ecut=12.75, grid=96, n_wells=64,
+                        well_seed=4, n_v=256, n_pert=256, pert_seed=5, kb=True),
+    # Tiny case (12^3) for quick host checks.
+    "tiny_L6_12": Config("tiny_L6_12", L=6.0, ecut=2.5, grid=12, n_wells=2,
+                         well_seed=7, n_v=2, n_pert=3, pert_seed=8),
+}
+
+
+def miller_sphere(L: float, ecut: float) -> np.ndarray:
+    """Miller triples of the sphere 0.5 (2 pi / L)^2 (h^2+k^2+l^2) <= ecut, canonical order."""
+    b = 2.0 * math.pi / L
+    nmax_sq = 2.0 * ecut / (b * b)
+    m = int(math.floor(math.sqrt(nmax_sq))) + 1
+    rng = np.arange(-m, m + 1)
+    h, k, l = np.meshgrid(rng, rng, rng, indexing="ij")
+    h, k, l = h.ravel(), k.ravel(), l.ravel()
+    n2 = h * h + k * k + l * l
+    keep = 0.5 * b * b * n2 <= ecut * (1.0 + 1e-12)
+    h, k, l, n2 = h[keep], k[keep], l[keep], n2[keep]
+    order = np.lexsort((l, k, h, n2))   # last key is primary
+    return np.stack([h[order], k[order], l[order]], axis=1).astype(np.int32)
+
+
+def real_basis_map(miller: np.ndarray):
+    """Pairs {G, -G} of a sphere in canonical order.
+
+    Returns (i0, pos, neg): the index of G = 0 and, for each pair, the index of
+    the member that is "positive" (h > 0, or h = 0 and k > 0, or h = k = 0 and
+    l > 0) and of its mirror.  Pairs are listed in the canonical order of their
+    positive member.
+    """
+    key = {tuple(g): i for i, g in enumerate(miller.tolist())}
+    i0 = key[(0, 0, 0)]
+    pos, neg = [], []
+    for i, (h, k, l) in enumerate(miller.tolist()):
+        if h > 0 or (h == 0 and (k > 0 or (k == 0 and l > 0))):
+            pos.append(i)
+            neg.append(key[(-h, -k, -l)])
+    return i0, np.asarray(pos, dtype=np.int64), np.asarray(neg, dtype=np.int64)
+
+
+@dataclasses.dataclass
+class System:
+    """Model ground state handed to the response code (what a DFT run would provide)."""
+    cfg: Config
+    L: float
+    omega_cell: float
+    ecut: float
+    grid: int
+    miller_wfc: np.ndarray       # (N_pw, 3) int32, canonical order
+    miller_rho: np.ndarray       # (N_rho, 3) int32, canonical order
+    vloc_G: np.ndarray           # (N_rho,) complex128, V_loc(G) on the density sphere
+    beta_G: np.ndarray           # (N_pw, n_proj) complex128, KB projectors (may have 0 columns)
+    d_proj: np.ndarray           # (n_proj,) float64, KB couplings [Ha]
+    proj_atom: np.ndarray        # (n_proj,) int32, owning atom
+    psi_v: np.ndarray            # (N_pw, n_v) complex128, occupied states, real in r
+    e_v: np.ndarray              # (n_v,) float64, ascending
+    e_lumo: float                # lowest unoccupied eigenvalue (gap check)
+    positions: np.ndarray        # (n_wells, 3) well / atom centres [bohr]
+    well_seed_used: int
+
+    @property
+    def n_pw(self) -> int:
+        return self.miller_wfc.shape[0]
+
+    @property
+    def n_rho(self) -> int:
+        return self.miller_rho.shape[0]
+
+    @property
+    def n_v(self) -> int:
+        return self.psi_v.shape[1]
+
+    @property
+    def gap(self) -> float:
+        return float(self.e_lumo - self.e_v[-1])
+
+
+def _structure_factor(miller: np.ndarray, positions: np.ndarray, L: float) -> np.ndarray:
+    """S_a(G) = exp(-i G . R_a) for every G (rows) and atom (columns)."""
+    G = (2.0 * math.pi / L) * miller.astype(np.float64)
+    return np.exp(-1j * (G @ positions.T))
+
+
+def _gaussian_wells(cfg: Config, miller_rho: np.ndarray, positions: np.ndarray) -> np.ndarray:
+    """V_loc(G) of V(r) = -D_w sum_a sum_images exp(-|r - R_a|^2 / (2 w^2)).
+
+    (1/Omega) times the 3D Fourier integral of a Gaussian: (2 pi w^2)^{3/2} exp(-w^2 G^2 / 2).
+    """
+    b = 2.0 * math.pi / cfg.L
+    G2 = (b * b) * np.sum(miller_rho.astype(np.float64) ** 2, axis=1)
+    w = cfg.well_width
+    form = -(cfg.well_depth / cfg.L ** 3) * (2.0 * math.pi * w * w) ** 1.5 * np.exp(-0.5 * w * w * G2)
+    return form * _structure_factor(miller_rho, positions, cfg.L).sum(axis=1)
+
+
+def _kb_projectors(cfg: Config, miller_wfc: np.ndarray, positions: np.ndarray):
+    """Per atom: beta_s(G) = Omega^{-1/2} e^{-wp^2 G^2/2} e^{-iG.R}, beta_p,alpha = (-i G_alpha wp) beta_s."""
+    n_pw = miller_wfc.shape[0]
+    if not cfg.kb:
+        return (np.zeros((n_pw, 0), np.complex128), np.zeros(0), np.zeros(0, np.int32))
+    b = 2.0 * math.pi / cfg.L
+    G = b * miller_wfc.astype(np.float64)
+    G2 = np.sum(G * G, axis=1)
+    wp = cfg.kb_width
+    radial = np.exp(-0.5 * wp * wp * G2) / math.sqrt(cfg.L ** 3)
+    S = _structure_factor(miller_wfc, positions, cfg.L)
+    cols, d, atom = [], [], []
+    for a in range(positions.shape[0]):
+        s = radial * S[:, a]
+        cols.append(s); d.append(cfg.kb_d_s); atom.append(a)
+        for alpha in range(3):
+            cols.append(-1j * G[:, alpha] * wp * s); d.append(cfg.kb_d_p); atom.append(a)
+    return (np.stack(cols, axis=1), np.asarray(d, np.float64), np.asarray(atom, np.int32))
+
+
+def _dense_h_real(cfg, miller_wfc, miller_rho, vloc_G, beta_G, d_proj):
+    """Model Kohn-Sham Hamiltonian in the real basis {1, sqrt2 cos(G.r), sqrt2 sin(G.r)}.
+
+    H_GG' = 0.5|G|^2 delta_GG' + V(G-G') + sum_p beta_p(G) D_p beta_p(G')^* on the
+    wavefunction sphere, then rotated with the unitary map between the complex
+    and real bases so that it is real symmetric (V and beta are real in r).
+    """
+    n = miller_wfc.shape[0]
+    b = 2.0 * math.pi / cfg.L
+    M = int(np.max(np.abs(miller_rho)))
+    span = 2 * M + 1
+    lookup = np.full(span ** 3, -1, np.int64)
+    mr = miller_rho.astype(np.int64) + M
+    lookup[(mr[:, 0] * span + mr[:, 1]) * span + mr[:, 2]] = np.arange(miller_rho.shape[0])
+    mw = miller_wfc.astype(np.int64)
+    H = np.empty((n, n), np.complex128)
+    for i in range(n):
+        d = mw[i][None, :] - mw + M
+        idx = lookup[(d[:, 0] * span + d[:, 1]) * span + d[:, 2]]
+        if np.any(idx < 0):
+            raise ValueError("G - G' outside the density sphere")
+        H[i] = vloc_G[idx]
+    H[np.diag_indices(n)] += 0.5 * b * b * np.sum(miller_wfc.astype(np.float64) ** 2, axis=1)
+    if beta_G.shape[1]:
+        H += (beta_G * d_proj[None, :]) @ beta_G.conj().T
+    i0, pos, neg = real_basis_map(miller_wfc)
+    s = 1.0 / math.sqrt(2.0)
+    HU = np.empty((n, n), np.complex128)
+    HU[:, 0] = H[:, i0]
+    HU[:, 1::2] = (H[:, pos] + H[:, neg]) * s
+    HU[:, 2::2] = (-1j * H[:, pos] + 1j * H[:, neg]) * s
+    Hr = np.empty((n, n), np.complex128)
+    Hr[0, :] = HU[i0, :]
+    Hr[1::2, :] = (HU[pos, :] + HU[neg, :]) * s
+    Hr[2::2, :] = (1j * HU[pos, :] - 1j * HU[neg, :]) * s
+    if np.max(np.abs(Hr.imag)) > 1e-10 * max(1.0, np.max(np.abs(Hr.real))):
+        raise ValueError("model Hamiltonian is not real in the real basis")
+    Hr = Hr.real
+    return 0.5 * (Hr + Hr.T), (i0, pos, neg)
+
+
+def _real_to_complex(y: np.ndarray, n: int, basis) -> np.ndarray:
+    """Map real-basis coefficient columns back to complex plane-wave coefficients."""
+    i0, pos, neg = basis
+    s = 1.0 / math.sqrt(2.0)
+    c = np.zeros((n, y.shape[1]), np.complex128)
+    c[i0] = y[0]
+    c[pos] = (y[1::2] - 1j * y[2::2]) * s
+    c[neg] = (y[1::2] + 1j * y[2::2]) * s
+    return c
+
+
+def make_system(cfg: Config | str) -> System:
+    """Build the model ground state of a configuration (dense host diagonalisation)."""
+    if isinstance(cfg, str):
+        cfg = CONFIGS[cfg]
+    miller_wfc = miller_sphere(cfg.L, cfg.ecut)
+    miller_rho = miller_sphere(cfg.L, 4.0 * cfg.ecut)
+    m_rho = int(np.max(np.abs(miller_rho)))
+    if cfg.grid <= 2 * m_rho:
+        raise ValueError(f"grid {cfg.grid} too small for density sphere (max Miller {m_rho})")
+    seed = cfg.well_seed
+    for _attempt in range(64):
+        rng = np.random.Generator(np.random.PCG64(seed))
+        positions = rng.uniform(0.0, cfg.L, size=(cfg.n_wells, 3))
+        vloc_G = _gaussian_wells(cfg, miller_rho, positions)
+        beta_G, d_proj, proj_atom = _kb_projectors(cfg, miller_wfc, positions)
+        Hr, basis = _dense_h_real(cfg, miller_wfc, miller_rho, vloc_G, beta_G, d_proj)
+        n = Hr.shape[0]
+        evals, evecs = scipy.linalg.eigh(Hr, subset_by_index=[0, cfg.n_v], driver="evr")
+        if evals[cfg.n_v] - evals[cfg.n_v - 1] >= cfg.min_gap:
+            break
+        seed += 1
+    else:
+        raise RuntimeError("no gapped model found")
+    y = evecs[:, : cfg.n_v].copy()
+    # Sign convention: the largest-magnitude real-basis component of each state is positive.
+    piv = np.argmax(np.abs(y), axis=0)
+    y *= np.sign(y[piv, np.arange(y.shape[1])])[None, :]
+    psi_v = _real_to_complex(y, n, basis)
+    return System(cfg=cfg, L=cfg.L, omega_cell=cfg.L ** 3, ecut=cfg.ecut, grid=cfg.grid,
+                  miller_wfc=miller_wfc, miller_rho=miller_rho, vloc_G=vloc_G,
+                  beta_G=beta_G, d_proj=d_proj, proj_atom=proj_atom, psi_v=psi_v,
+                  e_v=evals[: cfg.n_v].copy(), e_lumo=float(evals[cfg.n_v]),
+                  positions=positions, well_seed_used=seed)
+
+
+def perturbations(miller_rho: np.ndarray, L: float, n_pert: int, seed: int,
+                  hermitian: bool = True) -> np.ndarray:
+    """Seeded perturbations dV(G) on the density sphere, shape (N_rho, n_pert), complex128.
+
+    N(0,1) + i N(0,1) coefficients on the positive half of the sphere, mirrored
+    as dV(-G) = dV(G)^* (a real perturbation at Gamma) unless hermitian=False,
+    dV(0) = 0, multiplied by v^{1/2}(G) = sqrt(4 pi)/|G|, and normalised to
+    sum_G |dV(G)|^2 = 1.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = miller_rho.shape[0]
+    i0, pos, neg = real_basis_map(miller_rho)
+    out = np.zeros((n, n_pert), np.complex128)
+    draws = rng.standard_normal((2, pos.size, n_pert)) + 1j * rng.standard_normal((2, pos.size, n_pert))
+    out[pos] = draws[0]
+    out[neg] = draws[0].conj() if hermitian else draws[1]
+    out[i0] = 0.0
+    b = 2.0 * math.pi / L
+    g = b * np.sqrt(np.sum(miller_rho.astype(np.float64) ** 2, axis=1))
+    vh = np.zeros(n)
+    vh[g > 0] = math.sqrt(4.0 * math.pi) / g[g > 0]
+    out *= vh[:, None]
+    out /= np.linalg.norm(out, axis=0, keepdims=True)
+    return out
+
+
+def gauss_legendre_omega(n: int = 32, omega_max: float = 50.0):
+    """Imaginary frequencies: n Gauss-Legendre nodes mapped linearly from [-1, 1] to [0, omega_max]."""
+    x, w = np.polynomial.legendre.leggauss(n)
+    half = 0.5 * omega_max
+    return half * (x + 1.0), half * w

@@ -1,0 +1,293 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by the mathematics.
+
+Each pin compares two different routes (or a route and a closed form), so that
+a dropped term, a wrong sign or index, or a transposed operand in one of them
+fails.  The planted-mistake tests at the end modify the oracle on the CPU and
+check that a pin catches it.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import chi0, lanczos, pdep
+from oracle.model import Model, sphere
+
+
+def model_of(s, **kw):
+    return Model(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, s.beta_G, s.d_proj, **kw)
+
+
+def rel(a, b):
+    return np.max(np.abs(a - b)) / np.max(np.abs(b))
+
+
+# ---------------------------------------------------------------- spheres and H
+def test_sphere_enumeration_brute_force():
+    """Both sphere enumerations equal a brute-force lattice count, in the documented order."""
+    L, ecut = 10.0, 5.0
+    b = 2 * math.pi / L
+    count = sum(1 for h in range(-8, 9) for k in range(-8, 9) for l in range(-8, 9)
+                if 0.5 * b * b * (h * h + k * k + l * l) <= ecut)
+    a = sphere(L, ecut)
+    c = synth.miller_sphere(L, ecut)
+    assert a.shape[0] == count == 515
+    assert np.array_equal(a, c)
+    n2 = np.sum(a ** 2, axis=1)
+    assert np.all(np.diff(n2) >= 0)
+    assert synth.miller_sphere(L, 4 * ecut).shape[0] == 4337
+    assert synth.miller_sphere(16.0, 7.75).shape[0] == 4169
+
+
+def test_vloc_matches_real_space_gaussians(tiny):
+    """V_loc(G) of the generator, taken to r, equals the Gaussian wells summed over images (band-limited)."""
+    s = synth.make_system(synth.Config("g", L=6.0, ecut=12.0, grid=40, n_wells=2, well_seed=7, n_v=1,
+                                       min_gap=-1.0))
+    m = Model(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v)
+    v_r = m.vloc_r.real
+    x = np.arange(s.grid) * s.L / s.grid
+    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+    ref = np.zeros_like(X)
+    for R in s.positions:
+        for i in (-1, 0, 1):
+            for j in (-1, 0, 1):
+                for k in (-1, 0, 1):
+                    d2 = (X - R[0] - i * s.L) ** 2 + (Y - R[1] - j * s.L) ** 2 + (Z - R[2] - k * s.L) ** 2
+                    ref -= 2.0 * np.exp(-d2 / 2.0)
+    # 4 * ecut = 48 Ha keeps Gaussians of width 1 bohr to ~1e-8 (exp(-w^2 G^2 / 2) at the cutoff).
+    assert np.max(np.abs(v_r - ref)) < 1e-6
+
+
+def test_fft_h_equals_dense_h(cfg24):
+    m = model_of(cfg24)
+    H = m.h_dense()
+    assert np.max(np.abs(H - H.conj().T)) == 0.0
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((m.mw.shape[0], 3)) + 1j * rng.standard_normal((m.mw.shape[0], 3))
+    assert rel(m.apply_h(x), H @ x) < 1e-13
+    # The given occupied states are eigenvectors with the given eigenvalues.
+    assert np.max(np.abs(H @ m.psi_v - m.psi_v * m.e_v)) < 1e-12
+
+
+def test_fft_h_with_kb_equals_dense_h():
+    s = synth.make_system(synth.Config("kb", L=6.0, ecut=2.5, grid=12, n_wells=2, well_seed=7,
+                                       n_v=2, kb=True))
+    m = model_of(s)
+    assert s.beta_G.shape[1] == 8
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((m.mw.shape[0], 2)) + 1j * rng.standard_normal((m.mw.shape[0], 2))
+    assert rel(m.apply_h(x), m.h_dense() @ x) < 1e-13
+
+
+# ---------------------------------------------------------------- chi0 routes
+@pytest.mark.parametrize("omegas", [[0.0], [0.35, 4.0]])
+def test_sos_equals_sternheimer(tiny, omegas):
+    m = model_of(tiny)
+    dV = synth.perturbations(tiny.miller_rho, tiny.L, 3, 8)
+    assert rel(chi0.sos_drho(m, dV, omegas), chi0.sternheimer_drho(m, dV, omegas)) < 1e-12
+
+
+def test_sos_equals_sternheimer_complex_perturbation(tiny):
+    m = model_of(tiny)
+    dV = synth.perturbations(tiny.miller_rho, tiny.L, 2, 11, hermitian=False)
+    assert rel(chi0.sos_drho(m, dV, [0.0, 0.8]), chi0.sternheimer_drho(m, dV, [0.0, 0.8])) < 1e-12
+
+
+def test_sos_equals_sternheimer_config24(cfg24):
+    m = model_of(cfg24)
+    dV = synth.perturbations(cfg24.miller_rho, cfg24.L, 2, 2)
+    assert rel(chi0.sos_drho(m, dV, [0.0, 1.5]), chi0.sternheimer_drho(m, dV, [0.0, 1.5])) < 1e-11
+
+
+def test_static_response_is_density_derivative(tiny):
+    """chi0(0) dV equals d n / d lambda of the ground state of H + lambda dV (no response formula used)."""
+    m = model_of(tiny)
+    dV = synth.perturbations(tiny.miller_rho, tiny.L, 2, 8)
+    for p in range(2):
+        fd = chi0.finite_difference_drho(m, dV[:, p], 1e-3)
+        assert rel(chi0.sos_drho(m, dV[:, p], [0.0])[:, 0, 0], fd) < 1e-9
+
+
+def test_static_response_derivative_with_kb():
+    s = synth.make_system(synth.Config("kb", L=6.0, ecut=2.5, grid=12, n_wells=2, well_seed=7,
+                                       n_v=2, kb=True))
+    m = model_of(s)
+    dV = synth.perturbations(s.miller_rho, s.L, 1, 3)[:, 0]
+    fd = chi0.finite_difference_drho(m, dV, 1e-3)
+    assert rel(chi0.sternheimer_drho(m, dV, [0.0])[:, 0, 0], fd) < 1e-9
+
+
+def free_model(L=6.0, ecut=3.0, grid=16, n_occ=7):
+    mw = sphere(L, ecut)
+    mr = sphere(L, 4 * ecut)
+    psi = np.zeros((mw.shape[0], n_occ), np.complex128)
+    psi[np.arange(n_occ), np.arange(n_occ)] = 1.0
+    b = 2 * math.pi / L
+    e = 0.5 * b * b * np.sum(mw[:n_occ] ** 2, axis=1)
+    return Model(L, ecut, grid, np.zeros(mr.shape[0], np.complex128), psi, e)
+
+
+@pytest.mark.parametrize("n_occ", [1, 7, 19])
+def test_free_electron_closed_form(n_occ):
+    m = free_model(n_occ=n_occ)
+    mr, diag = chi0.free_electron_chi0_diag(m.L, m.ecut, n_occ, [0.0, 0.6])
+    assert np.array_equal(mr, m.mr)
+    dV = synth.perturbations(m.mr, m.L, 2, 4)
+    ref = diag[:, None, :] * dV[:, :, None]
+    assert rel(chi0.sternheimer_drho(m, dV, [0.0, 0.6]), ref) < 1e-12
+    assert rel(chi0.sos_drho(m, dV, [0.0, 0.6]), ref) < 1e-12
+
+
+def test_free_electron_pdep_eigenvalues():
+    m = free_model(n_occ=7)
+    mr, diag = chi0.free_electron_chi0_diag(m.L, m.ecut, 7, [0.0])
+    g2 = m.g2r
+    lam = np.sort(np.where(g2 > 0, 4 * math.pi / np.where(g2 > 0, g2, 1) * diag[:, 0], 0.0))
+    w, _ = pdep.pdep_dense(m, 20)
+    assert np.max(np.abs(w - lam[:20])) < 1e-12 * np.max(np.abs(lam))
+
+
+# ---------------------------------------------------------------- invariants
+def test_chibar0_hermitian_negative_semidefinite(tiny):
+    m = model_of(tiny)
+    for om in (0.0, 0.9):
+        X = chi0.chibar0_matrix(m, om)
+        assert np.max(np.abs(X - X.conj().T)) < 1e-14
+        assert np.max(np.linalg.eigvalsh(0.5 * (X + X.conj().T))) < 1e-12
+
+
+def test_charge_conservation_and_linearity(tiny):
+    m = model_of(tiny)
+    dV = synth.perturbations(tiny.miller_rho, tiny.L, 2, 8)
+    i0 = int(np.where(np.all(m.mr == 0, axis=1))[0][0])
+    d = chi0.sos_drho(m, dV, [0.0, 0.4])
+    assert np.max(np.abs(d[i0])) < 1e-15
+    comb = chi0.sos_drho(m, 0.3 * dV[:, 0] - 1.7j * dV[:, 1], [0.0, 0.4])[:, 0, :]
+    assert rel(comb, 0.3 * d[:, 0, :] - 1.7j * d[:, 1, :]) < 1e-13
+
+
+def test_response_decays_monotonically_with_frequency(tiny):
+    m = model_of(tiny)
+    dV = synth.perturbations(tiny.miller_rho, tiny.L, 1, 8)[:, 0]
+    oms = [0.0, 0.1, 0.5, 1.0, 3.0, 10.0]
+    d = chi0.sos_drho(m, dV, oms)[:, 0, :]
+    q = np.array([np.vdot(dV, d[:, k]).real for k in range(len(oms))])
+    assert np.all(q < 0) and np.all(np.diff(q) > 0)
+
+
+def test_frequency_integral_closed_form(tiny):
+    """int_0^inf <a|chi0(iw)|c> dw, by quadrature of the sum over states, equals a form with no empty states."""
+    m = model_of(tiny)
+    dV = synth.perturbations(tiny.miller_rho, tiny.L, 2, 12)
+    # w = s tan(t), t in [0, pi/2): Gauss-Legendre in t.
+    x, wq = np.polynomial.legendre.leggauss(400)
+    t = 0.25 * math.pi * (x + 1)
+    s = 1.0
+    oms = s * np.tan(t)
+    jac = 0.25 * math.pi * wq * s / np.cos(t) ** 2
+    d = chi0.sos_drho(m, dV[:, 1], oms)[:, 0, :]
+    integral = np.sum(jac * (dV[:, 0].conj() @ d))
+    ref = chi0.frequency_integral_closed_form(m, dV[:, 0], dV[:, 1])
+    assert abs(integral - ref) < 1e-9 * abs(ref)
+
+
+def test_cg_reaches_dense_solution(cfg24):
+    m = model_of(cfg24)
+    dV = synth.perturbations(cfg24.miller_rho, cfg24.L, 1, 2)
+    out, iters = chi0.sternheimer_cg_drho(m, dV, tol=1e-13, return_iters=True)
+    assert rel(out, chi0.sternheimer_drho(m, dV, [0.0])[:, :, 0]) < 1e-11
+    assert max(iters) < 200
+
+
+# ---------------------------------------------------------------- PDEP and Lanczos
+def test_davidson_matches_dense(tiny):
+    m = model_of(tiny)
+    X = chi0.chibar0_matrix(m)
+    w, U = pdep.pdep_dense(m, 8)
+    rng = np.random.default_rng(3)
+    th, V, it = pdep.davidson(lambda B: X @ B, X.shape[0], 8, rng.standard_normal((X.shape[0], 8)), tol=1e-12)
+    assert np.max(np.abs(th - w)) < 1e-12
+    assert np.max(np.abs(V.conj().T @ V - np.eye(8))) < 1e-12
+    # Subspace check (eigenvectors are defined up to rotations inside degenerate sets).
+    sv = np.linalg.svd(U.conj().T @ V, compute_uv=False)
+    assert np.min(sv) > 1 - 1e-8
+
+
+def test_lanczos_moments_orthogonality_and_exact_limit(tiny):
+    m = model_of(tiny)
+    rng = np.random.default_rng(5)
+    b = rng.standard_normal(m.mw.shape[0]) + 1j * rng.standard_normal(m.mw.shape[0])
+    n = 10
+    alpha, beta, Q = lanczos.chain(m, b, n)
+    assert np.max(np.abs(Q.conj().T @ Q - np.eye(n))) < 1e-13
+    T = np.diag(alpha) + np.diag(beta[1:], 1) + np.diag(beta[1:], -1)
+    P = np.eye(m.mw.shape[0]) - m.psi_v @ m.psi_v.conj().T
+    A = P @ m.h_dense() @ P
+    q1 = Q[:, 0]
+    Ak, Tk = q1.copy(), np.eye(n)
+    for k in range(1, 2 * n - 1):
+        Ak = A @ Ak
+        Tk = Tk @ T
+        assert abs(np.vdot(q1, Ak) - Tk[0, 0]) < 1e-10 * abs(Tk[0, 0])
+    # Exact limit: a chain spanning range(P_c) reproduces the spectrum of P_c H P_c there.
+    nfull = m.mw.shape[0] - m.psi_v.shape[1]
+    alpha, beta, Q = lanczos.chain(m, b, nfull)
+    d, _ = lanczos.tridiag_eig(alpha, beta)
+    ew = np.linalg.eigvalsh(P @ m.h_dense() @ P)
+    ew = np.sort(ew[np.abs(ew) > 1e-9]) if nfull < ew.size else ew
+    w_all, _ = np.linalg.eigh(m.h_dense())
+    assert np.max(np.abs(np.sort(d) - w_all[m.psi_v.shape[1]:])) < 1e-10
+
+
+def test_lanczos_chi0_pdep_exact_limit(tiny):
+    m = model_of(tiny)
+    w, U = pdep.pdep_dense(m, 3)
+    oms = [0.0, 0.5, 5.0]
+    n = m.mw.shape[0] - m.psi_v.shape[1]
+    L, A, B = lanczos.chi0_pdep(m, U, oms, n)
+    assert rel(L, lanczos.chi0_pdep_sos(m, U, oms)) < 1e-12
+    # In the PDEP basis chi0(0) is diagonal with the PDEP eigenvalues.
+    assert np.max(np.abs(L[:, :, 0] - np.diag(w))) < 1e-12
+
+
+# ---------------------------------------------------------------- planted mistakes
+def test_planted_wrong_eigenvalue_fails_sos_pin(tiny):
+    """A Sternheimer solve with a shifted e_v (wrong diagonal of Eq. sternheimer) fails the SOS pin."""
+    m = model_of(tiny)
+    dV = synth.perturbations(tiny.miller_rho, tiny.L, 1, 8)
+    good = chi0.sos_drho(m, dV, [0.0])
+    m.e_v = m.e_v + 0.01
+    assert rel(chi0.sternheimer_drho(m, dV, [0.0]), good) > 1e-3
+
+
+def test_planted_transposed_grid_fails_dense_h_pin(cfg24, monkeypatch):
+    """Placing coefficients on the grid with transposed axes fails the FFT-vs-dense H pin."""
+    m = model_of(cfg24)
+    H = m.h_dense()
+    orig = Model.to_grid
+
+    def transposed(self, c, miller):
+        return orig(self, c, miller[:, ::-1]) if miller is self.mr else orig(self, c, miller)
+    monkeypatch.setattr(Model, "to_grid", transposed)
+    m._vloc_r = None
+    x = np.random.default_rng(2).standard_normal(m.mw.shape[0]) + 0j
+    assert rel(m.apply_h(x), H @ x) > 1e-3
+
+
+def test_planted_wrong_spin_factor_fails_closed_form():
+    m = free_model(n_occ=7)
+    m.f_s = 1.0
+    mr, diag = chi0.free_electron_chi0_diag(m.L, m.ecut, 7, [0.0])
+    dV = synth.perturbations(m.mr, m.L, 1, 4)
+    assert rel(chi0.sos_drho(m, dV, [0.0])[:, 0, 0], diag[:, 0] * dV[:, 0]) > 0.4
+
+
+def test_planted_missing_projector_fails_sos_pin(tiny, monkeypatch):
+    """Solving without P_c on the right-hand side gives a wrong answer that the SOS pin catches."""
+    m = model_of(tiny)
+    dV = synth.perturbations(tiny.miller_rho, tiny.L, 1, 8)
+    monkeypatch.setattr(chi0, "_pc", lambda model, x: x)
+    bad = chi0.sternheimer_cg_drho(m, dV, tol=1e-12, max_iter=300)
+    monkeypatch.undo()
+    assert rel(bad, chi0.sos_drho(m, dV, [0.0])[:, :, 0]) > 1e-3
