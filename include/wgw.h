@@ -1,0 +1,151 @@
+/*
+ * wgw -- batched DFPT response chi0 for plane-wave full-frequency GW on one GPU.
+ *
+ * C interface of libwgw.so.  The library applies the independent-particle
+ * density response chi0 of a Gamma-point, spin-unpolarised Kohn-Sham system to
+ * a batch of perturbations without empty states (Sec. 3 of Yu & Govoni,
+ * "GPU Acceleration of Large-Scale Full-Frequency GW Calculations",
+ * arXiv:2203.05623):
+ *   for every occupied state v and perturbation dV_p, solve the Sternheimer
+ *   equation  P_c (H - e_v) P_c dpsi_vp = -P_c dV_p psi_v   (Eq. sternheimer,
+ *   P_c = 1 - P_v) by batched preconditioned CG, with H = T + V_loc applied in
+ *   dual space through FFTs (Sec. 4.1), then accumulate
+ *   drho_p = sum_sigma sum_v [psi_v^* dpsi_vp + c.c.]                (Eq. dfpt).
+ *
+ * Units are Hartree atomic units.  The cell is cubic with side L (bohr),
+ * volume Omega = L^3.  Plane waves G = (2 pi / L)(h, k, l).  The wavefunction
+ * sphere is 0.5|G|^2 <= ecut, the density sphere 0.5|G|^2 <= 4 ecut.  Both are
+ * in CANONICAL ORDER: ascending h^2+k^2+l^2, ties broken by (h, k, l) compared
+ * lexicographically as signed integers; wgw_get_gvectors returns the order.
+ *
+ * Complex arrays are interleaved (re, im) doubles.  Coefficient conventions:
+ * potentials and densities f(r) = sum_G f(G) e^{iG.r}; orbitals
+ * psi(r) = Omega^{-1/2} sum_G psi(G) e^{iG.r} with sum_G |psi(G)|^2 = 1.
+ * With these, drho(G) = sum_G' chi0_GG' dV(G'), chi0_GG' = (1/Omega) FT FT chi0(r, r').
+ *
+ * Ownership: every pointer argument is owned by the caller and only read (or
+ * written, for outputs) during the call.  The context owns all device memory
+ * it allocates (occupied states, potential, work space) until wgw_destroy.
+ * Host-pointer entry points copy inputs in and results out within the call.
+ * *_dev entry points take device pointers and a CUDA stream (cudaStream_t
+ * passed as void*), enqueue their work on that stream and return after it
+ * completes.
+ *
+ * Errors: every function returns a status code and never aborts or exits.
+ * wgw_last_error() describes the last failure of the calling thread.
+ * A context that returned WGW_ERR_CUDA should be destroyed.
+ */
+#ifndef WGW_H
+#define WGW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define WGW_OK 0
+#define WGW_ERR_ARG 1      /* invalid argument (sizes, layout, symmetry) */
+#define WGW_ERR_NOMEM 2    /* device allocation failed */
+#define WGW_ERR_NOCONV 3   /* some Sternheimer system missed cg_tol; outputs are still written */
+#define WGW_ERR_CUDA 4     /* a CUDA call failed */
+#define WGW_ERR_TIMEOUT 5  /* a bounded device wait gave up */
+#define WGW_ERR_STATE 6    /* call not valid in the context's state */
+
+#define WGW_FP64 0   /* every step in FP64 */
+#define WGW_MIXED 1  /* FP32 inner CG + FP64 residual refinement (Sec. 5.1, mixed precision) */
+
+#define WGW_SPHERE_WFC 0
+#define WGW_SPHERE_RHO 1
+
+typedef struct wgw_ctx wgw_ctx;
+
+typedef struct wgw_options {
+  int precision;       /* WGW_FP64 or WGW_MIXED */
+  double cg_tol;       /* per system: ||b - A x||_2 <= cg_tol ||b||_2, residual in FP64 */
+  int max_cg_iter;     /* CG iterations per solve (FP64) or per inner solve (MIXED) */
+  int max_refine;      /* MIXED: FP64 refinement steps */
+  double inner_tol;    /* MIXED: relative residual reduction of each inner FP32 solve */
+  double f_s;          /* occupation of each state (2 = spin-unpolarised, the sum over sigma of Eq. dfpt) */
+  int check_every;     /* CG iterations between convergence polls by the host */
+} wgw_options;
+
+typedef struct wgw_stats {
+  int n_systems;            /* real Sternheimer systems solved (states x real perturbation parts) */
+  int n_converged;          /* systems that met cg_tol */
+  int max_iters;            /* most CG iterations of one system (sum over refinement steps) */
+  int refinements;          /* MIXED: FP64 refinement steps taken */
+  double max_rel_residual;  /* max over systems of ||b - A x|| / ||b|| (FP64) */
+} wgw_stats;
+
+/* Fills *opt with defaults: WGW_FP64, cg_tol 1e-12, max_cg_iter 2000, max_refine 8,
+ * inner_tol 1e-4, f_s 2, check_every 8. */
+int wgw_default_options(wgw_options* opt);
+
+/*
+ * Creates a context for one ground state (the output of the DFT run that
+ * precedes the response calculation, Sec. 3).
+ *   L        cubic cell side [bohr], > 0.
+ *   ecut     wavefunction cutoff [Ha], > 0.
+ *   grid     FFT points per axis; a product of 2, 3, 5; must exceed 2 m_rho where m_rho is the
+ *            largest |Miller index| of the density sphere (then H psi by FFTs is alias-free).
+ *   vloc_G   V_loc(G) on the density sphere, N_rho complex; must be real in r (V(-G) = V(G)^*).
+ *   n_proj, beta_G, d_proj   Kleinman-Bylander projectors; this version requires n_proj = 0.
+ *   psi_v    occupied states, N_pw x n_v complex, column-major (state v at psi_v + 2 N_pw v);
+ *            each must be real in r (psi(-G) = psi(G)^*) and the set orthonormal.
+ *   e_v      their eigenvalues [Ha], n_v entries.
+ *   opt      options (NULL = defaults); copied.
+ * On success *out holds the new context.
+ */
+int wgw_setup(wgw_ctx** out, double L, double ecut, int grid, const double* vloc_G, int n_proj,
+              const double* beta_G, const double* d_proj, const double* psi_v, const double* e_v,
+              int n_v, const wgw_options* opt);
+
+/* Number of plane waves of a sphere (which = WGW_SPHERE_WFC or WGW_SPHERE_RHO). */
+int wgw_sphere_size(const wgw_ctx* ctx, int which, int* n);
+
+/* Miller indices (3 int32 per G, canonical order) of a sphere; miller has room for 3 * size. */
+int wgw_get_gvectors(const wgw_ctx* ctx, int which, int32_t* miller);
+
+/* Replaces the options of a context (precision, tolerances, f_s, ...). */
+int wgw_set_options(wgw_ctx* ctx, const wgw_options* opt);
+
+/*
+ * drho = chi0(i omega) dV for a batch of perturbations (Eq. sternheimer + Eq. dfpt).
+ *   dV      N_rho x n_pert complex (perturbation p at dV + 2 N_rho p), density-sphere order.
+ *           A perturbation need not be real in r: it is applied by linearity as
+ *           dV = A + i B with A, B real in r (B is skipped when it is zero).
+ *   omega   n_omega imaginary frequencies; this version accepts only omega = 0.
+ *   drho    N_rho x n_pert x n_omega complex output (p fastest after G).
+ *   st      optional statistics (may be NULL).
+ * Returns WGW_ERR_NOCONV (with drho written) when a system missed cg_tol.
+ */
+int wgw_apply_chi0(wgw_ctx* ctx, const double* dV, int n_pert, const double* omega, int n_omega,
+                   double* drho, wgw_stats* st);
+
+/* As wgw_apply_chi0 with dV and drho in device memory; work is enqueued on `stream`. */
+int wgw_apply_chi0_dev(wgw_ctx* ctx, const double* dV_dev, int n_pert, const double* omega,
+                       int n_omega, double* drho_dev, void* stream, wgw_stats* st);
+
+/*
+ * Symmetrised response chi0bar phi = v^1/2 chi0 v^1/2 phi (Sec. 2.1), v^1/2(G) = sqrt(4 pi)/|G|,
+ * zero at G = 0.  phi and out are dimensionless density-sphere coefficients; layout as for
+ * wgw_apply_chi0_dev (device pointers, work on `stream`).
+ */
+int wgw_apply_chibar0_dev(wgw_ctx* ctx, const double* phi_dev, int n_pert, const double* omega,
+                          int n_omega, double* out_dev, void* stream, wgw_stats* st);
+
+/* Releases the context and all device memory it owns.  NULL is allowed. */
+void wgw_destroy(wgw_ctx* ctx);
+
+/* Static description of a status code. */
+const char* wgw_status_string(int status);
+
+/* Description of the last failure of the calling thread ("" if none). */
+const char* wgw_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WGW_H */

@@ -1,0 +1,185 @@
+// In-place mixed-radix FFTs of many lines held in shared memory.
+//
+// Two transforms are provided, each the transpose of the other:
+//   * DIF (Gentleman-Sande): natural-order input, digit-reversed output.
+//   * DIT: digit-reversed input, natural-order output.
+// Reciprocal space is always in natural order (so sphere coefficients are
+// scattered and gathered at h mod N), and real space is always in the
+// digit-reversed order the DIF produces; the library never needs real-space
+// points in natural order, so no reordering pass exists.  Position of natural
+// index n for radices R_0, R_1, ...:  P_N(n) = (N/R_0)(n mod R_0) + P_{N/R_0}(n div R_0).
+//
+// Every butterfly reads and writes the same R positions, so a stage needs no
+// second buffer; one block-wide barrier separates stages.  Threads are mapped
+// line-fastest so that neighbouring threads touch neighbouring lines.
+#pragma once
+
+#include "common.cuh"
+
+namespace wgw {
+
+// Radix-R DFT of v[0..R-1] in registers, X_k = sum_j v_j exp(sign 2 pi i j k / R), natural order.
+template <typename T>
+WGW_HD void dft2(cplx<T>* v) {
+  cplx<T> a = v[0] + v[1], b = v[0] - v[1];
+  v[0] = a; v[1] = b;
+}
+
+template <typename T>
+WGW_HD void dft3(cplx<T>* v, int sign) {
+  const T h = T(0.86602540378443864676);  // sin(2 pi / 3)
+  cplx<T> t = v[1] + v[2];
+  cplx<T> u = v[0] - cscale(t, T(0.5));
+  cplx<T> w = mul_i(cscale(v[1] - v[2], h), sign);
+  v[0] = v[0] + t;
+  v[1] = u + w;
+  v[2] = u - w;
+}
+
+template <typename T>
+WGW_HD void dft4(cplx<T>* v, int sign) {
+  cplx<T> a = v[0] + v[2], b = v[0] - v[2];
+  cplx<T> c = v[1] + v[3], d = mul_i(v[1] - v[3], sign);
+  v[0] = a + c; v[2] = a - c;
+  v[1] = b + d; v[3] = b - d;
+}
+
+template <typename T>
+WGW_HD void dft5(cplx<T>* v, int sign) {
+  const T c1 = T(0.30901699437494742410), c2 = T(-0.80901699437494742410);  // cos(2pi/5), cos(4pi/5)
+  const T s1 = T(0.95105651629515357212), s2 = T(0.58778525229247312917);   // sin(2pi/5), sin(4pi/5)
+  cplx<T> a1 = v[1] + v[4], b1 = v[1] - v[4];
+  cplx<T> a2 = v[2] + v[3], b2 = v[2] - v[3];
+  cplx<T> u1 = v[0] + cscale(a1, c1) + cscale(a2, c2);
+  cplx<T> u2 = v[0] + cscale(a1, c2) + cscale(a2, c1);
+  cplx<T> w1 = mul_i(cscale(b1, s1) + cscale(b2, s2), sign);
+  cplx<T> w2 = mul_i(cscale(b1, s2) - cscale(b2, s1), sign);
+  v[0] = v[0] + a1 + a2;
+  v[1] = u1 + w1; v[4] = u1 - w1;
+  v[2] = u2 + w2; v[3] = u2 - w2;
+}
+
+template <typename T>
+WGW_HD void dft8(cplx<T>* v, int sign) {
+  const T r = T(0.70710678118654752440);  // 1/sqrt(2)
+  cplx<T> a[4], b[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) { a[j] = v[j] + v[j + 4]; b[j] = v[j] - v[j + 4]; }
+  // b_j *= exp(sign i pi j / 4)
+  b[1] = cscale(mk<T>(b[1].re - sign * b[1].im, b[1].im + sign * b[1].re), r);
+  b[2] = mul_i(b[2], sign);
+  b[3] = cscale(mk<T>(-b[3].re - sign * b[3].im, -b[3].im + sign * b[3].re), r);
+  dft4(a, sign);
+  dft4(b, sign);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) { v[2 * k] = a[k]; v[2 * k + 1] = b[k]; }
+}
+
+template <typename T>
+WGW_HD void dft_r(int R, cplx<T>* v, int sign) {
+  switch (R) {
+    case 2: dft2(v); break;
+    case 3: dft3(v, sign); break;
+    case 4: dft4(v, sign); break;
+    case 5: dft5(v, sign); break;
+    default: dft8(v, sign); break;
+  }
+}
+
+// exp(sign 2 pi i k / N) from a table of exp(+2 pi i k / N), k in [0, N).
+template <typename T>
+WGW_HD cplx<T> twiddle(const cplx<T>* tw, int k, int sign) {
+  cplx<T> w = tw[k];
+  if (sign < 0) w.im = -w.im;
+  return w;
+}
+
+// Map a line index to its offset when the lines are the rows 0..lo and
+// N-hi..N-1 of a block (the footprint of a sphere of radius lo = hi = m).
+WGW_HD int split_line(int li, int m, int n) { return li <= m ? li : li + n - 2 * m - 1; }
+
+// DIF over `nlines` lines: natural order in, digit-reversed order out.
+// Line li starts at buf + off(li) * line_stride, element e at + e * elem_stride,
+// with off(li) = li, or split_line(li, m_split, N) when m_split >= 0.
+template <typename T>
+WGW_HD void fft_dif(cplx<T>* buf, const FftPlan& p, const cplx<T>* tw, int sign, int nlines,
+                    int line_stride, int elem_stride, int m_split, Thr th) {
+  const int N = p.n;
+  int S = N;
+  for (int st = 0; st < p.nst; ++st) {
+    const int R = p.radix[st];
+    const int M = S / R;
+    const int step = N / S;
+    const int total = nlines * (N / R);
+    for (int t = th.tid; t < total; t += th.nth) {
+      const int li = t % nlines;
+      const int rest = t / nlines;
+      const int j2 = rest % M;
+      const int blk = rest / M;
+      const int line = m_split >= 0 ? split_line(li, m_split, N) : li;
+      cplx<T>* base = buf + (size_t)line * line_stride + (size_t)(blk * S + j2) * elem_stride;
+      cplx<T> v[8];
+      for (int r = 0; r < R; ++r) v[r] = base[(size_t)r * M * elem_stride];
+      dft_r(R, v, sign);
+      base[0] = v[0];
+      for (int r = 1; r < R; ++r) {
+        cplx<T> x = v[r];
+        if (j2) x = cmul(x, twiddle(tw, (step * j2 * r) % N, sign));
+        base[(size_t)r * M * elem_stride] = x;
+      }
+    }
+    WGW_SYNC();
+    S = M;
+  }
+}
+
+// DIT over `nlines` lines: digit-reversed order in, natural order out.
+template <typename T>
+WGW_HD void fft_dit(cplx<T>* buf, const FftPlan& p, const cplx<T>* tw, int sign, int nlines,
+                    int line_stride, int elem_stride, int m_split, Thr th) {
+  const int N = p.n;
+  int sizes[6];
+  {
+    int S = N;
+    for (int st = 0; st < p.nst; ++st) { sizes[st] = S; S /= p.radix[st]; }
+  }
+  for (int st = p.nst - 1; st >= 0; --st) {
+    const int R = p.radix[st];
+    const int S = sizes[st];
+    const int M = S / R;
+    const int step = N / S;
+    const int total = nlines * (N / R);
+    for (int t = th.tid; t < total; t += th.nth) {
+      const int li = t % nlines;
+      const int rest = t / nlines;
+      const int j2 = rest % M;
+      const int blk = rest / M;
+      const int line = m_split >= 0 ? split_line(li, m_split, N) : li;
+      cplx<T>* base = buf + (size_t)line * line_stride + (size_t)(blk * S + j2) * elem_stride;
+      cplx<T> v[8];
+      v[0] = base[0];
+      for (int r = 1; r < R; ++r) {
+        cplx<T> x = base[(size_t)r * M * elem_stride];
+        if (j2) x = cmul(x, twiddle(tw, (step * j2 * r) % N, sign));
+        v[r] = x;
+      }
+      dft_r(R, v, sign);
+      for (int r = 0; r < R; ++r) base[(size_t)r * M * elem_stride] = v[r];
+    }
+    WGW_SYNC();
+  }
+}
+
+// Digit-reversed storage position of natural index n (host and device).
+WGW_HD int fft_position(const FftPlan& p, int n) {
+  int pos = 0, N = p.n;
+  for (int st = 0; st < p.nst; ++st) {
+    const int R = p.radix[st];
+    N /= R;
+    pos += N * (n % R);
+    n /= R;
+  }
+  return pos;
+}
+
+}  // namespace wgw

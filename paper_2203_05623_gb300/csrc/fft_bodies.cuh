@@ -1,0 +1,296 @@
+// Bodies of the pruned 3D FFT kernels (dual-space H application, Sec. 4.1).
+//
+// A "pair" packs two real-in-r functions a(r), b(r) into one complex grid
+// z = a + i b (Gamma point).  In reciprocal space a function is held in the
+// real plane-wave basis: element 0 = f(G=0) (real), elements 2j-1, 2j =
+// sqrt2 Re f(G_j), sqrt2 Im f(G_j) for the j-th positive member G_j of the
+// sphere.  With Z(G) = A(G) + i B(G):
+//   Z(+G_j) = [(ar - bi) + i (ai + br)] / sqrt2,  Z(-G_j) = [(ar + bi) + i (br - ai)] / sqrt2,
+//   A(G_j) = [Z(G_j) + Z(-G_j)^*] / 2,  B(G_j) = [Z(G_j) - Z(-G_j)^*] / (2i).
+//
+// The transform G -> r of a sphere of radius m (in every Miller index) runs
+// along z on the 2m+1 rows |k| <= m of each plane h, then along y on the
+// whole plane (plane kernel), then along x for each (y, z) on the 2m+1
+// non-zero h (x-line kernel).  Between the kernels the data of one pair is
+// T[h + m][y][z] (2m+1 planes of N x N complex, y and z in digit-reversed
+// position).  Real-space arrays are [y][z][x] with all three coordinates in
+// digit-reversed position.
+#pragma once
+
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace wgw {
+
+// Strided batch of real-basis vectors: system s at base + s * ld.
+template <typename T>
+struct VecBatch {
+  T* p;
+  long ld;
+  int n_sys;
+};
+
+// Per-system activity (null = all active).
+WGW_HD bool is_active(const int* active, int s) { return active == nullptr || active[s] != 0; }
+
+// G -> r along z then y for plane hi of one pair; writes T[hi] of that pair.
+// smem: N * (N + 1) complex.
+template <typename T>
+WGW_HD void plane_g2r_body(int pair, int hi, const SphereTab& sp, const FftPlan& pl,
+                           const cplx<T>* tw, const T* X, long ldx, int n_sys, const int* active,
+                           cplx<T>* Tout, cplx<T>* B, Thr th) {
+  const int N = pl.n, LS = N + 1, m = sp.m;
+  const int s0 = 2 * pair, s1 = 2 * pair + 1;
+  const bool has1 = s1 < n_sys;
+  for (int i = th.tid; i < N * LS; i += th.nth) B[i] = mk<T>(0, 0);
+  WGW_SYNC();
+  const T* x0 = X + (size_t)s0 * ldx;
+  const T* x1 = X + (size_t)s1 * ldx;
+  const T s = T(kInvSqrt2);
+  for (int e = sp.plane_off[hi] + th.tid; e < sp.plane_off[hi + 1]; e += th.nth) {
+    const int2 en = sp.ent[e];
+    const int kk = en.x & 0xff, ll = (en.x >> 8) & 0xff, neg = (en.x >> 16) & 1;
+    const int j = en.y;
+    cplx<T> z;
+    if (j == 0) {
+      z = mk<T>(x0[0], has1 ? x1[0] : T(0));
+    } else {
+      const T ar = x0[2 * j - 1], ai = x0[2 * j];
+      const T br = has1 ? x1[2 * j - 1] : T(0), bi = has1 ? x1[2 * j] : T(0);
+      z = neg ? mk<T>((ar + bi) * s, (br - ai) * s) : mk<T>((ar - bi) * s, (ai + br) * s);
+    }
+    B[kk * LS + ll] = z;
+  }
+  WGW_SYNC();
+  fft_dif(B, pl, tw, +1, 2 * m + 1, LS, 1, m, th);   // rows |k| <= m, along l -> z
+  fft_dif(B, pl, tw, +1, N, 1, LS, -1, th);          // columns z, along k -> y
+  cplx<T>* out = Tout + ((size_t)pair * (2 * m + 1) + hi) * N * N;
+  for (int i = th.tid; i < N * N; i += th.nth) {
+    const int y = i / N, z = i % N;
+    out[i] = B[y * LS + z];
+  }
+  (void)active;
+}
+
+// x-line kernel modes.
+enum XMode : int {
+  XM_APPLY_V = 0,    // G->r along x, multiply by V(r), r->G along x (in place in T)
+  XM_TO_REAL = 1,    // G->r along x, write Re / Im to real-space arrays R0 / R1
+  XM_FROM_REAL = 2,  // read a0*b0 + i a1*b1 from real-space arrays, r->G along x into T
+};
+
+template <typename T>
+struct XArgs {
+  int mode;
+  const T* V;              // APPLY_V: real-space potential [y][z][x]
+  T* R0; T* R1;            // TO_REAL outputs (R1 may be null)
+  long ldr;                // stride between real-space arrays of successive systems
+  const T* A; const T* Bm; // FROM_REAL factors (Bm may be null = 1)
+  long lda, ldb;           // per-system strides of A and Bm
+  const int* a_index;      // FROM_REAL: index of the A array of system s (null = s)
+  const int* b_index;      // FROM_REAL: index of the Bm array of system s (null = s)
+  int n_sys;
+};
+
+// One (pair, y) slab: S[z][x], N x (N + 1) complex.
+template <typename T>
+WGW_HD void xline_body(int pair, int y, int m, const FftPlan& pl, const cplx<T>* tw,
+                       cplx<T>* Tbuf, const XArgs<T>& a, cplx<T>* S, Thr th) {
+  const int N = pl.n, LS = N + 1, NP = 2 * m + 1;
+  const int s0 = 2 * pair, s1 = 2 * pair + 1;
+  const bool has1 = s1 < a.n_sys;
+  cplx<T>* tp = Tbuf + (size_t)pair * NP * N * N + (size_t)y * N;   // T[hi][y][z] at tp[hi*N*N + z]
+  const size_t slab = (size_t)y * N * N;                              // real-space [y][z][x] offset
+  if (a.mode == XM_FROM_REAL) {
+    const T* A0 = a.A + (size_t)(a.a_index ? a.a_index[s0] : s0) * a.lda + slab;
+    const T* A1 = has1 ? a.A + (size_t)(a.a_index ? a.a_index[s1] : s1) * a.lda + slab : nullptr;
+    const T* B0 = a.Bm ? a.Bm + (size_t)(a.b_index ? a.b_index[s0] : s0) * a.ldb + slab : nullptr;
+    const T* B1 = (a.Bm && has1) ? a.Bm + (size_t)(a.b_index ? a.b_index[s1] : s1) * a.ldb + slab : nullptr;
+    for (int i = th.tid; i < N * N; i += th.nth) {
+      const int z = i / N, x = i % N;
+      T re = A0[i], im = A1 ? A1[i] : T(0);
+      if (B0) re *= B0[i];
+      if (B1) im *= B1[i];
+      S[z * LS + x] = mk<T>(re, im);
+    }
+    WGW_SYNC();
+  } else {
+    for (int i = th.tid; i < N * LS; i += th.nth) S[i] = mk<T>(0, 0);
+    WGW_SYNC();
+    for (int i = th.tid; i < NP * N; i += th.nth) {
+      const int hi = i / N, z = i % N;
+      const int x = (hi - m + N) % N;
+      S[z * LS + x] = tp[(size_t)hi * N * N + z];
+    }
+    WGW_SYNC();
+    fft_dif(S, pl, tw, +1, N, LS, 1, -1, th);
+  }
+  if (a.mode == XM_TO_REAL) {
+    T* r0 = a.R0 + (size_t)s0 * a.ldr + slab;
+    T* r1 = (has1 && a.R1) ? a.R1 + (size_t)s1 * a.ldr + slab : nullptr;
+    for (int i = th.tid; i < N * N; i += th.nth) {
+      const int z = i / N, x = i % N;
+      const cplx<T> v = S[z * LS + x];
+      r0[i] = v.re;
+      if (r1) r1[i] = v.im;
+    }
+    return;
+  }
+  if (a.mode == XM_APPLY_V) {
+    const T* v = a.V + slab;
+    for (int i = th.tid; i < N * N; i += th.nth) {
+      const int z = i / N, x = i % N;
+      S[z * LS + x] = cscale(S[z * LS + x], v[i]);
+    }
+    WGW_SYNC();
+  }
+  fft_dit(S, pl, tw, -1, N, LS, 1, -1, th);
+  for (int i = th.tid; i < NP * N; i += th.nth) {
+    const int hi = i / N, z = i % N;
+    const int x = (hi - m + N) % N;
+    tp[(size_t)hi * N * N + z] = S[z * LS + x];
+  }
+}
+
+// Epilogue of the r -> G plane kernel, per real-basis element i of system s:
+//   out[s][i] = vcoef * F[i] + (kin * g2[i] + shift[s]) * pin[s][i]   (pin may be null)
+// where F is the transformed function (already scaled by 1/N^3).
+template <typename T>
+struct Epi {
+  T* out; long ldo;
+  const T* pin; long ldp;
+  T vcoef;
+  T kin;
+  const T* shift;          // per system (null = 0)
+  int n_sys;
+  const int* active;
+};
+
+template <typename T>
+WGW_HD void epi_store(const Epi<T>& e, const SphereTab& sp, int s, int i, T f) {
+  T v = e.vcoef * f;
+  if (e.pin) {
+    T c = e.kin * T(sp.g2[i]);
+    if (e.shift) c += e.shift[s];
+    v += c * e.pin[(size_t)s * e.ldp + i];
+  }
+  e.out[(size_t)s * e.ldo + i] = v;
+}
+
+// Unpack one pair of values Z(G_j), Z(-G_j) into the two systems' real-basis elements.
+template <typename T>
+WGW_HD void unpack_store(const Epi<T>& ep, const SphereTab& sp, int s0, int s1, bool act0, bool act1,
+                         int j, cplx<T> zp, cplx<T> zm, T scale) {
+  const T a = zp.re, b = zp.im, c = zm.re, d = zm.im;
+  // A(G_j) = ((a + c) + i (b - d)) / 2,  B(G_j) = ((b + d) - i (a - c)) / 2
+  const T hs = T(0.5) * scale * T(kSqrt2);
+  if (act0) {
+    epi_store(ep, sp, s0, 2 * j - 1, (a + c) * hs);
+    epi_store(ep, sp, s0, 2 * j, (b - d) * hs);
+  }
+  if (act1) {
+    epi_store(ep, sp, s1, 2 * j - 1, (b + d) * hs);
+    epi_store(ep, sp, s1, 2 * j, (c - a) * hs);
+  }
+}
+
+// r -> G along y then z for plane hi of one pair (in B), natural k, l afterwards.
+template <typename T>
+WGW_HD void plane_r2g_load(int pair, int hi, const SphereTab& sp, const FftPlan& pl,
+                           const cplx<T>* tw, const cplx<T>* Tin, cplx<T>* B, Thr th) {
+  const int N = pl.n, LS = N + 1, m = sp.m, NP = 2 * m + 1;
+  const cplx<T>* in = Tin + ((size_t)pair * NP + hi) * N * N;
+  for (int i = th.tid; i < N * N; i += th.nth) {
+    const int y = i / N, z = i % N;
+    B[y * LS + z] = in[i];
+  }
+  WGW_SYNC();
+  fft_dit(B, pl, tw, -1, N, 1, LS, -1, th);          // columns z: y -> k (natural)
+  fft_dit(B, pl, tw, -1, 2 * m + 1, LS, 1, m, th);   // rows |k| <= m: z -> l (natural)
+}
+
+WGW_HD int ent_pos(int2 en, int LS) { return (en.x & 0xff) * LS + ((en.x >> 8) & 0xff); }
+
+// r -> G for planes +hp and -hp of one pair, gather the sphere, unpack, epilogue.
+// smem: N * (N + 1) complex for the plane + npt_max complex (values of plane +hp).
+template <typename T>
+WGW_HD void plane_r2g_body(int pair, int hp, const SphereTab& sp, const FftPlan& pl,
+                           const cplx<T>* tw, const cplx<T>* Tin, const Epi<T>& ep,
+                           cplx<T>* B, cplx<T>* Zp, Thr th) {
+  const int N = pl.n, LS = N + 1, m = sp.m;
+  const int s0 = 2 * pair, s1 = 2 * pair + 1;
+  const bool has1 = s1 < ep.n_sys;
+  const bool act0 = is_active(ep.active, s0), act1 = has1 && is_active(ep.active, s1);
+  const T scale = T(1.0) / (T(N) * T(N) * T(N));
+  const int off_p = sp.plane_off[m + hp];
+  const int cnt = sp.plane_off[m + hp + 1] - off_p;
+  plane_r2g_load(pair, m + hp, sp, pl, tw, Tin, B, th);
+  if (hp == 0) {
+    // Plane 0 lists [G = 0, K positives, K mirrors].
+    const int K = (cnt - 1) / 2;
+    for (int t = th.tid; t < K; t += th.nth) {
+      const int2 ep_ = sp.ent[off_p + 1 + t];
+      unpack_store(ep, sp, s0, s1, act0, act1, ep_.y, B[ent_pos(ep_, LS)],
+                   B[ent_pos(sp.ent[off_p + 1 + K + t], LS)], scale);
+    }
+    if (th.tid == 0) {
+      const cplx<T> z0 = B[ent_pos(sp.ent[off_p], LS)];
+      if (act0) epi_store(ep, sp, s0, 0, z0.re * scale);
+      if (act1) epi_store(ep, sp, s1, 0, z0.im * scale);
+    }
+    return;
+  }
+  for (int t = th.tid; t < cnt; t += th.nth) Zp[t] = B[ent_pos(sp.ent[off_p + t], LS)];
+  WGW_SYNC();
+  const int off_m = sp.plane_off[m - hp];
+  plane_r2g_load(pair, m - hp, sp, pl, tw, Tin, B, th);
+  for (int t = th.tid; t < cnt; t += th.nth) {
+    unpack_store(ep, sp, s0, s1, act0, act1, sp.ent[off_p + t].y, Zp[t],
+                 B[ent_pos(sp.ent[off_m + t], LS)], scale);
+  }
+}
+
+// Density response of perturbation p on slab y (Eq. dfpt, one spin channel
+// times f_s folded into coef):
+//   D_p[y][z][x] = coef * sum_{v} psi_v(r) x_{(v,p)}(r),
+// with systems ordered s = p * n_v + v and x_s(r) obtained from T by the
+// G -> r pass along x.  The sum runs over v in a fixed order, so the result
+// does not depend on how many perturbations share the launch.
+// smem: N * (N + 1) complex + N * N real.
+template <typename T>
+WGW_HD void drho_xline_body(int p, int y, int m, const FftPlan& pl, const cplx<T>* tw,
+                            const cplx<T>* Tbuf, const T* psi_r, long ldpsi, int n_v, int n_sys,
+                            T coef, T* D, long ldd, cplx<T>* S, T* acc, Thr th) {
+  const int N = pl.n, LS = N + 1, NP = 2 * m + 1;
+  const size_t slab = (size_t)y * N * N;
+  for (int i = th.tid; i < N * N; i += th.nth) acc[i] = T(0);
+  const int s_lo = p * n_v, s_hi = (p + 1) * n_v;   // systems of p: [s_lo, s_hi)
+  for (int q = s_lo / 2; 2 * q < s_hi; ++q) {
+    for (int i = th.tid; i < N * LS; i += th.nth) S[i] = mk<T>(0, 0);
+    WGW_SYNC();
+    const cplx<T>* tp = Tbuf + (size_t)q * NP * N * N + (size_t)y * N;
+    for (int i = th.tid; i < NP * N; i += th.nth) {
+      const int hi = i / N, z = i % N;
+      S[z * LS + (hi - m + N) % N] = tp[(size_t)hi * N * N + z];
+    }
+    WGW_SYNC();
+    fft_dif(S, pl, tw, +1, N, LS, 1, -1, th);
+    const int sa = 2 * q, sb = 2 * q + 1;
+    const bool ua = sa >= s_lo && sa < s_hi && sa < n_sys;
+    const bool ub = sb >= s_lo && sb < s_hi && sb < n_sys;
+    const T* pa = psi_r + (size_t)(sa - s_lo) * ldpsi + slab;
+    const T* pb = psi_r + (size_t)(sb - s_lo) * ldpsi + slab;
+    for (int i = th.tid; i < N * N; i += th.nth) {
+      const cplx<T> v = S[(i / N) * LS + (i % N)];
+      T a = acc[i];
+      if (ua) a += pa[i] * v.re;
+      if (ub) a += pb[i] * v.im;
+      acc[i] = a;
+    }
+    WGW_SYNC();
+  }
+  T* d = D + (size_t)p * ldd + slab;
+  for (int i = th.tid; i < N * N; i += th.nth) d[i] = coef * acc[i];
+}
+
+}  // namespace wgw

@@ -1,0 +1,70 @@
+// Launchers shared between the translation units of the wgw library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "fft_bodies.cuh"
+#include "la_bodies.cuh"
+
+namespace wgw {
+
+template <typename T>
+struct FftCtx {
+  FftPlan plan;
+  const cplx<T>* tw;   // exp(+2 pi i k / N), k < N
+};
+
+int fft_threads(int n);
+
+// Pruned 3D FFT pipeline (fft_kernels.cu).
+template <typename T>
+cudaError_t launch_plane_g2r(const SphereTab& sp, FftCtx<T> f, const T* X, long ldx, int n_sys,
+                             const int* active, cplx<T>* Tbuf, cudaStream_t st);
+template <typename T>
+cudaError_t launch_xline(int m, FftCtx<T> f, cplx<T>* Tbuf, const XArgs<T>& a, const int* active,
+                         cudaStream_t st);
+template <typename T>
+cudaError_t launch_plane_r2g(const SphereTab& sp, int npt_max, FftCtx<T> f, const cplx<T>* Tbuf,
+                             const Epi<T>& e, cudaStream_t st);
+template <typename T>
+cudaError_t launch_drho_xline(int m, FftCtx<T> f, const cplx<T>* Tbuf, const T* psi_r, long ldpsi,
+                              int n_v, int n_sys, int n_pert, T coef, T* D, long ldd, cudaStream_t st);
+
+// Linear algebra (la_kernels.cu).
+template <typename T>
+cudaError_t launch_pc(T* Y, long ldy, int n_sys, const T* Psi, long ldp, int n, int nv,
+                      const int* active, cudaStream_t st);
+template <typename T>
+cudaError_t launch_cg_init_a(const SphereTab& sp, int n, int n_sys, const T* Bv, T* X, T* R, T* Z,
+                             long ld, const double* eps, CgState cs, cudaStream_t st);
+template <typename T>
+cudaError_t launch_cg_init_b(int n, int n_sys, const T* R, const T* Z, T* P, long ld, CgState cs,
+                             cudaStream_t st);
+template <typename T>
+cudaError_t launch_cg_step_a(const SphereTab& sp, int n, int n_sys, T* X, T* R, T* Z, const T* P,
+                             const T* Q, long ld, const double* eps, CgState cs, double tol2,
+                             int max_iter, cudaStream_t st);
+template <typename T>
+cudaError_t launch_cg_step_b(int n, int n_sys, const T* R, const T* Z, T* P, long ld, CgState cs,
+                             cudaStream_t st);
+cudaError_t launch_sphere_to_rb(int n_sys, const double* c, long ldc, const double* scale, RbMap mp,
+                                int part, double* out, long ldo, cudaStream_t st);
+cudaError_t launch_rb_to_sphere(int n_sys, const double* in, long ldi, const int* b_row,
+                                const double* scale, RbMap mp, double* c, long ldc, cudaStream_t st);
+cudaError_t launch_axpby(int n_sys, int n, double alpha, const double* x, double beta,
+                         const double* y, double* out, long ld, const int* active, cudaStream_t st);
+template <typename Ti, typename To>
+cudaError_t launch_copy_cast(int n_sys, int n, const Ti* in, long ldi, To* out, long ldo,
+                             const int* active, cudaStream_t st);
+// y[s] += x[s] (x cast to double), for active systems (null = all).
+template <typename T>
+cudaError_t launch_add_to(int n_sys, int n, const T* x, long ldx, double* y, long ldy,
+                          const int* active, cudaStream_t st);
+// Per-system norms ||x_s||^2 into out[s].
+template <typename T>
+cudaError_t launch_norm2(int n_sys, int n, const T* x, long ld, double* out, cudaStream_t st);
+// Count of nonzero entries of flags[0..n) into *out (one block).
+cudaError_t launch_count(const int* flags, int n, int* out, cudaStream_t st);
+
+}  // namespace wgw

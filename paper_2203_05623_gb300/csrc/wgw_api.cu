@@ -1,0 +1,634 @@
+// Host side of libwgw: plane-wave spheres, context set-up, and the chi0 apply
+// driver (Eq. sternheimer solved by batched CG, then Eq. dfpt).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/wgw.h"
+#include "internal.h"
+#include "tables.h"
+
+using namespace wgw;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int status, const std::string& msg) {
+  g_last_error = msg;
+  return status;
+}
+
+#define WGW_CK(expr)                                                                         \
+  do {                                                                                       \
+    cudaError_t e_ = (expr);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return fail(WGW_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));         \
+  } while (0)
+
+#define WGW_TRY(expr)                 \
+  do {                                \
+    int s_ = (expr);                  \
+    if (s_ != WGW_OK) return s_;      \
+  } while (0)
+
+// Device buffer that only grows.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  int ensure(size_t need) {
+    if (need <= bytes) return WGW_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&p, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(WGW_ERR_NOMEM, "cudaMalloc of " + std::to_string(need) + " bytes failed");
+    }
+    bytes = need;
+    return WGW_OK;
+  }
+  template <typename T> T* as() const { return static_cast<T*>(p); }
+  void release() { if (p) cudaFree(p); p = nullptr; bytes = 0; }
+};
+
+long pad32(long n) { return (n + 31) / 32 * 32; }
+
+// A plane-wave sphere (host tables from tables.h) with device copies.
+struct HostSphere : SphereHostTables {
+  DevBuf d_off, d_ent, d_g2, d_i0, d_pos, d_neg, d_vsqrt;
+  SphereTab tab() const {
+    SphereTab t;
+    t.m = m; t.n_pairs = n_pairs;
+    t.plane_off = d_off.as<int>(); t.ent = d_ent.as<int2>(); t.g2 = d_g2.as<double>();
+    return t;
+  }
+  RbMap map() const {
+    RbMap r; r.n_pairs = n_pairs; r.i0 = d_i0.as<int>(); r.pos = d_pos.as<int>(); r.neg = d_neg.as<int>();
+    return r;
+  }
+  void release() { d_off.release(); d_ent.release(); d_g2.release(); d_i0.release(); d_pos.release(); d_neg.release(); d_vsqrt.release(); }
+};
+
+template <typename T>
+int upload(DevBuf& d, const std::vector<T>& h) {
+  WGW_TRY(d.ensure(sizeof(T) * std::max<size_t>(h.size(), 1)));
+  if (!h.empty()) WGW_CK(cudaMemcpy(d.p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+  return WGW_OK;
+}
+
+int upload_sphere(HostSphere& s) {
+  WGW_TRY(upload(s.d_off, s.plane_off));
+  WGW_TRY(upload(s.d_ent, s.ent));
+  WGW_TRY(upload(s.d_g2, s.g2));
+  WGW_TRY(upload(s.d_i0, std::vector<int>{s.i0}));
+  WGW_TRY(upload(s.d_pos, s.pos));
+  WGW_TRY(upload(s.d_neg, s.neg));
+  WGW_TRY(upload(s.d_vsqrt, s.vsqrt));
+  return WGW_OK;
+}
+
+// Per-precision device state of a context.
+template <typename T>
+struct Prec {
+  DevBuf tw;        // N twiddles
+  DevBuf psi;       // occupied states, real basis, n_v x ld_w
+  DevBuf psi_r;     // occupied states in real space, n_v x N^3
+  DevBuf v_r;       // V_loc in real space
+  // work
+  DevBuf X, R, Z, P, Q, Bv, Tw, shift;
+  FftCtx<T> fft(const FftPlan& pl) const { FftCtx<T> f; f.plan = pl; f.tw = tw.as<cplx<T>>(); return f; }
+  void release() {
+    DevBuf* all[] = {&tw, &psi, &psi_r, &v_r, &X, &R, &Z, &P, &Q, &Bv, &Tw, &shift};
+    for (DevBuf* b : all) b->release();
+  }
+};
+
+}  // namespace
+
+struct wgw_ctx {
+  double L = 0, ecut = 0, omega_cell = 0;
+  int N = 0, n_v = 0;
+  long ld_w = 0, ld_r = 0, grid3 = 0;
+  wgw_options opt{};
+  FftPlan plan{};
+  HostSphere wfc, rho;
+  std::vector<double> e_v;
+  Prec<double> d;
+  Prec<float> f;
+  DevBuf e_v_d;
+  // apply work space (double unless noted)
+  DevBuf dvin, dv_rb, dv_r, Trho, Dr, drho_rb, eps, a_idx, b_idx, brow, cg_rz, cg_bb, cg_rr,
+      cg_act, cg_it, cnt, rr64, act64, norms;
+  cudaStream_t stream = nullptr;
+  ~wgw_ctx() {
+    d.release(); f.release(); wfc.release(); rho.release();
+    DevBuf* all[] = {&e_v_d, &dvin, &dv_rb, &dv_r, &Trho, &Dr, &drho_rb, &eps, &a_idx, &b_idx, &brow,
+                     &cg_rz, &cg_bb, &cg_rr, &cg_act, &cg_it, &cnt, &rr64, &act64, &norms};
+    for (DevBuf* b : all) b->release();
+    if (stream) cudaStreamDestroy(stream);
+  }
+};
+
+namespace {
+
+// Real-space function(s) of a batch of real-basis vectors of one sphere:
+// out[s] (N^3 reals, digit-reversed positions) for s < n_sys.
+template <typename T>
+int to_real(wgw_ctx* c, Prec<T>& pr, const HostSphere& sp, const T* X, long ldx, int n_sys, T* out,
+            DevBuf& tbuf, cudaStream_t st) {
+  const int N = c->N, NP = 2 * sp.m + 1, pairs = (n_sys + 1) / 2;
+  WGW_TRY(tbuf.ensure(sizeof(cplx<T>) * (size_t)pairs * NP * N * N));
+  FftCtx<T> f = pr.fft(c->plan);
+  WGW_CK(launch_plane_g2r<T>(sp.tab(), f, X, ldx, n_sys, nullptr, tbuf.as<cplx<T>>(), st));
+  XArgs<T> a{};
+  a.mode = XM_TO_REAL; a.R0 = out; a.R1 = out; a.ldr = c->grid3; a.n_sys = n_sys;
+  WGW_CK(launch_xline<T>(sp.m, f, tbuf.as<cplx<T>>(), a, nullptr, st));
+  return WGW_OK;
+}
+
+// Q = P_c (H - e_v) P  for the active systems (P already in range(P_c)).
+template <typename T>
+int apply_A(wgw_ctx* c, Prec<T>& pr, const T* P, T* Q, int n_sys, const int* active, cudaStream_t st) {
+  const int N = c->N, NP = 2 * c->wfc.m + 1, pairs = (n_sys + 1) / 2;
+  WGW_TRY(pr.Tw.ensure(sizeof(cplx<T>) * (size_t)pairs * NP * N * N));
+  FftCtx<T> f = pr.fft(c->plan);
+  cplx<T>* Tb = pr.Tw.template as<cplx<T>>();
+  WGW_CK(launch_plane_g2r<T>(c->wfc.tab(), f, P, c->ld_w, n_sys, active, Tb, st));
+  XArgs<T> a{};
+  a.mode = XM_APPLY_V; a.V = pr.v_r.template as<T>(); a.n_sys = n_sys;
+  WGW_CK(launch_xline<T>(c->wfc.m, f, Tb, a, active, st));
+  Epi<T> e{};
+  e.out = Q; e.ldo = c->ld_w; e.pin = P; e.ldp = c->ld_w; e.vcoef = T(1); e.kin = T(1);
+  e.shift = pr.shift.template as<T>(); e.n_sys = n_sys; e.active = active;
+  WGW_CK(launch_plane_r2g<T>(c->wfc.tab(), c->wfc.npt_max, f, Tb, e, st));
+  WGW_CK(launch_pc<T>(Q, c->ld_w, n_sys, pr.psi.template as<T>(), c->ld_w, c->wfc.nrb(), c->n_v, active, st));
+  return WGW_OK;
+}
+
+CgState cg_state(wgw_ctx* c) {
+  CgState s;
+  s.rz = c->cg_rz.as<double>(); s.bb = c->cg_bb.as<double>(); s.rr = c->cg_rr.as<double>();
+  s.active = c->cg_act.as<int>(); s.iters = c->cg_it.as<int>();
+  return s;
+}
+
+int count_active(wgw_ctx* c, const int* flags, int n, cudaStream_t st, int* out) {
+  WGW_CK(launch_count(flags, n, c->cnt.as<int>(), st));
+  WGW_CK(cudaMemcpyAsync(out, c->cnt.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  WGW_CK(cudaStreamSynchronize(st));
+  return WGW_OK;
+}
+
+// Preconditioned CG on A x = b for all systems (b in pr.Bv, x into pr.X), to relative residual tol.
+template <typename T>
+int cg_solve(wgw_ctx* c, Prec<T>& pr, int n_sys, double tol, int max_iter, cudaStream_t st) {
+  const int n = c->wfc.nrb();
+  const long ld = c->ld_w;
+  T* X = pr.X.template as<T>();
+  T* R = pr.R.template as<T>();
+  T* Z = pr.Z.template as<T>();
+  T* P = pr.P.template as<T>();
+  T* Q = pr.Q.template as<T>();
+  const T* Bv = pr.Bv.template as<T>();
+  const T* Psi = pr.psi.template as<T>();
+  const double* eps = c->eps.as<double>();
+  CgState cs = cg_state(c);
+  const int* act = cs.active;
+  WGW_CK(launch_cg_init_a<T>(c->wfc.tab(), n, n_sys, Bv, X, R, Z, ld, eps, cs, st));
+  WGW_CK(launch_pc<T>(Z, ld, n_sys, Psi, ld, n, c->n_v, act, st));
+  WGW_CK(launch_cg_init_b<T>(n, n_sys, R, Z, P, ld, cs, st));
+  const int every = std::max(1, c->opt.check_every);
+  for (int it = 0; it < max_iter; ++it) {
+    WGW_TRY(apply_A<T>(c, pr, P, Q, n_sys, act, st));
+    WGW_CK(launch_cg_step_a<T>(c->wfc.tab(), n, n_sys, X, R, Z, P, Q, ld, eps, cs, tol * tol, max_iter, st));
+    WGW_CK(launch_pc<T>(Z, ld, n_sys, Psi, ld, n, c->n_v, act, st));
+    WGW_CK(launch_cg_step_b<T>(n, n_sys, R, Z, P, ld, cs, st));
+    if ((it + 1) % every == 0 || it + 1 == max_iter) {
+      int na = 0;
+      WGW_TRY(count_active(c, act, n_sys, st, &na));
+      if (na == 0) break;
+    }
+  }
+  return WGW_OK;
+}
+
+int ensure_work(wgw_ctx* c, int n_sys, int n_real) {
+  const size_t vb = (size_t)n_sys * c->ld_w;
+  DevBuf* dv[] = {&c->d.X, &c->d.R, &c->d.Z, &c->d.P, &c->d.Q, &c->d.Bv};
+  for (DevBuf* b : dv) WGW_TRY(b->ensure(sizeof(double) * vb));
+  WGW_TRY(c->d.shift.ensure(sizeof(double) * n_sys));
+  if (c->opt.precision == WGW_MIXED) {
+    DevBuf* fv[] = {&c->f.X, &c->f.R, &c->f.Z, &c->f.P, &c->f.Q, &c->f.Bv};
+    for (DevBuf* b : fv) WGW_TRY(b->ensure(sizeof(float) * vb));
+    WGW_TRY(c->f.shift.ensure(sizeof(float) * n_sys));
+  }
+  WGW_TRY(c->eps.ensure(sizeof(double) * n_sys));
+  WGW_TRY(c->a_idx.ensure(sizeof(int) * n_sys));
+  WGW_TRY(c->b_idx.ensure(sizeof(int) * n_sys));
+  WGW_TRY(c->cg_rz.ensure(sizeof(double) * n_sys));
+  WGW_TRY(c->cg_bb.ensure(sizeof(double) * n_sys));
+  WGW_TRY(c->cg_rr.ensure(sizeof(double) * n_sys));
+  WGW_TRY(c->cg_act.ensure(sizeof(int) * n_sys));
+  WGW_TRY(c->cg_it.ensure(sizeof(int) * n_sys));
+  WGW_TRY(c->rr64.ensure(sizeof(double) * n_sys));
+  WGW_TRY(c->act64.ensure(sizeof(int) * n_sys));
+  WGW_TRY(c->cnt.ensure(sizeof(int) * 4));
+  WGW_TRY(c->dv_r.ensure(sizeof(double) * (size_t)n_real * c->grid3));
+  WGW_TRY(c->Dr.ensure(sizeof(double) * (size_t)n_real * c->grid3));
+  WGW_TRY(c->drho_rb.ensure(sizeof(double) * (size_t)n_real * c->ld_r));
+  return WGW_OK;
+}
+
+__global__ void k_residual_flags(int n_sys, const double* rr, const double* bb, double tol2, int* act) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n_sys) act[s] = (bb[s] > 0.0 && rr[s] > tol2 * bb[s]) ? 1 : 0;
+}
+
+// Solve all systems to cg_tol.  Right-hand sides in d.Bv; solutions into d.X.
+int solve_all(wgw_ctx* c, int n_sys, cudaStream_t st, wgw_stats* stats) {
+  const int n = c->wfc.nrb();
+  const long ld = c->ld_w;
+  const double tol = c->opt.cg_tol;
+  std::vector<int> iters_total(n_sys, 0);
+  int refinements = 0;
+  if (c->opt.precision == WGW_FP64) {
+    WGW_TRY(cg_solve<double>(c, c->d, n_sys, tol, c->opt.max_cg_iter, st));
+    WGW_CK(cudaMemcpyAsync(iters_total.data(), c->cg_it.p, sizeof(int) * n_sys, cudaMemcpyDeviceToHost, st));
+  } else {
+    // Iterative refinement: x = 0, r = b; repeat { inner FP32 CG on A e = r; x += e; r = b - A x (FP64) }.
+    double* X = c->d.X.as<double>();
+    double* R = c->d.R.as<double>();
+    double* Q = c->d.Q.as<double>();
+    const double* Bv = c->d.Bv.as<double>();
+    WGW_CK(cudaMemsetAsync(X, 0, sizeof(double) * (size_t)n_sys * ld, st));
+    WGW_CK(cudaMemcpyAsync(R, Bv, sizeof(double) * (size_t)n_sys * ld, cudaMemcpyDeviceToDevice, st));
+    WGW_CK(launch_norm2<double>(n_sys, n, Bv, ld, c->cg_bb.as<double>(), st));
+    std::vector<int> it_host(n_sys);
+    // Keep the FP64 |b|^2 aside: the inner solves overwrite cg_bb.
+    WGW_TRY(c->norms.ensure(sizeof(double) * n_sys));
+    double* bb64 = c->norms.as<double>();
+    WGW_CK(cudaMemcpyAsync(bb64, c->cg_bb.p, sizeof(double) * n_sys, cudaMemcpyDeviceToDevice, st));
+    int* act64 = c->act64.as<int>();
+    for (int k = 0; k < c->opt.max_refine; ++k) {
+      WGW_CK(launch_norm2<double>(n_sys, n, R, ld, c->rr64.as<double>(), st));
+      k_residual_flags<<<(n_sys + 255) / 256, 256, 0, st>>>(n_sys, c->rr64.as<double>(), bb64, tol * tol, act64);
+      WGW_CK(cudaGetLastError());
+      int na = 0;
+      WGW_TRY(count_active(c, act64, n_sys, st, &na));
+      if (na == 0) break;
+      ++refinements;
+      // Inner right-hand side: the FP32 image of r (only active systems; others get b = 0).
+      WGW_CK(cudaMemsetAsync(c->f.Bv.p, 0, sizeof(float) * (size_t)n_sys * ld, st));
+      WGW_CK((launch_copy_cast<double, float>(n_sys, n, R, ld, c->f.Bv.as<float>(), ld, act64, st)));
+      WGW_TRY(cg_solve<float>(c, c->f, n_sys, c->opt.inner_tol, c->opt.max_cg_iter, st));
+      WGW_CK(cudaMemcpyAsync(it_host.data(), c->cg_it.p, sizeof(int) * n_sys, cudaMemcpyDeviceToHost, st));
+      WGW_CK(cudaStreamSynchronize(st));
+      for (int s = 0; s < n_sys; ++s) iters_total[s] += it_host[s];
+      WGW_CK(launch_add_to<float>(n_sys, n, c->f.X.as<float>(), ld, X, ld, act64, st));
+      // The FP32 correction carries an O(eps_32) component along the occupied
+      // states, which P_c (H - e_v) cannot see; the solution lies in range(P_c),
+      // so project it out in FP64.
+      WGW_CK(launch_pc<double>(X, ld, n_sys, c->d.psi.as<double>(), ld, n, c->n_v, act64, st));
+      // r = b - A x in FP64 for the systems that moved.
+      WGW_TRY(apply_A<double>(c, c->d, X, Q, n_sys, act64, st));
+      WGW_CK(launch_axpby(n_sys, n, 1.0, Bv, -1.0, Q, R, ld, act64, st));
+    }
+  }
+  // Final FP64 residual of every system (independent check of the stopping rule).
+  {
+    double* X = c->d.X.as<double>();
+    WGW_CK(launch_pc<double>(X, ld, n_sys, c->d.psi.as<double>(), ld, n, c->n_v, nullptr, st));
+    double* Q = c->d.Q.as<double>();
+    double* R = c->d.R.as<double>();
+    WGW_TRY(apply_A<double>(c, c->d, X, Q, n_sys, nullptr, st));
+    WGW_CK(launch_axpby(n_sys, n, 1.0, c->d.Bv.as<double>(), -1.0, Q, R, ld, nullptr, st));
+    WGW_CK(launch_norm2<double>(n_sys, n, R, ld, c->rr64.as<double>(), st));
+    WGW_CK(launch_norm2<double>(n_sys, n, c->d.Bv.as<double>(), ld, c->cg_bb.as<double>(), st));
+  }
+  std::vector<double> rr(n_sys), bb(n_sys);
+  WGW_CK(cudaMemcpyAsync(rr.data(), c->rr64.p, sizeof(double) * n_sys, cudaMemcpyDeviceToHost, st));
+  WGW_CK(cudaMemcpyAsync(bb.data(), c->cg_bb.p, sizeof(double) * n_sys, cudaMemcpyDeviceToHost, st));
+  WGW_CK(cudaStreamSynchronize(st));
+  int conv = 0, maxit = 0;
+  double maxrel = 0.0;
+  for (int s = 0; s < n_sys; ++s) {
+    const double rel = bb[s] > 0 ? std::sqrt(rr[s] / bb[s]) : 0.0;
+    maxrel = std::max(maxrel, rel);
+    if (rel <= tol * (1.0 + 1e-6) || bb[s] == 0.0) ++conv;
+    maxit = std::max(maxit, iters_total[s]);
+  }
+  if (stats) {
+    stats->n_systems = n_sys;
+    stats->n_converged = conv;
+    stats->max_iters = maxit;
+    stats->refinements = refinements;
+    stats->max_rel_residual = maxrel;
+  }
+  return conv == n_sys ? WGW_OK : fail(WGW_ERR_NOCONV, "some Sternheimer systems missed cg_tol");
+}
+
+// Core of chi0 / chibar0 application; dV and drho in device memory.
+int apply_core(wgw_ctx* c, const double* dV, int n_pert, const double* omega, int n_omega,
+               double* drho, bool symmetrized, cudaStream_t st, wgw_stats* stats) {
+  if (!c) return fail(WGW_ERR_ARG, "null context");
+  if (n_pert < 0 || n_omega < 1 || !omega) return fail(WGW_ERR_ARG, "need n_pert >= 0 and n_omega >= 1");
+  for (int k = 0; k < n_omega; ++k)
+    if (omega[k] != 0.0) return fail(WGW_ERR_ARG, "this version applies chi0 at omega = 0 only");
+  if (n_pert == 0) return WGW_OK;
+  if (!dV || !drho) return fail(WGW_ERR_ARG, "null dV or drho");
+  const int N = c->N, n_v = c->n_v;
+  const long ldr = c->ld_r, ldw = c->ld_w;
+  const HostSphere& rs = c->rho;
+  const double* scale = symmetrized ? rs.d_vsqrt.as<double>() : nullptr;
+  // 1. Real-in-r parts of each perturbation: rows [0, n_pert) = Hermitian parts,
+  //    rows n_pert + k = the non-zero anti-Hermitian parts.
+  WGW_TRY(c->dv_rb.ensure(sizeof(double) * (size_t)2 * n_pert * ldr));
+  double* dvrb = c->dv_rb.as<double>();
+  WGW_CK(cudaMemsetAsync(dvrb, 0, sizeof(double) * (size_t)2 * n_pert * ldr, st));
+  WGW_CK(launch_sphere_to_rb(n_pert, dV, 2L * rs.n, scale, rs.map(), 0, dvrb, ldr, st));
+  WGW_CK(launch_sphere_to_rb(n_pert, dV, 2L * rs.n, scale, rs.map(), 1, dvrb + (size_t)n_pert * ldr, ldr, st));
+  WGW_TRY(c->norms.ensure(sizeof(double) * 2 * n_pert));
+  WGW_CK(launch_norm2<double>(2 * n_pert, rs.nrb(), dvrb, ldr, c->norms.as<double>(), st));
+  std::vector<double> nrm(2 * n_pert);
+  WGW_CK(cudaMemcpyAsync(nrm.data(), c->norms.p, sizeof(double) * 2 * n_pert, cudaMemcpyDeviceToHost, st));
+  WGW_CK(cudaStreamSynchronize(st));
+  std::vector<int> brow(n_pert, -1);
+  int n_real = n_pert;
+  for (int p = 0; p < n_pert; ++p) {
+    if (nrm[n_pert + p] > 0.0) {
+      if (n_real != n_pert + p)
+        WGW_CK(cudaMemcpyAsync(dvrb + (size_t)n_real * ldr, dvrb + (size_t)(n_pert + p) * ldr,
+                               sizeof(double) * ldr, cudaMemcpyDeviceToDevice, st));
+      brow[p] = n_real++;
+    }
+  }
+  const int n_sys = n_real * n_v;
+  WGW_TRY(ensure_work(c, n_sys, n_real));
+  // 2. System tables: s = r * n_v + v.
+  std::vector<double> eps(n_sys), shift(n_sys);
+  std::vector<float> shiftf(n_sys);
+  std::vector<int> ai(n_sys), bi(n_sys);
+  for (int r = 0; r < n_real; ++r)
+    for (int v = 0; v < n_v; ++v) {
+      const int s = r * n_v + v;
+      eps[s] = c->e_v[v];
+      shift[s] = -c->e_v[v];
+      shiftf[s] = (float)shift[s];
+      ai[s] = v;
+      bi[s] = r;
+    }
+  WGW_CK(cudaMemcpyAsync(c->eps.p, eps.data(), sizeof(double) * n_sys, cudaMemcpyHostToDevice, st));
+  WGW_CK(cudaMemcpyAsync(c->d.shift.p, shift.data(), sizeof(double) * n_sys, cudaMemcpyHostToDevice, st));
+  if (c->opt.precision == WGW_MIXED)
+    WGW_CK(cudaMemcpyAsync(c->f.shift.p, shiftf.data(), sizeof(float) * n_sys, cudaMemcpyHostToDevice, st));
+  WGW_CK(cudaMemcpyAsync(c->a_idx.p, ai.data(), sizeof(int) * n_sys, cudaMemcpyHostToDevice, st));
+  WGW_CK(cudaMemcpyAsync(c->b_idx.p, bi.data(), sizeof(int) * n_sys, cudaMemcpyHostToDevice, st));
+  WGW_TRY(c->brow.ensure(sizeof(int) * n_pert));
+  WGW_CK(cudaMemcpyAsync(c->brow.p, brow.data(), sizeof(int) * n_pert, cudaMemcpyHostToDevice, st));
+  // 3. dV_r(r) for every real perturbation.
+  double* dvr = c->dv_r.as<double>();
+  WGW_TRY(to_real<double>(c, c->d, rs, dvrb, ldr, n_real, dvr, c->Trho, st));
+  // 4. Right-hand sides b_s = -P_c [psi_v(r) dV_r(r)] on the wavefunction sphere.
+  {
+    const int NP = 2 * c->wfc.m + 1, pairs = (n_sys + 1) / 2;
+    WGW_TRY(c->d.Tw.ensure(sizeof(cplx<double>) * (size_t)pairs * NP * N * N));
+    FftCtx<double> f = c->d.fft(c->plan);
+    XArgs<double> a{};
+    a.mode = XM_FROM_REAL; a.A = c->d.psi_r.as<double>(); a.lda = c->grid3; a.a_index = c->a_idx.as<int>();
+    a.Bm = dvr; a.ldb = c->grid3; a.b_index = c->b_idx.as<int>(); a.n_sys = n_sys;
+    WGW_CK(launch_xline<double>(c->wfc.m, f, c->d.Tw.as<cplx<double>>(), a, nullptr, st));
+    Epi<double> e{};
+    e.out = c->d.Bv.as<double>(); e.ldo = ldw; e.vcoef = -1.0; e.n_sys = n_sys;
+    WGW_CK(launch_plane_r2g<double>(c->wfc.tab(), c->wfc.npt_max, f, c->d.Tw.as<cplx<double>>(), e, st));
+    WGW_CK(launch_pc<double>(c->d.Bv.as<double>(), ldw, n_sys, c->d.psi.as<double>(), ldw, c->wfc.nrb(), n_v, nullptr, st));
+  }
+  // 5. Sternheimer solves.
+  const int solve_status = solve_all(c, n_sys, st, stats);
+  if (solve_status != WGW_OK && solve_status != WGW_ERR_NOCONV) return solve_status;
+  // 6. drho_r(r) = (2 f_s / Omega) sum_v psi_v(r) x_{v r}(r), then to the density sphere.
+  {
+    const int NP = 2 * c->wfc.m + 1, pairs = (n_sys + 1) / 2;
+    WGW_TRY(c->d.Tw.ensure(sizeof(cplx<double>) * (size_t)pairs * NP * N * N));
+    FftCtx<double> f = c->d.fft(c->plan);
+    WGW_CK(launch_plane_g2r<double>(c->wfc.tab(), f, c->d.X.as<double>(), ldw, n_sys, nullptr,
+                                    c->d.Tw.as<cplx<double>>(), st));
+    const double coef = 2.0 * c->opt.f_s / c->omega_cell;
+    WGW_CK(launch_drho_xline<double>(c->wfc.m, f, c->d.Tw.as<cplx<double>>(), c->d.psi_r.as<double>(),
+                                     c->grid3, n_v, n_sys, n_real, coef, c->Dr.as<double>(), c->grid3, st));
+    const int NPr = 2 * rs.m + 1, rpairs = (n_real + 1) / 2;
+    WGW_TRY(c->Trho.ensure(sizeof(cplx<double>) * (size_t)rpairs * NPr * N * N));
+    XArgs<double> a{};
+    a.mode = XM_FROM_REAL; a.A = c->Dr.as<double>(); a.lda = c->grid3; a.n_sys = n_real;
+    WGW_CK(launch_xline<double>(rs.m, f, c->Trho.as<cplx<double>>(), a, nullptr, st));
+    Epi<double> e{};
+    e.out = c->drho_rb.as<double>(); e.ldo = ldr; e.vcoef = 1.0; e.n_sys = n_real;
+    WGW_CK(launch_plane_r2g<double>(rs.tab(), rs.npt_max, f, c->Trho.as<cplx<double>>(), e, st));
+  }
+  // 7. Complex output drho_p = chi0 A_p + i chi0 B_p for every frequency (all omega = 0 here).
+  for (int k = 0; k < n_omega; ++k)
+    WGW_CK(launch_rb_to_sphere(n_pert, c->drho_rb.as<double>(), ldr, c->brow.as<int>(), scale, rs.map(),
+                               drho + (size_t)k * n_pert * 2 * rs.n, 2L * rs.n, st));
+  WGW_CK(cudaStreamSynchronize(st));
+  return solve_status;
+}
+
+}  // namespace
+
+extern "C" {
+
+int wgw_default_options(wgw_options* opt) {
+  if (!opt) return fail(WGW_ERR_ARG, "null options");
+  opt->precision = WGW_FP64;
+  opt->cg_tol = 1e-12;
+  opt->max_cg_iter = 2000;
+  opt->max_refine = 8;
+  opt->inner_tol = 1e-4;
+  opt->f_s = 2.0;
+  opt->check_every = 8;
+  return WGW_OK;
+}
+
+static int check_options(const wgw_options& o) {
+  if (o.precision != WGW_FP64 && o.precision != WGW_MIXED) return fail(WGW_ERR_ARG, "bad precision");
+  if (!(o.cg_tol > 0) || !(o.inner_tol > 0) || o.max_cg_iter < 1 || o.max_refine < 1 || !(o.f_s > 0))
+    return fail(WGW_ERR_ARG, "bad tolerances or iteration limits");
+  return WGW_OK;
+}
+
+int wgw_set_options(wgw_ctx* c, const wgw_options* opt) {
+  if (!c || !opt) return fail(WGW_ERR_ARG, "null argument");
+  WGW_TRY(check_options(*opt));
+  c->opt = *opt;
+  return WGW_OK;
+}
+
+static int setup_impl(wgw_ctx* c, const double* vloc_G, const double* psi_v, const double* e_v) {
+  const int N = c->N;
+  if (!make_plan(N, c->plan)) return fail(WGW_ERR_ARG, "grid must be a product of 2, 3 and 5");
+  build_sphere(c->L, c->ecut, N, c->wfc);
+  build_sphere(c->L, 4.0 * c->ecut, N, c->rho);
+  if (N <= 2 * c->rho.m) return fail(WGW_ERR_ARG, "grid too small: need grid > 2 * max |Miller| of the density sphere");
+  if (N > 255) return fail(WGW_ERR_ARG, "grid above 255 points per axis");
+  if (c->n_v > c->wfc.n) return fail(WGW_ERR_ARG, "more occupied states than plane waves");
+  c->ld_w = pad32(c->wfc.nrb());
+  c->ld_r = pad32(c->rho.nrb());
+  c->grid3 = (long)N * N * N;
+  WGW_TRY(upload_sphere(c->wfc));
+  WGW_TRY(upload_sphere(c->rho));
+  WGW_CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+  cudaStream_t st = c->stream;
+  // Twiddles exp(+2 pi i k / N).
+  std::vector<cplx<double>> twd(N);
+  std::vector<cplx<float>> twf(N);
+  for (int k = 0; k < N; ++k) {
+    const double a = 2.0 * M_PI * k / N;
+    twd[k] = mk<double>(std::cos(a), std::sin(a));
+    twf[k] = mk<float>((float)twd[k].re, (float)twd[k].im);
+  }
+  WGW_TRY(upload(c->d.tw, twd));
+  WGW_TRY(upload(c->f.tw, twf));
+  c->e_v.assign(e_v, e_v + c->n_v);
+  WGW_TRY(upload(c->e_v_d, c->e_v));
+  // Occupied states: complex sphere -> real basis (checking they are real in r).
+  const int n_v = c->n_v;
+  DevBuf tmp;
+  WGW_TRY(tmp.ensure(sizeof(double) * (size_t)2 * std::max(c->wfc.n * n_v, c->rho.n)));
+  WGW_CK(cudaMemcpy(tmp.p, psi_v, sizeof(double) * 2 * (size_t)c->wfc.n * n_v, cudaMemcpyHostToDevice));
+  WGW_TRY(c->d.psi.ensure(sizeof(double) * (size_t)n_v * c->ld_w));
+  WGW_CK(cudaMemsetAsync(c->d.psi.p, 0, sizeof(double) * (size_t)n_v * c->ld_w, st));
+  WGW_CK(launch_sphere_to_rb(n_v, tmp.as<double>(), 2L * c->wfc.n, nullptr, c->wfc.map(), 0, c->d.psi.as<double>(), c->ld_w, st));
+  DevBuf anti;
+  WGW_TRY(anti.ensure(sizeof(double) * (size_t)std::max(n_v, 1) * std::max(c->ld_w, c->ld_r)));
+  WGW_CK(cudaMemsetAsync(anti.p, 0, anti.bytes, st));
+  WGW_CK(launch_sphere_to_rb(n_v, tmp.as<double>(), 2L * c->wfc.n, nullptr, c->wfc.map(), 1, anti.as<double>(), c->ld_w, st));
+  DevBuf nrm;
+  WGW_TRY(nrm.ensure(sizeof(double) * 2 * (n_v + 1)));
+  WGW_CK(launch_norm2<double>(n_v, c->wfc.nrb(), c->d.psi.as<double>(), c->ld_w, nrm.as<double>(), st));
+  WGW_CK(launch_norm2<double>(n_v, c->wfc.nrb(), anti.as<double>(), c->ld_w, nrm.as<double>() + n_v, st));
+  std::vector<double> h(2 * n_v);
+  WGW_CK(cudaMemcpyAsync(h.data(), nrm.p, sizeof(double) * 2 * n_v, cudaMemcpyDeviceToHost, st));
+  WGW_CK(cudaStreamSynchronize(st));
+  for (int v = 0; v < n_v; ++v) {
+    if (std::fabs(h[v] - 1.0) > 1e-8) { tmp.release(); anti.release(); nrm.release(); return fail(WGW_ERR_ARG, "psi_v not normalised"); }
+    if (h[n_v + v] > 1e-20) { tmp.release(); anti.release(); nrm.release(); return fail(WGW_ERR_ARG, "psi_v not real in r (psi(-G) != psi(G)^*)"); }
+  }
+  WGW_TRY(c->f.psi.ensure(sizeof(float) * (size_t)n_v * c->ld_w));
+  WGW_CK((launch_copy_cast<double, float>(n_v, (int)c->ld_w, c->d.psi.as<double>(), c->ld_w, c->f.psi.as<float>(), c->ld_w, nullptr, st)));
+  // psi_v(r).
+  WGW_TRY(c->d.psi_r.ensure(sizeof(double) * (size_t)n_v * c->grid3));
+  WGW_TRY(to_real<double>(c, c->d, c->wfc, c->d.psi.as<double>(), c->ld_w, n_v, c->d.psi_r.as<double>(), c->d.Tw, st));
+  WGW_TRY(c->f.psi_r.ensure(sizeof(float) * (size_t)n_v * c->grid3));
+  WGW_CK((launch_copy_cast<double, float>(n_v, (int)c->grid3, c->d.psi_r.as<double>(), c->grid3, c->f.psi_r.as<float>(), c->grid3, nullptr, st)));
+  // V_loc(r).
+  WGW_CK(cudaMemcpy(tmp.p, vloc_G, sizeof(double) * 2 * (size_t)c->rho.n, cudaMemcpyHostToDevice));
+  DevBuf vrb;
+  WGW_TRY(vrb.ensure(sizeof(double) * c->ld_r));
+  WGW_CK(cudaMemsetAsync(vrb.p, 0, sizeof(double) * c->ld_r, st));
+  WGW_CK(launch_sphere_to_rb(1, tmp.as<double>(), 2L * c->rho.n, nullptr, c->rho.map(), 0, vrb.as<double>(), c->ld_r, st));
+  WGW_CK(cudaMemsetAsync(anti.p, 0, anti.bytes, st));
+  WGW_CK(launch_sphere_to_rb(1, tmp.as<double>(), 2L * c->rho.n, nullptr, c->rho.map(), 1, anti.as<double>(), c->ld_r, st));
+  WGW_CK(launch_norm2<double>(1, c->rho.nrb(), vrb.as<double>(), c->ld_r, nrm.as<double>(), st));
+  WGW_CK(launch_norm2<double>(1, c->rho.nrb(), anti.as<double>(), c->ld_r, nrm.as<double>() + 1, st));
+  WGW_CK(cudaMemcpyAsync(h.data(), nrm.p, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
+  WGW_CK(cudaStreamSynchronize(st));
+  if (h[1] > 1e-24 * std::max(1.0, h[0])) { tmp.release(); anti.release(); nrm.release(); vrb.release(); return fail(WGW_ERR_ARG, "vloc_G not real in r"); }
+  WGW_TRY(c->d.v_r.ensure(sizeof(double) * c->grid3));
+  DevBuf tr;
+  WGW_TRY(to_real<double>(c, c->d, c->rho, vrb.as<double>(), c->ld_r, 1, c->d.v_r.as<double>(), tr, st));
+  WGW_TRY(c->f.v_r.ensure(sizeof(float) * c->grid3));
+  WGW_CK((launch_copy_cast<double, float>(1, (int)c->grid3, c->d.v_r.as<double>(), c->grid3, c->f.v_r.as<float>(), c->grid3, nullptr, st)));
+  WGW_CK(cudaStreamSynchronize(st));
+  tmp.release(); anti.release(); nrm.release(); vrb.release(); tr.release();
+  return WGW_OK;
+}
+
+int wgw_setup(wgw_ctx** out, double L, double ecut, int grid, const double* vloc_G, int n_proj,
+              const double* beta_G, const double* d_proj, const double* psi_v, const double* e_v,
+              int n_v, const wgw_options* opt) {
+  g_last_error.clear();
+  if (!out) return fail(WGW_ERR_ARG, "null output pointer");
+  *out = nullptr;
+  if (!(L > 0) || !(ecut > 0) || grid < 4 || n_v < 1 || !vloc_G || !psi_v || !e_v)
+    return fail(WGW_ERR_ARG, "invalid L, ecut, grid, n_v or null input");
+  if (n_proj != 0) return fail(WGW_ERR_ARG, "Kleinman-Bylander projectors are not supported by this version");
+  (void)beta_G; (void)d_proj;
+  wgw_options o;
+  wgw_default_options(&o);
+  if (opt) o = *opt;
+  WGW_TRY(check_options(o));
+  wgw_ctx* c = new wgw_ctx();
+  c->L = L; c->ecut = ecut; c->N = grid; c->n_v = n_v; c->omega_cell = L * L * L; c->opt = o;
+  const int s = setup_impl(c, vloc_G, psi_v, e_v);
+  if (s != WGW_OK) { delete c; return s; }
+  *out = c;
+  return WGW_OK;
+}
+
+int wgw_sphere_size(const wgw_ctx* c, int which, int* n) {
+  if (!c || !n || (which != WGW_SPHERE_WFC && which != WGW_SPHERE_RHO)) return fail(WGW_ERR_ARG, "bad argument");
+  *n = which == WGW_SPHERE_WFC ? c->wfc.n : c->rho.n;
+  return WGW_OK;
+}
+
+int wgw_get_gvectors(const wgw_ctx* c, int which, int32_t* miller) {
+  if (!c || !miller || (which != WGW_SPHERE_WFC && which != WGW_SPHERE_RHO)) return fail(WGW_ERR_ARG, "bad argument");
+  const HostSphere& s = which == WGW_SPHERE_WFC ? c->wfc : c->rho;
+  for (int i = 0; i < 3 * s.n; ++i) miller[i] = s.miller[i];
+  return WGW_OK;
+}
+
+int wgw_apply_chi0_dev(wgw_ctx* c, const double* dV_dev, int n_pert, const double* omega, int n_omega,
+                       double* drho_dev, void* stream, wgw_stats* st) {
+  g_last_error.clear();
+  return apply_core(c, dV_dev, n_pert, omega, n_omega, drho_dev, false, (cudaStream_t)stream, st);
+}
+
+int wgw_apply_chibar0_dev(wgw_ctx* c, const double* phi_dev, int n_pert, const double* omega,
+                          int n_omega, double* out_dev, void* stream, wgw_stats* st) {
+  g_last_error.clear();
+  return apply_core(c, phi_dev, n_pert, omega, n_omega, out_dev, true, (cudaStream_t)stream, st);
+}
+
+int wgw_apply_chi0(wgw_ctx* c, const double* dV, int n_pert, const double* omega, int n_omega,
+                   double* drho, wgw_stats* st) {
+  g_last_error.clear();
+  if (!c) return fail(WGW_ERR_ARG, "null context");
+  if (n_pert <= 0) return n_pert == 0 ? WGW_OK : fail(WGW_ERR_ARG, "n_pert < 0");
+  if (n_omega < 1) return fail(WGW_ERR_ARG, "n_omega < 1");
+  if (!dV || !drho) return fail(WGW_ERR_ARG, "null dV or drho");
+  const size_t in_b = sizeof(double) * 2 * (size_t)c->rho.n * n_pert;
+  const size_t out_b = in_b * n_omega;
+  WGW_TRY(c->dvin.ensure(in_b + out_b));
+  double* din = c->dvin.as<double>();
+  double* dout = din + 2 * (size_t)c->rho.n * n_pert;
+  WGW_CK(cudaMemcpyAsync(din, dV, in_b, cudaMemcpyHostToDevice, c->stream));
+  const int s = apply_core(c, din, n_pert, omega, n_omega, dout, false, c->stream, st);
+  if (s != WGW_OK && s != WGW_ERR_NOCONV) return s;
+  WGW_CK(cudaMemcpyAsync(drho, dout, out_b, cudaMemcpyDeviceToHost, c->stream));
+  WGW_CK(cudaStreamSynchronize(c->stream));
+  return s;
+}
+
+void wgw_destroy(wgw_ctx* c) { delete c; }
+
+const char* wgw_status_string(int s) {
+  switch (s) {
+    case WGW_OK: return "ok";
+    case WGW_ERR_ARG: return "invalid argument";
+    case WGW_ERR_NOMEM: return "device allocation failed";
+    case WGW_ERR_NOCONV: return "Sternheimer solve did not converge";
+    case WGW_ERR_CUDA: return "CUDA error";
+    case WGW_ERR_TIMEOUT: return "bounded device wait timed out";
+    case WGW_ERR_STATE: return "invalid state";
+    default: return "unknown status";
+  }
+}
+
+const char* wgw_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

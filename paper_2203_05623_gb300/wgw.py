@@ -1,0 +1,196 @@
+"""ctypes binding of libwgw (include/wgw.h): argument marshalling only.
+
+Every step of the response calculation runs in the library's CUDA kernels;
+this module converts numpy / torch arrays to the C layouts (interleaved
+complex, column-major per perturbation) and raises WgwError on failure.  It
+never computes a result itself and fails loudly when libwgw.so is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+WGW_OK, WGW_ERR_ARG, WGW_ERR_NOMEM, WGW_ERR_NOCONV = 0, 1, 2, 3
+WGW_ERR_CUDA, WGW_ERR_TIMEOUT, WGW_ERR_STATE = 4, 5, 6
+WGW_FP64, WGW_MIXED = 0, 1
+WGW_SPHERE_WFC, WGW_SPHERE_RHO = 0, 1
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class WgwError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: status {status} ({msg})")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("cg_tol", ctypes.c_double),
+                ("max_cg_iter", ctypes.c_int), ("max_refine", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("f_s", ctypes.c_double),
+                ("check_every", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_systems", ctypes.c_int), ("n_converged", ctypes.c_int),
+                ("max_iters", ctypes.c_int), ("refinements", ctypes.c_int),
+                ("max_rel_residual", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib(path: str | None = None):
+    """The loaded libwgw.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libwgw.so not found at {path}: run paper_2203_05623_gb300.build.build() "
+                           "(the CUDA library is required; there is no other execution path)")
+    L = ctypes.CDLL(path)
+    L.wgw_default_options.argtypes = [ctypes.POINTER(Options)]
+    L.wgw_setup.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_double, ctypes.c_double,
+                            ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp, _dp, ctypes.c_int,
+                            ctypes.POINTER(Options)]
+    L.wgw_sphere_size.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    L.wgw_get_gvectors.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int32)]
+    L.wgw_set_options.argtypes = [ctypes.c_void_p, ctypes.POINTER(Options)]
+    L.wgw_apply_chi0.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, _dp, ctypes.c_int, _dp,
+                                 ctypes.POINTER(Stats)]
+    L.wgw_apply_chi0_dev.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, _dp,
+                                     ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.POINTER(Stats)]
+    L.wgw_apply_chibar0_dev.argtypes = L.wgw_apply_chi0_dev.argtypes
+    L.wgw_destroy.argtypes = [ctypes.c_void_p]
+    L.wgw_status_string.restype = ctypes.c_char_p
+    L.wgw_status_string.argtypes = [ctypes.c_int]
+    L.wgw_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(status: int, where: str, allow=(WGW_OK,)):
+    if status not in allow:
+        raise WgwError(status, where, lib().wgw_last_error().decode())
+    return status
+
+
+def _interleave(a: np.ndarray) -> np.ndarray:
+    """Complex array -> contiguous float64 (re, im) with the first axis fastest after re/im."""
+    a = np.asarray(a, np.complex128)
+    return np.ascontiguousarray(a.T).view(np.float64).ravel()
+
+
+def wgw_default_options(**overrides) -> Options:
+    o = Options()
+    _check(lib().wgw_default_options(ctypes.byref(o)), "wgw_default_options")
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+class Context:
+    """Owner of a wgw_ctx*; destroyed with wgw_destroy."""
+
+    def __init__(self, handle, n_pw, n_rho, n_v):
+        self.handle, self.n_pw, self.n_rho, self.n_v = handle, n_pw, n_rho, n_v
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            wgw_destroy(self)
+
+
+def wgw_setup(L, ecut, grid, vloc_G, psi_v, e_v, opt: Options | None = None, beta_G=None,
+              d_proj=None) -> Context:
+    psi_v = np.asarray(psi_v, np.complex128)
+    n_v = psi_v.shape[1]
+    v = _interleave(vloc_G)
+    ps = _interleave(psi_v)
+    ev = np.ascontiguousarray(e_v, np.float64)
+    n_proj = 0 if beta_G is None else np.asarray(beta_G).shape[1]
+    bg = _interleave(beta_G) if n_proj else None
+    dp = np.ascontiguousarray(d_proj, np.float64) if n_proj else None
+    h = ctypes.c_void_p()
+    _check(lib().wgw_setup(ctypes.byref(h), float(L), float(ecut), int(grid), v.ctypes.data_as(_dp),
+                           n_proj, bg.ctypes.data_as(_dp) if n_proj else None,
+                           dp.ctypes.data_as(_dp) if n_proj else None, ps.ctypes.data_as(_dp),
+                           ev.ctypes.data_as(_dp), n_v, ctypes.byref(opt) if opt else None),
+           "wgw_setup")
+    n_pw, n_rho = ctypes.c_int(), ctypes.c_int()
+    lib().wgw_sphere_size(h, WGW_SPHERE_WFC, ctypes.byref(n_pw))
+    lib().wgw_sphere_size(h, WGW_SPHERE_RHO, ctypes.byref(n_rho))
+    return Context(h, n_pw.value, n_rho.value, n_v)
+
+
+def wgw_sphere_size(ctx: Context, which: int) -> int:
+    n = ctypes.c_int()
+    _check(lib().wgw_sphere_size(ctx.handle, which, ctypes.byref(n)), "wgw_sphere_size")
+    return n.value
+
+
+def wgw_get_gvectors(ctx: Context, which: int) -> np.ndarray:
+    n = wgw_sphere_size(ctx, which)
+    out = np.zeros((n, 3), np.int32)
+    _check(lib().wgw_get_gvectors(ctx.handle, which, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))),
+           "wgw_get_gvectors")
+    return out
+
+
+def wgw_set_options(ctx: Context, opt: Options):
+    _check(lib().wgw_set_options(ctx.handle, ctypes.byref(opt)), "wgw_set_options")
+
+
+def wgw_apply_chi0(ctx: Context, dV, omega=(0.0,), allow_noconv=False):
+    """Host arrays: dV (N_rho, n_pert) complex -> (drho (N_rho, n_pert, n_omega), stats dict, status)."""
+    dV = np.asarray(dV, np.complex128)
+    dV = dV[:, None] if dV.ndim == 1 else dV
+    n_pert = dV.shape[1]
+    om = np.ascontiguousarray(omega, np.float64)
+    buf = _interleave(dV)
+    out = np.zeros((len(om), n_pert, ctx.n_rho), np.complex128)
+    st = Stats()
+    s = lib().wgw_apply_chi0(ctx.handle, buf.ctypes.data_as(_dp), n_pert, om.ctypes.data_as(_dp), len(om),
+                             out.view(np.float64).ctypes.data_as(_dp), ctypes.byref(st))
+    _check(s, "wgw_apply_chi0", (WGW_OK, WGW_ERR_NOCONV) if allow_noconv else (WGW_OK,))
+    return out.transpose(2, 1, 0), st.as_dict(), s
+
+
+def _dev_call(fn, name, ctx, x, omega, out, stream, allow_noconv):
+    """x, out: torch complex128 CUDA tensors of shape (n_pert, N_rho) / (n_omega, n_pert, N_rho)."""
+    import torch
+    assert x.is_cuda and x.dtype == torch.complex128 and x.is_contiguous()
+    assert out.is_cuda and out.dtype == torch.complex128 and out.is_contiguous()
+    n_pert = x.shape[0]
+    om = np.ascontiguousarray(omega, np.float64)
+    st = Stats()
+    if stream is None:
+        stream = torch.cuda.current_stream(x.device).cuda_stream
+    s = fn(ctx.handle, ctypes.c_void_p(x.data_ptr()), n_pert, om.ctypes.data_as(_dp), len(om),
+           ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream), ctypes.byref(st))
+    _check(s, name, (WGW_OK, WGW_ERR_NOCONV) if allow_noconv else (WGW_OK,))
+    return st.as_dict(), s
+
+
+def wgw_apply_chi0_dev(ctx: Context, dV_dev, omega, drho_dev, stream=None, allow_noconv=False):
+    return _dev_call(lib().wgw_apply_chi0_dev, "wgw_apply_chi0_dev", ctx, dV_dev, omega, drho_dev, stream,
+                     allow_noconv)
+
+
+def wgw_apply_chibar0_dev(ctx: Context, phi_dev, omega, out_dev, stream=None, allow_noconv=False):
+    return _dev_call(lib().wgw_apply_chibar0_dev, "wgw_apply_chibar0_dev", ctx, phi_dev, omega, out_dev,
+                     stream, allow_noconv)
+
+
+def wgw_destroy(ctx: Context):
+    if ctx.handle:
+        lib().wgw_destroy(ctx.handle)
+        ctx.handle = None

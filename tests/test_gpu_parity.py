@@ -1,0 +1,165 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, on a GB300.
+
+Tolerances: FP64 path 1e-10, mixed path 1e-8, as the relative error
+||drho_gpu - drho_ref||_2 / ||drho_ref||_2 per perturbation (max over the batch).
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import chi0
+from oracle.model import Model
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def W():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_05623_gb300 import build
+    build.build()
+    import paper_2203_05623_gb300 as W
+    return W
+
+
+def model_of(s):
+    return Model(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, s.beta_G, s.d_proj)
+
+
+def rel_err(got, ref):
+    """max over perturbations (and frequencies) of ||got - ref|| / ||ref||."""
+    num = np.linalg.norm(got - ref, axis=0)
+    den = np.linalg.norm(ref, axis=0)
+    return float(np.max(num / np.where(den > 0, den, 1.0)))
+
+
+def setup(W, s, **opt):
+    o = W.wgw_default_options(**opt)
+    return W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, o)
+
+
+def test_gvectors_match_generator(W, cfg24):
+    ctx = setup(W, cfg24)
+    assert np.array_equal(W.wgw_get_gvectors(ctx, W.WGW_SPHERE_WFC), cfg24.miller_wfc)
+    assert np.array_equal(W.wgw_get_gvectors(ctx, W.WGW_SPHERE_RHO), cfg24.miller_rho)
+
+
+@pytest.fixture(scope="module")
+def ref24(cfg24):
+    dV = synth.perturbations(cfg24.miller_rho, cfg24.L, 8, 2)
+    return dV, chi0.sos_drho(model_of(cfg24), dV, [0.0])
+
+
+def test_chi0_fp64_matches_sum_over_states(W, cfg24, ref24):
+    dV, ref = ref24
+    ctx = setup(W, cfg24, precision=W.WGW_FP64, cg_tol=1e-13)
+    drho, st, status = W.wgw_apply_chi0(ctx, dV)
+    assert st["n_systems"] == 32 and st["n_converged"] == 32
+    assert rel_err(drho, ref) < 1e-10
+
+
+def test_chi0_mixed_matches_sum_over_states(W, cfg24, ref24):
+    dV, ref = ref24
+    ctx = setup(W, cfg24, precision=W.WGW_MIXED, cg_tol=1e-11)
+    drho, st, status = W.wgw_apply_chi0(ctx, dV)
+    assert st["refinements"] >= 2
+    assert rel_err(drho, ref) < 1e-8
+
+
+def test_complex_perturbation_by_linearity(W, tiny):
+    dV = synth.perturbations(tiny.miller_rho, tiny.L, 3, 11, hermitian=False)
+    ref = chi0.sos_drho(model_of(tiny), dV, [0.0])
+    ctx = setup(W, tiny, cg_tol=1e-13)
+    drho, st, _ = W.wgw_apply_chi0(ctx, dV)
+    assert st["n_systems"] == 2 * 3 * tiny.n_v
+    assert rel_err(drho, ref) < 1e-10
+
+
+def test_odd_system_count_and_ragged_pairs(W):
+    s = synth.make_system(synth.Config("odd", L=7.0, ecut=3.0, grid=16, n_wells=3, well_seed=21,
+                                       n_v=3, min_gap=0.05))
+    dV = synth.perturbations(s.miller_rho, s.L, 3, 5)       # 9 systems: the last pair is half empty
+    ref = chi0.sos_drho(model_of(s), dV, [0.0])
+    ctx = setup(W, s, cg_tol=1e-13)
+    drho, st, _ = W.wgw_apply_chi0(ctx, dV)
+    assert st["n_systems"] == 9
+    assert rel_err(drho, ref) < 1e-10
+
+
+def test_device_entry_point_matches_host_and_symmetrised(W, cfg24, ref24):
+    import torch
+    dV, ref = ref24
+    ctx = setup(W, cfg24, cg_tol=1e-13)
+    host, _, _ = W.wgw_apply_chi0(ctx, dV)
+    x = torch.from_numpy(np.ascontiguousarray(dV.T)).cuda()
+    out = torch.zeros((1, dV.shape[1], dV.shape[0]), dtype=torch.complex128, device="cuda")
+    W.wgw_apply_chi0_dev(ctx, x, [0.0], out)
+    torch.cuda.synchronize()
+    dev = out.cpu().numpy().transpose(2, 1, 0)
+    assert np.array_equal(dev, host)
+    # chibar0 phi = v^1/2 chi0 (v^1/2 phi)
+    m = model_of(cfg24)
+    phi = synth.perturbations(cfg24.miller_rho, cfg24.L, 3, 17)
+    o2 = torch.zeros((1, 3, dV.shape[0]), dtype=torch.complex128, device="cuda")
+    W.wgw_apply_chibar0_dev(ctx, torch.from_numpy(np.ascontiguousarray(phi.T)).cuda(), [0.0], o2)
+    torch.cuda.synchronize()
+    got = o2.cpu().numpy().transpose(2, 1, 0)
+    assert rel_err(got, chi0.apply_chibar0(m, phi, [0.0])) < 1e-10
+
+
+def test_zero_and_empty_batches(W, tiny):
+    ctx = setup(W, tiny)
+    z = np.zeros((tiny.n_rho, 2), np.complex128)
+    drho, st, _ = W.wgw_apply_chi0(ctx, z)
+    assert np.all(drho == 0)
+    drho, st, _ = W.wgw_apply_chi0(ctx, np.zeros((tiny.n_rho, 0), np.complex128))
+    assert drho.shape == (tiny.n_rho, 0, 1)
+
+
+def test_invalid_inputs_are_rejected(W, tiny):
+    with pytest.raises(W.WgwError) as e:
+        ctx = setup(W, tiny)
+        W.wgw_apply_chi0(ctx, synth.perturbations(tiny.miller_rho, tiny.L, 1, 3), omega=[0.5])
+    assert e.value.status == W.WGW_ERR_ARG
+    bad = tiny.psi_v.copy()
+    bad[1, 0] += 0.3j          # no longer real in r
+    with pytest.raises(W.WgwError) as e:
+        W.wgw_setup(tiny.L, tiny.ecut, tiny.grid, tiny.vloc_G, bad, tiny.e_v)
+    assert e.value.status == W.WGW_ERR_ARG
+    with pytest.raises(W.WgwError) as e:
+        W.wgw_setup(tiny.L, tiny.ecut, 6, tiny.vloc_G, tiny.psi_v, tiny.e_v)   # grid too small
+    assert e.value.status == W.WGW_ERR_ARG
+
+
+def test_static_response_matches_finite_differences(W, tiny):
+    """Pins the GPU result to the derivative of the ground-state density (no response formula)."""
+    dV = synth.perturbations(tiny.miller_rho, tiny.L, 1, 8)
+    fd = chi0.finite_difference_drho(model_of(tiny), dV[:, 0], 1e-3)
+    ctx = setup(W, tiny, cg_tol=1e-13)
+    drho, _, _ = W.wgw_apply_chi0(ctx, dV)
+    assert rel_err(drho[:, 0, 0][:, None], fd[:, None]) < 1e-9
+
+
+@pytest.fixture(scope="module")
+def cfg48():
+    return synth.make_system("pdep_L16_48")
+
+
+@pytest.mark.slow
+def test_config48_full_batch_sampled_parity(W, cfg48):
+    """The benchmarked workload (64 perturbations x 64 states, mixed path), two perturbations checked."""
+    import torch
+    s = cfg48
+    phi = synth.perturbations(s.miller_rho, s.L, 64, 5)
+    ctx = setup(W, s, precision=W.WGW_MIXED, cg_tol=1e-10)
+    x = torch.from_numpy(np.ascontiguousarray(phi.T)).cuda()
+    out = torch.zeros((1, 64, s.n_rho), dtype=torch.complex128, device="cuda")
+    st, _ = W.wgw_apply_chibar0_dev(ctx, x, [0.0], out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().transpose(2, 1, 0)
+    assert st["n_systems"] == 4096 and st["n_converged"] == 4096
+    pick = [0, 37]
+    ref = chi0.apply_chibar0(model_of(s), phi[:, pick], [0.0])
+    assert rel_err(got[:, pick], ref) < 1e-8
