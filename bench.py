@@ -1,0 +1,286 @@
+#!/usr/bin/env python
+"""Benchmark of the batched chi0 path: Sternheimer solves per second on one GB300.
+
+Workload (default "pdep_L16_48"): one block application of the symmetrised
+response chi0bar = v^1/2 chi0 v^1/2 to 64 perturbations on the 48^3 Gaussian-well
+model (L = 16 bohr, ecut 7.75 Ha, N_pw = 4169, N_rho = 33833, 64 occupied states),
+i.e. 4096 Sternheimer systems, in the mixed path (FP32 CG, FP64 refinement to
+cg_tol 1e-10, which keeps drho within 1e-8 of the FP64 oracle).  A step is one
+such block apply: perturbations to real space, right-hand sides, P_c, the
+batched CG, refinement, and drho.
+
+Printed: one JSON line (rank 0).  `value` is device time with inputs resident in
+HBM (CUDA events on the launching stream, L2 flushed between steps outside the
+timed interval); `e2e` is the same metric through the host-pointer entry point
+with pinned host buffers (copies inside the timed region).  `--impl reference`
+times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "pdep_L16_48": dict(config="pdep_L16_48", n_pert=64, pert_seed=5, cg_tol=1e-10,
+                        desc="chibar0 block apply, 64 perturbations x 64 occupied states = 4096 "
+                             "Sternheimer systems, 48^3 grid, N_pw=4169, N_rho=33833, mixed FP32/FP64"),
+    "chi0_L10_24": dict(config="chi0_L10_24", n_pert=8, pert_seed=2, cg_tol=1e-10,
+                        desc="chi0 apply, 8 perturbations x 4 occupied states = 32 Sternheimer systems, "
+                             "24^3 grid, N_pw=515, N_rho=4337, mixed FP32/FP64"),
+}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{index}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        cmd = ["nvidia-smi", "-i", str(self.index),
+               "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+               "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"]
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+            self.f.close()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 7:
+                    continue
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+                for n, v in zip(names, parts[3:7]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        except Exception:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(wl, sys_, budget_s=20.0):
+    """The FP64 oracle's Sternheimer CG (plain numpy) on a bounded sample of the same systems."""
+    import numpy as np
+    import synth
+    from oracle import chi0
+    from oracle.model import Model
+    m = Model(sys_.L, sys_.ecut, sys_.grid, sys_.vloc_G, sys_.psi_v, sys_.e_v)
+    phi = synth.perturbations(sys_.miller_rho, sys_.L, wl["n_pert"], wl["pert_seed"])
+    dV = m.vsqrt[:, None] * phi
+    nv = sys_.n_v
+    order = [(v, p) for p in range(wl["n_pert"]) for v in range(nv)]
+    rng = np.random.default_rng(0)
+    pick = [order[i] for i in rng.permutation(len(order))]
+    done, t0 = 0, time.perf_counter()
+    for v, p in pick:
+        chi0.sternheimer_cg_drho(m, dV, tol=wl["cg_tol"], systems=[(v, p)])
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "Sternheimer solves/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{done} of {len(order)} (v, p) systems of the same workload, FP64 numpy CG with "
+                      f"FFT-applied H to the same cg_tol, {dt:.1f} s"}
+
+
+def run_reference(args, wl):
+    import synth
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    s = synth.make_system(wl["config"])
+    lat = []
+    for _ in range(args.warmup):
+        cpu_baseline(wl, s, budget_s=2.0)
+    vals = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        cb = cpu_baseline(wl, s, budget_s=8.0)
+        lat.append(time.perf_counter() - t0)
+        vals.append(cb["value"])
+    v = statistics.mean(vals)
+    line = {"impl": "reference", "metric": "Sternheimer solves/s at 1e-8 rel err vs FP64 oracle",
+            "value": v, "unit": "Sternheimer solves/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(lat), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"]},
+            "cpu_baseline": {"value": v, "unit": "Sternheimer solves/s", "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": cb["sample"]},
+            "e2e": {"value": v, "unit": "Sternheimer solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="pdep_L16_48", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import synth
+    s = synth.make_system(wl["config"])
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, s)            # host-only work before the first GPU call
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2203_05623_gb300 import build
+    build.build()
+    import paper_2203_05623_gb300 as W
+
+    phi = synth.perturbations(s.miller_rho, s.L, wl["n_pert"], wl["pert_seed"])
+    opt = W.wgw_default_options(precision=W.WGW_MIXED, cg_tol=wl["cg_tol"], max_cg_iter=200)
+    ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, opt)
+    stream = torch.cuda.current_stream()
+    x = torch.from_numpy(np.ascontiguousarray(phi.T)).cuda()
+    out = torch.zeros((1, wl["n_pert"], s.n_rho), dtype=torch.complex128, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        st, _ = W.wgw_apply_chibar0_dev(ctx, x, [0.0], out, stream=stream.cuda_stream)
+        return st
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    W.wgw_profile_enable(ctx, True)
+    times, stats = [], None
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)                      # evict L2 between steps (outside the timed interval)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            stats = step()
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b) / 1e3)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    prof = W.wgw_profile_read(ctx)
+    W.wgw_profile_enable(ctx, False)
+    total = sum(times)
+    if dist:
+        t = torch.tensor([total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    n_sys = stats["n_systems"]
+    value = world * n_sys * args.steps / total
+
+    # End to end through the host-pointer entry point (pinned buffers, copies timed).
+    ph = torch.from_numpy(np.ascontiguousarray(phi.T)).pin_memory().numpy()
+    oh = torch.zeros((1, wl["n_pert"], s.n_rho), dtype=torch.complex128).pin_memory().numpy()
+    W.wgw_apply_chibar0(ctx, ph.T, [0.0], out=oh)
+    e2e_t = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        W.wgw_apply_chibar0(ctx, ph.T, [0.0], out=oh)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_total = sum(e2e_t)
+    if dist:
+        t = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    io_bytes = wl["n_pert"] * s.n_rho * 16
+
+    hbm, peak_kind = peaks()
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9 if d["ms"] > 0 else 0.0
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            traffic = json.load(f).get(args.workload, {}).get(dom)
+    except Exception:
+        traffic = None
+    line = {
+        "metric": "Sternheimer solves/s at 1e-8 rel err vs FP64 oracle; p50/p99 request latency",
+        "value": value, "unit": "Sternheimer solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": wl["desc"], "cg_tol": wl["cg_tol"],
+                   "l2": "256 MB buffer written between steps, outside the timed interval",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "latency_ms": {"p50": 1e3 * statistics.median(times),
+                       "p99": 1e3 * sorted(times)[min(len(times) - 1, int(0.99 * len(times)))],
+                       "what": "one block-apply request, device time"},
+        "solve": {"n_systems": n_sys, "max_iters": stats["max_iters"], "refinements": stats["refinements"],
+                  "max_rel_residual": stats["max_rel_residual"]},
+        "e2e": {"value": world * n_sys * args.steps / e2e_total, "unit": "Sternheimer solves/s",
+                "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_kind,
+                     "launches": d["launches"], "avg_launch_ms": d["ms"] / max(d["launches"], 1)},
+        "kernel_share": {k: round(v["ms"] / max(sum(q["ms"] for q in prof.values()), 1e-9), 4)
+                         for k, v in prof.items() if v["launches"]},
+        "gpu_launches": int(sum(v["launches"] for v in prof.values())),
+        "clocks": clk.summary(),
+    }
+    if cpu:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    W.wgw_destroy(ctx)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

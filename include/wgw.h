@@ -79,7 +79,7 @@ typedef struct wgw_stats {
 } wgw_stats;
 
 /* Fills *opt with defaults: WGW_FP64, cg_tol 1e-12, max_cg_iter 2000, max_refine 8,
- * inner_tol 1e-4, f_s 2, check_every 8. */
+ * inner_tol 1e-5, f_s 2, check_every 8. */
 int wgw_default_options(wgw_options* opt);
 
 /*
@@ -127,6 +127,10 @@ int wgw_apply_chi0(wgw_ctx* ctx, const double* dV, int n_pert, const double* ome
 int wgw_apply_chi0_dev(wgw_ctx* ctx, const double* dV_dev, int n_pert, const double* omega,
                        int n_omega, double* drho_dev, void* stream, wgw_stats* st);
 
+/* As wgw_apply_chibar0_dev (below) with host arrays, copied in and out within the call. */
+int wgw_apply_chibar0(wgw_ctx* ctx, const double* phi, int n_pert, const double* omega, int n_omega,
+                      double* out, wgw_stats* st);
+
 /*
  * Symmetrised response chi0bar phi = v^1/2 chi0 v^1/2 phi (Sec. 2.1), v^1/2(G) = sqrt(4 pi)/|G|,
  * zero at G = 0.  phi and out are dimensionless density-sphere coefficients; layout as for
@@ -134,6 +138,31 @@ int wgw_apply_chi0_dev(wgw_ctx* ctx, const double* dV_dev, int n_pert, const dou
  */
 int wgw_apply_chibar0_dev(wgw_ctx* ctx, const double* phi_dev, int n_pert, const double* omega,
                           int n_omega, double* out_dev, void* stream, wgw_stats* st);
+
+/*
+ * Kernel timing (no counterpart in the paper; used to report roofline fractions).
+ * When enabled, every kernel launch of the context is bracketed by CUDA events on
+ * its stream and accumulated per kernel class; enabling resets the counters.
+ * Classes 0..WGW_PROF_KINDS-1: plane_g2r, xline, plane_r2g, drho_xline, pc_project,
+ * cg_update, convert, other.  wgw_profile_read returns, for one class, the summed
+ * device milliseconds, the launch count and the summed algorithmic bytes and flops
+ * (each launch's own compulsory inputs and outputs); any output pointer may be NULL.
+ */
+#define WGW_PROF_KINDS 8
+int wgw_profile_enable(wgw_ctx* ctx, int on);
+int wgw_profile_read(wgw_ctx* ctx, int kind, double* ms, long* launches, double* bytes, double* flops);
+const char* wgw_profile_kind_name(int kind);
+
+/*
+ * Per-system diagnostics of the last apply call on this context.  Systems are
+ * ordered s = r * n_v + v, where r runs over the real-in-r parts of the batch
+ * (the perturbations' real parts, then their non-zero imaginary parts).
+ * Writes min(n, n_systems) entries: CG iterations summed over refinement steps,
+ * and the final FP64 relative residual; either pointer may be NULL.  Returns the
+ * number of entries written, or WGW_ERR_ARG (with nothing written) on a NULL context
+ * or negative n.
+ */
+int wgw_system_info(const wgw_ctx* ctx, int n, int* iters, double* rel_residual);
 
 /* Releases the context and all device memory it owns.  NULL is allowed. */
 void wgw_destroy(wgw_ctx* ctx);

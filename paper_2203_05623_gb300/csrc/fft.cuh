@@ -98,6 +98,76 @@ WGW_HD cplx<T> twiddle(const cplx<T>* tw, int k, int sign) {
 // N-hi..N-1 of a block (the footprint of a sphere of radius lo = hi = m).
 WGW_HD int split_line(int li, int m, int n) { return li <= m ? li : li + n - 2 * m - 1; }
 
+template <typename T, int R>
+WGW_HD void dft_fixed(cplx<T>* v, int sign) {
+  if constexpr (R == 2) dft2(v);
+  else if constexpr (R == 3) dft3(v, sign);
+  else if constexpr (R == 4) dft4(v, sign);
+  else if constexpr (R == 5) dft5(v, sign);
+  else dft8(v, sign);
+}
+
+// One DIF stage of radix R over all lines (block size S, butterfly span M = S/R).
+template <typename T, int R>
+WGW_HD void dif_stage(cplx<T>* buf, int N, int S, const cplx<T>* tw, int sign, int nlines,
+                      int line_stride, int elem_stride, int m_split, Thr th) {
+  const int M = S / R, step = N / S, total = nlines * (N / R);
+  for (int t = th.tid; t < total; t += th.nth) {
+    const int li = t % nlines;
+    const int rest = t / nlines;
+    const int j2 = rest % M;
+    const int blk = rest / M;
+    const int line = m_split >= 0 ? split_line(li, m_split, N) : li;
+    cplx<T>* base = buf + (size_t)line * line_stride + (size_t)(blk * S + j2) * elem_stride;
+    cplx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = base[(size_t)r * M * elem_stride];
+    dft_fixed<T, R>(v, sign);
+    base[0] = v[0];
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      cplx<T> x = v[r];
+      if (j2) x = cmul(x, twiddle(tw, (step * j2 * r) % N, sign));
+      base[(size_t)r * M * elem_stride] = x;
+    }
+  }
+}
+
+// One DIT stage of radix R (twiddles before the butterfly).
+template <typename T, int R>
+WGW_HD void dit_stage(cplx<T>* buf, int N, int S, const cplx<T>* tw, int sign, int nlines,
+                      int line_stride, int elem_stride, int m_split, Thr th) {
+  const int M = S / R, step = N / S, total = nlines * (N / R);
+  for (int t = th.tid; t < total; t += th.nth) {
+    const int li = t % nlines;
+    const int rest = t / nlines;
+    const int j2 = rest % M;
+    const int blk = rest / M;
+    const int line = m_split >= 0 ? split_line(li, m_split, N) : li;
+    cplx<T>* base = buf + (size_t)line * line_stride + (size_t)(blk * S + j2) * elem_stride;
+    cplx<T> v[R];
+    v[0] = base[0];
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      cplx<T> x = base[(size_t)r * M * elem_stride];
+      if (j2) x = cmul(x, twiddle(tw, (step * j2 * r) % N, sign));
+      v[r] = x;
+    }
+    dft_fixed<T, R>(v, sign);
+#pragma unroll
+    for (int r = 0; r < R; ++r) base[(size_t)r * M * elem_stride] = v[r];
+  }
+}
+
+#define WGW_RADIX_DISPATCH(FN, R, ...)                 \
+  switch (R) {                                         \
+    case 2: FN<T, 2>(__VA_ARGS__); break;              \
+    case 3: FN<T, 3>(__VA_ARGS__); break;              \
+    case 4: FN<T, 4>(__VA_ARGS__); break;              \
+    case 5: FN<T, 5>(__VA_ARGS__); break;              \
+    default: FN<T, 8>(__VA_ARGS__); break;             \
+  }
+
 // DIF over `nlines` lines: natural order in, digit-reversed order out.
 // Line li starts at buf + off(li) * line_stride, element e at + e * elem_stride,
 // with off(li) = li, or split_line(li, m_split, N) when m_split >= 0.
@@ -107,29 +177,10 @@ WGW_HD void fft_dif(cplx<T>* buf, const FftPlan& p, const cplx<T>* tw, int sign,
   const int N = p.n;
   int S = N;
   for (int st = 0; st < p.nst; ++st) {
-    const int R = p.radix[st];
-    const int M = S / R;
-    const int step = N / S;
-    const int total = nlines * (N / R);
-    for (int t = th.tid; t < total; t += th.nth) {
-      const int li = t % nlines;
-      const int rest = t / nlines;
-      const int j2 = rest % M;
-      const int blk = rest / M;
-      const int line = m_split >= 0 ? split_line(li, m_split, N) : li;
-      cplx<T>* base = buf + (size_t)line * line_stride + (size_t)(blk * S + j2) * elem_stride;
-      cplx<T> v[8];
-      for (int r = 0; r < R; ++r) v[r] = base[(size_t)r * M * elem_stride];
-      dft_r(R, v, sign);
-      base[0] = v[0];
-      for (int r = 1; r < R; ++r) {
-        cplx<T> x = v[r];
-        if (j2) x = cmul(x, twiddle(tw, (step * j2 * r) % N, sign));
-        base[(size_t)r * M * elem_stride] = x;
-      }
-    }
+    WGW_RADIX_DISPATCH(dif_stage, p.radix[st], buf, N, S, tw, sign, nlines, line_stride, elem_stride,
+                       m_split, th)
     WGW_SYNC();
-    S = M;
+    S /= p.radix[st];
   }
 }
 
@@ -144,29 +195,118 @@ WGW_HD void fft_dit(cplx<T>* buf, const FftPlan& p, const cplx<T>* tw, int sign,
     for (int st = 0; st < p.nst; ++st) { sizes[st] = S; S /= p.radix[st]; }
   }
   for (int st = p.nst - 1; st >= 0; --st) {
-    const int R = p.radix[st];
-    const int S = sizes[st];
-    const int M = S / R;
-    const int step = N / S;
-    const int total = nlines * (N / R);
-    for (int t = th.tid; t < total; t += th.nth) {
-      const int li = t % nlines;
-      const int rest = t / nlines;
-      const int j2 = rest % M;
-      const int blk = rest / M;
-      const int line = m_split >= 0 ? split_line(li, m_split, N) : li;
-      cplx<T>* base = buf + (size_t)line * line_stride + (size_t)(blk * S + j2) * elem_stride;
-      cplx<T> v[8];
+    WGW_RADIX_DISPATCH(dit_stage, p.radix[st], buf, N, sizes[st], tw, sign, nlines, line_stride,
+                       elem_stride, m_split, th)
+    WGW_SYNC();
+  }
+}
+
+// ---------------------------------------------------------------- compile-time sizes
+// The same transforms with N known at compile time: the radix plan, strides and
+// every index division fold to constants.  Butterflies are mapped fastest, lines
+// slowest.  NC = 0 selects the runtime-N versions above.
+struct CPlan {
+  int nst;
+  int radix[6];
+  int size[6];   // block size S at each stage
+};
+
+constexpr CPlan cplan(int n) {
+  CPlan p{0, {0, 0, 0, 0, 0, 0}, {0, 0, 0, 0, 0, 0}};
+  int r = n;
+  int S = n;
+  const int order[5] = {8, 4, 2, 3, 5};
+  while (r > 1) {
+    int f = 0;
+    for (int i = 0; i < 5 && f == 0; ++i)
+      if (r % order[i] == 0) f = order[i];
+    if (f == 0 || p.nst >= 6) return CPlan{-1, {0, 0, 0, 0, 0, 0}, {0, 0, 0, 0, 0, 0}};
+    p.radix[p.nst] = f;
+    p.size[p.nst] = S;
+    ++p.nst;
+    S /= f;
+    r /= f;
+  }
+  return p;
+}
+
+template <typename T, int N, int S, int R, bool DIF>
+WGW_HD void stage_c(cplx<T>* buf, const cplx<T>* tw, int sign, int nlines, int line_stride,
+                    int elem_stride, int m_split, Thr th) {
+  constexpr int M = S / R, step = N / S, NB = N / R;
+  const int total = nlines * NB;
+  for (int t = th.tid; t < total; t += th.nth) {
+    const int b = t % NB, li = t / NB;
+    const int j2 = b % M, blk = b / M;
+    const int line = m_split >= 0 ? split_line(li, m_split, N) : li;
+    cplx<T>* base = buf + (size_t)line * line_stride + (size_t)(blk * S + j2) * elem_stride;
+    cplx<T> v[R];
+    if constexpr (DIF) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = base[(size_t)r * M * elem_stride];
+      dft_fixed<T, R>(v, sign);
+      base[0] = v[0];
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        cplx<T> x = v[r];
+        if (M > 1 && j2) x = cmul(x, twiddle(tw, step * j2 * r, sign));
+        base[(size_t)r * M * elem_stride] = x;
+      }
+    } else {
       v[0] = base[0];
+#pragma unroll
       for (int r = 1; r < R; ++r) {
         cplx<T> x = base[(size_t)r * M * elem_stride];
-        if (j2) x = cmul(x, twiddle(tw, (step * j2 * r) % N, sign));
+        if (M > 1 && j2) x = cmul(x, twiddle(tw, step * j2 * r, sign));
         v[r] = x;
       }
-      dft_r(R, v, sign);
+      dft_fixed<T, R>(v, sign);
+#pragma unroll
       for (int r = 0; r < R; ++r) base[(size_t)r * M * elem_stride] = v[r];
     }
+  }
+}
+
+template <typename T, int N, int ST>
+WGW_HD void dif_stages_c(cplx<T>* buf, const cplx<T>* tw, int sign, int nlines, int ls, int es,
+                         int m_split, Thr th) {
+  constexpr CPlan P = cplan(N);
+  if constexpr (ST < P.nst) {
+    stage_c<T, N, P.size[ST], P.radix[ST], true>(buf, tw, sign, nlines, ls, es, m_split, th);
     WGW_SYNC();
+    dif_stages_c<T, N, ST + 1>(buf, tw, sign, nlines, ls, es, m_split, th);
+  }
+}
+
+template <typename T, int N, int ST>
+WGW_HD void dit_stages_c(cplx<T>* buf, const cplx<T>* tw, int sign, int nlines, int ls, int es,
+                         int m_split, Thr th) {
+  constexpr CPlan P = cplan(N);
+  if constexpr (ST >= 0) {
+    stage_c<T, N, P.size[ST], P.radix[ST], false>(buf, tw, sign, nlines, ls, es, m_split, th);
+    WGW_SYNC();
+    dit_stages_c<T, N, ST - 1>(buf, tw, sign, nlines, ls, es, m_split, th);
+  }
+}
+
+// Dispatch: NC > 0 uses the compile-time transforms (p must describe N = NC).
+template <typename T, int NC>
+WGW_HD void fft_dif_n(cplx<T>* buf, const FftPlan& p, const cplx<T>* tw, int sign, int nlines,
+                      int line_stride, int elem_stride, int m_split, Thr th) {
+  if constexpr (NC > 0) {
+    dif_stages_c<T, NC, 0>(buf, tw, sign, nlines, line_stride, elem_stride, m_split, th);
+  } else {
+    fft_dif<T>(buf, p, tw, sign, nlines, line_stride, elem_stride, m_split, th);
+  }
+}
+
+template <typename T, int NC>
+WGW_HD void fft_dit_n(cplx<T>* buf, const FftPlan& p, const cplx<T>* tw, int sign, int nlines,
+                      int line_stride, int elem_stride, int m_split, Thr th) {
+  if constexpr (NC > 0) {
+    dit_stages_c<T, NC, cplan(NC).nst - 1>(buf, tw, sign, nlines, line_stride, elem_stride, m_split, th);
+  } else {
+    fft_dit<T>(buf, p, tw, sign, nlines, line_stride, elem_stride, m_split, th);
   }
 }
 

@@ -33,19 +33,27 @@ struct VecBatch {
 // Per-system activity (null = all active).
 WGW_HD bool is_active(const int* active, int s) { return active == nullptr || active[s] != 0; }
 
+// Members of pair q: entries 2q and 2q+1 of a system list (null = identity) of n_list
+// entries; the second member is -1 when 2q+1 >= n_list.
+WGW_HD void pair_members(const int* list, int n_list, int q, int& s0, int& s1) {
+  s0 = list ? list[2 * q] : 2 * q;
+  s1 = 2 * q + 1 < n_list ? (list ? list[2 * q + 1] : 2 * q + 1) : -1;
+}
+
 // G -> r along z then y for plane hi of one pair; writes T[hi] of that pair.
 // smem: N * (N + 1) complex.
-template <typename T>
+template <typename T, int NC = 0>
 WGW_HD void plane_g2r_body(int pair, int hi, const SphereTab& sp, const FftPlan& pl,
-                           const cplx<T>* tw, const T* X, long ldx, int n_sys, const int* active,
+                           const cplx<T>* tw, const T* X, long ldx, int n_list, const int* list,
                            cplx<T>* Tout, cplx<T>* B, Thr th) {
-  const int N = pl.n, LS = N + 1, m = sp.m;
-  const int s0 = 2 * pair, s1 = 2 * pair + 1;
-  const bool has1 = s1 < n_sys;
+  const int N = NC > 0 ? NC : pl.n, LS = N + 1, m = sp.m;
+  int s0, s1;
+  pair_members(list, n_list, pair, s0, s1);
+  const bool has1 = s1 >= 0;
   for (int i = th.tid; i < N * LS; i += th.nth) B[i] = mk<T>(0, 0);
   WGW_SYNC();
   const T* x0 = X + (size_t)s0 * ldx;
-  const T* x1 = X + (size_t)s1 * ldx;
+  const T* x1 = X + (size_t)(has1 ? s1 : s0) * ldx;
   const T s = T(kInvSqrt2);
   for (int e = sp.plane_off[hi] + th.tid; e < sp.plane_off[hi + 1]; e += th.nth) {
     const int2 en = sp.ent[e];
@@ -62,14 +70,13 @@ WGW_HD void plane_g2r_body(int pair, int hi, const SphereTab& sp, const FftPlan&
     B[kk * LS + ll] = z;
   }
   WGW_SYNC();
-  fft_dif(B, pl, tw, +1, 2 * m + 1, LS, 1, m, th);   // rows |k| <= m, along l -> z
-  fft_dif(B, pl, tw, +1, N, 1, LS, -1, th);          // columns z, along k -> y
+  fft_dif_n<T, NC>(B, pl, tw, +1, 2 * m + 1, LS, 1, m, th);   // rows |k| <= m, along l -> z
+  fft_dif_n<T, NC>(B, pl, tw, +1, N, 1, LS, -1, th);          // columns z, along k -> y
   cplx<T>* out = Tout + ((size_t)pair * (2 * m + 1) + hi) * N * N;
   for (int i = th.tid; i < N * N; i += th.nth) {
     const int y = i / N, z = i % N;
     out[i] = B[y * LS + z];
   }
-  (void)active;
 }
 
 // x-line kernel modes.
@@ -89,16 +96,18 @@ struct XArgs {
   long lda, ldb;           // per-system strides of A and Bm
   const int* a_index;      // FROM_REAL: index of the A array of system s (null = s)
   const int* b_index;      // FROM_REAL: index of the Bm array of system s (null = s)
-  int n_sys;
+  int n_sys;               // entries of the system list (pairs = (n_sys + 1) / 2)
+  const int* list;         // system list (null = identity)
 };
 
 // One (pair, y) slab: S[z][x], N x (N + 1) complex.
-template <typename T>
+template <typename T, int NC = 0>
 WGW_HD void xline_body(int pair, int y, int m, const FftPlan& pl, const cplx<T>* tw,
                        cplx<T>* Tbuf, const XArgs<T>& a, cplx<T>* S, Thr th) {
-  const int N = pl.n, LS = N + 1, NP = 2 * m + 1;
-  const int s0 = 2 * pair, s1 = 2 * pair + 1;
-  const bool has1 = s1 < a.n_sys;
+  const int N = NC > 0 ? NC : pl.n, LS = N + 1, NP = 2 * m + 1;
+  int s0, s1;
+  pair_members(a.list, a.n_sys, pair, s0, s1);
+  const bool has1 = s1 >= 0;
   cplx<T>* tp = Tbuf + (size_t)pair * NP * N * N + (size_t)y * N;   // T[hi][y][z] at tp[hi*N*N + z]
   const size_t slab = (size_t)y * N * N;                              // real-space [y][z][x] offset
   if (a.mode == XM_FROM_REAL) {
@@ -123,7 +132,7 @@ WGW_HD void xline_body(int pair, int y, int m, const FftPlan& pl, const cplx<T>*
       S[z * LS + x] = tp[(size_t)hi * N * N + z];
     }
     WGW_SYNC();
-    fft_dif(S, pl, tw, +1, N, LS, 1, -1, th);
+    fft_dif_n<T, NC>(S, pl, tw, +1, N, LS, 1, -1, th);
   }
   if (a.mode == XM_TO_REAL) {
     T* r0 = a.R0 + (size_t)s0 * a.ldr + slab;
@@ -144,7 +153,7 @@ WGW_HD void xline_body(int pair, int y, int m, const FftPlan& pl, const cplx<T>*
     }
     WGW_SYNC();
   }
-  fft_dit(S, pl, tw, -1, N, LS, 1, -1, th);
+  fft_dit_n<T, NC>(S, pl, tw, -1, N, LS, 1, -1, th);
   for (int i = th.tid; i < NP * N; i += th.nth) {
     const int hi = i / N, z = i % N;
     const int x = (hi - m + N) % N;
@@ -162,8 +171,9 @@ struct Epi {
   T vcoef;
   T kin;
   const T* shift;          // per system (null = 0)
-  int n_sys;
+  int n_sys;               // entries of the system list
   const int* active;
+  const int* list;         // system list (null = identity)
 };
 
 template <typename T>
@@ -195,36 +205,37 @@ WGW_HD void unpack_store(const Epi<T>& ep, const SphereTab& sp, int s0, int s1, 
 }
 
 // r -> G along y then z for plane hi of one pair (in B), natural k, l afterwards.
-template <typename T>
+template <typename T, int NC = 0>
 WGW_HD void plane_r2g_load(int pair, int hi, const SphereTab& sp, const FftPlan& pl,
                            const cplx<T>* tw, const cplx<T>* Tin, cplx<T>* B, Thr th) {
-  const int N = pl.n, LS = N + 1, m = sp.m, NP = 2 * m + 1;
+  const int N = NC > 0 ? NC : pl.n, LS = N + 1, m = sp.m, NP = 2 * m + 1;
   const cplx<T>* in = Tin + ((size_t)pair * NP + hi) * N * N;
   for (int i = th.tid; i < N * N; i += th.nth) {
     const int y = i / N, z = i % N;
     B[y * LS + z] = in[i];
   }
   WGW_SYNC();
-  fft_dit(B, pl, tw, -1, N, 1, LS, -1, th);          // columns z: y -> k (natural)
-  fft_dit(B, pl, tw, -1, 2 * m + 1, LS, 1, m, th);   // rows |k| <= m: z -> l (natural)
+  fft_dit_n<T, NC>(B, pl, tw, -1, N, 1, LS, -1, th);          // columns z: y -> k (natural)
+  fft_dit_n<T, NC>(B, pl, tw, -1, 2 * m + 1, LS, 1, m, th);   // rows |k| <= m: z -> l (natural)
 }
 
 WGW_HD int ent_pos(int2 en, int LS) { return (en.x & 0xff) * LS + ((en.x >> 8) & 0xff); }
 
 // r -> G for planes +hp and -hp of one pair, gather the sphere, unpack, epilogue.
 // smem: N * (N + 1) complex for the plane + npt_max complex (values of plane +hp).
-template <typename T>
+template <typename T, int NC = 0>
 WGW_HD void plane_r2g_body(int pair, int hp, const SphereTab& sp, const FftPlan& pl,
                            const cplx<T>* tw, const cplx<T>* Tin, const Epi<T>& ep,
                            cplx<T>* B, cplx<T>* Zp, Thr th) {
-  const int N = pl.n, LS = N + 1, m = sp.m;
-  const int s0 = 2 * pair, s1 = 2 * pair + 1;
-  const bool has1 = s1 < ep.n_sys;
+  const int N = NC > 0 ? NC : pl.n, LS = N + 1, m = sp.m;
+  int s0, s1;
+  pair_members(ep.list, ep.n_sys, pair, s0, s1);
+  const bool has1 = s1 >= 0;
   const bool act0 = is_active(ep.active, s0), act1 = has1 && is_active(ep.active, s1);
   const T scale = T(1.0) / (T(N) * T(N) * T(N));
   const int off_p = sp.plane_off[m + hp];
   const int cnt = sp.plane_off[m + hp + 1] - off_p;
-  plane_r2g_load(pair, m + hp, sp, pl, tw, Tin, B, th);
+  plane_r2g_load<T, NC>(pair, m + hp, sp, pl, tw, Tin, B, th);
   if (hp == 0) {
     // Plane 0 lists [G = 0, K positives, K mirrors].
     const int K = (cnt - 1) / 2;
@@ -243,7 +254,7 @@ WGW_HD void plane_r2g_body(int pair, int hp, const SphereTab& sp, const FftPlan&
   for (int t = th.tid; t < cnt; t += th.nth) Zp[t] = B[ent_pos(sp.ent[off_p + t], LS)];
   WGW_SYNC();
   const int off_m = sp.plane_off[m - hp];
-  plane_r2g_load(pair, m - hp, sp, pl, tw, Tin, B, th);
+  plane_r2g_load<T, NC>(pair, m - hp, sp, pl, tw, Tin, B, th);
   for (int t = th.tid; t < cnt; t += th.nth) {
     unpack_store(ep, sp, s0, s1, act0, act1, sp.ent[off_p + t].y, Zp[t],
                  B[ent_pos(sp.ent[off_m + t], LS)], scale);
@@ -257,11 +268,11 @@ WGW_HD void plane_r2g_body(int pair, int hp, const SphereTab& sp, const FftPlan&
 // G -> r pass along x.  The sum runs over v in a fixed order, so the result
 // does not depend on how many perturbations share the launch.
 // smem: N * (N + 1) complex + N * N real.
-template <typename T>
+template <typename T, int NC = 0>
 WGW_HD void drho_xline_body(int p, int y, int m, const FftPlan& pl, const cplx<T>* tw,
                             const cplx<T>* Tbuf, const T* psi_r, long ldpsi, int n_v, int n_sys,
                             T coef, T* D, long ldd, cplx<T>* S, T* acc, Thr th) {
-  const int N = pl.n, LS = N + 1, NP = 2 * m + 1;
+  const int N = NC > 0 ? NC : pl.n, LS = N + 1, NP = 2 * m + 1;
   const size_t slab = (size_t)y * N * N;
   for (int i = th.tid; i < N * N; i += th.nth) acc[i] = T(0);
   const int s_lo = p * n_v, s_hi = (p + 1) * n_v;   // systems of p: [s_lo, s_hi)
@@ -274,7 +285,7 @@ WGW_HD void drho_xline_body(int p, int y, int m, const FftPlan& pl, const cplx<T
       S[z * LS + (hi - m + N) % N] = tp[(size_t)hi * N * N + z];
     }
     WGW_SYNC();
-    fft_dif(S, pl, tw, +1, N, LS, 1, -1, th);
+    fft_dif_n<T, NC>(S, pl, tw, +1, N, LS, 1, -1, th);
     const int sa = 2 * q, sb = 2 * q + 1;
     const bool ua = sa >= s_lo && sa < s_hi && sa < n_sys;
     const bool ub = sb >= s_lo && sb < s_hi && sb < n_sys;

@@ -20,7 +20,7 @@ int fft_threads(int n);
 // Pruned 3D FFT pipeline (fft_kernels.cu).
 template <typename T>
 cudaError_t launch_plane_g2r(const SphereTab& sp, FftCtx<T> f, const T* X, long ldx, int n_sys,
-                             const int* active, cplx<T>* Tbuf, cudaStream_t st);
+                             const int* list, const int* active, cplx<T>* Tbuf, cudaStream_t st);
 template <typename T>
 cudaError_t launch_xline(int m, FftCtx<T> f, cplx<T>* Tbuf, const XArgs<T>& a, const int* active,
                          cudaStream_t st);
@@ -32,9 +32,15 @@ cudaError_t launch_drho_xline(int m, FftCtx<T> f, const cplx<T>* Tbuf, const T* 
                               int n_v, int n_sys, int n_pert, T coef, T* D, long ldd, cudaStream_t st);
 
 // Linear algebra (la_kernels.cu).
+// Y <- Y - Psi Psi^T Y for the active systems of a list (null = systems 0..n_sys-1);
+// work holds pc_work_elems(n, n_sys, nv) elements of T.
 template <typename T>
-cudaError_t launch_pc(T* Y, long ldy, int n_sys, const T* Psi, long ldp, int n, int nv,
-                      const int* active, cudaStream_t st);
+cudaError_t launch_pc(T* Y, long ldy, int n_sys, const int* list, const T* Psi, long ldp, int n, int nv,
+                      const int* active, T* work, cudaStream_t st);
+// Ordered list of the systems s < n_sys with active[s] != 0, and their count.
+cudaError_t launch_build_list(const int* active, int n_sys, int* list, int* count, cudaStream_t st);
+int pc_kblocks(int n, int n_sys);
+size_t pc_work_elems(int n, int n_sys, int nv);
 template <typename T>
 cudaError_t launch_cg_init_a(const SphereTab& sp, int n, int n_sys, const T* Bv, T* X, T* R, T* Z,
                              long ld, const double* eps, CgState cs, cudaStream_t st);
@@ -42,12 +48,12 @@ template <typename T>
 cudaError_t launch_cg_init_b(int n, int n_sys, const T* R, const T* Z, T* P, long ld, CgState cs,
                              cudaStream_t st);
 template <typename T>
-cudaError_t launch_cg_step_a(const SphereTab& sp, int n, int n_sys, T* X, T* R, T* Z, const T* P,
-                             const T* Q, long ld, const double* eps, CgState cs, double tol2,
+cudaError_t launch_cg_step_a(const SphereTab& sp, int n, int n_sys, const int* list, T* X, T* R, T* Z,
+                             const T* P, const T* Q, long ld, const double* eps, CgState cs, double tol2,
                              int max_iter, cudaStream_t st);
 template <typename T>
-cudaError_t launch_cg_step_b(int n, int n_sys, const T* R, const T* Z, T* P, long ld, CgState cs,
-                             cudaStream_t st);
+cudaError_t launch_cg_step_b(int n, int n_sys, const int* list, const T* R, const T* Z, T* P, long ld,
+                             CgState cs, cudaStream_t st);
 cudaError_t launch_sphere_to_rb(int n_sys, const double* c, long ldc, const double* scale, RbMap mp,
                                 int part, double* out, long ldo, cudaStream_t st);
 cudaError_t launch_rb_to_sphere(int n_sys, const double* in, long ldi, const int* b_row,

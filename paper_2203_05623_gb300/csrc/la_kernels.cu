@@ -1,4 +1,6 @@
 // __global__ wrappers of the linear-algebra kernels (bodies in la_bodies.cuh).
+#include <algorithm>
+
 #include "internal.h"
 
 namespace wgw {
@@ -40,15 +42,17 @@ __global__ void k_cg_init_b(int n, const T* R, const T* Z, T* P, long ld, CgStat
 
 template <typename T>
 __global__ void k_cg_step_a(SphereTab sp, int n, T* X, T* R, T* Z, const T* P, const T* Q, long ld,
-                            const double* eps, CgState cs, double tol2, int max_iter) {
+                            const double* eps, CgState cs, double tol2, int max_iter, const int* list) {
   __shared__ double red[33];
-  cg_step_a_body<T>(blockIdx.x, sp, n, X, R, Z, P, Q, ld, eps, cs, tol2, max_iter, red, thr());
+  const int s = list ? list[blockIdx.x] : blockIdx.x;
+  cg_step_a_body<T>(s, sp, n, X, R, Z, P, Q, ld, eps, cs, tol2, max_iter, red, thr());
 }
 
 template <typename T>
-__global__ void k_cg_step_b(int n, const T* R, const T* Z, T* P, long ld, CgState cs) {
+__global__ void k_cg_step_b(int n, const T* R, const T* Z, T* P, long ld, CgState cs, const int* list) {
   __shared__ double red[33];
-  cg_step_b_body<T>(blockIdx.x, n, R, Z, P, ld, cs, red, thr());
+  const int s = list ? list[blockIdx.x] : blockIdx.x;
+  cg_step_b_body<T>(s, n, R, Z, P, ld, cs, red, thr());
 }
 
 __global__ void k_sphere_to_rb(int n_sys, int n_el, const double* c, long ldc, const double* scale,
@@ -109,6 +113,207 @@ __global__ void k_count(const int* flags, int n, int* out) {
   if (threadIdx.x == 0) *out = int(c + 0.5);
 }
 
+
+// ---------------------------------------------------------------- P_c as two tiled GEMMs
+// Y <- Y - Psi (Psi^T Y) on the systems of a list (column j of the batch is system
+// s = list[j], identity when list is null).  Psi: n x nv (column v at Psi + v*ldp),
+// system s at Y + s*ldy.
+// Phase 1: Cpart[kb][v][j] = sum_{k in K-block kb} Psi[k][v] Y[k][s_j]   (64 x 64 tiles, 4x4 per thread)
+// Reduce:  C[v][j] = sum_kb Cpart[kb][v][j], in fixed order, into slice 0
+// Phase 2: Y[i][s_j] -= sum_v Psi[i][v] C[v][j]
+// No atomics: the result does not depend on the launch geometry of other systems' tiles.
+constexpr int kGT = 64;    // tile edge
+constexpr int kGK = 16;    // K chunk of phase 1
+
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
+
+template <typename T>
+__device__ __forceinline__ void load_kchunk(T (*dst)[kGT + 4], const T* __restrict__ base, long ld,
+                                            const int* __restrict__ cols, int col0, int n_cols, int k0,
+                                            int k_hi) {
+  // dst[kk][c] = base[col(c) * ld + k0 + kk] for kk < kGK, c < kGT (zero outside).
+  constexpr int V = Vec16<T>::n;
+  using VT = typename Vec16<T>::type;
+  for (int e = threadIdx.x; e < kGK * kGT / V; e += blockDim.x) {
+    const int c = e / (kGK / V), kq = (e % (kGK / V)) * V, k = k0 + kq;
+    const int cc = col0 + c;
+    T vals[V];
+    if (cc < n_cols) {
+      const int col = cols ? cols[cc] : cc;
+      const T* src = base + (size_t)col * ld + k;
+      if (k + V <= k_hi) {
+        const VT w = *reinterpret_cast<const VT*>(src);
+        const T* wp = reinterpret_cast<const T*>(&w);
+#pragma unroll
+        for (int j = 0; j < V; ++j) vals[j] = wp[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < V; ++j) vals[j] = (k + j < k_hi) ? src[j] : T(0);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < V; ++j) vals[j] = T(0);
+    }
+#pragma unroll
+    for (int j = 0; j < V; ++j) dst[kq + j][c] = vals[j];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_pc_gemm1(const T* __restrict__ Psi, long ldp,
+                                                  const T* __restrict__ Y, long ldy, int n, int nv,
+                                                  int n_list, const int* __restrict__ list, int kblk,
+                                                  T* __restrict__ Cpart) {
+  __shared__ __align__(16) T As[kGK][kGT + 4];
+  __shared__ __align__(16) T Bs[kGK][kGT + 4];
+  const int j0 = blockIdx.x * kGT, v0 = blockIdx.z * kGT, kb = blockIdx.y;
+  const int k_lo = kb * kblk, k_hi = min(n, k_lo + kblk);
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;   // tx: systems, ty: states
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  for (int k0 = k_lo; k0 < k_hi; k0 += kGK) {
+    load_kchunk<T>(As, Psi, ldp, nullptr, v0, nv, k0, k_hi);
+    load_kchunk<T>(Bs, Y, ldy, list, j0, n_list, k0, k_hi);
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kGK; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) { a[i] = As[kk][ty * 4 + i]; b[i] = Bs[kk][tx * 4 + i]; }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+    }
+    __syncthreads();
+  }
+  const int nvp = gridDim.z * kGT;
+  T* out = Cpart + (size_t)kb * nvp * n_list;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int v = v0 + ty * 4 + i;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int jx = j0 + tx * 4 + j;
+      if (jx < n_list) out[(size_t)v * n_list + jx] = acc[i][j];
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_pc_reduce(T* __restrict__ Cpart, size_t slice, int n_kb) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < slice; e += (size_t)gridDim.x * blockDim.x) {
+    T sum = Cpart[e];
+    for (int kb = 1; kb < n_kb; ++kb) sum += Cpart[(size_t)kb * slice + e];
+    Cpart[e] = sum;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_pc_gemm2(const T* __restrict__ Psi, long ldp, T* __restrict__ Y,
+                                                  long ldy, int n, int nv, int n_list,
+                                                  const int* __restrict__ list, const T* __restrict__ C,
+                                                  const int* __restrict__ active) {
+  __shared__ __align__(16) T Cs[kGT][kGT + 4];     // C[v][j] of one 64-state chunk
+  __shared__ __align__(16) T Ps[kGT][kGT + 4];     // Psi[i][v] stored as Ps[v][i]
+  const int i0 = blockIdx.x * kGT, j0 = blockIdx.y * kGT;
+  // tx: 4 consecutive rows i (vector access along the system's column), ty: 4 systems.
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  if (active) {
+    bool any = false;
+    for (int t = 0; t < kGT && j0 + t < n_list; ++t) any |= active[list ? list[j0 + t] : j0 + t] != 0;
+    if (!any) return;
+  }
+  T acc[4][4];   // [row][system]
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  for (int vc = 0; vc < nv; vc += kGT) {
+    for (int e = tid; e < kGT * kGT; e += 256) {
+      const int c = e % kGT, vv = e / kGT, v = vc + vv, jx = j0 + c;
+      Cs[vv][c] = (jx < n_list && v < nv) ? C[(size_t)v * n_list + jx] : T(0);
+      const int i = i0 + c;
+      Ps[vv][c] = (v < nv && i < n) ? Psi[(size_t)v * ldp + i] : T(0);
+    }
+    __syncthreads();
+    const int vmax = min(kGT, nv - vc);
+    for (int vv = 0; vv < vmax; ++vv) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) { a[i] = Ps[vv][tx * 4 + i]; b[i] = Cs[vv][ty * 4 + i]; }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+    }
+    __syncthreads();
+  }
+  constexpr int V = Vec16<T>::n;
+  using VT = typename Vec16<T>::type;
+  const int r0 = i0 + tx * 4;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int jx = j0 + ty * 4 + j;
+    if (jx >= n_list) continue;
+    const int sx = list ? list[jx] : jx;
+    if (active && !active[sx]) continue;
+    T* y = Y + (size_t)sx * ldy + r0;
+    if (r0 + 4 <= n) {
+#pragma unroll
+      for (int q = 0; q < 4; q += V) {
+        VT w = *reinterpret_cast<VT*>(y + q);
+        T* wp = reinterpret_cast<T*>(&w);
+#pragma unroll
+        for (int u = 0; u < V; ++u) wp[u] -= acc[q + u][j];
+        *reinterpret_cast<VT*>(y + q) = w;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (r0 + i < n) y[i] -= acc[i][j];
+    }
+  }
+}
+
+// Ordered list of the active systems (single block; prefix sums over chunks of 1024 flags).
+__global__ void __launch_bounds__(1024) k_build_list(const int* __restrict__ active, int n_sys,
+                                                     int* __restrict__ list, int* __restrict__ count) {
+  __shared__ int warp_sums[32];
+  __shared__ int base;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int c0 = 0; c0 < n_sys; c0 += blockDim.x) {
+    const int s = c0 + threadIdx.x;
+    const int f = (s < n_sys && active[s]) ? 1 : 0;
+    const unsigned mask = __ballot_sync(0xffffffffu, f);
+    const int before = __popc(mask & ((1u << lane) - 1u));
+    if (lane == 0) warp_sums[w] = __popc(mask);
+    __syncthreads();
+    if (w == 0) {
+      int v = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+      }
+      warp_sums[lane] = v;   // inclusive
+    }
+    __syncthreads();
+    const int woff = w ? warp_sums[w - 1] : 0;
+    if (f) list[base + woff + before] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) base += warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *count = base;
+}
+
 inline dim3 grid_el(int n, int n_sys) {
   int bx = (n + 255) / 256;
   if (bx > 64) bx = 64;
@@ -119,16 +324,43 @@ inline dim3 grid_el(int n, int n_sys) {
 }  // namespace
 
 template <typename T>
-cudaError_t launch_pc(T* Y, long ldy, int n_sys, const T* Psi, long ldp, int n, int nv,
-                      const int* active, cudaStream_t st) {
+cudaError_t launch_pc(T* Y, long ldy, int n_sys, const int* list, const T* Psi, long ldp, int n, int nv,
+                      const int* active, T* work, cudaStream_t st) {
   if (n_sys == 0 || nv == 0) return cudaSuccess;
-  const size_t smem = sizeof(T) * (size_t)(nv * kPcTS + kPcKC * nv + kPcKC * kPcTS);
-  if (smem > 48 * 1024) {
-    cudaError_t err = cudaFuncSetAttribute(k_pc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int n_kb = pc_kblocks(n, n_sys);
+  const int kblk = ((n + n_kb - 1) / n_kb + kGK - 1) / kGK * kGK;
+  const int nvp = (nv + kGT - 1) / kGT * kGT;
+  dim3 g1((n_sys + kGT - 1) / kGT, n_kb, nvp / kGT);
+  k_pc_gemm1<T><<<g1, 256, 0, st>>>(Psi, ldp, Y, ldy, n, nv, n_sys, list, kblk, work);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  if (n_kb > 1) {
+    const size_t slice = (size_t)nvp * n_sys;
+    k_pc_reduce<T><<<(int)std::min<size_t>((slice + 255) / 256, 4096), 256, 0, st>>>(work, slice, n_kb);
+    err = cudaGetLastError();
     if (err != cudaSuccess) return err;
   }
-  k_pc<T><<<(n_sys + kPcTS - 1) / kPcTS, 256, smem, st>>>(Y, ldy, n_sys, Psi, ldp, n, nv, active);
+  dim3 g2((n + kGT - 1) / kGT, (n_sys + kGT - 1) / kGT);
+  k_pc_gemm2<T><<<g2, 256, 0, st>>>(Psi, ldp, Y, ldy, n, nv, n_sys, list, work, active);
   return cudaGetLastError();
+}
+
+cudaError_t launch_build_list(const int* active, int n_sys, int* list, int* count, cudaStream_t st) {
+  k_build_list<<<1, 1024, 0, st>>>(active, n_sys, list, count);
+  return cudaGetLastError();
+}
+
+int pc_kblocks(int n, int n_sys) {
+  // Enough K blocks that phase 1 has >= ~4 CTAs per SM, each block >= 256 rows.
+  const int s_tiles = (n_sys + kGT - 1) / kGT;
+  int kb = (4 * 152 + s_tiles - 1) / s_tiles;
+  kb = std::max(1, std::min(kb, std::max(1, n / 256)));
+  return kb;
+}
+
+size_t pc_work_elems(int n, int n_sys, int nv) {
+  const int nvp = (nv + kGT - 1) / kGT * kGT;
+  return (size_t)pc_kblocks(n, n_sys) * nvp * n_sys;
 }
 
 template <typename T>
@@ -148,19 +380,19 @@ cudaError_t launch_cg_init_b(int n, int n_sys, const T* R, const T* Z, T* P, lon
 }
 
 template <typename T>
-cudaError_t launch_cg_step_a(const SphereTab& sp, int n, int n_sys, T* X, T* R, T* Z, const T* P,
-                             const T* Q, long ld, const double* eps, CgState cs, double tol2,
+cudaError_t launch_cg_step_a(const SphereTab& sp, int n, int n_sys, const int* list, T* X, T* R, T* Z,
+                             const T* P, const T* Q, long ld, const double* eps, CgState cs, double tol2,
                              int max_iter, cudaStream_t st) {
   if (n_sys == 0) return cudaSuccess;
-  k_cg_step_a<T><<<n_sys, kCgThreads, 0, st>>>(sp, n, X, R, Z, P, Q, ld, eps, cs, tol2, max_iter);
+  k_cg_step_a<T><<<n_sys, kCgThreads, 0, st>>>(sp, n, X, R, Z, P, Q, ld, eps, cs, tol2, max_iter, list);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_cg_step_b(int n, int n_sys, const T* R, const T* Z, T* P, long ld, CgState cs,
-                             cudaStream_t st) {
+cudaError_t launch_cg_step_b(int n, int n_sys, const int* list, const T* R, const T* Z, T* P, long ld,
+                             CgState cs, cudaStream_t st) {
   if (n_sys == 0) return cudaSuccess;
-  k_cg_step_b<T><<<n_sys, kCgThreads, 0, st>>>(n, R, Z, P, ld, cs);
+  k_cg_step_b<T><<<n_sys, kCgThreads, 0, st>>>(n, R, Z, P, ld, cs, list);
   return cudaGetLastError();
 }
 
@@ -215,17 +447,17 @@ cudaError_t launch_count(const int* flags, int n, int* out, cudaStream_t st) {
 }
 
 #define WGW_INST_LA(T)                                                                             \
-  template cudaError_t launch_pc<T>(T*, long, int, const T*, long, int, int, const int*,           \
-                                    cudaStream_t);                                                 \
+  template cudaError_t launch_pc<T>(T*, long, int, const int*, const T*, long, int, int,           \
+                                    const int*, T*, cudaStream_t);                                 \
   template cudaError_t launch_cg_init_a<T>(const SphereTab&, int, int, const T*, T*, T*, T*, long, \
                                            const double*, CgState, cudaStream_t);                 \
   template cudaError_t launch_cg_init_b<T>(int, int, const T*, const T*, T*, long, CgState,       \
                                            cudaStream_t);                                         \
-  template cudaError_t launch_cg_step_a<T>(const SphereTab&, int, int, T*, T*, T*, const T*,      \
-                                           const T*, long, const double*, CgState, double, int,   \
-                                           cudaStream_t);                                         \
-  template cudaError_t launch_cg_step_b<T>(int, int, const T*, const T*, T*, long, CgState,       \
-                                           cudaStream_t);                                         \
+  template cudaError_t launch_cg_step_a<T>(const SphereTab&, int, int, const int*, T*, T*, T*,     \
+                                           const T*, const T*, long, const double*, CgState,      \
+                                           double, int, cudaStream_t);                            \
+  template cudaError_t launch_cg_step_b<T>(int, int, const int*, const T*, const T*, T*, long,    \
+                                           CgState, cudaStream_t);                                \
   template cudaError_t launch_add_to<T>(int, int, const T*, long, double*, long, const int*,      \
                                         cudaStream_t);                                            \
   template cudaError_t launch_norm2<T>(int, int, const T*, long, double*, cudaStream_t);

@@ -108,6 +108,57 @@ struct Prec {
   }
 };
 
+// Per-kernel-class timing with CUDA events recorded on the launching stream
+// (enabled by wgw_profile_enable).  Each record brackets one launch.
+constexpr int kProfKinds = 8;
+const char* const kProfNames[kProfKinds] = {"plane_g2r", "xline", "plane_r2g", "drho_xline",
+                                            "pc_project", "cg_update", "convert", "other"};
+enum ProfKind { PK_G2R = 0, PK_XLINE, PK_R2G, PK_DRHO, PK_PC, PK_CG, PK_CONV, PK_OTHER };
+
+struct Prof {
+  bool on = false;
+  struct Rec { int kind; cudaEvent_t a, b; double bytes, flops; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  double ms[kProfKinds] = {}, bytes[kProfKinds] = {}, flops[kProfKinds] = {};
+  long n[kProfKinds] = {};
+  cudaEvent_t get() {
+    if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  template <typename F>
+  cudaError_t run(int kind, double by, double fl, cudaStream_t st, F&& f) {
+    if (!on) return f();
+    Rec r{kind, get(), get(), by, fl};
+    cudaEventRecord(r.a, st);
+    cudaError_t err = f();
+    cudaEventRecord(r.b, st);
+    recs.push_back(r);
+    return err;
+  }
+  void flush() {
+    for (Rec& r : recs) {
+      float t = 0.f;
+      if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+        ms[r.kind] += t; n[r.kind] += 1; bytes[r.kind] += r.bytes; flops[r.kind] += r.flops;
+      }
+      pool.push_back(r.a); pool.push_back(r.b);
+    }
+    recs.clear();
+  }
+  void reset() {
+    flush();
+    for (int k = 0; k < kProfKinds; ++k) { ms[k] = bytes[k] = flops[k] = 0; n[k] = 0; }
+  }
+  void release() {
+    flush();
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    pool.clear();
+  }
+};
+
 }  // namespace
 
 struct wgw_ctx {
@@ -123,18 +174,28 @@ struct wgw_ctx {
   DevBuf e_v_d;
   // apply work space (double unless noted)
   DevBuf dvin, dv_rb, dv_r, Trho, Dr, drho_rb, eps, a_idx, b_idx, brow, cg_rz, cg_bb, cg_rr,
-      cg_act, cg_it, cnt, rr64, act64, norms;
+      cg_act, cg_it, cnt, rr64, act64, norms, pc_work, sys_list, list64;
   cudaStream_t stream = nullptr;
+  Prof prof;
+  std::vector<int> last_iters;      // per system of the last apply: CG iterations (all refinements)
+  std::vector<double> last_relres;  // per system of the last apply: final FP64 ||b - A x|| / ||b||
   ~wgw_ctx() {
+    prof.release();
     d.release(); f.release(); wfc.release(); rho.release();
     DevBuf* all[] = {&e_v_d, &dvin, &dv_rb, &dv_r, &Trho, &Dr, &drho_rb, &eps, &a_idx, &b_idx, &brow,
-                     &cg_rz, &cg_bb, &cg_rr, &cg_act, &cg_it, &cnt, &rr64, &act64, &norms};
+                     &cg_rz, &cg_bb, &cg_rr, &cg_act, &cg_it, &cnt, &rr64, &act64, &norms, &pc_work, &sys_list, &list64};
     for (DevBuf* b : all) b->release();
     if (stream) cudaStreamDestroy(stream);
   }
 };
 
 namespace {
+
+// Algorithmic bytes of the FFT-pipeline kernels (their own inputs and outputs).
+template <typename T>
+double t_bytes(const wgw_ctx* c, int m, int pairs) {
+  return (double)pairs * (2 * m + 1) * c->N * c->N * sizeof(cplx<T>);
+}
 
 // Real-space function(s) of a batch of real-basis vectors of one sphere:
 // out[s] (N^3 reals, digit-reversed positions) for s < n_sys.
@@ -144,29 +205,50 @@ int to_real(wgw_ctx* c, Prec<T>& pr, const HostSphere& sp, const T* X, long ldx,
   const int N = c->N, NP = 2 * sp.m + 1, pairs = (n_sys + 1) / 2;
   WGW_TRY(tbuf.ensure(sizeof(cplx<T>) * (size_t)pairs * NP * N * N));
   FftCtx<T> f = pr.fft(c->plan);
-  WGW_CK(launch_plane_g2r<T>(sp.tab(), f, X, ldx, n_sys, nullptr, tbuf.as<cplx<T>>(), st));
+  const double tb = t_bytes<T>(c, sp.m, pairs);
+  WGW_CK(c->prof.run(PK_G2R, tb + (double)n_sys * sp.nrb() * sizeof(T), 0, st, [&] {
+    return launch_plane_g2r<T>(sp.tab(), f, X, ldx, n_sys, nullptr, nullptr, tbuf.as<cplx<T>>(), st); }));
   XArgs<T> a{};
   a.mode = XM_TO_REAL; a.R0 = out; a.R1 = out; a.ldr = c->grid3; a.n_sys = n_sys;
-  WGW_CK(launch_xline<T>(sp.m, f, tbuf.as<cplx<T>>(), a, nullptr, st));
+  WGW_CK(c->prof.run(PK_XLINE, tb + (double)n_sys * c->grid3 * sizeof(T), 0, st, [&] {
+    return launch_xline<T>(sp.m, f, tbuf.as<cplx<T>>(), a, nullptr, st); }));
   return WGW_OK;
 }
 
-// Q = P_c (H - e_v) P  for the active systems (P already in range(P_c)).
+// P_c applied to the systems of a list (null = 0..n_list-1), timed as pc_project.
 template <typename T>
-int apply_A(wgw_ctx* c, Prec<T>& pr, const T* P, T* Q, int n_sys, const int* active, cudaStream_t st) {
-  const int N = c->N, NP = 2 * c->wfc.m + 1, pairs = (n_sys + 1) / 2;
+int run_pc(wgw_ctx* c, T* Y, int n_list, const int* list, const T* Psi, const int* active, cudaStream_t st) {
+  const double n = c->wfc.nrb(), nv = c->n_v;
+  WGW_TRY(c->pc_work.ensure(sizeof(T) * pc_work_elems((int)n, n_list, c->n_v)));
+  T* work = c->pc_work.as<T>();
+  WGW_CK(c->prof.run(PK_PC, 2.0 * n_list * n * sizeof(T) + n * nv * sizeof(T), 4.0 * n * nv * n_list, st, [&] {
+    return launch_pc<T>(Y, c->ld_w, n_list, list, Psi, c->ld_w, (int)n, c->n_v, active, work, st); }));
+  return WGW_OK;
+}
+
+// Q = P_c (H - e_v) P for the active systems of a list (P already in range(P_c)).
+template <typename T>
+int apply_A(wgw_ctx* c, Prec<T>& pr, const T* P, T* Q, int n_list, const int* list, const int* active,
+            cudaStream_t st) {
+  const int N = c->N, NP = 2 * c->wfc.m + 1, pairs = (n_list + 1) / 2;
+  if (pairs == 0) return WGW_OK;
   WGW_TRY(pr.Tw.ensure(sizeof(cplx<T>) * (size_t)pairs * NP * N * N));
   FftCtx<T> f = pr.fft(c->plan);
   cplx<T>* Tb = pr.Tw.template as<cplx<T>>();
-  WGW_CK(launch_plane_g2r<T>(c->wfc.tab(), f, P, c->ld_w, n_sys, active, Tb, st));
+  const int nrb = c->wfc.nrb();
+  const double tb = t_bytes<T>(c, c->wfc.m, pairs);
+  WGW_CK(c->prof.run(PK_G2R, tb + (double)n_list * nrb * sizeof(T), 0, st, [&] {
+    return launch_plane_g2r<T>(c->wfc.tab(), f, P, c->ld_w, n_list, list, active, Tb, st); }));
   XArgs<T> a{};
-  a.mode = XM_APPLY_V; a.V = pr.v_r.template as<T>(); a.n_sys = n_sys;
-  WGW_CK(launch_xline<T>(c->wfc.m, f, Tb, a, active, st));
+  a.mode = XM_APPLY_V; a.V = pr.v_r.template as<T>(); a.n_sys = n_list; a.list = list;
+  WGW_CK(c->prof.run(PK_XLINE, 2 * tb + (double)c->grid3 * sizeof(T), 0, st, [&] {
+    return launch_xline<T>(c->wfc.m, f, Tb, a, active, st); }));
   Epi<T> e{};
   e.out = Q; e.ldo = c->ld_w; e.pin = P; e.ldp = c->ld_w; e.vcoef = T(1); e.kin = T(1);
-  e.shift = pr.shift.template as<T>(); e.n_sys = n_sys; e.active = active;
-  WGW_CK(launch_plane_r2g<T>(c->wfc.tab(), c->wfc.npt_max, f, Tb, e, st));
-  WGW_CK(launch_pc<T>(Q, c->ld_w, n_sys, pr.psi.template as<T>(), c->ld_w, c->wfc.nrb(), c->n_v, active, st));
+  e.shift = pr.shift.template as<T>(); e.n_sys = n_list; e.active = active; e.list = list;
+  WGW_CK(c->prof.run(PK_R2G, tb + 2.0 * n_list * nrb * sizeof(T), 0, st, [&] {
+    return launch_plane_r2g<T>(c->wfc.tab(), c->wfc.npt_max, f, Tb, e, st); }));
+  WGW_TRY(run_pc<T>(c, Q, n_list, list, pr.psi.template as<T>(), active, st));
   return WGW_OK;
 }
 
@@ -177,14 +259,17 @@ CgState cg_state(wgw_ctx* c) {
   return s;
 }
 
-int count_active(wgw_ctx* c, const int* flags, int n, cudaStream_t st, int* out) {
-  WGW_CK(launch_count(flags, n, c->cnt.as<int>(), st));
+// Ordered list of the systems with flags[s] != 0 into `list`; returns the count on the host.
+int build_list(wgw_ctx* c, const int* flags, int n, int* list, cudaStream_t st, int* out) {
+  WGW_CK(c->prof.run(PK_OTHER, 8.0 * n, 0, st, [&] { return launch_build_list(flags, n, list, c->cnt.as<int>(), st); }));
   WGW_CK(cudaMemcpyAsync(out, c->cnt.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   WGW_CK(cudaStreamSynchronize(st));
   return WGW_OK;
 }
 
 // Preconditioned CG on A x = b for all systems (b in pr.Bv, x into pr.X), to relative residual tol.
+// Every check_every iterations the host rebuilds the list of systems still iterating, and the
+// following iterations launch over that list only.
 template <typename T>
 int cg_solve(wgw_ctx* c, Prec<T>& pr, int n_sys, double tol, int max_iter, cudaStream_t st) {
   const int n = c->wfc.nrb();
@@ -199,20 +284,25 @@ int cg_solve(wgw_ctx* c, Prec<T>& pr, int n_sys, double tol, int max_iter, cudaS
   const double* eps = c->eps.as<double>();
   CgState cs = cg_state(c);
   const int* act = cs.active;
-  WGW_CK(launch_cg_init_a<T>(c->wfc.tab(), n, n_sys, Bv, X, R, Z, ld, eps, cs, st));
-  WGW_CK(launch_pc<T>(Z, ld, n_sys, Psi, ld, n, c->n_v, act, st));
-  WGW_CK(launch_cg_init_b<T>(n, n_sys, R, Z, P, ld, cs, st));
+  const double vb = (double)n_sys * n * sizeof(T);
+  WGW_CK(c->prof.run(PK_CG, 4 * vb, 0, st, [&] {
+    return launch_cg_init_a<T>(c->wfc.tab(), n, n_sys, Bv, X, R, Z, ld, eps, cs, st); }));
+  WGW_TRY(run_pc<T>(c, Z, n_sys, nullptr, Psi, act, st));
+  WGW_CK(c->prof.run(PK_CG, 3 * vb, 0, st, [&] { return launch_cg_init_b<T>(n, n_sys, R, Z, P, ld, cs, st); }));
+  int* lbuf = c->sys_list.as<int>();
+  int n_list = 0;
+  WGW_TRY(build_list(c, act, n_sys, lbuf, st, &n_list));
   const int every = std::max(1, c->opt.check_every);
-  for (int it = 0; it < max_iter; ++it) {
-    WGW_TRY(apply_A<T>(c, pr, P, Q, n_sys, act, st));
-    WGW_CK(launch_cg_step_a<T>(c->wfc.tab(), n, n_sys, X, R, Z, P, Q, ld, eps, cs, tol * tol, max_iter, st));
-    WGW_CK(launch_pc<T>(Z, ld, n_sys, Psi, ld, n, c->n_v, act, st));
-    WGW_CK(launch_cg_step_b<T>(n, n_sys, R, Z, P, ld, cs, st));
-    if ((it + 1) % every == 0 || it + 1 == max_iter) {
-      int na = 0;
-      WGW_TRY(count_active(c, act, n_sys, st, &na));
-      if (na == 0) break;
-    }
+  for (int it = 0; it < max_iter && n_list > 0; ++it) {
+    const double lb = (double)n_list * n * sizeof(T);
+    WGW_TRY(apply_A<T>(c, pr, P, Q, n_list, lbuf, act, st));
+    WGW_CK(c->prof.run(PK_CG, 7 * lb, 0, st, [&] {
+      return launch_cg_step_a<T>(c->wfc.tab(), n, n_list, lbuf, X, R, Z, P, Q, ld, eps, cs, tol * tol,
+                                 max_iter, st); }));
+    WGW_TRY(run_pc<T>(c, Z, n_list, lbuf, Psi, act, st));
+    WGW_CK(c->prof.run(PK_CG, 4 * lb, 0, st, [&] {
+      return launch_cg_step_b<T>(n, n_list, lbuf, R, Z, P, ld, cs, st); }));
+    if ((it + 1) % every == 0) WGW_TRY(build_list(c, act, n_sys, lbuf, st, &n_list));
   }
   return WGW_OK;
 }
@@ -237,6 +327,8 @@ int ensure_work(wgw_ctx* c, int n_sys, int n_real) {
   WGW_TRY(c->cg_it.ensure(sizeof(int) * n_sys));
   WGW_TRY(c->rr64.ensure(sizeof(double) * n_sys));
   WGW_TRY(c->act64.ensure(sizeof(int) * n_sys));
+  WGW_TRY(c->sys_list.ensure(sizeof(int) * n_sys));
+  WGW_TRY(c->list64.ensure(sizeof(int) * n_sys));
   WGW_TRY(c->cnt.ensure(sizeof(int) * 4));
   WGW_TRY(c->dv_r.ensure(sizeof(double) * (size_t)n_real * c->grid3));
   WGW_TRY(c->Dr.ensure(sizeof(double) * (size_t)n_real * c->grid3));
@@ -267,7 +359,7 @@ int solve_all(wgw_ctx* c, int n_sys, cudaStream_t st, wgw_stats* stats) {
     const double* Bv = c->d.Bv.as<double>();
     WGW_CK(cudaMemsetAsync(X, 0, sizeof(double) * (size_t)n_sys * ld, st));
     WGW_CK(cudaMemcpyAsync(R, Bv, sizeof(double) * (size_t)n_sys * ld, cudaMemcpyDeviceToDevice, st));
-    WGW_CK(launch_norm2<double>(n_sys, n, Bv, ld, c->cg_bb.as<double>(), st));
+    WGW_CK(c->prof.run(PK_OTHER, 8.0 * n_sys * n, 0, st, [&] { return launch_norm2<double>(n_sys, n, Bv, ld, c->cg_bb.as<double>(), st); }));
     std::vector<int> it_host(n_sys);
     // Keep the FP64 |b|^2 aside: the inner solves overwrite cg_bb.
     WGW_TRY(c->norms.ensure(sizeof(double) * n_sys));
@@ -275,40 +367,47 @@ int solve_all(wgw_ctx* c, int n_sys, cudaStream_t st, wgw_stats* stats) {
     WGW_CK(cudaMemcpyAsync(bb64, c->cg_bb.p, sizeof(double) * n_sys, cudaMemcpyDeviceToDevice, st));
     int* act64 = c->act64.as<int>();
     for (int k = 0; k < c->opt.max_refine; ++k) {
-      WGW_CK(launch_norm2<double>(n_sys, n, R, ld, c->rr64.as<double>(), st));
-      k_residual_flags<<<(n_sys + 255) / 256, 256, 0, st>>>(n_sys, c->rr64.as<double>(), bb64, tol * tol, act64);
-      WGW_CK(cudaGetLastError());
+      WGW_CK(c->prof.run(PK_OTHER, 8.0 * n_sys * n, 0, st, [&] { return launch_norm2<double>(n_sys, n, R, ld, c->rr64.as<double>(), st); }));
+      WGW_CK(c->prof.run(PK_OTHER, 20.0 * n_sys, 0, st, [&] {
+        k_residual_flags<<<(n_sys + 255) / 256, 256, 0, st>>>(n_sys, c->rr64.as<double>(), bb64, tol * tol, act64);
+        return cudaGetLastError(); }));
       int na = 0;
-      WGW_TRY(count_active(c, act64, n_sys, st, &na));
+      int* l64 = c->list64.as<int>();
+      WGW_TRY(build_list(c, act64, n_sys, l64, st, &na));
       if (na == 0) break;
       ++refinements;
       // Inner right-hand side: the FP32 image of r (only active systems; others get b = 0).
       WGW_CK(cudaMemsetAsync(c->f.Bv.p, 0, sizeof(float) * (size_t)n_sys * ld, st));
-      WGW_CK((launch_copy_cast<double, float>(n_sys, n, R, ld, c->f.Bv.as<float>(), ld, act64, st)));
+      WGW_CK(c->prof.run(PK_CONV, 12.0 * n_sys * n, 0, st, [&] { return launch_copy_cast<double, float>(n_sys, n, R, ld, c->f.Bv.as<float>(), ld, act64, st); }));
       WGW_TRY(cg_solve<float>(c, c->f, n_sys, c->opt.inner_tol, c->opt.max_cg_iter, st));
       WGW_CK(cudaMemcpyAsync(it_host.data(), c->cg_it.p, sizeof(int) * n_sys, cudaMemcpyDeviceToHost, st));
       WGW_CK(cudaStreamSynchronize(st));
       for (int s = 0; s < n_sys; ++s) iters_total[s] += it_host[s];
-      WGW_CK(launch_add_to<float>(n_sys, n, c->f.X.as<float>(), ld, X, ld, act64, st));
+      WGW_CK(c->prof.run(PK_CONV, 20.0 * n_sys * n, 0, st, [&] { return launch_add_to<float>(n_sys, n, c->f.X.as<float>(), ld, X, ld, act64, st); }));
       // The FP32 correction carries an O(eps_32) component along the occupied
       // states, which P_c (H - e_v) cannot see; the solution lies in range(P_c),
       // so project it out in FP64.
-      WGW_CK(launch_pc<double>(X, ld, n_sys, c->d.psi.as<double>(), ld, n, c->n_v, act64, st));
+      WGW_TRY(run_pc<double>(c, X, na, l64, c->d.psi.as<double>(), act64, st));
       // r = b - A x in FP64 for the systems that moved.
-      WGW_TRY(apply_A<double>(c, c->d, X, Q, n_sys, act64, st));
-      WGW_CK(launch_axpby(n_sys, n, 1.0, Bv, -1.0, Q, R, ld, act64, st));
+      WGW_TRY(apply_A<double>(c, c->d, X, Q, na, l64, act64, st));
+      WGW_CK(c->prof.run(PK_CONV, 24.0 * n_sys * n, 0, st, [&] { return launch_axpby(n_sys, n, 1.0, Bv, -1.0, Q, R, ld, act64, st); }));
     }
   }
-  // Final FP64 residual of every system (independent check of the stopping rule).
-  {
+  if (c->opt.precision == WGW_FP64) {
+    // Final FP64 residual of every system (independent check of the CG's recursive residual).
     double* X = c->d.X.as<double>();
-    WGW_CK(launch_pc<double>(X, ld, n_sys, c->d.psi.as<double>(), ld, n, c->n_v, nullptr, st));
     double* Q = c->d.Q.as<double>();
     double* R = c->d.R.as<double>();
-    WGW_TRY(apply_A<double>(c, c->d, X, Q, n_sys, nullptr, st));
-    WGW_CK(launch_axpby(n_sys, n, 1.0, c->d.Bv.as<double>(), -1.0, Q, R, ld, nullptr, st));
-    WGW_CK(launch_norm2<double>(n_sys, n, R, ld, c->rr64.as<double>(), st));
-    WGW_CK(launch_norm2<double>(n_sys, n, c->d.Bv.as<double>(), ld, c->cg_bb.as<double>(), st));
+    WGW_TRY(apply_A<double>(c, c->d, X, Q, n_sys, nullptr, nullptr, st));
+    WGW_CK(c->prof.run(PK_CONV, 24.0 * n_sys * n, 0, st, [&] { return launch_axpby(n_sys, n, 1.0, c->d.Bv.as<double>(), -1.0, Q, R, ld, nullptr, st); }));
+    WGW_CK(c->prof.run(PK_OTHER, 8.0 * n_sys * n, 0, st, [&] { return launch_norm2<double>(n_sys, n, R, ld, c->rr64.as<double>(), st); }));
+    WGW_CK(c->prof.run(PK_OTHER, 8.0 * n_sys * n, 0, st, [&] { return launch_norm2<double>(n_sys, n, c->d.Bv.as<double>(), ld, c->cg_bb.as<double>(), st); }));
+  } else {
+    // R holds b - A x in FP64 for every system's final x (recomputed after its last
+    // update); ||b||^2 was kept in norms.
+    WGW_CK(c->prof.run(PK_OTHER, 8.0 * n_sys * n, 0, st, [&] {
+      return launch_norm2<double>(n_sys, n, c->d.R.as<double>(), ld, c->rr64.as<double>(), st); }));
+    WGW_CK(cudaMemcpyAsync(c->cg_bb.p, c->norms.p, sizeof(double) * n_sys, cudaMemcpyDeviceToDevice, st));
   }
   std::vector<double> rr(n_sys), bb(n_sys);
   WGW_CK(cudaMemcpyAsync(rr.data(), c->rr64.p, sizeof(double) * n_sys, cudaMemcpyDeviceToHost, st));
@@ -316,8 +415,11 @@ int solve_all(wgw_ctx* c, int n_sys, cudaStream_t st, wgw_stats* stats) {
   WGW_CK(cudaStreamSynchronize(st));
   int conv = 0, maxit = 0;
   double maxrel = 0.0;
+  c->last_iters = iters_total;
+  c->last_relres.assign(n_sys, 0.0);
   for (int s = 0; s < n_sys; ++s) {
     const double rel = bb[s] > 0 ? std::sqrt(rr[s] / bb[s]) : 0.0;
+    c->last_relres[s] = rel;
     maxrel = std::max(maxrel, rel);
     if (rel <= tol * (1.0 + 1e-6) || bb[s] == 0.0) ++conv;
     maxit = std::max(maxit, iters_total[s]);
@@ -350,10 +452,11 @@ int apply_core(wgw_ctx* c, const double* dV, int n_pert, const double* omega, in
   WGW_TRY(c->dv_rb.ensure(sizeof(double) * (size_t)2 * n_pert * ldr));
   double* dvrb = c->dv_rb.as<double>();
   WGW_CK(cudaMemsetAsync(dvrb, 0, sizeof(double) * (size_t)2 * n_pert * ldr, st));
-  WGW_CK(launch_sphere_to_rb(n_pert, dV, 2L * rs.n, scale, rs.map(), 0, dvrb, ldr, st));
-  WGW_CK(launch_sphere_to_rb(n_pert, dV, 2L * rs.n, scale, rs.map(), 1, dvrb + (size_t)n_pert * ldr, ldr, st));
+  const double cb = 16.0 * n_pert * rs.n + 8.0 * n_pert * rs.nrb();
+  WGW_CK(c->prof.run(PK_CONV, cb, 0, st, [&] { return launch_sphere_to_rb(n_pert, dV, 2L * rs.n, scale, rs.map(), 0, dvrb, ldr, st); }));
+  WGW_CK(c->prof.run(PK_CONV, cb, 0, st, [&] { return launch_sphere_to_rb(n_pert, dV, 2L * rs.n, scale, rs.map(), 1, dvrb + (size_t)n_pert * ldr, ldr, st); }));
   WGW_TRY(c->norms.ensure(sizeof(double) * 2 * n_pert));
-  WGW_CK(launch_norm2<double>(2 * n_pert, rs.nrb(), dvrb, ldr, c->norms.as<double>(), st));
+  WGW_CK(c->prof.run(PK_OTHER, 16.0 * n_pert * rs.nrb(), 0, st, [&] { return launch_norm2<double>(2 * n_pert, rs.nrb(), dvrb, ldr, c->norms.as<double>(), st); }));
   std::vector<double> nrm(2 * n_pert);
   WGW_CK(cudaMemcpyAsync(nrm.data(), c->norms.p, sizeof(double) * 2 * n_pert, cudaMemcpyDeviceToHost, st));
   WGW_CK(cudaStreamSynchronize(st));
@@ -401,11 +504,14 @@ int apply_core(wgw_ctx* c, const double* dV, int n_pert, const double* omega, in
     XArgs<double> a{};
     a.mode = XM_FROM_REAL; a.A = c->d.psi_r.as<double>(); a.lda = c->grid3; a.a_index = c->a_idx.as<int>();
     a.Bm = dvr; a.ldb = c->grid3; a.b_index = c->b_idx.as<int>(); a.n_sys = n_sys;
-    WGW_CK(launch_xline<double>(c->wfc.m, f, c->d.Tw.as<cplx<double>>(), a, nullptr, st));
+    const double tb = t_bytes<double>(c, c->wfc.m, pairs);
+    WGW_CK(c->prof.run(PK_XLINE, tb + 2.0 * n_sys * c->grid3 * sizeof(double), 0, st, [&] {
+      return launch_xline<double>(c->wfc.m, f, c->d.Tw.as<cplx<double>>(), a, nullptr, st); }));
     Epi<double> e{};
     e.out = c->d.Bv.as<double>(); e.ldo = ldw; e.vcoef = -1.0; e.n_sys = n_sys;
-    WGW_CK(launch_plane_r2g<double>(c->wfc.tab(), c->wfc.npt_max, f, c->d.Tw.as<cplx<double>>(), e, st));
-    WGW_CK(launch_pc<double>(c->d.Bv.as<double>(), ldw, n_sys, c->d.psi.as<double>(), ldw, c->wfc.nrb(), n_v, nullptr, st));
+    WGW_CK(c->prof.run(PK_R2G, tb + (double)n_sys * c->wfc.nrb() * sizeof(double), 0, st, [&] {
+      return launch_plane_r2g<double>(c->wfc.tab(), c->wfc.npt_max, f, c->d.Tw.as<cplx<double>>(), e, st); }));
+    WGW_TRY(run_pc<double>(c, c->d.Bv.as<double>(), n_sys, nullptr, c->d.psi.as<double>(), nullptr, st));
   }
   // 5. Sternheimer solves.
   const int solve_status = solve_all(c, n_sys, st, stats);
@@ -415,25 +521,33 @@ int apply_core(wgw_ctx* c, const double* dV, int n_pert, const double* omega, in
     const int NP = 2 * c->wfc.m + 1, pairs = (n_sys + 1) / 2;
     WGW_TRY(c->d.Tw.ensure(sizeof(cplx<double>) * (size_t)pairs * NP * N * N));
     FftCtx<double> f = c->d.fft(c->plan);
-    WGW_CK(launch_plane_g2r<double>(c->wfc.tab(), f, c->d.X.as<double>(), ldw, n_sys, nullptr,
-                                    c->d.Tw.as<cplx<double>>(), st));
+    const double tb = t_bytes<double>(c, c->wfc.m, pairs);
+    WGW_CK(c->prof.run(PK_G2R, tb + (double)n_sys * c->wfc.nrb() * sizeof(double), 0, st, [&] {
+      return launch_plane_g2r<double>(c->wfc.tab(), f, c->d.X.as<double>(), ldw, n_sys, nullptr, nullptr,
+                                      c->d.Tw.as<cplx<double>>(), st); }));
     const double coef = 2.0 * c->opt.f_s / c->omega_cell;
-    WGW_CK(launch_drho_xline<double>(c->wfc.m, f, c->d.Tw.as<cplx<double>>(), c->d.psi_r.as<double>(),
-                                     c->grid3, n_v, n_sys, n_real, coef, c->Dr.as<double>(), c->grid3, st));
+    WGW_CK(c->prof.run(PK_DRHO, tb + (double)(n_v + n_real) * c->grid3 * sizeof(double), 0, st, [&] {
+      return launch_drho_xline<double>(c->wfc.m, f, c->d.Tw.as<cplx<double>>(), c->d.psi_r.as<double>(),
+                                       c->grid3, n_v, n_sys, n_real, coef, c->Dr.as<double>(), c->grid3, st); }));
     const int NPr = 2 * rs.m + 1, rpairs = (n_real + 1) / 2;
     WGW_TRY(c->Trho.ensure(sizeof(cplx<double>) * (size_t)rpairs * NPr * N * N));
     XArgs<double> a{};
     a.mode = XM_FROM_REAL; a.A = c->Dr.as<double>(); a.lda = c->grid3; a.n_sys = n_real;
-    WGW_CK(launch_xline<double>(rs.m, f, c->Trho.as<cplx<double>>(), a, nullptr, st));
+    const double tr = t_bytes<double>(c, rs.m, rpairs);
+    WGW_CK(c->prof.run(PK_XLINE, tr + (double)n_real * c->grid3 * sizeof(double), 0, st, [&] {
+      return launch_xline<double>(rs.m, f, c->Trho.as<cplx<double>>(), a, nullptr, st); }));
     Epi<double> e{};
     e.out = c->drho_rb.as<double>(); e.ldo = ldr; e.vcoef = 1.0; e.n_sys = n_real;
-    WGW_CK(launch_plane_r2g<double>(rs.tab(), rs.npt_max, f, c->Trho.as<cplx<double>>(), e, st));
+    WGW_CK(c->prof.run(PK_R2G, tr + (double)n_real * rs.nrb() * sizeof(double), 0, st, [&] {
+      return launch_plane_r2g<double>(rs.tab(), rs.npt_max, f, c->Trho.as<cplx<double>>(), e, st); }));
   }
   // 7. Complex output drho_p = chi0 A_p + i chi0 B_p for every frequency (all omega = 0 here).
   for (int k = 0; k < n_omega; ++k)
-    WGW_CK(launch_rb_to_sphere(n_pert, c->drho_rb.as<double>(), ldr, c->brow.as<int>(), scale, rs.map(),
-                               drho + (size_t)k * n_pert * 2 * rs.n, 2L * rs.n, st));
+    WGW_CK(c->prof.run(PK_CONV, 16.0 * n_pert * rs.n + 8.0 * n_pert * rs.nrb(), 0, st, [&] {
+      return launch_rb_to_sphere(n_pert, c->drho_rb.as<double>(), ldr, c->brow.as<int>(), scale, rs.map(),
+                                 drho + (size_t)k * n_pert * 2 * rs.n, 2L * rs.n, st); }));
   WGW_CK(cudaStreamSynchronize(st));
+  c->prof.flush();
   return solve_status;
 }
 
@@ -447,7 +561,7 @@ int wgw_default_options(wgw_options* opt) {
   opt->cg_tol = 1e-12;
   opt->max_cg_iter = 2000;
   opt->max_refine = 8;
-  opt->inner_tol = 1e-4;
+  opt->inner_tol = 1e-5;
   opt->f_s = 2.0;
   opt->check_every = 8;
   return WGW_OK;
@@ -594,8 +708,8 @@ int wgw_apply_chibar0_dev(wgw_ctx* c, const double* phi_dev, int n_pert, const d
   return apply_core(c, phi_dev, n_pert, omega, n_omega, out_dev, true, (cudaStream_t)stream, st);
 }
 
-int wgw_apply_chi0(wgw_ctx* c, const double* dV, int n_pert, const double* omega, int n_omega,
-                   double* drho, wgw_stats* st) {
+static int apply_host(wgw_ctx* c, const double* dV, int n_pert, const double* omega, int n_omega,
+                      double* drho, bool sym, wgw_stats* st) {
   g_last_error.clear();
   if (!c) return fail(WGW_ERR_ARG, "null context");
   if (n_pert <= 0) return n_pert == 0 ? WGW_OK : fail(WGW_ERR_ARG, "n_pert < 0");
@@ -607,11 +721,52 @@ int wgw_apply_chi0(wgw_ctx* c, const double* dV, int n_pert, const double* omega
   double* din = c->dvin.as<double>();
   double* dout = din + 2 * (size_t)c->rho.n * n_pert;
   WGW_CK(cudaMemcpyAsync(din, dV, in_b, cudaMemcpyHostToDevice, c->stream));
-  const int s = apply_core(c, din, n_pert, omega, n_omega, dout, false, c->stream, st);
+  const int s = apply_core(c, din, n_pert, omega, n_omega, dout, sym, c->stream, st);
   if (s != WGW_OK && s != WGW_ERR_NOCONV) return s;
   WGW_CK(cudaMemcpyAsync(drho, dout, out_b, cudaMemcpyDeviceToHost, c->stream));
   WGW_CK(cudaStreamSynchronize(c->stream));
   return s;
+}
+
+int wgw_apply_chi0(wgw_ctx* c, const double* dV, int n_pert, const double* omega, int n_omega,
+                   double* drho, wgw_stats* st) {
+  return apply_host(c, dV, n_pert, omega, n_omega, drho, false, st);
+}
+
+int wgw_apply_chibar0(wgw_ctx* c, const double* phi, int n_pert, const double* omega, int n_omega,
+                      double* out, wgw_stats* st) {
+  return apply_host(c, phi, n_pert, omega, n_omega, out, true, st);
+}
+
+int wgw_profile_enable(wgw_ctx* c, int on) {
+  if (!c) return fail(WGW_ERR_ARG, "null context");
+  c->prof.reset();
+  c->prof.on = on != 0;
+  return WGW_OK;
+}
+
+int wgw_profile_read(wgw_ctx* c, int kind, double* ms, long* launches, double* bytes, double* flops) {
+  if (!c || kind < 0 || kind >= kProfKinds) return fail(WGW_ERR_ARG, "bad profile kind");
+  c->prof.flush();
+  if (ms) *ms = c->prof.ms[kind];
+  if (launches) *launches = c->prof.n[kind];
+  if (bytes) *bytes = c->prof.bytes[kind];
+  if (flops) *flops = c->prof.flops[kind];
+  return WGW_OK;
+}
+
+const char* wgw_profile_kind_name(int kind) {
+  return (kind >= 0 && kind < kProfKinds) ? kProfNames[kind] : "";
+}
+
+int wgw_system_info(const wgw_ctx* c, int n, int* iters, double* rel_residual) {
+  if (!c || n < 0) return fail(WGW_ERR_ARG, "bad argument");
+  const int m = std::min<int>(n, (int)c->last_iters.size());
+  for (int s = 0; s < m; ++s) {
+    if (iters) iters[s] = c->last_iters[s];
+    if (rel_residual) rel_residual[s] = c->last_relres[s];
+  }
+  return m;
 }
 
 void wgw_destroy(wgw_ctx* c) { delete c; }

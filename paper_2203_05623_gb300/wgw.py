@@ -70,6 +70,12 @@ def lib(path: str | None = None):
                                      ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.POINTER(Stats)]
     L.wgw_apply_chibar0_dev.argtypes = L.wgw_apply_chi0_dev.argtypes
+    L.wgw_apply_chibar0.argtypes = L.wgw_apply_chi0.argtypes
+    L.wgw_profile_enable.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.wgw_profile_read.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_long), _dp, _dp]
+    L.wgw_profile_kind_name.restype = ctypes.c_char_p
+    L.wgw_profile_kind_name.argtypes = [ctypes.c_int]
+    L.wgw_system_info.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp]
     L.wgw_destroy.argtypes = [ctypes.c_void_p]
     L.wgw_status_string.restype = ctypes.c_char_p
     L.wgw_status_string.argtypes = [ctypes.c_int]
@@ -149,19 +155,57 @@ def wgw_set_options(ctx: Context, opt: Options):
     _check(lib().wgw_set_options(ctx.handle, ctypes.byref(opt)), "wgw_set_options")
 
 
-def wgw_apply_chi0(ctx: Context, dV, omega=(0.0,), allow_noconv=False):
-    """Host arrays: dV (N_rho, n_pert) complex -> (drho (N_rho, n_pert, n_omega), stats dict, status)."""
+def _host_call(fn, name, ctx, dV, omega, allow_noconv, out=None):
     dV = np.asarray(dV, np.complex128)
     dV = dV[:, None] if dV.ndim == 1 else dV
     n_pert = dV.shape[1]
     om = np.ascontiguousarray(omega, np.float64)
     buf = _interleave(dV)
-    out = np.zeros((len(om), n_pert, ctx.n_rho), np.complex128)
+    if out is None:
+        out = np.zeros((len(om), n_pert, ctx.n_rho), np.complex128)
     st = Stats()
-    s = lib().wgw_apply_chi0(ctx.handle, buf.ctypes.data_as(_dp), n_pert, om.ctypes.data_as(_dp), len(om),
-                             out.view(np.float64).ctypes.data_as(_dp), ctypes.byref(st))
-    _check(s, "wgw_apply_chi0", (WGW_OK, WGW_ERR_NOCONV) if allow_noconv else (WGW_OK,))
+    s = fn(ctx.handle, buf.ctypes.data_as(_dp), n_pert, om.ctypes.data_as(_dp), len(om),
+           out.view(np.float64).ctypes.data_as(_dp), ctypes.byref(st))
+    _check(s, name, (WGW_OK, WGW_ERR_NOCONV) if allow_noconv else (WGW_OK,))
     return out.transpose(2, 1, 0), st.as_dict(), s
+
+
+def wgw_apply_chi0(ctx: Context, dV, omega=(0.0,), allow_noconv=False, out=None):
+    """Host arrays: dV (N_rho, n_pert) complex -> (drho (N_rho, n_pert, n_omega), stats dict, status).
+
+    `out`, if given, is a C-contiguous complex128 array of shape (n_omega, n_pert, N_rho)
+    (for example pinned host memory) that receives the result."""
+    return _host_call(lib().wgw_apply_chi0, "wgw_apply_chi0", ctx, dV, omega, allow_noconv, out)
+
+
+def wgw_apply_chibar0(ctx: Context, phi, omega=(0.0,), allow_noconv=False, out=None):
+    """Host arrays: chibar0 phi = v^1/2 chi0 v^1/2 phi; layout as wgw_apply_chi0."""
+    return _host_call(lib().wgw_apply_chibar0, "wgw_apply_chibar0", ctx, phi, omega, allow_noconv, out)
+
+
+def wgw_profile_enable(ctx: Context, on: bool = True):
+    _check(lib().wgw_profile_enable(ctx.handle, int(on)), "wgw_profile_enable")
+
+
+def wgw_profile_read(ctx: Context) -> dict:
+    """Per kernel class: {name: {ms, launches, bytes, flops}}."""
+    out = {}
+    for k in range(8):
+        ms, n, by, fl = ctypes.c_double(), ctypes.c_long(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().wgw_profile_read(ctx.handle, k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(by),
+                                      ctypes.byref(fl)), "wgw_profile_read")
+        out[lib().wgw_profile_kind_name(k).decode()] = {"ms": ms.value, "launches": n.value,
+                                                        "bytes": by.value, "flops": fl.value}
+    return out
+
+
+def wgw_system_info(ctx: Context, n_sys: int):
+    """Per system of the last apply: (CG iterations, final FP64 relative residual)."""
+    it = np.zeros(n_sys, np.int32)
+    rr = np.zeros(n_sys, np.float64)
+    k = lib().wgw_system_info(ctx.handle, n_sys, it.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                              rr.ctypes.data_as(_dp))
+    return it[:k], rr[:k]
 
 
 def _dev_call(fn, name, ctx, x, omega, out, stream, allow_noconv):

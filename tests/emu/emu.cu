@@ -64,7 +64,7 @@ void sphere_to_rb_host(const Sph& sp, int n_sys, const double* c, long ldc, cons
   for (size_t i = 0; i < tmp.size(); ++i) out[i] = (T)tmp[i];
 }
 
-template <typename T>
+template <typename T, int NC = 0>
 void apply_h_impl(double L, double ecut, int N, const double* vloc_c, int n_sys, const double* Xd,
                   const double* shift, double* outd) {
   Sph w, r;
@@ -85,17 +85,17 @@ void apply_h_impl(double L, double ecut, int N, const double* vloc_c, int n_sys,
   std::vector<cplx<T>> Tb((size_t)pairs * NP * N * N), B((size_t)N * (N + 1)), Zp(w.h.npt_max + 1);
   for (int q = 0; q < pairs; ++q)
     for (int hi = 0; hi < NP; ++hi)
-      plane_g2r_body<T>(q, hi, w.tab(), pl, tw.data(), X.data(), nw, n_sys, nullptr, Tb.data(), B.data(), kOne);
+      plane_g2r_body<T, NC>(q, hi, w.tab(), pl, tw.data(), X.data(), nw, n_sys, nullptr, Tb.data(), B.data(), kOne);
   XArgs<T> a{};
   a.mode = XM_APPLY_V; a.V = vr.data(); a.n_sys = n_sys;
   for (int q = 0; q < pairs; ++q)
-    for (int y = 0; y < N; ++y) xline_body<T>(q, y, w.h.m, pl, tw.data(), Tb.data(), a, B.data(), kOne);
+    for (int y = 0; y < N; ++y) xline_body<T, NC>(q, y, w.h.m, pl, tw.data(), Tb.data(), a, B.data(), kOne);
   Epi<T> e{};
   e.out = out.data(); e.ldo = nw; e.pin = X.data(); e.ldp = nw; e.vcoef = T(1); e.kin = T(1);
   e.shift = sh.data(); e.n_sys = n_sys;
   for (int q = 0; q < pairs; ++q)
     for (int hp = 0; hp <= w.h.m; ++hp)
-      plane_r2g_body<T>(q, hp, w.tab(), pl, tw.data(), Tb.data(), e, B.data(), Zp.data(), kOne);
+      plane_r2g_body<T, NC>(q, hp, w.tab(), pl, tw.data(), Tb.data(), e, B.data(), Zp.data(), kOne);
   for (size_t i = 0; i < out.size(); ++i) outd[i] = (double)out[i];
 }
 
@@ -139,10 +139,39 @@ int emu_fft_position(int N, int n) {
 }
 
 // (H - shift_s) applied to real-basis vectors X (n_sys x nrb) via the plane / x-line / plane bodies.
+// flags bit 0: FP32; bit 1: the compile-time-N bodies (N = 24 only).
 int emu_apply_h(double L, double ecut, int N, const double* vloc_c, int n_sys, const double* X,
-                const double* shift, double* out, int fp32) {
-  if (fp32) apply_h_impl<float>(L, ecut, N, vloc_c, n_sys, X, shift, out);
-  else apply_h_impl<double>(L, ecut, N, vloc_c, n_sys, X, shift, out);
+                const double* shift, double* out, int flags) {
+  const bool fp32 = flags & 1, ct = flags & 2;
+  if (ct && N != 24) return 1;
+  if (fp32) {
+    if (ct) apply_h_impl<float, 24>(L, ecut, N, vloc_c, n_sys, X, shift, out);
+    else apply_h_impl<float>(L, ecut, N, vloc_c, n_sys, X, shift, out);
+  } else {
+    if (ct) apply_h_impl<double, 24>(L, ecut, N, vloc_c, n_sys, X, shift, out);
+    else apply_h_impl<double>(L, ecut, N, vloc_c, n_sys, X, shift, out);
+  }
+  return 0;
+}
+
+// Compile-time-N line transforms (N in {24, 32, 48, 64, 96}); dir as emu_fft_line.
+int emu_fft_line_ct(int N, int dir, const double* in, double* out) {
+  FftPlan pl;
+  if (!make_plan(N, pl)) return 1;
+  auto tw = twiddles<double>(N);
+  std::vector<cplx<double>> b(N);
+  for (int i = 0; i < N; ++i) b[i] = mk<double>(in[2 * i], in[2 * i + 1]);
+#define EMU_CT(NN)                                                                             \
+  case NN:                                                                                     \
+    if (dir == 0) fft_dif_n<double, NN>(b.data(), pl, tw.data(), +1, 1, N, 1, -1, kOne);       \
+    else fft_dit_n<double, NN>(b.data(), pl, tw.data(), -1, 1, N, 1, -1, kOne);                \
+    break;
+  switch (N) {
+    EMU_CT(24) EMU_CT(32) EMU_CT(48) EMU_CT(64) EMU_CT(96)
+    default: return 1;
+  }
+#undef EMU_CT
+  for (int i = 0; i < N; ++i) { out[2 * i] = b[i].re; out[2 * i + 1] = b[i].im; }
   return 0;
 }
 

@@ -109,6 +109,23 @@ def test_line_fft_dif_dit(emu, N):
     assert np.max(np.abs(w - np.fft.fft(z))) < 1e-12 * N
 
 
+@pytest.mark.parametrize("N", [24, 32, 48, 64, 96])
+def test_line_fft_compile_time_sizes(emu, N):
+    rng = np.random.default_rng(N + 1)
+    x = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    xin, xp = P(np.stack([x.real, x.imag], 1).ravel())
+    out = np.zeros(2 * N)
+    assert emu.emu_fft_line_ct(N, 0, xp, out.ctypes.data_as(dp)) == 0
+    pos = np.array([emu.emu_fft_position(N, k) for k in range(N)])
+    y = out[0::2] + 1j * out[1::2]
+    assert np.max(np.abs(y[pos] - np.fft.ifft(x) * N)) < 1e-12 * N
+    zin = np.zeros(N, np.complex128)
+    zin[pos] = x
+    zi, zp = P(np.stack([zin.real, zin.imag], 1).ravel())
+    emu.emu_fft_line_ct(N, 1, zp, out.ctypes.data_as(dp))
+    assert np.max(np.abs(out[0::2] + 1j * out[1::2] - np.fft.fft(x))) < 1e-12 * N
+
+
 def test_real_basis_roundtrip(emu):
     L, ecut, N = 10.0, 5.0, 24
     mp = Maps(emu, L, ecut, N)
@@ -131,7 +148,7 @@ def test_real_basis_roundtrip(emu):
     assert abs(mp.to_rb(A)[0] @ mp.to_rb(A)[1] - np.vdot(A[:, 0], A[:, 1]).real) < 1e-12
 
 
-@pytest.mark.parametrize("fp32", [0, 1])
+@pytest.mark.parametrize("fp32", [0, 1, 2, 3])
 def test_apply_h_bodies_equal_dense_h(emu, cfg24, fp32):
     s = cfg24
     m = Model(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v)
@@ -148,7 +165,7 @@ def test_apply_h_bodies_equal_dense_h(emu, cfg24, fp32):
                     out.ctypes.data_as(dp), fp32)
     ref = m.h_dense() @ mp.to_c(X) + shift[None, :] * mp.to_c(X)
     got = mp.to_c(out.reshape(n_sys, mp.nrb))
-    tol = 2e-6 if fp32 else 1e-13
+    tol = 2e-6 if fp32 & 1 else 1e-13
     assert np.max(np.abs(got - ref)) < tol * np.max(np.abs(ref))
 
 
