@@ -68,6 +68,11 @@ typedef struct wgw_options {
   double inner_tol;    /* MIXED: relative residual reduction of each inner FP32 solve */
   double f_s;          /* occupation of each state (2 = spin-unpolarised, the sum over sigma of Eq. dfpt) */
   int check_every;     /* CG iterations between convergence polls by the host */
+  double dav_tol;      /* Davidson: max |lambda_i(k) - lambda_i(k-1)| <= dav_tol and every Ritz residual
+                          norm <= sqrt(dav_tol) */
+  int dav_max_iter;    /* Davidson iterations */
+  int dav_factor;      /* Davidson subspace limit = dav_factor * n_pdep (Sec. 4.2: 4) */
+  int seed;            /* start block seed when none is given */
 } wgw_options;
 
 typedef struct wgw_stats {
@@ -79,7 +84,7 @@ typedef struct wgw_stats {
 } wgw_stats;
 
 /* Fills *opt with defaults: WGW_FP64, cg_tol 1e-12, max_cg_iter 2000, max_refine 8,
- * inner_tol 1e-5, f_s 2, check_every 8. */
+ * inner_tol 1e-5, f_s 2, check_every 8, dav_tol 1e-8, dav_max_iter 100, dav_factor 4, seed 12345. */
 int wgw_default_options(wgw_options* opt);
 
 /*
@@ -163,6 +168,33 @@ const char* wgw_profile_kind_name(int kind);
  * or negative n.
  */
 int wgw_system_info(const wgw_ctx* ctx, int n, int* iters, double* rel_residual);
+
+/*
+ * PDEP basis (Sec. 3): the n_pdep leading (most negative) eigenpairs of chi0bar(omega = 0) by a
+ * block Davidson iteration.  Start from an orthonormalised block, apply chi0bar (batched
+ * Sternheimer solves in the context's precision), Rayleigh-Ritz in FP64 on the GPU, expand with
+ * the residuals of unconverged pairs orthogonalised in FP64, restart from the Ritz vectors
+ * when the subspace would exceed dav_factor * n_pdep (Sec. 4.2).  Converged when the eigenvalues
+ * moved by at most dav_tol and every Ritz residual norm is at most sqrt(dav_tol).
+ *   x0     host, N_rho x n_pdep complex start block (its real-in-r part is used), or NULL for
+ *          a seeded block of uniform numbers weighted by v^1/2 (opt.seed).
+ *   eig    host, n_pdep eigenvalues, ascending (most negative first).
+ *   basis  host, N_rho x n_pdep complex eigenvectors (orthonormal in sum_G conj(a) b), or NULL.
+ *   st     n_systems = Sternheimer systems solved, n_converged = converged pairs,
+ *          max_iters = Davidson iterations, refinements = chi0bar block applications,
+ *          max_rel_residual = largest Ritz residual norm.
+ * Returns WGW_ERR_NOCONV (outputs written) if not converged in dav_max_iter iterations.
+ */
+int wgw_pdep_davidson(wgw_ctx* ctx, int n_pdep, const double* x0, double* eig, double* basis,
+                      wgw_stats* st);
+
+/*
+ * Dense symmetric eigensolver of the Rayleigh-Ritz step (Sec. 4.2): A = Z diag(w) Z^T in FP64
+ * on the GPU, one thread block (Householder tridiagonalisation, implicit-shift QL).  Device
+ * pointers: A n x n column-major (overwritten), w n (ascending), Z n x n column-major.
+ * 1 <= n <= 2048.  Work is enqueued on `stream` and the call returns when it completes.
+ */
+int wgw_symm_eig_dev(int n, double* A_dev, double* w_dev, double* Z_dev, void* stream);
 
 /* Releases the context and all device memory it owns.  NULL is allowed. */
 void wgw_destroy(wgw_ctx* ctx);

@@ -97,6 +97,37 @@ def sos_drho(model: Model, dV: np.ndarray, omegas=(0.0,)) -> np.ndarray:
     return out * (model.f_s / model.omega)
 
 
+def sos_static_block(model: Model, dV: np.ndarray, states=None) -> np.ndarray:
+    """Static (w = 0) sum over states for a block of perturbations that are real in r.
+
+    For such dV the two terms of the Adler-Wiser form are complex conjugates, so
+    drho(r) = (f_s/Omega) sum_v 2 Re[ psi_v^*(r) y_v(r) ],  y_v = sum_c psi_c <c|dV|v> / (e_v - e_c).
+    The same arithmetic as sos_drho, evaluated for all perturbations at once.
+    `states` = (eigenvalues, eigenvectors) of H may be passed to reuse a diagonalisation.
+    Returns drho(G) on the density sphere, shape (N_rho, n_pert).
+    """
+    dV = np.asarray(dV, np.complex128)
+    w, U = _states(model) if states is None else states
+    nv = model.psi_v.shape[1]
+    occ, emp = U[:, :nv], U[:, nv:]
+    N = model.N
+    dV_r = np.stack([model.to_r(dV[:, p], model.mr) for p in range(dV.shape[1])], axis=-1)
+    rho_r = np.zeros(dV_r.shape, np.float64)
+    iw = np.mod(model.mw, N)
+    for v in range(nv):
+        pv = model.to_r(occ[:, v], model.mw)
+        prod = np.fft.fftn(pv[..., None] * dV_r, axes=(0, 1, 2)) / N ** 3
+        W = prod[iw[:, 0], iw[:, 1], iw[:, 2], :]                  # [dV psi_v] on the sphere
+        Y = emp @ ((emp.conj().T @ W) / (w[v] - w[nv:])[:, None])
+        grid = np.zeros((N, N, N, Y.shape[1]), np.complex128)
+        grid[iw[:, 0], iw[:, 1], iw[:, 2], :] = Y
+        y_r = np.fft.ifftn(grid, axes=(0, 1, 2)) * N ** 3
+        rho_r += 2.0 * (pv.conj()[..., None] * y_r).real
+    out = np.fft.fftn(rho_r, axes=(0, 1, 2)) / N ** 3
+    ir = np.mod(model.mr, N)
+    return out[ir[:, 0], ir[:, 1], ir[:, 2], :] * (model.f_s / model.omega)
+
+
 def _pc(model: Model, x: np.ndarray) -> np.ndarray:
     """P_c x = x - sum_v psi_v <psi_v|x> (Sec. 3: P_c = 1 - P_v)."""
     P = model.psi_v

@@ -102,13 +102,17 @@ class Model:
         """H_GG' = 0.5|G|^2 delta_GG' + V(G - G') + sum_p beta_p(G) D_p beta_p(G')^*."""
         if self._dense is None:
             n = self.mw.shape[0]
-            where = {tuple(m): i for i, m in enumerate(self.mr.tolist())}
+            # V(G - G'): look the difference vectors up in the density sphere through a dense
+            # table indexed by Miller triples (every difference lies inside the density sphere).
+            M = int(np.max(np.abs(self.mr)))
+            box = np.full((2 * M + 1,) * 3, -1, np.int64)
+            box[self.mr[:, 0] + M, self.mr[:, 1] + M, self.mr[:, 2] + M] = np.arange(self.mr.shape[0])
             H = np.zeros((n, n), np.complex128)
             for i in range(n):
-                for j in range(n):
-                    d = (self.mw[i, 0] - self.mw[j, 0], self.mw[i, 1] - self.mw[j, 1],
-                         self.mw[i, 2] - self.mw[j, 2])
-                    H[i, j] = self.vloc_G[where[d]]
+                d = self.mw[i][None, :] - self.mw
+                idx = box[d[:, 0] + M, d[:, 1] + M, d[:, 2] + M]
+                assert np.all(idx >= 0)
+                H[i, :] = self.vloc_G[idx]
             H[np.diag_indices(n)] += 0.5 * self.g2w
             if self.beta.shape[1]:
                 H += self.beta @ np.diag(self.D) @ self.beta.conj().T

@@ -37,6 +37,23 @@ cudaError_t launch_drho_xline(int m, FftCtx<T> f, const cplx<T>* Tbuf, const T* 
 template <typename T>
 cudaError_t launch_pc(T* Y, long ldy, int n_sys, const int* list, const T* Psi, long ldp, int n, int nv,
                       const int* active, T* work, cudaStream_t st);
+// C = A^T B: A is K x m (column j at A + j*lda), B is K x n; C is written row-major with rows
+// of length n, padded to a multiple of 64 rows.  work: gemm_tn_work_elems(K, m, n) doubles.
+cudaError_t launch_gemm_tn(const double* A, long lda, const double* B, long ldb, int K, int m, int n, double* C,
+                           double* work, cudaStream_t st);
+size_t gemm_tn_work_elems(int K, int m, int n);
+// Y[:, j] = beta Y[:, j] + alpha sum_v A[:, v] C[v][j]: A is n x k, C row-major k x ncols (row length ldc).
+cudaError_t launch_gemm_nn(const double* A, long lda, int n, int k, const double* C, long ldc, int ncols,
+                           double* Y, long ldy, double alpha, double beta, cudaStream_t st);
+// Dense symmetric eigensolver (dense_kernels.cu): A = Z diag(w) Z^T, w ascending, n <= 2048.
+cudaError_t launch_syev(int n, double* A, int lda, double* w, double* Z, int ldz, double* work, int* info,
+                        cudaStream_t st);
+size_t syev_work_elems(int n);
+cudaError_t launch_ritz_residual(int n, int nb, const double* X, const double* AX, long ld, const double* theta,
+                                 double* R, double* rnorm, cudaStream_t st);
+cudaError_t launch_symmetrise(int m, double* T, int ldt, cudaStream_t st);
+cudaError_t launch_select_scale(int k, const double* Zc, int ldz, const int* cols, const double* scale, int nc,
+                                double* out, int ldo, cudaStream_t st);
 // Ordered list of the systems s < n_sys with active[s] != 0, and their count.
 cudaError_t launch_build_list(const int* active, int n_sys, int* list, int* count, cudaStream_t st);
 int pc_kblocks(int n, int n_sys);

@@ -205,6 +205,15 @@ __global__ void __launch_bounds__(256) k_pc_gemm1(const T* __restrict__ Psi, lon
   }
 }
 
+// C[e] = sum_kb Cpart[kb * slice + e] (fixed order).
+__global__ void k_sum_slices(const double* __restrict__ Cpart, size_t slice, int n_kb, double* __restrict__ C) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < slice; e += (size_t)gridDim.x * blockDim.x) {
+    double sum = Cpart[e];
+    for (int kb = 1; kb < n_kb; ++kb) sum += Cpart[(size_t)kb * slice + e];
+    C[e] = sum;
+  }
+}
+
 template <typename T>
 __global__ void k_pc_reduce(T* __restrict__ Cpart, size_t slice, int n_kb) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < slice; e += (size_t)gridDim.x * blockDim.x) {
@@ -214,10 +223,12 @@ __global__ void k_pc_reduce(T* __restrict__ Cpart, size_t slice, int n_kb) {
   }
 }
 
+// Y[:, s_j] = beta Y[:, s_j] + alpha sum_v Psi[:, v] C[v][j]   (C row length ldc; beta = 0 never reads Y).
 template <typename T>
 __global__ void __launch_bounds__(256) k_pc_gemm2(const T* __restrict__ Psi, long ldp, T* __restrict__ Y,
                                                   long ldy, int n, int nv, int n_list,
                                                   const int* __restrict__ list, const T* __restrict__ C,
+                                                  long ldc, T alpha, T beta,
                                                   const int* __restrict__ active) {
   __shared__ __align__(16) T Cs[kGT][kGT + 4];     // C[v][j] of one 64-state chunk
   __shared__ __align__(16) T Ps[kGT][kGT + 4];     // Psi[i][v] stored as Ps[v][i]
@@ -237,7 +248,7 @@ __global__ void __launch_bounds__(256) k_pc_gemm2(const T* __restrict__ Psi, lon
   for (int vc = 0; vc < nv; vc += kGT) {
     for (int e = tid; e < kGT * kGT; e += 256) {
       const int c = e % kGT, vv = e / kGT, v = vc + vv, jx = j0 + c;
-      Cs[vv][c] = (jx < n_list && v < nv) ? C[(size_t)v * n_list + jx] : T(0);
+      Cs[vv][c] = (jx < n_list && v < nv) ? C[(size_t)v * ldc + jx] : T(0);
       const int i = i0 + c;
       Ps[vv][c] = (v < nv && i < n) ? Psi[(size_t)v * ldp + i] : T(0);
     }
@@ -267,16 +278,17 @@ __global__ void __launch_bounds__(256) k_pc_gemm2(const T* __restrict__ Psi, lon
     if (r0 + 4 <= n) {
 #pragma unroll
       for (int q = 0; q < 4; q += V) {
-        VT w = *reinterpret_cast<VT*>(y + q);
+        VT w;
+        if (beta != T(0)) w = *reinterpret_cast<VT*>(y + q);
         T* wp = reinterpret_cast<T*>(&w);
 #pragma unroll
-        for (int u = 0; u < V; ++u) wp[u] -= acc[q + u][j];
+        for (int u = 0; u < V; ++u) wp[u] = (beta != T(0) ? beta * wp[u] : T(0)) + alpha * acc[q + u][j];
         *reinterpret_cast<VT*>(y + q) = w;
       }
     } else {
 #pragma unroll
       for (int i = 0; i < 4; ++i)
-        if (r0 + i < n) y[i] -= acc[i][j];
+        if (r0 + i < n) y[i] = (beta != T(0) ? beta * y[i] : T(0)) + alpha * acc[i][j];
     }
   }
 }
@@ -341,7 +353,40 @@ cudaError_t launch_pc(T* Y, long ldy, int n_sys, const int* list, const T* Psi, 
     if (err != cudaSuccess) return err;
   }
   dim3 g2((n + kGT - 1) / kGT, (n_sys + kGT - 1) / kGT);
-  k_pc_gemm2<T><<<g2, 256, 0, st>>>(Psi, ldp, Y, ldy, n, nv, n_sys, list, work, active);
+  k_pc_gemm2<T><<<g2, 256, 0, st>>>(Psi, ldp, Y, ldy, n, nv, n_sys, list, work, (long)n_sys, T(-1), T(1),
+                                    active);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_tn(const double* A, long lda, const double* B, long ldb, int K, int m, int n, double* C,
+                           double* work, cudaStream_t st) {
+  if (m == 0 || n == 0) return cudaSuccess;
+  const int n_kb = pc_kblocks(K, n);
+  const int kblk = ((K + n_kb - 1) / n_kb + kGK - 1) / kGK * kGK;
+  const int mp = (m + kGT - 1) / kGT * kGT;
+  dim3 g1((n + kGT - 1) / kGT, n_kb, mp / kGT);
+  k_pc_gemm1<double><<<g1, 256, 0, st>>>(A, lda, B, ldb, K, m, n, nullptr, kblk, work);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  const size_t slice = (size_t)mp * n;
+  k_sum_slices<<<(int)std::min<size_t>((slice + 255) / 256, 4096), 256, 0, st>>>(work, slice, n_kb, C);
+  return cudaGetLastError();
+}
+
+size_t gemm_tn_work_elems(int K, int m, int n) {
+  const int mp = (m + kGT - 1) / kGT * kGT;
+  return (size_t)pc_kblocks(K, n) * mp * n;
+}
+
+cudaError_t launch_gemm_nn(const double* A, long lda, int n, int k, const double* C, long ldc, int ncols,
+                           double* Y, long ldy, double alpha, double beta, cudaStream_t st) {
+  if (ncols == 0 || n == 0) return cudaSuccess;
+  if (k == 0) {
+    if (beta == 1.0) return cudaSuccess;
+    return cudaErrorInvalidValue;
+  }
+  dim3 g2((n + kGT - 1) / kGT, (ncols + kGT - 1) / kGT);
+  k_pc_gemm2<double><<<g2, 256, 0, st>>>(A, lda, Y, ldy, n, k, ncols, nullptr, C, ldc, alpha, beta, nullptr);
   return cudaGetLastError();
 }
 

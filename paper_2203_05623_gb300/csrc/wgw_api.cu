@@ -434,42 +434,13 @@ int solve_all(wgw_ctx* c, int n_sys, cudaStream_t st, wgw_stats* stats) {
   return conv == n_sys ? WGW_OK : fail(WGW_ERR_NOCONV, "some Sternheimer systems missed cg_tol");
 }
 
-// Core of chi0 / chibar0 application; dV and drho in device memory.
-int apply_core(wgw_ctx* c, const double* dV, int n_pert, const double* omega, int n_omega,
-               double* drho, bool symmetrized, cudaStream_t st, wgw_stats* stats) {
-  if (!c) return fail(WGW_ERR_ARG, "null context");
-  if (n_pert < 0 || n_omega < 1 || !omega) return fail(WGW_ERR_ARG, "need n_pert >= 0 and n_omega >= 1");
-  for (int k = 0; k < n_omega; ++k)
-    if (omega[k] != 0.0) return fail(WGW_ERR_ARG, "this version applies chi0 at omega = 0 only");
-  if (n_pert == 0) return WGW_OK;
-  if (!dV || !drho) return fail(WGW_ERR_ARG, "null dV or drho");
+// drho = chi0 dV for n_real perturbations that are real in r, given and returned in
+// real-basis form (rows of length ld_r): dV in dvrb, drho into c->drho_rb.  Steps 2-6
+// of the apply: system tables, dV(r), right-hand sides, Sternheimer solves, drho.
+int chi0_rb(wgw_ctx* c, const double* dvrb, int n_real, cudaStream_t st, wgw_stats* stats) {
   const int N = c->N, n_v = c->n_v;
   const long ldr = c->ld_r, ldw = c->ld_w;
   const HostSphere& rs = c->rho;
-  const double* scale = symmetrized ? rs.d_vsqrt.as<double>() : nullptr;
-  // 1. Real-in-r parts of each perturbation: rows [0, n_pert) = Hermitian parts,
-  //    rows n_pert + k = the non-zero anti-Hermitian parts.
-  WGW_TRY(c->dv_rb.ensure(sizeof(double) * (size_t)2 * n_pert * ldr));
-  double* dvrb = c->dv_rb.as<double>();
-  WGW_CK(cudaMemsetAsync(dvrb, 0, sizeof(double) * (size_t)2 * n_pert * ldr, st));
-  const double cb = 16.0 * n_pert * rs.n + 8.0 * n_pert * rs.nrb();
-  WGW_CK(c->prof.run(PK_CONV, cb, 0, st, [&] { return launch_sphere_to_rb(n_pert, dV, 2L * rs.n, scale, rs.map(), 0, dvrb, ldr, st); }));
-  WGW_CK(c->prof.run(PK_CONV, cb, 0, st, [&] { return launch_sphere_to_rb(n_pert, dV, 2L * rs.n, scale, rs.map(), 1, dvrb + (size_t)n_pert * ldr, ldr, st); }));
-  WGW_TRY(c->norms.ensure(sizeof(double) * 2 * n_pert));
-  WGW_CK(c->prof.run(PK_OTHER, 16.0 * n_pert * rs.nrb(), 0, st, [&] { return launch_norm2<double>(2 * n_pert, rs.nrb(), dvrb, ldr, c->norms.as<double>(), st); }));
-  std::vector<double> nrm(2 * n_pert);
-  WGW_CK(cudaMemcpyAsync(nrm.data(), c->norms.p, sizeof(double) * 2 * n_pert, cudaMemcpyDeviceToHost, st));
-  WGW_CK(cudaStreamSynchronize(st));
-  std::vector<int> brow(n_pert, -1);
-  int n_real = n_pert;
-  for (int p = 0; p < n_pert; ++p) {
-    if (nrm[n_pert + p] > 0.0) {
-      if (n_real != n_pert + p)
-        WGW_CK(cudaMemcpyAsync(dvrb + (size_t)n_real * ldr, dvrb + (size_t)(n_pert + p) * ldr,
-                               sizeof(double) * ldr, cudaMemcpyDeviceToDevice, st));
-      brow[p] = n_real++;
-    }
-  }
   const int n_sys = n_real * n_v;
   WGW_TRY(ensure_work(c, n_sys, n_real));
   // 2. System tables: s = r * n_v + v.
@@ -491,8 +462,6 @@ int apply_core(wgw_ctx* c, const double* dV, int n_pert, const double* omega, in
     WGW_CK(cudaMemcpyAsync(c->f.shift.p, shiftf.data(), sizeof(float) * n_sys, cudaMemcpyHostToDevice, st));
   WGW_CK(cudaMemcpyAsync(c->a_idx.p, ai.data(), sizeof(int) * n_sys, cudaMemcpyHostToDevice, st));
   WGW_CK(cudaMemcpyAsync(c->b_idx.p, bi.data(), sizeof(int) * n_sys, cudaMemcpyHostToDevice, st));
-  WGW_TRY(c->brow.ensure(sizeof(int) * n_pert));
-  WGW_CK(cudaMemcpyAsync(c->brow.p, brow.data(), sizeof(int) * n_pert, cudaMemcpyHostToDevice, st));
   // 3. dV_r(r) for every real perturbation.
   double* dvr = c->dv_r.as<double>();
   WGW_TRY(to_real<double>(c, c->d, rs, dvrb, ldr, n_real, dvr, c->Trho, st));
@@ -541,6 +510,48 @@ int apply_core(wgw_ctx* c, const double* dV, int n_pert, const double* omega, in
     WGW_CK(c->prof.run(PK_R2G, tr + (double)n_real * rs.nrb() * sizeof(double), 0, st, [&] {
       return launch_plane_r2g<double>(rs.tab(), rs.npt_max, f, c->Trho.as<cplx<double>>(), e, st); }));
   }
+  return solve_status;
+}
+
+// Core of chi0 / chibar0 application; dV and drho in device memory.
+int apply_core(wgw_ctx* c, const double* dV, int n_pert, const double* omega, int n_omega,
+               double* drho, bool symmetrized, cudaStream_t st, wgw_stats* stats) {
+  if (!c) return fail(WGW_ERR_ARG, "null context");
+  if (n_pert < 0 || n_omega < 1 || !omega) return fail(WGW_ERR_ARG, "need n_pert >= 0 and n_omega >= 1");
+  for (int k = 0; k < n_omega; ++k)
+    if (omega[k] != 0.0) return fail(WGW_ERR_ARG, "this version applies chi0 at omega = 0 only");
+  if (n_pert == 0) return WGW_OK;
+  if (!dV || !drho) return fail(WGW_ERR_ARG, "null dV or drho");
+  const long ldr = c->ld_r;
+  const HostSphere& rs = c->rho;
+  const double* scale = symmetrized ? rs.d_vsqrt.as<double>() : nullptr;
+  // 1. Real-in-r parts of each perturbation: rows [0, n_pert) = Hermitian parts,
+  //    rows n_pert + k = the non-zero anti-Hermitian parts.
+  WGW_TRY(c->dv_rb.ensure(sizeof(double) * (size_t)2 * n_pert * ldr));
+  double* dvrb = c->dv_rb.as<double>();
+  WGW_CK(cudaMemsetAsync(dvrb, 0, sizeof(double) * (size_t)2 * n_pert * ldr, st));
+  const double cb = 16.0 * n_pert * rs.n + 8.0 * n_pert * rs.nrb();
+  WGW_CK(c->prof.run(PK_CONV, cb, 0, st, [&] { return launch_sphere_to_rb(n_pert, dV, 2L * rs.n, scale, rs.map(), 0, dvrb, ldr, st); }));
+  WGW_CK(c->prof.run(PK_CONV, cb, 0, st, [&] { return launch_sphere_to_rb(n_pert, dV, 2L * rs.n, scale, rs.map(), 1, dvrb + (size_t)n_pert * ldr, ldr, st); }));
+  WGW_TRY(c->norms.ensure(sizeof(double) * 2 * n_pert));
+  WGW_CK(c->prof.run(PK_OTHER, 16.0 * n_pert * rs.nrb(), 0, st, [&] { return launch_norm2<double>(2 * n_pert, rs.nrb(), dvrb, ldr, c->norms.as<double>(), st); }));
+  std::vector<double> nrm(2 * n_pert);
+  WGW_CK(cudaMemcpyAsync(nrm.data(), c->norms.p, sizeof(double) * 2 * n_pert, cudaMemcpyDeviceToHost, st));
+  WGW_CK(cudaStreamSynchronize(st));
+  std::vector<int> brow(n_pert, -1);
+  int n_real = n_pert;
+  for (int p = 0; p < n_pert; ++p) {
+    if (nrm[n_pert + p] > 0.0) {
+      if (n_real != n_pert + p)
+        WGW_CK(cudaMemcpyAsync(dvrb + (size_t)n_real * ldr, dvrb + (size_t)(n_pert + p) * ldr,
+                               sizeof(double) * ldr, cudaMemcpyDeviceToDevice, st));
+      brow[p] = n_real++;
+    }
+  }
+  WGW_TRY(c->brow.ensure(sizeof(int) * n_pert));
+  WGW_CK(cudaMemcpyAsync(c->brow.p, brow.data(), sizeof(int) * n_pert, cudaMemcpyHostToDevice, st));
+  const int solve_status = chi0_rb(c, dvrb, n_real, st, stats);
+  if (solve_status != WGW_OK && solve_status != WGW_ERR_NOCONV) return solve_status;
   // 7. Complex output drho_p = chi0 A_p + i chi0 B_p for every frequency (all omega = 0 here).
   for (int k = 0; k < n_omega; ++k)
     WGW_CK(c->prof.run(PK_CONV, 16.0 * n_pert * rs.n + 8.0 * n_pert * rs.nrb(), 0, st, [&] {
@@ -549,6 +560,246 @@ int apply_core(wgw_ctx* c, const double* dV, int n_pert, const double* omega, in
   WGW_CK(cudaStreamSynchronize(st));
   c->prof.flush();
   return solve_status;
+}
+
+
+// ---------------------------------------------------------------- PDEP Davidson (Sec. 3, Sec. 4.2)
+__global__ void k_scale_rows(int n, int nb, const double* __restrict__ in, long ldi, const double* __restrict__ sc,
+                             double* __restrict__ out, long ldo) {
+  for (int j = blockIdx.y; j < nb; j += gridDim.y)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+      out[(size_t)j * ldo + i] = (sc ? sc[i] : 1.0) * in[(size_t)j * ldi + i];
+}
+
+// Start vectors when none are given: uniform numbers in (-1, 1) from a counter-based
+// hash (splitmix64 of seed and element index), weighted by v^1/2 so that the block
+// leans towards long wavelengths.
+__global__ void k_start_block(int n, int nb, unsigned long long seed, const double* __restrict__ vs,
+                              double* __restrict__ out, long ld) {
+  for (int j = blockIdx.y; j < nb; j += gridDim.y)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      unsigned long long z = seed + 0x9E3779B97F4A7C15ull * ((unsigned long long)j * n + i + 1);
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z ^= z >> 31;
+      const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+      out[(size_t)j * ld + i] = (2.0 * u - 1.0) * vs[i];
+    }
+}
+
+struct Davidson {
+  wgw_ctx* c;
+  cudaStream_t st;
+  int nr;           // real-basis length of the density sphere
+  long ld;
+  DevBuf vs_rb, gwork, Cbuf, Gbuf, Ubuf, sbuf, syw, info, cols, scl, Ysel;
+
+  int gemm_tn(const double* A, int m, const double* B, int n, double* C) {
+    WGW_TRY(gwork.ensure(sizeof(double) * gemm_tn_work_elems(nr, m, n)));
+    WGW_CK(c->prof.run(PK_OTHER, 8.0 * (double)nr * (m + n), 2.0 * nr * m * n, st, [&] {
+      return launch_gemm_tn(A, ld, B, ld, nr, m, n, C, gwork.as<double>(), st); }));
+    return WGW_OK;
+  }
+  int gemm_nn(const double* A, int k, const double* C, int ldc, int ncols, double* Y, double alpha, double beta) {
+    WGW_CK(c->prof.run(PK_OTHER, 8.0 * (double)nr * (k + 2 * ncols), 2.0 * nr * k * ncols, st, [&] {
+      return launch_gemm_nn(A, ld, nr, k, C, ldc, ncols, Y, ld, alpha, beta, st); }));
+    return WGW_OK;
+  }
+  int syev(int n, double* A, double* w, double* Z) {
+    WGW_TRY(syw.ensure(sizeof(double) * syev_work_elems(n)));
+    WGW_TRY(info.ensure(sizeof(int)));
+    WGW_CK(c->prof.run(PK_OTHER, 16.0 * n * n, 3.0 * n * n * n, st, [&] {
+      return launch_syev(n, A, n, w, Z, n, syw.as<double>(), info.as<int>(), st); }));
+    int h = 0;
+    WGW_CK(cudaMemcpyAsync(&h, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    WGW_CK(cudaStreamSynchronize(st));
+    if (h != 0) return fail(WGW_ERR_NOCONV, "dense eigensolver did not converge");
+    return WGW_OK;
+  }
+  // B <- B - V (V^T B), twice.
+  int orth_against(double* B, int nb, const double* V, int size) {
+    if (size == 0 || nb == 0) return WGW_OK;
+    const int mp = (size + 63) / 64 * 64;
+    WGW_TRY(Cbuf.ensure(sizeof(double) * (size_t)mp * nb));
+    for (int pass = 0; pass < 2; ++pass) {
+      WGW_TRY(gemm_tn(V, size, B, nb, Cbuf.as<double>()));
+      WGW_TRY(gemm_nn(V, size, Cbuf.as<double>(), nb, nb, B, -1.0, 1.0));
+    }
+    return WGW_OK;
+  }
+  // dest <- B U_keep diag(s_keep^-1/2) from the Gram matrix B^T B = U diag(s) U^T, dropping
+  // directions with s below 1e-12 s_max.  dest must not alias B.  Returns the kept count.
+  int orthonormalize(const double* B, int nb, double* dest, int* kept) {
+    *kept = 0;
+    if (nb == 0) return WGW_OK;
+    const int mp = (nb + 63) / 64 * 64;
+    WGW_TRY(Gbuf.ensure(sizeof(double) * (size_t)mp * nb));
+    WGW_TRY(Ubuf.ensure(sizeof(double) * (size_t)nb * nb));
+    WGW_TRY(sbuf.ensure(sizeof(double) * nb));
+    WGW_TRY(gemm_tn(B, nb, B, nb, Gbuf.as<double>()));
+    WGW_CK(launch_symmetrise(nb, Gbuf.as<double>(), nb, st));
+    WGW_TRY(syev(nb, Gbuf.as<double>(), sbuf.as<double>(), Ubuf.as<double>()));
+    std::vector<double> sv(nb);
+    WGW_CK(cudaMemcpyAsync(sv.data(), sbuf.p, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+    WGW_CK(cudaStreamSynchronize(st));
+    const double smax = sv[nb - 1];
+    std::vector<int> keep;
+    std::vector<double> sc;
+    for (int i = nb - 1; i >= 0; --i)
+      if (smax > 0 && sv[i] > 1e-12 * smax) { keep.push_back(i); sc.push_back(1.0 / std::sqrt(sv[i])); }
+    const int nk = (int)keep.size();
+    if (nk == 0) return WGW_OK;
+    WGW_TRY(cols.ensure(sizeof(int) * nk));
+    WGW_TRY(scl.ensure(sizeof(double) * nk));
+    WGW_TRY(Ysel.ensure(sizeof(double) * (size_t)nb * nk));
+    WGW_CK(cudaMemcpyAsync(cols.p, keep.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, st));
+    WGW_CK(cudaMemcpyAsync(scl.p, sc.data(), sizeof(double) * nk, cudaMemcpyHostToDevice, st));
+    WGW_CK(launch_select_scale(nb, Ubuf.as<double>(), nb, cols.as<int>(), scl.as<double>(), nk, Ysel.as<double>(), nk, st));
+    WGW_TRY(gemm_nn(B, nb, Ysel.as<double>(), nk, nk, dest, 1.0, 0.0));
+    *kept = nk;
+    return WGW_OK;
+  }
+  // out = chibar0 in for nb vectors (real basis): v^1/2 chi0 v^1/2.
+  int chibar0(const double* in, int nb, double* out, wgw_stats* acc) {
+    WGW_TRY(c->dv_rb.ensure(sizeof(double) * (size_t)nb * ld));
+    double* dv = c->dv_rb.as<double>();
+    dim3 g(std::max(1, std::min(64, (nr + 255) / 256)), std::min(nb, 65535));
+    k_scale_rows<<<g, 256, 0, st>>>(nr, nb, in, ld, vs_rb.as<double>(), dv, ld);
+    WGW_CK(cudaGetLastError());
+    wgw_stats s1{};
+    const int rc = chi0_rb(c, dv, nb, st, &s1);
+    if (rc != WGW_OK && rc != WGW_ERR_NOCONV) return rc;
+    k_scale_rows<<<g, 256, 0, st>>>(nr, nb, c->drho_rb.as<double>(), ld, vs_rb.as<double>(), out, ld);
+    WGW_CK(cudaGetLastError());
+    acc->n_systems += s1.n_systems;
+    acc->max_rel_residual = std::max(acc->max_rel_residual, s1.max_rel_residual);
+    return WGW_OK;
+  }
+};
+
+int davidson_impl(wgw_ctx* c, int npd, const double* x0, double* eig, double* basis, wgw_stats* out_st) {
+  Davidson D;
+  D.c = c;
+  D.st = c->stream;
+  D.nr = c->rho.nrb();
+  D.ld = c->ld_r;
+  cudaStream_t st = c->stream;
+  const long ld = D.ld;
+  const int nr = D.nr;
+  const int kmax = c->opt.dav_factor * npd;
+  if (kmax > 2048) return fail(WGW_ERR_ARG, "Davidson subspace above 2048 vectors");
+  // v^1/2 per real-basis element of the density sphere (0 at G = 0).
+  {
+    std::vector<double> vs(nr, 0.0);
+    for (int j = 1; j <= c->rho.n_pairs; ++j) vs[2 * j - 1] = vs[2 * j] = c->rho.vsqrt[c->rho.pos[j]];
+    WGW_TRY(D.vs_rb.ensure(sizeof(double) * nr));
+    WGW_CK(cudaMemcpy(D.vs_rb.p, vs.data(), sizeof(double) * nr, cudaMemcpyHostToDevice));
+  }
+  DevBuf V, Wb, X, AX, R, Tmp, T, Z, theta, rn;
+  WGW_TRY(V.ensure(sizeof(double) * (size_t)kmax * ld));
+  WGW_TRY(Wb.ensure(sizeof(double) * (size_t)kmax * ld));
+  DevBuf* nbufs[] = {&X, &AX, &R, &Tmp};
+  for (DevBuf* b : nbufs) WGW_TRY(b->ensure(sizeof(double) * (size_t)npd * ld));
+  const int kpad = (kmax + 63) / 64 * 64;
+  WGW_TRY(T.ensure(sizeof(double) * (size_t)kpad * kmax));
+  WGW_TRY(Z.ensure(sizeof(double) * (size_t)kmax * kmax));
+  WGW_TRY(theta.ensure(sizeof(double) * kmax));
+  WGW_TRY(rn.ensure(sizeof(double) * npd));
+  WGW_CK(cudaMemsetAsync(V.p, 0, V.bytes, st));
+  WGW_CK(cudaMemsetAsync(R.p, 0, R.bytes, st));
+  // Start block.
+  if (x0) {
+    DevBuf xin;
+    WGW_TRY(xin.ensure(sizeof(double) * 2 * (size_t)c->rho.n * npd));
+    WGW_CK(cudaMemcpy(xin.p, x0, sizeof(double) * 2 * (size_t)c->rho.n * npd, cudaMemcpyHostToDevice));
+    WGW_CK(launch_sphere_to_rb(npd, xin.as<double>(), 2L * c->rho.n, nullptr, c->rho.map(), 0, R.as<double>(), ld, st));
+    WGW_CK(cudaStreamSynchronize(st));
+  } else {
+    dim3 g(std::max(1, std::min(64, (nr + 255) / 256)), std::min(npd, 65535));
+    k_start_block<<<g, 256, 0, st>>>(nr, npd, (unsigned long long)c->opt.seed, D.vs_rb.as<double>(), R.as<double>(), ld);
+    WGW_CK(cudaGetLastError());
+  }
+  wgw_stats acc{};
+  int size = 0, nb = 0, kept = 0;
+  WGW_TRY(D.orthonormalize(R.as<double>(), npd, Tmp.as<double>(), &kept));
+  WGW_TRY(D.orthonormalize(Tmp.as<double>(), kept, V.as<double>(), &nb));
+  if (nb < npd) return fail(WGW_ERR_ARG, "start block has rank below n_pdep");
+  std::vector<double> th_prev, th(kmax), rnh(npd);
+  int it = 0, converged = 0;
+  double max_res = 0.0;
+  for (it = 1; it <= c->opt.dav_max_iter && nb > 0; ++it) {
+    WGW_TRY(D.chibar0(V.as<double>() + (size_t)size * ld, nb, Wb.as<double>() + (size_t)size * ld, &acc));
+    acc.refinements += 1;
+    size += nb;
+    // Rayleigh-Ritz: T = V^T W, T = Z diag(theta) Z^T.
+    WGW_TRY(D.gemm_tn(V.as<double>(), size, Wb.as<double>(), size, T.as<double>()));
+    WGW_CK(launch_symmetrise(size, T.as<double>(), size, st));
+    WGW_TRY(D.syev(size, T.as<double>(), theta.as<double>(), Z.as<double>()));
+    // Ritz vectors and residuals of the npd lowest.
+    std::vector<int> first(npd);
+    for (int j = 0; j < npd; ++j) first[j] = j;
+    WGW_TRY(D.cols.ensure(sizeof(int) * npd));
+    WGW_TRY(D.Ysel.ensure(sizeof(double) * (size_t)size * npd));
+    WGW_CK(cudaMemcpyAsync(D.cols.p, first.data(), sizeof(int) * npd, cudaMemcpyHostToDevice, st));
+    WGW_CK(launch_select_scale(size, Z.as<double>(), size, D.cols.as<int>(), nullptr, npd, D.Ysel.as<double>(), npd, st));
+    WGW_TRY(D.gemm_nn(V.as<double>(), size, D.Ysel.as<double>(), npd, npd, X.as<double>(), 1.0, 0.0));
+    WGW_TRY(D.gemm_nn(Wb.as<double>(), size, D.Ysel.as<double>(), npd, npd, AX.as<double>(), 1.0, 0.0));
+    WGW_CK(launch_ritz_residual(nr, npd, X.as<double>(), AX.as<double>(), ld, theta.as<double>(), R.as<double>(),
+                                rn.as<double>(), st));
+    WGW_CK(cudaMemcpyAsync(th.data(), theta.p, sizeof(double) * npd, cudaMemcpyDeviceToHost, st));
+    WGW_CK(cudaMemcpyAsync(rnh.data(), rn.p, sizeof(double) * npd, cudaMemcpyDeviceToHost, st));
+    WGW_CK(cudaStreamSynchronize(st));
+    const double tol = c->opt.dav_tol, rtol = std::sqrt(tol);
+    double dth = 1e300;
+    if (!th_prev.empty()) {
+      dth = 0.0;
+      for (int j = 0; j < npd; ++j) dth = std::max(dth, std::fabs(th[j] - th_prev[j]));
+    }
+    th_prev.assign(th.begin(), th.begin() + npd);
+    max_res = 0.0;
+    converged = 0;
+    std::vector<int> sel;
+    for (int j = 0; j < npd; ++j) {
+      max_res = std::max(max_res, rnh[j]);
+      if (rnh[j] <= rtol) ++converged;
+      else sel.push_back(j);
+    }
+    if (dth <= tol && converged == npd) break;
+    if (sel.empty()) { sel.resize(npd); for (int j = 0; j < npd; ++j) sel[j] = j; }
+    // Gather the residuals to expand with into Tmp.
+    for (size_t q = 0; q < sel.size(); ++q)
+      WGW_CK(cudaMemcpyAsync(Tmp.as<double>() + q * ld, R.as<double>() + (size_t)sel[q] * ld, sizeof(double) * ld,
+                             cudaMemcpyDeviceToDevice, st));
+    const int nsel = (int)sel.size();
+    if (size + nsel > kmax) {
+      // Restart from the Ritz vectors and their images.
+      WGW_CK(cudaMemcpyAsync(V.p, X.p, sizeof(double) * (size_t)npd * ld, cudaMemcpyDeviceToDevice, st));
+      WGW_CK(cudaMemcpyAsync(Wb.p, AX.p, sizeof(double) * (size_t)npd * ld, cudaMemcpyDeviceToDevice, st));
+      size = npd;
+    }
+    WGW_TRY(D.orth_against(Tmp.as<double>(), nsel, V.as<double>(), size));
+    WGW_TRY(D.orthonormalize(Tmp.as<double>(), nsel, R.as<double>(), &kept));
+    WGW_TRY(D.orth_against(R.as<double>(), kept, V.as<double>(), size));
+    WGW_TRY(D.orthonormalize(R.as<double>(), kept, V.as<double>() + (size_t)size * ld, &nb));
+  }
+  if (eig) std::copy(th.begin(), th.begin() + npd, eig);
+  if (basis) {
+    DevBuf bout;
+    WGW_TRY(bout.ensure(sizeof(double) * 2 * (size_t)c->rho.n * npd));
+    WGW_CK(launch_rb_to_sphere(npd, X.as<double>(), ld, nullptr, nullptr, c->rho.map(), bout.as<double>(),
+                               2L * c->rho.n, st));
+    WGW_CK(cudaMemcpyAsync(basis, bout.p, sizeof(double) * 2 * (size_t)c->rho.n * npd, cudaMemcpyDeviceToHost, st));
+    WGW_CK(cudaStreamSynchronize(st));
+  }
+  c->prof.flush();
+  if (out_st) {
+    out_st->n_systems = acc.n_systems;
+    out_st->n_converged = converged;
+    out_st->max_iters = std::min(it, c->opt.dav_max_iter);
+    out_st->refinements = acc.refinements;
+    out_st->max_rel_residual = max_res;
+  }
+  return converged == npd ? WGW_OK : fail(WGW_ERR_NOCONV, "Davidson did not converge");
 }
 
 }  // namespace
@@ -564,6 +815,10 @@ int wgw_default_options(wgw_options* opt) {
   opt->inner_tol = 1e-5;
   opt->f_s = 2.0;
   opt->check_every = 8;
+  opt->dav_tol = 1e-8;
+  opt->dav_max_iter = 100;
+  opt->dav_factor = 4;
+  opt->seed = 12345;
   return WGW_OK;
 }
 
@@ -571,6 +826,8 @@ static int check_options(const wgw_options& o) {
   if (o.precision != WGW_FP64 && o.precision != WGW_MIXED) return fail(WGW_ERR_ARG, "bad precision");
   if (!(o.cg_tol > 0) || !(o.inner_tol > 0) || o.max_cg_iter < 1 || o.max_refine < 1 || !(o.f_s > 0))
     return fail(WGW_ERR_ARG, "bad tolerances or iteration limits");
+  if (!(o.dav_tol > 0) || o.dav_max_iter < 1 || o.dav_factor < 2)
+    return fail(WGW_ERR_ARG, "bad Davidson options");
   return WGW_OK;
 }
 
@@ -767,6 +1024,27 @@ int wgw_system_info(const wgw_ctx* c, int n, int* iters, double* rel_residual) {
     if (rel_residual) rel_residual[s] = c->last_relres[s];
   }
   return m;
+}
+
+int wgw_pdep_davidson(wgw_ctx* c, int n_pdep, const double* x0, double* eig, double* basis, wgw_stats* st) {
+  g_last_error.clear();
+  if (!c || n_pdep < 1 || !eig) return fail(WGW_ERR_ARG, "need a context, n_pdep >= 1 and eig");
+  if (n_pdep > c->rho.nrb() / 2) return fail(WGW_ERR_ARG, "n_pdep too large for the density sphere");
+  return davidson_impl(c, n_pdep, x0, eig, basis, st);
+}
+
+int wgw_symm_eig_dev(int n, double* A_dev, double* w_dev, double* Z_dev, void* stream) {
+  g_last_error.clear();
+  if (n < 1 || n > 2048 || !A_dev || !w_dev || !Z_dev) return fail(WGW_ERR_ARG, "need 1 <= n <= 2048 and buffers");
+  cudaStream_t st = (cudaStream_t)stream;
+  DevBuf wk, info;
+  WGW_TRY(wk.ensure(sizeof(double) * syev_work_elems(n)));
+  WGW_TRY(info.ensure(sizeof(int)));
+  WGW_CK(launch_syev(n, A_dev, n, w_dev, Z_dev, n, wk.as<double>(), info.as<int>(), st));
+  int h = 0;
+  WGW_CK(cudaMemcpyAsync(&h, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  WGW_CK(cudaStreamSynchronize(st));
+  return h == 0 ? WGW_OK : fail(WGW_ERR_NOCONV, "dense eigensolver did not converge");
 }
 
 void wgw_destroy(wgw_ctx* c) { delete c; }

@@ -32,7 +32,8 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("cg_tol", ctypes.c_double),
                 ("max_cg_iter", ctypes.c_int), ("max_refine", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("f_s", ctypes.c_double),
-                ("check_every", ctypes.c_int)]
+                ("check_every", ctypes.c_int), ("dav_tol", ctypes.c_double),
+                ("dav_max_iter", ctypes.c_int), ("dav_factor", ctypes.c_int), ("seed", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -75,6 +76,8 @@ def lib(path: str | None = None):
     L.wgw_profile_read.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_long), _dp, _dp]
     L.wgw_profile_kind_name.restype = ctypes.c_char_p
     L.wgw_profile_kind_name.argtypes = [ctypes.c_int]
+    L.wgw_pdep_davidson.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, _dp, _dp, ctypes.POINTER(Stats)]
+    L.wgw_symm_eig_dev.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     L.wgw_system_info.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp]
     L.wgw_destroy.argtypes = [ctypes.c_void_p]
     L.wgw_status_string.restype = ctypes.c_char_p
@@ -197,6 +200,34 @@ def wgw_profile_read(ctx: Context) -> dict:
         out[lib().wgw_profile_kind_name(k).decode()] = {"ms": ms.value, "launches": n.value,
                                                         "bytes": by.value, "flops": fl.value}
     return out
+
+
+def wgw_pdep_davidson(ctx: Context, n_pdep: int, x0=None, want_basis=True, allow_noconv=False):
+    """PDEP eigenpairs: (eigenvalues (n_pdep,), basis (N_rho, n_pdep) complex or None, stats, status)."""
+    eig = np.zeros(n_pdep)
+    xb = _interleave(x0) if x0 is not None else None
+    basis = np.zeros((n_pdep, ctx.n_rho), np.complex128) if want_basis else None
+    st = Stats()
+    s = lib().wgw_pdep_davidson(ctx.handle, n_pdep, xb.ctypes.data_as(_dp) if xb is not None else None,
+                                eig.ctypes.data_as(_dp),
+                                basis.view(np.float64).ctypes.data_as(_dp) if want_basis else None,
+                                ctypes.byref(st))
+    _check(s, "wgw_pdep_davidson", (WGW_OK, WGW_ERR_NOCONV) if allow_noconv else (WGW_OK,))
+    return eig, (basis.T if want_basis else None), st.as_dict(), s
+
+
+def wgw_symm_eig_dev(A_dev, stream=None):
+    """Symmetric eigensolver on device (torch float64 n x n, overwritten): returns (w, Z) torch tensors."""
+    import torch
+    n = A_dev.shape[0]
+    assert A_dev.is_cuda and A_dev.dtype == torch.float64 and A_dev.is_contiguous()
+    w = torch.empty(n, dtype=torch.float64, device=A_dev.device)
+    Z = torch.empty((n, n), dtype=torch.float64, device=A_dev.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(A_dev.device).cuda_stream
+    _check(lib().wgw_symm_eig_dev(n, ctypes.c_void_p(A_dev.data_ptr()), ctypes.c_void_p(w.data_ptr()),
+                                  ctypes.c_void_p(Z.data_ptr()), ctypes.c_void_p(stream)), "wgw_symm_eig_dev")
+    return w, Z
 
 
 def wgw_system_info(ctx: Context, n_sys: int):

@@ -88,6 +88,12 @@ def test_sos_equals_sternheimer(tiny, omegas):
     assert rel(chi0.sos_drho(m, dV, omegas), chi0.sternheimer_drho(m, dV, omegas)) < 1e-12
 
 
+def test_static_block_sum_equals_sos(cfg24):
+    m = model_of(cfg24)
+    dV = synth.perturbations(cfg24.miller_rho, cfg24.L, 3, 4)
+    assert rel(chi0.sos_static_block(m, dV), chi0.sos_drho(m, dV, [0.0])[:, :, 0]) < 1e-12
+
+
 def test_sos_equals_sternheimer_complex_perturbation(tiny):
     m = model_of(tiny)
     dV = synth.perturbations(tiny.miller_rho, tiny.L, 2, 11, hermitian=False)
