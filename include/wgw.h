@@ -196,6 +196,20 @@ int wgw_pdep_davidson(wgw_ctx* ctx, int n_pdep, const double* x0, double* eig, d
  */
 int wgw_symm_eig_dev(int n, double* A_dev, double* w_dev, double* Z_dev, void* stream);
 
+/*
+ * wgw_symm_eig_dev without any allocation (the paper has no counterpart; this serves callers
+ * that cannot allocate device memory at the point of the call: a host process whose device
+ * memory is all reserved up front by another allocator, or code that must not pay for the
+ * device-wide synchronisation a cudaMalloc/cudaFree implies).  Same arguments, result and
+ * error codes as wgw_symm_eig_dev, for 1 <= n <= 512; larger n returns WGW_ERR_ARG.
+ * Its work space is one fixed array in device memory (about 2.1 MB) that every GPU loading
+ * the library keeps until the process exits.  The first call on a device looks up that
+ * array's device address (with the device current), so make that first call before any
+ * stream capture.  All calls share the array: calls whose work overlaps on a GPU (different
+ * streams or host threads at the same time) race and must be serialised by the caller.
+ */
+int wgw_symm_eig_noalloc_dev(int n, double* A_dev, double* w_dev, double* Z_dev, void* stream);
+
 /* Releases the context and all device memory it owns.  NULL is allowed. */
 void wgw_destroy(wgw_ctx* ctx);
 

@@ -3,7 +3,9 @@
 // updates.  The tall-skinny products use the tiled GEMMs of la_kernels.cu.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
+#include "../../include/wgw.h"
 #include "internal.h"
 
 namespace wgw {
@@ -268,3 +270,60 @@ cudaError_t launch_select_scale(int k, const double* Zc, int ldz, const int* col
 }
 
 }  // namespace wgw
+
+// ---------------------------------------------------------------- scratch-free variant
+// Work space of wgw_symm_eig_noalloc_dev: a file-scope device array sized for the largest
+// accepted n.  Every GPU that loads the library holds it (about 2.1 MB) until the process
+// exits, and every call shares it.
+namespace {
+
+constexpr int kNoAllocMaxN = 512;
+constexpr size_t kNoAllocElems = (size_t)kNoAllocMaxN * kNoAllocMaxN + 4 * kNoAllocMaxN + 2;
+static __device__ __align__(256) double g_syev_scratch[kNoAllocElems];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+double* g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of g_syev_scratch on the current device.  The host-side symbol is only a
+// stand-in and must never reach a kernel; the address is looked up once per device (with
+// that device current) and cached.
+int scratch_address(double** out) {
+  int dev = -1;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return wgw::report_error(WGW_ERR_CUDA, cudaGetErrorString(err));
+  if (dev < 0 || dev >= kMaxDevices) return wgw::report_error(WGW_ERR_STATE, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    err = cudaGetSymbolAddress(&p, g_syev_scratch);
+    if (err != cudaSuccess || !p)
+      return wgw::report_error(WGW_ERR_CUDA, "cudaGetSymbolAddress of the eigensolver scratch failed");
+    g_scratch_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_scratch_ptr[dev];
+  return WGW_OK;
+}
+
+}  // namespace
+
+extern "C" int wgw_symm_eig_noalloc_dev(int n, double* A_dev, double* w_dev, double* Z_dev, void* stream) {
+  wgw::clear_error();
+  if (n < 1 || n > kNoAllocMaxN)
+    return wgw::report_error(WGW_ERR_ARG, "wgw_symm_eig_noalloc_dev accepts 1 <= n <= 512");
+  if (!A_dev || !w_dev || !Z_dev) return wgw::report_error(WGW_ERR_ARG, "null device pointer");
+  double* scratch = nullptr;
+  const int rc = scratch_address(&scratch);
+  if (rc != WGW_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  // The kernel writes every work entry before reading it and sets info itself, so the
+  // previous call's contents need no clearing.
+  int* info = reinterpret_cast<int*>(scratch + wgw::syev_work_elems(n));
+  cudaError_t err = wgw::launch_syev(n, A_dev, n, w_dev, Z_dev, n, scratch, info, st);
+  if (err != cudaSuccess) return wgw::report_error(WGW_ERR_CUDA, cudaGetErrorString(err));
+  int h = 0;
+  err = cudaMemcpyAsync(&h, info, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+  if (err != cudaSuccess) return wgw::report_error(WGW_ERR_CUDA, cudaGetErrorString(err));
+  return h == 0 ? WGW_OK : wgw::report_error(WGW_ERR_NOCONV, "dense eigensolver did not converge");
+}

@@ -17,6 +17,10 @@ struct FftCtx {
 
 int fft_threads(int n);
 
+// Record a failure for wgw_last_error() and return `status` (wgw_api.cu).
+int report_error(int status, const char* msg);
+void clear_error();
+
 // Pruned 3D FFT pipeline (fft_kernels.cu).
 template <typename T>
 cudaError_t launch_plane_g2r(const SphereTab& sp, FftCtx<T> f, const T* X, long ldx, int n_sys,

@@ -804,6 +804,11 @@ int davidson_impl(wgw_ctx* c, int npd, const double* x0, double* eig, double* ba
 
 }  // namespace
 
+namespace wgw {
+int report_error(int status, const char* msg) { return fail(status, msg); }
+void clear_error() { g_last_error.clear(); }
+}  // namespace wgw
+
 extern "C" {
 
 int wgw_default_options(wgw_options* opt) {

@@ -78,6 +78,7 @@ def lib(path: str | None = None):
     L.wgw_profile_kind_name.argtypes = [ctypes.c_int]
     L.wgw_pdep_davidson.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, _dp, _dp, ctypes.POINTER(Stats)]
     L.wgw_symm_eig_dev.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.wgw_symm_eig_noalloc_dev.argtypes = L.wgw_symm_eig_dev.argtypes
     L.wgw_system_info.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp]
     L.wgw_destroy.argtypes = [ctypes.c_void_p]
     L.wgw_status_string.restype = ctypes.c_char_p
@@ -216,17 +217,25 @@ def wgw_pdep_davidson(ctx: Context, n_pdep: int, x0=None, want_basis=True, allow
     return eig, (basis.T if want_basis else None), st.as_dict(), s
 
 
-def wgw_symm_eig_dev(A_dev, stream=None):
-    """Symmetric eigensolver on device (torch float64 n x n, overwritten): returns (w, Z) torch tensors."""
+def wgw_symm_eig_dev(A_dev, stream=None, w=None, Z=None, noalloc=False):
+    """Symmetric eigensolver on device (torch float64 n x n, overwritten): returns (w, Z) torch tensors.
+
+    noalloc=True calls wgw_symm_eig_noalloc_dev (library-side work space in a fixed device array,
+    n <= 512); w and Z may then be passed in preallocated so that the call itself allocates nothing.
+    """
     import torch
     n = A_dev.shape[0]
     assert A_dev.is_cuda and A_dev.dtype == torch.float64 and A_dev.is_contiguous()
-    w = torch.empty(n, dtype=torch.float64, device=A_dev.device)
-    Z = torch.empty((n, n), dtype=torch.float64, device=A_dev.device)
+    if w is None:
+        w = torch.empty(n, dtype=torch.float64, device=A_dev.device)
+    if Z is None:
+        Z = torch.empty((n, n), dtype=torch.float64, device=A_dev.device)
     if stream is None:
         stream = torch.cuda.current_stream(A_dev.device).cuda_stream
-    _check(lib().wgw_symm_eig_dev(n, ctypes.c_void_p(A_dev.data_ptr()), ctypes.c_void_p(w.data_ptr()),
-                                  ctypes.c_void_p(Z.data_ptr()), ctypes.c_void_p(stream)), "wgw_symm_eig_dev")
+    fn = lib().wgw_symm_eig_noalloc_dev if noalloc else lib().wgw_symm_eig_dev
+    name = "wgw_symm_eig_noalloc_dev" if noalloc else "wgw_symm_eig_dev"
+    _check(fn(n, ctypes.c_void_p(A_dev.data_ptr()), ctypes.c_void_p(w.data_ptr()),
+              ctypes.c_void_p(Z.data_ptr()), ctypes.c_void_p(stream)), name)
     return w, Z
 
 
