@@ -181,7 +181,11 @@ def main():
     build.build()
     import paper_2203_05623_gb300 as W
 
-    phi = synth.perturbations(s.miller_rho, s.L, wl["n_pert"], wl["pert_seed"])
+    # Each rank owns one block of n_pert perturbations of a global seeded batch (no collective
+    # on the data path: the (v, p) systems are independent).
+    from paper_2203_05623_gb300.shard import owned_perturbations
+    phi_all = synth.perturbations(s.miller_rho, s.L, wl["n_pert"] * world, wl["pert_seed"])
+    phi = phi_all[:, owned_perturbations(wl["n_pert"] * world, rank, world, wl["n_pert"])]
     opt = W.wgw_default_options(precision=W.WGW_MIXED, cg_tol=wl["cg_tol"], max_cg_iter=200)
     ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, opt)
     stream = torch.cuda.current_stream()
@@ -257,7 +261,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
         "config": {"workload": args.workload, "desc": wl["desc"], "cg_tol": wl["cg_tol"],
                    "l2": "256 MB buffer written between steps, outside the timed interval",
-                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+                   "parallelism": f"perturbation shards x{world}" if world > 1 else "1 GPU"},
         "latency_ms": {"p50": 1e3 * statistics.median(times),
                        "p99": 1e3 * sorted(times)[min(len(times) - 1, int(0.99 * len(times)))],
                        "what": "one block-apply request, device time"},
