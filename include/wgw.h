@@ -120,7 +120,10 @@ int wgw_set_options(wgw_ctx* ctx, const wgw_options* opt);
  *   dV      N_rho x n_pert complex (perturbation p at dV + 2 N_rho p), density-sphere order.
  *           A perturbation need not be real in r: it is applied by linearity as
  *           dV = A + i B with A, B real in r (B is skipped when it is zero).
- *   omega   n_omega imaginary frequencies; this version accepts only omega = 0.
+ *   omega   n_omega imaginary frequencies omega >= 0 [Ha] (host array).  omega = 0 solves the
+ *           static Eq. sternheimer by PCG; every omega > 0 is solved, batched over frequencies,
+ *           as P_c (H - e_v + i omega) P_c x = -P_c dV psi_v by complex-symmetric CG (COCG), and
+ *           drho = f_s sum_v 2 Re(psi_v^* x) (the -i omega partner is the complex conjugate).
  *   drho    N_rho x n_pert x n_omega complex output (p fastest after G).
  *   st      optional statistics (may be NULL).
  * Returns WGW_ERR_NOCONV (with drho written) when a system missed cg_tol.

@@ -58,6 +58,27 @@ cudaError_t launch_ritz_residual(int n, int nb, const double* X, const double* A
 cudaError_t launch_symmetrise(int m, double* T, int ldt, cudaStream_t st);
 cudaError_t launch_select_scale(int k, const double* Zc, int ldz, const int* cols, const double* scale, int nc,
                                 double* out, int ldo, cudaStream_t st);
+// Complex-shifted CG (la_bodies.cuh): complex system s occupies rows 2s (real) and 2s+1 (imaginary).
+template <typename T>
+cudaError_t launch_cocg_init_a(const SphereTab& sp, int n, int n_cs, const T* Bv, T* X, T* R, T* Z, long ld,
+                               const double* eps, CocgState cs, cudaStream_t st);
+template <typename T>
+cudaError_t launch_cocg_init_b(int n, int n_cs, const T* R, const T* Z, T* P, long ld, CocgState cs,
+                               cudaStream_t st);
+template <typename T>
+cudaError_t launch_cocg_step_a(const SphereTab& sp, int n, int n_list, const int* list, T* X, T* R, T* Z,
+                               const T* P, T* Q, long ld, const double* eps, CocgState cs, double tol2,
+                               int max_iter, cudaStream_t st);
+template <typename T>
+cudaError_t launch_cocg_step_b(int n, int n_list, const int* list, const T* R, const T* Z, T* P, long ld,
+                               CocgState cs, cudaStream_t st);
+// rows[2j] = 2 sys[j], rows[2j+1] = 2 sys[j] + 1.
+cudaError_t launch_expand_rows(const int* sys, int n, int* rows, cudaStream_t st);
+// R = B - (Q + i w X) per complex system (active only).
+cudaError_t launch_shifted_residual(int n_cs, int n, const double* B, const double* Q, const double* X,
+                                    const double* omega, double* R, long ld, const int* active, cudaStream_t st);
+// out[s] = |x_{2s}|^2 + |x_{2s+1}|^2.
+cudaError_t launch_pair_norm2(int n_cs, int n, const double* x, long ld, double* out, cudaStream_t st);
 // Ordered list of the systems s < n_sys with active[s] != 0, and their count.
 cudaError_t launch_build_list(const int* active, int n_sys, int* list, int* count, cudaStream_t st);
 int pc_kblocks(int n, int n_sys);

@@ -192,6 +192,155 @@ WGW_HD void cg_step_b_body(int s, int n, const T* R, const T* Z, T* P, long ld, 
   if (th.tid == 0) st.rz[s] = rz;
 }
 
+// ---------------------------------------------------------------- complex-shifted CG (COCG)
+// (P_c (H - e_v) P_c + i w) x = b for a complex x = u + i v kept as two consecutive real
+// rows (u at row 2s, v at row 2s + 1 of every vector buffer).  With A = P_c (H - e_v) P_c
+// real symmetric, A + i w is complex symmetric, so conjugate gradients with the bilinear
+// form x^T y = (u.u' - v.v') + i (u.v' + v.u') (COCG, a reading: the paper names only a
+// preconditioned CG) applies; for w = 0 it reduces to the PCG above.
+struct CocgState {
+  double* rz_re; double* rz_im;   // rho = r^T z
+  double* bb; double* rr;
+  int* active;
+  int* iters;
+  const double* omega;            // per complex system
+};
+
+// x = 0, r = b, z = M^-1 r (both rows); ||b||^2 = |b_u|^2 + |b_v|^2.
+template <typename T>
+WGW_HD void cocg_init_a_body(int s, const SphereTab& sp, int n, const T* Bv, T* X, T* R, T* Z, long ld,
+                             const double* eps, CocgState st, double* red, Thr th) {
+  const double e = eps[s];
+  T part = T(0);
+  for (int row = 2 * s; row <= 2 * s + 1; ++row) {
+    const T* b = Bv + (size_t)row * ld;
+    T* x = X + (size_t)row * ld;
+    T* r = R + (size_t)row * ld;
+    T* z = Z + (size_t)row * ld;
+    for (int i = th.tid; i < n; i += th.nth) {
+      const T bi = b[i];
+      x[i] = T(0);
+      r[i] = bi;
+      z[i] = precond<T>(sp, i, e) * bi;
+      part += bi * bi;
+    }
+  }
+  const double bb = block_sum(double(part), red, th);
+  if (th.tid == 0) {
+    st.bb[s] = bb;
+    st.rr[s] = bb;
+    st.active[s] = bb > 0.0 ? 1 : 0;
+    st.iters[s] = 0;
+  }
+}
+
+// rho = r^T z, p = z.
+template <typename T>
+WGW_HD void cocg_init_b_body(int s, int n, const T* R, const T* Z, T* P, long ld, CocgState st,
+                             double* red, Thr th) {
+  if (!st.active[s]) return;
+  const T* ru = R + (size_t)(2 * s) * ld; const T* rv = ru + ld;
+  const T* zu = Z + (size_t)(2 * s) * ld; const T* zv = zu + ld;
+  T* pu = P + (size_t)(2 * s) * ld; T* pv = pu + ld;
+  T a = T(0), b = T(0);
+  for (int i = th.tid; i < n; i += th.nth) {
+    pu[i] = zu[i];
+    pv[i] = zv[i];
+    a += ru[i] * zu[i] - rv[i] * zv[i];
+    b += ru[i] * zv[i] + rv[i] * zu[i];
+  }
+  const double re = block_sum(double(a), red, th);
+  const double im = block_sum(double(b), red, th);
+  if (th.tid == 0) { st.rz_re[s] = re; st.rz_im[s] = im; }
+}
+
+// q <- A p + i w p (in place on Q), alpha = rho / p^T q, x += alpha p, r -= alpha q,
+// convergence test on |r|^2, z = M^-1 r.
+template <typename T>
+WGW_HD void cocg_step_a_body(int s, const SphereTab& sp, int n, T* X, T* R, T* Z, const T* P, T* Q,
+                             long ld, const double* eps, CocgState st, double tol2, int max_iter,
+                             double* red, Thr th) {
+  if (!st.active[s]) return;
+  const T w = T(st.omega[s]);
+  const T* pu = P + (size_t)(2 * s) * ld; const T* pv = pu + ld;
+  T* qu = Q + (size_t)(2 * s) * ld; T* qv = qu + ld;
+  T a = T(0), b = T(0);
+  for (int i = th.tid; i < n; i += th.nth) {
+    const T qa = qu[i] - w * pv[i], qb = qv[i] + w * pu[i];
+    qu[i] = qa;
+    qv[i] = qb;
+    a += pu[i] * qa - pv[i] * qb;
+    b += pu[i] * qb + pv[i] * qa;
+  }
+  const double sr = block_sum(double(a), red, th);
+  const double si = block_sum(double(b), red, th);
+  const double d2 = sr * sr + si * si;
+  const double rr0 = st.rz_re[s], ri0 = st.rz_im[s];
+  const double ar = d2 > 0 ? (rr0 * sr + ri0 * si) / d2 : 0.0;   // alpha = rho / sigma
+  const double ai = d2 > 0 ? (ri0 * sr - rr0 * si) / d2 : 0.0;
+  const T Ar = T(ar), Ai = T(ai);
+  T* xu = X + (size_t)(2 * s) * ld; T* xv = xu + ld;
+  T* ru = R + (size_t)(2 * s) * ld; T* rv = ru + ld;
+  T* zu = Z + (size_t)(2 * s) * ld; T* zv = zu + ld;
+  const double e = eps[s];
+  T part = T(0);
+  for (int i = th.tid; i < n; i += th.nth) {
+    xu[i] += Ar * pu[i] - Ai * pv[i];
+    xv[i] += Ar * pv[i] + Ai * pu[i];
+    const T nu = ru[i] - (Ar * qu[i] - Ai * qv[i]);
+    const T nv = rv[i] - (Ar * qv[i] + Ai * qu[i]);
+    ru[i] = nu;
+    rv[i] = nv;
+    const T m = precond<T>(sp, i, e);
+    zu[i] = m * nu;
+    zv[i] = m * nv;
+    part += nu * nu + nv * nv;
+  }
+  const double rr = block_sum(double(part), red, th);
+  if (th.tid == 0) {
+    st.rr[s] = rr;
+    const int it = st.iters[s] + 1;
+    st.iters[s] = it;
+    if (rr <= tol2 * st.bb[s] || it >= max_iter || !(d2 > 0.0)) st.active[s] = 0;
+  }
+}
+
+// rho' = r^T z, beta = rho'/rho, p = z + beta p.
+template <typename T>
+WGW_HD void cocg_step_b_body(int s, int n, const T* R, const T* Z, T* P, long ld, CocgState st,
+                             double* red, Thr th) {
+  if (!st.active[s]) return;
+  const T* ru = R + (size_t)(2 * s) * ld; const T* rv = ru + ld;
+  const T* zu = Z + (size_t)(2 * s) * ld; const T* zv = zu + ld;
+  T* pu = P + (size_t)(2 * s) * ld; T* pv = pu + ld;
+  T a = T(0), b = T(0);
+  for (int i = th.tid; i < n; i += th.nth) {
+    a += ru[i] * zu[i] - rv[i] * zv[i];
+    b += ru[i] * zv[i] + rv[i] * zu[i];
+  }
+  const double nr = block_sum(double(a), red, th);
+  const double ni = block_sum(double(b), red, th);
+  const double orr = st.rz_re[s], ori = st.rz_im[s];
+  const double d2 = orr * orr + ori * ori;
+  const double br = d2 > 0 ? (nr * orr + ni * ori) / d2 : 0.0;
+  const double bi = d2 > 0 ? (ni * orr - nr * ori) / d2 : 0.0;
+  const T Br = T(br), Bi = T(bi);
+  for (int i = th.tid; i < n; i += th.nth) {
+    const T ou = pu[i], ov = pv[i];
+    pu[i] = zu[i] + Br * ou - Bi * ov;
+    pv[i] = zv[i] + Br * ov + Bi * ou;
+  }
+  if (th.tid == 0) { st.rz_re[s] = nr; st.rz_im[s] = ni; }
+}
+
+// r = b - (q + i w x) for complex system s (q = A x already in Q), FP64.
+WGW_HD void shifted_residual(int s, int i, const double* B, const double* Q, const double* X, double w,
+                             double* R, long ld) {
+  const size_t u = (size_t)(2 * s) * ld + i, v = u + ld;
+  R[u] = B[u] - (Q[u] - w * X[v]);
+  R[v] = B[v] - (Q[v] + w * X[u]);
+}
+
 // ---------------------------------------------------------------- conversions
 // Index map of a sphere in real-basis form: idx[0] = canonical index of G = 0,
 // idx_pos[j], idx_neg[j] (j >= 1) = canonical indices of G_j and -G_j.

@@ -326,6 +326,59 @@ __global__ void __launch_bounds__(1024) k_build_list(const int* __restrict__ act
   if (threadIdx.x == 0) *count = base;
 }
 
+template <typename T>
+__global__ void k_cocg_init_a(SphereTab sp, int n, const T* Bv, T* X, T* R, T* Z, long ld, const double* eps,
+                              CocgState cs) {
+  __shared__ double red[33];
+  cocg_init_a_body<T>(blockIdx.x, sp, n, Bv, X, R, Z, ld, eps, cs, red, thr());
+}
+
+template <typename T>
+__global__ void k_cocg_init_b(int n, const T* R, const T* Z, T* P, long ld, CocgState cs) {
+  __shared__ double red[33];
+  cocg_init_b_body<T>(blockIdx.x, n, R, Z, P, ld, cs, red, thr());
+}
+
+template <typename T>
+__global__ void k_cocg_step_a(SphereTab sp, int n, T* X, T* R, T* Z, const T* P, T* Q, long ld,
+                              const double* eps, CocgState cs, double tol2, int max_iter, const int* list) {
+  __shared__ double red[33];
+  const int s = list ? list[blockIdx.x] : blockIdx.x;
+  cocg_step_a_body<T>(s, sp, n, X, R, Z, P, Q, ld, eps, cs, tol2, max_iter, red, thr());
+}
+
+template <typename T>
+__global__ void k_cocg_step_b(int n, const T* R, const T* Z, T* P, long ld, CocgState cs, const int* list) {
+  __shared__ double red[33];
+  const int s = list ? list[blockIdx.x] : blockIdx.x;
+  cocg_step_b_body<T>(s, n, R, Z, P, ld, cs, red, thr());
+}
+
+__global__ void k_expand_rows(const int* __restrict__ sys, int n, int* __restrict__ rows) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    rows[2 * j] = 2 * sys[j];
+    rows[2 * j + 1] = 2 * sys[j] + 1;
+  }
+}
+
+__global__ void k_shifted_residual(int n_cs, int n, const double* B, const double* Q, const double* X,
+                                   const double* omega, double* R, long ld, const int* active) {
+  for (int s = blockIdx.y; s < n_cs; s += gridDim.y) {
+    if (active && !active[s]) continue;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+      shifted_residual(s, i, B, Q, X, omega[s], R, ld);
+  }
+}
+
+__global__ void k_pair_norm2(int n, const double* x, long ld, double* out) {
+  __shared__ double red[33];
+  const double* u = x + (size_t)(2 * blockIdx.x) * ld;
+  double part = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) part += u[i] * u[i] + u[ld + i] * u[ld + i];
+  const double v = block_sum(part, red, thr());
+  if (threadIdx.x == 0) out[blockIdx.x] = v;
+}
+
 inline dim3 grid_el(int n, int n_sys) {
   int bx = (n + 255) / 256;
   if (bx > 64) bx = 64;
@@ -490,6 +543,72 @@ cudaError_t launch_count(const int* flags, int n, int* out, cudaStream_t st) {
   k_count<<<1, 256, 0, st>>>(flags, n, out);
   return cudaGetLastError();
 }
+
+
+template <typename T>
+cudaError_t launch_cocg_init_a(const SphereTab& sp, int n, int n_cs, const T* Bv, T* X, T* R, T* Z, long ld,
+                               const double* eps, CocgState cs, cudaStream_t st) {
+  if (n_cs == 0) return cudaSuccess;
+  k_cocg_init_a<T><<<n_cs, kCgThreads, 0, st>>>(sp, n, Bv, X, R, Z, ld, eps, cs);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cocg_init_b(int n, int n_cs, const T* R, const T* Z, T* P, long ld, CocgState cs,
+                               cudaStream_t st) {
+  if (n_cs == 0) return cudaSuccess;
+  k_cocg_init_b<T><<<n_cs, kCgThreads, 0, st>>>(n, R, Z, P, ld, cs);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cocg_step_a(const SphereTab& sp, int n, int n_list, const int* list, T* X, T* R, T* Z,
+                               const T* P, T* Q, long ld, const double* eps, CocgState cs, double tol2,
+                               int max_iter, cudaStream_t st) {
+  if (n_list == 0) return cudaSuccess;
+  k_cocg_step_a<T><<<n_list, kCgThreads, 0, st>>>(sp, n, X, R, Z, P, Q, ld, eps, cs, tol2, max_iter, list);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cocg_step_b(int n, int n_list, const int* list, const T* R, const T* Z, T* P, long ld,
+                               CocgState cs, cudaStream_t st) {
+  if (n_list == 0) return cudaSuccess;
+  k_cocg_step_b<T><<<n_list, kCgThreads, 0, st>>>(n, R, Z, P, ld, cs, list);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expand_rows(const int* sys, int n, int* rows, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_expand_rows<<<std::min(1024, (n + 255) / 256), 256, 0, st>>>(sys, n, rows);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shifted_residual(int n_cs, int n, const double* B, const double* Q, const double* X,
+                                    const double* omega, double* R, long ld, const int* active, cudaStream_t st) {
+  if (n_cs == 0) return cudaSuccess;
+  k_shifted_residual<<<grid_el(n, n_cs), 256, 0, st>>>(n_cs, n, B, Q, X, omega, R, ld, active);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair_norm2(int n_cs, int n, const double* x, long ld, double* out, cudaStream_t st) {
+  if (n_cs == 0) return cudaSuccess;
+  k_pair_norm2<<<n_cs, 256, 0, st>>>(n, x, ld, out);
+  return cudaGetLastError();
+}
+
+#define WGW_INST_COCG(T)                                                                           \
+  template cudaError_t launch_cocg_init_a<T>(const SphereTab&, int, int, const T*, T*, T*, T*, long, \
+                                             const double*, CocgState, cudaStream_t);               \
+  template cudaError_t launch_cocg_init_b<T>(int, int, const T*, const T*, T*, long, CocgState,     \
+                                             cudaStream_t);                                         \
+  template cudaError_t launch_cocg_step_a<T>(const SphereTab&, int, int, const int*, T*, T*, T*,    \
+                                             const T*, T*, long, const double*, CocgState, double,  \
+                                             int, cudaStream_t);                                    \
+  template cudaError_t launch_cocg_step_b<T>(int, int, const int*, const T*, const T*, T*, long,    \
+                                             CocgState, cudaStream_t);
+WGW_INST_COCG(float)
+WGW_INST_COCG(double)
 
 #define WGW_INST_LA(T)                                                                             \
   template cudaError_t launch_pc<T>(T*, long, int, const int*, const T*, long, int, int,           \

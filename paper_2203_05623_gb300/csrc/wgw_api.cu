@@ -174,7 +174,8 @@ struct wgw_ctx {
   DevBuf e_v_d;
   // apply work space (double unless noted)
   DevBuf dvin, dv_rb, dv_r, Trho, Dr, drho_rb, eps, a_idx, b_idx, brow, cg_rz, cg_bb, cg_rr,
-      cg_act, cg_it, cnt, rr64, act64, norms, pc_work, sys_list, list64;
+      cg_act, cg_it, cnt, rr64, act64, norms, pc_work, sys_list, list64, cg_rzi, omg, row_list, rowact,
+      drho_all;
   cudaStream_t stream = nullptr;
   Prof prof;
   std::vector<int> last_iters;      // per system of the last apply: CG iterations (all refinements)
@@ -183,7 +184,8 @@ struct wgw_ctx {
     prof.release();
     d.release(); f.release(); wfc.release(); rho.release();
     DevBuf* all[] = {&e_v_d, &dvin, &dv_rb, &dv_r, &Trho, &Dr, &drho_rb, &eps, &a_idx, &b_idx, &brow,
-                     &cg_rz, &cg_bb, &cg_rr, &cg_act, &cg_it, &cnt, &rr64, &act64, &norms, &pc_work, &sys_list, &list64};
+                     &cg_rz, &cg_bb, &cg_rr, &cg_act, &cg_it, &cnt, &rr64, &act64, &norms, &pc_work, &sys_list, &list64, &cg_rzi, &omg,
+                     &row_list, &rowact, &drho_all};
     for (DevBuf* b : all) b->release();
     if (stream) cudaStreamDestroy(stream);
   }
@@ -328,6 +330,9 @@ int ensure_work(wgw_ctx* c, int n_sys, int n_real) {
   WGW_TRY(c->rr64.ensure(sizeof(double) * n_sys));
   WGW_TRY(c->act64.ensure(sizeof(int) * n_sys));
   WGW_TRY(c->sys_list.ensure(sizeof(int) * n_sys));
+  WGW_TRY(c->cg_rzi.ensure(sizeof(double) * n_sys));
+  WGW_TRY(c->omg.ensure(sizeof(double) * n_sys));
+  WGW_TRY(c->row_list.ensure(sizeof(int) * n_sys));
   WGW_TRY(c->list64.ensure(sizeof(int) * n_sys));
   WGW_TRY(c->cnt.ensure(sizeof(int) * 4));
   WGW_TRY(c->dv_r.ensure(sizeof(double) * (size_t)n_real * c->grid3));
@@ -434,6 +439,143 @@ int solve_all(wgw_ctx* c, int n_sys, cudaStream_t st, wgw_stats* stats) {
   return conv == n_sys ? WGW_OK : fail(WGW_ERR_NOCONV, "some Sternheimer systems missed cg_tol");
 }
 
+__global__ void k_rows_from_systems(int n_cs, const int* __restrict__ act, int* __restrict__ rows) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_cs; s += gridDim.x * blockDim.x)
+    rows[2 * s] = rows[2 * s + 1] = act[s];
+}
+
+CocgState cocg_state(wgw_ctx* c) {
+  CocgState s;
+  s.rz_re = c->cg_rz.as<double>(); s.rz_im = c->cg_rzi.as<double>(); s.bb = c->cg_bb.as<double>();
+  s.rr = c->cg_rr.as<double>(); s.active = c->cg_act.as<int>(); s.iters = c->cg_it.as<int>();
+  s.omega = c->omg.as<double>();
+  return s;
+}
+
+// List of active complex systems into c->sys_list and the matching row list into c->row_list.
+int build_cs_lists(wgw_ctx* c, const int* flags, int n_cs, cudaStream_t st, int* n_out) {
+  WGW_TRY(build_list(c, flags, n_cs, c->sys_list.as<int>(), st, n_out));
+  WGW_CK(launch_expand_rows(c->sys_list.as<int>(), *n_out, c->row_list.as<int>(), st));
+  return WGW_OK;
+}
+
+// COCG on (A + i w_s) x = b for n_cs complex systems (rows 2s, 2s+1 of pr.Bv / pr.X).
+template <typename T>
+int cocg_solve(wgw_ctx* c, Prec<T>& pr, int n_cs, double tol, int max_iter, cudaStream_t st) {
+  const int n = c->wfc.nrb();
+  const long ld = c->ld_w;
+  T* X = pr.X.template as<T>();
+  T* R = pr.R.template as<T>();
+  T* Z = pr.Z.template as<T>();
+  T* P = pr.P.template as<T>();
+  T* Q = pr.Q.template as<T>();
+  const T* Bv = pr.Bv.template as<T>();
+  const T* Psi = pr.psi.template as<T>();
+  const double* eps = c->eps.as<double>();
+  CocgState cs = cocg_state(c);
+  const double vb = 2.0 * n_cs * n * sizeof(T);
+  WGW_CK(c->prof.run(PK_CG, 4 * vb, 0, st, [&] {
+    return launch_cocg_init_a<T>(c->wfc.tab(), n, n_cs, Bv, X, R, Z, ld, eps, cs, st); }));
+  WGW_TRY(run_pc<T>(c, Z, 2 * n_cs, nullptr, Psi, nullptr, st));
+  WGW_CK(c->prof.run(PK_CG, 3 * vb, 0, st, [&] { return launch_cocg_init_b<T>(n, n_cs, R, Z, P, ld, cs, st); }));
+  int n_list = 0;
+  WGW_TRY(build_cs_lists(c, cs.active, n_cs, st, &n_list));
+  const int* lbuf = c->sys_list.as<int>();
+  const int* rbuf = c->row_list.as<int>();
+  const int every = std::max(1, c->opt.check_every);
+  for (int it = 0; it < max_iter && n_list > 0; ++it) {
+    const double lb = 2.0 * n_list * n * sizeof(T);
+    WGW_TRY(apply_A<T>(c, pr, P, Q, 2 * n_list, rbuf, nullptr, st));
+    WGW_CK(c->prof.run(PK_CG, 9 * lb, 0, st, [&] {
+      return launch_cocg_step_a<T>(c->wfc.tab(), n, n_list, lbuf, X, R, Z, P, Q, ld, eps, cs, tol * tol,
+                                   max_iter, st); }));
+    WGW_TRY(run_pc<T>(c, Z, 2 * n_list, rbuf, Psi, nullptr, st));
+    WGW_CK(c->prof.run(PK_CG, 4 * lb, 0, st, [&] {
+      return launch_cocg_step_b<T>(n, n_list, lbuf, R, Z, P, ld, cs, st); }));
+    if ((it + 1) % every == 0) WGW_TRY(build_cs_lists(c, cs.active, n_cs, st, &n_list));
+  }
+  return WGW_OK;
+}
+
+// Solve all complex-shifted systems to cg_tol (right-hand sides in d.Bv rows, solutions into d.X).
+int solve_shifted(wgw_ctx* c, int n_cs, cudaStream_t st, wgw_stats* stats) {
+  const int n = c->wfc.nrb();
+  const long ld = c->ld_w;
+  const double tol = c->opt.cg_tol;
+  std::vector<int> iters_total(n_cs, 0), it_host(n_cs);
+  int refinements = 0;
+  double* X = c->d.X.as<double>();
+  double* R = c->d.R.as<double>();
+  double* Q = c->d.Q.as<double>();
+  const double* Bv = c->d.Bv.as<double>();
+  const double* omega = c->omg.as<double>();
+  WGW_TRY(c->norms.ensure(sizeof(double) * n_cs));
+  double* bb64 = c->norms.as<double>();
+  WGW_CK(launch_pair_norm2(n_cs, n, Bv, ld, bb64, st));
+  if (c->opt.precision == WGW_FP64) {
+    WGW_TRY(cocg_solve<double>(c, c->d, n_cs, tol, c->opt.max_cg_iter, st));
+    WGW_CK(cudaMemcpyAsync(iters_total.data(), c->cg_it.p, sizeof(int) * n_cs, cudaMemcpyDeviceToHost, st));
+    WGW_TRY(run_pc<double>(c, X, 2 * n_cs, nullptr, c->d.psi.as<double>(), nullptr, st));
+    WGW_TRY(apply_A<double>(c, c->d, X, Q, 2 * n_cs, nullptr, nullptr, st));
+    WGW_CK(launch_shifted_residual(n_cs, n, Bv, Q, X, omega, R, ld, nullptr, st));
+  } else {
+    WGW_CK(cudaMemsetAsync(X, 0, sizeof(double) * (size_t)2 * n_cs * ld, st));
+    WGW_CK(cudaMemcpyAsync(R, Bv, sizeof(double) * (size_t)2 * n_cs * ld, cudaMemcpyDeviceToDevice, st));
+    int* act64 = c->act64.as<int>();
+    WGW_TRY(c->rowact.ensure(sizeof(int) * 2 * n_cs));
+    int* rowact = c->rowact.as<int>();
+    for (int k = 0; k < c->opt.max_refine; ++k) {
+      WGW_CK(launch_pair_norm2(n_cs, n, R, ld, c->rr64.as<double>(), st));
+      k_residual_flags<<<(n_cs + 255) / 256, 256, 0, st>>>(n_cs, c->rr64.as<double>(), bb64, tol * tol, act64);
+      WGW_CK(cudaGetLastError());
+      int na = 0;
+      WGW_TRY(build_cs_lists(c, act64, n_cs, st, &na));
+      if (na == 0) break;
+      ++refinements;
+      // Keep the list of this refinement step: cocg_solve rebuilds sys_list / row_list.
+      WGW_TRY(c->list64.ensure(sizeof(int) * 2 * n_cs));
+      WGW_CK(cudaMemcpyAsync(c->list64.p, c->row_list.p, sizeof(int) * 2 * na, cudaMemcpyDeviceToDevice, st));
+      k_rows_from_systems<<<(n_cs + 255) / 256, 256, 0, st>>>(n_cs, act64, rowact);
+      WGW_CK(cudaGetLastError());
+      WGW_CK(cudaMemsetAsync(c->f.Bv.p, 0, sizeof(float) * (size_t)2 * n_cs * ld, st));
+      WGW_CK((launch_copy_cast<double, float>(2 * n_cs, n, R, ld, c->f.Bv.as<float>(), ld, rowact, st)));
+      WGW_TRY(cocg_solve<float>(c, c->f, n_cs, c->opt.inner_tol, c->opt.max_cg_iter, st));
+      WGW_CK(cudaMemcpyAsync(it_host.data(), c->cg_it.p, sizeof(int) * n_cs, cudaMemcpyDeviceToHost, st));
+      WGW_CK(cudaStreamSynchronize(st));
+      for (int q = 0; q < n_cs; ++q) iters_total[q] += it_host[q];
+      WGW_CK(launch_add_to<float>(2 * n_cs, n, c->f.X.as<float>(), ld, X, ld, rowact, st));
+      const int* l64 = c->list64.as<int>();
+      WGW_TRY(run_pc<double>(c, X, 2 * na, l64, c->d.psi.as<double>(), nullptr, st));
+      WGW_TRY(apply_A<double>(c, c->d, X, Q, 2 * na, l64, nullptr, st));
+      WGW_CK(launch_shifted_residual(n_cs, n, Bv, Q, X, omega, R, ld, act64, st));
+    }
+  }
+  WGW_CK(launch_pair_norm2(n_cs, n, R, ld, c->rr64.as<double>(), st));
+  std::vector<double> rr(n_cs), bb(n_cs);
+  WGW_CK(cudaMemcpyAsync(rr.data(), c->rr64.p, sizeof(double) * n_cs, cudaMemcpyDeviceToHost, st));
+  WGW_CK(cudaMemcpyAsync(bb.data(), bb64, sizeof(double) * n_cs, cudaMemcpyDeviceToHost, st));
+  WGW_CK(cudaStreamSynchronize(st));
+  int conv = 0, maxit = 0;
+  double maxrel = 0.0;
+  c->last_iters = iters_total;
+  c->last_relres.assign(n_cs, 0.0);
+  for (int q = 0; q < n_cs; ++q) {
+    const double rel = bb[q] > 0 ? std::sqrt(rr[q] / bb[q]) : 0.0;
+    c->last_relres[q] = rel;
+    maxrel = std::max(maxrel, rel);
+    if (rel <= tol * (1.0 + 1e-6) || bb[q] == 0.0) ++conv;
+    maxit = std::max(maxit, iters_total[q]);
+  }
+  if (stats) {
+    stats->n_systems += n_cs;
+    stats->n_converged += conv;
+    stats->max_iters = std::max(stats->max_iters, maxit);
+    stats->refinements = std::max(stats->refinements, refinements);
+    stats->max_rel_residual = std::max(stats->max_rel_residual, maxrel);
+  }
+  return conv == n_cs ? WGW_OK : fail(WGW_ERR_NOCONV, "some complex-shifted Sternheimer systems missed cg_tol");
+}
+
 // drho = chi0 dV for n_real perturbations that are real in r, given and returned in
 // real-basis form (rows of length ld_r): dV in dvrb, drho into c->drho_rb.  Steps 2-6
 // of the apply: system tables, dV(r), right-hand sides, Sternheimer solves, drho.
@@ -513,13 +655,103 @@ int chi0_rb(wgw_ctx* c, const double* dvrb, int n_real, cudaStream_t st, wgw_sta
   return solve_status;
 }
 
+// drho(i w_k) = chi0(i w_k) dV for n_real real-in-r perturbations (real-basis rows of dvrb) and
+// every w_k > 0, batched over frequencies: complex system (k, r, v) -> rows 2s, 2s+1 with
+// s = (k n_real + r) n_v + v.  Results into c->drho_all, row k * n_real + r.
+int chi0_rb_shifted(wgw_ctx* c, const double* dvrb, int n_real, const std::vector<double>& oms, cudaStream_t st,
+                    wgw_stats* stats) {
+  const int N = c->N, n_v = c->n_v, n_om = (int)oms.size();
+  const long ldr = c->ld_r, ldw = c->ld_w;
+  const HostSphere& rs = c->rho;
+  const int n_rs = n_real * n_v, n_cs = n_om * n_rs, rows = 2 * n_cs;
+  WGW_TRY(ensure_work(c, std::max(rows, n_rs), n_real));
+  std::vector<int> ai(n_rs), bi(n_rs);
+  for (int r = 0; r < n_real; ++r)
+    for (int v = 0; v < n_v; ++v) { ai[r * n_v + v] = v; bi[r * n_v + v] = r; }
+  std::vector<double> eps(n_cs), om(n_cs), shift(rows);
+  std::vector<float> shiftf(rows);
+  for (int k = 0; k < n_om; ++k)
+    for (int q = 0; q < n_rs; ++q) {
+      const int s = k * n_rs + q, v = q % n_v;
+      eps[s] = c->e_v[v];
+      om[s] = oms[k];
+      shift[2 * s] = shift[2 * s + 1] = -c->e_v[v];
+      shiftf[2 * s] = shiftf[2 * s + 1] = (float)-c->e_v[v];
+    }
+  WGW_CK(cudaMemcpyAsync(c->a_idx.p, ai.data(), sizeof(int) * n_rs, cudaMemcpyHostToDevice, st));
+  WGW_CK(cudaMemcpyAsync(c->b_idx.p, bi.data(), sizeof(int) * n_rs, cudaMemcpyHostToDevice, st));
+  WGW_CK(cudaMemcpyAsync(c->eps.p, eps.data(), sizeof(double) * n_cs, cudaMemcpyHostToDevice, st));
+  WGW_CK(cudaMemcpyAsync(c->omg.p, om.data(), sizeof(double) * n_cs, cudaMemcpyHostToDevice, st));
+  WGW_CK(cudaMemcpyAsync(c->d.shift.p, shift.data(), sizeof(double) * rows, cudaMemcpyHostToDevice, st));
+  if (c->opt.precision == WGW_MIXED)
+    WGW_CK(cudaMemcpyAsync(c->f.shift.p, shiftf.data(), sizeof(float) * rows, cudaMemcpyHostToDevice, st));
+  double* dvr = c->dv_r.as<double>();
+  WGW_TRY(to_real<double>(c, c->d, rs, dvrb, ldr, n_real, dvr, c->Trho, st));
+  FftCtx<double> f = c->d.fft(c->plan);
+  {
+    // Real right-hand sides -P_c [psi_v dV_r] of the n_rs (r, v) pairs into d.Q, then copied to
+    // the real row of every frequency's complex system (imaginary rows are zero).
+    const int NP = 2 * c->wfc.m + 1, pairs = (n_rs + 1) / 2;
+    WGW_TRY(c->d.Tw.ensure(sizeof(cplx<double>) * (size_t)pairs * NP * N * N));
+    XArgs<double> a{};
+    a.mode = XM_FROM_REAL; a.A = c->d.psi_r.as<double>(); a.lda = c->grid3; a.a_index = c->a_idx.as<int>();
+    a.Bm = dvr; a.ldb = c->grid3; a.b_index = c->b_idx.as<int>(); a.n_sys = n_rs;
+    const double tb = t_bytes<double>(c, c->wfc.m, pairs);
+    WGW_CK(c->prof.run(PK_XLINE, tb + 2.0 * n_rs * c->grid3 * sizeof(double), 0, st, [&] {
+      return launch_xline<double>(c->wfc.m, f, c->d.Tw.as<cplx<double>>(), a, nullptr, st); }));
+    Epi<double> e{};
+    e.out = c->d.Q.as<double>(); e.ldo = ldw; e.vcoef = -1.0; e.n_sys = n_rs;
+    WGW_CK(c->prof.run(PK_R2G, tb + (double)n_rs * c->wfc.nrb() * sizeof(double), 0, st, [&] {
+      return launch_plane_r2g<double>(c->wfc.tab(), c->wfc.npt_max, f, c->d.Tw.as<cplx<double>>(), e, st); }));
+    WGW_TRY(run_pc<double>(c, c->d.Q.as<double>(), n_rs, nullptr, c->d.psi.as<double>(), nullptr, st));
+    WGW_CK(cudaMemsetAsync(c->d.Bv.p, 0, sizeof(double) * (size_t)rows * ldw, st));
+    for (int k = 0; k < n_om; ++k)
+      WGW_CK(cudaMemcpy2DAsync(c->d.Bv.as<double>() + (size_t)2 * k * n_rs * ldw, 2 * ldw * sizeof(double),
+                               c->d.Q.p, ldw * sizeof(double), ldw * sizeof(double), n_rs,
+                               cudaMemcpyDeviceToDevice, st));
+  }
+  const int solve_status = solve_shifted(c, n_cs, st, stats);
+  if (solve_status != WGW_OK && solve_status != WGW_ERR_NOCONV) return solve_status;
+  WGW_TRY(c->drho_all.ensure(sizeof(double) * (size_t)n_om * n_real * ldr));
+  const int pairs = (n_rs + 1) / 2;
+  const int NPr = 2 * rs.m + 1, rpairs = (n_real + 1) / 2;
+  WGW_TRY(c->Trho.ensure(sizeof(cplx<double>) * (size_t)rpairs * NPr * N * N));
+  const double coef = 2.0 * c->opt.f_s / c->omega_cell;
+  for (int k = 0; k < n_om; ++k) {
+    // drho = (f_s/Omega) sum_v 2 Re(psi_v x_v) uses the real rows of frequency k (stride 2 ld).
+    const double* Xk = c->d.X.as<double>() + (size_t)2 * k * n_rs * ldw;
+    const double tb = t_bytes<double>(c, c->wfc.m, pairs);
+    WGW_CK(c->prof.run(PK_G2R, tb + (double)n_rs * c->wfc.nrb() * sizeof(double), 0, st, [&] {
+      return launch_plane_g2r<double>(c->wfc.tab(), f, Xk, 2 * ldw, n_rs, nullptr, nullptr,
+                                      c->d.Tw.as<cplx<double>>(), st); }));
+    WGW_CK(c->prof.run(PK_DRHO, tb + (double)(n_v + n_real) * c->grid3 * sizeof(double), 0, st, [&] {
+      return launch_drho_xline<double>(c->wfc.m, f, c->d.Tw.as<cplx<double>>(), c->d.psi_r.as<double>(),
+                                       c->grid3, n_v, n_rs, n_real, coef, c->Dr.as<double>(), c->grid3, st); }));
+    XArgs<double> a{};
+    a.mode = XM_FROM_REAL; a.A = c->Dr.as<double>(); a.lda = c->grid3; a.n_sys = n_real;
+    const double tr = t_bytes<double>(c, rs.m, rpairs);
+    WGW_CK(c->prof.run(PK_XLINE, tr + (double)n_real * c->grid3 * sizeof(double), 0, st, [&] {
+      return launch_xline<double>(rs.m, f, c->Trho.as<cplx<double>>(), a, nullptr, st); }));
+    Epi<double> e{};
+    e.out = c->drho_all.as<double>() + (size_t)k * n_real * ldr; e.ldo = ldr; e.vcoef = 1.0; e.n_sys = n_real;
+    WGW_CK(c->prof.run(PK_R2G, tr + (double)n_real * rs.nrb() * sizeof(double), 0, st, [&] {
+      return launch_plane_r2g<double>(rs.tab(), rs.npt_max, f, c->Trho.as<cplx<double>>(), e, st); }));
+  }
+  return solve_status;
+}
+
 // Core of chi0 / chibar0 application; dV and drho in device memory.
 int apply_core(wgw_ctx* c, const double* dV, int n_pert, const double* omega, int n_omega,
                double* drho, bool symmetrized, cudaStream_t st, wgw_stats* stats) {
   if (!c) return fail(WGW_ERR_ARG, "null context");
   if (n_pert < 0 || n_omega < 1 || !omega) return fail(WGW_ERR_ARG, "need n_pert >= 0 and n_omega >= 1");
-  for (int k = 0; k < n_omega; ++k)
-    if (omega[k] != 0.0) return fail(WGW_ERR_ARG, "this version applies chi0 at omega = 0 only");
+  std::vector<int> k_zero, k_pos;
+  std::vector<double> w_pos;
+  for (int k = 0; k < n_omega; ++k) {
+    if (!(omega[k] >= 0.0)) return fail(WGW_ERR_ARG, "imaginary frequencies must be >= 0");
+    if (omega[k] == 0.0) k_zero.push_back(k);
+    else { k_pos.push_back(k); w_pos.push_back(omega[k]); }
+  }
   if (n_pert == 0) return WGW_OK;
   if (!dV || !drho) return fail(WGW_ERR_ARG, "null dV or drho");
   const long ldr = c->ld_r;
@@ -550,13 +782,26 @@ int apply_core(wgw_ctx* c, const double* dV, int n_pert, const double* omega, in
   }
   WGW_TRY(c->brow.ensure(sizeof(int) * n_pert));
   WGW_CK(cudaMemcpyAsync(c->brow.p, brow.data(), sizeof(int) * n_pert, cudaMemcpyHostToDevice, st));
-  const int solve_status = chi0_rb(c, dvrb, n_real, st, stats);
-  if (solve_status != WGW_OK && solve_status != WGW_ERR_NOCONV) return solve_status;
-  // 7. Complex output drho_p = chi0 A_p + i chi0 B_p for every frequency (all omega = 0 here).
-  for (int k = 0; k < n_omega; ++k)
+  if (stats) *stats = wgw_stats{};
+  int solve_status = WGW_OK;
+  if (!k_zero.empty()) {
+    solve_status = chi0_rb(c, dvrb, n_real, st, stats);
+    if (solve_status != WGW_OK && solve_status != WGW_ERR_NOCONV) return solve_status;
+  }
+  // 7. Complex output drho_p = chi0 A_p + i chi0 B_p for every frequency.
+  for (int k : k_zero)
     WGW_CK(c->prof.run(PK_CONV, 16.0 * n_pert * rs.n + 8.0 * n_pert * rs.nrb(), 0, st, [&] {
       return launch_rb_to_sphere(n_pert, c->drho_rb.as<double>(), ldr, c->brow.as<int>(), scale, rs.map(),
                                  drho + (size_t)k * n_pert * 2 * rs.n, 2L * rs.n, st); }));
+  if (!k_pos.empty()) {
+    const int s2 = chi0_rb_shifted(c, dvrb, n_real, w_pos, st, stats);
+    if (s2 != WGW_OK && s2 != WGW_ERR_NOCONV) return s2;
+    if (s2 == WGW_ERR_NOCONV) solve_status = s2;
+    for (size_t j = 0; j < k_pos.size(); ++j)
+      WGW_CK(c->prof.run(PK_CONV, 16.0 * n_pert * rs.n + 8.0 * n_pert * rs.nrb(), 0, st, [&] {
+        return launch_rb_to_sphere(n_pert, c->drho_all.as<double>() + j * n_real * ldr, ldr, c->brow.as<int>(),
+                                   scale, rs.map(), drho + (size_t)k_pos[j] * n_pert * 2 * rs.n, 2L * rs.n, st); }));
+  }
   WGW_CK(cudaStreamSynchronize(st));
   c->prof.flush();
   return solve_status;

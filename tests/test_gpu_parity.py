@@ -109,6 +109,44 @@ def test_device_entry_point_matches_host_and_symmetrised(W, cfg24, ref24):
     assert rel_err(got, chi0.apply_chibar0(m, phi, [0.0])) < 1e-10
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_imaginary_frequencies_match_sum_over_states(W, cfg24, prec):
+    """chi0(i w) at several w, batched over frequencies (complex-shifted solves), incl. w = 0."""
+    dV = synth.perturbations(cfg24.miller_rho, cfg24.L, 8, 2)
+    oms = [0.35, 0.0, 4.0, 25.0]
+    ref = chi0.sos_drho(model_of(cfg24), dV, oms)
+    opt = dict(precision=W.WGW_FP64, cg_tol=1e-13) if prec == "fp64" else dict(precision=W.WGW_MIXED, cg_tol=1e-11)
+    ctx = setup(W, cfg24, **opt)
+    drho, st, _ = W.wgw_apply_chi0(ctx, dV, omega=oms)
+    assert st["n_systems"] == 32 * len(oms)
+    assert rel_err(drho.reshape(drho.shape[0], -1), ref.reshape(ref.shape[0], -1)) < (1e-10 if prec == "fp64" else 1e-8)
+
+
+def test_imaginary_frequency_complex_perturbation(W, tiny):
+    dV = synth.perturbations(tiny.miller_rho, tiny.L, 2, 13, hermitian=False)
+    ref = chi0.sos_drho(model_of(tiny), dV, [0.7, 3.0])
+    ctx = setup(W, tiny, cg_tol=1e-13)
+    drho, st, _ = W.wgw_apply_chi0(ctx, dV, omega=[0.7, 3.0])
+    assert rel_err(drho.reshape(drho.shape[0], -1), ref.reshape(ref.shape[0], -1)) < 1e-10
+
+
+def test_gauss_legendre_frequency_batch(W, cfg24):
+    """32 Gauss-Legendre frequencies on [0, 50 Ha] for 8 perturbations (1024 complex systems, mixed path)."""
+    oms, _ = synth.gauss_legendre_omega(32, 50.0)
+    phi = synth.perturbations(cfg24.miller_rho, cfg24.L, 8, 17)
+    m = model_of(cfg24)
+    ref = chi0.apply_chibar0(m, phi, oms)
+    ctx = setup(W, cfg24, precision=W.WGW_MIXED, cg_tol=1e-11)
+    import torch
+    x = torch.from_numpy(np.ascontiguousarray(phi.T)).cuda()
+    out = torch.zeros((32, 8, cfg24.n_rho), dtype=torch.complex128, device="cuda")
+    st, _ = W.wgw_apply_chibar0_dev(ctx, x, oms, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().transpose(2, 1, 0)
+    assert st["n_systems"] == 32 * 32 and st["n_converged"] == 32 * 32
+    assert rel_err(got.reshape(got.shape[0], -1), ref.reshape(ref.shape[0], -1)) < 1e-8
+
+
 def test_zero_and_empty_batches(W, tiny):
     ctx = setup(W, tiny)
     z = np.zeros((tiny.n_rho, 2), np.complex128)
@@ -121,7 +159,7 @@ def test_zero_and_empty_batches(W, tiny):
 def test_invalid_inputs_are_rejected(W, tiny):
     with pytest.raises(W.WgwError) as e:
         ctx = setup(W, tiny)
-        W.wgw_apply_chi0(ctx, synth.perturbations(tiny.miller_rho, tiny.L, 1, 3), omega=[0.5])
+        W.wgw_apply_chi0(ctx, synth.perturbations(tiny.miller_rho, tiny.L, 1, 3), omega=[0.5, -0.5])
     assert e.value.status == W.WGW_ERR_ARG
     bad = tiny.psi_v.copy()
     bad[1, 0] += 0.3j          # no longer real in r
