@@ -192,6 +192,26 @@ int wgw_pdep_davidson(wgw_ctx* ctx, int n_pdep, const double* x0, double* eig, d
                       wgw_stats* st);
 
 /*
+ * Frequency dependence of chi0 in a basis by Lanczos chains (Sec. 3, the recurrence above
+ * Eq. lanczos, and Eq. lanczos).  For every occupied state v and basis vector m, a chain on
+ * P_c H P_c starts from b = P_c [phi~_m psi_v] (phi~ = v^1/2 phi), q^1 = b/|b|, beta_1 = |b|,
+ * q^{l+1} = [(H - alpha_l) q^l - beta_l q^{l-1}] / beta_{l+1} with full reorthogonalisation
+ * (two classical Gram-Schmidt passes, each followed by P_c), all in FP64 on the GPU.  With d, U
+ * the eigenpairs of each chain's tridiagonal matrix,
+ *   chi0_nm(i w) = (f_s/Omega) sum_v beta_1 sum_{l,l'} <P_c phi~_n psi_v|q^l> U_{l l'} U_{1 l'}
+ *                  [1/(e_v - d_l' - i w) + 1/(e_v - d_l' + i w)]   (real).
+ *   phi        host, N_rho x n_pdep complex basis (its real-in-r part is used), e.g. the PDEP basis.
+ *   n_steps    chain length, 1..255.
+ *   omega      host, n_omega >= 0 imaginary frequencies (may be NULL when n_omega = 0).
+ *   alpha, beta  host outputs (or NULL), n_v x n_pdep x n_steps, l fastest; beta[..][0] = |b|.
+ *   chi0_pdep  host output (or NULL), n_omega x n_pdep x n_pdep: chi0_nm(i w_k) at
+ *              chi0_pdep[(k * n_pdep + m) * n_pdep + n].
+ * A chain whose residual vanishes (Krylov space exhausted) continues with zero vectors.
+ */
+int wgw_lanczos(wgw_ctx* ctx, const double* phi, int n_pdep, int n_steps, const double* omega, int n_omega,
+                double* alpha, double* beta, double* chi0_pdep, wgw_stats* st);
+
+/*
  * Dense symmetric eigensolver of the Rayleigh-Ritz step (Sec. 4.2): A = Z diag(w) Z^T in FP64
  * on the GPU, one thread block (Householder tridiagonalisation, implicit-shift QL).  Device
  * pointers: A n x n column-major (overwritten), w n (ascending), Z n x n column-major.

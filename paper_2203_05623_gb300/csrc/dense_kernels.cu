@@ -34,6 +34,12 @@ __global__ void __launch_bounds__(1024) k_syev(int n, double* __restrict__ A, in
   extern __shared__ double rot[];            // 2 * n: cosines and sines of one QL sweep
   const int tid = threadIdx.x, nth = blockDim.x;
   Thr th{tid, nth};
+  // Batched use: block b works on matrix b (consecutive n x n blocks of A, Z, work, w, info).
+  A += (size_t)blockIdx.x * lda * n;
+  Z += (size_t)blockIdx.x * ldz * n;
+  w += (size_t)blockIdx.x * n;
+  work += (size_t)blockIdx.x * ((size_t)n * n + 4 * (size_t)n);
+  info += blockIdx.x;
   double* v = work;                          // n
   double* p = work + n;                      // n
   double* d = work + 2 * n;                  // n
@@ -232,6 +238,142 @@ __global__ void k_select_scale(int k, const double* __restrict__ Zc, int ldz, co
   }
 }
 
+
+// ---------------------------------------------------------------- Lanczos chains (Sec. 3, Eq. lanczos)
+// Chain s holds q^l at Q + (l * n_ch + s) * ld.  One block per chain.
+
+// alpha_l = q^l . Hq^l, r = Hq^l - alpha_l q^l - beta_l q^{l-1} (into R).
+__global__ void k_lz_three_term(int n, int l, int n_ch, const double* __restrict__ Q, const double* __restrict__ HQ,
+                                double* __restrict__ R, long ld, double* __restrict__ alpha,
+                                const double* __restrict__ beta, int n_steps) {
+  __shared__ double red[33];
+  const int s = blockIdx.x;
+  Thr th{(int)threadIdx.x, (int)blockDim.x};
+  const double* q = Q + ((size_t)l * n_ch + s) * ld;
+  const double* hq = HQ + (size_t)s * ld;
+  double part = 0.0;
+  for (int i = th.tid; i < n; i += th.nth) part += q[i] * hq[i];
+  const double a = block_sum(part, red, th);
+  const double b = l > 0 ? beta[(size_t)s * n_steps + l] : 0.0;
+  const double* qp = l > 0 ? Q + ((size_t)(l - 1) * n_ch + s) * ld : nullptr;
+  double* r = R + (size_t)s * ld;
+  for (int i = th.tid; i < n; i += th.nth) r[i] = hq[i] - a * q[i] - (qp ? b * qp[i] : 0.0);
+  if (th.tid == 0) alpha[(size_t)s * n_steps + l] = a;
+}
+
+// One classical Gram-Schmidt pass of r against q^0 .. q^l of its chain.
+__global__ void k_lz_reorth(int n, int l, int n_ch, const double* __restrict__ Q, double* __restrict__ R, long ld) {
+  __shared__ double red[33];
+  __shared__ double coef[256];
+  const int s = blockIdx.x;
+  Thr th{(int)threadIdx.x, (int)blockDim.x};
+  double* r = R + (size_t)s * ld;
+  for (int j = 0; j <= l; ++j) {
+    const double* q = Q + ((size_t)j * n_ch + s) * ld;
+    double part = 0.0;
+    for (int i = th.tid; i < n; i += th.nth) part += q[i] * r[i];
+    const double cj = block_sum(part, red, th);
+    if (th.tid == 0) coef[j] = cj;
+  }
+  __syncthreads();
+  for (int i = th.tid; i < n; i += th.nth) {
+    double acc = r[i];
+    for (int j = 0; j <= l; ++j) acc -= coef[j] * Q[((size_t)j * n_ch + s) * ld + i];
+    r[i] = acc;
+  }
+}
+
+// beta_{l+1} = |r|, q^{l+1} = r / beta_{l+1} (a chain whose |r| vanished relative to beta_0 stops:
+// q^{l+1} = 0).
+__global__ void k_lz_normalise(int n, int l, int n_ch, const double* __restrict__ R, double* __restrict__ Q, long ld,
+                               double* __restrict__ beta, int n_steps) {
+  __shared__ double red[33];
+  const int s = blockIdx.x;
+  Thr th{(int)threadIdx.x, (int)blockDim.x};
+  const double* r = R + (size_t)s * ld;
+  double part = 0.0;
+  for (int i = th.tid; i < n; i += th.nth) part += r[i] * r[i];
+  const double nb = sqrt(block_sum(part, red, th));
+  const double b0 = beta[(size_t)s * n_steps];
+  const bool stop = !(nb > 1e-14 * b0);
+  double* q = Q + ((size_t)(l + 1) * n_ch + s) * ld;
+  for (int i = th.tid; i < n; i += th.nth) q[i] = stop ? 0.0 : r[i] / nb;
+  if (th.tid == 0) beta[(size_t)s * n_steps + l + 1] = stop ? 0.0 : nb;
+}
+
+// beta_0 = |b|, q^0 = b / beta_0.
+__global__ void k_lz_start(int n, const double* __restrict__ B, double* __restrict__ Q, long ld,
+                           double* __restrict__ beta, int n_steps) {
+  __shared__ double red[33];
+  const int s = blockIdx.x;
+  Thr th{(int)threadIdx.x, (int)blockDim.x};
+  const double* b = B + (size_t)s * ld;
+  double part = 0.0;
+  for (int i = th.tid; i < n; i += th.nth) part += b[i] * b[i];
+  const double nb = sqrt(block_sum(part, red, th));
+  double* q = Q + (size_t)s * ld;
+  for (int i = th.tid; i < n; i += th.nth) q[i] = nb > 0 ? b[i] / nb : 0.0;
+  if (th.tid == 0) beta[(size_t)s * n_steps] = nb;
+}
+
+// Dense tridiagonal matrix of each chain: alpha on the diagonal, beta_1.. off it.
+__global__ void k_lz_tridiag(int n_ch, int n_steps, const double* __restrict__ alpha, const double* __restrict__ beta,
+                             double* __restrict__ T) {
+  const size_t total = (size_t)n_ch * n_steps * n_steps;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int s = (int)(e / ((size_t)n_steps * n_steps));
+    const int rem = (int)(e % ((size_t)n_steps * n_steps));
+    const int i = rem % n_steps, j = rem / n_steps;
+    double v = 0.0;
+    if (i == j) v = alpha[(size_t)s * n_steps + i];
+    else if (j == i + 1) v = beta[(size_t)s * n_steps + j];
+    else if (i == j + 1) v = beta[(size_t)s * n_steps + i];
+    T[e] = v;
+  }
+}
+
+// y[(k, s, l)] = beta_0 sum_l' U_{l l'} U_{0 l'} g_k(d_l'), g = 1/(e_v - d - i w) + 1/(e_v - d + i w)
+// = 2 (e_v - d) / ((e_v - d)^2 + w^2), for chain s = m * n_v + v.
+__global__ void k_lz_resolvent(int n_ch, int n_steps, int n_v, int n_om, const double* __restrict__ d,
+                               const double* __restrict__ U, const double* __restrict__ beta,
+                               const double* __restrict__ e_v, const double* __restrict__ omega,
+                               double* __restrict__ y) {
+  const size_t total = (size_t)n_om * n_ch * n_steps;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int l = (int)(e % n_steps);
+    const int s = (int)((e / n_steps) % n_ch);
+    const int k = (int)(e / ((size_t)n_steps * n_ch));
+    const double ev = e_v[s % n_v], w = omega[k];
+    const double* Us = U + (size_t)s * n_steps * n_steps;   // column-major: U(i, j) at j * n_steps + i
+    const double* ds = d + (size_t)s * n_steps;
+    double acc = 0.0;
+    for (int lp = 0; lp < n_steps; ++lp) {
+      const double x = ev - ds[lp];
+      acc += Us[(size_t)lp * n_steps + l] * Us[(size_t)lp * n_steps] * (2.0 * x / (x * x + w * w));
+    }
+    y[e] = beta[(size_t)s * n_steps] * acc;
+  }
+}
+
+// chi0[k][m][n] = coef sum_v sum_l ov_v[n][l * n_pdep + m] y[k][m n_v + v][l].
+__global__ void k_lz_assemble(int n_pdep, int n_v, int n_steps, int n_om, const double* __restrict__ ov,
+                              const double* __restrict__ y, double coef, double* __restrict__ chi) {
+  const int n_ch = n_pdep * n_v;
+  const size_t total = (size_t)n_om * n_pdep * n_pdep;
+  const size_t ovs = (size_t)((n_pdep + 63) / 64 * 64) * n_steps * n_pdep;   // per-v block of gemm output
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int n = (int)(e % n_pdep);
+    const int m = (int)((e / n_pdep) % n_pdep);
+    const int k = (int)(e / ((size_t)n_pdep * n_pdep));
+    double acc = 0.0;
+    for (int v = 0; v < n_v; ++v) {
+      const double* o = ov + (size_t)v * ovs + (size_t)n * n_steps * n_pdep;
+      const double* yy = y + ((size_t)k * n_ch + (size_t)m * n_v + v) * n_steps;
+      for (int l = 0; l < n_steps; ++l) acc += o[(size_t)l * n_pdep + m] * yy[l];
+    }
+    chi[e] = coef * acc;
+  }
+}
 }  // namespace
 
 cudaError_t launch_syev(int n, double* A, int lda, double* w, double* Z, int ldz, double* work, int* info,
@@ -244,6 +386,60 @@ cudaError_t launch_syev(int n, double* A, int lda, double* w, double* Z, int ldz
     if (err != cudaSuccess) return err;
   }
   k_syev<<<1, 1024, smem, st>>>(n, A, lda, w, Z, ldz, work, info);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_syev_batched(int n, int batch, double* A, double* w, double* Z, double* work, int* info,
+                                cudaStream_t st) {
+  if (n <= 0 || batch <= 0) return cudaSuccess;
+  if (n > kSyevMax) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(double) * 2 * (size_t)n;
+  if (smem > 48 * 1024) {
+    cudaError_t err = cudaFuncSetAttribute(k_syev, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+  }
+  k_syev<<<batch, n <= 128 ? 128 : 1024, smem, st>>>(n, A, n, w, Z, n, work, info);
+  return cudaGetLastError();
+}
+
+#define WGW_G1D(total) std::max<size_t>(1, std::min<size_t>(4096, ((size_t)(total) + 255) / 256))
+
+cudaError_t launch_lz_start(int n, int n_ch, const double* B, double* Q, long ld, double* beta, int n_steps,
+                            cudaStream_t st) {
+  k_lz_start<<<n_ch, 256, 0, st>>>(n, B, Q, ld, beta, n_steps);
+  return cudaGetLastError();
+}
+cudaError_t launch_lz_three_term(int n, int l, int n_ch, const double* Q, const double* HQ, double* R, long ld,
+                                 double* alpha, const double* beta, int n_steps, cudaStream_t st) {
+  k_lz_three_term<<<n_ch, 256, 0, st>>>(n, l, n_ch, Q, HQ, R, ld, alpha, beta, n_steps);
+  return cudaGetLastError();
+}
+cudaError_t launch_lz_reorth(int n, int l, int n_ch, const double* Q, double* R, long ld, cudaStream_t st) {
+  if (l >= 256) return cudaErrorInvalidValue;
+  k_lz_reorth<<<n_ch, 256, 0, st>>>(n, l, n_ch, Q, R, ld);
+  return cudaGetLastError();
+}
+cudaError_t launch_lz_normalise(int n, int l, int n_ch, const double* R, double* Q, long ld, double* beta,
+                                int n_steps, cudaStream_t st) {
+  k_lz_normalise<<<n_ch, 256, 0, st>>>(n, l, n_ch, R, Q, ld, beta, n_steps);
+  return cudaGetLastError();
+}
+cudaError_t launch_lz_tridiag(int n_ch, int n_steps, const double* alpha, const double* beta, double* T,
+                              cudaStream_t st) {
+  k_lz_tridiag<<<WGW_G1D((size_t)n_ch * n_steps * n_steps), 256, 0, st>>>(n_ch, n_steps, alpha, beta, T);
+  return cudaGetLastError();
+}
+cudaError_t launch_lz_resolvent(int n_ch, int n_steps, int n_v, int n_om, const double* d, const double* U,
+                                const double* beta, const double* e_v, const double* omega, double* y,
+                                cudaStream_t st) {
+  k_lz_resolvent<<<WGW_G1D((size_t)n_om * n_ch * n_steps), 256, 0, st>>>(n_ch, n_steps, n_v, n_om, d, U, beta,
+                                                                          e_v, omega, y);
+  return cudaGetLastError();
+}
+cudaError_t launch_lz_assemble(int n_pdep, int n_v, int n_steps, int n_om, const double* ov, const double* y,
+                               double coef, double* chi, cudaStream_t st) {
+  k_lz_assemble<<<WGW_G1D((size_t)n_om * n_pdep * n_pdep), 256, 0, st>>>(n_pdep, n_v, n_steps, n_om, ov, y,
+                                                                          coef, chi);
   return cudaGetLastError();
 }
 

@@ -41,10 +41,11 @@ cudaError_t launch_drho_xline(int m, FftCtx<T> f, const cplx<T>* Tbuf, const T* 
 template <typename T>
 cudaError_t launch_pc(T* Y, long ldy, int n_sys, const int* list, const T* Psi, long ldp, int n, int nv,
                       const int* active, T* work, cudaStream_t st);
-// C = A^T B: A is K x m (column j at A + j*lda), B is K x n; C is written row-major with rows
-// of length n, padded to a multiple of 64 rows.  work: gemm_tn_work_elems(K, m, n) doubles.
+// C = A^T B: A is K x m (column j at A + j*lda), B is K x n (column j at B + c_j * ldb with
+// c_j = cols[j], or j when cols is null); C is written row-major with rows of length n, padded
+// to a multiple of 64 rows.  work: gemm_tn_work_elems(K, m, n) doubles.
 cudaError_t launch_gemm_tn(const double* A, long lda, const double* B, long ldb, int K, int m, int n, double* C,
-                           double* work, cudaStream_t st);
+                           double* work, cudaStream_t st, const int* cols = nullptr);
 size_t gemm_tn_work_elems(int K, int m, int n);
 // Y[:, j] = beta Y[:, j] + alpha sum_v A[:, v] C[v][j]: A is n x k, C row-major k x ncols (row length ldc).
 cudaError_t launch_gemm_nn(const double* A, long lda, int n, int k, const double* C, long ldc, int ncols,
@@ -79,6 +80,23 @@ cudaError_t launch_shifted_residual(int n_cs, int n, const double* B, const doub
                                     const double* omega, double* R, long ld, const int* active, cudaStream_t st);
 // out[s] = |x_{2s}|^2 + |x_{2s+1}|^2.
 cudaError_t launch_pair_norm2(int n_cs, int n, const double* x, long ld, double* out, cudaStream_t st);
+// Lanczos chains (dense_kernels.cu); chain s keeps q^l at Q + (l * n_ch + s) * ld.
+cudaError_t launch_syev_batched(int n, int batch, double* A, double* w, double* Z, double* work, int* info,
+                                cudaStream_t st);
+cudaError_t launch_lz_start(int n, int n_ch, const double* B, double* Q, long ld, double* beta, int n_steps,
+                            cudaStream_t st);
+cudaError_t launch_lz_three_term(int n, int l, int n_ch, const double* Q, const double* HQ, double* R, long ld,
+                                 double* alpha, const double* beta, int n_steps, cudaStream_t st);
+cudaError_t launch_lz_reorth(int n, int l, int n_ch, const double* Q, double* R, long ld, cudaStream_t st);
+cudaError_t launch_lz_normalise(int n, int l, int n_ch, const double* R, double* Q, long ld, double* beta,
+                                int n_steps, cudaStream_t st);
+cudaError_t launch_lz_tridiag(int n_ch, int n_steps, const double* alpha, const double* beta, double* T,
+                              cudaStream_t st);
+cudaError_t launch_lz_resolvent(int n_ch, int n_steps, int n_v, int n_om, const double* d, const double* U,
+                                const double* beta, const double* e_v, const double* omega, double* y,
+                                cudaStream_t st);
+cudaError_t launch_lz_assemble(int n_pdep, int n_v, int n_steps, int n_om, const double* ov, const double* y,
+                               double coef, double* chi, cudaStream_t st);
 // Ordered list of the systems s < n_sys with active[s] != 0, and their count.
 cudaError_t launch_build_list(const int* active, int n_sys, int* list, int* count, cudaStream_t st);
 int pc_kblocks(int n, int n_sys);

@@ -1047,6 +1047,135 @@ int davidson_impl(wgw_ctx* c, int npd, const double* x0, double* eig, double* ba
   return converged == npd ? WGW_OK : fail(WGW_ERR_NOCONV, "Davidson did not converge");
 }
 
+// ---------------------------------------------------------------- Lanczos chains (Sec. 3)
+// Chains on P_c H P_c for every (state v, basis vector m), started from P_c [phi~_m psi_v]
+// (phi~ = v^1/2 phi), FP64 throughout; chi0_nm(i w) from the chains' tridiagonal spectra.
+int lanczos_impl(wgw_ctx* c, const double* phi, int npd, int n_steps, const double* omega, int n_om,
+                 double* alpha_out, double* beta_out, double* chi_out, wgw_stats* st_out) {
+  cudaStream_t st = c->stream;
+  const int N = c->N, n_v = c->n_v, n = c->wfc.nrb(), nr = c->rho.nrb();
+  const long ldw = c->ld_w, ldr = c->ld_r;
+  const int n_ch = npd * n_v;
+  // Perturbations phi~_m = v^1/2 phi_m (real-in-r part), to real space.
+  WGW_TRY(c->dv_rb.ensure(sizeof(double) * (size_t)npd * ldr));
+  {
+    DevBuf xin;
+    WGW_TRY(xin.ensure(sizeof(double) * 2 * (size_t)c->rho.n * npd));
+    WGW_CK(cudaMemcpy(xin.p, phi, sizeof(double) * 2 * (size_t)c->rho.n * npd, cudaMemcpyHostToDevice));
+    WGW_CK(cudaMemsetAsync(c->dv_rb.p, 0, sizeof(double) * (size_t)npd * ldr, st));
+    WGW_CK(launch_sphere_to_rb(npd, xin.as<double>(), 2L * c->rho.n, c->rho.d_vsqrt.as<double>(), c->rho.map(), 0,
+                               c->dv_rb.as<double>(), ldr, st));
+    WGW_CK(cudaStreamSynchronize(st));
+  }
+  WGW_TRY(ensure_work(c, n_ch, npd));
+  std::vector<int> ai(n_ch), bi(n_ch);
+  for (int m = 0; m < npd; ++m)
+    for (int v = 0; v < n_v; ++v) { ai[m * n_v + v] = v; bi[m * n_v + v] = m; }
+  WGW_CK(cudaMemcpyAsync(c->a_idx.p, ai.data(), sizeof(int) * n_ch, cudaMemcpyHostToDevice, st));
+  WGW_CK(cudaMemcpyAsync(c->b_idx.p, bi.data(), sizeof(int) * n_ch, cudaMemcpyHostToDevice, st));
+  WGW_CK(cudaMemsetAsync(c->d.shift.p, 0, sizeof(double) * n_ch, st));   // A = P_c H P_c
+  double* dvr = c->dv_r.as<double>();
+  WGW_TRY(to_real<double>(c, c->d, c->rho, c->dv_rb.as<double>(), ldr, npd, dvr, c->Trho, st));
+  FftCtx<double> f = c->d.fft(c->plan);
+  double* S = c->d.Bv.as<double>();
+  {
+    const int NP = 2 * c->wfc.m + 1, pairs = (n_ch + 1) / 2;
+    WGW_TRY(c->d.Tw.ensure(sizeof(cplx<double>) * (size_t)pairs * NP * N * N));
+    XArgs<double> a{};
+    a.mode = XM_FROM_REAL; a.A = c->d.psi_r.as<double>(); a.lda = c->grid3; a.a_index = c->a_idx.as<int>();
+    a.Bm = dvr; a.ldb = c->grid3; a.b_index = c->b_idx.as<int>(); a.n_sys = n_ch;
+    WGW_CK(launch_xline<double>(c->wfc.m, f, c->d.Tw.as<cplx<double>>(), a, nullptr, st));
+    Epi<double> e{};
+    e.out = S; e.ldo = ldw; e.vcoef = 1.0; e.n_sys = n_ch;
+    WGW_CK(launch_plane_r2g<double>(c->wfc.tab(), c->wfc.npt_max, f, c->d.Tw.as<cplx<double>>(), e, st));
+    WGW_TRY(run_pc<double>(c, S, n_ch, nullptr, c->d.psi.as<double>(), nullptr, st));
+  }
+  DevBuf Qb, al, be, T, dd, U, wk, inf, ov, y, om, lists;
+  WGW_TRY(Qb.ensure(sizeof(double) * (size_t)(n_steps + 1) * n_ch * ldw));
+  WGW_TRY(al.ensure(sizeof(double) * (size_t)n_ch * n_steps));
+  WGW_TRY(be.ensure(sizeof(double) * (size_t)n_ch * n_steps));
+  WGW_CK(cudaMemsetAsync(al.p, 0, al.bytes, st));
+  WGW_CK(cudaMemsetAsync(be.p, 0, be.bytes, st));
+  double* Q = Qb.as<double>();
+  double* HQ = c->d.Q.as<double>();
+  double* R = c->d.R.as<double>();
+  WGW_CK(launch_lz_start(n, n_ch, S, Q, ldw, be.as<double>(), n_steps, st));
+  for (int l = 0; l < n_steps; ++l) {
+    double* ql = Q + (size_t)l * n_ch * ldw;
+    WGW_TRY(apply_A<double>(c, c->d, ql, HQ, n_ch, nullptr, nullptr, st));
+    WGW_CK(launch_lz_three_term(n, l, n_ch, Q, HQ, R, ldw, al.as<double>(), be.as<double>(), n_steps, st));
+    if (l + 1 == n_steps) break;
+    for (int pass = 0; pass < 2; ++pass) {
+      WGW_CK(launch_lz_reorth(n, l, n_ch, Q, R, ldw, st));
+      WGW_TRY(run_pc<double>(c, R, n_ch, nullptr, c->d.psi.as<double>(), nullptr, st));
+    }
+    WGW_CK(launch_lz_normalise(n, l, n_ch, R, Q, ldw, be.as<double>(), n_steps, st));
+  }
+  // Overlaps <P_c phi~_n psi_v | q^l_(m,v)>, one product per state v.
+  const int mp = (npd + 63) / 64 * 64;
+  const size_t ovs = (size_t)mp * n_steps * npd;
+  WGW_TRY(ov.ensure(sizeof(double) * ovs * n_v));
+  WGW_TRY(lists.ensure(sizeof(int) * (size_t)n_steps * npd));
+  DevBuf gw;
+  WGW_TRY(gw.ensure(sizeof(double) * gemm_tn_work_elems(n, npd, n_steps * npd)));
+  std::vector<int> cols((size_t)n_steps * npd);
+  for (int v = 0; v < n_v; ++v) {
+    for (int l = 0; l < n_steps; ++l)
+      for (int m = 0; m < npd; ++m) cols[(size_t)l * npd + m] = l * n_ch + m * n_v + v;
+    WGW_CK(cudaMemcpyAsync(lists.p, cols.data(), sizeof(int) * cols.size(), cudaMemcpyHostToDevice, st));
+    WGW_CK(launch_gemm_tn(S + (size_t)v * ldw, (long)n_v * ldw, Q, ldw, n, npd, n_steps * npd,
+                          ov.as<double>() + (size_t)v * ovs, gw.as<double>(), st, lists.as<int>()));
+    WGW_CK(cudaStreamSynchronize(st));   // cols is reused for the next state
+  }
+  // Tridiagonal spectra d, U of every chain.
+  WGW_TRY(T.ensure(sizeof(double) * (size_t)n_ch * n_steps * n_steps));
+  WGW_TRY(U.ensure(sizeof(double) * (size_t)n_ch * n_steps * n_steps));
+  WGW_TRY(dd.ensure(sizeof(double) * (size_t)n_ch * n_steps));
+  WGW_TRY(wk.ensure(sizeof(double) * (size_t)n_ch * syev_work_elems(n_steps)));
+  WGW_TRY(inf.ensure(sizeof(int) * n_ch));
+  WGW_CK(launch_lz_tridiag(n_ch, n_steps, al.as<double>(), be.as<double>(), T.as<double>(), st));
+  WGW_CK(launch_syev_batched(n_steps, n_ch, T.as<double>(), dd.as<double>(), U.as<double>(), wk.as<double>(),
+                             inf.as<int>(), st));
+  std::vector<int> infh(n_ch);
+  WGW_CK(cudaMemcpyAsync(infh.data(), inf.p, sizeof(int) * n_ch, cudaMemcpyDeviceToHost, st));
+  WGW_CK(cudaStreamSynchronize(st));
+  for (int q = 0; q < n_ch; ++q)
+    if (infh[q] != 0) return fail(WGW_ERR_NOCONV, "tridiagonal eigensolver did not converge");
+  if (chi_out && n_om > 0) {
+    WGW_TRY(om.ensure(sizeof(double) * n_om));
+    WGW_CK(cudaMemcpyAsync(om.p, omega, sizeof(double) * n_om, cudaMemcpyHostToDevice, st));
+    WGW_TRY(y.ensure(sizeof(double) * (size_t)n_om * n_ch * n_steps));
+    WGW_CK(launch_lz_resolvent(n_ch, n_steps, n_v, n_om, dd.as<double>(), U.as<double>(), be.as<double>(),
+                               c->e_v_d.as<double>(), om.as<double>(), y.as<double>(), st));
+    DevBuf chi;
+    WGW_TRY(chi.ensure(sizeof(double) * (size_t)n_om * npd * npd));
+    WGW_CK(launch_lz_assemble(npd, n_v, n_steps, n_om, ov.as<double>(), y.as<double>(), c->opt.f_s / c->omega_cell,
+                              chi.as<double>(), st));
+    WGW_CK(cudaMemcpyAsync(chi_out, chi.p, sizeof(double) * (size_t)n_om * npd * npd, cudaMemcpyDeviceToHost, st));
+    WGW_CK(cudaStreamSynchronize(st));
+  }
+  std::vector<double> ah((size_t)n_ch * n_steps), bh((size_t)n_ch * n_steps);
+  WGW_CK(cudaMemcpyAsync(ah.data(), al.p, sizeof(double) * ah.size(), cudaMemcpyDeviceToHost, st));
+  WGW_CK(cudaMemcpyAsync(bh.data(), be.p, sizeof(double) * bh.size(), cudaMemcpyDeviceToHost, st));
+  WGW_CK(cudaStreamSynchronize(st));
+  for (int v = 0; v < n_v; ++v)
+    for (int m = 0; m < npd; ++m)
+      for (int l = 0; l < n_steps; ++l) {
+        const size_t dst = ((size_t)v * npd + m) * n_steps + l, src = ((size_t)m * n_v + v) * n_steps + l;
+        if (alpha_out) alpha_out[dst] = ah[src];
+        if (beta_out) beta_out[dst] = bh[src];
+      }
+  c->prof.flush();
+  if (st_out) {
+    *st_out = wgw_stats{};
+    st_out->n_systems = n_ch;
+    st_out->n_converged = n_ch;
+    st_out->max_iters = n_steps;
+  }
+  (void)nr;
+  return WGW_OK;
+}
+
 }  // namespace
 
 namespace wgw {
@@ -1281,6 +1410,16 @@ int wgw_pdep_davidson(wgw_ctx* c, int n_pdep, const double* x0, double* eig, dou
   if (!c || n_pdep < 1 || !eig) return fail(WGW_ERR_ARG, "need a context, n_pdep >= 1 and eig");
   if (n_pdep > c->rho.nrb() / 2) return fail(WGW_ERR_ARG, "n_pdep too large for the density sphere");
   return davidson_impl(c, n_pdep, x0, eig, basis, st);
+}
+
+int wgw_lanczos(wgw_ctx* c, const double* phi, int n_pdep, int n_steps, const double* omega, int n_omega,
+                double* alpha, double* beta, double* chi0_pdep, wgw_stats* st) {
+  g_last_error.clear();
+  if (!c || !phi || n_pdep < 1 || n_steps < 1 || n_steps > 255 || n_omega < 0 || (n_omega > 0 && !omega))
+    return fail(WGW_ERR_ARG, "need a context, phi, n_pdep >= 1, 1 <= n_steps <= 255, n_omega >= 0");
+  for (int k = 0; k < n_omega; ++k)
+    if (!(omega[k] >= 0.0)) return fail(WGW_ERR_ARG, "imaginary frequencies must be >= 0");
+  return lanczos_impl(c, phi, n_pdep, n_steps, omega, n_omega, alpha, beta, chi0_pdep, st);
 }
 
 int wgw_symm_eig_dev(int n, double* A_dev, double* w_dev, double* Z_dev, void* stream) {

@@ -79,6 +79,8 @@ def lib(path: str | None = None):
     L.wgw_pdep_davidson.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, _dp, _dp, ctypes.POINTER(Stats)]
     L.wgw_symm_eig_dev.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     L.wgw_symm_eig_noalloc_dev.argtypes = L.wgw_symm_eig_dev.argtypes
+    L.wgw_lanczos.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp,
+                              ctypes.POINTER(Stats)]
     L.wgw_system_info.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp]
     L.wgw_destroy.argtypes = [ctypes.c_void_p]
     L.wgw_status_string.restype = ctypes.c_char_p
@@ -215,6 +217,24 @@ def wgw_pdep_davidson(ctx: Context, n_pdep: int, x0=None, want_basis=True, allow
                                 ctypes.byref(st))
     _check(s, "wgw_pdep_davidson", (WGW_OK, WGW_ERR_NOCONV) if allow_noconv else (WGW_OK,))
     return eig, (basis.T if want_basis else None), st.as_dict(), s
+
+
+def wgw_lanczos(ctx: Context, phi, n_steps: int, omega=()):
+    """Lanczos chains for every (v, m): returns (chi0 (n_pdep, n_pdep, n_omega) as [n, m, k],
+    alpha, beta (n_v, n_pdep, n_steps), stats)."""
+    phi = np.asarray(phi, np.complex128)
+    npd = phi.shape[1]
+    om = np.ascontiguousarray(omega, np.float64)
+    a = np.zeros((ctx.n_v, npd, n_steps))
+    b = np.zeros((ctx.n_v, npd, n_steps))
+    chi = np.zeros((max(len(om), 1), npd, npd))
+    st = Stats()
+    pb = _interleave(phi)
+    _check(lib().wgw_lanczos(ctx.handle, pb.ctypes.data_as(_dp), npd, n_steps,
+                             om.ctypes.data_as(_dp) if len(om) else None, len(om), a.ctypes.data_as(_dp),
+                             b.ctypes.data_as(_dp), chi.ctypes.data_as(_dp) if len(om) else None,
+                             ctypes.byref(st)), "wgw_lanczos")
+    return chi[: len(om)].transpose(2, 1, 0), a, b, st.as_dict()
 
 
 def wgw_symm_eig_dev(A_dev, stream=None, w=None, Z=None, noalloc=False):
