@@ -95,7 +95,10 @@ int wgw_default_options(wgw_options* opt);
  *   grid     FFT points per axis; a product of 2, 3, 5; must exceed 2 m_rho where m_rho is the
  *            largest |Miller index| of the density sphere (then H psi by FFTs is alias-free).
  *   vloc_G   V_loc(G) on the density sphere, N_rho complex; must be real in r (V(-G) = V(G)^*).
- *   n_proj, beta_G, d_proj   Kleinman-Bylander projectors; this version requires n_proj = 0.
+ *   n_proj   number of Kleinman-Bylander projectors (>= 0); H gains sum_p |beta_p> D_p <beta_p| (Sec. 3).
+ *   beta_G   N_pw x n_proj complex projectors on the wavefunction sphere (column-major), each real
+ *            in r; may be NULL when n_proj = 0.
+ *   d_proj   n_proj couplings D_p [Ha]; may be NULL when n_proj = 0.
  *   psi_v    occupied states, N_pw x n_v complex, column-major (state v at psi_v + 2 N_pw v);
  *            each must be real in r (psi(-G) = psi(G)^*) and the set orthonormal.
  *   e_v      their eigenvalues [Ha], n_v entries.

@@ -97,6 +97,11 @@ cudaError_t launch_lz_resolvent(int n_ch, int n_steps, int n_v, int n_om, const 
                                 cudaStream_t st);
 cudaError_t launch_lz_assemble(int n_pdep, int n_v, int n_steps, int n_om, const double* ov, const double* y,
                                double coef, double* chi, cudaStream_t st);
+// Q[:, s] += B diag(D) B^T P[:, s] for the systems of a list (Kleinman-Bylander term); B is n x n_proj.
+// work: pc_work_elems(n, n_sys, n_proj) elements of T.
+template <typename T>
+cudaError_t launch_kb(T* Q, const T* P, long ld, int n_sys, const int* list, const T* B, long ldb, int n, int n_proj,
+                      const T* D, T* work, cudaStream_t st);
 // Ordered list of the systems s < n_sys with active[s] != 0, and their count.
 cudaError_t launch_build_list(const int* active, int n_sys, int* list, int* count, cudaStream_t st);
 int pc_kblocks(int n, int n_sys);

@@ -379,6 +379,13 @@ __global__ void k_pair_norm2(int n, const double* x, long ld, double* out) {
   if (threadIdx.x == 0) out[blockIdx.x] = v;
 }
 
+template <typename T>
+__global__ void k_scale_c_rows(T* __restrict__ C, int rows, int ncols, const T* __restrict__ d) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)rows * ncols;
+       e += (size_t)gridDim.x * blockDim.x)
+    C[e] *= d[e / ncols];
+}
+
 inline dim3 grid_el(int n, int n_sys) {
   int bx = (n + 255) / 256;
   if (bx > 64) bx = 64;
@@ -609,6 +616,37 @@ cudaError_t launch_pair_norm2(int n_cs, int n, const double* x, long ld, double*
                                              CocgState, cudaStream_t);
 WGW_INST_COCG(float)
 WGW_INST_COCG(double)
+
+// Q[:, s_j] += B diag(D) B^T P[:, s_j]  (Kleinman-Bylander term, Sec. 3: V_NL = sum_p |beta_p> D_p <beta_p|).
+template <typename T>
+cudaError_t launch_kb(T* Q, const T* P, long ld, int n_sys, const int* list, const T* B, long ldb, int n, int n_proj,
+                      const T* D, T* work, cudaStream_t st) {
+  if (n_sys == 0 || n_proj == 0) return cudaSuccess;
+  const int n_kb = pc_kblocks(n, n_sys);
+  const int kblk = ((n + n_kb - 1) / n_kb + kGK - 1) / kGK * kGK;
+  const int nvp = (n_proj + kGT - 1) / kGT * kGT;
+  dim3 g1((n_sys + kGT - 1) / kGT, n_kb, nvp / kGT);
+  k_pc_gemm1<T><<<g1, 256, 0, st>>>(B, ldb, P, ld, n, n_proj, n_sys, list, kblk, work);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  const size_t slice = (size_t)nvp * n_sys;
+  if (n_kb > 1) {
+    k_pc_reduce<T><<<(int)std::min<size_t>((slice + 255) / 256, 4096), 256, 0, st>>>(work, slice, n_kb);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+  }
+  k_scale_c_rows<T><<<(int)std::min<size_t>(((size_t)n_proj * n_sys + 255) / 256, 4096), 256, 0, st>>>(
+      work, n_proj, n_sys, D);
+  err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  dim3 g2((n + kGT - 1) / kGT, (n_sys + kGT - 1) / kGT);
+  k_pc_gemm2<T><<<g2, 256, 0, st>>>(B, ldb, Q, ld, n, n_proj, n_sys, list, work, (long)n_sys, T(1), T(1), nullptr);
+  return cudaGetLastError();
+}
+template cudaError_t launch_kb<float>(float*, const float*, long, int, const int*, const float*, long, int, int,
+                                      const float*, float*, cudaStream_t);
+template cudaError_t launch_kb<double>(double*, const double*, long, int, const int*, const double*, long, int, int,
+                                       const double*, double*, cudaStream_t);
 
 #define WGW_INST_LA(T)                                                                             \
   template cudaError_t launch_pc<T>(T*, long, int, const int*, const T*, long, int, int,           \

@@ -101,9 +101,10 @@ struct Prec {
   DevBuf v_r;       // V_loc in real space
   // work
   DevBuf X, R, Z, P, Q, Bv, Tw, shift;
+  DevBuf kbB, kbD;  // KB projectors in the real basis (n_proj x ld_w) and couplings
   FftCtx<T> fft(const FftPlan& pl) const { FftCtx<T> f; f.plan = pl; f.tw = tw.as<cplx<T>>(); return f; }
   void release() {
-    DevBuf* all[] = {&tw, &psi, &psi_r, &v_r, &X, &R, &Z, &P, &Q, &Bv, &Tw, &shift};
+    DevBuf* all[] = {&tw, &psi, &psi_r, &v_r, &X, &R, &Z, &P, &Q, &Bv, &Tw, &shift, &kbB, &kbD};
     for (DevBuf* b : all) b->release();
   }
 };
@@ -163,7 +164,7 @@ struct Prof {
 
 struct wgw_ctx {
   double L = 0, ecut = 0, omega_cell = 0;
-  int N = 0, n_v = 0;
+  int N = 0, n_v = 0, n_proj = 0;
   long ld_w = 0, ld_r = 0, grid3 = 0;
   wgw_options opt{};
   FftPlan plan{};
@@ -221,7 +222,7 @@ int to_real(wgw_ctx* c, Prec<T>& pr, const HostSphere& sp, const T* X, long ldx,
 template <typename T>
 int run_pc(wgw_ctx* c, T* Y, int n_list, const int* list, const T* Psi, const int* active, cudaStream_t st) {
   const double n = c->wfc.nrb(), nv = c->n_v;
-  WGW_TRY(c->pc_work.ensure(sizeof(T) * pc_work_elems((int)n, n_list, c->n_v)));
+  WGW_TRY(c->pc_work.ensure(sizeof(T) * pc_work_elems((int)n, n_list, std::max(c->n_v, c->n_proj))));
   T* work = c->pc_work.as<T>();
   WGW_CK(c->prof.run(PK_PC, 2.0 * n_list * n * sizeof(T) + n * nv * sizeof(T), 4.0 * n * nv * n_list, st, [&] {
     return launch_pc<T>(Y, c->ld_w, n_list, list, Psi, c->ld_w, (int)n, c->n_v, active, work, st); }));
@@ -250,6 +251,12 @@ int apply_A(wgw_ctx* c, Prec<T>& pr, const T* P, T* Q, int n_list, const int* li
   e.shift = pr.shift.template as<T>(); e.n_sys = n_list; e.active = active; e.list = list;
   WGW_CK(c->prof.run(PK_R2G, tb + 2.0 * n_list * nrb * sizeof(T), 0, st, [&] {
     return launch_plane_r2g<T>(c->wfc.tab(), c->wfc.npt_max, f, Tb, e, st); }));
+  if (c->n_proj > 0) {
+    WGW_TRY(c->pc_work.ensure(sizeof(T) * pc_work_elems(nrb, n_list, std::max(c->n_v, c->n_proj))));
+    WGW_CK(c->prof.run(PK_PC, 3.0 * n_list * nrb * sizeof(T), 4.0 * nrb * c->n_proj * n_list, st, [&] {
+      return launch_kb<T>(Q, P, c->ld_w, n_list, list, pr.kbB.template as<T>(), c->ld_w, nrb, c->n_proj,
+                          pr.kbD.template as<T>(), c->pc_work.template as<T>(), st); }));
+  }
   WGW_TRY(run_pc<T>(c, Q, n_list, list, pr.psi.template as<T>(), active, st));
   return WGW_OK;
 }
@@ -1297,6 +1304,38 @@ static int setup_impl(wgw_ctx* c, const double* vloc_G, const double* psi_v, con
   return WGW_OK;
 }
 
+static int setup_kb(wgw_ctx* c, const double* beta_G, const double* d_proj) {
+  // Projectors beta_p(G) (wavefunction sphere, real in r) -> real basis, in FP64 and FP32.
+  const int np = c->n_proj;
+  cudaStream_t st = c->stream;
+  DevBuf tmp, anti, nrm;
+  WGW_TRY(tmp.ensure(sizeof(double) * 2 * (size_t)c->wfc.n * np));
+  WGW_CK(cudaMemcpy(tmp.p, beta_G, sizeof(double) * 2 * (size_t)c->wfc.n * np, cudaMemcpyHostToDevice));
+  WGW_TRY(c->d.kbB.ensure(sizeof(double) * (size_t)np * c->ld_w));
+  WGW_TRY(anti.ensure(sizeof(double) * (size_t)np * c->ld_w));
+  WGW_CK(cudaMemsetAsync(c->d.kbB.p, 0, c->d.kbB.bytes, st));
+  WGW_CK(cudaMemsetAsync(anti.p, 0, anti.bytes, st));
+  WGW_CK(launch_sphere_to_rb(np, tmp.as<double>(), 2L * c->wfc.n, nullptr, c->wfc.map(), 0, c->d.kbB.as<double>(), c->ld_w, st));
+  WGW_CK(launch_sphere_to_rb(np, tmp.as<double>(), 2L * c->wfc.n, nullptr, c->wfc.map(), 1, anti.as<double>(), c->ld_w, st));
+  WGW_TRY(nrm.ensure(sizeof(double) * 2 * np));
+  WGW_CK(launch_norm2<double>(np, c->wfc.nrb(), c->d.kbB.as<double>(), c->ld_w, nrm.as<double>(), st));
+  WGW_CK(launch_norm2<double>(np, c->wfc.nrb(), anti.as<double>(), c->ld_w, nrm.as<double>() + np, st));
+  std::vector<double> h(2 * np);
+  WGW_CK(cudaMemcpyAsync(h.data(), nrm.p, sizeof(double) * 2 * np, cudaMemcpyDeviceToHost, st));
+  WGW_CK(cudaStreamSynchronize(st));
+  for (int p = 0; p < np; ++p)
+    if (h[np + p] > 1e-24 * std::max(1.0, h[p])) return fail(WGW_ERR_ARG, "KB projector not real in r");
+  WGW_TRY(c->f.kbB.ensure(sizeof(float) * (size_t)np * c->ld_w));
+  WGW_CK((launch_copy_cast<double, float>(np, (int)c->ld_w, c->d.kbB.as<double>(), c->ld_w, c->f.kbB.as<float>(), c->ld_w, nullptr, st)));
+  std::vector<double> dd(d_proj, d_proj + np);
+  std::vector<float> df(np);
+  for (int p = 0; p < np; ++p) df[p] = (float)dd[p];
+  WGW_TRY(upload(c->d.kbD, dd));
+  WGW_TRY(upload(c->f.kbD, df));
+  WGW_CK(cudaStreamSynchronize(st));
+  return WGW_OK;
+}
+
 int wgw_setup(wgw_ctx** out, double L, double ecut, int grid, const double* vloc_G, int n_proj,
               const double* beta_G, const double* d_proj, const double* psi_v, const double* e_v,
               int n_v, const wgw_options* opt) {
@@ -1305,15 +1344,15 @@ int wgw_setup(wgw_ctx** out, double L, double ecut, int grid, const double* vloc
   *out = nullptr;
   if (!(L > 0) || !(ecut > 0) || grid < 4 || n_v < 1 || !vloc_G || !psi_v || !e_v)
     return fail(WGW_ERR_ARG, "invalid L, ecut, grid, n_v or null input");
-  if (n_proj != 0) return fail(WGW_ERR_ARG, "Kleinman-Bylander projectors are not supported by this version");
-  (void)beta_G; (void)d_proj;
+  if (n_proj < 0 || (n_proj > 0 && (!beta_G || !d_proj))) return fail(WGW_ERR_ARG, "bad Kleinman-Bylander projectors");
   wgw_options o;
   wgw_default_options(&o);
   if (opt) o = *opt;
   WGW_TRY(check_options(o));
   wgw_ctx* c = new wgw_ctx();
-  c->L = L; c->ecut = ecut; c->N = grid; c->n_v = n_v; c->omega_cell = L * L * L; c->opt = o;
-  const int s = setup_impl(c, vloc_G, psi_v, e_v);
+  c->L = L; c->ecut = ecut; c->N = grid; c->n_v = n_v; c->n_proj = n_proj; c->omega_cell = L * L * L; c->opt = o;
+  int s = setup_impl(c, vloc_G, psi_v, e_v);
+  if (s == WGW_OK && n_proj > 0) s = setup_kb(c, beta_G, d_proj);
   if (s != WGW_OK) { delete c; return s; }
   *out = c;
   return WGW_OK;

@@ -37,7 +37,9 @@ def rel_err(got, ref):
 
 def setup(W, s, **opt):
     o = W.wgw_default_options(**opt)
-    return W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, o)
+    kb = s.beta_G.shape[1] > 0
+    return W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, o,
+                       beta_G=s.beta_G if kb else None, d_proj=s.d_proj if kb else None)
 
 
 def test_gvectors_match_generator(W, cfg24):
@@ -145,6 +147,29 @@ def test_gauss_legendre_frequency_batch(W, cfg24):
     got = out.cpu().numpy().transpose(2, 1, 0)
     assert st["n_systems"] == 32 * 32 and st["n_converged"] == 32 * 32
     assert rel_err(got.reshape(got.shape[0], -1), ref.reshape(ref.shape[0], -1)) < 1e-8
+
+
+@pytest.fixture(scope="module", params=["kb12", "kb24"])
+def kbsys(request):
+    if request.param == "kb12":
+        cfg = synth.Config("kb12", L=6.0, ecut=2.5, grid=12, n_wells=2, well_seed=7, n_v=2, kb=True)
+    else:
+        cfg = synth.Config("kb24", L=10.0, ecut=5.0, grid=24, n_wells=4, well_seed=1, n_v=4, kb=True)
+    return synth.make_system(cfg)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_kb_projectors_match_sum_over_states(W, kbsys, prec):
+    """H = T + V_loc + sum_p |beta_p> D_p <beta_p| (Kleinman-Bylander), static and at i w."""
+    s = kbsys
+    assert s.beta_G.shape[1] == 4 * s.cfg.n_wells
+    dV = synth.perturbations(s.miller_rho, s.L, 3, 19)
+    oms = [0.0, 0.6]
+    ref = chi0.sos_drho(model_of(s), dV, oms)
+    opt = dict(precision=W.WGW_FP64, cg_tol=1e-13) if prec == "fp64" else dict(precision=W.WGW_MIXED, cg_tol=1e-11)
+    ctx = setup(W, s, **opt)
+    drho, st, _ = W.wgw_apply_chi0(ctx, dV, omega=oms)
+    assert rel_err(drho.reshape(drho.shape[0], -1), ref.reshape(ref.shape[0], -1)) < (1e-10 if prec == "fp64" else 1e-8)
 
 
 def test_zero_and_empty_batches(W, tiny):
