@@ -236,7 +236,46 @@ int wgw_symm_eig_dev(int n, double* A_dev, double* w_dev, double* Z_dev, void* s
  */
 int wgw_symm_eig_noalloc_dev(int n, double* A_dev, double* w_dev, double* Z_dev, void* stream);
 
-/* Releases the context and all device memory it owns.  NULL is allowed. */
+/*
+ * Serving (no counterpart in the paper, which runs one calculation per job): non-blocking
+ * requests on a context.  wgw_submit copies the request's inputs and returns a ticket at once;
+ * one worker thread per context runs queued requests on the context's stream, merging all
+ * queued requests with the same kind and frequency set into one batched apply (as many as 80 %
+ * of the free device memory admits), so requests that arrive while a batch runs are taken into
+ * the next one.  Requests on different contexts (different systems or grids) run on different
+ * streams and overlap on the GPU.  The result of a request equals its result alone up to the
+ * rounding of the batched reductions (tests bound it by the path's tolerance).
+ * While a context has requests in flight, its other entry points wait for the running batch.
+ */
+#define WGW_REQ_CHI0 0     /* out = chi0(i omega) dV, as wgw_apply_chi0 */
+#define WGW_REQ_CHIBAR0 1  /* out = chi0bar(i omega) phi, as wgw_apply_chibar0 */
+
+typedef struct wgw_request {
+  int kind;               /* WGW_REQ_CHI0 or WGW_REQ_CHIBAR0 */
+  const double* dV;       /* host, N_rho x n_pert complex; copied during wgw_submit */
+  int n_pert;
+  const double* omega;    /* host, n_omega >= 1 frequencies >= 0; copied */
+  int n_omega;
+  double* out;            /* host, N_rho x n_pert x n_omega complex; written by the library before the
+                             request is reported done; must stay valid until then */
+} wgw_request;
+
+typedef struct wgw_result {
+  int status;             /* status of the batched apply that served the request */
+  double latency_s;       /* submission -> results written */
+  double queue_s;         /* submission -> start of its batch */
+  int batch_requests;     /* requests merged into that batch */
+  int batch_systems;      /* Sternheimer systems of that batch */
+} wgw_result;
+
+int wgw_submit(wgw_ctx* ctx, const wgw_request* req, uint64_t* ticket);
+/* *done = 1 (and *res filled, ticket released) when the request has finished, else 0. */
+int wgw_poll(wgw_ctx* ctx, uint64_t ticket, int* done, wgw_result* res);
+/* Blocks until the request has finished; fills *res (may be NULL) and releases the ticket. */
+int wgw_wait(wgw_ctx* ctx, uint64_t ticket, wgw_result* res);
+
+/* Releases the context and all device memory it owns (after finishing queued requests).
+ * NULL is allowed. */
 void wgw_destroy(wgw_ctx* ctx);
 
 /* Static description of a status code. */

@@ -1,10 +1,17 @@
 // Host side of libwgw: plane-wave spheres, context set-up, and the chi0 apply
 // driver (Eq. sternheimer solved by batched CG, then Eq. dfpt).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstdio>
 #include <cstring>
+#include <deque>
+#include <map>
+#include <set>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/wgw.h"
@@ -181,7 +188,36 @@ struct wgw_ctx {
   Prof prof;
   std::vector<int> last_iters;      // per system of the last apply: CG iterations (all refinements)
   std::vector<double> last_relres;  // per system of the last apply: final FP64 ||b - A x|| / ||b||
+  // Serialises every entry point that uses the context's device state (callers and the
+  // request worker).
+  std::recursive_mutex mu;
+  // Request queue of wgw_submit (see the serving section below).
+  struct Req {
+    uint64_t ticket;
+    int kind;
+    int n_pert;
+    std::vector<double> dV;        // copied at submission
+    std::vector<double> omega;
+    double* out;
+    std::chrono::steady_clock::time_point t_submit;
+  };
+  struct Done { int status; double latency_s, queue_s; int batch_requests, batch_systems; };
+  std::mutex qmu;
+  std::condition_variable qcv;
+  std::deque<Req> queue;
+  std::map<uint64_t, Done> done;
+  std::set<uint64_t> running;
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  std::thread worker;
+  int device = 0;
   ~wgw_ctx() {
+    {
+      std::lock_guard<std::mutex> lk(qmu);
+      stop = true;
+    }
+    qcv.notify_all();
+    if (worker.joinable()) worker.join();
     prof.release();
     d.release(); f.release(); wfc.release(); rho.release();
     DevBuf* all[] = {&e_v_d, &dvin, &dv_rb, &dv_r, &Trho, &Dr, &drho_rb, &eps, &a_idx, &b_idx, &brow,
@@ -1220,6 +1256,7 @@ static int check_options(const wgw_options& o) {
 int wgw_set_options(wgw_ctx* c, const wgw_options* opt) {
   if (!c || !opt) return fail(WGW_ERR_ARG, "null argument");
   WGW_TRY(check_options(*opt));
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
   c->opt = *opt;
   return WGW_OK;
 }
@@ -1237,6 +1274,7 @@ static int setup_impl(wgw_ctx* c, const double* vloc_G, const double* psi_v, con
   c->grid3 = (long)N * N * N;
   WGW_TRY(upload_sphere(c->wfc));
   WGW_TRY(upload_sphere(c->rho));
+  WGW_CK(cudaGetDevice(&c->device));
   WGW_CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
   cudaStream_t st = c->stream;
   // Twiddles exp(+2 pi i k / N).
@@ -1374,12 +1412,16 @@ int wgw_get_gvectors(const wgw_ctx* c, int which, int32_t* miller) {
 int wgw_apply_chi0_dev(wgw_ctx* c, const double* dV_dev, int n_pert, const double* omega, int n_omega,
                        double* drho_dev, void* stream, wgw_stats* st) {
   g_last_error.clear();
+  if (!c) return fail(WGW_ERR_ARG, "null context");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
   return apply_core(c, dV_dev, n_pert, omega, n_omega, drho_dev, false, (cudaStream_t)stream, st);
 }
 
 int wgw_apply_chibar0_dev(wgw_ctx* c, const double* phi_dev, int n_pert, const double* omega,
                           int n_omega, double* out_dev, void* stream, wgw_stats* st) {
   g_last_error.clear();
+  if (!c) return fail(WGW_ERR_ARG, "null context");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
   return apply_core(c, phi_dev, n_pert, omega, n_omega, out_dev, true, (cudaStream_t)stream, st);
 }
 
@@ -1387,6 +1429,7 @@ static int apply_host(wgw_ctx* c, const double* dV, int n_pert, const double* om
                       double* drho, bool sym, wgw_stats* st) {
   g_last_error.clear();
   if (!c) return fail(WGW_ERR_ARG, "null context");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
   if (n_pert <= 0) return n_pert == 0 ? WGW_OK : fail(WGW_ERR_ARG, "n_pert < 0");
   if (n_omega < 1) return fail(WGW_ERR_ARG, "n_omega < 1");
   if (!dV || !drho) return fail(WGW_ERR_ARG, "null dV or drho");
@@ -1447,6 +1490,7 @@ int wgw_system_info(const wgw_ctx* c, int n, int* iters, double* rel_residual) {
 int wgw_pdep_davidson(wgw_ctx* c, int n_pdep, const double* x0, double* eig, double* basis, wgw_stats* st) {
   g_last_error.clear();
   if (!c || n_pdep < 1 || !eig) return fail(WGW_ERR_ARG, "need a context, n_pdep >= 1 and eig");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
   if (n_pdep > c->rho.nrb() / 2) return fail(WGW_ERR_ARG, "n_pdep too large for the density sphere");
   return davidson_impl(c, n_pdep, x0, eig, basis, st);
 }
@@ -1458,6 +1502,7 @@ int wgw_lanczos(wgw_ctx* c, const double* phi, int n_pdep, int n_steps, const do
     return fail(WGW_ERR_ARG, "need a context, phi, n_pdep >= 1, 1 <= n_steps <= 255, n_omega >= 0");
   for (int k = 0; k < n_omega; ++k)
     if (!(omega[k] >= 0.0)) return fail(WGW_ERR_ARG, "imaginary frequencies must be >= 0");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
   return lanczos_impl(c, phi, n_pdep, n_steps, omega, n_omega, alpha, beta, chi0_pdep, st);
 }
 
@@ -1473,6 +1518,152 @@ int wgw_symm_eig_dev(int n, double* A_dev, double* w_dev, double* Z_dev, void* s
   WGW_CK(cudaMemcpyAsync(&h, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   WGW_CK(cudaStreamSynchronize(st));
   return h == 0 ? WGW_OK : fail(WGW_ERR_NOCONV, "dense eigensolver did not converge");
+}
+
+
+// ---------------------------------------------------------------- serving: request queue
+// Requests are copied in by wgw_submit and executed by one worker thread per context on the
+// context's stream.  The worker merges every queued request with the same kind and frequency
+// set into one batched apply (as many as the free device memory admits), then scatters the
+// results back; requests to different contexts run on different streams and overlap on the GPU.
+static double batch_bytes(const wgw_ctx* c, int n_real) {
+  const double per_sys = 72.0 * c->ld_w + 12.0 * (2 * c->wfc.m + 1) * (double)c->N * c->N;
+  const double per_pert = 3.0 * 8.0 * c->grid3 + 64.0 * c->ld_r + 12.0 * (2 * c->rho.m + 1) * (double)c->N * c->N;
+  return n_real * (per_sys * c->n_v + per_pert);
+}
+
+static void serve_loop(wgw_ctx* c) {
+  cudaSetDevice(c->device);
+  for (;;) {
+    std::vector<wgw_ctx::Req> batch;
+    {
+      std::unique_lock<std::mutex> lk(c->qmu);
+      c->qcv.wait(lk, [&] { return c->stop || !c->queue.empty(); });
+      if (c->queue.empty()) return;
+      size_t free_b = 0, total_b = 0;
+      cudaMemGetInfo(&free_b, &total_b);
+      const double budget = 0.8 * (double)free_b;
+      const wgw_ctx::Req& head = c->queue.front();
+      const int kind = head.kind;
+      const std::vector<double> om = head.omega;
+      int n_tot = 0;
+      for (auto it = c->queue.begin(); it != c->queue.end();) {
+        const bool same = it->kind == kind && it->omega == om;
+        // Real perturbation count is at most 2 n_pert (non-Hermitian parts).
+        if (same && (batch.empty() || batch_bytes(c, 2 * (n_tot + it->n_pert)) <= budget)) {
+          n_tot += it->n_pert;
+          c->running.insert(it->ticket);
+          batch.push_back(std::move(*it));
+          it = c->queue.erase(it);
+        } else {
+          ++it;
+        }
+      }
+    }
+    const auto t_start = std::chrono::steady_clock::now();
+    const int n_rho = c->rho.n, n_om = (int)batch[0].omega.size();
+    int n_tot = 0;
+    for (auto& r : batch) n_tot += r.n_pert;
+    std::vector<double> dv((size_t)2 * n_rho * n_tot), out((size_t)2 * n_rho * n_tot * n_om);
+    int off = 0;
+    for (auto& r : batch) {
+      std::copy(r.dV.begin(), r.dV.end(), dv.begin() + (size_t)2 * n_rho * off);
+      off += r.n_pert;
+    }
+    wgw_stats stt{};
+    const int status = apply_host(c, dv.data(), n_tot, batch[0].omega.data(), n_om, out.data(),
+                                  batch[0].kind == WGW_REQ_CHIBAR0, &stt);
+    off = 0;
+    for (auto& r : batch) {
+      if (status == WGW_OK || status == WGW_ERR_NOCONV)
+        for (int k = 0; k < n_om; ++k)
+          std::copy(out.begin() + (size_t)2 * n_rho * ((size_t)k * n_tot + off),
+                    out.begin() + (size_t)2 * n_rho * ((size_t)k * n_tot + off + r.n_pert),
+                    r.out + (size_t)2 * n_rho * ((size_t)k * r.n_pert));
+      off += r.n_pert;
+    }
+    const auto t_end = std::chrono::steady_clock::now();
+    {
+      std::lock_guard<std::mutex> lk(c->qmu);
+      for (auto& r : batch) {
+        wgw_ctx::Done d;
+        d.status = status;
+        d.latency_s = std::chrono::duration<double>(t_end - r.t_submit).count();
+        d.queue_s = std::chrono::duration<double>(t_start - r.t_submit).count();
+        d.batch_requests = (int)batch.size();
+        d.batch_systems = stt.n_systems;
+        c->done[r.ticket] = d;
+        c->running.erase(r.ticket);
+      }
+    }
+    c->qcv.notify_all();
+  }
+}
+
+int wgw_submit(wgw_ctx* c, const wgw_request* req, uint64_t* ticket) {
+  g_last_error.clear();
+  if (!c || !req || !ticket) return fail(WGW_ERR_ARG, "null argument");
+  if (req->kind != WGW_REQ_CHI0 && req->kind != WGW_REQ_CHIBAR0) return fail(WGW_ERR_ARG, "unknown request kind");
+  if (req->n_pert < 1 || !req->dV || !req->out || req->n_omega < 1 || !req->omega)
+    return fail(WGW_ERR_ARG, "need n_pert >= 1, dV, out and n_omega >= 1 frequencies");
+  for (int k = 0; k < req->n_omega; ++k)
+    if (!(req->omega[k] >= 0.0)) return fail(WGW_ERR_ARG, "imaginary frequencies must be >= 0");
+  wgw_ctx::Req r;
+  r.kind = req->kind;
+  r.n_pert = req->n_pert;
+  r.dV.assign(req->dV, req->dV + (size_t)2 * c->rho.n * req->n_pert);
+  r.omega.assign(req->omega, req->omega + req->n_omega);
+  r.out = req->out;
+  r.t_submit = std::chrono::steady_clock::now();
+  {
+    std::lock_guard<std::mutex> lk(c->qmu);
+    if (c->stop) return fail(WGW_ERR_STATE, "context is shutting down");
+    r.ticket = c->next_ticket++;
+    *ticket = r.ticket;
+    c->queue.push_back(std::move(r));
+    if (!c->worker.joinable()) c->worker = std::thread(serve_loop, c);
+  }
+  c->qcv.notify_all();
+  return WGW_OK;
+}
+
+static void fill_result(const wgw_ctx::Done& d, wgw_result* res) {
+  if (!res) return;
+  res->status = d.status;
+  res->latency_s = d.latency_s;
+  res->queue_s = d.queue_s;
+  res->batch_requests = d.batch_requests;
+  res->batch_systems = d.batch_systems;
+}
+
+int wgw_poll(wgw_ctx* c, uint64_t ticket, int* done, wgw_result* res) {
+  g_last_error.clear();
+  if (!c || !done) return fail(WGW_ERR_ARG, "null argument");
+  std::lock_guard<std::mutex> lk(c->qmu);
+  auto it = c->done.find(ticket);
+  if (it != c->done.end()) {
+    *done = 1;
+    fill_result(it->second, res);
+    c->done.erase(it);
+    return WGW_OK;
+  }
+  if (c->running.count(ticket)) { *done = 0; return WGW_OK; }
+  for (const auto& r : c->queue)
+    if (r.ticket == ticket) { *done = 0; return WGW_OK; }
+  return fail(WGW_ERR_ARG, "unknown or already released ticket");
+}
+
+int wgw_wait(wgw_ctx* c, uint64_t ticket, wgw_result* res) {
+  g_last_error.clear();
+  if (!c) return fail(WGW_ERR_ARG, "null argument");
+  std::unique_lock<std::mutex> lk(c->qmu);
+  bool known = c->done.count(ticket) || c->running.count(ticket);
+  for (const auto& r : c->queue) known = known || r.ticket == ticket;
+  if (!known) return fail(WGW_ERR_ARG, "unknown or already released ticket");
+  c->qcv.wait(lk, [&] { return c->done.count(ticket) > 0; });
+  fill_result(c->done[ticket], res);
+  c->done.erase(ticket);
+  return WGW_OK;
 }
 
 void wgw_destroy(wgw_ctx* c) { delete c; }

@@ -18,6 +18,7 @@ WGW_OK, WGW_ERR_ARG, WGW_ERR_NOMEM, WGW_ERR_NOCONV = 0, 1, 2, 3
 WGW_ERR_CUDA, WGW_ERR_TIMEOUT, WGW_ERR_STATE = 4, 5, 6
 WGW_FP64, WGW_MIXED = 0, 1
 WGW_SPHERE_WFC, WGW_SPHERE_RHO = 0, 1
+WGW_REQ_CHI0, WGW_REQ_CHIBAR0 = 0, 1
 
 _dp = ctypes.POINTER(ctypes.c_double)
 
@@ -40,6 +41,19 @@ class Stats(ctypes.Structure):
     _fields_ = [("n_systems", ctypes.c_int), ("n_converged", ctypes.c_int),
                 ("max_iters", ctypes.c_int), ("refinements", ctypes.c_int),
                 ("max_rel_residual", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("dV", _dp), ("n_pert", ctypes.c_int), ("omega", _dp),
+                ("n_omega", ctypes.c_int), ("out", _dp)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("latency_s", ctypes.c_double), ("queue_s", ctypes.c_double),
+                ("batch_requests", ctypes.c_int), ("batch_systems", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -82,6 +96,9 @@ def lib(path: str | None = None):
     L.wgw_lanczos.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp,
                               ctypes.POINTER(Stats)]
     L.wgw_system_info.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp]
+    L.wgw_submit.argtypes = [ctypes.c_void_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+    L.wgw_poll.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Result)]
+    L.wgw_wait.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(Result)]
     L.wgw_destroy.argtypes = [ctypes.c_void_p]
     L.wgw_status_string.restype = ctypes.c_char_p
     L.wgw_status_string.argtypes = [ctypes.c_int]
@@ -187,6 +204,42 @@ def wgw_apply_chi0(ctx: Context, dV, omega=(0.0,), allow_noconv=False, out=None)
 def wgw_apply_chibar0(ctx: Context, phi, omega=(0.0,), allow_noconv=False, out=None):
     """Host arrays: chibar0 phi = v^1/2 chi0 v^1/2 phi; layout as wgw_apply_chi0."""
     return _host_call(lib().wgw_apply_chibar0, "wgw_apply_chibar0", ctx, phi, omega, allow_noconv, out)
+
+
+class Ticket:
+    """A submitted request; holds the output buffer until the library reports it done."""
+
+    def __init__(self, ctx, ticket, out):
+        self.ctx, self.ticket, self.out = ctx, ticket, out
+
+
+def wgw_submit(ctx: Context, dV, omega=(0.0,), kind: int = WGW_REQ_CHI0) -> Ticket:
+    """Queues chi0 (or chibar0) dV on the context's worker; returns at once."""
+    dV = np.asarray(dV, np.complex128)
+    dV = dV[:, None] if dV.ndim == 1 else dV
+    n_pert = dV.shape[1]
+    om = np.ascontiguousarray(omega, np.float64)
+    buf = _interleave(dV)
+    out = np.zeros((len(om), n_pert, ctx.n_rho), np.complex128)
+    req = Request(kind, buf.ctypes.data_as(_dp), n_pert, om.ctypes.data_as(_dp), len(om),
+                  out.view(np.float64).ctypes.data_as(_dp))
+    t = ctypes.c_uint64()
+    _check(lib().wgw_submit(ctx.handle, ctypes.byref(req), ctypes.byref(t)), "wgw_submit")
+    return Ticket(ctx, t.value, out)
+
+
+def wgw_poll(t: Ticket):
+    """(done, result dict or None); a finished ticket is released by the call that reports it."""
+    done, res = ctypes.c_int(), Result()
+    _check(lib().wgw_poll(t.ctx.handle, t.ticket, ctypes.byref(done), ctypes.byref(res)), "wgw_poll")
+    return bool(done.value), (res.as_dict() if done.value else None)
+
+
+def wgw_wait(t: Ticket):
+    """Blocks until done -> (result (N_rho, n_pert, n_omega), result dict)."""
+    res = Result()
+    _check(lib().wgw_wait(t.ctx.handle, t.ticket, ctypes.byref(res)), "wgw_wait")
+    return t.out.transpose(2, 1, 0), res.as_dict()
 
 
 def wgw_profile_enable(ctx: Context, on: bool = True):

@@ -1,0 +1,108 @@
+"""Serving entry points (wgw_submit / wgw_poll / wgw_wait) on a GB300.
+
+Requests queued on one context are merged into batched applies; each request's
+result must equal the oracle's within the path's tolerance (FP64 1e-10) and
+its own synchronous wgw_apply_chi0 result, whatever it was batched with.
+"""
+import threading
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import chi0
+from oracle.model import Model
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def W():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_05623_gb300 import build
+    build.build()
+    import paper_2203_05623_gb300 as W
+    return W
+
+
+def model_of(s):
+    return Model(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, s.beta_G, s.d_proj)
+
+
+def rel_err(got, ref):
+    num = np.linalg.norm(got - ref, axis=0)
+    den = np.linalg.norm(ref, axis=0)
+    return float(np.max(num / np.where(den > 0, den, 1.0)))
+
+
+def ctx_of(W, s):
+    return W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v,
+                       W.wgw_default_options(precision=W.WGW_FP64, cg_tol=1e-13))
+
+
+def test_queued_requests_match_oracle_and_sync(W, cfg24):
+    s = cfg24
+    ctx = ctx_of(W, s)
+    m = model_of(s)
+    # Ten requests of 1..4 perturbations: two frequency sets, so the worker forms separate batches.
+    reqs = []
+    for k in range(10):
+        dV = synth.perturbations(s.miller_rho, s.L, 1 + k % 4, 100 + k)
+        om = [0.0] if k % 3 else [0.0, 0.4]
+        reqs.append((dV, om))
+    tickets = [None] * len(reqs)
+
+    def submit(i):
+        tickets[i] = W.wgw_submit(ctx, *reqs[i])
+
+    th = [threading.Thread(target=submit, args=(i,)) for i in range(len(reqs))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    merged = 0
+    for (dV, om), t in zip(reqs, tickets):
+        got, res = W.wgw_wait(t)
+        assert res["status"] == W.WGW_OK
+        assert res["latency_s"] >= res["queue_s"] >= 0
+        merged = max(merged, res["batch_requests"])
+        ref = chi0.sos_drho(m, dV, om)
+        assert rel_err(got, ref) < 1e-10
+        alone, _, _ = W.wgw_apply_chi0(ctx, dV, om)
+        assert rel_err(got, alone) < 1e-10
+    assert merged >= 1
+
+
+def test_two_contexts_overlap_and_poll(W, cfg24, tiny):
+    c1, c2 = ctx_of(W, cfg24), ctx_of(W, tiny)
+    d1 = synth.perturbations(cfg24.miller_rho, cfg24.L, 3, 7)
+    d2 = synth.perturbations(tiny.miller_rho, tiny.L, 2, 8)
+    t1 = W.wgw_submit(c1, d1, [0.0, 0.3])
+    t2 = W.wgw_submit(c2, d2, [0.0], kind=W.WGW_REQ_CHIBAR0)
+    import time
+    done2 = False
+    for _ in range(6000):
+        done2, res2 = W.wgw_poll(t2)
+        if done2:
+            break
+        time.sleep(0.005)
+    assert done2 and res2["status"] == W.WGW_OK
+    got1, res1 = W.wgw_wait(t1)
+    assert res1["status"] == W.WGW_OK
+    assert rel_err(got1, chi0.sos_drho(model_of(cfg24), d1, [0.0, 0.3])) < 1e-10
+    ref2, _, _ = W.wgw_apply_chibar0(c2, d2, [0.0])
+    assert rel_err(t2.out.transpose(2, 1, 0), ref2) < 1e-10
+    # A released ticket is unknown afterwards.
+    with pytest.raises(W.WgwError):
+        W.wgw_poll(t2)
+
+
+def test_submit_rejects_bad_requests(W, tiny):
+    ctx = ctx_of(W, tiny)
+    d = synth.perturbations(tiny.miller_rho, tiny.L, 1, 3)
+    with pytest.raises(W.WgwError):
+        W.wgw_submit(ctx, d, [-0.1])
+    with pytest.raises(W.WgwError):
+        W.wgw_submit(ctx, d, [0.0], kind=7)
