@@ -156,8 +156,15 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="pdep_L16_48", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-pert", type=int, default=0,
+                    help="perturbations per rank (default: the workload's); smaller values serve profiling")
+    ap.add_argument("--fp64-emulation", type=int, default=1, choices=[0, 1],
+                    help="1: FP64-accuracy FFT passes in float-float (default); 0: native FP64")
     args = ap.parse_args()
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.n_pert > 0:
+        wl["n_pert"] = args.n_pert
+        wl["desc"] += f" (reduced to {args.n_pert} perturbations)"
     if args.impl == "reference":
         return run_reference(args, wl)
 
@@ -186,7 +193,8 @@ def main():
     from paper_2203_05623_gb300.shard import owned_perturbations
     phi_all = synth.perturbations(s.miller_rho, s.L, wl["n_pert"] * world, wl["pert_seed"])
     phi = phi_all[:, owned_perturbations(wl["n_pert"] * world, rank, world, wl["n_pert"])]
-    opt = W.wgw_default_options(precision=W.WGW_MIXED, cg_tol=wl["cg_tol"], max_cg_iter=200)
+    opt = W.wgw_default_options(precision=W.WGW_MIXED, cg_tol=wl["cg_tol"], max_cg_iter=200,
+                                fp64_emulation=args.fp64_emulation)
     ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, opt)
     stream = torch.cuda.current_stream()
     x = torch.from_numpy(np.ascontiguousarray(phi.T)).cuda()
@@ -260,6 +268,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
         "config": {"workload": args.workload, "desc": wl["desc"], "cg_tol": wl["cg_tol"],
+                   "fp64_passes": "float-float" if args.fp64_emulation else "native FP64",
                    "l2": "256 MB buffer written between steps, outside the timed interval",
                    "parallelism": f"perturbation shards x{world}" if world > 1 else "1 GPU"},
         "latency_ms": {"p50": 1e3 * statistics.median(times),

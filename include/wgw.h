@@ -73,6 +73,10 @@ typedef struct wgw_options {
   int dav_max_iter;    /* Davidson iterations */
   int dav_factor;      /* Davidson subspace limit = dav_factor * n_pdep (Sec. 4.2: 4) */
   int seed;            /* start block seed when none is given */
+  int fp64_emulation;  /* MIXED: 1 = the FP64-accuracy FFT passes (right-hand sides, refinement
+                          residuals, drho) compute in float-float (two FP32 values per number, about
+                          48 significant bits) because GB300's FP64 rate is 1/64 of its FP32 rate;
+                          0 = native FP64.  Storage stays FP64 either way. */
 } wgw_options;
 
 typedef struct wgw_stats {
@@ -84,7 +88,8 @@ typedef struct wgw_stats {
 } wgw_stats;
 
 /* Fills *opt with defaults: WGW_FP64, cg_tol 1e-12, max_cg_iter 2000, max_refine 8,
- * inner_tol 1e-5, f_s 2, check_every 8, dav_tol 1e-8, dav_max_iter 100, dav_factor 4, seed 12345. */
+ * inner_tol 1e-5, f_s 2, check_every 8, dav_tol 1e-8, dav_max_iter 100, dav_factor 4, seed 12345,
+ * fp64_emulation 1. */
 int wgw_default_options(wgw_options* opt);
 
 /*

@@ -9,6 +9,7 @@
 
 #include <cstdint>
 #include <cstddef>
+#include <cmath>
 
 #include <cuda_runtime.h>
 
@@ -25,6 +26,64 @@
 #endif
 
 namespace wgw {
+
+// ---------------------------------------------------------------- float-float arithmetic
+// A value held as the unevaluated sum hi + lo of two floats with |lo| <= ulp(hi): about 48
+// significant bits computed on the FP32 pipes only.  On GB300 the FP64 rate is 1/64 of the
+// FP32 rate, so FFT passes that need more than FP32 accuracy run in this format instead of
+// FP64.  The operations are the error-free transformations TwoSum (Knuth), Fast2Sum (Dekker)
+// and the FMA TwoProduct, combined as in the double-double literature (Dekker 1971; Hida, Li
+// and Bailey 2001); additions use the "sloppy" form, whose error is bounded by about 2^-47
+// (|a| + |b|), enough for norm-wise stable sums such as FFT butterflies.
+// Every primitive below must be evaluated exactly as written: on the device through the
+// round-to-nearest intrinsics (never contracted into FMAs), on the host through volatile
+// temporaries.
+#if defined(__CUDA_ARCH__)
+WGW_HD float ffa(float a, float b) { return __fadd_rn(a, b); }
+WGW_HD float ffs(float a, float b) { return __fsub_rn(a, b); }
+WGW_HD float ffm(float a, float b) { return __fmul_rn(a, b); }
+WGW_HD float fff(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+#else
+inline float ffa(float a, float b) { volatile float r = a + b; return r; }
+inline float ffs(float a, float b) { volatile float r = a - b; return r; }
+inline float ffm(float a, float b) { volatile float r = a * b; return r; }
+inline float fff(float a, float b, float c) { return std::fmaf(a, b, c); }
+#endif
+
+struct alignas(8) ff {
+  float hi, lo;
+  ff() = default;
+  WGW_HD constexpr ff(float h, float l) : hi(h), lo(l) {}
+  // Nearest float to d, and the nearest float to the remainder.
+  WGW_HD constexpr explicit ff(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+  WGW_HD constexpr explicit ff(int i) : hi((float)i), lo((float)((double)i - (double)(float)i)) {}
+  WGW_HD explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+// s + e = a + b exactly (any a, b).
+WGW_HD ff two_sum(float a, float b) {
+  const float s = ffa(a, b), bb = ffs(s, a);
+  return ff(s, ffa(ffs(a, ffs(s, bb)), ffs(b, bb)));
+}
+// s + e = a + b exactly when the exponent of a is not below that of b.
+WGW_HD ff fast_two_sum(float a, float b) {
+  const float s = ffa(a, b);
+  return ff(s, ffs(b, ffs(s, a)));
+}
+WGW_HD ff operator+(ff a, ff b) {
+  const ff s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, ffa(s.lo, ffa(a.lo, b.lo)));
+}
+WGW_HD ff operator-(ff a) { return ff(-a.hi, -a.lo); }
+WGW_HD ff operator-(ff a, ff b) { return a + (-b); }
+WGW_HD ff operator*(ff a, ff b) {
+  const float p = ffm(a.hi, b.hi);
+  float e = fff(a.hi, b.hi, -p);            // exact low part of a.hi * b.hi
+  e = fff(a.hi, b.lo, fff(a.lo, b.hi, e));
+  return fast_two_sum(p, e);
+}
+WGW_HD ff& operator+=(ff& a, ff b) { a = a + b; return a; }
+WGW_HD ff& operator*=(ff& a, ff b) { a = a * b; return a; }
 
 constexpr double kInvSqrt2 = 0.70710678118654752440;
 constexpr double kSqrt2 = 1.41421356237309504880;

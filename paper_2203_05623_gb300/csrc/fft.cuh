@@ -65,10 +65,10 @@ WGW_HD void dft8(cplx<T>* v, int sign) {
   cplx<T> a[4], b[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) { a[j] = v[j] + v[j + 4]; b[j] = v[j] - v[j + 4]; }
-  // b_j *= exp(sign i pi j / 4)
-  b[1] = cscale(mk<T>(b[1].re - sign * b[1].im, b[1].im + sign * b[1].re), r);
+  // b_j *= exp(sign i pi j / 4):  exp(sign i pi / 4) = (1 + sign i) r,  exp(sign 3 i pi / 4) = (-1 + sign i) r
+  b[1] = cscale(b[1] + mul_i(b[1], sign), r);
   b[2] = mul_i(b[2], sign);
-  b[3] = cscale(mk<T>(-b[3].re - sign * b[3].im, -b[3].im + sign * b[3].re), r);
+  b[3] = cscale(mul_i(b[3], sign) - b[3], r);
   dft4(a, sign);
   dft4(b, sign);
 #pragma unroll

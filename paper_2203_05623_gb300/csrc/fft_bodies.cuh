@@ -15,6 +15,12 @@
 // T[h + m][y][z] (2m+1 planes of N x N complex, y and z in digit-reversed
 // position).  Real-space arrays are [y][z][x] with all three coordinates in
 // digit-reversed position.
+//
+// Every body has a storage type T (of the sphere vectors and real-space arrays
+// in global memory) and a compute type C (of the butterflies, the twiddles,
+// shared memory and the pair intermediate T[h][y][z]); C = T except for the
+// float-float instances (T = double, C = ff).  Values cross between the two
+// only where global T arrays are read or written.
 #pragma once
 
 #include "common.cuh"
@@ -42,37 +48,37 @@ WGW_HD void pair_members(const int* list, int n_list, int q, int& s0, int& s1) {
 
 // G -> r along z then y for plane hi of one pair; writes T[hi] of that pair.
 // smem: N * (N + 1) complex.
-template <typename T, int NC = 0>
+template <typename T, int NC = 0, typename C = T>
 WGW_HD void plane_g2r_body(int pair, int hi, const SphereTab& sp, const FftPlan& pl,
-                           const cplx<T>* tw, const T* X, long ldx, int n_list, const int* list,
-                           cplx<T>* Tout, cplx<T>* B, Thr th) {
+                           const cplx<C>* tw, const T* X, long ldx, int n_list, const int* list,
+                           cplx<C>* Tout, cplx<C>* B, Thr th) {
   const int N = NC > 0 ? NC : pl.n, LS = N + 1, m = sp.m;
   int s0, s1;
   pair_members(list, n_list, pair, s0, s1);
   const bool has1 = s1 >= 0;
-  for (int i = th.tid; i < N * LS; i += th.nth) B[i] = mk<T>(0, 0);
+  for (int i = th.tid; i < N * LS; i += th.nth) B[i] = mk<C>(C(0), C(0));
   WGW_SYNC();
   const T* x0 = X + (size_t)s0 * ldx;
   const T* x1 = X + (size_t)(has1 ? s1 : s0) * ldx;
-  const T s = T(kInvSqrt2);
+  const C s = C(kInvSqrt2);
   for (int e = sp.plane_off[hi] + th.tid; e < sp.plane_off[hi + 1]; e += th.nth) {
     const int2 en = sp.ent[e];
     const int kk = en.x & 0xff, ll = (en.x >> 8) & 0xff, neg = (en.x >> 16) & 1;
     const int j = en.y;
-    cplx<T> z;
+    cplx<C> z;
     if (j == 0) {
-      z = mk<T>(x0[0], has1 ? x1[0] : T(0));
+      z = mk<C>(C(x0[0]), has1 ? C(x1[0]) : C(0));
     } else {
-      const T ar = x0[2 * j - 1], ai = x0[2 * j];
-      const T br = has1 ? x1[2 * j - 1] : T(0), bi = has1 ? x1[2 * j] : T(0);
-      z = neg ? mk<T>((ar + bi) * s, (br - ai) * s) : mk<T>((ar - bi) * s, (ai + br) * s);
+      const C ar = C(x0[2 * j - 1]), ai = C(x0[2 * j]);
+      const C br = has1 ? C(x1[2 * j - 1]) : C(0), bi = has1 ? C(x1[2 * j]) : C(0);
+      z = neg ? mk<C>((ar + bi) * s, (br - ai) * s) : mk<C>((ar - bi) * s, (ai + br) * s);
     }
     B[kk * LS + ll] = z;
   }
   WGW_SYNC();
-  fft_dif_n<T, NC>(B, pl, tw, +1, 2 * m + 1, LS, 1, m, th);   // rows |k| <= m, along l -> z
-  fft_dif_n<T, NC>(B, pl, tw, +1, N, 1, LS, -1, th);          // columns z, along k -> y
-  cplx<T>* out = Tout + ((size_t)pair * (2 * m + 1) + hi) * N * N;
+  fft_dif_n<C, NC>(B, pl, tw, +1, 2 * m + 1, LS, 1, m, th);   // rows |k| <= m, along l -> z
+  fft_dif_n<C, NC>(B, pl, tw, +1, N, 1, LS, -1, th);          // columns z, along k -> y
+  cplx<C>* out = Tout + ((size_t)pair * (2 * m + 1) + hi) * N * N;
   for (int i = th.tid; i < N * N; i += th.nth) {
     const int y = i / N, z = i % N;
     out[i] = B[y * LS + z];
@@ -101,14 +107,14 @@ struct XArgs {
 };
 
 // One (pair, y) slab: S[z][x], N x (N + 1) complex.
-template <typename T, int NC = 0>
-WGW_HD void xline_body(int pair, int y, int m, const FftPlan& pl, const cplx<T>* tw,
-                       cplx<T>* Tbuf, const XArgs<T>& a, cplx<T>* S, Thr th) {
+template <typename T, int NC = 0, typename C = T>
+WGW_HD void xline_body(int pair, int y, int m, const FftPlan& pl, const cplx<C>* tw,
+                       cplx<C>* Tbuf, const XArgs<T>& a, cplx<C>* S, Thr th) {
   const int N = NC > 0 ? NC : pl.n, LS = N + 1, NP = 2 * m + 1;
   int s0, s1;
   pair_members(a.list, a.n_sys, pair, s0, s1);
   const bool has1 = s1 >= 0;
-  cplx<T>* tp = Tbuf + (size_t)pair * NP * N * N + (size_t)y * N;   // T[hi][y][z] at tp[hi*N*N + z]
+  cplx<C>* tp = Tbuf + (size_t)pair * NP * N * N + (size_t)y * N;   // T[hi][y][z] at tp[hi*N*N + z]
   const size_t slab = (size_t)y * N * N;                              // real-space [y][z][x] offset
   if (a.mode == XM_FROM_REAL) {
     const T* A0 = a.A + (size_t)(a.a_index ? a.a_index[s0] : s0) * a.lda + slab;
@@ -117,14 +123,14 @@ WGW_HD void xline_body(int pair, int y, int m, const FftPlan& pl, const cplx<T>*
     const T* B1 = (a.Bm && has1) ? a.Bm + (size_t)(a.b_index ? a.b_index[s1] : s1) * a.ldb + slab : nullptr;
     for (int i = th.tid; i < N * N; i += th.nth) {
       const int z = i / N, x = i % N;
-      T re = A0[i], im = A1 ? A1[i] : T(0);
-      if (B0) re *= B0[i];
-      if (B1) im *= B1[i];
-      S[z * LS + x] = mk<T>(re, im);
+      C re = C(A0[i]), im = A1 ? C(A1[i]) : C(0);
+      if (B0) re = re * C(B0[i]);
+      if (B1) im = im * C(B1[i]);
+      S[z * LS + x] = mk<C>(re, im);
     }
     WGW_SYNC();
   } else {
-    for (int i = th.tid; i < N * LS; i += th.nth) S[i] = mk<T>(0, 0);
+    for (int i = th.tid; i < N * LS; i += th.nth) S[i] = mk<C>(C(0), C(0));
     WGW_SYNC();
     for (int i = th.tid; i < NP * N; i += th.nth) {
       const int hi = i / N, z = i % N;
@@ -132,16 +138,16 @@ WGW_HD void xline_body(int pair, int y, int m, const FftPlan& pl, const cplx<T>*
       S[z * LS + x] = tp[(size_t)hi * N * N + z];
     }
     WGW_SYNC();
-    fft_dif_n<T, NC>(S, pl, tw, +1, N, LS, 1, -1, th);
+    fft_dif_n<C, NC>(S, pl, tw, +1, N, LS, 1, -1, th);
   }
   if (a.mode == XM_TO_REAL) {
     T* r0 = a.R0 + (size_t)s0 * a.ldr + slab;
     T* r1 = (has1 && a.R1) ? a.R1 + (size_t)s1 * a.ldr + slab : nullptr;
     for (int i = th.tid; i < N * N; i += th.nth) {
       const int z = i / N, x = i % N;
-      const cplx<T> v = S[z * LS + x];
-      r0[i] = v.re;
-      if (r1) r1[i] = v.im;
+      const cplx<C> v = S[z * LS + x];
+      r0[i] = T(v.re);
+      if (r1) r1[i] = T(v.im);
     }
     return;
   }
@@ -149,11 +155,11 @@ WGW_HD void xline_body(int pair, int y, int m, const FftPlan& pl, const cplx<T>*
     const T* v = a.V + slab;
     for (int i = th.tid; i < N * N; i += th.nth) {
       const int z = i / N, x = i % N;
-      S[z * LS + x] = cscale(S[z * LS + x], v[i]);
+      S[z * LS + x] = cscale(S[z * LS + x], C(v[i]));
     }
     WGW_SYNC();
   }
-  fft_dit_n<T, NC>(S, pl, tw, -1, N, LS, 1, -1, th);
+  fft_dit_n<C, NC>(S, pl, tw, -1, N, LS, 1, -1, th);
   for (int i = th.tid; i < NP * N; i += th.nth) {
     const int hi = i / N, z = i % N;
     const int x = (hi - m + N) % N;
@@ -176,24 +182,24 @@ struct Epi {
   const int* list;         // system list (null = identity)
 };
 
-template <typename T>
-WGW_HD void epi_store(const Epi<T>& e, const SphereTab& sp, int s, int i, T f) {
-  T v = e.vcoef * f;
+template <typename T, typename C>
+WGW_HD void epi_store(const Epi<T>& e, const SphereTab& sp, int s, int i, C f) {
+  C v = C(e.vcoef) * f;
   if (e.pin) {
-    T c = e.kin * T(sp.g2[i]);
-    if (e.shift) c += e.shift[s];
-    v += c * e.pin[(size_t)s * e.ldp + i];
+    C c = C(e.kin) * C(sp.g2[i]);
+    if (e.shift) c += C(e.shift[s]);
+    v += c * C(e.pin[(size_t)s * e.ldp + i]);
   }
-  e.out[(size_t)s * e.ldo + i] = v;
+  e.out[(size_t)s * e.ldo + i] = T(v);
 }
 
 // Unpack one pair of values Z(G_j), Z(-G_j) into the two systems' real-basis elements.
-template <typename T>
+template <typename T, typename C>
 WGW_HD void unpack_store(const Epi<T>& ep, const SphereTab& sp, int s0, int s1, bool act0, bool act1,
-                         int j, cplx<T> zp, cplx<T> zm, T scale) {
-  const T a = zp.re, b = zp.im, c = zm.re, d = zm.im;
+                         int j, cplx<C> zp, cplx<C> zm, C scale) {
+  const C a = zp.re, b = zp.im, c = zm.re, d = zm.im;
   // A(G_j) = ((a + c) + i (b - d)) / 2,  B(G_j) = ((b + d) - i (a - c)) / 2
-  const T hs = T(0.5) * scale * T(kSqrt2);
+  const C hs = C(0.5) * scale * C(kSqrt2);
   if (act0) {
     epi_store(ep, sp, s0, 2 * j - 1, (a + c) * hs);
     epi_store(ep, sp, s0, 2 * j, (b - d) * hs);
@@ -205,37 +211,37 @@ WGW_HD void unpack_store(const Epi<T>& ep, const SphereTab& sp, int s0, int s1, 
 }
 
 // r -> G along y then z for plane hi of one pair (in B), natural k, l afterwards.
-template <typename T, int NC = 0>
+template <typename C, int NC = 0>
 WGW_HD void plane_r2g_load(int pair, int hi, const SphereTab& sp, const FftPlan& pl,
-                           const cplx<T>* tw, const cplx<T>* Tin, cplx<T>* B, Thr th) {
+                           const cplx<C>* tw, const cplx<C>* Tin, cplx<C>* B, Thr th) {
   const int N = NC > 0 ? NC : pl.n, LS = N + 1, m = sp.m, NP = 2 * m + 1;
-  const cplx<T>* in = Tin + ((size_t)pair * NP + hi) * N * N;
+  const cplx<C>* in = Tin + ((size_t)pair * NP + hi) * N * N;
   for (int i = th.tid; i < N * N; i += th.nth) {
     const int y = i / N, z = i % N;
     B[y * LS + z] = in[i];
   }
   WGW_SYNC();
-  fft_dit_n<T, NC>(B, pl, tw, -1, N, 1, LS, -1, th);          // columns z: y -> k (natural)
-  fft_dit_n<T, NC>(B, pl, tw, -1, 2 * m + 1, LS, 1, m, th);   // rows |k| <= m: z -> l (natural)
+  fft_dit_n<C, NC>(B, pl, tw, -1, N, 1, LS, -1, th);          // columns z: y -> k (natural)
+  fft_dit_n<C, NC>(B, pl, tw, -1, 2 * m + 1, LS, 1, m, th);   // rows |k| <= m: z -> l (natural)
 }
 
 WGW_HD int ent_pos(int2 en, int LS) { return (en.x & 0xff) * LS + ((en.x >> 8) & 0xff); }
 
 // r -> G for planes +hp and -hp of one pair, gather the sphere, unpack, epilogue.
 // smem: N * (N + 1) complex for the plane + npt_max complex (values of plane +hp).
-template <typename T, int NC = 0>
+template <typename T, int NC = 0, typename C = T>
 WGW_HD void plane_r2g_body(int pair, int hp, const SphereTab& sp, const FftPlan& pl,
-                           const cplx<T>* tw, const cplx<T>* Tin, const Epi<T>& ep,
-                           cplx<T>* B, cplx<T>* Zp, Thr th) {
+                           const cplx<C>* tw, const cplx<C>* Tin, const Epi<T>& ep,
+                           cplx<C>* B, cplx<C>* Zp, Thr th) {
   const int N = NC > 0 ? NC : pl.n, LS = N + 1, m = sp.m;
   int s0, s1;
   pair_members(ep.list, ep.n_sys, pair, s0, s1);
   const bool has1 = s1 >= 0;
   const bool act0 = is_active(ep.active, s0), act1 = has1 && is_active(ep.active, s1);
-  const T scale = T(1.0) / (T(N) * T(N) * T(N));
+  const C scale = C(1.0 / ((double)N * N * N));
   const int off_p = sp.plane_off[m + hp];
   const int cnt = sp.plane_off[m + hp + 1] - off_p;
-  plane_r2g_load<T, NC>(pair, m + hp, sp, pl, tw, Tin, B, th);
+  plane_r2g_load<C, NC>(pair, m + hp, sp, pl, tw, Tin, B, th);
   if (hp == 0) {
     // Plane 0 lists [G = 0, K positives, K mirrors].
     const int K = (cnt - 1) / 2;
@@ -245,7 +251,7 @@ WGW_HD void plane_r2g_body(int pair, int hp, const SphereTab& sp, const FftPlan&
                    B[ent_pos(sp.ent[off_p + 1 + K + t], LS)], scale);
     }
     if (th.tid == 0) {
-      const cplx<T> z0 = B[ent_pos(sp.ent[off_p], LS)];
+      const cplx<C> z0 = B[ent_pos(sp.ent[off_p], LS)];
       if (act0) epi_store(ep, sp, s0, 0, z0.re * scale);
       if (act1) epi_store(ep, sp, s1, 0, z0.im * scale);
     }
@@ -254,7 +260,7 @@ WGW_HD void plane_r2g_body(int pair, int hp, const SphereTab& sp, const FftPlan&
   for (int t = th.tid; t < cnt; t += th.nth) Zp[t] = B[ent_pos(sp.ent[off_p + t], LS)];
   WGW_SYNC();
   const int off_m = sp.plane_off[m - hp];
-  plane_r2g_load<T, NC>(pair, m - hp, sp, pl, tw, Tin, B, th);
+  plane_r2g_load<C, NC>(pair, m - hp, sp, pl, tw, Tin, B, th);
   for (int t = th.tid; t < cnt; t += th.nth) {
     unpack_store(ep, sp, s0, s1, act0, act1, sp.ent[off_p + t].y, Zp[t],
                  B[ent_pos(sp.ent[off_m + t], LS)], scale);
@@ -268,40 +274,40 @@ WGW_HD void plane_r2g_body(int pair, int hp, const SphereTab& sp, const FftPlan&
 // G -> r pass along x.  The sum runs over v in a fixed order, so the result
 // does not depend on how many perturbations share the launch.
 // smem: N * (N + 1) complex + N * N real.
-template <typename T, int NC = 0>
-WGW_HD void drho_xline_body(int p, int y, int m, const FftPlan& pl, const cplx<T>* tw,
-                            const cplx<T>* Tbuf, const T* psi_r, long ldpsi, int n_v, int n_sys,
-                            T coef, T* D, long ldd, cplx<T>* S, T* acc, Thr th) {
+template <typename T, int NC = 0, typename C = T>
+WGW_HD void drho_xline_body(int p, int y, int m, const FftPlan& pl, const cplx<C>* tw,
+                            const cplx<C>* Tbuf, const T* psi_r, long ldpsi, int n_v, int n_sys,
+                            T coef, T* D, long ldd, cplx<C>* S, C* acc, Thr th) {
   const int N = NC > 0 ? NC : pl.n, LS = N + 1, NP = 2 * m + 1;
   const size_t slab = (size_t)y * N * N;
-  for (int i = th.tid; i < N * N; i += th.nth) acc[i] = T(0);
+  for (int i = th.tid; i < N * N; i += th.nth) acc[i] = C(0);
   const int s_lo = p * n_v, s_hi = (p + 1) * n_v;   // systems of p: [s_lo, s_hi)
   for (int q = s_lo / 2; 2 * q < s_hi; ++q) {
-    for (int i = th.tid; i < N * LS; i += th.nth) S[i] = mk<T>(0, 0);
+    for (int i = th.tid; i < N * LS; i += th.nth) S[i] = mk<C>(C(0), C(0));
     WGW_SYNC();
-    const cplx<T>* tp = Tbuf + (size_t)q * NP * N * N + (size_t)y * N;
+    const cplx<C>* tp = Tbuf + (size_t)q * NP * N * N + (size_t)y * N;
     for (int i = th.tid; i < NP * N; i += th.nth) {
       const int hi = i / N, z = i % N;
       S[z * LS + (hi - m + N) % N] = tp[(size_t)hi * N * N + z];
     }
     WGW_SYNC();
-    fft_dif_n<T, NC>(S, pl, tw, +1, N, LS, 1, -1, th);
+    fft_dif_n<C, NC>(S, pl, tw, +1, N, LS, 1, -1, th);
     const int sa = 2 * q, sb = 2 * q + 1;
     const bool ua = sa >= s_lo && sa < s_hi && sa < n_sys;
     const bool ub = sb >= s_lo && sb < s_hi && sb < n_sys;
     const T* pa = psi_r + (size_t)(sa - s_lo) * ldpsi + slab;
     const T* pb = psi_r + (size_t)(sb - s_lo) * ldpsi + slab;
     for (int i = th.tid; i < N * N; i += th.nth) {
-      const cplx<T> v = S[(i / N) * LS + (i % N)];
-      T a = acc[i];
-      if (ua) a += pa[i] * v.re;
-      if (ub) a += pb[i] * v.im;
+      const cplx<C> v = S[(i / N) * LS + (i % N)];
+      C a = acc[i];
+      if (ua) a += C(pa[i]) * v.re;
+      if (ub) a += C(pb[i]) * v.im;
       acc[i] = a;
     }
     WGW_SYNC();
   }
   T* d = D + (size_t)p * ldd + slab;
-  for (int i = th.tid; i < N * N; i += th.nth) d[i] = coef * acc[i];
+  for (int i = th.tid; i < N * N; i += th.nth) d[i] = T(C(coef) * acc[i]);
 }
 
 }  // namespace wgw

@@ -5,6 +5,6 @@ namespace wgw {
 
 int fft_threads(int n) { return n >= 40 ? 256 : 128; }
 
-WGW_INST_FFT(float)
+WGW_INST_FFT(float, float)
 
 }  // namespace wgw

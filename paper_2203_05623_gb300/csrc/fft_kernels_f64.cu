@@ -3,6 +3,6 @@
 
 namespace wgw {
 
-WGW_INST_FFT(double)
+WGW_INST_FFT(double, double)
 
 }  // namespace wgw

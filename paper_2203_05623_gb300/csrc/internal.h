@@ -12,7 +12,9 @@ namespace wgw {
 template <typename T>
 struct FftCtx {
   FftPlan plan;
-  const cplx<T>* tw;   // exp(+2 pi i k / N), k < N
+  const cplx<T>* tw;              // exp(+2 pi i k / N), k < N
+  const cplx<ff>* twe = nullptr;  // the same in float-float; non-null selects float-float
+                                  // compute for T = double (pair buffers then hold cplx<ff>)
 };
 
 int fft_threads(int n);
@@ -21,19 +23,60 @@ int fft_threads(int n);
 int report_error(int status, const char* msg);
 void clear_error();
 
-// Pruned 3D FFT pipeline (fft_kernels.cu).
+// Pruned 3D FFT pipeline (fft_kernels_*.cu), storage type T and compute type C.
+template <typename T, typename C>
+cudaError_t launch_plane_g2r_c(const SphereTab& sp, const FftPlan& plan, const cplx<C>* tw, const T* X, long ldx,
+                               int n_sys, const int* list, const int* active, cplx<C>* Tbuf, cudaStream_t st);
+template <typename T, typename C>
+cudaError_t launch_xline_c(int m, const FftPlan& plan, const cplx<C>* tw, cplx<C>* Tbuf, const XArgs<T>& a,
+                           const int* active, cudaStream_t st);
+template <typename T, typename C>
+cudaError_t launch_plane_r2g_c(const SphereTab& sp, int npt_max, const FftPlan& plan, const cplx<C>* tw,
+                               const cplx<C>* Tbuf, const Epi<T>& e, cudaStream_t st);
+template <typename T, typename C>
+cudaError_t launch_drho_xline_c(int m, const FftPlan& plan, const cplx<C>* tw, const cplx<C>* Tbuf,
+                                const T* psi_r, long ldpsi, int n_v, int n_sys, int n_pert, T coef, T* D,
+                                long ldd, cudaStream_t st);
+
+// Dispatch on the context's compute type: T = float and T = double compute in T, or, when
+// f.twe is set (T = double only), in float-float with the pair buffer Tbuf holding cplx<ff>
+// (the same size as cplx<double>).
+inline bool ff_grid_supported(int n) { return n == 24 || n == 32 || n == 48 || n == 64 || n == 96; }
+template <typename T>
+inline bool use_ff(const FftCtx<T>& f) {
+  return sizeof(T) == sizeof(double) && f.twe != nullptr && ff_grid_supported(f.plan.n);
+}
+
 template <typename T>
 cudaError_t launch_plane_g2r(const SphereTab& sp, FftCtx<T> f, const T* X, long ldx, int n_sys,
-                             const int* list, const int* active, cplx<T>* Tbuf, cudaStream_t st);
+                             const int* list, const int* active, cplx<T>* Tbuf, cudaStream_t st) {
+  if (use_ff(f))
+    return launch_plane_g2r_c<T, ff>(sp, f.plan, f.twe, X, ldx, n_sys, list, active,
+                                     reinterpret_cast<cplx<ff>*>(Tbuf), st);
+  return launch_plane_g2r_c<T, T>(sp, f.plan, f.tw, X, ldx, n_sys, list, active, Tbuf, st);
+}
 template <typename T>
 cudaError_t launch_xline(int m, FftCtx<T> f, cplx<T>* Tbuf, const XArgs<T>& a, const int* active,
-                         cudaStream_t st);
+                         cudaStream_t st) {
+  if (use_ff(f))
+    return launch_xline_c<T, ff>(m, f.plan, f.twe, reinterpret_cast<cplx<ff>*>(Tbuf), a, active, st);
+  return launch_xline_c<T, T>(m, f.plan, f.tw, Tbuf, a, active, st);
+}
 template <typename T>
 cudaError_t launch_plane_r2g(const SphereTab& sp, int npt_max, FftCtx<T> f, const cplx<T>* Tbuf,
-                             const Epi<T>& e, cudaStream_t st);
+                             const Epi<T>& e, cudaStream_t st) {
+  if (use_ff(f))
+    return launch_plane_r2g_c<T, ff>(sp, npt_max, f.plan, f.twe, reinterpret_cast<const cplx<ff>*>(Tbuf), e, st);
+  return launch_plane_r2g_c<T, T>(sp, npt_max, f.plan, f.tw, Tbuf, e, st);
+}
 template <typename T>
 cudaError_t launch_drho_xline(int m, FftCtx<T> f, const cplx<T>* Tbuf, const T* psi_r, long ldpsi,
-                              int n_v, int n_sys, int n_pert, T coef, T* D, long ldd, cudaStream_t st);
+                              int n_v, int n_sys, int n_pert, T coef, T* D, long ldd, cudaStream_t st) {
+  if (use_ff(f))
+    return launch_drho_xline_c<T, ff>(m, f.plan, f.twe, reinterpret_cast<const cplx<ff>*>(Tbuf), psi_r, ldpsi,
+                                      n_v, n_sys, n_pert, coef, D, ldd, st);
+  return launch_drho_xline_c<T, T>(m, f.plan, f.tw, Tbuf, psi_r, ldpsi, n_v, n_sys, n_pert, coef, D, ldd, st);
+}
 
 // Linear algebra (la_kernels.cu).
 // Y <- Y - Psi Psi^T Y for the active systems of a list (null = systems 0..n_sys-1);

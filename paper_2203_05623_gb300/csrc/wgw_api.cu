@@ -103,15 +103,23 @@ int upload_sphere(HostSphere& s) {
 template <typename T>
 struct Prec {
   DevBuf tw;        // N twiddles
+  DevBuf twe;       // the same in float-float (T = double)
+  bool use_ff = false;   // FFT passes compute in float-float (T = double)
   DevBuf psi;       // occupied states, real basis, n_v x ld_w
   DevBuf psi_r;     // occupied states in real space, n_v x N^3
   DevBuf v_r;       // V_loc in real space
   // work
   DevBuf X, R, Z, P, Q, Bv, Tw, shift;
   DevBuf kbB, kbD;  // KB projectors in the real basis (n_proj x ld_w) and couplings
-  FftCtx<T> fft(const FftPlan& pl) const { FftCtx<T> f; f.plan = pl; f.tw = tw.as<cplx<T>>(); return f; }
+  FftCtx<T> fft(const FftPlan& pl) const {
+    FftCtx<T> f;
+    f.plan = pl;
+    f.tw = tw.as<cplx<T>>();
+    f.twe = use_ff ? twe.as<cplx<ff>>() : nullptr;
+    return f;
+  }
   void release() {
-    DevBuf* all[] = {&tw, &psi, &psi_r, &v_r, &X, &R, &Z, &P, &Q, &Bv, &Tw, &shift, &kbB, &kbD};
+    DevBuf* all[] = {&tw, &twe, &psi, &psi_r, &v_r, &X, &R, &Z, &P, &Q, &Bv, &Tw, &shift, &kbB, &kbD};
     for (DevBuf* b : all) b->release();
   }
 };
@@ -787,6 +795,7 @@ int chi0_rb_shifted(wgw_ctx* c, const double* dvrb, int n_real, const std::vecto
 int apply_core(wgw_ctx* c, const double* dV, int n_pert, const double* omega, int n_omega,
                double* drho, bool symmetrized, cudaStream_t st, wgw_stats* stats) {
   if (!c) return fail(WGW_ERR_ARG, "null context");
+  c->d.use_ff = c->opt.precision == WGW_MIXED && c->opt.fp64_emulation != 0;
   if (n_pert < 0 || n_omega < 1 || !omega) return fail(WGW_ERR_ARG, "need n_pert >= 0 and n_omega >= 1");
   std::vector<int> k_zero, k_pos;
   std::vector<double> w_pos;
@@ -1096,6 +1105,7 @@ int davidson_impl(wgw_ctx* c, int npd, const double* x0, double* eig, double* ba
 int lanczos_impl(wgw_ctx* c, const double* phi, int npd, int n_steps, const double* omega, int n_om,
                  double* alpha_out, double* beta_out, double* chi_out, wgw_stats* st_out) {
   cudaStream_t st = c->stream;
+  c->d.use_ff = false;   // the chains run in native FP64
   const int N = c->N, n_v = c->n_v, n = c->wfc.nrb(), nr = c->rho.nrb();
   const long ldw = c->ld_w, ldr = c->ld_r;
   const int n_ch = npd * n_v;
@@ -1231,6 +1241,7 @@ extern "C" {
 int wgw_default_options(wgw_options* opt) {
   if (!opt) return fail(WGW_ERR_ARG, "null options");
   opt->precision = WGW_FP64;
+  opt->fp64_emulation = 1;
   opt->cg_tol = 1e-12;
   opt->max_cg_iter = 2000;
   opt->max_refine = 8;
@@ -1280,13 +1291,16 @@ static int setup_impl(wgw_ctx* c, const double* vloc_G, const double* psi_v, con
   // Twiddles exp(+2 pi i k / N).
   std::vector<cplx<double>> twd(N);
   std::vector<cplx<float>> twf(N);
+  std::vector<cplx<ff>> twff(N);
   for (int k = 0; k < N; ++k) {
     const double a = 2.0 * M_PI * k / N;
     twd[k] = mk<double>(std::cos(a), std::sin(a));
     twf[k] = mk<float>((float)twd[k].re, (float)twd[k].im);
+    twff[k] = mk<ff>(ff(twd[k].re), ff(twd[k].im));
   }
   WGW_TRY(upload(c->d.tw, twd));
   WGW_TRY(upload(c->f.tw, twf));
+  WGW_TRY(upload(c->d.twe, twff));
   c->e_v.assign(e_v, e_v + c->n_v);
   WGW_TRY(upload(c->e_v_d, c->e_v));
   // Occupied states: complex sphere -> real basis (checking they are real in r).

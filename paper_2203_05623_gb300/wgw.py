@@ -34,7 +34,8 @@ class Options(ctypes.Structure):
                 ("max_cg_iter", ctypes.c_int), ("max_refine", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("f_s", ctypes.c_double),
                 ("check_every", ctypes.c_int), ("dav_tol", ctypes.c_double),
-                ("dav_max_iter", ctypes.c_int), ("dav_factor", ctypes.c_int), ("seed", ctypes.c_int)]
+                ("dav_max_iter", ctypes.c_int), ("dav_factor", ctypes.c_int), ("seed", ctypes.c_int),
+                ("fp64_emulation", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

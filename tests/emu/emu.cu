@@ -64,7 +64,8 @@ void sphere_to_rb_host(const Sph& sp, int n_sys, const double* c, long ldc, cons
   for (size_t i = 0; i < tmp.size(); ++i) out[i] = (T)tmp[i];
 }
 
-template <typename T, int NC = 0>
+// Storage type T, compute type C of the pipeline bodies (C = ff: float-float).
+template <typename T, int NC = 0, typename C = T>
 void apply_h_impl(double L, double ecut, int N, const double* vloc_c, int n_sys, const double* Xd,
                   const double* shift, double* outd) {
   Sph w, r;
@@ -72,30 +73,31 @@ void apply_h_impl(double L, double ecut, int N, const double* vloc_c, int n_sys,
   build_sphere(L, 4 * ecut, N, r.h);
   FftPlan pl;
   make_plan(N, pl);
-  auto tw = twiddles<T>(N);
+  auto tws = twiddles<T>(N);
+  auto tw = twiddles<C>(N);
   const long N3 = (long)N * N * N;
   const int nw = w.h.nrb(), nr = r.h.nrb();
   std::vector<T> vrb(nr), vr(N3);
   sphere_to_rb_host<T>(r, 1, vloc_c, 2L * r.h.n, nullptr, 0, vrb.data(), nr);
-  to_real<T>(r, pl, tw, vrb.data(), nr, 1, vr.data());
+  to_real<T>(r, pl, tws, vrb.data(), nr, 1, vr.data());
   std::vector<T> X((size_t)n_sys * nw), out((size_t)n_sys * nw), sh(n_sys);
   for (size_t i = 0; i < X.size(); ++i) X[i] = (T)Xd[i];
   for (int s = 0; s < n_sys; ++s) sh[s] = (T)shift[s];
   const int NP = 2 * w.h.m + 1, pairs = (n_sys + 1) / 2;
-  std::vector<cplx<T>> Tb((size_t)pairs * NP * N * N), B((size_t)N * (N + 1)), Zp(w.h.npt_max + 1);
+  std::vector<cplx<C>> Tb((size_t)pairs * NP * N * N), B((size_t)N * (N + 1)), Zp(w.h.npt_max + 1);
   for (int q = 0; q < pairs; ++q)
     for (int hi = 0; hi < NP; ++hi)
-      plane_g2r_body<T, NC>(q, hi, w.tab(), pl, tw.data(), X.data(), nw, n_sys, nullptr, Tb.data(), B.data(), kOne);
+      plane_g2r_body<T, NC, C>(q, hi, w.tab(), pl, tw.data(), X.data(), nw, n_sys, nullptr, Tb.data(), B.data(), kOne);
   XArgs<T> a{};
   a.mode = XM_APPLY_V; a.V = vr.data(); a.n_sys = n_sys;
   for (int q = 0; q < pairs; ++q)
-    for (int y = 0; y < N; ++y) xline_body<T, NC>(q, y, w.h.m, pl, tw.data(), Tb.data(), a, B.data(), kOne);
+    for (int y = 0; y < N; ++y) xline_body<T, NC, C>(q, y, w.h.m, pl, tw.data(), Tb.data(), a, B.data(), kOne);
   Epi<T> e{};
   e.out = out.data(); e.ldo = nw; e.pin = X.data(); e.ldp = nw; e.vcoef = T(1); e.kin = T(1);
   e.shift = sh.data(); e.n_sys = n_sys;
   for (int q = 0; q < pairs; ++q)
     for (int hp = 0; hp <= w.h.m; ++hp)
-      plane_r2g_body<T, NC>(q, hp, w.tab(), pl, tw.data(), Tb.data(), e, B.data(), Zp.data(), kOne);
+      plane_r2g_body<T, NC, C>(q, hp, w.tab(), pl, tw.data(), Tb.data(), e, B.data(), Zp.data(), kOne);
   for (size_t i = 0; i < out.size(); ++i) outd[i] = (double)out[i];
 }
 
@@ -132,6 +134,29 @@ int emu_fft_line(int N, int dir, const double* in, double* out) {
   return 0;
 }
 
+// One line in float-float arithmetic (input rounded to float-float); dir as emu_fft_line.
+int emu_fft_line_ff(int N, int dir, const double* in, double* out) {
+  FftPlan pl;
+  if (!make_plan(N, pl)) return 1;
+  auto tw = twiddles<ff>(N);
+  std::vector<cplx<ff>> b(N);
+  for (int i = 0; i < N; ++i) b[i] = mk<ff>(ff(in[2 * i]), ff(in[2 * i + 1]));
+  if (dir == 0) fft_dif<ff>(b.data(), pl, tw.data(), +1, 1, N, 1, -1, kOne);
+  else fft_dit<ff>(b.data(), pl, tw.data(), -1, 1, N, 1, -1, kOne);
+  for (int i = 0; i < N; ++i) { out[2 * i] = (double)b[i].re; out[2 * i + 1] = (double)b[i].im; }
+  return 0;
+}
+
+// Float-float primitives on arrays: op 0 = a + b, 1 = a * b, 2 = a - b (inputs rounded to float-float).
+int emu_ff_op(int op, int n, const double* a, const double* b, double* out) {
+  for (int i = 0; i < n; ++i) {
+    const ff x(a[i]), y(b[i]);
+    const ff r = op == 0 ? x + y : op == 1 ? x * y : x - y;
+    out[i] = (double)r;
+  }
+  return 0;
+}
+
 int emu_fft_position(int N, int n) {
   FftPlan pl;
   make_plan(N, pl);
@@ -139,12 +164,15 @@ int emu_fft_position(int N, int n) {
 }
 
 // (H - shift_s) applied to real-basis vectors X (n_sys x nrb) via the plane / x-line / plane bodies.
-// flags bit 0: FP32; bit 1: the compile-time-N bodies (N = 24 only).
+// flags bit 0: FP32; bit 1: the compile-time-N bodies (N = 24 only); bit 2: FP64 storage with
+// float-float compute (compile-time N = 24 only).
 int emu_apply_h(double L, double ecut, int N, const double* vloc_c, int n_sys, const double* X,
                 const double* shift, double* out, int flags) {
-  const bool fp32 = flags & 1, ct = flags & 2;
-  if (ct && N != 24) return 1;
-  if (fp32) {
+  const bool fp32 = flags & 1, ct = flags & 2, ffc = flags & 4;
+  if ((ct || ffc) && N != 24) return 1;
+  if (ffc) {
+    apply_h_impl<double, 24, ff>(L, ecut, N, vloc_c, n_sys, X, shift, out);
+  } else if (fp32) {
     if (ct) apply_h_impl<float, 24>(L, ecut, N, vloc_c, n_sys, X, shift, out);
     else apply_h_impl<float>(L, ecut, N, vloc_c, n_sys, X, shift, out);
   } else {

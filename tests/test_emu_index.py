@@ -35,7 +35,8 @@ def emu():
     deps = [EMU_SRC] + [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     if not os.path.exists(EMU_LIB) or any(os.path.getmtime(d) > os.path.getmtime(EMU_LIB) for d in deps):
         os.makedirs(os.path.dirname(EMU_LIB), exist_ok=True)
-        cmd = [nvcc, "-std=c++17", "-O2", "-Xcompiler", "-fPIC", "-shared", "-I", CSRC,
+        cmd = [nvcc, "-std=c++17", "-O2", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+               "-shared", "-I", CSRC,
                "-gencode", "arch=compute_103a,code=sm_103a", EMU_SRC, "-o", EMU_LIB]
         subprocess.run(cmd, check=True, capture_output=True)
     return ctypes.CDLL(EMU_LIB)
@@ -148,7 +149,49 @@ def test_real_basis_roundtrip(emu):
     assert abs(mp.to_rb(A)[0] @ mp.to_rb(A)[1] - np.vdot(A[:, 0], A[:, 1]).real) < 1e-12
 
 
-@pytest.mark.parametrize("fp32", [0, 1, 2, 3])
+def test_float_float_primitives_error_bounds(emu):
+    """Float-float sum and product against the exact double results: the sloppy sum is within
+    about 2^-47 (|a| + |b|), the product within about 2^-47 |a b| (Dekker; Hida, Li, Bailey)."""
+    rng = np.random.default_rng(5)
+    n = 20000
+    a = rng.standard_normal(n) * 10.0 ** rng.integers(-6, 6, n)
+    b = rng.standard_normal(n) * 10.0 ** rng.integers(-6, 6, n)
+    b[:200] = -a[:200] * (1 + 1e-9 * rng.standard_normal(200))   # heavy cancellation
+    ai, ap = P(a)
+    bi, bp = P(b)
+    out = np.zeros(n)
+    # Inputs are first rounded to float-float: |x - ff(x)| <= 2^-48 |x|.
+    emu.emu_ff_op(0, n, ap, bp, out.ctypes.data_as(dp))
+    assert np.all(np.abs(out - (a + b)) <= 2.0 ** -45 * (np.abs(a) + np.abs(b)))
+    emu.emu_ff_op(2, n, ap, bp, out.ctypes.data_as(dp))
+    assert np.all(np.abs(out - (a - b)) <= 2.0 ** -45 * (np.abs(a) + np.abs(b)))
+    emu.emu_ff_op(1, n, ap, bp, out.ctypes.data_as(dp))
+    assert np.all(np.abs(out - a * b) <= 2.0 ** -45 * np.abs(a * b))
+    # Far below FP32 accuracy: a float-rounded sum would miss by ~2^-24.
+    assert np.max(np.abs(out - a * b) / np.abs(a * b)) < 1e-13
+
+
+@pytest.mark.parametrize("N", [24, 48, 96])
+def test_line_fft_float_float(emu, N):
+    rng = np.random.default_rng(N + 2)
+    x = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    xin, xp = P(np.stack([x.real, x.imag], 1).ravel())
+    out = np.zeros(2 * N)
+    assert emu.emu_fft_line_ff(N, 0, xp, out.ctypes.data_as(dp)) == 0
+    pos = np.array([emu.emu_fft_position(N, k) for k in range(N)])
+    y = out[0::2] + 1j * out[1::2]
+    ref = np.fft.ifft(x) * N
+    err = np.max(np.abs(y[pos] - ref)) / np.max(np.abs(ref))
+    assert err < 2e-13          # about 48-bit arithmetic; FP32 would give ~1e-7
+    zin = np.zeros(N, np.complex128)
+    zin[pos] = x
+    zi, zp = P(np.stack([zin.real, zin.imag], 1).ravel())
+    emu.emu_fft_line_ff(N, 1, zp, out.ctypes.data_as(dp))
+    ref = np.fft.fft(x)
+    assert np.max(np.abs(out[0::2] + 1j * out[1::2] - ref)) / np.max(np.abs(ref)) < 2e-13
+
+
+@pytest.mark.parametrize("fp32", [0, 1, 2, 3, 4])
 def test_apply_h_bodies_equal_dense_h(emu, cfg24, fp32):
     s = cfg24
     m = Model(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v)
@@ -165,7 +208,7 @@ def test_apply_h_bodies_equal_dense_h(emu, cfg24, fp32):
                     out.ctypes.data_as(dp), fp32)
     ref = m.h_dense() @ mp.to_c(X) + shift[None, :] * mp.to_c(X)
     got = mp.to_c(out.reshape(n_sys, mp.nrb))
-    tol = 2e-6 if fp32 & 1 else 1e-13
+    tol = 2e-6 if fp32 & 1 else 1e-12 if fp32 & 4 else 1e-13
     assert np.max(np.abs(got - ref)) < tol * np.max(np.abs(ref))
 
 
