@@ -159,13 +159,17 @@ int wgw_apply_chibar0_dev(wgw_ctx* ctx, const double* phi_dev, int n_pert, const
  * Kernel timing (no counterpart in the paper; used to report roofline fractions).
  * When enabled, every kernel launch of the context is bracketed by CUDA events on
  * its stream and accumulated per kernel class; enabling resets the counters.
- * Classes 0..WGW_PROF_KINDS-1: plane_g2r, xline, plane_r2g, drho_xline, pc_project,
- * cg_update, convert, other.  wgw_profile_read returns, for one class, the summed
+ * Classes 0..7: plane_g2r, xline, plane_r2g, drho_xline, pc_project, cg_update, convert,
+ * other, for the kernels on FP32 arrays; classes 8..15: the same names with "_f64", for the
+ * kernels on FP64 arrays (native FP64 or float-float compute).  wgw_profile_read returns, for one class, the summed
  * device milliseconds, the launch count and the summed algorithmic bytes and flops
  * (each launch's own compulsory inputs and outputs); any output pointer may be NULL.
  */
-#define WGW_PROF_KINDS 8
+#define WGW_PROF_KINDS 16
 int wgw_profile_enable(wgw_ctx* ctx, int on);
+/* Restricts recording to the classes whose bit is set in mask (bit k = class k; default all),
+ * so that a timed run can bracket only the launches of one class. */
+int wgw_profile_classes(wgw_ctx* ctx, unsigned mask);
 int wgw_profile_read(wgw_ctx* ctx, int kind, double* ms, long* launches, double* bytes, double* flops);
 const char* wgw_profile_kind_name(int kind);
 

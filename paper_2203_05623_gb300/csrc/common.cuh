@@ -85,6 +85,21 @@ WGW_HD ff operator*(ff a, ff b) {
 WGW_HD ff& operator+=(ff& a, ff b) { a = a + b; return a; }
 WGW_HD ff& operator*=(ff& a, ff b) { a = a * b; return a; }
 
+// acc += a * b.  The float-float form keeps the running sum unnormalised (acc.hi holds the
+// rounded sum of the leading products, acc.lo collects their exact rounding errors and the low
+// parts), which is accurate to about 2^-47 of the magnitudes summed for sums of thousands of
+// terms; convert with double(acc).
+WGW_HD void mac(float& acc, float a, float b) { acc += a * b; }
+WGW_HD void mac(double& acc, double a, double b) { acc += a * b; }
+WGW_HD void mac(ff& acc, ff a, ff b) {
+  const float p = ffm(a.hi, b.hi);
+  float e = fff(a.hi, b.hi, -p);
+  e = fff(a.hi, b.lo, fff(a.lo, b.hi, e));
+  const ff s = two_sum(acc.hi, p);
+  acc.hi = s.hi;
+  acc.lo = ffa(acc.lo, ffa(s.lo, e));
+}
+
 constexpr double kInvSqrt2 = 0.70710678118654752440;
 constexpr double kSqrt2 = 1.41421356237309504880;
 

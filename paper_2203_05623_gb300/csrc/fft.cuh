@@ -310,6 +310,60 @@ WGW_HD void fft_dit_n(cplx<T>* buf, const FftPlan& p, const cplx<T>* tw, int sig
   }
 }
 
+// ---------------------------------------------------------------- register-resident lines
+// One line of compile-time length N held by one thread (v[0..N-1], kept in registers once the
+// loops are unrolled): the same stages as dif_stages_c / dit_stages_c, so the same
+// digit-reversed positions, with every index and twiddle index a compile-time constant.
+template <typename T, int N, int ST, int SIGN>
+WGW_HD void reg_dif(cplx<T>* v, const cplx<T>* tw) {
+  constexpr CPlan P = cplan(N);
+  if constexpr (ST < P.nst) {
+    constexpr int S = P.size[ST], R = P.radix[ST], M = S / R, step = N / S;
+#pragma unroll
+    for (int blk = 0; blk < N / S; ++blk) {
+#pragma unroll
+      for (int j2 = 0; j2 < M; ++j2) {
+        cplx<T> u[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) u[r] = v[blk * S + j2 + r * M];
+        dft_fixed<T, R>(u, SIGN);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          cplx<T> x = u[r];
+          if (r > 0 && j2 > 0) x = cmul(x, twiddle(tw, step * j2 * r, SIGN));
+          v[blk * S + j2 + r * M] = x;
+        }
+      }
+    }
+    reg_dif<T, N, ST + 1, SIGN>(v, tw);
+  }
+}
+
+template <typename T, int N, int ST, int SIGN>
+WGW_HD void reg_dit(cplx<T>* v, const cplx<T>* tw) {
+  constexpr CPlan P = cplan(N);
+  if constexpr (ST >= 0) {
+    constexpr int S = P.size[ST], R = P.radix[ST], M = S / R, step = N / S;
+#pragma unroll
+    for (int blk = 0; blk < N / S; ++blk) {
+#pragma unroll
+      for (int j2 = 0; j2 < M; ++j2) {
+        cplx<T> u[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          cplx<T> x = v[blk * S + j2 + r * M];
+          if (r > 0 && j2 > 0) x = cmul(x, twiddle(tw, step * j2 * r, SIGN));
+          u[r] = x;
+        }
+        dft_fixed<T, R>(u, SIGN);
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[blk * S + j2 + r * M] = u[r];
+      }
+    }
+    reg_dit<T, N, ST - 1, SIGN>(v, tw);
+  }
+}
+
 // Digit-reversed storage position of natural index n (host and device).
 WGW_HD int fft_position(const FftPlan& p, int n) {
   int pos = 0, N = p.n;

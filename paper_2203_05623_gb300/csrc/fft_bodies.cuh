@@ -167,6 +167,64 @@ WGW_HD void xline_body(int pair, int y, int m, const FftPlan& pl, const cplx<C>*
   }
 }
 
+// The x-line pass with one line per thread held in registers (compile-time N): line l = y N + z
+// of pair `pair`, same modes, layouts and positions as xline_body.  The pair intermediate is
+// read and written at T[hi][l], so consecutive threads touch consecutive addresses.
+template <typename T, int N, typename C>
+WGW_HD void xline_reg_body(int pair, int l, int m, const cplx<C>* tw, cplx<C>* Tbuf, const XArgs<T>& a) {
+  const int NP = 2 * m + 1;
+  int s0, s1;
+  pair_members(a.list, a.n_sys, pair, s0, s1);
+  const bool has1 = s1 >= 0;
+  cplx<C>* tp = Tbuf + (size_t)pair * NP * N * N + l;   // T[hi][y][z] at tp[hi * N * N]
+  const size_t line = (size_t)l * N;                     // real-space [y][z][x] offset
+  cplx<C> v[N];
+  if (a.mode == XM_FROM_REAL) {
+    const T* A0 = a.A + (size_t)(a.a_index ? a.a_index[s0] : s0) * a.lda + line;
+    const T* A1 = has1 ? a.A + (size_t)(a.a_index ? a.a_index[s1] : s1) * a.lda + line : nullptr;
+    const T* B0 = a.Bm ? a.Bm + (size_t)(a.b_index ? a.b_index[s0] : s0) * a.ldb + line : nullptr;
+    const T* B1 = (a.Bm && has1) ? a.Bm + (size_t)(a.b_index ? a.b_index[s1] : s1) * a.ldb + line : nullptr;
+#pragma unroll
+    for (int x = 0; x < N; ++x) {
+      C re = C(A0[x]), im = A1 ? C(A1[x]) : C(0);
+      if (B0) re = re * C(B0[x]);
+      if (B1) im = im * C(B1[x]);
+      v[x] = mk<C>(re, im);
+    }
+  } else {
+#pragma unroll
+    for (int x = 0; x < N; ++x) {
+      // natural index x <-> Miller h = x (x <= m) or x - N (x >= N - m); plane hi = h + m
+      const bool in = x <= m || x >= N - m;
+      const int hi = x <= m ? x + m : x - N + m;
+      v[x] = in ? tp[(size_t)hi * N * N] : mk<C>(C(0), C(0));
+    }
+    reg_dif<C, N, 0, +1>(v, tw);
+  }
+  if (a.mode == XM_TO_REAL) {
+    T* r0 = a.R0 + (size_t)s0 * a.ldr + line;
+    T* r1 = (has1 && a.R1) ? a.R1 + (size_t)s1 * a.ldr + line : nullptr;
+#pragma unroll
+    for (int x = 0; x < N; ++x) {
+      r0[x] = T(v[x].re);
+      if (r1) r1[x] = T(v[x].im);
+    }
+    return;
+  }
+  if (a.mode == XM_APPLY_V) {
+    const T* vr = a.V + line;
+#pragma unroll
+    for (int x = 0; x < N; ++x) v[x] = cscale(v[x], C(vr[x]));
+  }
+  reg_dit<C, N, cplan(N).nst - 1, -1>(v, tw);
+#pragma unroll
+  for (int x = 0; x < N; ++x) {
+    const bool in = x <= m || x >= N - m;
+    const int hi = x <= m ? x + m : x - N + m;
+    if (in) tp[(size_t)hi * N * N] = v[x];
+  }
+}
+
 // Epilogue of the r -> G plane kernel, per real-basis element i of system s:
 //   out[s][i] = vcoef * F[i] + (kin * g2[i] + shift[s]) * pin[s][i]   (pin may be null)
 // where F is the transformed function (already scaled by 1/N^3).

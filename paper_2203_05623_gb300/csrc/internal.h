@@ -81,9 +81,10 @@ cudaError_t launch_drho_xline(int m, FftCtx<T> f, const cplx<T>* Tbuf, const T* 
 // Linear algebra (la_kernels.cu).
 // Y <- Y - Psi Psi^T Y for the active systems of a list (null = systems 0..n_sys-1);
 // work holds pc_work_elems(n, n_sys, nv) elements of T.
+// ffc: for T = double, compute in float-float (operands rounded to float-float pairs).
 template <typename T>
 cudaError_t launch_pc(T* Y, long ldy, int n_sys, const int* list, const T* Psi, long ldp, int n, int nv,
-                      const int* active, T* work, cudaStream_t st);
+                      const int* active, T* work, cudaStream_t st, bool ffc = false);
 // C = A^T B: A is K x m (column j at A + j*lda), B is K x n (column j at B + c_j * ldb with
 // c_j = cols[j], or j when cols is null); C is written row-major with rows of length n, padded
 // to a multiple of 64 rows.  work: gemm_tn_work_elems(K, m, n) doubles.
@@ -144,7 +145,7 @@ cudaError_t launch_lz_assemble(int n_pdep, int n_v, int n_steps, int n_om, const
 // work: pc_work_elems(n, n_sys, n_proj) elements of T.
 template <typename T>
 cudaError_t launch_kb(T* Q, const T* P, long ld, int n_sys, const int* list, const T* B, long ldb, int n, int n_proj,
-                      const T* D, T* work, cudaStream_t st);
+                      const T* D, T* work, cudaStream_t st, bool ffc = false);
 // Ordered list of the systems s < n_sys with active[s] != 0, and their count.
 cudaError_t launch_build_list(const int* active, int n_sys, int* list, int* count, cudaStream_t st);
 int pc_kblocks(int n, int n_sys);

@@ -129,8 +129,13 @@ template <typename T> struct Vec16;
 template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
 template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
 
-template <typename T>
-__device__ __forceinline__ void load_kchunk(T (*dst)[kGT + 4], const T* __restrict__ base, long ld,
+// Float-float compute type for FP64 storage (T itself otherwise).
+template <typename T> struct FfIfDouble { using type = T; };
+template <> struct FfIfDouble<double> { using type = ff; };
+template <typename T> using ff_if_double = typename FfIfDouble<T>::type;
+
+template <typename T, typename C>
+__device__ __forceinline__ void load_kchunk(C (*dst)[kGT + 4], const T* __restrict__ base, long ld,
                                             const int* __restrict__ cols, int col0, int n_cols, int k0,
                                             int k_hi) {
   // dst[kk][c] = base[col(c) * ld + k0 + kk] for kk < kGK, c < kGT (zero outside).
@@ -157,38 +162,40 @@ __device__ __forceinline__ void load_kchunk(T (*dst)[kGT + 4], const T* __restri
       for (int j = 0; j < V; ++j) vals[j] = T(0);
     }
 #pragma unroll
-    for (int j = 0; j < V; ++j) dst[kq + j][c] = vals[j];
+    for (int j = 0; j < V; ++j) dst[kq + j][c] = C(vals[j]);
   }
 }
 
-template <typename T>
+// C = compute type (T, or ff for T = double: operands converted once while staged in shared
+// memory, products accumulated in float-float).
+template <typename T, typename C = T>
 __global__ void __launch_bounds__(256) k_pc_gemm1(const T* __restrict__ Psi, long ldp,
                                                   const T* __restrict__ Y, long ldy, int n, int nv,
                                                   int n_list, const int* __restrict__ list, int kblk,
                                                   T* __restrict__ Cpart) {
-  __shared__ __align__(16) T As[kGK][kGT + 4];
-  __shared__ __align__(16) T Bs[kGK][kGT + 4];
+  __shared__ __align__(16) C As[kGK][kGT + 4];
+  __shared__ __align__(16) C Bs[kGK][kGT + 4];
   const int j0 = blockIdx.x * kGT, v0 = blockIdx.z * kGT, kb = blockIdx.y;
   const int k_lo = kb * kblk, k_hi = min(n, k_lo + kblk);
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;   // tx: systems, ty: states
-  T acc[4][4];
+  C acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    for (int j = 0; j < 4; ++j) acc[i][j] = C(0);
   for (int k0 = k_lo; k0 < k_hi; k0 += kGK) {
-    load_kchunk<T>(As, Psi, ldp, nullptr, v0, nv, k0, k_hi);
-    load_kchunk<T>(Bs, Y, ldy, list, j0, n_list, k0, k_hi);
+    load_kchunk<T, C>(As, Psi, ldp, nullptr, v0, nv, k0, k_hi);
+    load_kchunk<T, C>(Bs, Y, ldy, list, j0, n_list, k0, k_hi);
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < kGK; ++kk) {
-      T a[4], b[4];
+      C a[4], b[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) { a[i] = As[kk][ty * 4 + i]; b[i] = Bs[kk][tx * 4 + i]; }
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        for (int j = 0; j < 4; ++j) mac(acc[i][j], a[i], b[j]);
     }
     __syncthreads();
   }
@@ -200,7 +207,7 @@ __global__ void __launch_bounds__(256) k_pc_gemm1(const T* __restrict__ Psi, lon
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int jx = j0 + tx * 4 + j;
-      if (jx < n_list) out[(size_t)v * n_list + jx] = acc[i][j];
+      if (jx < n_list) out[(size_t)v * n_list + jx] = T(acc[i][j]);
     }
   }
 }
@@ -224,14 +231,14 @@ __global__ void k_pc_reduce(T* __restrict__ Cpart, size_t slice, int n_kb) {
 }
 
 // Y[:, s_j] = beta Y[:, s_j] + alpha sum_v Psi[:, v] C[v][j]   (C row length ldc; beta = 0 never reads Y).
-template <typename T>
+template <typename T, typename CT = T>
 __global__ void __launch_bounds__(256) k_pc_gemm2(const T* __restrict__ Psi, long ldp, T* __restrict__ Y,
                                                   long ldy, int n, int nv, int n_list,
                                                   const int* __restrict__ list, const T* __restrict__ C,
                                                   long ldc, T alpha, T beta,
                                                   const int* __restrict__ active) {
-  __shared__ __align__(16) T Cs[kGT][kGT + 4];     // C[v][j] of one 64-state chunk
-  __shared__ __align__(16) T Ps[kGT][kGT + 4];     // Psi[i][v] stored as Ps[v][i]
+  __shared__ __align__(16) CT Cs[kGT][kGT + 4];     // C[v][j] of one 64-state chunk
+  __shared__ __align__(16) CT Ps[kGT][kGT + 4];     // Psi[i][v] stored as Ps[v][i]
   const int i0 = blockIdx.x * kGT, j0 = blockIdx.y * kGT;
   // tx: 4 consecutive rows i (vector access along the system's column), ty: 4 systems.
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
@@ -240,28 +247,28 @@ __global__ void __launch_bounds__(256) k_pc_gemm2(const T* __restrict__ Psi, lon
     for (int t = 0; t < kGT && j0 + t < n_list; ++t) any |= active[list ? list[j0 + t] : j0 + t] != 0;
     if (!any) return;
   }
-  T acc[4][4];   // [row][system]
+  CT acc[4][4];   // [row][system]
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    for (int j = 0; j < 4; ++j) acc[i][j] = CT(0);
   for (int vc = 0; vc < nv; vc += kGT) {
     for (int e = tid; e < kGT * kGT; e += 256) {
       const int c = e % kGT, vv = e / kGT, v = vc + vv, jx = j0 + c;
-      Cs[vv][c] = (jx < n_list && v < nv) ? C[(size_t)v * ldc + jx] : T(0);
+      Cs[vv][c] = (jx < n_list && v < nv) ? CT(C[(size_t)v * ldc + jx]) : CT(0);
       const int i = i0 + c;
-      Ps[vv][c] = (v < nv && i < n) ? Psi[(size_t)v * ldp + i] : T(0);
+      Ps[vv][c] = (v < nv && i < n) ? CT(Psi[(size_t)v * ldp + i]) : CT(0);
     }
     __syncthreads();
     const int vmax = min(kGT, nv - vc);
     for (int vv = 0; vv < vmax; ++vv) {
-      T a[4], b[4];
+      CT a[4], b[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) { a[i] = Ps[vv][tx * 4 + i]; b[i] = Cs[vv][ty * 4 + i]; }
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        for (int j = 0; j < 4; ++j) mac(acc[i][j], a[i], b[j]);
     }
     __syncthreads();
   }
@@ -282,13 +289,13 @@ __global__ void __launch_bounds__(256) k_pc_gemm2(const T* __restrict__ Psi, lon
         if (beta != T(0)) w = *reinterpret_cast<VT*>(y + q);
         T* wp = reinterpret_cast<T*>(&w);
 #pragma unroll
-        for (int u = 0; u < V; ++u) wp[u] = (beta != T(0) ? beta * wp[u] : T(0)) + alpha * acc[q + u][j];
+        for (int u = 0; u < V; ++u) wp[u] = (beta != T(0) ? beta * wp[u] : T(0)) + alpha * T(acc[q + u][j]);
         *reinterpret_cast<VT*>(y + q) = w;
       }
     } else {
 #pragma unroll
       for (int i = 0; i < 4; ++i)
-        if (r0 + i < n) y[i] = (beta != T(0) ? beta * y[i] : T(0)) + alpha * acc[i][j];
+        if (r0 + i < n) y[i] = (beta != T(0) ? beta * y[i] : T(0)) + alpha * T(acc[i][j]);
     }
   }
 }
@@ -397,13 +404,15 @@ inline dim3 grid_el(int n, int n_sys) {
 
 template <typename T>
 cudaError_t launch_pc(T* Y, long ldy, int n_sys, const int* list, const T* Psi, long ldp, int n, int nv,
-                      const int* active, T* work, cudaStream_t st) {
+                      const int* active, T* work, cudaStream_t st, bool ffc) {
   if (n_sys == 0 || nv == 0) return cudaSuccess;
   const int n_kb = pc_kblocks(n, n_sys);
   const int kblk = ((n + n_kb - 1) / n_kb + kGK - 1) / kGK * kGK;
   const int nvp = (nv + kGT - 1) / kGT * kGT;
   dim3 g1((n_sys + kGT - 1) / kGT, n_kb, nvp / kGT);
-  k_pc_gemm1<T><<<g1, 256, 0, st>>>(Psi, ldp, Y, ldy, n, nv, n_sys, list, kblk, work);
+  const bool use_ff = ffc && sizeof(T) == sizeof(double);
+  if (use_ff) k_pc_gemm1<T, ff_if_double<T>><<<g1, 256, 0, st>>>(Psi, ldp, Y, ldy, n, nv, n_sys, list, kblk, work);
+  else k_pc_gemm1<T><<<g1, 256, 0, st>>>(Psi, ldp, Y, ldy, n, nv, n_sys, list, kblk, work);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   if (n_kb > 1) {
@@ -413,8 +422,12 @@ cudaError_t launch_pc(T* Y, long ldy, int n_sys, const int* list, const T* Psi, 
     if (err != cudaSuccess) return err;
   }
   dim3 g2((n + kGT - 1) / kGT, (n_sys + kGT - 1) / kGT);
-  k_pc_gemm2<T><<<g2, 256, 0, st>>>(Psi, ldp, Y, ldy, n, nv, n_sys, list, work, (long)n_sys, T(-1), T(1),
-                                    active);
+  if (use_ff)
+    k_pc_gemm2<T, ff_if_double<T>><<<g2, 256, 0, st>>>(Psi, ldp, Y, ldy, n, nv, n_sys, list, work, (long)n_sys,
+                                                        T(-1), T(1), active);
+  else
+    k_pc_gemm2<T><<<g2, 256, 0, st>>>(Psi, ldp, Y, ldy, n, nv, n_sys, list, work, (long)n_sys, T(-1), T(1),
+                                      active);
   return cudaGetLastError();
 }
 
@@ -620,13 +633,15 @@ WGW_INST_COCG(double)
 // Q[:, s_j] += B diag(D) B^T P[:, s_j]  (Kleinman-Bylander term, Sec. 3: V_NL = sum_p |beta_p> D_p <beta_p|).
 template <typename T>
 cudaError_t launch_kb(T* Q, const T* P, long ld, int n_sys, const int* list, const T* B, long ldb, int n, int n_proj,
-                      const T* D, T* work, cudaStream_t st) {
+                      const T* D, T* work, cudaStream_t st, bool ffc) {
+  const bool use_ff = ffc && sizeof(T) == sizeof(double);
   if (n_sys == 0 || n_proj == 0) return cudaSuccess;
   const int n_kb = pc_kblocks(n, n_sys);
   const int kblk = ((n + n_kb - 1) / n_kb + kGK - 1) / kGK * kGK;
   const int nvp = (n_proj + kGT - 1) / kGT * kGT;
   dim3 g1((n_sys + kGT - 1) / kGT, n_kb, nvp / kGT);
-  k_pc_gemm1<T><<<g1, 256, 0, st>>>(B, ldb, P, ld, n, n_proj, n_sys, list, kblk, work);
+  if (use_ff) k_pc_gemm1<T, ff_if_double<T>><<<g1, 256, 0, st>>>(B, ldb, P, ld, n, n_proj, n_sys, list, kblk, work);
+  else k_pc_gemm1<T><<<g1, 256, 0, st>>>(B, ldb, P, ld, n, n_proj, n_sys, list, kblk, work);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   const size_t slice = (size_t)nvp * n_sys;
@@ -640,17 +655,21 @@ cudaError_t launch_kb(T* Q, const T* P, long ld, int n_sys, const int* list, con
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   dim3 g2((n + kGT - 1) / kGT, (n_sys + kGT - 1) / kGT);
-  k_pc_gemm2<T><<<g2, 256, 0, st>>>(B, ldb, Q, ld, n, n_proj, n_sys, list, work, (long)n_sys, T(1), T(1), nullptr);
+  if (use_ff)
+    k_pc_gemm2<T, ff_if_double<T>><<<g2, 256, 0, st>>>(B, ldb, Q, ld, n, n_proj, n_sys, list, work, (long)n_sys,
+                                                        T(1), T(1), nullptr);
+  else
+    k_pc_gemm2<T><<<g2, 256, 0, st>>>(B, ldb, Q, ld, n, n_proj, n_sys, list, work, (long)n_sys, T(1), T(1), nullptr);
   return cudaGetLastError();
 }
 template cudaError_t launch_kb<float>(float*, const float*, long, int, const int*, const float*, long, int, int,
-                                      const float*, float*, cudaStream_t);
+                                      const float*, float*, cudaStream_t, bool);
 template cudaError_t launch_kb<double>(double*, const double*, long, int, const int*, const double*, long, int, int,
-                                       const double*, double*, cudaStream_t);
+                                       const double*, double*, cudaStream_t, bool);
 
 #define WGW_INST_LA(T)                                                                             \
   template cudaError_t launch_pc<T>(T*, long, int, const int*, const T*, long, int, int,           \
-                                    const int*, T*, cudaStream_t);                                 \
+                                    const int*, T*, cudaStream_t, bool);                           \
   template cudaError_t launch_cg_init_a<T>(const SphereTab&, int, int, const T*, T*, T*, T*, long, \
                                            const double*, CgState, cudaStream_t);                 \
   template cudaError_t launch_cg_init_b<T>(int, int, const T*, const T*, T*, long, CgState,       \

@@ -126,13 +126,19 @@ struct Prec {
 
 // Per-kernel-class timing with CUDA events recorded on the launching stream
 // (enabled by wgw_profile_enable).  Each record brackets one launch.
-constexpr int kProfKinds = 8;
+// Classes 0..7 time the FP32 kernels, 8..15 the same kernels on FP64 arrays (native FP64 or
+// float-float compute).
+constexpr int kProfKinds = 16;
 const char* const kProfNames[kProfKinds] = {"plane_g2r", "xline", "plane_r2g", "drho_xline",
-                                            "pc_project", "cg_update", "convert", "other"};
+                                            "pc_project", "cg_update", "convert", "other",
+                                            "plane_g2r_f64", "xline_f64", "plane_r2g_f64", "drho_xline_f64",
+                                            "pc_project_f64", "cg_update_f64", "convert_f64", "other_f64"};
 enum ProfKind { PK_G2R = 0, PK_XLINE, PK_R2G, PK_DRHO, PK_PC, PK_CG, PK_CONV, PK_OTHER };
 
 struct Prof {
   bool on = false;
+  unsigned mask = 0xffffu;   // classes recorded while on
+  bool f64 = true;    // storage precision of the launches being recorded
   struct Rec { int kind; cudaEvent_t a, b; double bytes, flops; };
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
@@ -146,8 +152,9 @@ struct Prof {
   }
   template <typename F>
   cudaError_t run(int kind, double by, double fl, cudaStream_t st, F&& f) {
-    if (!on) return f();
-    Rec r{kind, get(), get(), by, fl};
+    const int k = kind + (f64 ? 8 : 0);
+    if (!on || !((mask >> k) & 1u)) return f();
+    Rec r{k, get(), get(), by, fl};
     cudaEventRecord(r.a, st);
     cudaError_t err = f();
     cudaEventRecord(r.b, st);
@@ -173,6 +180,14 @@ struct Prof {
     for (cudaEvent_t e : pool) cudaEventDestroy(e);
     pool.clear();
   }
+};
+
+// Sets the precision recorded by a Prof for the lifetime of the guard.
+struct ProfPrec {
+  Prof& p;
+  bool old;
+  ProfPrec(Prof& prof, bool f64) : p(prof), old(prof.f64) { p.f64 = f64; }
+  ~ProfPrec() { p.f64 = old; }
 };
 
 }  // namespace
@@ -249,6 +264,7 @@ double t_bytes(const wgw_ctx* c, int m, int pairs) {
 template <typename T>
 int to_real(wgw_ctx* c, Prec<T>& pr, const HostSphere& sp, const T* X, long ldx, int n_sys, T* out,
             DevBuf& tbuf, cudaStream_t st) {
+  ProfPrec pp(c->prof, sizeof(T) == 8);
   const int N = c->N, NP = 2 * sp.m + 1, pairs = (n_sys + 1) / 2;
   WGW_TRY(tbuf.ensure(sizeof(cplx<T>) * (size_t)pairs * NP * N * N));
   FftCtx<T> f = pr.fft(c->plan);
@@ -265,11 +281,13 @@ int to_real(wgw_ctx* c, Prec<T>& pr, const HostSphere& sp, const T* X, long ldx,
 // P_c applied to the systems of a list (null = 0..n_list-1), timed as pc_project.
 template <typename T>
 int run_pc(wgw_ctx* c, T* Y, int n_list, const int* list, const T* Psi, const int* active, cudaStream_t st) {
+  ProfPrec pp(c->prof, sizeof(T) == 8);
   const double n = c->wfc.nrb(), nv = c->n_v;
   WGW_TRY(c->pc_work.ensure(sizeof(T) * pc_work_elems((int)n, n_list, std::max(c->n_v, c->n_proj))));
   T* work = c->pc_work.as<T>();
   WGW_CK(c->prof.run(PK_PC, 2.0 * n_list * n * sizeof(T) + n * nv * sizeof(T), 4.0 * n * nv * n_list, st, [&] {
-    return launch_pc<T>(Y, c->ld_w, n_list, list, Psi, c->ld_w, (int)n, c->n_v, active, work, st); }));
+    return launch_pc<T>(Y, c->ld_w, n_list, list, Psi, c->ld_w, (int)n, c->n_v, active, work, st,
+                        sizeof(T) == 8 && c->d.use_ff); }));
   return WGW_OK;
 }
 
@@ -277,6 +295,7 @@ int run_pc(wgw_ctx* c, T* Y, int n_list, const int* list, const T* Psi, const in
 template <typename T>
 int apply_A(wgw_ctx* c, Prec<T>& pr, const T* P, T* Q, int n_list, const int* list, const int* active,
             cudaStream_t st) {
+  ProfPrec pp(c->prof, sizeof(T) == 8);
   const int N = c->N, NP = 2 * c->wfc.m + 1, pairs = (n_list + 1) / 2;
   if (pairs == 0) return WGW_OK;
   WGW_TRY(pr.Tw.ensure(sizeof(cplx<T>) * (size_t)pairs * NP * N * N));
@@ -299,7 +318,8 @@ int apply_A(wgw_ctx* c, Prec<T>& pr, const T* P, T* Q, int n_list, const int* li
     WGW_TRY(c->pc_work.ensure(sizeof(T) * pc_work_elems(nrb, n_list, std::max(c->n_v, c->n_proj))));
     WGW_CK(c->prof.run(PK_PC, 3.0 * n_list * nrb * sizeof(T), 4.0 * nrb * c->n_proj * n_list, st, [&] {
       return launch_kb<T>(Q, P, c->ld_w, n_list, list, pr.kbB.template as<T>(), c->ld_w, nrb, c->n_proj,
-                          pr.kbD.template as<T>(), c->pc_work.template as<T>(), st); }));
+                          pr.kbD.template as<T>(), c->pc_work.template as<T>(), st,
+                          sizeof(T) == 8 && c->d.use_ff); }));
   }
   WGW_TRY(run_pc<T>(c, Q, n_list, list, pr.psi.template as<T>(), active, st));
   return WGW_OK;
@@ -325,6 +345,7 @@ int build_list(wgw_ctx* c, const int* flags, int n, int* list, cudaStream_t st, 
 // following iterations launch over that list only.
 template <typename T>
 int cg_solve(wgw_ctx* c, Prec<T>& pr, int n_sys, double tol, int max_iter, cudaStream_t st) {
+  ProfPrec pp(c->prof, sizeof(T) == 8);
   const int n = c->wfc.nrb();
   const long ld = c->ld_w;
   T* X = pr.X.template as<T>();
@@ -513,6 +534,7 @@ int build_cs_lists(wgw_ctx* c, const int* flags, int n_cs, cudaStream_t st, int*
 // COCG on (A + i w_s) x = b for n_cs complex systems (rows 2s, 2s+1 of pr.Bv / pr.X).
 template <typename T>
 int cocg_solve(wgw_ctx* c, Prec<T>& pr, int n_cs, double tol, int max_iter, cudaStream_t st) {
+  ProfPrec pp(c->prof, sizeof(T) == 8);
   const int n = c->wfc.nrb();
   const long ld = c->ld_w;
   T* X = pr.X.template as<T>();
@@ -1474,6 +1496,13 @@ int wgw_profile_enable(wgw_ctx* c, int on) {
   if (!c) return fail(WGW_ERR_ARG, "null context");
   c->prof.reset();
   c->prof.on = on != 0;
+  return WGW_OK;
+}
+
+int wgw_profile_classes(wgw_ctx* c, unsigned mask) {
+  if (!c) return fail(WGW_ERR_ARG, "null context");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  c->prof.mask = mask;
   return WGW_OK;
 }
 

@@ -19,6 +19,7 @@ WGW_ERR_CUDA, WGW_ERR_TIMEOUT, WGW_ERR_STATE = 4, 5, 6
 WGW_FP64, WGW_MIXED = 0, 1
 WGW_SPHERE_WFC, WGW_SPHERE_RHO = 0, 1
 WGW_REQ_CHI0, WGW_REQ_CHIBAR0 = 0, 1
+WGW_PROF_KINDS = 16
 
 _dp = ctypes.POINTER(ctypes.c_double)
 
@@ -88,6 +89,7 @@ def lib(path: str | None = None):
     L.wgw_apply_chibar0_dev.argtypes = L.wgw_apply_chi0_dev.argtypes
     L.wgw_apply_chibar0.argtypes = L.wgw_apply_chi0.argtypes
     L.wgw_profile_enable.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.wgw_profile_classes.argtypes = [ctypes.c_void_p, ctypes.c_uint]
     L.wgw_profile_read.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_long), _dp, _dp]
     L.wgw_profile_kind_name.restype = ctypes.c_char_p
     L.wgw_profile_kind_name.argtypes = [ctypes.c_int]
@@ -247,10 +249,20 @@ def wgw_profile_enable(ctx: Context, on: bool = True):
     _check(lib().wgw_profile_enable(ctx.handle, int(on)), "wgw_profile_enable")
 
 
+def wgw_profile_classes(ctx: Context, names=None):
+    """Record only the named classes (None = all)."""
+    if names is None:
+        mask = (1 << WGW_PROF_KINDS) - 1
+    else:
+        idx = {lib().wgw_profile_kind_name(k).decode(): k for k in range(WGW_PROF_KINDS)}
+        mask = sum(1 << idx[n] for n in names)
+    _check(lib().wgw_profile_classes(ctx.handle, mask), "wgw_profile_classes")
+
+
 def wgw_profile_read(ctx: Context) -> dict:
     """Per kernel class: {name: {ms, launches, bytes, flops}}."""
     out = {}
-    for k in range(8):
+    for k in range(WGW_PROF_KINDS):
         ms, n, by, fl = ctypes.c_double(), ctypes.c_long(), ctypes.c_double(), ctypes.c_double()
         _check(lib().wgw_profile_read(ctx.handle, k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(by),
                                       ctypes.byref(fl)), "wgw_profile_read")

@@ -40,6 +40,20 @@ std::vector<cplx<T>> twiddles(int N) {
   return tw;
 }
 
+// When set, x-line passes at N = 24 go through the register-resident body.
+bool g_reg = false;
+
+template <typename T>
+void run_xline(int q, int m, const FftPlan& pl, const std::vector<cplx<T>>& tw, cplx<T>* Tb, const XArgs<T>& a,
+               cplx<T>* B) {
+  const int N = pl.n;
+  if (g_reg && N == 24) {
+    for (int l = 0; l < N * N; ++l) xline_reg_body<T, 24, T>(q, l, m, tw.data(), Tb, a);
+    return;
+  }
+  for (int y = 0; y < N; ++y) xline_body<T>(q, y, m, pl, tw.data(), Tb, a, B, kOne);
+}
+
 // G -> r of a batch of real-basis vectors (real-space arrays out[s], N^3 each).
 template <typename T>
 void to_real(const Sph& sp, const FftPlan& pl, const std::vector<cplx<T>>& tw, const T* X, long ldx,
@@ -51,8 +65,7 @@ void to_real(const Sph& sp, const FftPlan& pl, const std::vector<cplx<T>>& tw, c
       plane_g2r_body<T>(q, hi, sp.tab(), pl, tw.data(), X, ldx, n_sys, nullptr, Tb.data(), B.data(), kOne);
   XArgs<T> a{};
   a.mode = XM_TO_REAL; a.R0 = out; a.R1 = out; a.ldr = (long)N * N * N; a.n_sys = n_sys;
-  for (int q = 0; q < pairs; ++q)
-    for (int y = 0; y < N; ++y) xline_body<T>(q, y, sp.h.m, pl, tw.data(), Tb.data(), a, B.data(), kOne);
+  for (int q = 0; q < pairs; ++q) run_xline<T>(q, sp.h.m, pl, tw, Tb.data(), a, B.data());
 }
 
 template <typename T>
@@ -67,7 +80,7 @@ void sphere_to_rb_host(const Sph& sp, int n_sys, const double* c, long ldc, cons
 // Storage type T, compute type C of the pipeline bodies (C = ff: float-float).
 template <typename T, int NC = 0, typename C = T>
 void apply_h_impl(double L, double ecut, int N, const double* vloc_c, int n_sys, const double* Xd,
-                  const double* shift, double* outd) {
+                  const double* shift, double* outd, bool reg = false) {
   Sph w, r;
   build_sphere(L, ecut, N, w.h);
   build_sphere(L, 4 * ecut, N, r.h);
@@ -90,8 +103,15 @@ void apply_h_impl(double L, double ecut, int N, const double* vloc_c, int n_sys,
       plane_g2r_body<T, NC, C>(q, hi, w.tab(), pl, tw.data(), X.data(), nw, n_sys, nullptr, Tb.data(), B.data(), kOne);
   XArgs<T> a{};
   a.mode = XM_APPLY_V; a.V = vr.data(); a.n_sys = n_sys;
-  for (int q = 0; q < pairs; ++q)
+  for (int q = 0; q < pairs; ++q) {
+    if constexpr (NC > 0) {
+      if (reg) {
+        for (int l = 0; l < N * N; ++l) xline_reg_body<T, NC, C>(q, l, w.h.m, tw.data(), Tb.data(), a);
+        continue;
+      }
+    }
     for (int y = 0; y < N; ++y) xline_body<T, NC, C>(q, y, w.h.m, pl, tw.data(), Tb.data(), a, B.data(), kOne);
+  }
   Epi<T> e{};
   e.out = out.data(); e.ldo = nw; e.pin = X.data(); e.ldp = nw; e.vcoef = T(1); e.kin = T(1);
   e.shift = sh.data(); e.n_sys = n_sys;
@@ -104,6 +124,8 @@ void apply_h_impl(double L, double ecut, int N, const double* vloc_c, int n_sys,
 }  // namespace
 
 extern "C" {
+
+void emu_set_reg_xline(int on) { g_reg = on != 0; }
 
 int emu_sphere_size(double L, double ecut, int N, int* n, int* n_pairs, int* m) {
   Sph s;
@@ -168,15 +190,15 @@ int emu_fft_position(int N, int n) {
 // float-float compute (compile-time N = 24 only).
 int emu_apply_h(double L, double ecut, int N, const double* vloc_c, int n_sys, const double* X,
                 const double* shift, double* out, int flags) {
-  const bool fp32 = flags & 1, ct = flags & 2, ffc = flags & 4;
-  if ((ct || ffc) && N != 24) return 1;
+  const bool fp32 = flags & 1, ct = flags & 2, ffc = flags & 4, reg = flags & 8;
+  if ((ct || ffc || reg) && N != 24) return 1;
   if (ffc) {
-    apply_h_impl<double, 24, ff>(L, ecut, N, vloc_c, n_sys, X, shift, out);
+    apply_h_impl<double, 24, ff>(L, ecut, N, vloc_c, n_sys, X, shift, out, reg);
   } else if (fp32) {
-    if (ct) apply_h_impl<float, 24>(L, ecut, N, vloc_c, n_sys, X, shift, out);
+    if (ct || reg) apply_h_impl<float, 24>(L, ecut, N, vloc_c, n_sys, X, shift, out, reg);
     else apply_h_impl<float>(L, ecut, N, vloc_c, n_sys, X, shift, out);
   } else {
-    if (ct) apply_h_impl<double, 24>(L, ecut, N, vloc_c, n_sys, X, shift, out);
+    if (ct || reg) apply_h_impl<double, 24>(L, ecut, N, vloc_c, n_sys, X, shift, out, reg);
     else apply_h_impl<double>(L, ecut, N, vloc_c, n_sys, X, shift, out);
   }
   return 0;
@@ -225,8 +247,7 @@ int emu_products(double L, double ecut, int N, int n_psi, const double* psi_c, i
   XArgs<double> a{};
   a.mode = XM_FROM_REAL; a.A = pr.data(); a.lda = N3; a.a_index = a_idx; a.Bm = fr.data(); a.ldb = N3;
   a.b_index = b_idx; a.n_sys = n_sys;
-  for (int q = 0; q < pairs; ++q)
-    for (int y = 0; y < N; ++y) xline_body<double>(q, y, w.h.m, pl, tw.data(), Tb.data(), a, B.data(), kOne);
+  for (int q = 0; q < pairs; ++q) run_xline<double>(q, w.h.m, pl, tw, Tb.data(), a, B.data());
   Epi<double> e{};
   e.out = out; e.ldo = nw; e.vcoef = 1.0; e.n_sys = n_sys;
   for (int q = 0; q < pairs; ++q)
@@ -264,8 +285,7 @@ int emu_drho(double L, double ecut, int N, int n_v, const double* psi_c, int n_p
   std::vector<cplx<double>> Tr((size_t)rpairs * NPr * N * N), Zp(r.h.npt_max + 1);
   XArgs<double> a{};
   a.mode = XM_FROM_REAL; a.A = D.data(); a.lda = N3; a.n_sys = n_pert;
-  for (int q = 0; q < rpairs; ++q)
-    for (int y = 0; y < N; ++y) xline_body<double>(q, y, r.h.m, pl, tw.data(), Tr.data(), a, B.data(), kOne);
+  for (int q = 0; q < rpairs; ++q) run_xline<double>(q, r.h.m, pl, tw, Tr.data(), a, B.data());
   Epi<double> e{};
   e.out = out; e.ldo = nr; e.vcoef = 1.0; e.n_sys = n_pert;
   for (int q = 0; q < rpairs; ++q)

@@ -191,7 +191,7 @@ def test_line_fft_float_float(emu, N):
     assert np.max(np.abs(out[0::2] + 1j * out[1::2] - ref)) / np.max(np.abs(ref)) < 2e-13
 
 
-@pytest.mark.parametrize("fp32", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("fp32", [0, 1, 2, 3, 4, 8, 9, 12])
 def test_apply_h_bodies_equal_dense_h(emu, cfg24, fp32):
     s = cfg24
     m = Model(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v)
@@ -212,7 +212,11 @@ def test_apply_h_bodies_equal_dense_h(emu, cfg24, fp32):
     assert np.max(np.abs(got - ref)) < tol * np.max(np.abs(ref))
 
 
-def test_products_bodies_equal_oracle(emu, cfg24):
+@pytest.mark.parametrize("reg", [0, 1])
+def test_products_bodies_equal_oracle(emu, cfg24, reg):
+    """Right-hand-side products (FROM_REAL and TO_REAL x-line passes), shared-memory or
+    register-resident x-line bodies."""
+    emu.emu_set_reg_xline(reg)
     s = cfg24
     m = Model(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v)
     mp = Maps(emu, s.L, s.ecut, s.grid)
@@ -228,9 +232,12 @@ def test_products_bodies_equal_oracle(emu, cfg24):
     for k, (a, b) in enumerate(zip(a_idx, b_idx)):
         ref = m.multiply_r(dV[:, b], s.psi_v[:, a])
         assert np.max(np.abs(got[:, k] - ref)) < 1e-13 * np.max(np.abs(ref))
+    emu.emu_set_reg_xline(0)
 
 
-def test_drho_bodies_equal_oracle(emu, cfg24):
+@pytest.mark.parametrize("reg", [0, 1])
+def test_drho_bodies_equal_oracle(emu, cfg24, reg):
+    emu.emu_set_reg_xline(reg)
     s = cfg24
     m = Model(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v)
     mw = Maps(emu, s.L, s.ecut, s.grid)
@@ -249,6 +256,7 @@ def test_drho_bodies_equal_oracle(emu, cfg24):
         rho_r = sum(m.to_r(s.psi_v[:, v], m.mw) * m.to_r(xc[:, p * s.n_v + v], m.mw) for v in range(s.n_v))
         ref = 0.75 * m.to_G(rho_r, m.mr)
         assert np.max(np.abs(got[:, p] - ref)) < 1e-13 * np.max(np.abs(ref))
+    emu.emu_set_reg_xline(0)
 
 
 def test_projector_body(emu):
