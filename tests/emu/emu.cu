@@ -54,6 +54,26 @@ void run_xline(int q, int m, const FftPlan& pl, const std::vector<cplx<T>>& tw, 
   for (int y = 0; y < N; ++y) xline_body<T>(q, y, m, pl, tw.data(), Tb, a, B, kOne);
 }
 
+template <typename T>
+void run_g2r(int q, int hi, const Sph& sp, const FftPlan& pl, const std::vector<cplx<T>>& tw, const T* X, long ldx,
+             int n_sys, cplx<T>* Tb, cplx<T>* B) {
+  if (g_reg && pl.n == 24) {
+    plane_g2r_reg_body<T, 24, T>(q, hi, sp.tab(), tw.data(), X, ldx, n_sys, nullptr, Tb, B, kOne);
+    return;
+  }
+  plane_g2r_body<T>(q, hi, sp.tab(), pl, tw.data(), X, ldx, n_sys, nullptr, Tb, B, kOne);
+}
+
+template <typename T>
+void run_r2g(int q, int hp, const Sph& sp, const FftPlan& pl, const std::vector<cplx<T>>& tw, const cplx<T>* Tb,
+             const Epi<T>& e, cplx<T>* B, cplx<T>* Zp) {
+  if (g_reg && pl.n == 24) {
+    plane_r2g_reg_body<T, 24, T>(q, hp, sp.tab(), tw.data(), Tb, e, B, Zp, kOne);
+    return;
+  }
+  plane_r2g_body<T>(q, hp, sp.tab(), pl, tw.data(), Tb, e, B, Zp, kOne);
+}
+
 // G -> r of a batch of real-basis vectors (real-space arrays out[s], N^3 each).
 template <typename T>
 void to_real(const Sph& sp, const FftPlan& pl, const std::vector<cplx<T>>& tw, const T* X, long ldx,
@@ -62,7 +82,7 @@ void to_real(const Sph& sp, const FftPlan& pl, const std::vector<cplx<T>>& tw, c
   std::vector<cplx<T>> Tb((size_t)pairs * NP * N * N), B((size_t)N * (N + 1));
   for (int q = 0; q < pairs; ++q)
     for (int hi = 0; hi < NP; ++hi)
-      plane_g2r_body<T>(q, hi, sp.tab(), pl, tw.data(), X, ldx, n_sys, nullptr, Tb.data(), B.data(), kOne);
+      run_g2r<T>(q, hi, sp, pl, tw, X, ldx, n_sys, Tb.data(), B.data());
   XArgs<T> a{};
   a.mode = XM_TO_REAL; a.R0 = out; a.R1 = out; a.ldr = (long)N * N * N; a.n_sys = n_sys;
   for (int q = 0; q < pairs; ++q) run_xline<T>(q, sp.h.m, pl, tw, Tb.data(), a, B.data());
@@ -99,8 +119,15 @@ void apply_h_impl(double L, double ecut, int N, const double* vloc_c, int n_sys,
   const int NP = 2 * w.h.m + 1, pairs = (n_sys + 1) / 2;
   std::vector<cplx<C>> Tb((size_t)pairs * NP * N * N), B((size_t)N * (N + 1)), Zp(w.h.npt_max + 1);
   for (int q = 0; q < pairs; ++q)
-    for (int hi = 0; hi < NP; ++hi)
+    for (int hi = 0; hi < NP; ++hi) {
+      if constexpr (NC > 0) {
+        if (reg) {
+          plane_g2r_reg_body<T, NC, C>(q, hi, w.tab(), tw.data(), X.data(), nw, n_sys, nullptr, Tb.data(), B.data(), kOne);
+          continue;
+        }
+      }
       plane_g2r_body<T, NC, C>(q, hi, w.tab(), pl, tw.data(), X.data(), nw, n_sys, nullptr, Tb.data(), B.data(), kOne);
+    }
   XArgs<T> a{};
   a.mode = XM_APPLY_V; a.V = vr.data(); a.n_sys = n_sys;
   for (int q = 0; q < pairs; ++q) {
@@ -116,8 +143,15 @@ void apply_h_impl(double L, double ecut, int N, const double* vloc_c, int n_sys,
   e.out = out.data(); e.ldo = nw; e.pin = X.data(); e.ldp = nw; e.vcoef = T(1); e.kin = T(1);
   e.shift = sh.data(); e.n_sys = n_sys;
   for (int q = 0; q < pairs; ++q)
-    for (int hp = 0; hp <= w.h.m; ++hp)
+    for (int hp = 0; hp <= w.h.m; ++hp) {
+      if constexpr (NC > 0) {
+        if (reg) {
+          plane_r2g_reg_body<T, NC, C>(q, hp, w.tab(), tw.data(), Tb.data(), e, B.data(), Zp.data(), kOne);
+          continue;
+        }
+      }
       plane_r2g_body<T, NC, C>(q, hp, w.tab(), pl, tw.data(), Tb.data(), e, B.data(), Zp.data(), kOne);
+    }
   for (size_t i = 0; i < out.size(); ++i) outd[i] = (double)out[i];
 }
 
@@ -251,8 +285,7 @@ int emu_products(double L, double ecut, int N, int n_psi, const double* psi_c, i
   Epi<double> e{};
   e.out = out; e.ldo = nw; e.vcoef = 1.0; e.n_sys = n_sys;
   for (int q = 0; q < pairs; ++q)
-    for (int hp = 0; hp <= w.h.m; ++hp)
-      plane_r2g_body<double>(q, hp, w.tab(), pl, tw.data(), Tb.data(), e, B.data(), Zp.data(), kOne);
+    for (int hp = 0; hp <= w.h.m; ++hp) run_r2g<double>(q, hp, w, pl, tw, Tb.data(), e, B.data(), Zp.data());
   return 0;
 }
 
@@ -276,7 +309,7 @@ int emu_drho(double L, double ecut, int N, int n_v, const double* psi_c, int n_p
   std::vector<double> acc((size_t)N * N);
   for (int q = 0; q < pairs; ++q)
     for (int hi = 0; hi < NP; ++hi)
-      plane_g2r_body<double>(q, hi, w.tab(), pl, tw.data(), Xd, nw, n_sys, nullptr, Tb.data(), B.data(), kOne);
+      run_g2r<double>(q, hi, w, pl, tw, Xd, nw, n_sys, Tb.data(), B.data());
   for (int p = 0; p < n_pert; ++p)
     for (int y = 0; y < N; ++y)
       drho_xline_body<double>(p, y, w.h.m, pl, tw.data(), Tb.data(), pr.data(), N3, n_v, n_sys, coef,
@@ -289,8 +322,7 @@ int emu_drho(double L, double ecut, int N, int n_v, const double* psi_c, int n_p
   Epi<double> e{};
   e.out = out; e.ldo = nr; e.vcoef = 1.0; e.n_sys = n_pert;
   for (int q = 0; q < rpairs; ++q)
-    for (int hp = 0; hp <= r.h.m; ++hp)
-      plane_r2g_body<double>(q, hp, r.tab(), pl, tw.data(), Tr.data(), e, B.data(), Zp.data(), kOne);
+    for (int hp = 0; hp <= r.h.m; ++hp) run_r2g<double>(q, hp, r, pl, tw, Tr.data(), e, B.data(), Zp.data());
   return 0;
 }
 
