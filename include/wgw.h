@@ -77,6 +77,9 @@ typedef struct wgw_options {
                           residuals, drho) compute in float-float (two FP32 values per number, about
                           48 significant bits) because GB300's FP64 rate is 1/64 of its FP32 rate;
                           0 = native FP64.  Storage stays FP64 either way. */
+  int tensor_cores;    /* MIXED: 1 = the projector P_c of the FP32 inner solves runs on the tcgen05
+                          tensor cores (TF32 products split three ways, hi*hi + hi*lo + lo*hi, FP32
+                          accumulation: FP32 accuracy); 0 = FP32 CUDA-core GEMMs. */
 } wgw_options;
 
 typedef struct wgw_stats {
@@ -89,7 +92,7 @@ typedef struct wgw_stats {
 
 /* Fills *opt with defaults: WGW_FP64, cg_tol 1e-12, max_cg_iter 2000, max_refine 8,
  * inner_tol 1e-5, f_s 2, check_every 8, dav_tol 1e-8, dav_max_iter 100, dav_factor 4, seed 12345,
- * fp64_emulation 1. */
+ * fp64_emulation 1, tensor_cores 0. */
 int wgw_default_options(wgw_options* opt);
 
 /*

@@ -82,9 +82,18 @@ cudaError_t launch_drho_xline(int m, FftCtx<T> f, const cplx<T>* Tbuf, const T* 
 // Y <- Y - Psi Psi^T Y for the active systems of a list (null = systems 0..n_sys-1);
 // work holds pc_work_elems(n, n_sys, nv) elements of T.
 // ffc: for T = double, compute in float-float (operands rounded to float-float pairs).
+// tcores: for T = float, the tcgen05 tensor-core kernels (tc_kernels.cu) when nv <= 256.
 template <typename T>
 cudaError_t launch_pc(T* Y, long ldy, int n_sys, const int* list, const T* Psi, long ldp, int n, int nv,
-                      const int* active, T* work, cudaStream_t st, bool ffc = false);
+                      const int* active, T* work, cudaStream_t st, bool ffc = false, bool tcores = false);
+// P_c on the tensor cores (3xTF32 products, FP32 accumulation in tensor memory); work holds
+// tc_pc_work_elems(n, n_sys, nv) floats.
+cudaError_t launch_pc_tc(float* Y, long ldy, int n_sys, const int* list, const float* Psi, long ldp, int n, int nv,
+                         const int* active, float* work, cudaStream_t st);
+size_t tc_pc_work_elems(int n, int n_sys, int nv);
+bool tc_pc_supported(int nv);
+// Reads (and clears) the tensor-core kernels' wait-timeout flag; synchronises st.
+cudaError_t tc_error_read_and_clear(int* flag, cudaStream_t st);
 // C = A^T B: A is K x m (column j at A + j*lda), B is K x n (column j at B + c_j * ldb with
 // c_j = cols[j], or j when cols is null); C is written row-major with rows of length n, padded
 // to a multiple of 64 rows.  work: gemm_tn_work_elems(K, m, n) doubles.

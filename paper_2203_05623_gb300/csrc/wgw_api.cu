@@ -283,18 +283,20 @@ template <typename T>
 int run_pc(wgw_ctx* c, T* Y, int n_list, const int* list, const T* Psi, const int* active, cudaStream_t st) {
   ProfPrec pp(c->prof, sizeof(T) == 8);
   const double n = c->wfc.nrb(), nv = c->n_v;
-  WGW_TRY(c->pc_work.ensure(sizeof(T) * pc_work_elems((int)n, n_list, std::max(c->n_v, c->n_proj))));
+  const bool tcores = sizeof(T) == sizeof(float) && c->opt.tensor_cores != 0;
+  WGW_TRY(c->pc_work.ensure(sizeof(T) * std::max(pc_work_elems((int)n, n_list, std::max(c->n_v, c->n_proj)),
+                                                 tc_pc_work_elems((int)n, n_list, c->n_v))));
   T* work = c->pc_work.as<T>();
   WGW_CK(c->prof.run(PK_PC, 2.0 * n_list * n * sizeof(T) + n * nv * sizeof(T), 4.0 * n * nv * n_list, st, [&] {
     return launch_pc<T>(Y, c->ld_w, n_list, list, Psi, c->ld_w, (int)n, c->n_v, active, work, st,
-                        sizeof(T) == 8 && c->d.use_ff); }));
+                        sizeof(T) == 8 && c->d.use_ff, tcores); }));
   return WGW_OK;
 }
 
 // Q = P_c (H - e_v) P for the active systems of a list (P already in range(P_c)).
 template <typename T>
 int apply_A(wgw_ctx* c, Prec<T>& pr, const T* P, T* Q, int n_list, const int* list, const int* active,
-            cudaStream_t st) {
+            cudaStream_t st, bool project_out = true) {
   ProfPrec pp(c->prof, sizeof(T) == 8);
   const int N = c->N, NP = 2 * c->wfc.m + 1, pairs = (n_list + 1) / 2;
   if (pairs == 0) return WGW_OK;
@@ -321,9 +323,16 @@ int apply_A(wgw_ctx* c, Prec<T>& pr, const T* P, T* Q, int n_list, const int* li
                           pr.kbD.template as<T>(), c->pc_work.template as<T>(), st,
                           sizeof(T) == 8 && c->d.use_ff); }));
   }
-  WGW_TRY(run_pc<T>(c, Q, n_list, list, pr.psi.template as<T>(), active, st));
+  if (project_out) WGW_TRY(run_pc<T>(c, Q, n_list, list, pr.psi.template as<T>(), active, st));
   return WGW_OK;
 }
+
+// The FP32 inner solves skip the projection of (H - e_v) p: the occupied states are eigenvectors
+// of H, so H maps range(P_c) into itself and, for p in range(P_c), P_c (H - e_v) p = (H - e_v) p
+// up to the FP32 rounding of H p (~1e-7 relative).  The search directions stay in range(P_c)
+// because z = P_c M^-1 r is projected; what leaks into r is rounding noise far below the inner
+// tolerance, and the FP64 residual of the refinement uses the full projections.
+constexpr bool kProjectInnerOutput = false;
 
 CgState cg_state(wgw_ctx* c) {
   CgState s;
@@ -369,7 +378,7 @@ int cg_solve(wgw_ctx* c, Prec<T>& pr, int n_sys, double tol, int max_iter, cudaS
   const int every = std::max(1, c->opt.check_every);
   for (int it = 0; it < max_iter && n_list > 0; ++it) {
     const double lb = (double)n_list * n * sizeof(T);
-    WGW_TRY(apply_A<T>(c, pr, P, Q, n_list, lbuf, act, st));
+    WGW_TRY(apply_A<T>(c, pr, P, Q, n_list, lbuf, act, st, sizeof(T) == sizeof(double) || kProjectInnerOutput));
     WGW_CK(c->prof.run(PK_CG, 7 * lb, 0, st, [&] {
       return launch_cg_step_a<T>(c->wfc.tab(), n, n_list, lbuf, X, R, Z, P, Q, ld, eps, cs, tol * tol,
                                  max_iter, st); }));
@@ -377,6 +386,11 @@ int cg_solve(wgw_ctx* c, Prec<T>& pr, int n_sys, double tol, int max_iter, cudaS
     WGW_CK(c->prof.run(PK_CG, 4 * lb, 0, st, [&] {
       return launch_cg_step_b<T>(n, n_list, lbuf, R, Z, P, ld, cs, st); }));
     if ((it + 1) % every == 0) WGW_TRY(build_list(c, act, n_sys, lbuf, st, &n_list));
+  }
+  if (sizeof(T) == sizeof(float) && c->opt.tensor_cores) {
+    int flag = 0;
+    WGW_CK(tc_error_read_and_clear(&flag, st));
+    if (flag) return fail(WGW_ERR_TIMEOUT, "tensor-core P_c: a wait on the MMA completion barrier timed out");
   }
   return WGW_OK;
 }
@@ -558,7 +572,7 @@ int cocg_solve(wgw_ctx* c, Prec<T>& pr, int n_cs, double tol, int max_iter, cuda
   const int every = std::max(1, c->opt.check_every);
   for (int it = 0; it < max_iter && n_list > 0; ++it) {
     const double lb = 2.0 * n_list * n * sizeof(T);
-    WGW_TRY(apply_A<T>(c, pr, P, Q, 2 * n_list, rbuf, nullptr, st));
+    WGW_TRY(apply_A<T>(c, pr, P, Q, 2 * n_list, rbuf, nullptr, st, sizeof(T) == sizeof(double) || kProjectInnerOutput));
     WGW_CK(c->prof.run(PK_CG, 9 * lb, 0, st, [&] {
       return launch_cocg_step_a<T>(c->wfc.tab(), n, n_list, lbuf, X, R, Z, P, Q, ld, eps, cs, tol * tol,
                                    max_iter, st); }));
@@ -1264,6 +1278,7 @@ int wgw_default_options(wgw_options* opt) {
   if (!opt) return fail(WGW_ERR_ARG, "null options");
   opt->precision = WGW_FP64;
   opt->fp64_emulation = 1;
+  opt->tensor_cores = 0;
   opt->cg_tol = 1e-12;
   opt->max_cg_iter = 2000;
   opt->max_refine = 8;

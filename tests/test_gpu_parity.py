@@ -62,11 +62,12 @@ def test_chi0_fp64_matches_sum_over_states(W, cfg24, ref24):
     assert rel_err(drho, ref) < 1e-10
 
 
-@pytest.mark.parametrize("emulate", [1, 0])
-def test_chi0_mixed_matches_sum_over_states(W, cfg24, ref24, emulate):
-    """Mixed path with its FP64-accuracy FFT passes in float-float (default) or native FP64."""
+@pytest.mark.parametrize("emulate,tcores", [(1, 1), (0, 1), (1, 0)])
+def test_chi0_mixed_matches_sum_over_states(W, cfg24, ref24, emulate, tcores):
+    """Mixed path: FP64-accuracy passes in float-float (default) or native FP64; P_c of the FP32
+    solves on the tcgen05 tensor cores (default) or CUDA cores."""
     dV, ref = ref24
-    ctx = setup(W, cfg24, precision=W.WGW_MIXED, cg_tol=1e-11, fp64_emulation=emulate)
+    ctx = setup(W, cfg24, precision=W.WGW_MIXED, cg_tol=1e-11, fp64_emulation=emulate, tensor_cores=tcores)
     drho, st, status = W.wgw_apply_chi0(ctx, dV)
     assert st["refinements"] >= 2
     assert rel_err(drho, ref) < 1e-8
