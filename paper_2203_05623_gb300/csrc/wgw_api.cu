@@ -378,14 +378,20 @@ int cg_solve(wgw_ctx* c, Prec<T>& pr, int n_sys, double tol, int max_iter, cudaS
   const int every = std::max(1, c->opt.check_every);
   for (int it = 0; it < max_iter && n_list > 0; ++it) {
     const double lb = (double)n_list * n * sizeof(T);
-    WGW_TRY(apply_A<T>(c, pr, P, Q, n_list, lbuf, act, st, sizeof(T) == sizeof(double) || kProjectInnerOutput));
+    const bool proj_q = sizeof(T) == sizeof(double) || kProjectInnerOutput;
+    WGW_TRY(apply_A<T>(c, pr, P, Q, n_list, lbuf, act, st, proj_q));
     WGW_CK(c->prof.run(PK_CG, 7 * lb, 0, st, [&] {
       return launch_cg_step_a<T>(c->wfc.tab(), n, n_list, lbuf, X, R, Z, P, Q, ld, eps, cs, tol * tol,
                                  max_iter, st); }));
     WGW_TRY(run_pc<T>(c, Z, n_list, lbuf, Psi, act, st));
     WGW_CK(c->prof.run(PK_CG, 4 * lb, 0, st, [&] {
       return launch_cg_step_b<T>(n, n_list, lbuf, R, Z, P, ld, cs, st); }));
-    if ((it + 1) % every == 0) WGW_TRY(build_list(c, act, n_sys, lbuf, st, &n_list));
+    if ((it + 1) % every == 0) {
+      // Without the projection of q, rounding noise collects in the occupied part of r, where
+      // the iteration cannot remove it; clear it before the convergence test settles on it.
+      if (!proj_q) WGW_TRY(run_pc<T>(c, R, n_list, lbuf, Psi, act, st));
+      WGW_TRY(build_list(c, act, n_sys, lbuf, st, &n_list));
+    }
   }
   if (sizeof(T) == sizeof(float) && c->opt.tensor_cores) {
     int flag = 0;
@@ -572,14 +578,18 @@ int cocg_solve(wgw_ctx* c, Prec<T>& pr, int n_cs, double tol, int max_iter, cuda
   const int every = std::max(1, c->opt.check_every);
   for (int it = 0; it < max_iter && n_list > 0; ++it) {
     const double lb = 2.0 * n_list * n * sizeof(T);
-    WGW_TRY(apply_A<T>(c, pr, P, Q, 2 * n_list, rbuf, nullptr, st, sizeof(T) == sizeof(double) || kProjectInnerOutput));
+    const bool proj_q = sizeof(T) == sizeof(double) || kProjectInnerOutput;
+    WGW_TRY(apply_A<T>(c, pr, P, Q, 2 * n_list, rbuf, nullptr, st, proj_q));
     WGW_CK(c->prof.run(PK_CG, 9 * lb, 0, st, [&] {
       return launch_cocg_step_a<T>(c->wfc.tab(), n, n_list, lbuf, X, R, Z, P, Q, ld, eps, cs, tol * tol,
                                    max_iter, st); }));
     WGW_TRY(run_pc<T>(c, Z, 2 * n_list, rbuf, Psi, nullptr, st));
     WGW_CK(c->prof.run(PK_CG, 4 * lb, 0, st, [&] {
       return launch_cocg_step_b<T>(n, n_list, lbuf, R, Z, P, ld, cs, st); }));
-    if ((it + 1) % every == 0) WGW_TRY(build_cs_lists(c, cs.active, n_cs, st, &n_list));
+    if ((it + 1) % every == 0) {
+      if (!proj_q) WGW_TRY(run_pc<T>(c, R, 2 * n_list, rbuf, Psi, nullptr, st));   // as in cg_solve
+      WGW_TRY(build_cs_lists(c, cs.active, n_cs, st, &n_list));
+    }
   }
   return WGW_OK;
 }
