@@ -13,8 +13,9 @@
 // whole plane (plane kernel), then along x for each (y, z) on the 2m+1
 // non-zero h (x-line kernel).  Between the kernels the data of one pair is
 // T[h + m][y][z] (2m+1 planes of N x N complex, y and z in digit-reversed
-// position).  Real-space arrays are [y][z][x] with all three coordinates in
-// digit-reversed position.
+// position).  Real-space arrays are [y][x][z] with all three coordinates in
+// digit-reversed position (z fastest, so that threads that own consecutive
+// x-lines (y, z) read and write consecutive addresses for every x).
 //
 // Every body has a storage type T (of the sphere vectors and real-space arrays
 // in global memory) and a compute type C (of the butterflies, the twiddles,
@@ -150,7 +151,7 @@ enum XMode : int {
 template <typename T>
 struct XArgs {
   int mode;
-  const T* V;              // APPLY_V: real-space potential [y][z][x]
+  const T* V;              // APPLY_V: real-space potential [y][x][z]
   T* R0; T* R1;            // TO_REAL outputs (R1 may be null)
   long ldr;                // stride between real-space arrays of successive systems
   const T* A; const T* Bm; // FROM_REAL factors (Bm may be null = 1)
@@ -170,14 +171,14 @@ WGW_HD void xline_body(int pair, int y, int m, const FftPlan& pl, const cplx<C>*
   pair_members(a.list, a.n_sys, pair, s0, s1);
   const bool has1 = s1 >= 0;
   cplx<C>* tp = Tbuf + (size_t)pair * NP * N * N + (size_t)y * N;   // T[hi][y][z] at tp[hi*N*N + z]
-  const size_t slab = (size_t)y * N * N;                              // real-space [y][z][x] offset
+  const size_t slab = (size_t)y * N * N;                              // real-space [y][x][z] offset
   if (a.mode == XM_FROM_REAL) {
     const T* A0 = a.A + (size_t)(a.a_index ? a.a_index[s0] : s0) * a.lda + slab;
     const T* A1 = has1 ? a.A + (size_t)(a.a_index ? a.a_index[s1] : s1) * a.lda + slab : nullptr;
     const T* B0 = a.Bm ? a.Bm + (size_t)(a.b_index ? a.b_index[s0] : s0) * a.ldb + slab : nullptr;
     const T* B1 = (a.Bm && has1) ? a.Bm + (size_t)(a.b_index ? a.b_index[s1] : s1) * a.ldb + slab : nullptr;
     for (int i = th.tid; i < N * N; i += th.nth) {
-      const int z = i / N, x = i % N;
+      const int x = i / N, z = i % N;
       C re = C(A0[i]), im = A1 ? C(A1[i]) : C(0);
       if (B0) re = re * C(B0[i]);
       if (B1) im = im * C(B1[i]);
@@ -199,7 +200,7 @@ WGW_HD void xline_body(int pair, int y, int m, const FftPlan& pl, const cplx<C>*
     T* r0 = a.R0 + (size_t)s0 * a.ldr + slab;
     T* r1 = (has1 && a.R1) ? a.R1 + (size_t)s1 * a.ldr + slab : nullptr;
     for (int i = th.tid; i < N * N; i += th.nth) {
-      const int z = i / N, x = i % N;
+      const int x = i / N, z = i % N;
       const cplx<C> v = S[z * LS + x];
       r0[i] = T(v.re);
       if (r1) r1[i] = T(v.im);
@@ -209,7 +210,7 @@ WGW_HD void xline_body(int pair, int y, int m, const FftPlan& pl, const cplx<C>*
   if (a.mode == XM_APPLY_V) {
     const T* v = a.V + slab;
     for (int i = th.tid; i < N * N; i += th.nth) {
-      const int z = i / N, x = i % N;
+      const int x = i / N, z = i % N;
       S[z * LS + x] = cscale(S[z * LS + x], C(v[i]));
     }
     WGW_SYNC();
@@ -232,7 +233,7 @@ WGW_HD void xline_reg_body(int pair, int l, int m, const cplx<C>* tw, cplx<C>* T
   pair_members(a.list, a.n_sys, pair, s0, s1);
   const bool has1 = s1 >= 0;
   cplx<C>* tp = Tbuf + (size_t)pair * NP * N * N + l;   // T[hi][y][z] at tp[hi * N * N]
-  const size_t line = (size_t)l * N;                     // real-space [y][z][x] offset
+  const size_t line = (size_t)(l / N) * N * N + (l % N); // real-space [y][x][z]: element x at line + x N
   cplx<C> v[N];
   if (a.mode == XM_FROM_REAL) {
     const T* A0 = a.A + (size_t)(a.a_index ? a.a_index[s0] : s0) * a.lda + line;
@@ -241,9 +242,9 @@ WGW_HD void xline_reg_body(int pair, int l, int m, const cplx<C>* tw, cplx<C>* T
     const T* B1 = (a.Bm && has1) ? a.Bm + (size_t)(a.b_index ? a.b_index[s1] : s1) * a.ldb + line : nullptr;
 #pragma unroll
     for (int x = 0; x < N; ++x) {
-      C re = C(A0[x]), im = A1 ? C(A1[x]) : C(0);
-      if (B0) re = re * C(B0[x]);
-      if (B1) im = im * C(B1[x]);
+      C re = C(A0[x * N]), im = A1 ? C(A1[x * N]) : C(0);
+      if (B0) re = re * C(B0[x * N]);
+      if (B1) im = im * C(B1[x * N]);
       v[x] = mk<C>(re, im);
     }
   } else {
@@ -261,15 +262,15 @@ WGW_HD void xline_reg_body(int pair, int l, int m, const cplx<C>* tw, cplx<C>* T
     T* r1 = (has1 && a.R1) ? a.R1 + (size_t)s1 * a.ldr + line : nullptr;
 #pragma unroll
     for (int x = 0; x < N; ++x) {
-      r0[x] = T(v[x].re);
-      if (r1) r1[x] = T(v[x].im);
+      r0[x * N] = T(v[x].re);
+      if (r1) r1[x * N] = T(v[x].im);
     }
     return;
   }
   if (a.mode == XM_APPLY_V) {
     const T* vr = a.V + line;
 #pragma unroll
-    for (int x = 0; x < N; ++x) v[x] = cscale(v[x], C(vr[x]));
+    for (int x = 0; x < N; ++x) v[x] = cscale(v[x], C(vr[x * N]));
   }
   reg_dit<C, N, cplan(N).nst - 1, -1>(v, tw);
 #pragma unroll
@@ -456,7 +457,7 @@ WGW_HD void plane_r2g_reg_body(int pair, int hp, const SphereTab& sp, const cplx
 
 // Density response of perturbation p on slab y (Eq. dfpt, one spin channel
 // times f_s folded into coef):
-//   D_p[y][z][x] = coef * sum_{v} psi_v(r) x_{(v,p)}(r),
+//   D_p[y][x][z] = coef * sum_{v} psi_v(r) x_{(v,p)}(r),
 // with systems ordered s = p * n_v + v and x_s(r) obtained from T by the
 // G -> r pass along x.  The sum runs over v in a fixed order, so the result
 // does not depend on how many perturbations share the launch.
@@ -484,8 +485,8 @@ WGW_HD void drho_xline_body(int p, int y, int m, const FftPlan& pl, const cplx<C
     const bool ub = sb >= s_lo && sb < s_hi && sb < n_sys;
     const T* pa = psi_r + (size_t)(sa - s_lo) * ldpsi + slab;
     const T* pb = psi_r + (size_t)(sb - s_lo) * ldpsi + slab;
-    for (int i = th.tid; i < N * N; i += th.nth) {
-      const cplx<C> v = S[(i / N) * LS + (i % N)];
+    for (int i = th.tid; i < N * N; i += th.nth) {   // i = x N + z
+      const cplx<C> v = S[(i % N) * LS + (i / N)];
       C a = acc[i];
       if (ua) a += C(pa[i]) * v.re;
       if (ub) a += C(pb[i]) * v.im;
