@@ -296,6 +296,9 @@ def main():
         "kernel_share": {k: round(v["ms"] / max(sum(q["ms"] for q in prof_all.values()), 1e-9), 4)
                          for k, v in sorted(prof_all.items(), key=lambda kv: -kv[1]["ms"]) if v["launches"]},
         "kernel_share_from": "one untimed step after warm-up with every launch bracketed by CUDA events",
+        "kernel_gbs": {k: round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1)
+                       for k, v in sorted(prof_all.items(), key=lambda kv: -kv[1]["ms"]) if v["ms"] > 0},
+        "kernel_gbs_what": "algorithmic bytes of each class (the kernels' own inputs and outputs) / its event time",
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),
     }

@@ -156,6 +156,7 @@ struct SphereTab {
   const int* plane_off;   // 2m+2 entries
   const int2* ent;        // plane_off[2m+1] entries
   const double* g2;       // 0.5 |G|^2 per real-basis element (length 2 n_pairs + 1)
+  const float* g2f;       // the same rounded to FP32 (for the FP32 kernels)
 };
 
 }  // namespace wgw

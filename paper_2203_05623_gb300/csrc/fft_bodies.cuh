@@ -296,11 +296,17 @@ struct Epi {
   const int* list;         // system list (null = identity)
 };
 
+// 0.5 |G|^2 of element i in compute type C (FP32 kernels read the FP32 copy).
+template <typename C>
+WGW_HD C g2_as(const SphereTab& sp, int i) { return C(sp.g2[i]); }
+template <>
+WGW_HD float g2_as<float>(const SphereTab& sp, int i) { return sp.g2f[i]; }
+
 template <typename T, typename C>
 WGW_HD void epi_store(const Epi<T>& e, const SphereTab& sp, int s, int i, C f) {
   C v = C(e.vcoef) * f;
   if (e.pin) {
-    C c = C(e.kin) * C(sp.g2[i]);
+    C c = C(e.kin) * g2_as<C>(sp, i);
     if (e.shift) c += C(e.shift[s]);
     v += c * C(e.pin[(size_t)s * e.ldp + i]);
   }

@@ -24,6 +24,7 @@ struct SphereHostTables {
   std::vector<int> plane_off;
   std::vector<int2> ent;
   std::vector<double> g2;    // 0.5 |G|^2 per real-basis element
+  std::vector<float> g2f;    // g2 rounded to FP32
   std::vector<double> vsqrt; // sqrt(4 pi)/|G| per canonical index (0 at G = 0)
   int nrb() const { return 2 * n_pairs + 1; }
 };
@@ -73,6 +74,7 @@ inline void build_sphere(double L, double ecut, int N, SphereHostTables& s) {
   s.n_pairs = (int)s.pos.size() - 1;
   s.g2.assign(s.nrb(), 0.0);
   for (int j = 1; j <= s.n_pairs; ++j) s.g2[2 * j - 1] = s.g2[2 * j] = 0.5 * b * b * pts[s.pos[j]].n2;
+  s.g2f.assign(s.g2.begin(), s.g2.end());
   s.vsqrt.assign(s.n, 0.0);
   for (int i = 0; i < s.n; ++i)
     if (pts[i].n2 > 0) s.vsqrt[i] = std::sqrt(4.0 * M_PI) / (b * std::sqrt((double)pts[i].n2));

@@ -67,18 +67,19 @@ long pad32(long n) { return (n + 31) / 32 * 32; }
 
 // A plane-wave sphere (host tables from tables.h) with device copies.
 struct HostSphere : SphereHostTables {
-  DevBuf d_off, d_ent, d_g2, d_i0, d_pos, d_neg, d_vsqrt;
+  DevBuf d_off, d_ent, d_g2, d_g2f, d_i0, d_pos, d_neg, d_vsqrt;
   SphereTab tab() const {
     SphereTab t;
     t.m = m; t.n_pairs = n_pairs;
     t.plane_off = d_off.as<int>(); t.ent = d_ent.as<int2>(); t.g2 = d_g2.as<double>();
+    t.g2f = d_g2f.as<float>();
     return t;
   }
   RbMap map() const {
     RbMap r; r.n_pairs = n_pairs; r.i0 = d_i0.as<int>(); r.pos = d_pos.as<int>(); r.neg = d_neg.as<int>();
     return r;
   }
-  void release() { d_off.release(); d_ent.release(); d_g2.release(); d_i0.release(); d_pos.release(); d_neg.release(); d_vsqrt.release(); }
+  void release() { d_off.release(); d_ent.release(); d_g2.release(); d_g2f.release(); d_i0.release(); d_pos.release(); d_neg.release(); d_vsqrt.release(); }
 };
 
 template <typename T>
@@ -92,6 +93,7 @@ int upload_sphere(HostSphere& s) {
   WGW_TRY(upload(s.d_off, s.plane_off));
   WGW_TRY(upload(s.d_ent, s.ent));
   WGW_TRY(upload(s.d_g2, s.g2));
+  WGW_TRY(upload(s.d_g2f, s.g2f));
   WGW_TRY(upload(s.d_i0, std::vector<int>{s.i0}));
   WGW_TRY(upload(s.d_pos, s.pos));
   WGW_TRY(upload(s.d_neg, s.neg));

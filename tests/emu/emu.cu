@@ -25,6 +25,7 @@ struct Sph {
     SphereTab t;
     t.m = h.m; t.n_pairs = h.n_pairs; t.plane_off = h.plane_off.data(); t.ent = h.ent.data();
     t.g2 = h.g2.data();
+    t.g2f = h.g2f.data();
     return t;
   }
   RbMap map() const {
