@@ -29,6 +29,18 @@
 
 namespace wgw {
 
+// Real-space arrays of the float-float passes hold float-float pairs in the 8-byte slots of their
+// FP64 buffers (produced and consumed only by those passes), so that no element is converted on
+// the FP64 pipe; every other pass stores T.
+template <typename C, typename T>
+WGW_HD C rs_ld(const T* p, size_t i) { return C(p[i]); }
+template <>
+WGW_HD ff rs_ld<ff, double>(const double* p, size_t i) { return reinterpret_cast<const ff*>(p)[i]; }
+template <typename C, typename T>
+WGW_HD void rs_st(T* p, size_t i, C v) { p[i] = T(v); }
+template <>
+WGW_HD void rs_st<ff, double>(double* p, size_t i, ff v) { reinterpret_cast<ff*>(p)[i] = v; }
+
 // Strided batch of real-basis vectors: system s at base + s * ld.
 template <typename T>
 struct VecBatch {
@@ -179,9 +191,9 @@ WGW_HD void xline_body(int pair, int y, int m, const FftPlan& pl, const cplx<C>*
     const T* B1 = (a.Bm && has1) ? a.Bm + (size_t)(a.b_index ? a.b_index[s1] : s1) * a.ldb + slab : nullptr;
     for (int i = th.tid; i < N * N; i += th.nth) {
       const int x = i / N, z = i % N;
-      C re = C(A0[i]), im = A1 ? C(A1[i]) : C(0);
-      if (B0) re = re * C(B0[i]);
-      if (B1) im = im * C(B1[i]);
+      C re = rs_ld<C>(A0, i), im = A1 ? rs_ld<C>(A1, i) : C(0);
+      if (B0) re = re * rs_ld<C>(B0, i);
+      if (B1) im = im * rs_ld<C>(B1, i);
       S[z * LS + x] = mk<C>(re, im);
     }
     WGW_SYNC();
@@ -202,8 +214,8 @@ WGW_HD void xline_body(int pair, int y, int m, const FftPlan& pl, const cplx<C>*
     for (int i = th.tid; i < N * N; i += th.nth) {
       const int x = i / N, z = i % N;
       const cplx<C> v = S[z * LS + x];
-      r0[i] = T(v.re);
-      if (r1) r1[i] = T(v.im);
+      rs_st<C>(r0, i, v.re);
+      if (r1) rs_st<C>(r1, i, v.im);
     }
     return;
   }
@@ -211,7 +223,7 @@ WGW_HD void xline_body(int pair, int y, int m, const FftPlan& pl, const cplx<C>*
     const T* v = a.V + slab;
     for (int i = th.tid; i < N * N; i += th.nth) {
       const int x = i / N, z = i % N;
-      S[z * LS + x] = cscale(S[z * LS + x], C(v[i]));
+      S[z * LS + x] = cscale(S[z * LS + x], rs_ld<C>(v, i));
     }
     WGW_SYNC();
   }
@@ -242,9 +254,9 @@ WGW_HD void xline_reg_body(int pair, int l, int m, const cplx<C>* tw, cplx<C>* T
     const T* B1 = (a.Bm && has1) ? a.Bm + (size_t)(a.b_index ? a.b_index[s1] : s1) * a.ldb + line : nullptr;
 #pragma unroll
     for (int x = 0; x < N; ++x) {
-      C re = C(A0[x * N]), im = A1 ? C(A1[x * N]) : C(0);
-      if (B0) re = re * C(B0[x * N]);
-      if (B1) im = im * C(B1[x * N]);
+      C re = rs_ld<C>(A0, (size_t)x * N), im = A1 ? rs_ld<C>(A1, (size_t)x * N) : C(0);
+      if (B0) re = re * rs_ld<C>(B0, (size_t)x * N);
+      if (B1) im = im * rs_ld<C>(B1, (size_t)x * N);
       v[x] = mk<C>(re, im);
     }
   } else {
@@ -262,15 +274,15 @@ WGW_HD void xline_reg_body(int pair, int l, int m, const cplx<C>* tw, cplx<C>* T
     T* r1 = (has1 && a.R1) ? a.R1 + (size_t)s1 * a.ldr + line : nullptr;
 #pragma unroll
     for (int x = 0; x < N; ++x) {
-      r0[x * N] = T(v[x].re);
-      if (r1) r1[x * N] = T(v[x].im);
+      rs_st<C>(r0, (size_t)x * N, v[x].re);
+      if (r1) rs_st<C>(r1, (size_t)x * N, v[x].im);
     }
     return;
   }
   if (a.mode == XM_APPLY_V) {
     const T* vr = a.V + line;
 #pragma unroll
-    for (int x = 0; x < N; ++x) v[x] = cscale(v[x], C(vr[x * N]));
+    for (int x = 0; x < N; ++x) v[x] = cscale(v[x], rs_ld<C>(vr, (size_t)x * N));
   }
   reg_dit<C, N, cplan(N).nst - 1, -1>(v, tw);
 #pragma unroll
@@ -494,14 +506,14 @@ WGW_HD void drho_xline_body(int p, int y, int m, const FftPlan& pl, const cplx<C
     for (int i = th.tid; i < N * N; i += th.nth) {   // i = x N + z
       const cplx<C> v = S[(i % N) * LS + (i / N)];
       C a = acc[i];
-      if (ua) a += C(pa[i]) * v.re;
-      if (ub) a += C(pb[i]) * v.im;
+      if (ua) a += rs_ld<C>(pa, i) * v.re;
+      if (ub) a += rs_ld<C>(pb, i) * v.im;
       acc[i] = a;
     }
     WGW_SYNC();
   }
   T* d = D + (size_t)p * ldd + slab;
-  for (int i = th.tid; i < N * N; i += th.nth) d[i] = T(C(coef) * acc[i]);
+  for (int i = th.tid; i < N * N; i += th.nth) rs_st<C>(d, i, C(coef) * acc[i]);
 }
 
 }  // namespace wgw

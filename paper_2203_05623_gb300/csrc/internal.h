@@ -188,6 +188,8 @@ cudaError_t launch_add_to(int n_sys, int n, const T* x, long ldx, double* y, lon
 // Per-system norms ||x_s||^2 into out[s].
 template <typename T>
 cudaError_t launch_norm2(int n_sys, int n, const T* x, long ld, double* out, cudaStream_t st);
+// out[i] = in[i] as a float-float pair stored in the 8-byte slot i of out.
+cudaError_t launch_to_ff(size_t n, const double* in, double* out, cudaStream_t st);
 // Count of nonzero entries of flags[0..n) into *out (one block).
 cudaError_t launch_count(const int* flags, int n, int* out, cudaStream_t st);
 

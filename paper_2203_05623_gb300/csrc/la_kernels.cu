@@ -468,6 +468,17 @@ cudaError_t launch_gemm_nn(const double* A, long lda, int n, int k, const double
   return cudaGetLastError();
 }
 
+__global__ void k_to_ff(size_t n, const double* __restrict__ in, ff* __restrict__ out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = ff(in[i]);
+}
+
+cudaError_t launch_to_ff(size_t n, const double* in, double* out, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_to_ff<<<(int)std::min<size_t>((n + 255) / 256, 8192), 256, 0, st>>>(n, in, reinterpret_cast<ff*>(out));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_build_list(const int* active, int n_sys, int* list, int* count, cudaStream_t st) {
   k_build_list<<<1, 1024, 0, st>>>(active, n_sys, list, count);
   return cudaGetLastError();

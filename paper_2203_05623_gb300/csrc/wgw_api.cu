@@ -110,9 +110,13 @@ struct Prec {
   DevBuf psi;       // occupied states, real basis, n_v x ld_w
   DevBuf psi_r;     // occupied states in real space, n_v x N^3
   DevBuf v_r;       // V_loc in real space
+  DevBuf psi_r_ff, v_r_ff;   // T = double: the same as float-float pairs, for the float-float passes
   // work
   DevBuf X, R, Z, P, Q, Bv, Tw, shift;
   DevBuf kbB, kbD;  // KB projectors in the real basis (n_proj x ld_w) and couplings
+  // Real-space inputs of the FFT passes in the storage their compute type reads.
+  const T* psi_r_fft() const { return use_ff ? psi_r_ff.as<T>() : psi_r.as<T>(); }
+  const T* v_r_fft() const { return use_ff ? v_r_ff.as<T>() : v_r.as<T>(); }
   FftCtx<T> fft(const FftPlan& pl) const {
     FftCtx<T> f;
     f.plan = pl;
@@ -121,7 +125,7 @@ struct Prec {
     return f;
   }
   void release() {
-    DevBuf* all[] = {&tw, &twe, &psi, &psi_r, &v_r, &X, &R, &Z, &P, &Q, &Bv, &Tw, &shift, &kbB, &kbD};
+    DevBuf* all[] = {&tw, &twe, &psi, &psi_r, &v_r, &psi_r_ff, &v_r_ff, &X, &R, &Z, &P, &Q, &Bv, &Tw, &shift, &kbB, &kbD};
     for (DevBuf* b : all) b->release();
   }
 };
@@ -310,7 +314,7 @@ int apply_A(wgw_ctx* c, Prec<T>& pr, const T* P, T* Q, int n_list, const int* li
   WGW_CK(c->prof.run(PK_G2R, tb + (double)n_list * nrb * sizeof(T), 0, st, [&] {
     return launch_plane_g2r<T>(c->wfc.tab(), f, P, c->ld_w, n_list, list, active, Tb, st); }));
   XArgs<T> a{};
-  a.mode = XM_APPLY_V; a.V = pr.v_r.template as<T>(); a.n_sys = n_list; a.list = list;
+  a.mode = XM_APPLY_V; a.V = pr.v_r_fft(); a.n_sys = n_list; a.list = list;
   WGW_CK(c->prof.run(PK_XLINE, 2 * tb + (double)c->grid3 * sizeof(T), 0, st, [&] {
     return launch_xline<T>(c->wfc.m, f, Tb, a, active, st); }));
   Epi<T> e{};
@@ -712,7 +716,7 @@ int chi0_rb(wgw_ctx* c, const double* dvrb, int n_real, cudaStream_t st, wgw_sta
     WGW_TRY(c->d.Tw.ensure(sizeof(cplx<double>) * (size_t)pairs * NP * N * N));
     FftCtx<double> f = c->d.fft(c->plan);
     XArgs<double> a{};
-    a.mode = XM_FROM_REAL; a.A = c->d.psi_r.as<double>(); a.lda = c->grid3; a.a_index = c->a_idx.as<int>();
+    a.mode = XM_FROM_REAL; a.A = c->d.psi_r_fft(); a.lda = c->grid3; a.a_index = c->a_idx.as<int>();
     a.Bm = dvr; a.ldb = c->grid3; a.b_index = c->b_idx.as<int>(); a.n_sys = n_sys;
     const double tb = t_bytes<double>(c, c->wfc.m, pairs);
     WGW_CK(c->prof.run(PK_XLINE, tb + 2.0 * n_sys * c->grid3 * sizeof(double), 0, st, [&] {
@@ -737,7 +741,7 @@ int chi0_rb(wgw_ctx* c, const double* dvrb, int n_real, cudaStream_t st, wgw_sta
                                       c->d.Tw.as<cplx<double>>(), st); }));
     const double coef = 2.0 * c->opt.f_s / c->omega_cell;
     WGW_CK(c->prof.run(PK_DRHO, tb + (double)(n_v + n_real) * c->grid3 * sizeof(double), 0, st, [&] {
-      return launch_drho_xline<double>(c->wfc.m, f, c->d.Tw.as<cplx<double>>(), c->d.psi_r.as<double>(),
+      return launch_drho_xline<double>(c->wfc.m, f, c->d.Tw.as<cplx<double>>(), c->d.psi_r_fft(),
                                        c->grid3, n_v, n_sys, n_real, coef, c->Dr.as<double>(), c->grid3, st); }));
     const int NPr = 2 * rs.m + 1, rpairs = (n_real + 1) / 2;
     WGW_TRY(c->Trho.ensure(sizeof(cplx<double>) * (size_t)rpairs * NPr * N * N));
@@ -793,7 +797,7 @@ int chi0_rb_shifted(wgw_ctx* c, const double* dvrb, int n_real, const std::vecto
     const int NP = 2 * c->wfc.m + 1, pairs = (n_rs + 1) / 2;
     WGW_TRY(c->d.Tw.ensure(sizeof(cplx<double>) * (size_t)pairs * NP * N * N));
     XArgs<double> a{};
-    a.mode = XM_FROM_REAL; a.A = c->d.psi_r.as<double>(); a.lda = c->grid3; a.a_index = c->a_idx.as<int>();
+    a.mode = XM_FROM_REAL; a.A = c->d.psi_r_fft(); a.lda = c->grid3; a.a_index = c->a_idx.as<int>();
     a.Bm = dvr; a.ldb = c->grid3; a.b_index = c->b_idx.as<int>(); a.n_sys = n_rs;
     const double tb = t_bytes<double>(c, c->wfc.m, pairs);
     WGW_CK(c->prof.run(PK_XLINE, tb + 2.0 * n_rs * c->grid3 * sizeof(double), 0, st, [&] {
@@ -824,7 +828,7 @@ int chi0_rb_shifted(wgw_ctx* c, const double* dvrb, int n_real, const std::vecto
       return launch_plane_g2r<double>(c->wfc.tab(), f, Xk, 2 * ldw, n_rs, nullptr, nullptr,
                                       c->d.Tw.as<cplx<double>>(), st); }));
     WGW_CK(c->prof.run(PK_DRHO, tb + (double)(n_v + n_real) * c->grid3 * sizeof(double), 0, st, [&] {
-      return launch_drho_xline<double>(c->wfc.m, f, c->d.Tw.as<cplx<double>>(), c->d.psi_r.as<double>(),
+      return launch_drho_xline<double>(c->wfc.m, f, c->d.Tw.as<cplx<double>>(), c->d.psi_r_fft(),
                                        c->grid3, n_v, n_rs, n_real, coef, c->Dr.as<double>(), c->grid3, st); }));
     XArgs<double> a{};
     a.mode = XM_FROM_REAL; a.A = c->Dr.as<double>(); a.lda = c->grid3; a.n_sys = n_real;
@@ -843,7 +847,8 @@ int chi0_rb_shifted(wgw_ctx* c, const double* dvrb, int n_real, const std::vecto
 int apply_core(wgw_ctx* c, const double* dV, int n_pert, const double* omega, int n_omega,
                double* drho, bool symmetrized, cudaStream_t st, wgw_stats* stats) {
   if (!c) return fail(WGW_ERR_ARG, "null context");
-  c->d.use_ff = c->opt.precision == WGW_MIXED && c->opt.fp64_emulation != 0;
+  // Float-float kernels exist for the compiled grid sizes only; other grids run native FP64.
+  c->d.use_ff = c->opt.precision == WGW_MIXED && c->opt.fp64_emulation != 0 && ff_grid_supported(c->N);
   if (n_pert < 0 || n_omega < 1 || !omega) return fail(WGW_ERR_ARG, "need n_pert >= 0 and n_omega >= 1");
   std::vector<int> k_zero, k_pos;
   std::vector<double> w_pos;
@@ -1183,7 +1188,7 @@ int lanczos_impl(wgw_ctx* c, const double* phi, int npd, int n_steps, const doub
     const int NP = 2 * c->wfc.m + 1, pairs = (n_ch + 1) / 2;
     WGW_TRY(c->d.Tw.ensure(sizeof(cplx<double>) * (size_t)pairs * NP * N * N));
     XArgs<double> a{};
-    a.mode = XM_FROM_REAL; a.A = c->d.psi_r.as<double>(); a.lda = c->grid3; a.a_index = c->a_idx.as<int>();
+    a.mode = XM_FROM_REAL; a.A = c->d.psi_r_fft(); a.lda = c->grid3; a.a_index = c->a_idx.as<int>();
     a.Bm = dvr; a.ldb = c->grid3; a.b_index = c->b_idx.as<int>(); a.n_sys = n_ch;
     WGW_CK(launch_xline<double>(c->wfc.m, f, c->d.Tw.as<cplx<double>>(), a, nullptr, st));
     Epi<double> e{};
@@ -1400,6 +1405,10 @@ static int setup_impl(wgw_ctx* c, const double* vloc_G, const double* psi_v, con
   WGW_TRY(to_real<double>(c, c->d, c->rho, vrb.as<double>(), c->ld_r, 1, c->d.v_r.as<double>(), tr, st));
   WGW_TRY(c->f.v_r.ensure(sizeof(float) * c->grid3));
   WGW_CK((launch_copy_cast<double, float>(1, (int)c->grid3, c->d.v_r.as<double>(), c->grid3, c->f.v_r.as<float>(), c->grid3, nullptr, st)));
+  WGW_TRY(c->d.psi_r_ff.ensure(sizeof(double) * (size_t)n_v * c->grid3));
+  WGW_CK(launch_to_ff((size_t)n_v * c->grid3, c->d.psi_r.as<double>(), c->d.psi_r_ff.as<double>(), st));
+  WGW_TRY(c->d.v_r_ff.ensure(sizeof(double) * c->grid3));
+  WGW_CK(launch_to_ff((size_t)c->grid3, c->d.v_r.as<double>(), c->d.v_r_ff.as<double>(), st));
   WGW_CK(cudaStreamSynchronize(st));
   tmp.release(); anti.release(); nrm.release(); vrb.release(); tr.release();
   return WGW_OK;

@@ -5,6 +5,7 @@
 // host execution path.
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -114,6 +115,10 @@ void apply_h_impl(double L, double ecut, int N, const double* vloc_c, int n_sys,
   std::vector<T> vrb(nr), vr(N3);
   sphere_to_rb_host<T>(r, 1, vloc_c, 2L * r.h.n, nullptr, 0, vrb.data(), nr);
   to_real<T>(r, pl, tws, vrb.data(), nr, 1, vr.data());
+  if constexpr (std::is_same<C, ff>::value) {
+    // float-float passes read real-space arrays as float-float pairs (in the FP64 slots)
+    for (size_t i = 0; i < vr.size(); ++i) reinterpret_cast<ff*>(vr.data())[i] = ff(double(vr[i]));
+  }
   std::vector<T> X((size_t)n_sys * nw), out((size_t)n_sys * nw), sh(n_sys);
   for (size_t i = 0; i < X.size(); ++i) X[i] = (T)Xd[i];
   for (int s = 0; s < n_sys; ++s) sh[s] = (T)shift[s];
