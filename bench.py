@@ -160,6 +160,8 @@ def main():
                     help="perturbations per rank (default: the workload's); smaller values serve profiling")
     ap.add_argument("--fp64-emulation", type=int, default=1, choices=[0, 1],
                     help="1: FP64-accuracy FFT passes in float-float (default); 0: native FP64")
+    ap.add_argument("--tensor-cores", type=int, default=None, choices=[0, 1],
+                    help="P_c of the FP32 solves on the tcgen05 tensor cores (default: the library's)")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.n_pert > 0:
@@ -195,6 +197,8 @@ def main():
     phi = phi_all[:, owned_perturbations(wl["n_pert"] * world, rank, world, wl["n_pert"])]
     opt = W.wgw_default_options(precision=W.WGW_MIXED, cg_tol=wl["cg_tol"], max_cg_iter=200,
                                 fp64_emulation=args.fp64_emulation)
+    if args.tensor_cores is not None:
+        opt.tensor_cores = args.tensor_cores
     ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, opt)
     stream = torch.cuda.current_stream()
     x = torch.from_numpy(np.ascontiguousarray(phi.T)).cuda()
@@ -280,6 +284,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
         "config": {"workload": args.workload, "desc": wl["desc"], "cg_tol": wl["cg_tol"],
                    "fp64_passes": "float-float" if args.fp64_emulation else "native FP64",
+                   "pc_fp32": "tcgen05 3xTF32" if opt.tensor_cores else "CUDA-core FP32",
                    "l2": "256 MB buffer written between steps, outside the timed interval",
                    "parallelism": f"perturbation shards x{world}" if world > 1 else "1 GPU"},
         "latency_ms": {"p50": 1e3 * statistics.median(times),

@@ -82,16 +82,22 @@ cudaError_t launch_drho_xline(int m, FftCtx<T> f, const cplx<T>* Tbuf, const T* 
 // Y <- Y - Psi Psi^T Y for the active systems of a list (null = systems 0..n_sys-1);
 // work holds pc_work_elems(n, n_sys, nv) elements of T.
 // ffc: for T = double, compute in float-float (operands rounded to float-float pairs).
-// tcores: for T = float, the tcgen05 tensor-core kernels (tc_kernels.cu) when nv <= 256.
+// tc_tiles: for T = float, the tensor-core kernels (tc_kernels.cu) with Psi pre-split into these
+// tiles (launch_tc_tile_psi); null selects the CUDA-core GEMMs.
 template <typename T>
 cudaError_t launch_pc(T* Y, long ldy, int n_sys, const int* list, const T* Psi, long ldp, int n, int nv,
-                      const int* active, T* work, cudaStream_t st, bool ffc = false, bool tcores = false);
+                      const int* active, T* work, cudaStream_t st, bool ffc = false,
+                      const unsigned char* tc_tiles = nullptr);
 // P_c on the tensor cores (3xTF32 products, FP32 accumulation in tensor memory); work holds
-// tc_pc_work_elems(n, n_sys, nv) floats.
-cudaError_t launch_pc_tc(float* Y, long ldy, int n_sys, const int* list, const float* Psi, long ldp, int n, int nv,
+// tc_pc_work_elems(n, n_sys, nv) floats; tiles from launch_tc_tile_psi.
+cudaError_t launch_pc_tc(float* Y, long ldy, int n_sys, const int* list, const unsigned char* tiles, int n, int nv,
                          const int* active, float* work, cudaStream_t st);
 size_t tc_pc_work_elems(int n, int n_sys, int nv);
 bool tc_pc_supported(int nv);
+// Psi (n x nv, column v at Psi + v ldp) split into TF32 hi/lo parts and laid out as the operand
+// tiles of both phases; tc_psi_tile_bytes(n, nv) bytes.
+size_t tc_psi_tile_bytes(int n, int nv);
+cudaError_t launch_tc_tile_psi(const float* Psi, long ldp, int n, int nv, unsigned char* tiles, cudaStream_t st);
 // Reads (and clears) the tensor-core kernels' wait-timeout flag; synchronises st.
 cudaError_t tc_error_read_and_clear(int* flag, cudaStream_t st);
 // C = A^T B: A is K x m (column j at A + j*lda), B is K x n (column j at B + c_j * ldb with

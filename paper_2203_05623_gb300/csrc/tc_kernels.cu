@@ -177,81 +177,143 @@ __device__ __forceinline__ void issue_chunk(uint32_t tmem_d, uint32_t a_hi, uint
   }
 }
 
-// Phase 1.  Grid (ceil(n_list / 128), n_kb).  Cpart[kb][j][v] (row length ldc) for j < n_list,
-// v < ldc (zero for v >= nv).  N = states padded to 16 (<= 256).
-__global__ void __launch_bounds__(kThreads) k_tc_pc1(const float* __restrict__ Psi, long ldp,
-                                                     const float* __restrict__ Y, long ldy, int n, int nv,
-                                                     int n_list, const int* __restrict__ list, int kblk, int N,
-                                                     int ldc, float* __restrict__ Cpart) {
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// 1-D bulk copy global -> shared through the TMA engine, completing on an mbarrier.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(mbar)
+      : "memory");
+}
+
+constexpr uint32_t kTile = kRowsA * kKC * 4;   // bytes of one 128 x 32 TF32 part (16 KB)
+
+// Operand tiles of a constant matrix, split and laid out once:
+//  tiles1 (phase-1 B): chunk kc of 32 k, part (hi, lo), Nn rows v: ((kc * 2 + part) * Nn * 128) + tile_off(v, k % 32)
+//  tiles2 (phase-2 A): row tile rt of 128 k, state chunk vc, part: ((rt * nvc + vc) * 2 + part) * kTile + tile_off(k % 128, v % 32)
+__global__ void k_tc_tile_psi(const float* __restrict__ Psi, long ldp, int n, int nv, int Nn, int nkc, int nrt,
+                              int nvc, unsigned char* __restrict__ t1, unsigned char* __restrict__ t2) {
+  const long total = static_cast<long>(nkc) * kKC * Nn;
+  for (long e = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<long>(gridDim.x) * blockDim.x) {
+    const int v = static_cast<int>(e % Nn);
+    const int k = static_cast<int>(e / Nn);
+    const float x = (v < nv && k < n) ? Psi[static_cast<size_t>(v) * ldp + k] : 0.f;
+    float hi, lo;
+    split_tf32(x, hi, lo);
+    const int kc = k / kKC, kk = k % kKC;
+    const size_t b1 = static_cast<size_t>(kc) * 2 * Nn * 128;
+    *reinterpret_cast<float*>(t1 + b1 + tile_off(v, kk)) = hi;
+    *reinterpret_cast<float*>(t1 + b1 + static_cast<size_t>(Nn) * 128 + tile_off(v, kk)) = lo;
+    if (k < nrt * kRowsA && v < nvc * kKC) {
+      const int rt = k / kRowsA, r = k % kRowsA, vc = v / kKC, vv = v % kKC;
+      const size_t b2 = (static_cast<size_t>(rt) * nvc + vc) * 2 * kTile;
+      *reinterpret_cast<float*>(t2 + b2 + tile_off(r, vv)) = hi;
+      *reinterpret_cast<float*>(t2 + b2 + kTile + tile_off(r, vv)) = lo;
+    }
+  }
+}
+
+// Phase 1.  Grid (ceil(n_list / 128), n_kb); CTA (jt, kb) owns K chunks [kb * kcpb, ...).
+// A (128 systems x 32 k) is staged by the threads (split on the fly, next chunk prefetched
+// into registers while the current MMAs run); B (Nn states x 32 k) arrives by bulk copy
+// from tiles1.  Two shared-memory stages.  Cpart[kb][j][v] (row length ldc).
+__global__ void __launch_bounds__(kThreads) k_tc_pc1(const unsigned char* __restrict__ t1, const float* __restrict__ Y,
+                                                     long ldy, int n, int nv, int n_list,
+                                                     const int* __restrict__ list, int kcpb, int Nn, int ldc,
+                                                     float* __restrict__ Cpart) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int j0 = blockIdx.x * kRowsA, kb = blockIdx.y;
-  const int k_lo = kb * kblk, k_hi = min(n, k_lo + kblk);
-  const uint32_t a_bytes = kRowsA * kKC * 4, b_bytes = static_cast<uint32_t>(N) * kKC * 4;
-  unsigned char* a_hi = smem;
-  unsigned char* a_lo = a_hi + a_bytes;
-  unsigned char* b_hi = a_lo + a_bytes;
-  unsigned char* b_lo = b_hi + b_bytes;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(b_lo + b_bytes);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int nkc = (n + kKC - 1) / kKC;
+  const int kc_lo = kb * kcpb, kc_hi = min(nkc, kc_lo + kcpb);
+  const uint32_t b_bytes = 2u * Nn * 128;
+  const uint32_t stage_bytes = 2 * kTile + b_bytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * stage_bytes);   // full[2], mma[2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 4);
   uint32_t ncols = 32;
-  while (ncols < static_cast<uint32_t>(N)) ncols <<= 1;
+  while (ncols < static_cast<uint32_t>(Nn)) ncols <<= 1;
   if (warp == 0) tmem_alloc(tslot, ncols);
   if (tid == 0) {
-    mbar_init(smem_u32(mbar), 1);
+    for (int i = 0; i < 4; ++i) mbar_init(smem_u32(bars + i), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tslot;
-  const uint32_t idesc = idesc_tf32(kRowsA, N);
-  // A rows: systems j0 + r (r < 128); thread -> (rr, kq, half) with 8 rows per pass.
+  const uint32_t idesc = idesc_tf32(kRowsA, Nn);
+  // This thread's 8 A rows (systems) and its 16-byte column within a chunk.
   const int rr = tid & 7, kq = (tid >> 3) & 7, mg0 = tid >> 6;
-  uint32_t parity = 0;
+  const float* rowp[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int j = j0 + (mg0 + 2 * i) * 8 + rr;
+    rowp[i] = j < n_list ? Y + static_cast<size_t>(list ? list[j] : j) * ldy : nullptr;
+  }
+  float4 pre[8];
+  auto load_a = [&](int kc) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      pre[i] = rowp[i] ? load4(rowp[i], kc * kKC + kq * 4, n) : make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+  auto stage_in = [&](int kc, int st) {
+    unsigned char* base = smem + st * stage_bytes;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) put4(base, base + kTile, (mg0 + 2 * i) * 8 + rr, kq * 4, pre[i]);
+    if (tid == 0) {
+      const uint32_t fb = smem_u32(bars + st);
+      mbar_expect_tx(fb, b_bytes);
+      bulk_g2s(smem_u32(base + 2 * kTile), t1 + static_cast<size_t>(kc) * b_bytes, b_bytes, fb);
+    }
+  };
   bool ok = true;
-  int chunk = 0;
-  for (int k0 = k_lo; k0 < k_hi; k0 += kKC, ++chunk) {
-    if (chunk > 0) {
-      const bool w = mbar_wait(smem_u32(mbar), parity);
-      parity ^= 1u;
-      ok = __syncthreads_and(w) != 0;
-      if (!ok) break;
-    }
-    for (int mg = mg0; mg < kRowsA / 8; mg += 2) {
-      const int r = mg * 8 + rr, j = j0 + r;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (j < n_list) {
-        const int s = list ? list[j] : j;
-        v = load4(Y + static_cast<size_t>(s) * ldy, k0 + kq * 4, k_hi);
-      }
-      put4(a_hi, a_lo, r, kq * 4, v);
-    }
-    for (int mg = mg0; mg < N / 8; mg += 2) {
-      const int r = mg * 8 + rr;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (r < nv) v = load4(Psi + static_cast<size_t>(r) * ldp, k0 + kq * 4, k_hi);
-      put4(b_hi, b_lo, r, kq * 4, v);
-    }
+  const int nc = kc_hi - kc_lo;
+  if (nc > 0) {
+    load_a(kc_lo);
+    stage_in(kc_lo, 0);
     fence_async_smem();
     __syncthreads();
+  }
+  for (int c = 0; c < nc; ++c) {
+    const int st = c & 1;
     if (tid == 0) {
-      fence_after();
-      issue_chunk(tmem, smem_u32(a_hi), smem_u32(a_lo), smem_u32(b_hi), smem_u32(b_lo), idesc, chunk == 0);
-      mma_commit(smem_u32(mbar));
+      ok = ok && mbar_wait(smem_u32(bars + st), (c >> 1) & 1);   // B of chunk c landed
+      if (ok) {
+        fence_after();
+        unsigned char* base = smem + st * stage_bytes;
+        issue_chunk(tmem, smem_u32(base), smem_u32(base + kTile), smem_u32(base + 2 * kTile),
+                    smem_u32(base + 2 * kTile + Nn * 128), idesc, c == 0);
+        mma_commit(smem_u32(bars + 2 + st));
+      }
+    }
+    if (c + 1 < nc) {
+      load_a(kc_lo + c + 1);                 // global loads in flight while the MMAs run
+      const int s1 = (c + 1) & 1;
+      if (c >= 1) {                          // stage s1 was read by the MMAs of chunk c - 1
+        const bool w = mbar_wait(smem_u32(bars + 2 + s1), ((c - 1) >> 1) & 1);
+        ok = ok && w;
+      }
+      ok = __syncthreads_and(ok) != 0;
+      if (!ok) break;
+      stage_in(kc_lo + c + 1, s1);
+      fence_async_smem();
+      __syncthreads();
     }
   }
-  if (ok && chunk > 0) {
-    const bool w = mbar_wait(smem_u32(mbar), parity);
+  if (nc > 0) {
+    const bool w = ok && mbar_wait(smem_u32(bars + 2 + ((nc - 1) & 1)), ((nc - 1) >> 1) & 1);
     ok = __syncthreads_and(w) != 0;
   }
   fence_after();
-  // Epilogue: lane (32 warp + lane) = system j0 + that; columns = states.
   const int j = j0 + warp * 32 + lane;
   float* out = Cpart + (static_cast<size_t>(kb) * n_list + (j < n_list ? j : 0)) * ldc;
   for (int c0 = 0; c0 < ldc; c0 += 16) {
     float v[16];
-    if (ok && chunk > 0 && c0 < N) {
+    if (ok && nc > 0 && c0 < Nn) {
       tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
     } else {
 #pragma unroll
@@ -271,42 +333,56 @@ __global__ void __launch_bounds__(kThreads) k_tc_pc1(const float* __restrict__ P
   if (warp == 0) tmem_dealloc(tmem, ncols);
 }
 
-// C^T[j][v] = sum_kb Cpart[kb][j][v], fixed order (in place into slice 0).
-__global__ void k_tc_reduce(float* __restrict__ Cpart, size_t slice, int n_kb) {
-  for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < slice;
-       e += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    float s = Cpart[e];
-    for (int kb = 1; kb < n_kb; ++kb) s += Cpart[static_cast<size_t>(kb) * slice + e];
-    Cpart[e] = s;
+// C^T[j][v] = sum_kb Cpart[kb][j][v] (fixed order), written split and tiled for phase 2:
+// ((jt * nvc + vc) * 2 + part) * kTile + tile_off(j % 128, v % 32); zero outside n_list x nv.
+__global__ void k_tc_reduce(const float* __restrict__ Cpart, int n_list, int ldc, int n_kb, int nv, int njt,
+                            int nvc, unsigned char* __restrict__ ct) {
+  const long total = static_cast<long>(njt) * kRowsA * nvc * kKC;
+  const size_t slice = static_cast<size_t>(n_list) * ldc;
+  for (long e = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<long>(gridDim.x) * blockDim.x) {
+    const int v = static_cast<int>(e % (nvc * kKC));
+    const int j = static_cast<int>(e / (nvc * kKC));
+    float sum = 0.f;
+    if (j < n_list && v < nv) {
+      const size_t o = static_cast<size_t>(j) * ldc + v;
+      sum = Cpart[o];
+      for (int kb = 1; kb < n_kb; ++kb) sum += Cpart[static_cast<size_t>(kb) * slice + o];
+    }
+    float hi, lo;
+    split_tf32(sum, hi, lo);
+    const int jt = j / kRowsA, vc = v / kKC;
+    const size_t b = (static_cast<size_t>(jt) * nvc + vc) * 2 * kTile;
+    *reinterpret_cast<float*>(ct + b + tile_off(j % kRowsA, v % kKC)) = hi;
+    *reinterpret_cast<float*>(ct + b + kTile + tile_off(j % kRowsA, v % kKC)) = lo;
   }
 }
 
-// Phase 2.  Grid (ceil(n / 128), ceil(n_list / 128)).  D = rows k0..k0+127 x systems j0..j0+127,
-// K = states in chunks of 32 (Ct row length ldc, a multiple of 32).
-__global__ void __launch_bounds__(kThreads) k_tc_pc2(const float* __restrict__ Psi, long ldp, float* __restrict__ Y,
-                                                     long ldy, int n, int nv, int n_list,
-                                                     const int* __restrict__ list, const float* __restrict__ Ct,
-                                                     int ldc, float alpha, float beta,
+// Phase 2.  Grid (ceil(n / 128), ceil(n_list / 128)).  D = rows rt x systems jt, K = states in
+// chunks of 32; A from tiles2 and B from the reduced C^T tiles, both by bulk copy, two stages.
+constexpr int kThreads2 = 256;   // phase 2: warp w reads TMEM lanes 32 (w % 4); warps 4-7 take columns 64-127
+
+__global__ void __launch_bounds__(kThreads2) k_tc_pc2(const unsigned char* __restrict__ t2,
+                                                     const unsigned char* __restrict__ ct, float* __restrict__ Y,
+                                                     long ldy, int n, int nvc, int n_list,
+                                                     const int* __restrict__ list, float alpha, float beta,
                                                      const int* __restrict__ active) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int r0 = blockIdx.x * kRowsA, j0 = blockIdx.y * kRowsA;
-  const uint32_t t_bytes = kRowsA * kKC * 4;
-  unsigned char* a_hi = smem;
-  unsigned char* a_lo = a_hi + t_bytes;
-  unsigned char* b_hi = a_lo + t_bytes;
-  unsigned char* b_lo = b_hi + t_bytes;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(b_lo + t_bytes);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
-  if (active) {   // skip tiles whose systems are all finished
+  const int rt = blockIdx.x, jt = blockIdx.y;
+  const int r0 = rt * kRowsA, j0 = jt * kRowsA;
+  constexpr uint32_t stage_bytes = 4 * kTile;   // A hi, A lo, B hi, B lo
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * stage_bytes);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 4);
+  if (active) {   // skip tiles whose systems have all finished
     int any = 0;
-    for (int t = tid; t < kRowsA && j0 + t < n_list; t += kThreads) any |= active[list ? list[j0 + t] : j0 + t];
+    for (int t = tid; t < kRowsA && j0 + t < n_list; t += kThreads2) any |= active[list ? list[j0 + t] : j0 + t];
     if (!__syncthreads_or(any)) return;
   }
-  const uint32_t ncols = kRowsA;
+  constexpr uint32_t ncols = kRowsA;
   if (warp == 0) tmem_alloc(tslot, ncols);
   if (tid == 0) {
-    mbar_init(smem_u32(mbar), 1);
+    for (int i = 0; i < 4; ++i) mbar_init(smem_u32(bars + i), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   fence_before();
@@ -314,66 +390,62 @@ __global__ void __launch_bounds__(kThreads) k_tc_pc2(const float* __restrict__ P
   fence_after();
   const uint32_t tmem = *tslot;
   const uint32_t idesc = idesc_tf32(kRowsA, kRowsA);
-  uint32_t parity = 0;
+  auto fetch = [&](int vc, int st) {
+    const uint32_t fb = smem_u32(bars + st);
+    unsigned char* base = smem + st * stage_bytes;
+    mbar_expect_tx(fb, 4 * kTile);
+    bulk_g2s(smem_u32(base), t2 + (static_cast<size_t>(rt) * nvc + vc) * 2 * kTile, 2 * kTile, fb);
+    bulk_g2s(smem_u32(base + 2 * kTile), ct + (static_cast<size_t>(jt) * nvc + vc) * 2 * kTile, 2 * kTile, fb);
+  };
   bool ok = true;
-  int chunk = 0;
-  for (int v0 = 0; v0 < nv; v0 += kKC, ++chunk) {
-    if (chunk > 0) {
-      const bool w = mbar_wait(smem_u32(mbar), parity);
-      parity ^= 1u;
-      ok = __syncthreads_and(w) != 0;
+  if (tid == 0) {
+    for (int vc = 0; vc < nvc && vc < 2; ++vc) fetch(vc, vc);
+    for (int vc = 0; vc < nvc && ok; ++vc) {
+      const int st = vc & 1;
+      ok = mbar_wait(smem_u32(bars + st), (vc >> 1) & 1);
       if (!ok) break;
-    }
-    // A: rows k (M) x states (K) from Psi[v][k]: thread -> state vv = tid & 31, rows in quads.
-    {
-      const int vv = tid & 31, v = v0 + vv;
-      const float* col = Psi + static_cast<size_t>(v < nv ? v : 0) * ldp;
-      for (int q = tid >> 5; q < kRowsA / 4; q += kThreads / 32) {
-        const int r = q * 4, k = r0 + r;
-        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (v < nv) x = load4(col, k, n);
-        put1(a_hi, a_lo, r + 0, vv, x.x);
-        put1(a_hi, a_lo, r + 1, vv, x.y);
-        put1(a_hi, a_lo, r + 2, vv, x.z);
-        put1(a_hi, a_lo, r + 3, vv, x.w);
-      }
-    }
-    // B: systems j (N) x states (K) from Ct[j][v] (row length ldc >= v0 + 32).
-    {
-      const int rr = tid & 7, kq = (tid >> 3) & 7, mg0 = tid >> 6;
-      for (int mg = mg0; mg < kRowsA / 8; mg += 2) {
-        const int r = mg * 8 + rr, j = j0 + r;
-        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (j < n_list) x = *reinterpret_cast<const float4*>(Ct + static_cast<size_t>(j) * ldc + v0 + kq * 4);
-        put4(b_hi, b_lo, r, kq * 4, x);
-      }
-    }
-    fence_async_smem();
-    __syncthreads();
-    if (tid == 0) {
       fence_after();
-      issue_chunk(tmem, smem_u32(a_hi), smem_u32(a_lo), smem_u32(b_hi), smem_u32(b_lo), idesc, chunk == 0);
-      mma_commit(smem_u32(mbar));
+      unsigned char* base = smem + st * stage_bytes;
+      issue_chunk(tmem, smem_u32(base), smem_u32(base + kTile), smem_u32(base + 2 * kTile),
+                  smem_u32(base + 3 * kTile), idesc, vc == 0);
+      mma_commit(smem_u32(bars + 2 + st));
+      if (vc + 2 < nvc) {   // refill this stage once its MMAs have read it
+        ok = mbar_wait(smem_u32(bars + 2 + st), (vc >> 1) & 1);
+        if (ok) fetch(vc + 2, st);
+      }
     }
   }
-  if (ok && chunk > 0) {
-    const bool w = mbar_wait(smem_u32(mbar), parity);
+  ok = __syncthreads_and(ok) != 0;
+  if (ok && nvc > 0) {
+    const bool w = mbar_wait(smem_u32(bars + 2 + ((nvc - 1) & 1)), ((nvc - 1) >> 1) & 1);
     ok = __syncthreads_and(w) != 0;
   }
   fence_after();
-  const int k = r0 + warp * 32 + lane;   // this thread's row
-  if (ok && chunk > 0) {
-    for (int c0 = 0; c0 < kRowsA; c0 += 16) {
+  const int quad = warp & 3, half = warp >> 2;
+  const int k = r0 + quad * 32 + lane;   // this thread's row; columns [64 half, 64 half + 64)
+  if (ok && nvc > 0) {
+    // All 64 old values of this thread in flight before any arithmetic or store.
+    float old[64];
+#pragma unroll
+    for (int i = 0; i < 64; ++i) {
+      const int j = j0 + half * 64 + i;
+      old[i] = 0.f;
+      if (beta != 0.f && j < n_list && k < n) {
+        const int s = list ? list[j] : j;
+        if (!active || active[s]) old[i] = Y[static_cast<size_t>(s) * ldy + k];
+      }
+    }
+#pragma unroll
+    for (int c0 = 0; c0 < 64; c0 += 16) {
       float v[16];
-      tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
+      tmem_ld16(tmem + (static_cast<uint32_t>(quad * 32) << 16) + half * 64 + c0, v);
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
-        const int j = j0 + c0 + i;
-        if (j >= n_list || k >= n) continue;
-        const int s = list ? list[j] : j;
-        if (active && !active[s]) continue;
-        float* y = Y + static_cast<size_t>(s) * ldy + k;
-        *y = (beta != 0.f ? beta * *y : 0.f) + alpha * v[i];
+        const int j = j0 + half * 64 + c0 + i;
+        if (j < n_list && k < n) {
+          const int s = list ? list[j] : j;
+          if (!active || active[s]) Y[static_cast<size_t>(s) * ldy + k] = beta * old[c0 + i] + alpha * v[i];
+        }
       }
     }
   }
@@ -384,41 +456,79 @@ __global__ void __launch_bounds__(kThreads) k_tc_pc2(const float* __restrict__ P
 
 }  // namespace tc
 
+namespace {
+struct TcGeom {
+  int Nn, ldc, nkc, nrt, nvc, njt, n_kb, kcpb;
+};
+TcGeom tc_geom(int n, int n_sys, int nv) {
+  TcGeom g;
+  g.Nn = (nv + 15) / 16 * 16;
+  g.ldc = (nv + 31) / 32 * 32;
+  g.nkc = (n + tc::kKC - 1) / tc::kKC;
+  g.nrt = (n + tc::kRowsA - 1) / tc::kRowsA;
+  g.nvc = g.ldc / tc::kKC;
+  g.njt = (n_sys + tc::kRowsA - 1) / tc::kRowsA;
+  // About 8 phase-1 CTAs per SM (two resident at a time), each with at least 4 chunks of K.
+  int kb = (8 * 152 + g.njt - 1) / g.njt;
+  kb = std::max(1, std::min(kb, std::max(1, g.nkc / 4)));
+  g.kcpb = (g.nkc + kb - 1) / kb;
+  g.n_kb = (g.nkc + g.kcpb - 1) / g.kcpb;
+  return g;
+}
+}  // namespace
+
+size_t tc_psi_tile_bytes(int n, int nv) {
+  const TcGeom g = tc_geom(n, 1, nv);
+  return static_cast<size_t>(g.nkc) * 2 * g.Nn * 128 + static_cast<size_t>(g.nrt) * g.nvc * 2 * tc::kTile;
+}
+
+cudaError_t launch_tc_tile_psi(const float* Psi, long ldp, int n, int nv, unsigned char* tiles, cudaStream_t st) {
+  const TcGeom g = tc_geom(n, 1, nv);
+  unsigned char* t1 = tiles;
+  unsigned char* t2 = tiles + static_cast<size_t>(g.nkc) * 2 * g.Nn * 128;
+  cudaError_t e = cudaMemsetAsync(tiles, 0, tc_psi_tile_bytes(n, nv), st);
+  if (e != cudaSuccess) return e;
+  const long total = static_cast<long>(g.nkc) * tc::kKC * g.Nn;
+  tc::k_tc_tile_psi<<<static_cast<int>(std::min<long>((total + 255) / 256, 8192)), 256, 0, st>>>(
+      Psi, ldp, n, nv, g.Nn, g.nkc, g.nrt, g.nvc, t1, t2);
+  return cudaGetLastError();
+}
+
 size_t tc_pc_work_elems(int n, int n_sys, int nv) {
-  const int ldc = (nv + 31) / 32 * 32;
-  return static_cast<size_t>(pc_kblocks(n, n_sys)) * n_sys * ldc;
+  const TcGeom g = tc_geom(n, n_sys, nv);
+  // Cpart floats, then the split C^T tiles (bytes / 4).
+  return static_cast<size_t>(g.n_kb) * n_sys * g.ldc + static_cast<size_t>(g.njt) * g.nvc * 2 * tc::kTile / 4;
 }
 
 bool tc_pc_supported(int nv) { return nv >= 1 && nv <= 256; }
 
-cudaError_t launch_pc_tc(float* Y, long ldy, int n_sys, const int* list, const float* Psi, long ldp, int n, int nv,
+cudaError_t launch_pc_tc(float* Y, long ldy, int n_sys, const int* list, const unsigned char* tiles, int n, int nv,
                          const int* active, float* work, cudaStream_t st) {
   if (n_sys == 0 || nv == 0) return cudaSuccess;
   if (!tc_pc_supported(nv)) return cudaErrorInvalidValue;
-  const int n_kb = pc_kblocks(n, n_sys);
-  const int kblk = ((n + n_kb - 1) / n_kb + tc::kKC - 1) / tc::kKC * tc::kKC;
-  const int N = (nv + 15) / 16 * 16;
-  const int ldc = (nv + 31) / 32 * 32;
-  const size_t smem1 = 2u * (tc::kRowsA + N) * tc::kKC * 4 + 16;
-  cudaError_t e1 = cudaFuncSetAttribute(tc::k_tc_pc1, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        static_cast<int>(2u * (tc::kRowsA + 256) * tc::kKC * 4 + 16));
-  if (e1 != cudaSuccess) return e1;
-  dim3 g1((n_sys + tc::kRowsA - 1) / tc::kRowsA, n_kb);
-  tc::k_tc_pc1<<<g1, tc::kThreads, smem1, st>>>(Psi, ldp, Y, ldy, n, nv, n_sys, list, kblk, N, ldc, work);
-  cudaError_t err = cudaGetLastError();
-  if (err != cudaSuccess) return err;
-  const size_t slice = static_cast<size_t>(n_sys) * ldc;
-  if (n_kb > 1) {
-    tc::k_tc_reduce<<<static_cast<int>(std::min<size_t>((slice + 255) / 256, 4096)), 256, 0, st>>>(work, slice, n_kb);
-    err = cudaGetLastError();
-    if (err != cudaSuccess) return err;
-  }
-  const size_t smem2 = 4u * tc::kRowsA * tc::kKC * 4 + 16;
-  cudaError_t e2 = cudaFuncSetAttribute(tc::k_tc_pc2, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        static_cast<int>(smem2));
-  if (e2 != cudaSuccess) return e2;
-  dim3 g2((n + tc::kRowsA - 1) / tc::kRowsA, (n_sys + tc::kRowsA - 1) / tc::kRowsA);
-  tc::k_tc_pc2<<<g2, tc::kThreads, smem2, st>>>(Psi, ldp, Y, ldy, n, nv, n_sys, list, work, ldc, -1.f, 1.f, active);
+  const TcGeom g = tc_geom(n, n_sys, nv);
+  const unsigned char* t1 = tiles;
+  const unsigned char* t2 = tiles + static_cast<size_t>(g.nkc) * 2 * g.Nn * 128;
+  float* Cpart = work;
+  unsigned char* ct = reinterpret_cast<unsigned char*>(work + static_cast<size_t>(g.n_kb) * n_sys * g.ldc);
+  const size_t smem1 = 2u * (2u * tc::kTile + 2u * g.Nn * 128) + 64;
+  cudaError_t e = cudaFuncSetAttribute(tc::k_tc_pc1, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem1));
+  if (e != cudaSuccess) return e;
+  tc::k_tc_pc1<<<dim3(g.njt, g.n_kb), tc::kThreads, smem1, st>>>(t1, Y, ldy, n, nv, n_sys, list, g.kcpb, g.Nn,
+                                                                 g.ldc, Cpart);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long total = static_cast<long>(g.njt) * tc::kRowsA * g.nvc * tc::kKC;
+  tc::k_tc_reduce<<<static_cast<int>(std::min<long>((total + 255) / 256, 8192)), 256, 0, st>>>(
+      Cpart, n_sys, g.ldc, g.n_kb, nv, g.njt, g.nvc, ct);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t smem2 = 2u * 4u * tc::kTile + 64;
+  e = cudaFuncSetAttribute(tc::k_tc_pc2, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem2));
+  if (e != cudaSuccess) return e;
+  tc::k_tc_pc2<<<dim3(g.nrt, g.njt), tc::kThreads2, smem2, st>>>(t2, ct, Y, ldy, n, g.nvc, n_sys, list, -1.f, 1.f,
+                                                                active);
   return cudaGetLastError();
 }
 

@@ -212,7 +212,7 @@ struct wgw_ctx {
   // apply work space (double unless noted)
   DevBuf dvin, dv_rb, dv_r, Trho, Dr, drho_rb, eps, a_idx, b_idx, brow, cg_rz, cg_bb, cg_rr,
       cg_act, cg_it, cnt, rr64, act64, norms, pc_work, sys_list, list64, cg_rzi, omg, row_list, rowact,
-      drho_all;
+      drho_all, psi_tc;
   cudaStream_t stream = nullptr;
   Prof prof;
   std::vector<int> last_iters;      // per system of the last apply: CG iterations (all refinements)
@@ -251,7 +251,7 @@ struct wgw_ctx {
     d.release(); f.release(); wfc.release(); rho.release();
     DevBuf* all[] = {&e_v_d, &dvin, &dv_rb, &dv_r, &Trho, &Dr, &drho_rb, &eps, &a_idx, &b_idx, &brow,
                      &cg_rz, &cg_bb, &cg_rr, &cg_act, &cg_it, &cnt, &rr64, &act64, &norms, &pc_work, &sys_list, &list64, &cg_rzi, &omg,
-                     &row_list, &rowact, &drho_all};
+                     &row_list, &rowact, &drho_all, &psi_tc};
     for (DevBuf* b : all) b->release();
     if (stream) cudaStreamDestroy(stream);
   }
@@ -289,13 +289,19 @@ template <typename T>
 int run_pc(wgw_ctx* c, T* Y, int n_list, const int* list, const T* Psi, const int* active, cudaStream_t st) {
   ProfPrec pp(c->prof, sizeof(T) == 8);
   const double n = c->wfc.nrb(), nv = c->n_v;
-  const bool tcores = sizeof(T) == sizeof(float) && c->opt.tensor_cores != 0;
+  const bool tcores = sizeof(T) == sizeof(float) && c->opt.tensor_cores != 0 && tc_pc_supported(c->n_v) &&
+                      Psi == reinterpret_cast<const T*>(c->f.psi.p);
   WGW_TRY(c->pc_work.ensure(sizeof(T) * std::max(pc_work_elems((int)n, n_list, std::max(c->n_v, c->n_proj)),
                                                  tc_pc_work_elems((int)n, n_list, c->n_v))));
   T* work = c->pc_work.as<T>();
+  if (tcores && !c->psi_tc.p) {   // operand tiles of the occupied block, once per context
+    WGW_TRY(c->psi_tc.ensure(tc_psi_tile_bytes((int)n, c->n_v)));
+    WGW_CK(launch_tc_tile_psi(c->f.psi.as<float>(), c->ld_w, (int)n, c->n_v, c->psi_tc.as<unsigned char>(), st));
+  }
+  const unsigned char* tiles = tcores ? c->psi_tc.as<unsigned char>() : nullptr;
   WGW_CK(c->prof.run(PK_PC, 2.0 * n_list * n * sizeof(T) + n * nv * sizeof(T), 4.0 * n * nv * n_list, st, [&] {
     return launch_pc<T>(Y, c->ld_w, n_list, list, Psi, c->ld_w, (int)n, c->n_v, active, work, st,
-                        sizeof(T) == 8 && c->d.use_ff, tcores); }));
+                        sizeof(T) == 8 && c->d.use_ff, tiles); }));
   return WGW_OK;
 }
 
