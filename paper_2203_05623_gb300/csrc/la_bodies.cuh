@@ -98,7 +98,14 @@ struct CgState {
   double* rr;      // ||r||^2 after the last update
   int* active;     // 1 while the system iterates
   int* iters;      // iterations done
+  // Stagnation test (null = off): smallest ||r||^2 so far and the iteration it was reached.
+  double* rr_best;
+  int* it_best;
 };
+
+// A system whose residual norm has not halved within this many iterations has reached the
+// attainable accuracy of its arithmetic (FP32 inner solves: the FP64 refinement takes over).
+constexpr int kStagnationWindow = 30;
 
 // Diagonal preconditioner 1 / max(0.5|G|^2 - e_v, 1 Ha) (a reading: the paper
 // says only that the CG is preconditioned).
@@ -136,6 +143,7 @@ WGW_HD void cg_init_a_body(int s, const SphereTab& sp, int n, const T* Bv, T* X,
     st.rr[s] = bb;
     st.active[s] = bb > 0.0 ? 1 : 0;
     st.iters[s] = 0;
+    if (st.rr_best) { st.rr_best[s] = bb; st.it_best[s] = 0; }
   }
 }
 
@@ -180,7 +188,12 @@ WGW_HD void cg_step_a_body(int s, const SphereTab& sp, int n, T* X, T* R, T* Z, 
     st.rr[s] = rr;
     const int it = st.iters[s] + 1;
     st.iters[s] = it;
-    if (rr <= tol2 * st.bb[s] || it >= max_iter || !(pq > 0.0)) st.active[s] = 0;
+    bool stalled = false;
+    if (st.rr_best) {
+      if (rr < 0.25 * st.rr_best[s]) { st.rr_best[s] = rr; st.it_best[s] = it; }
+      else stalled = it - st.it_best[s] >= kStagnationWindow;
+    }
+    if (rr <= tol2 * st.bb[s] || it >= max_iter || !(pq > 0.0) || stalled) st.active[s] = 0;
   }
 }
 

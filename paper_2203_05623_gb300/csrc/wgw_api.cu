@@ -212,7 +212,7 @@ struct wgw_ctx {
   // apply work space (double unless noted)
   DevBuf dvin, dv_rb, dv_r, Trho, Dr, drho_rb, eps, a_idx, b_idx, brow, cg_rz, cg_bb, cg_rr,
       cg_act, cg_it, cnt, rr64, act64, norms, pc_work, sys_list, list64, cg_rzi, omg, row_list, rowact,
-      drho_all, psi_tc;
+      drho_all, psi_tc, cg_best, cg_itbest;
   cudaStream_t stream = nullptr;
   Prof prof;
   std::vector<int> last_iters;      // per system of the last apply: CG iterations (all refinements)
@@ -251,7 +251,7 @@ struct wgw_ctx {
     d.release(); f.release(); wfc.release(); rho.release();
     DevBuf* all[] = {&e_v_d, &dvin, &dv_rb, &dv_r, &Trho, &Dr, &drho_rb, &eps, &a_idx, &b_idx, &brow,
                      &cg_rz, &cg_bb, &cg_rr, &cg_act, &cg_it, &cnt, &rr64, &act64, &norms, &pc_work, &sys_list, &list64, &cg_rzi, &omg,
-                     &row_list, &rowact, &drho_all, &psi_tc};
+                     &row_list, &rowact, &drho_all, &psi_tc, &cg_best, &cg_itbest};
     for (DevBuf* b : all) b->release();
     if (stream) cudaStreamDestroy(stream);
   }
@@ -346,10 +346,13 @@ int apply_A(wgw_ctx* c, Prec<T>& pr, const T* P, T* Q, int n_list, const int* li
 // tolerance, and the FP64 residual of the refinement uses the full projections.
 constexpr bool kProjectInnerOutput = false;
 
-CgState cg_state(wgw_ctx* c) {
+// stagnation: stop a system whose residual has stopped decreasing (FP32 inner solves only).
+CgState cg_state(wgw_ctx* c, bool stagnation = false) {
   CgState s;
   s.rz = c->cg_rz.as<double>(); s.bb = c->cg_bb.as<double>(); s.rr = c->cg_rr.as<double>();
   s.active = c->cg_act.as<int>(); s.iters = c->cg_it.as<int>();
+  s.rr_best = stagnation ? c->cg_best.as<double>() : nullptr;
+  s.it_best = stagnation ? c->cg_itbest.as<int>() : nullptr;
   return s;
 }
 
@@ -377,7 +380,7 @@ int cg_solve(wgw_ctx* c, Prec<T>& pr, int n_sys, double tol, int max_iter, cudaS
   const T* Bv = pr.Bv.template as<T>();
   const T* Psi = pr.psi.template as<T>();
   const double* eps = c->eps.as<double>();
-  CgState cs = cg_state(c);
+  CgState cs = cg_state(c, sizeof(T) == sizeof(float));
   const int* act = cs.active;
   const double vb = (double)n_sys * n * sizeof(T);
   WGW_CK(c->prof.run(PK_CG, 4 * vb, 0, st, [&] {
@@ -431,6 +434,8 @@ int ensure_work(wgw_ctx* c, int n_sys, int n_real) {
   WGW_TRY(c->cg_rr.ensure(sizeof(double) * n_sys));
   WGW_TRY(c->cg_act.ensure(sizeof(int) * n_sys));
   WGW_TRY(c->cg_it.ensure(sizeof(int) * n_sys));
+  WGW_TRY(c->cg_best.ensure(sizeof(double) * n_sys));
+  WGW_TRY(c->cg_itbest.ensure(sizeof(int) * n_sys));
   WGW_TRY(c->rr64.ensure(sizeof(double) * n_sys));
   WGW_TRY(c->act64.ensure(sizeof(int) * n_sys));
   WGW_TRY(c->sys_list.ensure(sizeof(int) * n_sys));
