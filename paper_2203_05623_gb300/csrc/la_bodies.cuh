@@ -31,12 +31,47 @@ WGW_HD double block_sum(double v, double* red, Thr th) {
 #endif
 }
 
-// Dot product of two length-n vectors: per-thread partial sums in T, block sum in double.
+// FP32 partial sums: reduced within each warp in FP32, across warps in FP64 (a warp-level
+// FP64 tree would run on GB300's FP64 pipe, 1/64 of the FP32 rate, for every thread).
+WGW_HD double block_sum(float v, double* red, Thr th) {
+#if defined(__CUDA_ARCH__)
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = th.tid >> 5, l = th.tid & 31, nw = (th.nth + 31) >> 5;
+  if (l == 0) red[w] = double(v);
+  __syncthreads();
+  if (th.tid == 0) {
+    double s = 0.0;
+    for (int k = 0; k < nw; ++k) s += red[k];
+    red[32] = s;
+  }
+  __syncthreads();
+  const double r = red[32];
+  __syncthreads();
+  return r;
+#else
+  (void)red; (void)th;
+  return double(v);
+#endif
+}
+
+// Dot product of two length-n vectors: per-thread partial sums in T, then block_sum.
+// Rows start 16-byte aligned (row lengths are multiples of 32), so FP32 rows are read as float4.
 template <typename T>
 WGW_HD double block_dot(const T* a, const T* b, int n, double* red, Thr th) {
   T part = T(0);
-  for (int i = th.tid; i < n; i += th.nth) part += a[i] * b[i];
-  return block_sum(double(part), red, th);
+  int i0 = 0;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    const int n4 = n / 4;
+    const float4* a4 = reinterpret_cast<const float4*>(a);
+    const float4* b4 = reinterpret_cast<const float4*>(b);
+    for (int q = th.tid; q < n4; q += th.nth) {
+      const float4 x = a4[q], y = b4[q];
+      part += x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w;
+    }
+    i0 = 4 * n4;
+  }
+  for (int i = i0 + th.tid; i < n; i += th.nth) part += a[i] * b[i];
+  return block_sum(part, red, th);
 }
 
 // ---------------------------------------------------------------- P_c = 1 - P_v
@@ -176,14 +211,35 @@ WGW_HD void cg_step_a_body(int s, const SphereTab& sp, int n, T* X, T* R, T* Z, 
   const T a = T(alpha);
   const double e = eps[s];
   T part = T(0);
-  for (int i = th.tid; i < n; i += th.nth) {
+  int i0 = 0;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    const int n4 = n / 4;
+    const float ef = static_cast<float>(e);
+    for (int qd = th.tid; qd < n4; qd += th.nth) {
+      const float4 pv = reinterpret_cast<const float4*>(p)[qd], qv = reinterpret_cast<const float4*>(q)[qd];
+      float4 xv = reinterpret_cast<float4*>(x)[qd], rv = reinterpret_cast<float4*>(r)[qd];
+      const float4 gv = reinterpret_cast<const float4*>(sp.g2f)[qd];
+      xv.x += a * pv.x; xv.y += a * pv.y; xv.z += a * pv.z; xv.w += a * pv.w;
+      rv.x -= a * qv.x; rv.y -= a * qv.y; rv.z -= a * qv.z; rv.w -= a * qv.w;
+      float4 zv;
+      // z = M^-1 r with M^-1 evaluated exactly as precond<float>
+      zv.x = (1.0f / fmaxf(gv.x - ef, 1.0f)) * rv.x; zv.y = (1.0f / fmaxf(gv.y - ef, 1.0f)) * rv.y;
+      zv.z = (1.0f / fmaxf(gv.z - ef, 1.0f)) * rv.z; zv.w = (1.0f / fmaxf(gv.w - ef, 1.0f)) * rv.w;
+      reinterpret_cast<float4*>(x)[qd] = xv;
+      reinterpret_cast<float4*>(r)[qd] = rv;
+      reinterpret_cast<float4*>(z)[qd] = zv;
+      part += rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
+    }
+    i0 = 4 * n4;
+  }
+  for (int i = i0 + th.tid; i < n; i += th.nth) {
     x[i] += a * p[i];
     const T ri = r[i] - a * q[i];
     r[i] = ri;
     z[i] = precond<T>(sp, i, e) * ri;
     part += ri * ri;
   }
-  const double rr = block_sum(double(part), red, th);
+  const double rr = block_sum(part, red, th);
   if (th.tid == 0) {
     st.rr[s] = rr;
     const int it = st.iters[s] + 1;
@@ -208,7 +264,18 @@ WGW_HD void cg_step_b_body(int s, int n, const T* R, const T* Z, T* P, long ld, 
   const double rz = block_dot(r, z, n, red, th);
   const double beta = st.rz[s] != 0.0 ? rz / st.rz[s] : 0.0;
   const T bt = T(beta);
-  for (int i = th.tid; i < n; i += th.nth) p[i] = z[i] + bt * p[i];
+  int i0 = 0;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    const int n4 = n / 4;
+    for (int qd = th.tid; qd < n4; qd += th.nth) {
+      const float4 zv = reinterpret_cast<const float4*>(z)[qd];
+      float4 pv = reinterpret_cast<float4*>(p)[qd];
+      pv.x = zv.x + bt * pv.x; pv.y = zv.y + bt * pv.y; pv.z = zv.z + bt * pv.z; pv.w = zv.w + bt * pv.w;
+      reinterpret_cast<float4*>(p)[qd] = pv;
+    }
+    i0 = 4 * n4;
+  }
+  for (int i = i0 + th.tid; i < n; i += th.nth) p[i] = z[i] + bt * p[i];
   if (th.tid == 0) st.rz[s] = rz;
 }
 
@@ -245,7 +312,7 @@ WGW_HD void cocg_init_a_body(int s, const SphereTab& sp, int n, const T* Bv, T* 
       part += bi * bi;
     }
   }
-  const double bb = block_sum(double(part), red, th);
+  const double bb = block_sum(part, red, th);
   if (th.tid == 0) {
     st.bb[s] = bb;
     st.rr[s] = bb;
@@ -269,8 +336,8 @@ WGW_HD void cocg_init_b_body(int s, int n, const T* R, const T* Z, T* P, long ld
     a += ru[i] * zu[i] - rv[i] * zv[i];
     b += ru[i] * zv[i] + rv[i] * zu[i];
   }
-  const double re = block_sum(double(a), red, th);
-  const double im = block_sum(double(b), red, th);
+  const double re = block_sum(a, red, th);
+  const double im = block_sum(b, red, th);
   if (th.tid == 0) { st.rz_re[s] = re; st.rz_im[s] = im; }
 }
 
@@ -292,8 +359,8 @@ WGW_HD void cocg_step_a_body(int s, const SphereTab& sp, int n, T* X, T* R, T* Z
     a += pu[i] * qa - pv[i] * qb;
     b += pu[i] * qb + pv[i] * qa;
   }
-  const double sr = block_sum(double(a), red, th);
-  const double si = block_sum(double(b), red, th);
+  const double sr = block_sum(a, red, th);
+  const double si = block_sum(b, red, th);
   const double d2 = sr * sr + si * si;
   const double rr0 = st.rz_re[s], ri0 = st.rz_im[s];
   const double ar = d2 > 0 ? (rr0 * sr + ri0 * si) / d2 : 0.0;   // alpha = rho / sigma
@@ -316,7 +383,7 @@ WGW_HD void cocg_step_a_body(int s, const SphereTab& sp, int n, T* X, T* R, T* Z
     zv[i] = m * nv;
     part += nu * nu + nv * nv;
   }
-  const double rr = block_sum(double(part), red, th);
+  const double rr = block_sum(part, red, th);
   if (th.tid == 0) {
     st.rr[s] = rr;
     const int it = st.iters[s] + 1;
@@ -338,8 +405,8 @@ WGW_HD void cocg_step_b_body(int s, int n, const T* R, const T* Z, T* P, long ld
     a += ru[i] * zu[i] - rv[i] * zv[i];
     b += ru[i] * zv[i] + rv[i] * zu[i];
   }
-  const double nr = block_sum(double(a), red, th);
-  const double ni = block_sum(double(b), red, th);
+  const double nr = block_sum(a, red, th);
+  const double ni = block_sum(b, red, th);
   const double orr = st.rz_re[s], ori = st.rz_im[s];
   const double d2 = orr * orr + ori * ori;
   const double br = d2 > 0 ? (nr * orr + ni * ori) / d2 : 0.0;

@@ -1310,7 +1310,7 @@ int wgw_default_options(wgw_options* opt) {
   opt->cg_tol = 1e-12;
   opt->max_cg_iter = 2000;
   opt->max_refine = 8;
-  opt->inner_tol = 1e-5;
+  opt->inner_tol = 5e-6;
   opt->f_s = 2.0;
   opt->check_every = 8;
   opt->dav_tol = 1e-8;
