@@ -270,11 +270,20 @@ def main():
 
     hbm, peak_kind = peaks()
     d = prof[dom]
-    achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9 if d["ms"] > 0 else 0.0
+    per_launch = d["bytes"] / max(d["launches"], 1)
+    if dom == "pc_project":
+        # CUDA-core FP32 GEMMs: bound by the FP32 FMA rate (152 SMs x 128 lanes x 2 flop x 2.07 GHz).
+        bound, unit, peak, peak_src = "alu", "TFLOP/s", 152 * 128 * 2 * 2.07e9 / 1e12, "FP32 FMA unit count x max SM clock"
+        achieved = d["flops"] / (d["ms"] / 1e3) / 1e12 if d["ms"] > 0 else 0.0
+    else:
+        bound, unit, peak, peak_src = "hbm", "GB/s", hbm, peak_kind
+        achieved = per_launch / (d["ms"] / 1e3 / max(d["launches"], 1)) / 1e9 if d["ms"] > 0 else 0.0
     traffic = None
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            traffic = json.load(f).get(args.workload, {}).get(dom)
+            t = json.load(f).get(args.workload, {}).get(dom)
+        if t:
+            traffic = t["dram_over_algorithmic"] * per_launch
     except Exception:
         traffic = None
     line = {
@@ -294,10 +303,13 @@ def main():
                   "max_rel_residual": stats["max_rel_residual"]},
         "e2e": {"value": world * n_sys * args.steps / e2e_total, "unit": "Sternheimer solves/s",
                 "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_kind,
+        "roofline": {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                     "algorithmic_bytes_per_launch": per_launch,
                      "launches": d["launches"], "avg_launch_ms": d["ms"] / max(d["launches"], 1),
-                     "timed_from": "CUDA events around each launch of this class inside the timed steps"},
+                     "timed_from": "CUDA events around each launch of this class inside the timed steps",
+                     "traffic_from": "DRAM/algorithmic byte ratio of one ncu capture (profiles/traffic.json) "
+                                     "x the algorithmic bytes of the average timed launch"},
         "kernel_share": {k: round(v["ms"] / max(sum(q["ms"] for q in prof_all.values()), 1e-9), 4)
                          for k, v in sorted(prof_all.items(), key=lambda kv: -kv[1]["ms"]) if v["launches"]},
         "kernel_share_from": "one untimed step after warm-up with every launch bracketed by CUDA events",
