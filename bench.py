@@ -32,6 +32,10 @@ WORKLOADS = {
     "pdep_L16_48": dict(config="pdep_L16_48", n_pert=64, pert_seed=5, cg_tol=1e-10,
                         desc="chibar0 block apply, 64 perturbations x 64 occupied states = 4096 "
                              "Sternheimer systems, 48^3 grid, N_pw=4169, N_rho=33833, mixed FP32/FP64"),
+    "serve_L16_48": dict(config="pdep_L16_48", n_pert=16, pert_seed=5, cg_tol=1e-10,
+                         desc="served stream on the 48^3 model: chibar0 requests of 4-16 perturbations "
+                              "(256-1024 Sternheimer systems), Poisson arrivals (seed 6) at 0.3/0.6/0.9 of "
+                              "the measured closed-loop capacity, merged into batched applies"),
     "chi0_L10_24": dict(config="chi0_L10_24", n_pert=8, pert_seed=2, cg_tol=1e-10,
                         desc="chi0 apply, 8 perturbations x 4 occupied states = 32 Sternheimer systems, "
                              "24^3 grid, N_pw=515, N_rho=4337, mixed FP32/FP64"),
@@ -148,6 +152,72 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args, wl):
+    """Served stream: requests submitted at Poisson arrival times through wgw_submit/wgw_wait."""
+    import numpy as np
+    import synth
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2203_05623_gb300 import build
+    build.build()
+    import paper_2203_05623_gb300 as W
+    s = synth.make_system(wl["config"])
+    pool = synth.perturbations(s.miller_rho, s.L, wl["n_pert"], wl["pert_seed"])
+    opt = W.wgw_default_options(precision=W.WGW_MIXED, cg_tol=wl["cg_tol"], max_cg_iter=200)
+    ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, opt)
+    for _ in range(max(args.warmup, 1)):
+        W.wgw_apply_chibar0(ctx, pool)
+    t0 = time.perf_counter()
+    _, st, _ = W.wgw_apply_chibar0(ctx, pool)
+    capacity = st["n_systems"] / (time.perf_counter() - t0)      # closed-loop systems/s
+    rng = np.random.default_rng(6)
+    results = []
+    with Clocks(local) as clk:
+        for load in (0.3, 0.6, 0.9):
+            sizes = rng.integers(4, wl["n_pert"] + 1, size=100000)
+            mean_sys = float(np.mean(sizes)) * s.n_v
+            rate = load * capacity / mean_sys                       # requests/s
+            duration = max(2.0, 4.0 * args.steps)
+            gaps = rng.exponential(1.0 / rate, size=100000)
+            arrivals = np.cumsum(gaps)
+            n_req = int(np.searchsorted(arrivals, duration))
+            tickets, t_start = [], time.perf_counter()
+            for k in range(n_req):
+                dt = arrivals[k] - (time.perf_counter() - t_start)
+                if dt > 0:
+                    time.sleep(dt)
+                cols = rng.choice(wl["n_pert"], size=int(sizes[k]), replace=False)
+                tickets.append((W.wgw_submit(ctx, pool[:, cols]), int(sizes[k]) * s.n_v))
+            lat, systems, merged = [], 0, []
+            for t, nsys in tickets:
+                _, res = W.wgw_wait(t)
+                if res["status"] != W.WGW_OK:
+                    raise RuntimeError(f"request failed with status {res['status']}")
+                lat.append(res["latency_s"])
+                merged.append(res["batch_requests"])
+                systems += nsys
+            span = time.perf_counter() - t_start
+            lat = np.sort(np.array(lat))
+            results.append({"load": load, "requests": n_req, "offered_systems_per_s": load * capacity,
+                            "served_systems_per_s": systems / span,
+                            "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)),
+                                           "p99": 1e3 * float(np.percentile(lat, 99))},
+                            "mean_requests_per_batch": float(np.mean(merged))})
+    if rank == 0:
+        mid = results[1]
+        print(json.dumps({
+            "metric": "served Sternheimer solves/s and request latency (arrival -> result on the host)",
+            "value": mid["served_systems_per_s"], "unit": "Sternheimer solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"], "cg_tol": wl["cg_tol"],
+                       "closed_loop_capacity_systems_per_s": capacity},
+            "latency_ms": mid["latency_ms"], "loads": results, "clocks": clk.summary()}), flush=True)
+    W.wgw_destroy(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -169,6 +239,8 @@ def main():
         wl["desc"] += f" (reduced to {args.n_pert} perturbations)"
     if args.impl == "reference":
         return run_reference(args, wl)
+    if args.workload.startswith("serve"):
+        return run_serve(args, wl)
 
     import numpy as np
     import torch

@@ -101,7 +101,7 @@ def test_davidson_config48_matches_golden(W):
     s = synth.make_system("pdep_L16_48")
     ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v,
                       W.wgw_default_options(precision=W.WGW_MIXED, cg_tol=1e-10, dav_tol=1e-10,
-                                            max_cg_iter=200))
+                                            max_cg_iter=200, dav_max_iter=250))
     x0 = synth.perturbations(s.miller_rho, s.L, 64, 11)
     eig, _, st, _ = W.wgw_pdep_davidson(ctx, 64, x0, want_basis=False)
     assert st["n_converged"] == 64
