@@ -4,7 +4,8 @@
 // z = a + i b (Gamma point).  In reciprocal space a function is held in the
 // real plane-wave basis: element 0 = f(G=0) (real), elements 2j-1, 2j =
 // sqrt2 Re f(G_j), sqrt2 Im f(G_j) for the j-th positive member G_j of the
-// sphere.  With Z(G) = A(G) + i B(G):
+// sphere (positive members numbered plane by plane in ascending (h, k, l)).
+// With Z(G) = A(G) + i B(G):
 //   Z(+G_j) = [(ar - bi) + i (ai + br)] / sqrt2,  Z(-G_j) = [(ar + bi) + i (br - ai)] / sqrt2,
 //   A(G_j) = [Z(G_j) + Z(-G_j)^*] / 2,  B(G_j) = [Z(G_j) - Z(-G_j)^*] / (2i).
 //

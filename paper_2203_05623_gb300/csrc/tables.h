@@ -13,6 +13,9 @@ namespace wgw {
 // A plane-wave sphere 0.5|G|^2 <= ecut of a cubic cell, in canonical order
 // (ascending h^2+k^2+l^2, then (h, k, l) lexicographically), with its
 // real-basis pairing and the per-plane grid tables described in common.cuh.
+// The real basis (internal to the library) numbers the pairs plane by plane: positive
+// members in ascending (h, k, l), so that the points of one plane h are a contiguous range
+// of real-basis elements and the plane kernels read and write them coalesced.
 struct SphereHostTables {
   int n = 0;                 // plane waves
   int n_pairs = 0;           // positive members
@@ -63,12 +66,19 @@ inline void build_sphere(double L, double ecut, int N, SphereHostTables& s) {
   for (int i = 0; i < s.n; ++i) where[key(pts[i].h, pts[i].k, pts[i].l)] = i;
   s.pos.assign(1, 0);
   s.neg.assign(1, 0);
+  std::vector<int> posi;
   for (int i = 0; i < s.n; ++i) {
     if (pts[i].n2 == 0) s.i0 = i;
-    if (positive_member(pts[i].h, pts[i].k, pts[i].l)) {
-      s.pos.push_back(i);
-      s.neg.push_back(where[key(-pts[i].h, -pts[i].k, -pts[i].l)]);
-    }
+    if (positive_member(pts[i].h, pts[i].k, pts[i].l)) posi.push_back(i);
+  }
+  std::sort(posi.begin(), posi.end(), [&](int a, int c) {
+    if (pts[a].h != pts[c].h) return pts[a].h < pts[c].h;
+    if (pts[a].k != pts[c].k) return pts[a].k < pts[c].k;
+    return pts[a].l < pts[c].l;
+  });
+  for (int i : posi) {
+    s.pos.push_back(i);
+    s.neg.push_back(where[key(-pts[i].h, -pts[i].k, -pts[i].l)]);
   }
   s.pos[0] = s.neg[0] = s.i0;
   s.n_pairs = (int)s.pos.size() - 1;
