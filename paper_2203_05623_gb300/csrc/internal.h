@@ -164,6 +164,7 @@ cudaError_t launch_kb(T* Q, const T* P, long ld, int n_sys, const int* list, con
 // Ordered list of the systems s < n_sys with active[s] != 0, and their count.
 cudaError_t launch_build_list(const int* active, int n_sys, int* list, int* count, cudaStream_t st);
 int pc_kblocks(int n, int n_sys);
+int pcf_kblocks(int n, int n_sys);
 size_t pc_work_elems(int n, int n_sys, int nv);
 template <typename T>
 cudaError_t launch_cg_init_a(const SphereTab& sp, int n, int n_sys, const T* Bv, T* X, T* R, T* Z,

@@ -212,6 +212,186 @@ __global__ void __launch_bounds__(256) k_pc_gemm1(const T* __restrict__ Psi, lon
   }
 }
 
+// ---------------------------------------------------------------- FP32 P_c, wide tiles
+// The FP32 projector of the inner solves: tiles of 128 systems x 64 states with 4 x 8 values
+// per thread (three float4 shared-memory reads per 32 FMAs), K chunks of 32 double-buffered
+// through registers.  Same partial-sum layout as k_pc_gemm1 (Cpart[kb][v][j], v padded to 64).
+constexpr int kFS = 128, kFV = 64, kFK = 32, kFLA = kFV + 4, kFLB = kFS + 4;
+constexpr size_t kF1Smem = sizeof(float) * 2 * kFK * (kFLA + kFLB);
+
+__device__ __forceinline__ float4 ldg4z(const float* row, int k, int k_hi) {
+  if (k + 4 <= k_hi) return *reinterpret_cast<const float4*>(row + k);
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (k < k_hi) v.x = row[k];
+  if (k + 1 < k_hi) v.y = row[k + 1];
+  if (k + 2 < k_hi) v.z = row[k + 2];
+  if (k + 3 < k_hi) v.w = row[k + 3];
+  return v;
+}
+
+__global__ void __launch_bounds__(256) k_pcf_gemm1(const float* __restrict__ Psi, long ldp,
+                                                   const float* __restrict__ Y, long ldy, int n, int nv,
+                                                   int n_list, const int* __restrict__ list, int kblk,
+                                                   float* __restrict__ Cpart) {
+  extern __shared__ __align__(16) float fsm[];
+  float* As = fsm;                        // [2][kFK][kFLA]  (k, state)
+  float* Bs = fsm + 2 * kFK * kFLA;       // [2][kFK][kFLB]  (k, system)
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int j0 = blockIdx.x * kFS, kb = blockIdx.y, v0 = blockIdx.z * kFV;
+  const int k_lo = kb * kblk, k_hi = min(n, k_lo + kblk);
+  const int lr = tid >> 3, lq = tid & 7;   // loader: row (of 32) and 16-byte column
+  const float* brow[4];
+  const float* arow[2];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int j = j0 + lr + 32 * r;
+    brow[r] = j < n_list ? Y + (size_t)(list ? list[j] : j) * ldy : nullptr;
+  }
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int v = v0 + lr + 32 * r;
+    arow[r] = v < nv ? Psi + (size_t)v * ldp : nullptr;
+  }
+  float4 pa[2], pb[4];
+  auto fetch = [&](int k0) {
+    const int k = k0 + lq * 4;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) pa[r] = arow[r] ? ldg4z(arow[r], k, k_hi) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) pb[r] = brow[r] ? ldg4z(brow[r], k, k_hi) : make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+  auto stash = [&](int st) {
+    float* A = As + st * kFK * kFLA;
+    float* B = Bs + st * kFK * kFLB;
+    const int kk = lq * 4;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int v = lr + 32 * r;
+      A[(kk + 0) * kFLA + v] = pa[r].x; A[(kk + 1) * kFLA + v] = pa[r].y;
+      A[(kk + 2) * kFLA + v] = pa[r].z; A[(kk + 3) * kFLA + v] = pa[r].w;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int j = lr + 32 * r;
+      B[(kk + 0) * kFLB + j] = pb[r].x; B[(kk + 1) * kFLB + j] = pb[r].y;
+      B[(kk + 2) * kFLB + j] = pb[r].z; B[(kk + 3) * kFLB + j] = pb[r].w;
+    }
+  };
+  float acc[4][8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  int st = 0;
+  if (k_lo < k_hi) {
+    fetch(k_lo);
+    stash(0);
+    __syncthreads();
+  }
+  for (int k0 = k_lo; k0 < k_hi; k0 += kFK) {
+    const bool more = k0 + kFK < k_hi;
+    if (more) fetch(k0 + kFK);
+    const float* A = As + st * kFK * kFLA;
+    const float* B = Bs + st * kFK * kFLB;
+#pragma unroll 8
+    for (int kk = 0; kk < kFK; ++kk) {
+      const float4 a = *reinterpret_cast<const float4*>(A + kk * kFLA + ty * 4);
+      const float4 b0 = *reinterpret_cast<const float4*>(B + kk * kFLB + tx * 8);
+      const float4 b1 = *reinterpret_cast<const float4*>(B + kk * kFLB + tx * 8 + 4);
+      const float av[4] = {a.x, a.y, a.z, a.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    if (more) {
+      stash(st ^ 1);
+      __syncthreads();
+      st ^= 1;
+    }
+  }
+  const int nvp = gridDim.z * kFV;
+  float* out = Cpart + (size_t)kb * nvp * n_list;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int v = v0 + ty * 4 + i;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int jx = j0 + tx * 8 + j;
+      if (jx < n_list) out[(size_t)v * n_list + jx] = acc[i][j];
+    }
+  }
+}
+
+// Y[:, s_j] = beta Y + alpha Psi C for 64 rows x 128 systems per block, 4 rows x 8 systems per thread.
+constexpr int kF2R = 64, kF2LP = kF2R + 4;
+constexpr size_t kF2Smem = sizeof(float) * kFV * (kF2LP + kFLB);
+
+__global__ void __launch_bounds__(256) k_pcf_gemm2(const float* __restrict__ Psi, long ldp, float* __restrict__ Y,
+                                                   long ldy, int n, int nv, int n_list,
+                                                   const int* __restrict__ list, const float* __restrict__ C,
+                                                   long ldc, float alpha, float beta,
+                                                   const int* __restrict__ active) {
+  extern __shared__ __align__(16) float fsm[];
+  float* Ps = fsm;                    // [kFV][kF2LP]  (state, row)
+  float* Cs = fsm + kFV * kF2LP;      // [kFV][kFLB]   (state, system)
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int i0 = blockIdx.x * kF2R, j0 = blockIdx.y * kFS;
+  if (active) {
+    int any = 0;
+    for (int t = tid; t < kFS && j0 + t < n_list; t += 256) any |= active[list ? list[j0 + t] : j0 + t];
+    if (!__syncthreads_or(any)) return;
+  }
+  float acc[4][8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  for (int vc = 0; vc < nv; vc += kFV) {
+    for (int e = tid; e < kFV * (kF2R / 4); e += 256) {   // Psi rows as float4 along k
+      const int vv = e / (kF2R / 4), q = e % (kF2R / 4), v = vc + vv, i = i0 + q * 4;
+      const float4 x = v < nv ? ldg4z(Psi + (size_t)v * ldp, i, n) : make_float4(0.f, 0.f, 0.f, 0.f);
+      *reinterpret_cast<float4*>(Ps + vv * kF2LP + q * 4) = x;
+    }
+    for (int e = tid; e < kFV * kFS; e += 256) {
+      const int vv = e / kFS, c = e % kFS, v = vc + vv, jx = j0 + c;
+      Cs[vv * kFLB + c] = (v < nv && jx < n_list) ? C[(size_t)v * ldc + jx] : 0.f;
+    }
+    __syncthreads();
+    const int vmax = min(kFV, nv - vc);
+    for (int vv = 0; vv < vmax; ++vv) {
+      const float4 a = *reinterpret_cast<const float4*>(Ps + vv * kF2LP + tx * 4);
+      const float4 b0 = *reinterpret_cast<const float4*>(Cs + vv * kFLB + ty * 8);
+      const float4 b1 = *reinterpret_cast<const float4*>(Cs + vv * kFLB + ty * 8 + 4);
+      const float av[4] = {a.x, a.y, a.z, a.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  const int r0 = i0 + tx * 4;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int jx = j0 + ty * 8 + j;
+    if (jx >= n_list) continue;
+    const int sx = list ? list[jx] : jx;
+    if (active && !active[sx]) continue;
+    float* y = Y + (size_t)sx * ldy + r0;
+    if (r0 + 4 <= n) {
+      float4 w = beta != 0.f ? *reinterpret_cast<float4*>(y) : make_float4(0.f, 0.f, 0.f, 0.f);
+      w.x = beta * w.x + alpha * acc[0][j]; w.y = beta * w.y + alpha * acc[1][j];
+      w.z = beta * w.z + alpha * acc[2][j]; w.w = beta * w.w + alpha * acc[3][j];
+      *reinterpret_cast<float4*>(y) = w;
+    } else {
+      for (int i = 0; i < 4 && r0 + i < n; ++i) y[i] = (beta != 0.f ? beta * y[i] : 0.f) + alpha * acc[i][j];
+    }
+  }
+}
+
 // C[e] = sum_kb Cpart[kb * slice + e] (fixed order).
 __global__ void k_sum_slices(const double* __restrict__ Cpart, size_t slice, int n_kb, double* __restrict__ C) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < slice; e += (size_t)gridDim.x * blockDim.x) {
@@ -416,6 +596,33 @@ cudaError_t launch_pc(T* Y, long ldy, int n_sys, const int* list, const T* Psi, 
   const int nvp = (nv + kGT - 1) / kGT * kGT;
   dim3 g1((n_sys + kGT - 1) / kGT, n_kb, nvp / kGT);
   const bool use_ff = ffc && sizeof(T) == sizeof(double);
+  if constexpr (sizeof(T) == sizeof(float)) {
+    // FP32: the wide-tile kernels, split over K so that even a short list of systems fills the
+    // GPU (kblk a multiple of the 32-element K chunk).
+    const int nkb_f = pcf_kblocks(n, n_sys);
+    const int kblk32 = ((n + nkb_f - 1) / nkb_f + kFK - 1) / kFK * kFK;
+    cudaError_t e = cudaFuncSetAttribute(k_pcf_gemm1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kF1Smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_pcf_gemm2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kF2Smem);
+    if (e != cudaSuccess) return e;
+    dim3 gf1((n_sys + kFS - 1) / kFS, (n + kblk32 - 1) / kblk32, nvp / kGT);
+    const int n_kb32 = (int)gf1.y;
+    k_pcf_gemm1<<<gf1, 256, kF1Smem, st>>>(reinterpret_cast<const float*>(Psi), ldp, reinterpret_cast<const float*>(Y),
+                                           ldy, n, nv, n_sys, list, kblk32, reinterpret_cast<float*>(work));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (n_kb32 > 1) {
+      const size_t slice = (size_t)nvp * n_sys;
+      k_pc_reduce<T><<<(int)std::min<size_t>((slice + 255) / 256, 4096), 256, 0, st>>>(work, slice, n_kb32);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    dim3 gf2((n + kF2R - 1) / kF2R, (n_sys + kFS - 1) / kFS);
+    k_pcf_gemm2<<<gf2, 256, kF2Smem, st>>>(reinterpret_cast<const float*>(Psi), ldp, reinterpret_cast<float*>(Y), ldy,
+                                           n, nv, n_sys, list, reinterpret_cast<const float*>(work), (long)n_sys,
+                                           -1.f, 1.f, active);
+    return cudaGetLastError();
+  }
   if (use_ff) k_pc_gemm1<T, ff_if_double<T>><<<g1, 256, 0, st>>>(Psi, ldp, Y, ldy, n, nv, n_sys, list, kblk, work);
   else k_pc_gemm1<T><<<g1, 256, 0, st>>>(Psi, ldp, Y, ldy, n, nv, n_sys, list, kblk, work);
   cudaError_t err = cudaGetLastError();
@@ -484,6 +691,13 @@ cudaError_t launch_build_list(const int* active, int n_sys, int* list, int* coun
   return cudaGetLastError();
 }
 
+// K blocks of the FP32 wide-tile P_c: about two CTAs per SM, each at least one 32-element chunk.
+int pcf_kblocks(int n, int n_sys) {
+  const int tiles = (n_sys + 127) / 128;
+  const int nkc = std::max(1, (n + 31) / 32);
+  return std::max(1, std::min(nkc, (2 * 152 + tiles - 1) / tiles));
+}
+
 int pc_kblocks(int n, int n_sys) {
   // Enough K blocks that phase 1 has >= ~4 CTAs per SM, each block >= 256 rows.
   const int s_tiles = (n_sys + kGT - 1) / kGT;
@@ -494,7 +708,7 @@ int pc_kblocks(int n, int n_sys) {
 
 size_t pc_work_elems(int n, int n_sys, int nv) {
   const int nvp = (nv + kGT - 1) / kGT * kGT;
-  return (size_t)pc_kblocks(n, n_sys) * nvp * n_sys;
+  return (size_t)std::max(pc_kblocks(n, n_sys), pcf_kblocks(n, n_sys)) * nvp * n_sys;
 }
 
 template <typename T>
