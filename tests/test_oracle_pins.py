@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import chi0, lanczos, pdep
+from oracle import chi0, dyson, lanczos, pdep
 from oracle.model import Model, sphere
 
 
@@ -297,3 +297,35 @@ def test_planted_missing_projector_fails_sos_pin(tiny, monkeypatch):
     bad = chi0.sternheimer_cg_drho(m, dV, tol=1e-12, max_iter=300)
     monkeypatch.undo()
     assert rel(bad, chi0.sos_drho(m, dV, [0.0])[:, :, 0]) > 1e-3
+
+
+def test_dyson_closed_form_on_the_spectrum():
+    """(1 - A)^-1 A = Q diag(l/(1-l)) Q^T for A = Q diag(l) Q^T; X commutes with A and, for
+    negative semidefinite A, has eigenvalues in (-1, 0] (epsilon^-1 - 1)."""
+    rng = np.random.default_rng(8)
+    n, nw = 12, 3
+    A = np.zeros((nw, n, n))
+    ref = np.zeros((nw, n, n))
+    for k in range(nw):
+        Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+        lam = -rng.uniform(0.0, 6.0, n)
+        A[k] = (Q * lam) @ Q.T
+        ref[k] = (Q * (lam / (1.0 - lam))) @ Q.T
+    X = dyson.chibar(A)
+    assert np.max(np.abs(X - ref)) < 1e-12
+    for k in range(nw):
+        assert np.max(np.abs(X[k] @ A[k] - A[k] @ X[k])) < 1e-12
+        w = np.linalg.eigvalsh(0.5 * (X[k] + X[k].T))
+        assert np.all(w > -1.0) and np.all(w <= 1e-12)
+    # Scalar case and a non-symmetric matrix: (1 - a)^-1 a, and (1 - A) X = A.
+    assert abs(dyson.chibar(np.array([[-3.0]]))[0, 0] - (-0.75)) < 1e-15
+    B = rng.standard_normal((5, 5)) * 0.1
+    assert np.max(np.abs((np.eye(5) - B) @ dyson.chibar(B) - B)) < 1e-13
+
+
+def test_planted_sign_error_fails_dyson_pin():
+    """Plant (1 + A)^-1 A in place of (1 - A)^-1 A: the spectral pin must fail."""
+    lam = np.array([-0.5, -2.0])
+    A = np.diag(lam)
+    wrong = np.linalg.solve(np.eye(2) + A, A)
+    assert np.max(np.abs(wrong - np.diag(lam / (1.0 - lam)))) > 0.1
