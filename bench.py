@@ -36,6 +36,9 @@ WORKLOADS = {
                          desc="served stream on the 48^3 model: chibar0 requests of 4-16 perturbations "
                               "(256-1024 Sternheimer systems), Poisson arrivals (seed 6) at 0.3/0.6/0.9 of "
                               "the measured closed-loop capacity, merged into batched applies"),
+    "dyson_P64_W32": dict(config=None, n_pert=64, pert_seed=32, cg_tol=0.0,
+                          desc="Dyson step (1 - chibar0)^-1 chibar0 for 32 imaginary frequencies of a "
+                               "64 x 64 PDEP-basis chibar0 (negative semidefinite, spectrum in [-8, 0])"),
     "chi0_L10_24": dict(config="chi0_L10_24", n_pert=8, pert_seed=2, cg_tol=1e-10,
                         desc="chi0 apply, 8 perturbations x 4 occupied states = 32 Sternheimer systems, "
                              "24^3 grid, N_pw=515, N_rho=4337, mixed FP32/FP64"),
@@ -152,6 +155,37 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def run_dyson(args, wl):
+    """The Dyson step of the next stage (wgw_dyson), host buffers, copies included."""
+    import numpy as np
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2203_05623_gb300 import build
+    build.build()
+    import paper_2203_05623_gb300 as W
+    n, nw = wl["n_pert"], wl["pert_seed"]
+    rng = np.random.default_rng(7)
+    A = np.zeros((nw, n, n))
+    for k in range(nw):
+        Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+        A[k] = (Q * -rng.uniform(0.0, 8.0, n)) @ Q.T
+    for _ in range(max(args.warmup, 1)):
+        W.wgw_dyson(A)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        W.wgw_dyson(A)
+        ts.append(time.perf_counter() - t0)
+    total = sum(ts)
+    print(json.dumps({"metric": "Dyson solves per second (one n x n matrix per imaginary frequency)",
+                      "value": nw * args.steps / total, "unit": "matrices/s", "n_gpus": 1, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": args.workload, "desc": wl["desc"],
+                                 "timed": "host call including the host <-> device copies"}}), flush=True)
+
+
 def run_serve(args, wl):
     """Served stream: requests submitted at Poisson arrival times through wgw_submit/wgw_wait."""
     import numpy as np
@@ -241,6 +275,8 @@ def main():
         return run_reference(args, wl)
     if args.workload.startswith("serve"):
         return run_serve(args, wl)
+    if args.workload.startswith("dyson"):
+        return run_dyson(args, wl)
 
     import numpy as np
     import torch

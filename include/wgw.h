@@ -249,6 +249,19 @@ int wgw_symm_eig_dev(int n, double* A_dev, double* w_dev, double* Z_dev, void* s
 int wgw_symm_eig_noalloc_dev(int n, double* A_dev, double* w_dev, double* Z_dev, void* stream);
 
 /*
+ * Dyson equation in a basis (Sec. 2: the screened response from the independent-particle one,
+ * epsilon^-1 - 1 = (1 - chibar0)^-1 chibar0 for the symmetrised responses), for every frequency
+ * of a batch, in FP64 on the GPU (Gaussian elimination with partial pivoting, one CTA per
+ * frequency).  No context is needed.
+ *   chi0bar  host, n_omega matrices n x n, row-major, frequency-major (the layout of
+ *            wgw_lanczos's chi0_pdep; a transposed layout gives the transposed result, since
+ *            the two factors commute).
+ *   chibar   host output, same layout: (1 - chi0bar)^-1 chi0bar.
+ * Returns WGW_ERR_ARG for n outside 1..4096 or when 1 - chi0bar is singular.
+ */
+int wgw_dyson(int n, int n_omega, const double* chi0bar, double* chibar);
+
+/*
  * Serving (no counterpart in the paper, which runs one calculation per job): non-blocking
  * requests on a context.  wgw_submit copies the request's inputs and returns a ticket at once;
  * one worker thread per context runs queued requests on the context's stream, merging all

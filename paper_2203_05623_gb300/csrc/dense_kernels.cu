@@ -465,6 +465,88 @@ cudaError_t launch_select_scale(int k, const double* Zc, int ldz, const int* col
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- Dyson equation
+// X = (1 - A)^-1 A for one n x n matrix per block (row-major, batch over imaginary
+// frequencies): Gaussian elimination of M = 1 - A with partial pivoting (ties to the lower
+// row), applied to the right-hand side X = A, then back substitution.  M is work space.
+// info[k] = 1 if frequency k met a zero pivot.
+__global__ void __launch_bounds__(256) k_dyson(int n, const double* __restrict__ A, double* __restrict__ X,
+                                               double* __restrict__ M, int* __restrict__ info) {
+  __shared__ double rv[32];
+  __shared__ int ri[32];
+  __shared__ int piv;
+  const size_t off = (size_t)blockIdx.x * n * n;
+  const double* a = A + off;
+  double* x = X + off;
+  double* m = M + off;
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, w = tid >> 5, nw = (nth + 31) >> 5;
+  for (int e = tid; e < n * n; e += nth) {
+    m[e] = (e / n == e % n ? 1.0 : 0.0) - a[e];
+    x[e] = a[e];
+  }
+  if (tid == 0) info[blockIdx.x] = 0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    double best = -1.0;
+    int bi = n;
+    for (int i = k + tid; i < n; i += nth) {
+      const double v = fabs(m[(size_t)i * n + k]);
+      if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { rv[w] = best; ri[w] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double b = -1.0;
+      int p = n;
+      for (int q = 0; q < nw; ++q)
+        if (rv[q] > b || (rv[q] == b && ri[q] < p)) { b = rv[q]; p = ri[q]; }
+      piv = p;
+      if (!(b > 0.0)) info[blockIdx.x] = 1;
+    }
+    __syncthreads();
+    const int p = piv;
+    if (p != k && p < n) {
+      for (int j = tid; j < n; j += nth) {
+        const double t = m[(size_t)k * n + j]; m[(size_t)k * n + j] = m[(size_t)p * n + j]; m[(size_t)p * n + j] = t;
+        const double u = x[(size_t)k * n + j]; x[(size_t)k * n + j] = x[(size_t)p * n + j]; x[(size_t)p * n + j] = u;
+      }
+    }
+    __syncthreads();
+    const double d = m[(size_t)k * n + k];
+    if (d != 0.0) {
+      const int rows = n - k - 1, cols = (n - k - 1) + n;   // M columns k+1.. then all X columns
+      for (int e = tid; e < rows * cols; e += nth) {
+        const int i = k + 1 + e / cols, c = e % cols;
+        const double f = m[(size_t)i * n + k] / d;
+        if (c < n - k - 1) m[(size_t)i * n + k + 1 + c] -= f * m[(size_t)k * n + k + 1 + c];
+        else x[(size_t)i * n + (c - (n - k - 1))] -= f * x[(size_t)k * n + (c - (n - k - 1))];
+      }
+    }
+    __syncthreads();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    const double d = m[(size_t)k * n + k];
+    for (int j = tid; j < n; j += nth) x[(size_t)k * n + j] = d != 0.0 ? x[(size_t)k * n + j] / d : 0.0;
+    __syncthreads();
+    for (int e = tid; e < k * n; e += nth) {
+      const int i = e / n, j = e % n;
+      x[(size_t)i * n + j] -= m[(size_t)i * n + k] * x[(size_t)k * n + j];
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_dyson(int n, int n_omega, const double* A, double* X, double* M, int* info, cudaStream_t st) {
+  if (n <= 0 || n_omega <= 0) return cudaSuccess;
+  k_dyson<<<n_omega, 256, 0, st>>>(n, A, X, M, info);
+  return cudaGetLastError();
+}
+
 }  // namespace wgw
 
 // ---------------------------------------------------------------- scratch-free variant

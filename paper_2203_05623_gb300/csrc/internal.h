@@ -197,6 +197,8 @@ template <typename T>
 cudaError_t launch_norm2(int n_sys, int n, const T* x, long ld, double* out, cudaStream_t st);
 // out[i] = in[i] as a float-float pair stored in the 8-byte slot i of out.
 cudaError_t launch_to_ff(size_t n, const double* in, double* out, cudaStream_t st);
+// X = (1 - A)^-1 A per n x n row-major matrix of a batch (dense_kernels.cu); M: work of the same size.
+cudaError_t launch_dyson(int n, int n_omega, const double* A, double* X, double* M, int* info, cudaStream_t st);
 // Count of nonzero entries of flags[0..n) into *out (one block).
 cudaError_t launch_count(const int* flags, int n, int* out, cudaStream_t st);
 

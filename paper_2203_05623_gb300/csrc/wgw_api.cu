@@ -1585,6 +1585,29 @@ int wgw_pdep_davidson(wgw_ctx* c, int n_pdep, const double* x0, double* eig, dou
   return davidson_impl(c, n_pdep, x0, eig, basis, st);
 }
 
+int wgw_dyson(int n, int n_omega, const double* chi0bar, double* chibar) {
+  g_last_error.clear();
+  if (n < 1 || n > 4096 || n_omega < 0) return fail(WGW_ERR_ARG, "need 1 <= n <= 4096 and n_omega >= 0");
+  if (n_omega == 0) return WGW_OK;
+  if (!chi0bar || !chibar) return fail(WGW_ERR_ARG, "null argument");
+  const size_t bytes = sizeof(double) * (size_t)n * n * n_omega;
+  cudaStream_t st = cudaStreamPerThread;
+  DevBuf a, x, m, info;
+  WGW_TRY(a.ensure(bytes));
+  WGW_TRY(x.ensure(bytes));
+  WGW_TRY(m.ensure(bytes));
+  WGW_TRY(info.ensure(sizeof(int) * n_omega));
+  WGW_CK(cudaMemcpyAsync(a.p, chi0bar, bytes, cudaMemcpyHostToDevice, st));
+  WGW_CK(launch_dyson(n, n_omega, a.as<double>(), x.as<double>(), m.as<double>(), info.as<int>(), st));
+  std::vector<int> flags(n_omega);
+  WGW_CK(cudaMemcpyAsync(chibar, x.p, bytes, cudaMemcpyDeviceToHost, st));
+  WGW_CK(cudaMemcpyAsync(flags.data(), info.p, sizeof(int) * n_omega, cudaMemcpyDeviceToHost, st));
+  WGW_CK(cudaStreamSynchronize(st));
+  for (int k = 0; k < n_omega; ++k)
+    if (flags[k]) return fail(WGW_ERR_ARG, "1 - chi0bar is singular at one of the frequencies");
+  return WGW_OK;
+}
+
 int wgw_lanczos(wgw_ctx* c, const double* phi, int n_pdep, int n_steps, const double* omega, int n_omega,
                 double* alpha, double* beta, double* chi0_pdep, wgw_stats* st) {
   g_last_error.clear();

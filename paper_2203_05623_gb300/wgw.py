@@ -102,6 +102,7 @@ def lib(path: str | None = None):
     L.wgw_submit.argtypes = [ctypes.c_void_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
     L.wgw_poll.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Result)]
     L.wgw_wait.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(Result)]
+    L.wgw_dyson.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp]
     L.wgw_destroy.argtypes = [ctypes.c_void_p]
     L.wgw_status_string.restype = ctypes.c_char_p
     L.wgw_status_string.argtypes = [ctypes.c_int]
@@ -243,6 +244,17 @@ def wgw_wait(t: Ticket):
     res = Result()
     _check(lib().wgw_wait(t.ctx.handle, t.ticket, ctypes.byref(res)), "wgw_wait")
     return t.out.transpose(2, 1, 0), res.as_dict()
+
+
+def wgw_dyson(chi0bar):
+    """(1 - A)^-1 A for each A of chi0bar (n_omega, n, n) or (n, n), float64 -> same shape."""
+    a = np.ascontiguousarray(chi0bar, np.float64)
+    single = a.ndim == 2
+    a3 = a[None] if single else a
+    out = np.zeros_like(a3)
+    n_om, n = a3.shape[0], a3.shape[-1]
+    _check(lib().wgw_dyson(n, n_om, a3.ctypes.data_as(_dp), out.ctypes.data_as(_dp)), "wgw_dyson")
+    return out[0] if single else out
 
 
 def wgw_profile_enable(ctx: Context, on: bool = True):

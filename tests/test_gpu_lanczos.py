@@ -53,3 +53,38 @@ def test_lanczos_exact_limit_equals_sum_over_states(W, tiny):
     chi, a, b, st = W.wgw_lanczos(ctx, phi, n_full, oms)
     ref = lanczos.chi0_pdep_sos(model_of(s), phi, oms).real
     assert np.max(np.abs(chi - ref)) < 1e-10 * np.max(np.abs(ref))
+
+
+def test_dyson_matches_oracle_and_closed_form(W):
+    """(1 - chibar0)^-1 chibar0 per frequency: closed form on a known spectrum, the oracle's
+    solve on non-symmetric input, n = 1 and a singular case."""
+    from oracle import dyson
+    rng = np.random.default_rng(31)
+    n, nw = 64, 32
+    A = np.zeros((nw, n, n))
+    ref = np.zeros((nw, n, n))
+    for k in range(nw):
+        Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+        lam = -rng.uniform(0.0, 8.0, n)
+        A[k] = (Q * lam) @ Q.T
+        ref[k] = (Q * (lam / (1.0 - lam))) @ Q.T
+    X = W.wgw_dyson(A)
+    assert np.max(np.abs(X - ref)) < 1e-12 * np.max(np.abs(ref))
+    B = rng.standard_normal((3, 17, 17)) * 0.2
+    assert np.max(np.abs(W.wgw_dyson(B) - dyson.chibar(B))) < 1e-12
+    assert abs(W.wgw_dyson(np.array([[-3.0]]))[0, 0] + 0.75) < 1e-15
+    with pytest.raises(W.WgwError):
+        W.wgw_dyson(np.eye(4))
+
+
+def test_dyson_on_lanczos_chi0(W, cfg24):
+    """The Dyson step on the GPU's own chi0 in a basis (Lanczos, 4 frequencies) equals the
+    oracle's solve of the same matrices."""
+    from oracle import dyson
+    s = cfg24
+    phi = synth.perturbations(s.miller_rho, s.L, 8, 23)
+    ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, W.wgw_default_options())
+    chi, _, _, _ = W.wgw_lanczos(ctx, phi, 12, [0.0, 0.3, 1.0, 4.0])
+    layout = np.ascontiguousarray(np.moveaxis(chi, 2, 0))     # (n_omega, n, n)
+    got = W.wgw_dyson(layout)
+    assert np.max(np.abs(got - dyson.chibar(layout))) < 1e-12 * max(1.0, np.max(np.abs(got)))
