@@ -99,56 +99,64 @@ WGW_HD void plane_g2r_body(int pair, int hi, const SphereTab& sp, const FftPlan&
   }
 }
 
-// Register-resident form of plane_g2r_body (compile-time N): the rows |k| <= m of plane hi are
-// transformed along l -> z one row per thread, exchanged once through shared memory, then the
-// N columns z along k -> y one column per thread, written straight to T[hi][y][z].
-// smem B: (2m+1) x (N+1) complex, row kr = k + m.
+// Register-resident form of plane_g2r_body (compile-time N) for planes hi0 .. hi0+np-1 of one
+// pair: the rows |k| <= m of each plane are transformed along l -> z one row per thread,
+// exchanged once through shared memory, then the N columns z of each plane along k -> y one
+// column per thread, written straight to T[hi][y][z].  Several planes per block keep the
+// threads busy in both phases (2m+1 rows, N columns per plane).
+// smem B: np x (2m+1) x (N+1) complex, row kr = k + m of plane p at (p (2m+1) + kr) (N+1).
 template <typename T, int N, typename C>
-WGW_HD void plane_g2r_reg_body(int pair, int hi, const SphereTab& sp, const cplx<C>* tw, const T* X, long ldx,
-                               int n_list, const int* list, cplx<C>* Tout, cplx<C>* B, Thr th) {
+WGW_HD void plane_g2r_reg_body(int pair, int hi0, int np, const SphereTab& sp, const cplx<C>* tw, const T* X,
+                               long ldx, int n_list, const int* list, cplx<C>* Tout, cplx<C>* B, Thr th) {
   const int m = sp.m, NR = 2 * m + 1, LS = N + 1;
   int s0, s1;
   pair_members(list, n_list, pair, s0, s1);
   const bool has1 = s1 >= 0;
-  for (int i = th.tid; i < NR * LS; i += th.nth) B[i] = mk<C>(C(0), C(0));
+  for (int i = th.tid; i < np * NR * LS; i += th.nth) B[i] = mk<C>(C(0), C(0));
   WGW_SYNC();
   const T* x0 = X + (size_t)s0 * ldx;
   const T* x1 = X + (size_t)(has1 ? s1 : s0) * ldx;
   const C s = C(kInvSqrt2);
-  for (int e = sp.plane_off[hi] + th.tid; e < sp.plane_off[hi + 1]; e += th.nth) {
-    const int2 en = sp.ent[e];
-    const int kk = en.x & 0xff, ll = (en.x >> 8) & 0xff, neg = (en.x >> 16) & 1;
-    const int kr = kk <= m ? kk + m : kk - N + m;
-    const int j = en.y;
-    cplx<C> z;
-    if (j == 0) {
-      z = mk<C>(C(x0[0]), has1 ? C(x1[0]) : C(0));
-    } else {
-      const C ar = C(x0[2 * j - 1]), ai = C(x0[2 * j]);
-      const C br = has1 ? C(x1[2 * j - 1]) : C(0), bi = has1 ? C(x1[2 * j]) : C(0);
-      z = neg ? mk<C>((ar + bi) * s, (br - ai) * s) : mk<C>((ar - bi) * s, (ai + br) * s);
+  for (int p = 0; p < np; ++p) {
+    cplx<C>* Bp = B + (size_t)p * NR * LS;
+    for (int e = sp.plane_off[hi0 + p] + th.tid; e < sp.plane_off[hi0 + p + 1]; e += th.nth) {
+      const int2 en = sp.ent[e];
+      const int kk = en.x & 0xff, ll = (en.x >> 8) & 0xff, neg = (en.x >> 16) & 1;
+      const int kr = kk <= m ? kk + m : kk - N + m;
+      const int j = en.y;
+      cplx<C> z;
+      if (j == 0) {
+        z = mk<C>(C(x0[0]), has1 ? C(x1[0]) : C(0));
+      } else {
+        const C ar = C(x0[2 * j - 1]), ai = C(x0[2 * j]);
+        const C br = has1 ? C(x1[2 * j - 1]) : C(0), bi = has1 ? C(x1[2 * j]) : C(0);
+        z = neg ? mk<C>((ar + bi) * s, (br - ai) * s) : mk<C>((ar - bi) * s, (ai + br) * s);
+      }
+      Bp[kr * LS + ll] = z;
     }
-    B[kr * LS + ll] = z;
   }
   WGW_SYNC();
-  for (int r = th.tid; r < NR; r += th.nth) {   // rows: l -> z
+  for (int t = th.tid; t < np * NR; t += th.nth) {   // rows: l -> z
+    cplx<C>* row = B + (size_t)t * LS;
     cplx<C> v[N];
 #pragma unroll
-    for (int x = 0; x < N; ++x) v[x] = B[r * LS + x];
+    for (int x = 0; x < N; ++x) v[x] = row[x];
     reg_dif<C, N, 0, +1>(v, tw);
 #pragma unroll
-    for (int x = 0; x < N; ++x) B[r * LS + x] = v[x];
+    for (int x = 0; x < N; ++x) row[x] = v[x];
   }
   WGW_SYNC();
-  cplx<C>* out = Tout + ((size_t)pair * NR + hi) * N * N;
-  for (int zc = th.tid; zc < N; zc += th.nth) {   // columns: k -> y
+  for (int t = th.tid; t < np * N; t += th.nth) {    // columns: k -> y
+    const int p = t / N, zc = t % N;
+    const cplx<C>* Bp = B + (size_t)p * NR * LS;
     cplx<C> v[N];
 #pragma unroll
     for (int y = 0; y < N; ++y) {
       const int kr = y <= m ? y + m : (y >= N - m ? y - N + m : -1);
-      v[y] = kr >= 0 ? B[kr * LS + zc] : mk<C>(C(0), C(0));
+      v[y] = kr >= 0 ? Bp[kr * LS + zc] : mk<C>(C(0), C(0));
     }
     reg_dif<C, N, 0, +1>(v, tw);
+    cplx<C>* out = Tout + ((size_t)pair * NR + hi0 + p) * N * N;
 #pragma unroll
     for (int y = 0; y < N; ++y) out[(size_t)y * N + zc] = v[y];
   }
@@ -400,32 +408,37 @@ WGW_HD void plane_r2g_body(int pair, int hp, const SphereTab& sp, const FftPlan&
   }
 }
 
-// Register-resident r -> G of plane hi (compile-time N): the N columns along y -> k one per
-// thread straight from T[hi][y][z] (rows |k| <= m kept), one exchange through shared memory, then
-// the rows along z -> l one per thread.  Leaves the plane in B[k + m][l] (natural l).
+// Register-resident r -> G of np planes hi[0..np) of one pair (compile-time N): the columns of
+// every plane along y -> k one per thread straight from T[hi][y][z] (rows |k| <= m kept), one
+// exchange through shared memory, then the rows along z -> l one per thread.  Leaves plane q in
+// B + q (2m+1)(N+1) as B[k + m][l] (natural l).
 template <typename C, int N>
-WGW_HD void plane_r2g_reg_load(int pair, int hi, int m, const cplx<C>* tw, const cplx<C>* Tin, cplx<C>* B, Thr th) {
+WGW_HD void plane_r2g_reg_load(int pair, const int* his, int np, int m, const cplx<C>* tw, const cplx<C>* Tin,
+                               cplx<C>* B, Thr th) {
   const int NR = 2 * m + 1, LS = N + 1;
-  const cplx<C>* in = Tin + ((size_t)pair * NR + hi) * N * N;
-  for (int zc = th.tid; zc < N; zc += th.nth) {
+  for (int t = th.tid; t < np * N; t += th.nth) {
+    const int q = t / N, zc = t % N;
+    const cplx<C>* in = Tin + ((size_t)pair * NR + his[q]) * N * N;
+    cplx<C>* Bq = B + (size_t)q * NR * LS;
     cplx<C> v[N];
 #pragma unroll
     for (int y = 0; y < N; ++y) v[y] = in[(size_t)y * N + zc];
     reg_dit<C, N, cplan(N).nst - 1, -1>(v, tw);
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-      if (k <= m) B[(k + m) * LS + zc] = v[k];
-      else if (k >= N - m) B[(k - N + m) * LS + zc] = v[k];
+      if (k <= m) Bq[(k + m) * LS + zc] = v[k];
+      else if (k >= N - m) Bq[(k - N + m) * LS + zc] = v[k];
     }
   }
   WGW_SYNC();
-  for (int r = th.tid; r < NR; r += th.nth) {
+  for (int t = th.tid; t < np * NR; t += th.nth) {
+    cplx<C>* row = B + (size_t)t * LS;
     cplx<C> v[N];
 #pragma unroll
-    for (int x = 0; x < N; ++x) v[x] = B[r * LS + x];
+    for (int x = 0; x < N; ++x) v[x] = row[x];
     reg_dit<C, N, cplan(N).nst - 1, -1>(v, tw);
 #pragma unroll
-    for (int x = 0; x < N; ++x) B[r * LS + x] = v[x];
+    for (int x = 0; x < N; ++x) row[x] = v[x];
   }
   WGW_SYNC();
 }
@@ -436,12 +449,13 @@ WGW_HD int ent_pos_rows(int2 en, int m) {
   return (kk <= m ? kk + m : kk - N + m) * (N + 1) + ((en.x >> 8) & 0xff);
 }
 
-// plane_r2g_body with the register-resident load: planes +hp and -hp of one pair, gather,
-// unpack, epilogue.  smem: (2m+1) x (N+1) complex for the plane + npt_max complex.
+// plane_r2g_body with the register-resident load: planes +hp and -hp of one pair transformed
+// together, then gathered, unpacked and passed through the epilogue.
+// smem: 2 (2m+1)(N+1) complex.
 template <typename T, int N, typename C>
 WGW_HD void plane_r2g_reg_body(int pair, int hp, const SphereTab& sp, const cplx<C>* tw, const cplx<C>* Tin,
-                               const Epi<T>& ep, cplx<C>* B, cplx<C>* Zp, Thr th) {
-  const int m = sp.m;
+                               const Epi<T>& ep, cplx<C>* B, Thr th) {
+  const int m = sp.m, plane = (2 * m + 1) * (N + 1);
   int s0, s1;
   pair_members(ep.list, ep.n_sys, pair, s0, s1);
   const bool has1 = s1 >= 0;
@@ -449,7 +463,8 @@ WGW_HD void plane_r2g_reg_body(int pair, int hp, const SphereTab& sp, const cplx
   const C scale = C(1.0 / ((double)N * N * N));
   const int off_p = sp.plane_off[m + hp];
   const int cnt = sp.plane_off[m + hp + 1] - off_p;
-  plane_r2g_reg_load<C, N>(pair, m + hp, m, tw, Tin, B, th);
+  const int his[2] = {m + hp, m - hp};
+  plane_r2g_reg_load<C, N>(pair, his, hp == 0 ? 1 : 2, m, tw, Tin, B, th);
   if (hp == 0) {
     const int K = (cnt - 1) / 2;
     for (int t = th.tid; t < K; t += th.nth) {
@@ -464,13 +479,10 @@ WGW_HD void plane_r2g_reg_body(int pair, int hp, const SphereTab& sp, const cplx
     }
     return;
   }
-  for (int t = th.tid; t < cnt; t += th.nth) Zp[t] = B[ent_pos_rows<N>(sp.ent[off_p + t], m)];
-  WGW_SYNC();
   const int off_m = sp.plane_off[m - hp];
-  plane_r2g_reg_load<C, N>(pair, m - hp, m, tw, Tin, B, th);
   for (int t = th.tid; t < cnt; t += th.nth) {
-    unpack_store(ep, sp, s0, s1, act0, act1, sp.ent[off_p + t].y, Zp[t],
-                 B[ent_pos_rows<N>(sp.ent[off_m + t], m)], scale);
+    unpack_store(ep, sp, s0, s1, act0, act1, sp.ent[off_p + t].y, B[ent_pos_rows<N>(sp.ent[off_p + t], m)],
+                 B[plane + ent_pos_rows<N>(sp.ent[off_m + t], m)], scale);
   }
 }
 

@@ -3,6 +3,7 @@
 // be checked against numpy and the oracle without a GPU.  It is built only by
 // tests/test_emu_index.py and is not part of libwgw; the library itself has no
 // host execution path.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <type_traits>
@@ -60,7 +61,13 @@ template <typename T>
 void run_g2r(int q, int hi, const Sph& sp, const FftPlan& pl, const std::vector<cplx<T>>& tw, const T* X, long ldx,
              int n_sys, cplx<T>* Tb, cplx<T>* B) {
   if (g_reg && pl.n == 24) {
-    plane_g2r_reg_body<T, 24, T>(q, hi, sp.tab(), tw.data(), X, ldx, n_sys, nullptr, Tb, B, kOne);
+    // Blocks of three planes as on the device (the block starting at a multiple of 3 handles
+    // planes hi0 .. hi0+2; called once per plane, it acts only at the block's first plane).
+    if (hi % 3 == 0) {
+      std::vector<cplx<T>> Bm((size_t)3 * (2 * sp.h.m + 1) * (pl.n + 1));
+      plane_g2r_reg_body<T, 24, T>(q, hi, std::min(3, 2 * sp.h.m + 1 - hi), sp.tab(), tw.data(), X, ldx, n_sys,
+                                   nullptr, Tb, Bm.data(), kOne);
+    }
     return;
   }
   plane_g2r_body<T>(q, hi, sp.tab(), pl, tw.data(), X, ldx, n_sys, nullptr, Tb, B, kOne);
@@ -70,7 +77,8 @@ template <typename T>
 void run_r2g(int q, int hp, const Sph& sp, const FftPlan& pl, const std::vector<cplx<T>>& tw, const cplx<T>* Tb,
              const Epi<T>& e, cplx<T>* B, cplx<T>* Zp) {
   if (g_reg && pl.n == 24) {
-    plane_r2g_reg_body<T, 24, T>(q, hp, sp.tab(), tw.data(), Tb, e, B, Zp, kOne);
+    std::vector<cplx<T>> B2((size_t)2 * (2 * sp.h.m + 1) * (pl.n + 1));
+    plane_r2g_reg_body<T, 24, T>(q, hp, sp.tab(), tw.data(), Tb, e, B2.data(), kOne);
     return;
   }
   plane_r2g_body<T>(q, hp, sp.tab(), pl, tw.data(), Tb, e, B, Zp, kOne);
@@ -124,11 +132,14 @@ void apply_h_impl(double L, double ecut, int N, const double* vloc_c, int n_sys,
   for (int s = 0; s < n_sys; ++s) sh[s] = (T)shift[s];
   const int NP = 2 * w.h.m + 1, pairs = (n_sys + 1) / 2;
   std::vector<cplx<C>> Tb((size_t)pairs * NP * N * N), B((size_t)N * (N + 1)), Zp(w.h.npt_max + 1);
+  std::vector<cplx<C>> Bm((size_t)3 * NP * (N + 1));
   for (int q = 0; q < pairs; ++q)
     for (int hi = 0; hi < NP; ++hi) {
       if constexpr (NC > 0) {
         if (reg) {
-          plane_g2r_reg_body<T, NC, C>(q, hi, w.tab(), tw.data(), X.data(), nw, n_sys, nullptr, Tb.data(), B.data(), kOne);
+          if (hi % 3 == 0)
+            plane_g2r_reg_body<T, NC, C>(q, hi, std::min(3, NP - hi), w.tab(), tw.data(), X.data(), nw, n_sys, nullptr,
+                                         Tb.data(), Bm.data(), kOne);
           continue;
         }
       }
@@ -152,7 +163,7 @@ void apply_h_impl(double L, double ecut, int N, const double* vloc_c, int n_sys,
     for (int hp = 0; hp <= w.h.m; ++hp) {
       if constexpr (NC > 0) {
         if (reg) {
-          plane_r2g_reg_body<T, NC, C>(q, hp, w.tab(), tw.data(), Tb.data(), e, B.data(), Zp.data(), kOne);
+          plane_r2g_reg_body<T, NC, C>(q, hp, w.tab(), tw.data(), Tb.data(), e, Bm.data(), kOne);
           continue;
         }
       }
