@@ -498,14 +498,15 @@ int solve_all(wgw_ctx* c, int n_sys, cudaStream_t st, wgw_stats* stats) {
       WGW_CK(cudaStreamSynchronize(st));
       for (int s = 0; s < n_sys; ++s) iters_total[s] += it_host[s];
       WGW_CK(c->prof.run(PK_CONV, 20.0 * n_sys * n, 0, st, [&] { return launch_add_to<float>(n_sys, n, c->f.X.as<float>(), ld, X, ld, act64, st); }));
-      // The FP32 correction carries an O(eps_32) component along the occupied
-      // states, which P_c (H - e_v) cannot see; the solution lies in range(P_c),
-      // so project it out in FP64.
-      WGW_TRY(run_pc<double>(c, X, na, l64, c->d.psi.as<double>(), act64, st));
-      // r = b - A x in FP64 for the systems that moved.
+      // r = b - A x in FP64 for the systems that moved.  The FP32 corrections carry an
+      // O(eps_32) component along the occupied states; P_c (H - e_v) maps it to zero (the
+      // occupied states are eigenvectors of H), so the residual does not see it and it is
+      // projected out once, after the last refinement.
       WGW_TRY(apply_A<double>(c, c->d, X, Q, na, l64, act64, st));
       WGW_CK(c->prof.run(PK_CONV, 24.0 * n_sys * n, 0, st, [&] { return launch_axpby(n_sys, n, 1.0, Bv, -1.0, Q, R, ld, act64, st); }));
     }
+    // The solution lies in range(P_c): remove the occupied component in FP64.
+    WGW_TRY(run_pc<double>(c, X, n_sys, nullptr, c->d.psi.as<double>(), nullptr, st));
   }
   if (c->opt.precision == WGW_FP64) {
     // Final FP64 residual of every system (independent check of the CG's recursive residual).
