@@ -54,6 +54,24 @@ WGW_HD double block_sum(float v, double* red, Thr th) {
 #endif
 }
 
+// A block-uniform scalar computed by thread 0 (in FP64) and handed to every thread in T, so
+// that the FP64 arithmetic runs once per block instead of once per thread (GB300's FP64 pipe
+// runs at 1/64 of the FP32 rate).  red: the shared scratch of block_sum.
+template <typename T, typename F>
+WGW_HD T block_scalar(F f, double* red, Thr th) {
+#if defined(__CUDA_ARCH__)
+  T* slot = reinterpret_cast<T*>(red + 32);
+  if (th.tid == 0) *slot = T(f());
+  __syncthreads();
+  const T v = *slot;
+  __syncthreads();
+  return v;
+#else
+  (void)red; (void)th;
+  return T(f());
+#endif
+}
+
 // Dot product of two length-n vectors: per-thread partial sums in T, then block_sum.
 // Rows start 16-byte aligned (row lengths are multiples of 32), so FP32 rows are read as float4.
 template <typename T>
@@ -207,8 +225,8 @@ WGW_HD void cg_step_a_body(int s, const SphereTab& sp, int n, T* X, T* R, T* Z, 
   const T* p = P + (size_t)s * ld;
   const T* q = Q + (size_t)s * ld;
   const double pq = block_dot(p, q, n, red, th);
-  const double alpha = pq != 0.0 ? st.rz[s] / pq : 0.0;
-  const T a = T(alpha);
+  const double rz0 = st.rz[s];
+  const T a = block_scalar<T>([&] { return pq != 0.0 ? rz0 / pq : 0.0; }, red, th);
   const double e = eps[s];
   T part = T(0);
   int i0 = 0;
@@ -262,8 +280,8 @@ WGW_HD void cg_step_b_body(int s, int n, const T* R, const T* Z, T* P, long ld, 
   const T* z = Z + (size_t)s * ld;
   T* p = P + (size_t)s * ld;
   const double rz = block_dot(r, z, n, red, th);
-  const double beta = st.rz[s] != 0.0 ? rz / st.rz[s] : 0.0;
-  const T bt = T(beta);
+  const double rz_old = st.rz[s];
+  const T bt = block_scalar<T>([&] { return rz_old != 0.0 ? rz / rz_old : 0.0; }, red, th);
   int i0 = 0;
   if constexpr (sizeof(T) == sizeof(float)) {
     const int n4 = n / 4;
