@@ -84,10 +84,11 @@ cudaError_t launch_drho_xline(int m, FftCtx<T> f, const cplx<T>* Tbuf, const T* 
 // ffc: for T = double, compute in float-float (operands rounded to float-float pairs).
 // tc_tiles: for T = float, the tensor-core kernels (tc_kernels.cu) with Psi pre-split into these
 // tiles (launch_tc_tile_psi); null selects the CUDA-core GEMMs.
+// psi_ff: with ffc, Psi as float-float pairs in 8-byte slots (no per-load conversion), or null.
 template <typename T>
 cudaError_t launch_pc(T* Y, long ldy, int n_sys, const int* list, const T* Psi, long ldp, int n, int nv,
                       const int* active, T* work, cudaStream_t st, bool ffc = false,
-                      const unsigned char* tc_tiles = nullptr);
+                      const unsigned char* tc_tiles = nullptr, const T* psi_ff = nullptr);
 // P_c on the tensor cores (3xTF32 products, FP32 accumulation in tensor memory); work holds
 // tc_pc_work_elems(n, n_sys, nv) floats; tiles from launch_tc_tile_psi.
 cudaError_t launch_pc_tc(float* Y, long ldy, int n_sys, const int* list, const unsigned char* tiles, int n, int nv,

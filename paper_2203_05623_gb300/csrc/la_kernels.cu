@@ -134,7 +134,8 @@ template <typename T> struct FfIfDouble { using type = T; };
 template <> struct FfIfDouble<double> { using type = ff; };
 template <typename T> using ff_if_double = typename FfIfDouble<T>::type;
 
-template <typename T, typename C>
+// RAW: base holds float-float pairs in its 8-byte slots (C = ff, T = double): no conversion.
+template <typename T, typename C, bool RAW = false>
 __device__ __forceinline__ void load_kchunk(C (*dst)[kGT + 4], const T* __restrict__ base, long ld,
                                             const int* __restrict__ cols, int col0, int n_cols, int k0,
                                             int k_hi) {
@@ -162,13 +163,16 @@ __device__ __forceinline__ void load_kchunk(C (*dst)[kGT + 4], const T* __restri
       for (int j = 0; j < V; ++j) vals[j] = T(0);
     }
 #pragma unroll
-    for (int j = 0; j < V; ++j) dst[kq + j][c] = C(vals[j]);
+    for (int j = 0; j < V; ++j) {
+      if constexpr (RAW) dst[kq + j][c] = *reinterpret_cast<const C*>(&vals[j]);
+      else dst[kq + j][c] = C(vals[j]);
+    }
   }
 }
 
 // C = compute type (T, or ff for T = double: operands converted once while staged in shared
 // memory, products accumulated in float-float).
-template <typename T, typename C = T>
+template <typename T, typename C = T, bool PsiRaw = false>
 __global__ void __launch_bounds__(256) k_pc_gemm1(const T* __restrict__ Psi, long ldp,
                                                   const T* __restrict__ Y, long ldy, int n, int nv,
                                                   int n_list, const int* __restrict__ list, int kblk,
@@ -184,7 +188,7 @@ __global__ void __launch_bounds__(256) k_pc_gemm1(const T* __restrict__ Psi, lon
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = C(0);
   for (int k0 = k_lo; k0 < k_hi; k0 += kGK) {
-    load_kchunk<T, C>(As, Psi, ldp, nullptr, v0, nv, k0, k_hi);
+    load_kchunk<T, C, PsiRaw>(As, Psi, ldp, nullptr, v0, nv, k0, k_hi);
     load_kchunk<T, C>(Bs, Y, ldy, list, j0, n_list, k0, k_hi);
     __syncthreads();
 #pragma unroll
@@ -404,14 +408,22 @@ __global__ void k_sum_slices(const double* __restrict__ Cpart, size_t slice, int
 template <typename T>
 __global__ void k_pc_reduce(T* __restrict__ Cpart, size_t slice, int n_kb) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < slice; e += (size_t)gridDim.x * blockDim.x) {
-    T sum = Cpart[e];
-    for (int kb = 1; kb < n_kb; ++kb) sum += Cpart[(size_t)kb * slice + e];
-    Cpart[e] = sum;
+    // Four independent partial sums keep four loads in flight; combined in a fixed order.
+    T s0 = Cpart[e], s1 = T(0), s2 = T(0), s3 = T(0);
+    int kb = 1;
+    for (; kb + 3 < n_kb; kb += 4) {
+      s1 += Cpart[(size_t)kb * slice + e];
+      s2 += Cpart[(size_t)(kb + 1) * slice + e];
+      s3 += Cpart[(size_t)(kb + 2) * slice + e];
+      s0 += Cpart[(size_t)(kb + 3) * slice + e];
+    }
+    for (; kb < n_kb; ++kb) s1 += Cpart[(size_t)kb * slice + e];
+    Cpart[e] = (s0 + s1) + (s2 + s3);
   }
 }
 
 // Y[:, s_j] = beta Y[:, s_j] + alpha sum_v Psi[:, v] C[v][j]   (C row length ldc; beta = 0 never reads Y).
-template <typename T, typename CT = T>
+template <typename T, typename CT = T, bool PsiRaw = false>
 __global__ void __launch_bounds__(256) k_pc_gemm2(const T* __restrict__ Psi, long ldp, T* __restrict__ Y,
                                                   long ldy, int n, int nv, int n_list,
                                                   const int* __restrict__ list, const T* __restrict__ C,
@@ -437,7 +449,10 @@ __global__ void __launch_bounds__(256) k_pc_gemm2(const T* __restrict__ Psi, lon
       const int c = e % kGT, vv = e / kGT, v = vc + vv, jx = j0 + c;
       Cs[vv][c] = (jx < n_list && v < nv) ? CT(C[(size_t)v * ldc + jx]) : CT(0);
       const int i = i0 + c;
-      Ps[vv][c] = (v < nv && i < n) ? CT(Psi[(size_t)v * ldp + i]) : CT(0);
+      if constexpr (PsiRaw)
+        Ps[vv][c] = (v < nv && i < n) ? reinterpret_cast<const CT*>(Psi)[(size_t)v * ldp + i] : CT(0);
+      else
+        Ps[vv][c] = (v < nv && i < n) ? CT(Psi[(size_t)v * ldp + i]) : CT(0);
     }
     __syncthreads();
     const int vmax = min(kGT, nv - vc);
@@ -584,7 +599,8 @@ inline dim3 grid_el(int n, int n_sys) {
 
 template <typename T>
 cudaError_t launch_pc(T* Y, long ldy, int n_sys, const int* list, const T* Psi, long ldp, int n, int nv,
-                      const int* active, T* work, cudaStream_t st, bool ffc, const unsigned char* tc_tiles) {
+                      const int* active, T* work, cudaStream_t st, bool ffc, const unsigned char* tc_tiles,
+                      const T* psi_ff) {
   if (n_sys == 0 || nv == 0) return cudaSuccess;
   if constexpr (sizeof(T) == sizeof(float)) {
     if (tc_tiles && tc_pc_supported(nv))
@@ -623,7 +639,9 @@ cudaError_t launch_pc(T* Y, long ldy, int n_sys, const int* list, const T* Psi, 
                                            -1.f, 1.f, active);
     return cudaGetLastError();
   }
-  if (use_ff) k_pc_gemm1<T, ff_if_double<T>><<<g1, 256, 0, st>>>(Psi, ldp, Y, ldy, n, nv, n_sys, list, kblk, work);
+  const bool raw = use_ff && psi_ff != nullptr;
+  if (raw) k_pc_gemm1<T, ff_if_double<T>, true><<<g1, 256, 0, st>>>(psi_ff, ldp, Y, ldy, n, nv, n_sys, list, kblk, work);
+  else if (use_ff) k_pc_gemm1<T, ff_if_double<T>><<<g1, 256, 0, st>>>(Psi, ldp, Y, ldy, n, nv, n_sys, list, kblk, work);
   else k_pc_gemm1<T><<<g1, 256, 0, st>>>(Psi, ldp, Y, ldy, n, nv, n_sys, list, kblk, work);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
@@ -634,7 +652,10 @@ cudaError_t launch_pc(T* Y, long ldy, int n_sys, const int* list, const T* Psi, 
     if (err != cudaSuccess) return err;
   }
   dim3 g2((n + kGT - 1) / kGT, (n_sys + kGT - 1) / kGT);
-  if (use_ff)
+  if (raw)
+    k_pc_gemm2<T, ff_if_double<T>, true><<<g2, 256, 0, st>>>(psi_ff, ldp, Y, ldy, n, nv, n_sys, list, work,
+                                                              (long)n_sys, T(-1), T(1), active);
+  else if (use_ff)
     k_pc_gemm2<T, ff_if_double<T>><<<g2, 256, 0, st>>>(Psi, ldp, Y, ldy, n, nv, n_sys, list, work, (long)n_sys,
                                                         T(-1), T(1), active);
   else
@@ -695,7 +716,7 @@ cudaError_t launch_build_list(const int* active, int n_sys, int* list, int* coun
 int pcf_kblocks(int n, int n_sys) {
   const int tiles = (n_sys + 127) / 128;
   const int nkc = std::max(1, (n + 31) / 32);
-  return std::max(1, std::min(nkc, (2 * 152 + tiles - 1) / tiles));
+  return std::max(1, std::min(std::min(nkc, 32), (2 * 152 + tiles - 1) / tiles));
 }
 
 int pc_kblocks(int n, int n_sys) {
@@ -899,7 +920,8 @@ template cudaError_t launch_kb<double>(double*, const double*, long, int, const 
 
 #define WGW_INST_LA(T)                                                                             \
   template cudaError_t launch_pc<T>(T*, long, int, const int*, const T*, long, int, int,           \
-                                    const int*, T*, cudaStream_t, bool, const unsigned char*);     \
+                                    const int*, T*, cudaStream_t, bool, const unsigned char*,      \
+                                    const T*);                                                     \
   template cudaError_t launch_cg_init_a<T>(const SphereTab&, int, int, const T*, T*, T*, T*, long, \
                                            const double*, CgState, cudaStream_t);                 \
   template cudaError_t launch_cg_init_b<T>(int, int, const T*, const T*, T*, long, CgState,       \

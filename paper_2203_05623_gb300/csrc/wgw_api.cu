@@ -110,7 +110,7 @@ struct Prec {
   DevBuf psi;       // occupied states, real basis, n_v x ld_w
   DevBuf psi_r;     // occupied states in real space, n_v x N^3
   DevBuf v_r;       // V_loc in real space
-  DevBuf psi_r_ff, v_r_ff;   // T = double: the same as float-float pairs, for the float-float passes
+  DevBuf psi_r_ff, v_r_ff, psi_ff;   // T = double: float-float copies for the float-float passes
   // work
   DevBuf X, R, Z, P, Q, Bv, Tw, shift;
   DevBuf kbB, kbD;  // KB projectors in the real basis (n_proj x ld_w) and couplings
@@ -125,7 +125,7 @@ struct Prec {
     return f;
   }
   void release() {
-    DevBuf* all[] = {&tw, &twe, &psi, &psi_r, &v_r, &psi_r_ff, &v_r_ff, &X, &R, &Z, &P, &Q, &Bv, &Tw, &shift, &kbB, &kbD};
+    DevBuf* all[] = {&tw, &twe, &psi, &psi_r, &v_r, &psi_r_ff, &v_r_ff, &psi_ff, &X, &R, &Z, &P, &Q, &Bv, &Tw, &shift, &kbB, &kbD};
     for (DevBuf* b : all) b->release();
   }
 };
@@ -300,8 +300,11 @@ int run_pc(wgw_ctx* c, T* Y, int n_list, const int* list, const T* Psi, const in
   }
   const unsigned char* tiles = tcores ? c->psi_tc.as<unsigned char>() : nullptr;
   WGW_CK(c->prof.run(PK_PC, 2.0 * n_list * n * sizeof(T) + n * nv * sizeof(T), 4.0 * n * nv * n_list, st, [&] {
-    return launch_pc<T>(Y, c->ld_w, n_list, list, Psi, c->ld_w, (int)n, c->n_v, active, work, st,
-                        sizeof(T) == 8 && c->d.use_ff, tiles); }));
+    const bool ffc = sizeof(T) == 8 && c->d.use_ff;
+    const T* psi_ff = (ffc && Psi == reinterpret_cast<const T*>(c->d.psi.p)) ? reinterpret_cast<const T*>(c->d.psi_ff.p)
+                                                                             : nullptr;
+    return launch_pc<T>(Y, c->ld_w, n_list, list, Psi, c->ld_w, (int)n, c->n_v, active, work, st, ffc, tiles,
+                        psi_ff); }));
   return WGW_OK;
 }
 
@@ -1421,6 +1424,8 @@ static int setup_impl(wgw_ctx* c, const double* vloc_G, const double* psi_v, con
   WGW_CK(launch_to_ff((size_t)n_v * c->grid3, c->d.psi_r.as<double>(), c->d.psi_r_ff.as<double>(), st));
   WGW_TRY(c->d.v_r_ff.ensure(sizeof(double) * c->grid3));
   WGW_CK(launch_to_ff((size_t)c->grid3, c->d.v_r.as<double>(), c->d.v_r_ff.as<double>(), st));
+  WGW_TRY(c->d.psi_ff.ensure(sizeof(double) * (size_t)n_v * c->ld_w));
+  WGW_CK(launch_to_ff((size_t)n_v * c->ld_w, c->d.psi.as<double>(), c->d.psi_ff.as<double>(), st));
   WGW_CK(cudaStreamSynchronize(st));
   tmp.release(); anti.release(); nrm.release(); vrb.release(); tr.release();
   return WGW_OK;
