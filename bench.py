@@ -264,6 +264,8 @@ def main():
                     help="perturbations per rank (default: the workload's); smaller values serve profiling")
     ap.add_argument("--fp64-emulation", type=int, default=1, choices=[0, 1],
                     help="1: FP64-accuracy FFT passes in float-float (default); 0: native FP64")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
+                    help="mixed (FP32 CG + FP64-accuracy refinement, default) or the all-FP64 path")
     ap.add_argument("--tensor-cores", type=int, default=None, choices=[0, 1],
                     help="P_c of the FP32 solves on the tcgen05 tensor cores (default: the library's)")
     args = ap.parse_args()
@@ -303,8 +305,11 @@ def main():
     from paper_2203_05623_gb300.shard import owned_perturbations
     phi_all = synth.perturbations(s.miller_rho, s.L, wl["n_pert"] * world, wl["pert_seed"])
     phi = phi_all[:, owned_perturbations(wl["n_pert"] * world, rank, world, wl["n_pert"])]
-    opt = W.wgw_default_options(precision=W.WGW_MIXED, cg_tol=wl["cg_tol"], max_cg_iter=200,
-                                fp64_emulation=args.fp64_emulation)
+    if args.precision == "fp64":
+        opt = W.wgw_default_options(precision=W.WGW_FP64, cg_tol=wl["cg_tol"], max_cg_iter=2000)
+    else:
+        opt = W.wgw_default_options(precision=W.WGW_MIXED, cg_tol=wl["cg_tol"], max_cg_iter=200,
+                                    fp64_emulation=args.fp64_emulation)
     if args.tensor_cores is not None:
         opt.tensor_cores = args.tensor_cores
     ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, opt)
@@ -398,9 +403,11 @@ def main():
         "metric": "Sternheimer solves/s at 1e-8 rel err vs FP64 oracle; p50/p99 request latency",
         "value": value, "unit": "Sternheimer solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64" if args.precision == "mixed" else "f64",
+        "data": "synthetic",
         "config": {"workload": args.workload, "desc": wl["desc"], "cg_tol": wl["cg_tol"],
-                   "fp64_passes": "float-float" if args.fp64_emulation else "native FP64",
+                   "precision": args.precision,
+                   "fp64_passes": ("float-float" if args.fp64_emulation else "native FP64") if args.precision == "mixed" else "n/a",
                    "pc_fp32": "tcgen05 3xTF32" if opt.tensor_cores else "CUDA-core FP32",
                    "l2": "256 MB buffer written between steps, outside the timed interval",
                    "parallelism": f"perturbation shards x{world}" if world > 1 else "1 GPU"},
