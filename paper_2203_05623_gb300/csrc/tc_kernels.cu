@@ -29,7 +29,7 @@ constexpr int kRowsA = 128;      // M of every MMA
 constexpr uint32_t kCoreBytes = 128;
 constexpr uint32_t kLbo = kCoreBytes;             // K-adjacent core matrices
 constexpr uint32_t kSbo = (kKC / 4) * kCoreBytes; // M/N-adjacent core matrices (8 rows)
-constexpr long kWaitLimit = 1L << 26;
+constexpr unsigned long long kWaitNs = 1000000000ull;   // bound of every mbarrier wait: 1 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -79,12 +79,23 @@ __device__ __forceinline__ bool mbar_test(uint32_t mbar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait for the completion of phase `parity`; false (and g_tc_error set) on timeout.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait (about one second of wall time) for the completion of phase `parity`; false,
+// with g_tc_error set, on timeout.
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (long i = 0; i < kWaitLimit; ++i)
-    if (mbar_test(mbar, parity)) return true;
-  atomicExch(&g_tc_error, 1);
-  return false;
+  if (mbar_test(mbar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_test(mbar, parity))
+    if (global_ns() - t0 > kWaitNs) {
+      atomicExch(&g_tc_error, 1);
+      return false;
+    }
+  return true;
 }
 
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -346,8 +357,16 @@ __global__ void k_tc_reduce(const float* __restrict__ Cpart, int n_list, int ldc
     float sum = 0.f;
     if (j < n_list && v < nv) {
       const size_t o = static_cast<size_t>(j) * ldc + v;
-      sum = Cpart[o];
-      for (int kb = 1; kb < n_kb; ++kb) sum += Cpart[static_cast<size_t>(kb) * slice + o];
+      float s0 = Cpart[o], s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      int kb = 1;
+      for (; kb + 3 < n_kb; kb += 4) {
+        s1 += Cpart[static_cast<size_t>(kb) * slice + o];
+        s2 += Cpart[static_cast<size_t>(kb + 1) * slice + o];
+        s3 += Cpart[static_cast<size_t>(kb + 2) * slice + o];
+        s0 += Cpart[static_cast<size_t>(kb + 3) * slice + o];
+      }
+      for (; kb < n_kb; ++kb) s1 += Cpart[static_cast<size_t>(kb) * slice + o];
+      sum = (s0 + s1) + (s2 + s3);
     }
     float hi, lo;
     split_tf32(sum, hi, lo);
@@ -359,30 +378,40 @@ __global__ void k_tc_reduce(const float* __restrict__ Cpart, int n_list, int ldc
 }
 
 // Phase 2.  Grid (ceil(n / 128), ceil(n_list / 128)).  D = rows rt x systems jt, K = states in
-// chunks of 32; A from tiles2 and B from the reduced C^T tiles, both by bulk copy, two stages.
+// chunks of 32; A from tiles2 and B from the reduced C^T tiles, both by bulk copy into one
+// 64 KB stage (several CTAs per SM), chunk after chunk.
 constexpr int kThreads2 = 256;   // phase 2: warp w reads TMEM lanes 32 (w % 4); warps 4-7 take columns 64-127
 
-__global__ void __launch_bounds__(kThreads2) k_tc_pc2(const unsigned char* __restrict__ t2,
-                                                     const unsigned char* __restrict__ ct, float* __restrict__ Y,
-                                                     long ldy, int n, int nvc, int n_list,
-                                                     const int* __restrict__ list, float alpha, float beta,
-                                                     const int* __restrict__ active) {
+__global__ void __launch_bounds__(kThreads2, 2) k_tc_pc2(const unsigned char* __restrict__ t2,
+                                                      const unsigned char* __restrict__ ct, float* __restrict__ Y,
+                                                      long ldy, int n, int nvc, int n_list,
+                                                      const int* __restrict__ list, float alpha, float beta,
+                                                      const int* __restrict__ active) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int rt = blockIdx.x, jt = blockIdx.y;
   const int r0 = rt * kRowsA, j0 = jt * kRowsA;
   constexpr uint32_t stage_bytes = 4 * kTile;   // A hi, A lo, B hi, B lo
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * stage_bytes);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 4);
-  if (active) {   // skip tiles whose systems have all finished
-    int any = 0;
-    for (int t = tid; t < kRowsA && j0 + t < n_list; t += kThreads2) any |= active[list ? list[j0 + t] : j0 + t];
-    if (!__syncthreads_or(any)) return;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + stage_bytes);   // full, mma
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
+  int* sys = reinterpret_cast<int*>(tslot + 2);                       // 128 target systems (-1: skip)
+  int any = 0;
+  for (int t = tid; t < kRowsA; t += kThreads2) {
+    const int j = j0 + t;
+    int sx = -1;
+    if (j < n_list) {
+      sx = list ? list[j] : j;
+      if (active && !active[sx]) sx = -1;
+    }
+    sys[t] = sx;
+    any |= sx >= 0;
   }
+  if (!__syncthreads_or(any)) return;   // every system of the tile has finished
   constexpr uint32_t ncols = kRowsA;
   if (warp == 0) tmem_alloc(tslot, ncols);
   if (tid == 0) {
-    for (int i = 0; i < 4; ++i) mbar_init(smem_u32(bars + i), 1);
+    mbar_init(smem_u32(bars), 1);
+    mbar_init(smem_u32(bars + 1), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   fence_before();
@@ -390,61 +419,51 @@ __global__ void __launch_bounds__(kThreads2) k_tc_pc2(const unsigned char* __res
   fence_after();
   const uint32_t tmem = *tslot;
   const uint32_t idesc = idesc_tf32(kRowsA, kRowsA);
-  auto fetch = [&](int vc, int st) {
-    const uint32_t fb = smem_u32(bars + st);
-    unsigned char* base = smem + st * stage_bytes;
-    mbar_expect_tx(fb, 4 * kTile);
-    bulk_g2s(smem_u32(base), t2 + (static_cast<size_t>(rt) * nvc + vc) * 2 * kTile, 2 * kTile, fb);
-    bulk_g2s(smem_u32(base + 2 * kTile), ct + (static_cast<size_t>(jt) * nvc + vc) * 2 * kTile, 2 * kTile, fb);
-  };
   bool ok = true;
   if (tid == 0) {
-    for (int vc = 0; vc < nvc && vc < 2; ++vc) fetch(vc, vc);
     for (int vc = 0; vc < nvc && ok; ++vc) {
-      const int st = vc & 1;
-      ok = mbar_wait(smem_u32(bars + st), (vc >> 1) & 1);
+      if (vc > 0) ok = mbar_wait(smem_u32(bars + 1), (vc - 1) & 1);   // previous MMAs read the stage
+      if (!ok) break;
+      const uint32_t fb = smem_u32(bars);
+      mbar_expect_tx(fb, 4 * kTile);
+      bulk_g2s(smem_u32(smem), t2 + (static_cast<size_t>(rt) * nvc + vc) * 2 * kTile, 2 * kTile, fb);
+      bulk_g2s(smem_u32(smem + 2 * kTile), ct + (static_cast<size_t>(jt) * nvc + vc) * 2 * kTile, 2 * kTile, fb);
+      ok = mbar_wait(fb, vc & 1);
       if (!ok) break;
       fence_after();
-      unsigned char* base = smem + st * stage_bytes;
-      issue_chunk(tmem, smem_u32(base), smem_u32(base + kTile), smem_u32(base + 2 * kTile),
-                  smem_u32(base + 3 * kTile), idesc, vc == 0);
-      mma_commit(smem_u32(bars + 2 + st));
-      if (vc + 2 < nvc) {   // refill this stage once its MMAs have read it
-        ok = mbar_wait(smem_u32(bars + 2 + st), (vc >> 1) & 1);
-        if (ok) fetch(vc + 2, st);
-      }
+      issue_chunk(tmem, smem_u32(smem), smem_u32(smem + kTile), smem_u32(smem + 2 * kTile),
+                  smem_u32(smem + 3 * kTile), idesc, vc == 0);
+      mma_commit(smem_u32(bars + 1));
     }
   }
   ok = __syncthreads_and(ok) != 0;
   if (ok && nvc > 0) {
-    const bool w = mbar_wait(smem_u32(bars + 2 + ((nvc - 1) & 1)), ((nvc - 1) >> 1) & 1);
+    const bool w = mbar_wait(smem_u32(bars + 1), (nvc - 1) & 1);
     ok = __syncthreads_and(w) != 0;
   }
   fence_after();
   const int quad = warp & 3, half = warp >> 2;
   const int k = r0 + quad * 32 + lane;   // this thread's row; columns [64 half, 64 half + 64)
+  // The TMEM loads are warp-collective: every lane executes the same sequence, and only the
+  // global accesses depend on the lane's row (rows past n take part without storing).
+  const bool row_ok = k < n;
   if (ok && nvc > 0) {
-    // All 64 old values of this thread in flight before any arithmetic or store.
-    float old[64];
 #pragma unroll
-    for (int i = 0; i < 64; ++i) {
-      const int j = j0 + half * 64 + i;
-      old[i] = 0.f;
-      if (beta != 0.f && j < n_list && k < n) {
-        const int s = list ? list[j] : j;
-        if (!active || active[s]) old[i] = Y[static_cast<size_t>(s) * ldy + k];
+    for (int c0 = 0; c0 < 64; c0 += 32) {
+      float old[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int sx = sys[half * 64 + c0 + i];
+        old[i] = (row_ok && sx >= 0 && beta != 0.f) ? Y[static_cast<size_t>(sx) * ldy + k] : 0.f;
       }
-    }
 #pragma unroll
-    for (int c0 = 0; c0 < 64; c0 += 16) {
-      float v[16];
-      tmem_ld16(tmem + (static_cast<uint32_t>(quad * 32) << 16) + half * 64 + c0, v);
+      for (int c1 = 0; c1 < 32; c1 += 16) {
+        float v[16];
+        tmem_ld16(tmem + (static_cast<uint32_t>(quad * 32) << 16) + half * 64 + c0 + c1, v);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int j = j0 + half * 64 + c0 + i;
-        if (j < n_list && k < n) {
-          const int s = list ? list[j] : j;
-          if (!active || active[s]) Y[static_cast<size_t>(s) * ldy + k] = beta * old[c0 + i] + alpha * v[i];
+        for (int i = 0; i < 16; ++i) {
+          const int sx = sys[half * 64 + c0 + c1 + i];
+          if (row_ok && sx >= 0) Y[static_cast<size_t>(sx) * ldy + k] = beta * old[c1 + i] + alpha * v[i];
         }
       }
     }
@@ -524,7 +543,7 @@ cudaError_t launch_pc_tc(float* Y, long ldy, int n_sys, const int* list, const u
       Cpart, n_sys, g.ldc, g.n_kb, nv, g.njt, g.nvc, ct);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t smem2 = 2u * 4u * tc::kTile + 64;
+  const size_t smem2 = 4u * tc::kTile + 64 + tc::kRowsA * sizeof(int);
   e = cudaFuncSetAttribute(tc::k_tc_pc2, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem2));
   if (e != cudaSuccess) return e;
   tc::k_tc_pc2<<<dim3(g.nrt, g.njt), tc::kThreads2, smem2, st>>>(t2, ct, Y, ldy, n, g.nvc, n_sys, list, -1.f, 1.f,

@@ -1310,7 +1310,7 @@ int wgw_default_options(wgw_options* opt) {
   if (!opt) return fail(WGW_ERR_ARG, "null options");
   opt->precision = WGW_FP64;
   opt->fp64_emulation = 1;
-  opt->tensor_cores = 0;
+  opt->tensor_cores = 1;
   opt->cg_tol = 1e-12;
   opt->max_cg_iter = 2000;
   opt->max_refine = 8;
