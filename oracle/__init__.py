@@ -18,6 +18,10 @@ the paper by eye:
   pdep.py     PDEP eigenpairs of chi0bar (Sec. 3) by dense diagonalisation and
               by a textbook block Davidson iteration
   lanczos.py  Lanczos chains (Eq. lanczos and the recurrence above it, Sec. 3)
+              on P_c h P_c and chi0 in the PDEP basis at imaginary frequencies
+  dyson.py    the Dyson step chibar = (1 - chi0bar)^-1 chi0bar in a basis (Sec. 2)
+  g0.py       G0 Lanczos chains of the unprojected h for the short-range
+              correlation integral (Eq. ISR, Eq. lanczos, Sec. 3)
 
 Parity status of each function is stated in its module header.
 """

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import chi0, dyson, lanczos, pdep
+from oracle import chi0, dyson, g0, lanczos, pdep
 from oracle.model import Model, sphere
 
 
@@ -329,3 +329,68 @@ def test_planted_sign_error_fails_dyson_pin():
     A = np.diag(lam)
     wrong = np.linalg.solve(np.eye(2) + A, A)
     assert np.max(np.abs(wrong - np.diag(lam / (1.0 - lam)))) > 0.1
+
+
+# ---------------------------------------------------------------- G0 Lanczos (Eq. ISR, Eq. lanczos)
+Z_G0 = np.array([-0.4 + 0.3j, 0.1 + 0.05j, 0.7 + 1.5j, 2.0 + 10.0j])
+
+
+def test_g0_lanczos_exact_limit_equals_dense_resolvent(tiny):
+    """A chain that exhausts its Krylov space gives <b_n|(h - z)^-1|b_m> exactly (h with KB)."""
+    m = model_of(tiny)
+    phi = synth.perturbations(tiny.miller_rho, tiny.L, 3, 21)
+    out = g0.g0_lanczos(m, phi, [0, 1], m.mw.shape[0], Z_G0)
+    ref = g0.g0_exact(m, phi, [0, 1], Z_G0)
+    assert rel(out["g0"], ref) < 1e-10
+    # Real h and real-in-r start vectors: real residues, and a symmetric resolvent matrix.
+    assert np.max(np.abs(out["C"].imag)) < 1e-12 * np.max(np.abs(out["C"]))
+    assert rel(ref.transpose(0, 1, 3, 2), ref) < 1e-12
+
+
+def test_g0_free_electron_resolvent_is_diagonal_sum(tiny):
+    """V = 0, no projectors: h is diagonal in plane waves, so the dense solve reduces to
+    sum_G b_n(G)^* b_m(G) / (|G|^2/2 - z), and the exhausted chain gives the same."""
+    m = Model(tiny.L, tiny.ecut, tiny.grid, np.zeros_like(tiny.vloc_G), tiny.psi_v, tiny.e_v)
+    phi = synth.perturbations(tiny.miller_rho, tiny.L, 2, 22)
+    closed = []
+    S = g0.start_vectors(m, phi, 1)
+    kin = 0.5 * m.g2w
+    for zk in Z_G0:
+        closed.append(S.conj().T @ (S / (kin - zk)[:, None]))
+    closed = np.asarray(closed)[None]
+    assert rel(g0.g0_exact(m, phi, [1], Z_G0), closed) < 1e-12
+    assert rel(g0.g0_lanczos(m, phi, [1], m.mw.shape[0], Z_G0)["g0"], closed) < 1e-10
+
+
+def test_g0_chain_moments_and_orthonormality(tiny):
+    """<q1|h^k|q1> = (T^k)_11 for k < 2 n_steps - 1, orthonormal q, unprojected h."""
+    m = model_of(tiny)
+    phi = synth.perturbations(tiny.miller_rho, tiny.L, 1, 23)
+    b = g0.start_vectors(m, phi, 0)[:, 0]
+    n = 8
+    alpha, beta, Q = g0.chain(m, b, n)
+    assert abs(beta[0] - np.linalg.norm(b)) < 1e-14 * beta[0]
+    assert np.max(np.abs(Q.conj().T @ Q - np.eye(n))) < 1e-13
+    T = np.diag(alpha) + np.diag(beta[1:], 1) + np.diag(beta[1:], -1)
+    H = m.h_dense()
+    q1 = Q[:, 0]
+    hk, Tk = q1.copy(), np.eye(n)
+    for k in range(1, 2 * n - 1):
+        hk = H @ hk
+        Tk = Tk @ T
+        assert abs(np.vdot(q1, hk) - Tk[0, 0]) < 1e-10 * abs(Tk[0, 0])
+
+
+def test_planted_transposed_tridiagonal_vectors_fail_g0_pin(tiny, monkeypatch):
+    m = model_of(tiny)
+    phi = synth.perturbations(tiny.miller_rho, tiny.L, 2, 24)
+    real = g0.scipy.linalg.eigh_tridiagonal
+
+    def transposed(a, b):
+        d, U = real(a, b)
+        return d, U.T
+
+    monkeypatch.setattr(g0.scipy.linalg, "eigh_tridiagonal", transposed)
+    out = g0.g0_lanczos(m, phi, [0], m.mw.shape[0], Z_G0)
+    monkeypatch.undo()
+    assert rel(out["g0"], g0.g0_exact(m, phi, [0], Z_G0)) > 1e-3
