@@ -39,6 +39,11 @@ WORKLOADS = {
     "dyson_P64_W32": dict(config=None, n_pert=64, pert_seed=32, cg_tol=0.0,
                           desc="Dyson step (1 - chibar0)^-1 chibar0 for 32 imaginary frequencies of a "
                                "64 x 64 PDEP-basis chibar0 (negative semidefinite, spectrum in [-8, 0])"),
+    "g0_L16_48": dict(config="pdep_L16_48", n_pert=64, pert_seed=41, cg_tol=0.0,
+                      desc="G0 Lanczos chains of H for I^SR on the 48^3 model: 64 basis vectors x the 4 "
+                           "highest occupied states = 256 chains of 32 steps (FP64, full "
+                           "reorthogonalisation), residues and resolvent matrices at 16 complex "
+                           "frequencies"),
     "chi0_L10_24": dict(config="chi0_L10_24", n_pert=8, pert_seed=2, cg_tol=1e-10,
                         desc="chi0 apply, 8 perturbations x 4 occupied states = 32 Sternheimer systems, "
                              "24^3 grid, N_pw=515, N_rho=4337, mixed FP32/FP64"),
@@ -186,6 +191,40 @@ def run_dyson(args, wl):
                                  "timed": "host call including the host <-> device copies"}}), flush=True)
 
 
+def run_g0(args, wl):
+    """G0 Lanczos chains for I^SR (wgw_g0_lanczos), host buffers, copies included."""
+    import numpy as np
+    import synth
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2203_05623_gb300 import build
+    build.build()
+    import paper_2203_05623_gb300 as W
+    s = synth.make_system(wl["config"])
+    phi = synth.perturbations(s.miller_rho, s.L, wl["n_pert"], wl["pert_seed"])
+    states = list(range(s.n_v - 4, s.n_v))
+    n_steps = 32
+    z = np.linspace(-1.0, 1.0, 4)[:, None] + 1j * np.array([0.05, 0.5, 2.0, 8.0])[None, :]
+    ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, W.wgw_default_options())
+    for _ in range(max(args.warmup, 1)):
+        W.wgw_g0_lanczos(ctx, phi, states, n_steps, z)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        W.wgw_g0_lanczos(ctx, phi, states, n_steps, z)
+        ts.append(time.perf_counter() - t0)
+    total = sum(ts)
+    units = len(states) * wl["n_pert"] * n_steps
+    print(json.dumps({"metric": "G0 Lanczos chain steps per second (one application of H per chain and step)",
+                      "value": units * args.steps / total, "unit": "chain steps/s", "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic",
+                      "config": {"workload": args.workload, "desc": wl["desc"],
+                                 "timed": "host call including the host <-> device copies"}}), flush=True)
+
+
 def run_serve(args, wl):
     """Served stream: requests submitted at Poisson arrival times through wgw_submit/wgw_wait."""
     import numpy as np
@@ -279,6 +318,8 @@ def main():
         return run_serve(args, wl)
     if args.workload.startswith("dyson"):
         return run_dyson(args, wl)
+    if args.workload.startswith("g0"):
+        return run_g0(args, wl)
 
     import numpy as np
     import torch
