@@ -196,33 +196,74 @@ def run_g0(args, wl):
     import numpy as np
     import synth
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    import torch
-    torch.cuda.set_device(local)
-    from paper_2203_05623_gb300 import build
-    build.build()
-    import paper_2203_05623_gb300 as W
     s = synth.make_system(wl["config"])
     phi = synth.perturbations(s.miller_rho, s.L, wl["n_pert"], wl["pert_seed"])
     states = list(range(s.n_v - 4, s.n_v))
     n_steps = 32
     z = np.linspace(-1.0, 1.0, 4)[:, None] + 1j * np.array([0.05, 0.5, 2.0, 8.0])[None, :]
-    ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, W.wgw_default_options())
+    cpu = None
+    if not args.no_cpu_baseline:
+        # The oracle's chains on a bounded sample (one state, 32 basis vectors, ~10 s), host cores
+        # only, before the first GPU call.
+        from oracle import g0 as g0_oracle
+        from oracle.model import Model
+        m = Model(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v)
+        t0 = time.perf_counter()
+        g0_oracle.g0_lanczos(m, phi[:, :32], states[-1:], n_steps, z)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 32 * n_steps / dt, "unit": "chain steps/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"32 chains (1 state x 32 basis vectors) of {n_steps} steps of the same workload, "
+                         f"oracle.g0.g0_lanczos, {dt:.1f} s"}
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2203_05623_gb300 import build
+    build.build()
+    import paper_2203_05623_gb300 as W
+    prec = W.WGW_MIXED if args.precision == "mixed" else W.WGW_FP64
+    ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v,
+                      W.wgw_default_options(precision=prec, fp64_emulation=args.fp64_emulation))
     for _ in range(max(args.warmup, 1)):
         W.wgw_g0_lanczos(ctx, phi, states, n_steps, z)
+    # One untimed call with every launch bracketed by CUDA events: class shares and the roofline.
+    W.wgw_profile_enable(ctx, True)
+    W.wgw_g0_lanczos(ctx, phi, states, n_steps, z)
+    prof = W.wgw_profile_read(ctx)
+    W.wgw_profile_enable(ctx, False)
     ts = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        W.wgw_g0_lanczos(ctx, phi, states, n_steps, z)
-        ts.append(time.perf_counter() - t0)
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            W.wgw_g0_lanczos(ctx, phi, states, n_steps, z)
+            ts.append(time.perf_counter() - t0)
     total = sum(ts)
     units = len(states) * wl["n_pert"] * n_steps
-    print(json.dumps({"metric": "G0 Lanczos chain steps per second (one application of H per chain and step)",
-                      "value": units * args.steps / total, "unit": "chain steps/s", "n_gpus": 1,
-                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
-                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                      "data": "synthetic",
-                      "config": {"workload": args.workload, "desc": wl["desc"],
-                                 "timed": "host call including the host <-> device copies"}}), flush=True)
+    tot_ms = max(sum(v["ms"] for v in prof.values()), 1e-9)
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    hbm, peak_kind = peaks()
+    achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9 if d["ms"] > 0 else 0.0
+    line = {"metric": "G0 Lanczos chain steps per second (one application of H per chain and step)",
+            "value": units * args.steps / total, "unit": "chain steps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"], "precision": args.precision,
+                       "fp64_passes": ("float-float" if args.fp64_emulation else "native FP64")
+                       if args.precision == "mixed" else "native FP64",
+                       "timed": "host call including the host <-> device copies (35 MB in, 4 MB out)"},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None, "peak_source": peak_kind,
+                         "launches": d["launches"],
+                         "timed_from": "CUDA events around every launch of one untimed call"},
+            "kernel_share": {k: round(v["ms"] / tot_ms, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])
+                             if v["launches"]},
+            "kernel_gbs": {k: round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1)
+                           for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"]) if v["ms"] > 0},
+            "gpu_launches": int(sum(v["launches"] for v in prof.values())) * args.steps,
+            "clocks": clk.summary()}
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
 
 
 def run_serve(args, wl):

@@ -249,6 +249,32 @@ int wgw_symm_eig_dev(int n, double* A_dev, double* w_dev, double* Z_dev, void* s
 int wgw_symm_eig_noalloc_dev(int n, double* A_dev, double* w_dev, double* Z_dev, void* stream);
 
 /*
+ * G0 Lanczos chains for the short-range correlation integral (Sec. 3, Eq. ISR, the Lanczos
+ * recurrence under it and Eq. lanczos).  For every listed occupied state i and basis vector m a
+ * chain of H itself (NOT projected) starts from b = [psi_i phi~_m] (phi~ = v^1/2 phi, the product
+ * taken on the wavefunction sphere), q^1 = b/|b|, beta_1 = |b|, with full reorthogonalisation
+ * (two classical Gram-Schmidt passes), in FP64 on the GPU.  With d, U the eigenpairs of each
+ * chain's tridiagonal matrix, the frequency-independent residues
+ *   C[i][n][l'][m] = beta_1 U_{1 l'} sum_l <psi_i phi~_n | q^l_m> U_{l l'}
+ * give the resolvent matrices at any complex frequency z = w + i w' analytically:
+ *   g0[i][k][n][m] = <psi_i phi~_n | (H - z_k)^-1 | psi_i phi~_m> = sum_l' C[i][n][l'][m] / (d_l' - z_k).
+ *   phi        host, N_rho x n_pdep complex basis (its real-in-r part is used), e.g. the PDEP basis.
+ *   states     host, n_states indices of occupied states (0..n_v-1, as given to wgw_setup).
+ *   n_steps    chain length, 1..255.
+ *   z          host, n_z complex frequencies, interleaved (re, im); may be NULL when n_z = 0.
+ *   alpha, beta, d  host outputs (or NULL), n_states x n_pdep x n_steps, l fastest; beta[..][0] = |b|;
+ *              d ascending per chain.
+ *   residues   host output (or NULL), n_states x n_pdep x n_steps x n_pdep reals, C[i][n][l'][m].
+ *   g0         host output (or NULL), n_states x n_z x n_pdep x n_pdep complex, interleaved.
+ *   st         n_systems = chains, max_iters = n_steps.
+ * A chain whose residual vanishes (Krylov space exhausted) continues with zero vectors.
+ * Returns WGW_ERR_ARG for a state index outside 0..n_v-1 or n_steps outside 1..255.
+ */
+int wgw_g0_lanczos(wgw_ctx* ctx, const double* phi, int n_pdep, const int* states, int n_states, int n_steps,
+                   const double* z, int n_z, double* alpha, double* beta, double* d, double* residues,
+                   double* g0, wgw_stats* st);
+
+/*
  * Dyson equation in a basis (Sec. 2: the screened response from the independent-particle one,
  * epsilon^-1 - 1 = (1 - chibar0)^-1 chibar0 for the symmetrised responses), for every frequency
  * of a batch, in FP64 on the GPU (Gaussian elimination with partial pivoting, one CTA per

@@ -374,6 +374,49 @@ __global__ void k_lz_assemble(int n_pdep, int n_v, int n_steps, int n_om, const 
     chi[e] = coef * acc;
   }
 }
+// G0 chains (Eq. ISR): residues C[v][n][l'][m] = beta_1 U_{0 l'} sum_l ov_v[n][l n_pdep + m] U_{l l'}
+// for chain s = m n_v + v (v indexes the list of states).
+__global__ void k_lz_residues(int n_pdep, int n_v, int n_steps, const double* __restrict__ ov,
+                              const double* __restrict__ U, const double* __restrict__ beta, double* __restrict__ C) {
+  const size_t total = (size_t)n_v * n_pdep * n_steps * n_pdep;
+  const size_t ovs = (size_t)((n_pdep + 63) / 64 * 64) * n_steps * n_pdep;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int m = (int)(e % n_pdep);
+    const int lp = (int)((e / n_pdep) % n_steps);
+    const int nn = (int)((e / ((size_t)n_pdep * n_steps)) % n_pdep);
+    const int v = (int)(e / ((size_t)n_pdep * n_steps * n_pdep));
+    const int s = m * n_v + v;
+    const double* Us = U + (size_t)s * n_steps * n_steps + (size_t)lp * n_steps;   // column l'
+    const double* o = ov + (size_t)v * ovs + (size_t)nn * n_steps * n_pdep + m;
+    double acc = 0.0;
+    for (int l = 0; l < n_steps; ++l) acc += o[(size_t)l * n_pdep] * Us[l];
+    C[e] = beta[(size_t)s * n_steps] * Us[0] * acc;
+  }
+}
+
+// g0[v][k][n][m] = sum_l' C[v][n][l'][m] / (d_s[l'] - z_k), complex (interleaved), s = m n_v + v.
+__global__ void k_lz_g0_eval(int n_pdep, int n_v, int n_steps, int n_z, const double* __restrict__ C,
+                             const double* __restrict__ d, const double* __restrict__ z, double* __restrict__ g) {
+  const size_t total = (size_t)n_v * n_z * n_pdep * n_pdep;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int m = (int)(e % n_pdep);
+    const int nn = (int)((e / n_pdep) % n_pdep);
+    const int k = (int)((e / ((size_t)n_pdep * n_pdep)) % n_z);
+    const int v = (int)(e / ((size_t)n_pdep * n_pdep * n_z));
+    const double zr = z[2 * k], zi = z[2 * k + 1];
+    const double* ds = d + (size_t)(m * n_v + v) * n_steps;
+    const double* c = C + ((size_t)v * n_pdep + nn) * n_steps * n_pdep + m;
+    double re = 0.0, im = 0.0;
+    for (int lp = 0; lp < n_steps; ++lp) {
+      // 1 / (x - i zi) = (x + i zi) / (x^2 + zi^2), x = d - zr
+      const double x = ds[lp] - zr, den = x * x + zi * zi, cv = c[(size_t)lp * n_pdep];
+      re += cv * x / den;
+      im += cv * zi / den;
+    }
+    g[2 * e] = re;
+    g[2 * e + 1] = im;
+  }
+}
 }  // namespace
 
 cudaError_t launch_syev(int n, double* A, int lda, double* w, double* Z, int ldz, double* work, int* info,
@@ -440,6 +483,19 @@ cudaError_t launch_lz_assemble(int n_pdep, int n_v, int n_steps, int n_om, const
                                double coef, double* chi, cudaStream_t st) {
   k_lz_assemble<<<WGW_G1D((size_t)n_om * n_pdep * n_pdep), 256, 0, st>>>(n_pdep, n_v, n_steps, n_om, ov, y,
                                                                           coef, chi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lz_residues(int n_pdep, int n_v, int n_steps, const double* ov, const double* U, const double* beta,
+                               double* C, cudaStream_t st) {
+  k_lz_residues<<<WGW_G1D((size_t)n_v * n_pdep * n_steps * n_pdep), 256, 0, st>>>(n_pdep, n_v, n_steps, ov, U, beta,
+                                                                                   C);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lz_g0_eval(int n_pdep, int n_v, int n_steps, int n_z, const double* C, const double* d,
+                              const double* z, double* g, cudaStream_t st) {
+  k_lz_g0_eval<<<WGW_G1D((size_t)n_v * n_z * n_pdep * n_pdep), 256, 0, st>>>(n_pdep, n_v, n_steps, n_z, C, d, z, g);
   return cudaGetLastError();
 }
 

@@ -157,6 +157,10 @@ cudaError_t launch_lz_resolvent(int n_ch, int n_steps, int n_v, int n_om, const 
                                 cudaStream_t st);
 cudaError_t launch_lz_assemble(int n_pdep, int n_v, int n_steps, int n_om, const double* ov, const double* y,
                                double coef, double* chi, cudaStream_t st);
+cudaError_t launch_lz_residues(int n_pdep, int n_v, int n_steps, const double* ov, const double* U, const double* beta,
+                               double* C, cudaStream_t st);
+cudaError_t launch_lz_g0_eval(int n_pdep, int n_v, int n_steps, int n_z, const double* C, const double* d,
+                              const double* z, double* g, cudaStream_t st);
 // Q[:, s] += B diag(D) B^T P[:, s] for the systems of a list (Kleinman-Bylander term); B is n x n_proj.
 // work: pc_work_elems(n, n_sys, n_proj) elements of T.
 template <typename T>

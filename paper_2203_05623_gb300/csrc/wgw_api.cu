@@ -1170,11 +1170,30 @@ int davidson_impl(wgw_ctx* c, int npd, const double* x0, double* eig, double* ba
 // ---------------------------------------------------------------- Lanczos chains (Sec. 3)
 // Chains on P_c H P_c for every (state v, basis vector m), started from P_c [phi~_m psi_v]
 // (phi~ = v^1/2 phi), FP64 throughout; chi0_nm(i w) from the chains' tridiagonal spectra.
+// G0 mode of the Lanczos chains (Eq. ISR): chains of h itself from [phi~_m psi_i], i over a list
+// of occupied states, with the frequency-independent residues and the resolvent matrices at
+// complex frequencies as outputs.
+struct LzG0 {
+  const int* states;
+  int n_states;
+  const double* z;   // n_z complex, interleaved
+  int n_z;
+  double* d;         // host outputs, or null
+  double* C;
+  double* g0;
+};
+
+// Lanczos chains of every (state, basis vector) pair.  Without g0: chains of P_c H P_c from
+// P_c [phi~_m psi_v], every occupied v, and chi0 in the basis.  With g0: chains of H.
 int lanczos_impl(wgw_ctx* c, const double* phi, int npd, int n_steps, const double* omega, int n_om,
-                 double* alpha_out, double* beta_out, double* chi_out, wgw_stats* st_out) {
+                 double* alpha_out, double* beta_out, double* chi_out, wgw_stats* st_out,
+                 const LzG0* g0 = nullptr) {
   cudaStream_t st = c->stream;
-  c->d.use_ff = false;   // the chains run in native FP64
-  const int N = c->N, n_v = c->n_v, n = c->wfc.nrb(), nr = c->rho.nrb();
+  // FP64-accurate chains: float-float FFT passes on the mixed path (compiled grids), native FP64
+  // otherwise.
+  c->d.use_ff = c->opt.precision == WGW_MIXED && c->opt.fp64_emulation != 0 && ff_grid_supported(c->N);
+  const bool proj = g0 == nullptr;
+  const int N = c->N, n_v = proj ? c->n_v : g0->n_states, n = c->wfc.nrb(), nr = c->rho.nrb();
   const long ldw = c->ld_w, ldr = c->ld_r;
   const int n_ch = npd * n_v;
   // Perturbations phi~_m = v^1/2 phi_m (real-in-r part), to real space.
@@ -1191,10 +1210,10 @@ int lanczos_impl(wgw_ctx* c, const double* phi, int npd, int n_steps, const doub
   WGW_TRY(ensure_work(c, n_ch, npd));
   std::vector<int> ai(n_ch), bi(n_ch);
   for (int m = 0; m < npd; ++m)
-    for (int v = 0; v < n_v; ++v) { ai[m * n_v + v] = v; bi[m * n_v + v] = m; }
+    for (int v = 0; v < n_v; ++v) { ai[m * n_v + v] = proj ? v : g0->states[v]; bi[m * n_v + v] = m; }
   WGW_CK(cudaMemcpyAsync(c->a_idx.p, ai.data(), sizeof(int) * n_ch, cudaMemcpyHostToDevice, st));
   WGW_CK(cudaMemcpyAsync(c->b_idx.p, bi.data(), sizeof(int) * n_ch, cudaMemcpyHostToDevice, st));
-  WGW_CK(cudaMemsetAsync(c->d.shift.p, 0, sizeof(double) * n_ch, st));   // A = P_c H P_c
+  WGW_CK(cudaMemsetAsync(c->d.shift.p, 0, sizeof(double) * n_ch, st));   // A = (P_c) H (P_c)
   double* dvr = c->dv_r.as<double>();
   WGW_TRY(to_real<double>(c, c->d, c->rho, c->dv_rb.as<double>(), ldr, npd, dvr, c->Trho, st));
   FftCtx<double> f = c->d.fft(c->plan);
@@ -1209,7 +1228,7 @@ int lanczos_impl(wgw_ctx* c, const double* phi, int npd, int n_steps, const doub
     Epi<double> e{};
     e.out = S; e.ldo = ldw; e.vcoef = 1.0; e.n_sys = n_ch;
     WGW_CK(launch_plane_r2g<double>(c->wfc.tab(), c->wfc.npt_max, f, c->d.Tw.as<cplx<double>>(), e, st));
-    WGW_TRY(run_pc<double>(c, S, n_ch, nullptr, c->d.psi.as<double>(), nullptr, st));
+    if (proj) WGW_TRY(run_pc<double>(c, S, n_ch, nullptr, c->d.psi.as<double>(), nullptr, st));
   }
   DevBuf Qb, al, be, T, dd, U, wk, inf, ov, y, om, lists;
   WGW_TRY(Qb.ensure(sizeof(double) * (size_t)(n_steps + 1) * n_ch * ldw));
@@ -1220,19 +1239,26 @@ int lanczos_impl(wgw_ctx* c, const double* phi, int npd, int n_steps, const doub
   double* Q = Qb.as<double>();
   double* HQ = c->d.Q.as<double>();
   double* R = c->d.R.as<double>();
+  // The recurrence kernels are timed as other_f64; algorithmic bytes are the vectors each
+  // reads and writes once (the Gram-Schmidt pass: q^0..q^l and r in, r out).
+  ProfPrec pp(c->prof, true);
+  const double vb = (double)n_ch * n * sizeof(double);
   WGW_CK(launch_lz_start(n, n_ch, S, Q, ldw, be.as<double>(), n_steps, st));
   for (int l = 0; l < n_steps; ++l) {
     double* ql = Q + (size_t)l * n_ch * ldw;
-    WGW_TRY(apply_A<double>(c, c->d, ql, HQ, n_ch, nullptr, nullptr, st));
-    WGW_CK(launch_lz_three_term(n, l, n_ch, Q, HQ, R, ldw, al.as<double>(), be.as<double>(), n_steps, st));
+    WGW_TRY(apply_A<double>(c, c->d, ql, HQ, n_ch, nullptr, nullptr, st, proj));
+    WGW_CK(c->prof.run(PK_OTHER, (l > 0 ? 4 : 3) * vb, 0, st, [&] {
+      return launch_lz_three_term(n, l, n_ch, Q, HQ, R, ldw, al.as<double>(), be.as<double>(), n_steps, st); }));
     if (l + 1 == n_steps) break;
     for (int pass = 0; pass < 2; ++pass) {
-      WGW_CK(launch_lz_reorth(n, l, n_ch, Q, R, ldw, st));
-      WGW_TRY(run_pc<double>(c, R, n_ch, nullptr, c->d.psi.as<double>(), nullptr, st));
+      WGW_CK(c->prof.run(PK_OTHER, (l + 3) * vb, 4.0 * (l + 1) * n * n_ch, st, [&] {
+        return launch_lz_reorth(n, l, n_ch, Q, R, ldw, st); }));
+      if (proj) WGW_TRY(run_pc<double>(c, R, n_ch, nullptr, c->d.psi.as<double>(), nullptr, st));
     }
-    WGW_CK(launch_lz_normalise(n, l, n_ch, R, Q, ldw, be.as<double>(), n_steps, st));
+    WGW_CK(c->prof.run(PK_OTHER, 2 * vb, 0, st, [&] {
+      return launch_lz_normalise(n, l, n_ch, R, Q, ldw, be.as<double>(), n_steps, st); }));
   }
-  // Overlaps <P_c phi~_n psi_v | q^l_(m,v)>, one product per state v.
+  // Overlaps <(P_c) phi~_n psi_v | q^l_(m,v)>, one product per state v.
   const int mp = (npd + 63) / 64 * 64;
   const size_t ovs = (size_t)mp * n_steps * npd;
   WGW_TRY(ov.ensure(sizeof(double) * ovs * n_v));
@@ -1262,7 +1288,36 @@ int lanczos_impl(wgw_ctx* c, const double* phi, int npd, int n_steps, const doub
   WGW_CK(cudaStreamSynchronize(st));
   for (int q = 0; q < n_ch; ++q)
     if (infh[q] != 0) return fail(WGW_ERR_NOCONV, "tridiagonal eigensolver did not converge");
-  if (chi_out && n_om > 0) {
+  if (!proj) {
+    // Residues C[i][n][l'][m] = beta_1 U_{1 l'} sum_l <b_n|q^l_m> U_{l l'}, then the resolvent
+    // matrices g0[i][k][n][m] = sum_l' C[i][n][l'][m] / (d_l' - z_k).
+    DevBuf Cd, zd, gd;
+    const size_t nC = (size_t)n_v * npd * n_steps * npd;
+    WGW_TRY(Cd.ensure(sizeof(double) * nC));
+    WGW_CK(launch_lz_residues(npd, n_v, n_steps, ov.as<double>(), U.as<double>(), be.as<double>(), Cd.as<double>(),
+                              st));
+    if (g0->C) WGW_CK(cudaMemcpyAsync(g0->C, Cd.p, sizeof(double) * nC, cudaMemcpyDeviceToHost, st));
+    if (g0->g0 && g0->n_z > 0) {
+      const size_t ng = (size_t)n_v * g0->n_z * npd * npd;
+      WGW_TRY(zd.ensure(sizeof(double) * 2 * g0->n_z));
+      WGW_TRY(gd.ensure(sizeof(double) * 2 * ng));
+      WGW_CK(cudaMemcpyAsync(zd.p, g0->z, sizeof(double) * 2 * g0->n_z, cudaMemcpyHostToDevice, st));
+      WGW_CK(launch_lz_g0_eval(npd, n_v, n_steps, g0->n_z, Cd.as<double>(), dd.as<double>(), zd.as<double>(),
+                               gd.as<double>(), st));
+      WGW_CK(cudaMemcpyAsync(g0->g0, gd.p, sizeof(double) * 2 * ng, cudaMemcpyDeviceToHost, st));
+    }
+    if (g0->d) {
+      std::vector<double> dh((size_t)n_ch * n_steps);
+      WGW_CK(cudaMemcpyAsync(dh.data(), dd.p, sizeof(double) * dh.size(), cudaMemcpyDeviceToHost, st));
+      WGW_CK(cudaStreamSynchronize(st));
+      for (int v = 0; v < n_v; ++v)
+        for (int m = 0; m < npd; ++m)
+          for (int l = 0; l < n_steps; ++l)
+            g0->d[((size_t)v * npd + m) * n_steps + l] = dh[((size_t)m * n_v + v) * n_steps + l];
+    }
+    WGW_CK(cudaStreamSynchronize(st));
+  }
+  if (proj && chi_out && n_om > 0) {
     WGW_TRY(om.ensure(sizeof(double) * n_om));
     WGW_CK(cudaMemcpyAsync(om.p, omega, sizeof(double) * n_om, cudaMemcpyHostToDevice, st));
     WGW_TRY(y.ensure(sizeof(double) * (size_t)n_om * n_ch * n_steps));
@@ -1623,6 +1678,20 @@ int wgw_lanczos(wgw_ctx* c, const double* phi, int n_pdep, int n_steps, const do
     if (!(omega[k] >= 0.0)) return fail(WGW_ERR_ARG, "imaginary frequencies must be >= 0");
   std::lock_guard<std::recursive_mutex> lk(c->mu);
   return lanczos_impl(c, phi, n_pdep, n_steps, omega, n_omega, alpha, beta, chi0_pdep, st);
+}
+
+int wgw_g0_lanczos(wgw_ctx* c, const double* phi, int n_pdep, const int* states, int n_states, int n_steps,
+                   const double* z, int n_z, double* alpha, double* beta, double* d, double* residues,
+                   double* g0, wgw_stats* st) {
+  g_last_error.clear();
+  if (!c || !phi || n_pdep < 1 || !states || n_states < 1 || n_steps < 1 || n_steps > 255 || n_z < 0 ||
+      (n_z > 0 && !z))
+    return fail(WGW_ERR_ARG, "need a context, phi, n_pdep >= 1, states, n_states >= 1, 1 <= n_steps <= 255, n_z >= 0");
+  for (int i = 0; i < n_states; ++i)
+    if (states[i] < 0 || states[i] >= c->n_v) return fail(WGW_ERR_ARG, "state index outside 0..n_v-1");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  const LzG0 g{states, n_states, z, n_z, d, residues, g0};
+  return lanczos_impl(c, phi, n_pdep, n_steps, nullptr, 0, alpha, beta, nullptr, st, &g);
 }
 
 int wgw_symm_eig_dev(int n, double* A_dev, double* w_dev, double* Z_dev, void* stream) {

@@ -103,6 +103,8 @@ def lib(path: str | None = None):
     L.wgw_poll.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Result)]
     L.wgw_wait.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(Result)]
     L.wgw_dyson.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp]
+    L.wgw_g0_lanczos.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                 ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, ctypes.POINTER(Stats)]
     L.wgw_destroy.argtypes = [ctypes.c_void_p]
     L.wgw_status_string.restype = ctypes.c_char_p
     L.wgw_status_string.argtypes = [ctypes.c_int]
@@ -313,6 +315,36 @@ def wgw_lanczos(ctx: Context, phi, n_steps: int, omega=()):
                              b.ctypes.data_as(_dp), chi.ctypes.data_as(_dp) if len(om) else None,
                              ctypes.byref(st)), "wgw_lanczos")
     return chi[: len(om)].transpose(2, 1, 0), a, b, st.as_dict()
+
+
+def wgw_g0_lanczos(ctx: Context, phi, states, n_steps: int, z=()):
+    """G0 Lanczos chains of H from [psi_i phi~_m] for the listed occupied states i.
+
+    Returns a dict: alpha, beta, d (n_states, n_pdep, n_steps); residues C (n_states, n_pdep,
+    n_steps, n_pdep) as [i, n, l', m]; g0 (n_states, n_z, n_pdep, n_pdep) complex as [i, k, n, m]
+    = <psi_i phi~_n|(H - z_k)^-1|psi_i phi~_m>; stats.
+    """
+    phi = np.asarray(phi, np.complex128)
+    npd = phi.shape[1]
+    sts = np.ascontiguousarray(states, np.int32)
+    ns = sts.size
+    zz = np.ascontiguousarray(np.asarray(z, np.complex128).ravel())
+    nz = zz.size
+    a = np.zeros((ns, npd, n_steps))
+    b = np.zeros((ns, npd, n_steps))
+    d = np.zeros((ns, npd, n_steps))
+    C = np.zeros((ns, npd, n_steps, npd))
+    g = np.zeros((ns, nz, npd, npd), np.complex128)
+    st = Stats()
+    pb = _interleave(phi)
+    zb = zz.view(np.float64)
+    _check(lib().wgw_g0_lanczos(ctx.handle, pb.ctypes.data_as(_dp), npd,
+                                sts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ns, n_steps,
+                                zb.ctypes.data_as(_dp) if nz else None, nz, a.ctypes.data_as(_dp),
+                                b.ctypes.data_as(_dp), d.ctypes.data_as(_dp), C.ctypes.data_as(_dp),
+                                g.view(np.float64).ctypes.data_as(_dp) if nz else None,
+                                ctypes.byref(st)), "wgw_g0_lanczos")
+    return dict(alpha=a, beta=b, d=d, C=C, g0=g, stats=st.as_dict())
 
 
 def wgw_symm_eig_dev(A_dev, stream=None, w=None, Z=None, noalloc=False):
