@@ -238,67 +238,183 @@ __global__ void k_select_scale(int k, const double* __restrict__ Zc, int ldz, co
   }
 }
 
-
 // ---------------------------------------------------------------- Lanczos chains (Sec. 3, Eq. lanczos)
-// Chain s holds q^l at Q + (l * n_ch + s) * ld.  One block per chain.
+// Chain s holds q^l at Q + (l * n_ch + s) * ld.
 
-// alpha_l = q^l . Hq^l, r = Hq^l - alpha_l q^l - beta_l q^{l-1} (into R).
-__global__ void k_lz_three_term(int n, int l, int n_ch, const double* __restrict__ Q, const double* __restrict__ HQ,
-                                double* __restrict__ R, long ld, double* __restrict__ alpha,
-                                const double* __restrict__ beta, int n_steps) {
-  __shared__ double red[33];
-  const int s = blockIdx.x;
-  Thr th{(int)threadIdx.x, (int)blockDim.x};
-  const double* q = Q + ((size_t)l * n_ch + s) * ld;
-  const double* hq = HQ + (size_t)s * ld;
-  double part = 0.0;
-  for (int i = th.tid; i < n; i += th.nth) part += q[i] * hq[i];
-  const double a = block_sum(part, red, th);
-  const double b = l > 0 ? beta[(size_t)s * n_steps + l] : 0.0;
-  const double* qp = l > 0 ? Q + ((size_t)(l - 1) * n_ch + s) * ld : nullptr;
-  double* r = R + (size_t)s * ld;
-  for (int i = th.tid; i < n; i += th.nth) r[i] = hq[i] - a * q[i] - (qp ? b * qp[i] : 0.0);
-  if (th.tid == 0) alpha[(size_t)s * n_steps + l] = a;
+// Split Gram-Schmidt: chain s = blockIdx.x, chunk blockIdx.y of the n reals (gridDim.y chunks),
+// so that a few hundred chains still fill the GPU.  Partial sums go to part[(s nb + b)(l+1) + j]
+// and are summed in chunk order by the consumer (deterministic).  The arithmetic type C is
+// double (native FP64) or ff (float-float on the FP32 units, for GPUs whose FP64 rate is a small
+// fraction of FP32): with C = ff the previous Lanczos vectors are read from a float-float copy
+// (8 bytes per real, like a double) and the vectors in and out stay double.
+__device__ __forceinline__ void lz_chunk(int n, int& i0, int& i1) {
+  const int per = (n + (int)gridDim.y - 1) / (int)gridDim.y;
+  i0 = (int)blockIdx.y * per;
+  i1 = min(n, i0 + per);
 }
 
-// One classical Gram-Schmidt pass of r against q^0 .. q^l of its chain.
-__global__ void k_lz_reorth(int n, int l, int n_ch, const double* __restrict__ Q, double* __restrict__ R, long ld) {
+template <typename C> __device__ __forceinline__ C lz_c(double v);
+template <> __device__ __forceinline__ double lz_c<double>(double v) { return v; }
+template <> __device__ __forceinline__ ff lz_c<ff>(double v) { return ff(v); }
+__device__ __forceinline__ double lz_d(double v) { return v; }
+__device__ __forceinline__ double lz_d(ff v) { return double(v); }
+__device__ __forceinline__ void lz_warp_sum(double& a) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+}
+__device__ __forceinline__ void lz_warp_sum(ff& a) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+    a = a + ff(__shfl_xor_sync(0xffffffffu, a.hi, off), __shfl_xor_sync(0xffffffffu, a.lo, off));
+}
+
+constexpr int kLzJ = 8;   // dot products accumulated per sweep over the chunk
+constexpr int kLzE = 4;   // elements per thread per sweep (256-thread blocks)
+
+// part[(s nb + b)(l+1) + j] = sum over chunk b of q^j[i] x[i], j = 0..l.  256 threads; each thread
+// holds kLzE elements of x so that kLzJ x kLzE independent loads are in flight per sweep.
+template <typename C>
+__global__ void __launch_bounds__(256) k_lz_gs_dots(int n, int l, int n_ch, const C* __restrict__ Qg, long ld,
+                                                    const double* X, double* __restrict__ part) {
+  __shared__ double red[8][kLzJ];
+  const int s = blockIdx.x, nb = gridDim.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int i0, i1;
+  lz_chunk(n, i0, i1);
+  const double* x = X + (size_t)s * ld;
+  for (int j0 = 0; j0 <= l; j0 += kLzJ) {
+    const int nj = min(kLzJ, l + 1 - j0);
+    C acc[kLzJ];
+#pragma unroll
+    for (int jj = 0; jj < kLzJ; ++jj) acc[jj] = lz_c<C>(0.0);
+    for (int base = i0 + (int)threadIdx.x; base < i1; base += kLzE * 256) {
+      C xv[kLzE];
+#pragma unroll
+      for (int e = 0; e < kLzE; ++e) {
+        const int i = base + e * 256;
+        xv[e] = lz_c<C>(i < i1 ? x[i] : 0.0);
+      }
+#pragma unroll
+      for (int jj = 0; jj < kLzJ; ++jj) {
+        if (jj < nj) {
+          const C* q = Qg + ((size_t)(j0 + jj) * n_ch + s) * ld;
+#pragma unroll
+          for (int e = 0; e < kLzE; ++e) {
+            const int i = base + e * 256;
+            if (i < i1) mac(acc[jj], q[i], xv[e]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int jj = 0; jj < kLzJ; ++jj) lz_warp_sum(acc[jj]);
+    if (lane == 0) {
+#pragma unroll
+      for (int jj = 0; jj < kLzJ; ++jj) red[warp][jj] = lz_d(acc[jj]);
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nj) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][threadIdx.x];
+      part[((size_t)s * nb + blockIdx.y) * (l + 1) + j0 + threadIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// r = x - sum_j c_j q^j on chunk b, c_j = sum over chunks of part (x may alias r).  With alpha,
+// block (s, 0) stores alpha_l = c_l (the first pass, over x = H q^l, is the three-term step and
+// the first Gram-Schmidt pass at once); alpha_only stops there.  With npart, the chunk's
+// partial |r|^2 goes to npart[s nb + b].  256 threads.
+template <typename C>
+__global__ void __launch_bounds__(256) k_lz_gs_update(int n, int l, int n_ch, const C* __restrict__ Qg, long ld,
+                                                      const double* X, double* R, const double* __restrict__ part,
+                                                      double* __restrict__ alpha, int n_steps, int alpha_only,
+                                                      double* __restrict__ npart) {
+  __shared__ C ncoef[256];
   __shared__ double red[33];
-  __shared__ double coef[256];
-  const int s = blockIdx.x;
-  Thr th{(int)threadIdx.x, (int)blockDim.x};
-  double* r = R + (size_t)s * ld;
-  for (int j = 0; j <= l; ++j) {
-    const double* q = Q + ((size_t)j * n_ch + s) * ld;
-    double part = 0.0;
-    for (int i = th.tid; i < n; i += th.nth) part += q[i] * r[i];
-    const double cj = block_sum(part, red, th);
-    if (th.tid == 0) coef[j] = cj;
+  const int s = blockIdx.x, nb = gridDim.y;
+  for (int j = threadIdx.x; j <= l; j += blockDim.x) {
+    double t = 0.0;
+    for (int b = 0; b < nb; ++b) t += part[((size_t)s * nb + b) * (l + 1) + j];
+    ncoef[j] = lz_c<C>(-t);
+    if (j == l && alpha && blockIdx.y == 0) alpha[(size_t)s * n_steps + l] = t;
   }
   __syncthreads();
-  for (int i = th.tid; i < n; i += th.nth) {
-    double acc = r[i];
-    for (int j = 0; j <= l; ++j) acc -= coef[j] * Q[((size_t)j * n_ch + s) * ld + i];
-    r[i] = acc;
+  if (alpha_only) return;
+  int i0, i1;
+  lz_chunk(n, i0, i1);
+  const double* x = X + (size_t)s * ld;
+  double* r = R + (size_t)s * ld;
+  double nn = 0.0;
+  // kLzE elements per thread, j outermost: kLzE independent loads per j, four j unrolled.
+  for (int base = i0 + (int)threadIdx.x; base < i1; base += kLzE * 256) {
+    C acc[kLzE];
+#pragma unroll
+    for (int e = 0; e < kLzE; ++e) {
+      const int i = base + e * 256;
+      acc[e] = lz_c<C>(i < i1 ? x[i] : 0.0);
+    }
+#pragma unroll 4
+    for (int j = 0; j <= l; ++j) {
+      const C cj = ncoef[j];
+      const C* q = Qg + ((size_t)j * n_ch + s) * ld;
+#pragma unroll
+      for (int e = 0; e < kLzE; ++e) {
+        const int i = base + e * 256;
+        if (i < i1) mac(acc[e], cj, q[i]);
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < kLzE; ++e) {
+      const int i = base + e * 256;
+      if (i < i1) {
+        const double rd = lz_d(acc[e]);
+        r[i] = rd;
+        nn = fma(rd, rd, nn);
+      }
+    }
+  }
+  if (npart) {
+    Thr th{(int)threadIdx.x, (int)blockDim.x};
+    const double t = block_sum(nn, red, th);
+    if (threadIdx.x == 0) npart[(size_t)s * nb + blockIdx.y] = t;
   }
 }
 
-// beta_{l+1} = |r|, q^{l+1} = r / beta_{l+1} (a chain whose |r| vanished relative to beta_0 stops:
-// q^{l+1} = 0).
-__global__ void k_lz_normalise(int n, int l, int n_ch, const double* __restrict__ R, double* __restrict__ Q, long ld,
-                               double* __restrict__ beta, int n_steps) {
+// beta_{l+1} = |r|, q^{l+1} = r / beta_{l+1} on chunk b; a chain whose |r| fell to 1e-14 beta_0
+// or below stops (q^{l+1} = 0, beta_{l+1} = 0).  |r|^2 comes from the partial norms npart, or,
+// with npart null and a single chunk, from the block itself.  With C = ff the float-float copy
+// Qf of q^{l+1} is written too.
+template <typename C>
+__global__ void __launch_bounds__(256) k_lz_normalise_split(int n, int l, int n_ch, const double* __restrict__ R,
+                                                            double* __restrict__ Q, C* __restrict__ Qf, long ld,
+                                                            double* __restrict__ beta, int n_steps,
+                                                            const double* __restrict__ npart) {
   __shared__ double red[33];
-  const int s = blockIdx.x;
-  Thr th{(int)threadIdx.x, (int)blockDim.x};
+  const int s = blockIdx.x, nb = gridDim.y;
   const double* r = R + (size_t)s * ld;
-  double part = 0.0;
-  for (int i = th.tid; i < n; i += th.nth) part += r[i] * r[i];
-  const double nb = sqrt(block_sum(part, red, th));
+  int i0, i1;
+  lz_chunk(n, i0, i1);
+  double t = 0.0;
+  if (npart) {
+    for (int b = 0; b < nb; ++b) t += npart[(size_t)s * nb + b];
+  } else {
+    double part = 0.0;
+    for (int i = i0 + (int)threadIdx.x; i < i1; i += blockDim.x) part = fma(r[i], r[i], part);
+    Thr th{(int)threadIdx.x, (int)blockDim.x};
+    t = block_sum(part, red, th);
+  }
+  const double nrm = sqrt(t);
   const double b0 = beta[(size_t)s * n_steps];
-  const bool stop = !(nb > 1e-14 * b0);
-  double* q = Q + ((size_t)(l + 1) * n_ch + s) * ld;
-  for (int i = th.tid; i < n; i += th.nth) q[i] = stop ? 0.0 : r[i] / nb;
-  if (th.tid == 0) beta[(size_t)s * n_steps + l + 1] = stop ? 0.0 : nb;
+  const bool stop = !(nrm > 1e-14 * b0);
+  const double inv = stop ? 0.0 : 1.0 / nrm;
+  const size_t off = ((size_t)(l + 1) * n_ch + s) * ld;
+  for (int i = i0 + (int)threadIdx.x; i < i1; i += blockDim.x) {
+    const double qv = r[i] * inv;
+    Q[off + i] = qv;
+    if (Qf) Qf[off + i] = lz_c<C>(qv);
+  }
+  if (blockIdx.y == 0 && threadIdx.x == 0) beta[(size_t)s * n_steps + l + 1] = stop ? 0.0 : nrm;
 }
 
 // beta_0 = |b|, q^0 = b / beta_0.
@@ -452,21 +568,7 @@ cudaError_t launch_lz_start(int n, int n_ch, const double* B, double* Q, long ld
   k_lz_start<<<n_ch, 256, 0, st>>>(n, B, Q, ld, beta, n_steps);
   return cudaGetLastError();
 }
-cudaError_t launch_lz_three_term(int n, int l, int n_ch, const double* Q, const double* HQ, double* R, long ld,
-                                 double* alpha, const double* beta, int n_steps, cudaStream_t st) {
-  k_lz_three_term<<<n_ch, 256, 0, st>>>(n, l, n_ch, Q, HQ, R, ld, alpha, beta, n_steps);
-  return cudaGetLastError();
-}
-cudaError_t launch_lz_reorth(int n, int l, int n_ch, const double* Q, double* R, long ld, cudaStream_t st) {
-  if (l >= 256) return cudaErrorInvalidValue;
-  k_lz_reorth<<<n_ch, 256, 0, st>>>(n, l, n_ch, Q, R, ld);
-  return cudaGetLastError();
-}
-cudaError_t launch_lz_normalise(int n, int l, int n_ch, const double* R, double* Q, long ld, double* beta,
-                                int n_steps, cudaStream_t st) {
-  k_lz_normalise<<<n_ch, 256, 0, st>>>(n, l, n_ch, R, Q, ld, beta, n_steps);
-  return cudaGetLastError();
-}
+
 cudaError_t launch_lz_tridiag(int n_ch, int n_steps, const double* alpha, const double* beta, double* T,
                               cudaStream_t st) {
   k_lz_tridiag<<<WGW_G1D((size_t)n_ch * n_steps * n_steps), 256, 0, st>>>(n_ch, n_steps, alpha, beta, T);
@@ -483,6 +585,46 @@ cudaError_t launch_lz_assemble(int n_pdep, int n_v, int n_steps, int n_om, const
                                double coef, double* chi, cudaStream_t st) {
   k_lz_assemble<<<WGW_G1D((size_t)n_om * n_pdep * n_pdep), 256, 0, st>>>(n_pdep, n_v, n_steps, n_om, ov, y,
                                                                           coef, chi);
+  return cudaGetLastError();
+}
+
+int lz_split(int n, int n_ch) {
+  const int want = (4 * 304 + n_ch - 1) / n_ch;      // about eight 256-thread blocks per SM
+  return std::max(1, std::min(want, (n + 511) / 512));
+}
+
+cudaError_t launch_lz_gs_dots(int n, int l, int n_ch, const double* Q, const double* Qf, long ld, const double* X,
+                              double* part, int nb, cudaStream_t st) {
+  if (l > 255) return cudaErrorInvalidValue;
+  if (Qf)
+    k_lz_gs_dots<ff><<<dim3(n_ch, nb), 256, 0, st>>>(n, l, n_ch, reinterpret_cast<const ff*>(Qf), ld, X, part);
+  else
+    k_lz_gs_dots<double><<<dim3(n_ch, nb), 256, 0, st>>>(n, l, n_ch, Q, ld, X, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lz_gs_update(int n, int l, int n_ch, const double* Q, const double* Qf, long ld, const double* X,
+                                double* R, const double* part, double* alpha, int n_steps, bool alpha_only,
+                                double* npart, int nb, cudaStream_t st) {
+  if (l > 255) return cudaErrorInvalidValue;
+  if (Qf)
+    k_lz_gs_update<ff><<<dim3(n_ch, nb), 256, 0, st>>>(n, l, n_ch, reinterpret_cast<const ff*>(Qf), ld, X, R, part,
+                                                       alpha, n_steps, alpha_only ? 1 : 0, npart);
+  else
+    k_lz_gs_update<double><<<dim3(n_ch, nb), 256, 0, st>>>(n, l, n_ch, Q, ld, X, R, part, alpha, n_steps,
+                                                           alpha_only ? 1 : 0, npart);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lz_normalise(int n, int l, int n_ch, const double* R, double* Q, double* Qf, long ld,
+                                double* beta, int n_steps, const double* npart, int nb, cudaStream_t st) {
+  if (!npart) nb = 1;   // the norm is then reduced inside the one block of each chain
+  if (Qf)
+    k_lz_normalise_split<ff><<<dim3(n_ch, nb), 256, 0, st>>>(n, l, n_ch, R, Q, reinterpret_cast<ff*>(Qf), ld, beta,
+                                                             n_steps, npart);
+  else
+    k_lz_normalise_split<double><<<dim3(n_ch, nb), 256, 0, st>>>(n, l, n_ch, R, Q, nullptr, ld, beta, n_steps,
+                                                                 npart);
   return cudaGetLastError();
 }
 

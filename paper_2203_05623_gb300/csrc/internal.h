@@ -145,11 +145,6 @@ cudaError_t launch_syev_batched(int n, int batch, double* A, double* w, double* 
                                 cudaStream_t st);
 cudaError_t launch_lz_start(int n, int n_ch, const double* B, double* Q, long ld, double* beta, int n_steps,
                             cudaStream_t st);
-cudaError_t launch_lz_three_term(int n, int l, int n_ch, const double* Q, const double* HQ, double* R, long ld,
-                                 double* alpha, const double* beta, int n_steps, cudaStream_t st);
-cudaError_t launch_lz_reorth(int n, int l, int n_ch, const double* Q, double* R, long ld, cudaStream_t st);
-cudaError_t launch_lz_normalise(int n, int l, int n_ch, const double* R, double* Q, long ld, double* beta,
-                                int n_steps, cudaStream_t st);
 cudaError_t launch_lz_tridiag(int n_ch, int n_steps, const double* alpha, const double* beta, double* T,
                               cudaStream_t st);
 cudaError_t launch_lz_resolvent(int n_ch, int n_steps, int n_v, int n_om, const double* d, const double* U,
@@ -157,6 +152,18 @@ cudaError_t launch_lz_resolvent(int n_ch, int n_steps, int n_v, int n_om, const 
                                 cudaStream_t st);
 cudaError_t launch_lz_assemble(int n_pdep, int n_v, int n_steps, int n_om, const double* ov, const double* y,
                                double coef, double* chi, cudaStream_t st);
+// Split Gram-Schmidt of the Lanczos chains: gridDim.y = nb chunks of the n reals per chain.
+// Qf: float-float copy of the chain vectors (ff pairs in double-sized slots), or null for
+// native FP64 arithmetic.
+int lz_split(int n, int n_ch);
+cudaError_t launch_lz_gs_dots(int n, int l, int n_ch, const double* Q, const double* Qf, long ld, const double* X,
+                              double* part, int nb, cudaStream_t st);
+cudaError_t launch_lz_gs_update(int n, int l, int n_ch, const double* Q, const double* Qf, long ld, const double* X,
+                                double* R, const double* part, double* alpha, int n_steps, bool alpha_only,
+                                double* npart, int nb, cudaStream_t st);
+// q^{l+1} = r / |r| (and its float-float copy); npart null: one block per chain reduces |r|.
+cudaError_t launch_lz_normalise(int n, int l, int n_ch, const double* R, double* Q, double* Qf, long ld,
+                                double* beta, int n_steps, const double* npart, int nb, cudaStream_t st);
 cudaError_t launch_lz_residues(int n_pdep, int n_v, int n_steps, const double* ov, const double* U, const double* beta,
                                double* C, cudaStream_t st);
 cudaError_t launch_lz_g0_eval(int n_pdep, int n_v, int n_steps, int n_z, const double* C, const double* d,

@@ -1239,24 +1239,48 @@ int lanczos_impl(wgw_ctx* c, const double* phi, int npd, int n_steps, const doub
   double* Q = Qb.as<double>();
   double* HQ = c->d.Q.as<double>();
   double* R = c->d.R.as<double>();
-  // The recurrence kernels are timed as other_f64; algorithmic bytes are the vectors each
-  // reads and writes once (the Gram-Schmidt pass: q^0..q^l and r in, r out).
+  // Each step: r = Hq^l - sum_j c_j q^j with c_j = q^j . Hq^l over all previous vectors (the
+  // three-term step, alpha_l = c_l, and the first Gram-Schmidt pass at once: with orthonormal q
+  // the coefficients of q^l and q^(l-1) are alpha_l and beta_l), then a second classical
+  // Gram-Schmidt pass (each pass followed by P_c on the projected chains), then beta_(l+1) = |r|.
+  // Every pass is split over chunks of the n reals so that a few hundred chains fill the GPU; on
+  // the float-float path the passes read a float-float copy of the chain vectors and compute on
+  // the FP32 units.  The recurrence kernels are timed as other_f64; algorithmic bytes are the
+  // vectors each reads and writes once.
   ProfPrec pp(c->prof, true);
   const double vb = (double)n_ch * n * sizeof(double);
+  const int nb = lz_split(n, n_ch);
+  DevBuf part, npart, Qfb;
+  WGW_TRY(part.ensure(sizeof(double) * (size_t)n_ch * nb * n_steps));
+  WGW_TRY(npart.ensure(sizeof(double) * (size_t)n_ch * nb));
+  double* Qf = nullptr;
+  if (c->d.use_ff) {
+    WGW_TRY(Qfb.ensure(sizeof(double) * (size_t)(n_steps + 1) * n_ch * ldw));
+    Qf = Qfb.as<double>();
+  }
+  double* pt = part.as<double>();
   WGW_CK(launch_lz_start(n, n_ch, S, Q, ldw, be.as<double>(), n_steps, st));
+  if (Qf) WGW_CK(launch_to_ff((size_t)n_ch * ldw, Q, Qf, st));
   for (int l = 0; l < n_steps; ++l) {
     double* ql = Q + (size_t)l * n_ch * ldw;
     WGW_TRY(apply_A<double>(c, c->d, ql, HQ, n_ch, nullptr, nullptr, st, proj));
-    WGW_CK(c->prof.run(PK_OTHER, (l > 0 ? 4 : 3) * vb, 0, st, [&] {
-      return launch_lz_three_term(n, l, n_ch, Q, HQ, R, ldw, al.as<double>(), be.as<double>(), n_steps, st); }));
-    if (l + 1 == n_steps) break;
+    const bool last = l + 1 == n_steps;
     for (int pass = 0; pass < 2; ++pass) {
-      WGW_CK(c->prof.run(PK_OTHER, (l + 3) * vb, 4.0 * (l + 1) * n * n_ch, st, [&] {
-        return launch_lz_reorth(n, l, n_ch, Q, R, ldw, st); }));
+      const double* X = pass == 0 ? HQ : R;
+      WGW_CK(c->prof.run(PK_OTHER, (l + 2) * vb, 2.0 * (l + 1) * n * n_ch, st, [&] {
+        return launch_lz_gs_dots(n, l, n_ch, Q, Qf, ldw, X, pt, nb, st); }));
+      WGW_CK(c->prof.run(PK_OTHER, last ? 0.0 : (l + 3) * vb, last ? 0.0 : 2.0 * (l + 1) * n * n_ch, st, [&] {
+        return launch_lz_gs_update(n, l, n_ch, Q, Qf, ldw, X, R, pt, pass == 0 ? al.as<double>() : nullptr,
+                                   n_steps, last, (!proj && pass == 1) ? npart.as<double>() : nullptr, nb, st); }));
+      if (last) break;
       if (proj) WGW_TRY(run_pc<double>(c, R, n_ch, nullptr, c->d.psi.as<double>(), nullptr, st));
     }
-    WGW_CK(c->prof.run(PK_OTHER, 2 * vb, 0, st, [&] {
-      return launch_lz_normalise(n, l, n_ch, R, Q, ldw, be.as<double>(), n_steps, st); }));
+    if (last) break;
+    // After P_c the partial norms of the update are stale: the projected chains reduce |r|
+    // inside one block per chain.
+    WGW_CK(c->prof.run(PK_OTHER, (Qf ? 3 : 2) * vb, 0, st, [&] {
+      return launch_lz_normalise(n, l, n_ch, R, Q, Qf, ldw, be.as<double>(), n_steps,
+                                 proj ? nullptr : npart.as<double>(), nb, st); }));
   }
   // Overlaps <(P_c) phi~_n psi_v | q^l_(m,v)>, one product per state v.
   const int mp = (npd + 63) / 64 * 64;
