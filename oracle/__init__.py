@@ -14,7 +14,8 @@ the paper by eye:
   chi0.py     density response: sum over states (Adler-Wiser, Sec. 2.2),
               Sternheimer solves (Eq. sternheimer) + Eq. dfpt, the free-electron
               closed form, finite differences of the ground-state density,
-              the dense symmetrised matrix chi0bar = v^1/2 chi0 v^1/2 (Sec. 2.1)
+              the dense symmetrised matrix chi0bar = v^1/2 chi0 v^1/2 (Sec. 2.1),
+              the sum over spin channels of a spin-polarised system
   pdep.py     PDEP eigenpairs of chi0bar (Sec. 3) by dense diagonalisation and
               by a textbook block Davidson iteration
   lanczos.py  Lanczos chains (Eq. lanczos and the recurrence above it, Sec. 3)

@@ -97,6 +97,12 @@ def sos_drho(model: Model, dV: np.ndarray, omegas=(0.0,)) -> np.ndarray:
     return out * (model.f_s / model.omega)
 
 
+def sos_drho_channels(models, dV: np.ndarray, omegas=(0.0,)) -> np.ndarray:
+    """Spin-polarised response: the sum over spin channels sigma of Eq. dfpt, each channel a
+    Model of its own (V_sigma, psi_sigma, e_sigma; f_s = 1 for a spin-polarised system)."""
+    return sum(sos_drho(m, dV, omegas) for m in models)
+
+
 def sos_static_block(model: Model, dV: np.ndarray, states=None) -> np.ndarray:
     """Static (w = 0) sum over states for a block of perturbations that are real in r.
 

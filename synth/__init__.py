@@ -29,7 +29,7 @@ import numpy as np
 import scipy.linalg
 
 __all__ = [
-    "Config", "CONFIGS", "System", "miller_sphere", "make_system",
+    "Config", "CONFIGS", "System", "miller_sphere", "make_system", "make_spin_system",
     "perturbations", "gauss_legendre_omega", "real_basis_map",
 ]
 
@@ -265,6 +265,20 @@ def make_system(cfg: Config | str) -> System:
                   beta_G=beta_G, d_proj=d_proj, proj_atom=proj_atom, psi_v=psi_v,
                   e_v=evals[: cfg.n_v].copy(), e_lumo=float(evals[cfg.n_v]),
                   positions=positions, well_seed_used=seed)
+
+
+def make_spin_system(cfg: Config | str, depth_split: float = 0.4, n_v_down: int | None = None):
+    """Two spin channels of one model: the same cell, cutoff and well positions, wells deeper by
+    depth_split/2 for spin up and shallower by depth_split/2 for spin down (a model exchange
+    splitting), n_v occupied up states and n_v_down (default n_v - 1) down states.
+    Returns (up, down) Systems; the down channel keeps the up channel's well seed."""
+    if isinstance(cfg, str):
+        cfg = CONFIGS[cfg]
+    up = make_system(dataclasses.replace(cfg, well_depth=cfg.well_depth + 0.5 * depth_split))
+    down = make_system(dataclasses.replace(cfg, well_depth=cfg.well_depth - 0.5 * depth_split,
+                                           well_seed=up.well_seed_used, min_gap=-1.0,
+                                           n_v=cfg.n_v - 1 if n_v_down is None else n_v_down))
+    return up, down
 
 
 def perturbations(miller_rho: np.ndarray, L: float, n_pert: int, seed: int,

@@ -394,3 +394,24 @@ def test_planted_transposed_tridiagonal_vectors_fail_g0_pin(tiny, monkeypatch):
     out = g0.g0_lanczos(m, phi, [0], m.mw.shape[0], Z_G0)
     monkeypatch.undo()
     assert rel(out["g0"], g0.g0_exact(m, phi, [0], Z_G0)) > 1e-3
+
+
+# ---------------------------------------------------------------- spin channels (sum over sigma, Eq. dfpt)
+def test_spin_channels_identical_equal_unpolarised(tiny):
+    """Two identical channels with f_s = 1 each give the spin-unpolarised response (f_s = 2)."""
+    dV = synth.perturbations(tiny.miller_rho, tiny.L, 2, 41)
+    one = model_of(tiny, f_s=1.0)
+    both = chi0.sos_drho_channels([one, one], dV, [0.0, 0.7])
+    assert rel(both, chi0.sos_drho(model_of(tiny), dV, [0.0, 0.7])) < 1e-14
+
+
+def test_spin_channels_are_derivative_of_total_density():
+    """chi0 dV of a spin-polarised model (split wells, N_up != N_down) equals the derivative of
+    the total ground-state density of both channels under dV (no response formula used)."""
+    up, dn = synth.make_spin_system("tiny_L6_12")
+    assert up.psi_v.shape[1] == 2 and dn.psi_v.shape[1] == 1
+    assert np.array_equal(up.positions, dn.positions)
+    models = [model_of(up, f_s=1.0), model_of(dn, f_s=1.0)]
+    dV = synth.perturbations(up.miller_rho, up.L, 1, 42)[:, 0]
+    fd = sum(chi0.finite_difference_drho(m, dV, 1e-3) for m in models)
+    assert rel(chi0.sos_drho_channels(models, dV, [0.0])[:, 0, 0], fd) < 1e-9
