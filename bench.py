@@ -44,6 +44,11 @@ WORKLOADS = {
                            "highest occupied states = 256 chains of 32 steps (FP64, full "
                            "reorthogonalisation), residues and resolvent matrices at 16 complex "
                            "frequencies"),
+    "spin_L16_48": dict(config="pdep_L16_48", n_pert=64, pert_seed=5, cg_tol=1e-10,
+                        desc="spin-polarised chibar0 block apply on the 48^3 model: channels with wells "
+                             "split by +-0.2 Ha, 64 up + 62 down occupied states x 64 perturbations = "
+                             "8064 Sternheimer systems, one context per channel (f_s = 1) run "
+                             "concurrently, mixed FP32/FP64"),
     "chi0_L10_24": dict(config="chi0_L10_24", n_pert=8, pert_seed=2, cg_tol=1e-10,
                         desc="chi0 apply, 8 perturbations x 4 occupied states = 32 Sternheimer systems, "
                              "24^3 grid, N_pw=515, N_rho=4337, mixed FP32/FP64"),
@@ -266,6 +271,45 @@ def run_g0(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def run_spin(args, wl):
+    """Spin-polarised block apply through wgw_apply_channels (host arrays, copies included)."""
+    import numpy as np
+    import synth
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    up, dn = synth.make_spin_system(wl["config"])
+    phi = synth.perturbations(up.miller_rho, up.L, wl["n_pert"], wl["pert_seed"])
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2203_05623_gb300 import build
+    build.build()
+    import paper_2203_05623_gb300 as W
+    prec = W.WGW_MIXED if args.precision == "mixed" else W.WGW_FP64
+    ctxs = [W.wgw_setup(c.L, c.ecut, c.grid, c.vloc_G, c.psi_v, c.e_v,
+                        W.wgw_default_options(precision=prec, cg_tol=wl["cg_tol"], f_s=1.0,
+                                              fp64_emulation=args.fp64_emulation)) for c in (up, dn)]
+    for _ in range(max(args.warmup, 1)):
+        W.wgw_apply_channels(ctxs, phi, [0.0], symmetrized=True)
+    ts, st = [], None
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            _, st, _ = W.wgw_apply_channels(ctxs, phi, [0.0], symmetrized=True)
+            ts.append(time.perf_counter() - t0)
+    total = sum(ts)
+    n_sys = st["n_systems"]
+    io = wl["n_pert"] * up.n_rho * 16
+    print(json.dumps({"metric": "Sternheimer solves/s, spin-polarised (both channels)", "value": n_sys * args.steps / total,
+                      "unit": "Sternheimer solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+                      "vs_baseline": None, "dtype": "f32/f64" if args.precision == "mixed" else "f64",
+                      "data": "synthetic",
+                      "config": {"workload": args.workload, "desc": wl["desc"], "precision": args.precision,
+                                 "timed": "host call including the host <-> device copies"},
+                      "solve": st, "e2e": {"value": n_sys * args.steps / total, "unit": "Sternheimer solves/s",
+                                           "h2d_bytes_per_step": 2 * io, "d2h_bytes_per_step": 2 * io},
+                      "clocks": clk.summary()}), flush=True)
+
+
 def run_serve(args, wl):
     """Served stream: requests submitted at Poisson arrival times through wgw_submit/wgw_wait."""
     import numpy as np
@@ -361,6 +405,8 @@ def main():
         return run_dyson(args, wl)
     if args.workload.startswith("g0"):
         return run_g0(args, wl)
+    if args.workload.startswith("spin"):
+        return run_spin(args, wl)
 
     import numpy as np
     import torch

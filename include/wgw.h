@@ -151,6 +151,22 @@ int wgw_apply_chibar0(wgw_ctx* ctx, const double* phi, int n_pert, const double*
                       double* out, wgw_stats* st);
 
 /*
+ * Spin-polarised response: the sum over spin channels sigma of Eq. dfpt (Sec. 3; the
+ * Sternheimer systems of every channel and state are independent).  Each context is one channel
+ * of the same system: the same cell, cutoff and grid, its own V_sigma, psi_sigma, e_sigma and
+ * options, normally f_s = 1 (wgw_options.f_s).  Then
+ *   out = sum_sigma chi0_sigma(i omega) dV       (symmetrized = 0, arguments as wgw_apply_chi0)
+ *   out = sum_sigma chi0bar_sigma(i omega) phi   (symmetrized = 1, as wgw_apply_chibar0),
+ * host arrays, summed in the order of ctxs.  The channels run concurrently, each on its own
+ * context's stream from its own host thread.  st: n_systems and n_converged summed, the other
+ * fields the maximum over channels.
+ * Returns WGW_ERR_ARG for n_ctx outside 1..8, a context listed twice, or contexts that differ in
+ * cell, cutoff or grid; WGW_ERR_NOCONV (out written) when a channel missed cg_tol.
+ */
+int wgw_apply_channels(wgw_ctx* const* ctxs, int n_ctx, int symmetrized, const double* dV, int n_pert,
+                       const double* omega, int n_omega, double* out, wgw_stats* st);
+
+/*
  * Symmetrised response chi0bar phi = v^1/2 chi0 v^1/2 phi (Sec. 2.1), v^1/2(G) = sqrt(4 pi)/|G|,
  * zero at G = 0.  phi and out are dimensionless density-sphere coefficients; layout as for
  * wgw_apply_chi0_dev (device pointers, work on `stream`).

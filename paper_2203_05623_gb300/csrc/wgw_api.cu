@@ -1624,6 +1624,58 @@ int wgw_apply_chibar0(wgw_ctx* c, const double* phi, int n_pert, const double* o
   return apply_host(c, phi, n_pert, omega, n_omega, out, true, st);
 }
 
+int wgw_apply_channels(wgw_ctx* const* ctxs, int n_ctx, int symmetrized, const double* dV, int n_pert,
+                       const double* omega, int n_omega, double* out, wgw_stats* st) {
+  g_last_error.clear();
+  if (!ctxs || n_ctx < 1 || n_ctx > 8) return fail(WGW_ERR_ARG, "need 1..8 contexts");
+  for (int k = 0; k < n_ctx; ++k) {
+    const wgw_ctx* c = ctxs[k];
+    if (!c) return fail(WGW_ERR_ARG, "null context");
+    for (int j = 0; j < k; ++j)
+      if (ctxs[j] == c) return fail(WGW_ERR_ARG, "a context is listed twice");
+    if (c->N != ctxs[0]->N || c->L != ctxs[0]->L || c->ecut != ctxs[0]->ecut)
+      return fail(WGW_ERR_ARG, "the channels differ in cell, cutoff or grid");
+  }
+  if (n_pert <= 0) return n_pert == 0 ? WGW_OK : fail(WGW_ERR_ARG, "n_pert < 0");
+  if (n_omega < 1 || !omega || !dV || !out) return fail(WGW_ERR_ARG, "need dV, out and n_omega >= 1 frequencies");
+  const size_t n_out = 2 * (size_t)ctxs[0]->rho.n * n_pert * n_omega;
+  // Every channel on its own context (own stream and buffers) from its own host thread, so that
+  // the channels overlap on the GPU; the sum is taken in channel order.
+  std::vector<std::vector<double>> part(n_ctx);
+  std::vector<int> status(n_ctx, WGW_OK);
+  std::vector<std::string> err(n_ctx);
+  std::vector<wgw_stats> sts(n_ctx);
+  std::vector<std::thread> th;
+  for (int k = 0; k < n_ctx; ++k) {
+    part[k].assign(n_out, 0.0);
+    th.emplace_back([&, k] {
+      if (cudaSetDevice(ctxs[k]->device) != cudaSuccess) { status[k] = WGW_ERR_CUDA; err[k] = "cudaSetDevice"; return; }
+      status[k] = apply_host(ctxs[k], dV, n_pert, omega, n_omega, part[k].data(), symmetrized != 0, &sts[k]);
+      err[k] = g_last_error;
+    });
+  }
+  for (std::thread& t : th) t.join();
+  for (int k = 0; k < n_ctx; ++k)
+    if (status[k] != WGW_OK && status[k] != WGW_ERR_NOCONV) return fail(status[k], err[k].c_str());
+  for (size_t i = 0; i < n_out; ++i) {
+    double acc = 0.0;
+    for (int k = 0; k < n_ctx; ++k) acc += part[k][i];
+    out[i] = acc;
+  }
+  int result = WGW_OK;
+  wgw_stats tot{};
+  for (int k = 0; k < n_ctx; ++k) {
+    tot.n_systems += sts[k].n_systems;
+    tot.n_converged += sts[k].n_converged;
+    tot.max_iters = std::max(tot.max_iters, sts[k].max_iters);
+    tot.refinements = std::max(tot.refinements, sts[k].refinements);
+    tot.max_rel_residual = std::max(tot.max_rel_residual, sts[k].max_rel_residual);
+    if (status[k] == WGW_ERR_NOCONV) result = fail(WGW_ERR_NOCONV, err[k].c_str());
+  }
+  if (st) *st = tot;
+  return result;
+}
+
 int wgw_profile_enable(wgw_ctx* c, int on) {
   if (!c) return fail(WGW_ERR_ARG, "null context");
   c->prof.reset();

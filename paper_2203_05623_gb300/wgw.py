@@ -103,6 +103,8 @@ def lib(path: str | None = None):
     L.wgw_poll.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Result)]
     L.wgw_wait.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(Result)]
     L.wgw_dyson.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp]
+    L.wgw_apply_channels.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int,
+                                     _dp, ctypes.c_int, _dp, ctypes.POINTER(Stats)]
     L.wgw_g0_lanczos.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                  ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, ctypes.POINTER(Stats)]
     L.wgw_destroy.argtypes = [ctypes.c_void_p]
@@ -210,6 +212,25 @@ def wgw_apply_chi0(ctx: Context, dV, omega=(0.0,), allow_noconv=False, out=None)
 def wgw_apply_chibar0(ctx: Context, phi, omega=(0.0,), allow_noconv=False, out=None):
     """Host arrays: chibar0 phi = v^1/2 chi0 v^1/2 phi; layout as wgw_apply_chi0."""
     return _host_call(lib().wgw_apply_chibar0, "wgw_apply_chibar0", ctx, phi, omega, allow_noconv, out)
+
+
+def wgw_apply_channels(ctxs, dV, omega=(0.0,), symmetrized=False, allow_noconv=False):
+    """Spin-polarised response: the sum over the channels (one context each, normally f_s = 1)
+    of chi0 dV (or chibar0 phi with symmetrized=True); layout as wgw_apply_chi0."""
+    ctxs = list(ctxs)
+    dV = np.asarray(dV, np.complex128)
+    dV = dV[:, None] if dV.ndim == 1 else dV
+    n_pert = dV.shape[1]
+    om = np.ascontiguousarray(omega, np.float64)
+    buf = _interleave(dV)
+    out = np.zeros((len(om), n_pert, ctxs[0].n_rho), np.complex128)
+    handles = (ctypes.c_void_p * len(ctxs))(*[c.handle for c in ctxs])
+    st = Stats()
+    s = lib().wgw_apply_channels(handles, len(ctxs), 1 if symmetrized else 0, buf.ctypes.data_as(_dp), n_pert,
+                                 om.ctypes.data_as(_dp), len(om), out.view(np.float64).ctypes.data_as(_dp),
+                                 ctypes.byref(st))
+    _check(s, "wgw_apply_channels", (WGW_OK, WGW_ERR_NOCONV) if allow_noconv else (WGW_OK,))
+    return out.transpose(2, 1, 0), st.as_dict(), s
 
 
 class Ticket:

@@ -52,6 +52,8 @@ class Config:
     kb_width: float = 0.8     # w_p [bohr]
     kb_d_s: float = 1.0       # D_s [Ha]
     kb_d_p: float = 0.5       # D_p [Ha]
+    kb_dch: bool = False      # five more (d-type) KB projectors per atom
+    kb_d_d: float = 0.3       # D_d [Ha]
     min_gap: float = 0.01     # reseed (seed + 1) while HOMO-LUMO gap < this [Ha]
 
 
@@ -161,7 +163,9 @@ def _gaussian_wells(cfg: Config, miller_rho: np.ndarray, positions: np.ndarray) 
 
 
 def _kb_projectors(cfg: Config, miller_wfc: np.ndarray, positions: np.ndarray):
-    """Per atom: beta_s(G) = Omega^{-1/2} e^{-wp^2 G^2/2} e^{-iG.R}, beta_p,alpha = (-i G_alpha wp) beta_s."""
+    """Per atom: beta_s(G) = Omega^{-1/2} e^{-wp^2 G^2/2} e^{-iG.R}, beta_p,alpha = (-i G_alpha wp) beta_s,
+    and with kb_dch five d-type beta_d,k = -wp^2 Q_k(G) beta_s, Q = (GxGy, GyGz, GzGx, (Gx^2 - Gy^2)/2,
+    (3Gz^2 - G^2)/(2 sqrt 3)) (the transforms of the l = 2 real harmonics times a Gaussian)."""
     n_pw = miller_wfc.shape[0]
     if not cfg.kb:
         return (np.zeros((n_pw, 0), np.complex128), np.zeros(0), np.zeros(0, np.int32))
@@ -177,6 +181,11 @@ def _kb_projectors(cfg: Config, miller_wfc: np.ndarray, positions: np.ndarray):
         cols.append(s); d.append(cfg.kb_d_s); atom.append(a)
         for alpha in range(3):
             cols.append(-1j * G[:, alpha] * wp * s); d.append(cfg.kb_d_p); atom.append(a)
+        if cfg.kb_dch:
+            gx, gy, gz = G[:, 0], G[:, 1], G[:, 2]
+            for q in (gx * gy, gy * gz, gz * gx, 0.5 * (gx * gx - gy * gy),
+                      (3.0 * gz * gz - G2) / (2.0 * math.sqrt(3.0))):
+                cols.append(-wp * wp * q * s); d.append(cfg.kb_d_d); atom.append(a)
     return (np.stack(cols, axis=1), np.asarray(d, np.float64), np.asarray(atom, np.int32))
 
 
@@ -270,14 +279,23 @@ def make_system(cfg: Config | str) -> System:
 def make_spin_system(cfg: Config | str, depth_split: float = 0.4, n_v_down: int | None = None):
     """Two spin channels of one model: the same cell, cutoff and well positions, wells deeper by
     depth_split/2 for spin up and shallower by depth_split/2 for spin down (a model exchange
-    splitting), n_v occupied up states and n_v_down (default n_v - 1) down states.
-    Returns (up, down) Systems; the down channel keeps the up channel's well seed."""
+    splitting).  Spin up holds n_v occupied states; spin down n_v_down, by default the largest
+    count in n_v-1 .. n_v-4 whose gap to the next state is at least min_gap (else the count
+    with the largest gap).  Returns (up, down) Systems; the down channel keeps the up channel's
+    well seed."""
     if isinstance(cfg, str):
         cfg = CONFIGS[cfg]
     up = make_system(dataclasses.replace(cfg, well_depth=cfg.well_depth + 0.5 * depth_split))
-    down = make_system(dataclasses.replace(cfg, well_depth=cfg.well_depth - 0.5 * depth_split,
-                                           well_seed=up.well_seed_used, min_gap=-1.0,
-                                           n_v=cfg.n_v - 1 if n_v_down is None else n_v_down))
+    full = make_system(dataclasses.replace(cfg, well_depth=cfg.well_depth - 0.5 * depth_split,
+                                           well_seed=up.well_seed_used, min_gap=-1.0))
+    levels = np.append(full.e_v, full.e_lumo)
+    if n_v_down is None:
+        counts = list(range(cfg.n_v - 1, max(1, cfg.n_v - 4) - 1, -1))
+        gaps = [levels[c] - levels[c - 1] for c in counts]
+        ok = [c for c, g in zip(counts, gaps) if g >= cfg.min_gap]
+        n_v_down = ok[0] if ok else counts[int(np.argmax(gaps))]
+    down = dataclasses.replace(full, psi_v=full.psi_v[:, :n_v_down].copy(), e_v=full.e_v[:n_v_down].copy(),
+                               e_lumo=float(levels[n_v_down]))
     return up, down
 
 

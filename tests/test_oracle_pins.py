@@ -415,3 +415,18 @@ def test_spin_channels_are_derivative_of_total_density():
     dV = synth.perturbations(up.miller_rho, up.L, 1, 42)[:, 0]
     fd = sum(chi0.finite_difference_drho(m, dV, 1e-3) for m in models)
     assert rel(chi0.sos_drho_channels(models, dV, [0.0])[:, 0, 0], fd) < 1e-9
+
+
+def test_static_response_derivative_with_d_channels():
+    """KB with s, p and d channels (9 per atom): the static response still equals the density
+    derivative, and the dense H still equals its FFT application."""
+    s = synth.make_system(synth.Config("kbd", L=6.0, ecut=2.5, grid=12, n_wells=2, well_seed=7,
+                                       n_v=2, kb=True, kb_dch=True))
+    assert s.beta_G.shape[1] == 18
+    m = model_of(s)
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((m.mw.shape[0], 2)) + 1j * rng.standard_normal((m.mw.shape[0], 2))
+    assert rel(m.apply_h(x), m.h_dense() @ x) < 1e-13
+    dV = synth.perturbations(s.miller_rho, s.L, 1, 43)[:, 0]
+    fd = chi0.finite_difference_drho(m, dV, 1e-3)
+    assert rel(chi0.sos_drho(m, dV, [0.0])[:, 0, 0], fd) < 1e-9
