@@ -28,7 +28,7 @@ constexpr int kSyevMax = 2048;
 
 __global__ void __launch_bounds__(1024) k_syev(int n, double* __restrict__ A, int lda, double* __restrict__ w,
                                                double* __restrict__ Z, int ldz, double* __restrict__ work,
-                                               int* __restrict__ info) {
+                                               int* __restrict__ info, int tridiagonal) {
   __shared__ double red[33];
   __shared__ int sh_int[4];
   extern __shared__ double rot[];            // 2 * n: cosines and sines of one QL sweep
@@ -50,7 +50,8 @@ __global__ void __launch_bounds__(1024) k_syev(int n, double* __restrict__ A, in
     Z[(size_t)c * ldz + r] = (r == c) ? 1.0 : 0.0;
   }
   __syncthreads();
-  for (int k = 0; k + 2 < n; ++k) {
+  // A tridiagonal input is already in the form the Householder stage produces (Z = I).
+  for (int k = 0; !tridiagonal && k + 2 < n; ++k) {
     const int m = n - k - 1;   // length of the column below the diagonal
     double part = 0.0;
     for (int i = tid; i < m; i += nth) {
@@ -270,17 +271,24 @@ __device__ __forceinline__ void lz_warp_sum(ff& a) {
 
 constexpr int kLzJ = 8;   // dot products accumulated per sweep over the chunk
 constexpr int kLzE = 4;   // elements per thread per sweep (256-thread blocks)
+constexpr int kLzChunkMax = 4096;   // reals per chunk (32 KB of shared memory in the dots kernel)
 
 // part[(s nb + b)(l+1) + j] = sum over chunk b of q^j[i] x[i], j = 0..l.  256 threads; each thread
-// holds kLzE elements of x so that kLzJ x kLzE independent loads are in flight per sweep.
+// holds kLzE elements of x so that kLzJ x kLzE independent loads are in flight per sweep.  The
+// chunk of x is converted to C once into shared memory (dynamic, chunk x sizeof(C) bytes): a
+// double -> float-float conversion runs on the FP64 unit.
 template <typename C>
 __global__ void __launch_bounds__(256) k_lz_gs_dots(int n, int l, int n_ch, const C* __restrict__ Qg, long ld,
                                                     const double* X, double* __restrict__ part) {
   __shared__ double red[8][kLzJ];
+  extern __shared__ __align__(16) unsigned char lz_smem[];
+  C* xs = reinterpret_cast<C*>(lz_smem);
   const int s = blockIdx.x, nb = gridDim.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int i0, i1;
   lz_chunk(n, i0, i1);
   const double* x = X + (size_t)s * ld;
+  for (int i = i0 + (int)threadIdx.x; i < i1; i += blockDim.x) xs[i - i0] = lz_c<C>(x[i]);
+  __syncthreads();
   for (int j0 = 0; j0 <= l; j0 += kLzJ) {
     const int nj = min(kLzJ, l + 1 - j0);
     C acc[kLzJ];
@@ -291,7 +299,7 @@ __global__ void __launch_bounds__(256) k_lz_gs_dots(int n, int l, int n_ch, cons
 #pragma unroll
       for (int e = 0; e < kLzE; ++e) {
         const int i = base + e * 256;
-        xv[e] = lz_c<C>(i < i1 ? x[i] : 0.0);
+        xv[e] = i < i1 ? xs[i - i0] : lz_c<C>(0.0);
       }
 #pragma unroll
       for (int jj = 0; jj < kLzJ; ++jj) {
@@ -345,7 +353,7 @@ __global__ void __launch_bounds__(256) k_lz_gs_update(int n, int l, int n_ch, co
   lz_chunk(n, i0, i1);
   const double* x = X + (size_t)s * ld;
   double* r = R + (size_t)s * ld;
-  double nn = 0.0;
+  C nn = lz_c<C>(0.0);
   // kLzE elements per thread, j outermost: kLzE independent loads per j, four j unrolled.
   for (int base = i0 + (int)threadIdx.x; base < i1; base += kLzE * 256) {
     C acc[kLzE];
@@ -368,15 +376,14 @@ __global__ void __launch_bounds__(256) k_lz_gs_update(int n, int l, int n_ch, co
     for (int e = 0; e < kLzE; ++e) {
       const int i = base + e * 256;
       if (i < i1) {
-        const double rd = lz_d(acc[e]);
-        r[i] = rd;
-        nn = fma(rd, rd, nn);
+        r[i] = lz_d(acc[e]);
+        mac(nn, acc[e], acc[e]);
       }
     }
   }
   if (npart) {
     Thr th{(int)threadIdx.x, (int)blockDim.x};
-    const double t = block_sum(nn, red, th);
+    const double t = block_sum(lz_d(nn), red, th);
     if (threadIdx.x == 0) npart[(size_t)s * nb + blockIdx.y] = t;
   }
 }
@@ -544,12 +551,12 @@ cudaError_t launch_syev(int n, double* A, int lda, double* w, double* Z, int ldz
     cudaError_t err = cudaFuncSetAttribute(k_syev, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
   }
-  k_syev<<<1, 1024, smem, st>>>(n, A, lda, w, Z, ldz, work, info);
+  k_syev<<<1, 1024, smem, st>>>(n, A, lda, w, Z, ldz, work, info, 0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_syev_batched(int n, int batch, double* A, double* w, double* Z, double* work, int* info,
-                                cudaStream_t st) {
+                                cudaStream_t st, bool tridiagonal) {
   if (n <= 0 || batch <= 0) return cudaSuccess;
   if (n > kSyevMax) return cudaErrorInvalidValue;
   const size_t smem = sizeof(double) * 2 * (size_t)n;
@@ -557,7 +564,7 @@ cudaError_t launch_syev_batched(int n, int batch, double* A, double* w, double* 
     cudaError_t err = cudaFuncSetAttribute(k_syev, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
   }
-  k_syev<<<batch, n <= 128 ? 128 : 1024, smem, st>>>(n, A, n, w, Z, n, work, info);
+  k_syev<<<batch, n <= 128 ? 128 : 1024, smem, st>>>(n, A, n, w, Z, n, work, info, tridiagonal ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -590,16 +597,20 @@ cudaError_t launch_lz_assemble(int n_pdep, int n_v, int n_steps, int n_om, const
 
 int lz_split(int n, int n_ch) {
   const int want = (4 * 304 + n_ch - 1) / n_ch;      // about eight 256-thread blocks per SM
-  return std::max(1, std::min(want, (n + 511) / 512));
+  // Chunks of 512 .. 4096 reals (the dots kernel stages a chunk in 32 KB of shared memory).
+  return std::max((n + kLzChunkMax - 1) / kLzChunkMax, std::max(1, std::min(want, (n + 511) / 512)));
 }
 
 cudaError_t launch_lz_gs_dots(int n, int l, int n_ch, const double* Q, const double* Qf, long ld, const double* X,
                               double* part, int nb, cudaStream_t st) {
   if (l > 255) return cudaErrorInvalidValue;
+  const int per = (n + nb - 1) / nb;
+  if (per > kLzChunkMax) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(double) * (size_t)per;   // sizeof(ff) == sizeof(double)
   if (Qf)
-    k_lz_gs_dots<ff><<<dim3(n_ch, nb), 256, 0, st>>>(n, l, n_ch, reinterpret_cast<const ff*>(Qf), ld, X, part);
+    k_lz_gs_dots<ff><<<dim3(n_ch, nb), 256, smem, st>>>(n, l, n_ch, reinterpret_cast<const ff*>(Qf), ld, X, part);
   else
-    k_lz_gs_dots<double><<<dim3(n_ch, nb), 256, 0, st>>>(n, l, n_ch, Q, ld, X, part);
+    k_lz_gs_dots<double><<<dim3(n_ch, nb), 256, smem, st>>>(n, l, n_ch, Q, ld, X, part);
   return cudaGetLastError();
 }
 

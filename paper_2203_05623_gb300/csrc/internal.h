@@ -103,9 +103,10 @@ cudaError_t launch_tc_tile_psi(const float* Psi, long ldp, int n, int nv, unsign
 cudaError_t tc_error_read_and_clear(int* flag, cudaStream_t st);
 // C = A^T B: A is K x m (column j at A + j*lda), B is K x n (column j at B + c_j * ldb with
 // c_j = cols[j], or j when cols is null); C is written row-major with rows of length n, padded
-// to a multiple of 64 rows.  work: gemm_tn_work_elems(K, m, n) doubles.
+// to a multiple of 64 rows.  work: gemm_tn_work_elems(K, m, n) doubles.  ffc: float-float
+// products and sums (operands converted once into shared memory) instead of native FP64.
 cudaError_t launch_gemm_tn(const double* A, long lda, const double* B, long ldb, int K, int m, int n, double* C,
-                           double* work, cudaStream_t st, const int* cols = nullptr);
+                           double* work, cudaStream_t st, const int* cols = nullptr, bool ffc = false);
 size_t gemm_tn_work_elems(int K, int m, int n);
 // Y[:, j] = beta Y[:, j] + alpha sum_v A[:, v] C[v][j]: A is n x k, C row-major k x ncols (row length ldc).
 cudaError_t launch_gemm_nn(const double* A, long lda, int n, int k, const double* C, long ldc, int ncols,
@@ -141,8 +142,9 @@ cudaError_t launch_shifted_residual(int n_cs, int n, const double* B, const doub
 // out[s] = |x_{2s}|^2 + |x_{2s+1}|^2.
 cudaError_t launch_pair_norm2(int n_cs, int n, const double* x, long ld, double* out, cudaStream_t st);
 // Lanczos chains (dense_kernels.cu); chain s keeps q^l at Q + (l * n_ch + s) * ld.
+// tridiagonal: the input matrices are tridiagonal (the Householder stage is skipped).
 cudaError_t launch_syev_batched(int n, int batch, double* A, double* w, double* Z, double* work, int* info,
-                                cudaStream_t st);
+                                cudaStream_t st, bool tridiagonal = false);
 cudaError_t launch_lz_start(int n, int n_ch, const double* B, double* Q, long ld, double* beta, int n_steps,
                             cudaStream_t st);
 cudaError_t launch_lz_tridiag(int n_ch, int n_steps, const double* alpha, const double* beta, double* T,

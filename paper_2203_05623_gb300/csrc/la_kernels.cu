@@ -665,13 +665,14 @@ cudaError_t launch_pc(T* Y, long ldy, int n_sys, const int* list, const T* Psi, 
 }
 
 cudaError_t launch_gemm_tn(const double* A, long lda, const double* B, long ldb, int K, int m, int n, double* C,
-                           double* work, cudaStream_t st, const int* cols) {
+                           double* work, cudaStream_t st, const int* cols, bool ffc) {
   if (m == 0 || n == 0) return cudaSuccess;
   const int n_kb = pc_kblocks(K, n);
   const int kblk = ((K + n_kb - 1) / n_kb + kGK - 1) / kGK * kGK;
   const int mp = (m + kGT - 1) / kGT * kGT;
   dim3 g1((n + kGT - 1) / kGT, n_kb, mp / kGT);
-  k_pc_gemm1<double><<<g1, 256, 0, st>>>(A, lda, B, ldb, K, m, n, cols, kblk, work);
+  if (ffc) k_pc_gemm1<double, ff><<<g1, 256, 0, st>>>(A, lda, B, ldb, K, m, n, cols, kblk, work);
+  else k_pc_gemm1<double><<<g1, 256, 0, st>>>(A, lda, B, ldb, K, m, n, cols, kblk, work);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   const size_t slice = (size_t)mp * n;

@@ -212,7 +212,7 @@ struct wgw_ctx {
   // apply work space (double unless noted)
   DevBuf dvin, dv_rb, dv_r, Trho, Dr, drho_rb, eps, a_idx, b_idx, brow, cg_rz, cg_bb, cg_rr,
       cg_act, cg_it, cnt, rr64, act64, norms, pc_work, sys_list, list64, cg_rzi, omg, row_list, rowact,
-      drho_all, psi_tc, cg_best, cg_itbest;
+      drho_all, psi_tc, cg_best, cg_itbest, lz_q, lz_qf;
   cudaStream_t stream = nullptr;
   Prof prof;
   std::vector<int> last_iters;      // per system of the last apply: CG iterations (all refinements)
@@ -251,7 +251,7 @@ struct wgw_ctx {
     d.release(); f.release(); wfc.release(); rho.release();
     DevBuf* all[] = {&e_v_d, &dvin, &dv_rb, &dv_r, &Trho, &Dr, &drho_rb, &eps, &a_idx, &b_idx, &brow,
                      &cg_rz, &cg_bb, &cg_rr, &cg_act, &cg_it, &cnt, &rr64, &act64, &norms, &pc_work, &sys_list, &list64, &cg_rzi, &omg,
-                     &row_list, &rowact, &drho_all, &psi_tc, &cg_best, &cg_itbest};
+                     &row_list, &rowact, &drho_all, &psi_tc, &cg_best, &cg_itbest, &lz_q, &lz_qf};
     for (DevBuf* b : all) b->release();
     if (stream) cudaStreamDestroy(stream);
   }
@@ -1230,7 +1230,9 @@ int lanczos_impl(wgw_ctx* c, const double* phi, int npd, int n_steps, const doub
     WGW_CK(launch_plane_r2g<double>(c->wfc.tab(), c->wfc.npt_max, f, c->d.Tw.as<cplx<double>>(), e, st));
     if (proj) WGW_TRY(run_pc<double>(c, S, n_ch, nullptr, c->d.psi.as<double>(), nullptr, st));
   }
-  DevBuf Qb, al, be, T, dd, U, wk, inf, ov, y, om, lists;
+  // The chain vectors (and their float-float copy) stay with the context between calls.
+  DevBuf& Qb = c->lz_q;
+  DevBuf al, be, T, dd, U, wk, inf, ov, y, om, lists;
   WGW_TRY(Qb.ensure(sizeof(double) * (size_t)(n_steps + 1) * n_ch * ldw));
   WGW_TRY(al.ensure(sizeof(double) * (size_t)n_ch * n_steps));
   WGW_TRY(be.ensure(sizeof(double) * (size_t)n_ch * n_steps));
@@ -1250,7 +1252,8 @@ int lanczos_impl(wgw_ctx* c, const double* phi, int npd, int n_steps, const doub
   ProfPrec pp(c->prof, true);
   const double vb = (double)n_ch * n * sizeof(double);
   const int nb = lz_split(n, n_ch);
-  DevBuf part, npart, Qfb;
+  DevBuf part, npart;
+  DevBuf& Qfb = c->lz_qf;
   WGW_TRY(part.ensure(sizeof(double) * (size_t)n_ch * nb * n_steps));
   WGW_TRY(npart.ensure(sizeof(double) * (size_t)n_ch * nb));
   double* Qf = nullptr;
@@ -1295,7 +1298,7 @@ int lanczos_impl(wgw_ctx* c, const double* phi, int npd, int n_steps, const doub
       for (int m = 0; m < npd; ++m) cols[(size_t)l * npd + m] = l * n_ch + m * n_v + v;
     WGW_CK(cudaMemcpyAsync(lists.p, cols.data(), sizeof(int) * cols.size(), cudaMemcpyHostToDevice, st));
     WGW_CK(launch_gemm_tn(S + (size_t)v * ldw, (long)n_v * ldw, Q, ldw, n, npd, n_steps * npd,
-                          ov.as<double>() + (size_t)v * ovs, gw.as<double>(), st, lists.as<int>()));
+                          ov.as<double>() + (size_t)v * ovs, gw.as<double>(), st, lists.as<int>(), Qf != nullptr));
     WGW_CK(cudaStreamSynchronize(st));   // cols is reused for the next state
   }
   // Tridiagonal spectra d, U of every chain.
@@ -1306,7 +1309,7 @@ int lanczos_impl(wgw_ctx* c, const double* phi, int npd, int n_steps, const doub
   WGW_TRY(inf.ensure(sizeof(int) * n_ch));
   WGW_CK(launch_lz_tridiag(n_ch, n_steps, al.as<double>(), be.as<double>(), T.as<double>(), st));
   WGW_CK(launch_syev_batched(n_steps, n_ch, T.as<double>(), dd.as<double>(), U.as<double>(), wk.as<double>(),
-                             inf.as<int>(), st));
+                             inf.as<int>(), st, true));
   std::vector<int> infh(n_ch);
   WGW_CK(cudaMemcpyAsync(infh.data(), inf.p, sizeof(int) * n_ch, cudaMemcpyDeviceToHost, st));
   WGW_CK(cudaStreamSynchronize(st));
