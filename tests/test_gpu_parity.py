@@ -73,6 +73,21 @@ def test_chi0_mixed_matches_sum_over_states(W, cfg24, ref24, emulate, tcores):
     assert rel_err(drho, ref) < 1e-8
 
 
+@pytest.mark.parametrize("n_v,n_wells", [(70, 16), (256, 48)])
+def test_many_occupied_states_tensor_core_projector(W, n_v, n_wells):
+    """P_c with more occupied states than one 64-wide MMA tile (70: a ragged tile; 256: the
+    largest count the tensor-core projector takes), mixed path on both projector kinds."""
+    s = synth.make_system(synth.Config(f"nv{n_v}", L=10.0, ecut=5.0, grid=24, n_wells=n_wells,
+                                       well_seed=1, n_v=n_v))
+    dV = synth.perturbations(s.miller_rho, s.L, 3, 61)
+    ref = chi0.sos_drho(model_of(s), dV, [0.0])[:, :, 0]
+    for tcores in (1, 0):
+        ctx = setup(W, s, precision=W.WGW_MIXED, cg_tol=1e-11, tensor_cores=tcores)
+        drho, st, _ = W.wgw_apply_chi0(ctx, dV)
+        assert st["n_systems"] == 3 * n_v and st["n_converged"] == 3 * n_v
+        assert rel_err(drho[:, :, 0], ref) < 1e-8, tcores
+
+
 def test_complex_perturbation_by_linearity(W, tiny):
     dV = synth.perturbations(tiny.miller_rho, tiny.L, 3, 11, hermitian=False)
     ref = chi0.sos_drho(model_of(tiny), dV, [0.0])
