@@ -223,6 +223,17 @@ int wgw_pdep_davidson(wgw_ctx* ctx, int n_pdep, const double* x0, double* eig, d
                       wgw_stats* st);
 
 /*
+ * PDEP basis of a spin-polarised system: as wgw_pdep_davidson, for the spin-summed response
+ * chi0bar = sum_sigma chi0bar_sigma, with one context per spin channel (as for
+ * wgw_apply_channels).  Every block application runs the channels concurrently (the first on
+ * ctxs[0]'s stream, the others on their own) and sums them; the Davidson options (dav_tol,
+ * dav_max_iter, dav_factor, seed) and the Rayleigh-Ritz work are those of ctxs[0].
+ * Returns WGW_ERR_ARG as wgw_apply_channels does, otherwise as wgw_pdep_davidson.
+ */
+int wgw_pdep_davidson_channels(wgw_ctx* const* ctxs, int n_ctx, int n_pdep, const double* x0, double* eig,
+                               double* basis, wgw_stats* st);
+
+/*
  * Frequency dependence of chi0 in a basis by Lanczos chains (Sec. 3, the recurrence above
  * Eq. lanczos, and Eq. lanczos).  For every occupied state v and basis vector m, a chain on
  * P_c H P_c starts from b = P_c [phi~_m psi_v] (phi~ = v^1/2 phi), q^1 = b/|b|, beta_1 = |b|,

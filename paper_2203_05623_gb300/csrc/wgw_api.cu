@@ -858,12 +858,17 @@ int chi0_rb_shifted(wgw_ctx* c, const double* dvrb, int n_real, const std::vecto
   return solve_status;
 }
 
+// Float-float FP64-accuracy passes: the mixed path on the compiled grids.
+void set_ff(wgw_ctx* c) {
+  c->d.use_ff = c->opt.precision == WGW_MIXED && c->opt.fp64_emulation != 0 && ff_grid_supported(c->N);
+}
+
 // Core of chi0 / chibar0 application; dV and drho in device memory.
 int apply_core(wgw_ctx* c, const double* dV, int n_pert, const double* omega, int n_omega,
                double* drho, bool symmetrized, cudaStream_t st, wgw_stats* stats) {
   if (!c) return fail(WGW_ERR_ARG, "null context");
   // Float-float kernels exist for the compiled grid sizes only; other grids run native FP64.
-  c->d.use_ff = c->opt.precision == WGW_MIXED && c->opt.fp64_emulation != 0 && ff_grid_supported(c->N);
+  set_ff(c);
   if (n_pert < 0 || n_omega < 1 || !omega) return fail(WGW_ERR_ARG, "need n_pert >= 0 and n_omega >= 1");
   std::vector<int> k_zero, k_pos;
   std::vector<double> w_pos;
@@ -954,6 +959,7 @@ __global__ void k_start_block(int n, int nb, unsigned long long seed, const doub
 
 struct Davidson {
   wgw_ctx* c;
+  std::vector<wgw_ctx*> chans;   // further spin channels (chibar0 is the sum over c and these)
   cudaStream_t st;
   int nr;           // real-basis length of the density sphere
   long ld;
@@ -1032,8 +1038,35 @@ struct Davidson {
     k_scale_rows<<<g, 256, 0, st>>>(nr, nb, in, ld, vs_rb.as<double>(), dv, ld);
     WGW_CK(cudaGetLastError());
     wgw_stats s1{};
+    if (!chans.empty()) WGW_CK(cudaStreamSynchronize(st));   // dv is read on the channels' streams
+    // The further channels run on their own contexts and streams from their own host threads,
+    // concurrently with the first.
+    const size_t nch = chans.size();
+    std::vector<int> rcs(nch, WGW_OK);
+    std::vector<wgw_stats> ss(nch);
+    std::vector<std::string> errs(nch);
+    std::vector<std::thread> th;
+    for (size_t k = 0; k < nch; ++k)
+      th.emplace_back([&, k] {
+        wgw_ctx* ck = chans[k];
+        if (cudaSetDevice(ck->device) != cudaSuccess) { rcs[k] = WGW_ERR_CUDA; errs[k] = "cudaSetDevice"; return; }
+        std::lock_guard<std::recursive_mutex> lk(ck->mu);
+        set_ff(ck);
+        rcs[k] = chi0_rb(ck, dv, nb, ck->stream, &ss[k]);
+        if ((rcs[k] == WGW_OK || rcs[k] == WGW_ERR_NOCONV) && cudaStreamSynchronize(ck->stream) != cudaSuccess)
+          rcs[k] = WGW_ERR_CUDA;
+        errs[k] = g_last_error;
+      });
     const int rc = chi0_rb(c, dv, nb, st, &s1);
+    for (std::thread& t : th) t.join();
     if (rc != WGW_OK && rc != WGW_ERR_NOCONV) return rc;
+    for (size_t k = 0; k < nch; ++k) {
+      if (rcs[k] != WGW_OK && rcs[k] != WGW_ERR_NOCONV) return fail(rcs[k], errs[k].c_str());
+      WGW_CK(launch_axpby(nb, nr, 1.0, c->drho_rb.as<double>(), 1.0, chans[k]->drho_rb.as<double>(),
+                          c->drho_rb.as<double>(), ld, nullptr, st));
+      s1.n_systems += ss[k].n_systems;
+      s1.max_rel_residual = std::max(s1.max_rel_residual, ss[k].max_rel_residual);
+    }
     k_scale_rows<<<g, 256, 0, st>>>(nr, nb, c->drho_rb.as<double>(), ld, vs_rb.as<double>(), out, ld);
     WGW_CK(cudaGetLastError());
     acc->n_systems += s1.n_systems;
@@ -1042,9 +1075,12 @@ struct Davidson {
   }
 };
 
-int davidson_impl(wgw_ctx* c, int npd, const double* x0, double* eig, double* basis, wgw_stats* out_st) {
+int davidson_impl(wgw_ctx* c, int npd, const double* x0, double* eig, double* basis, wgw_stats* out_st,
+                  const std::vector<wgw_ctx*>& chans = {}) {
   Davidson D;
   D.c = c;
+  D.chans = chans;
+  set_ff(c);
   D.st = c->stream;
   D.nr = c->rho.nrb();
   D.ld = c->ld_r;
@@ -1191,7 +1227,7 @@ int lanczos_impl(wgw_ctx* c, const double* phi, int npd, int n_steps, const doub
   cudaStream_t st = c->stream;
   // FP64-accurate chains: float-float FFT passes on the mixed path (compiled grids), native FP64
   // otherwise.
-  c->d.use_ff = c->opt.precision == WGW_MIXED && c->opt.fp64_emulation != 0 && ff_grid_supported(c->N);
+  set_ff(c);
   const bool proj = g0 == nullptr;
   const int N = c->N, n_v = proj ? c->n_v : g0->n_states, n = c->wfc.nrb(), nr = c->rho.nrb();
   const long ldw = c->ld_w, ldr = c->ld_r;
@@ -1723,6 +1759,25 @@ int wgw_pdep_davidson(wgw_ctx* c, int n_pdep, const double* x0, double* eig, dou
   std::lock_guard<std::recursive_mutex> lk(c->mu);
   if (n_pdep > c->rho.nrb() / 2) return fail(WGW_ERR_ARG, "n_pdep too large for the density sphere");
   return davidson_impl(c, n_pdep, x0, eig, basis, st);
+}
+
+int wgw_pdep_davidson_channels(wgw_ctx* const* ctxs, int n_ctx, int n_pdep, const double* x0, double* eig,
+                               double* basis, wgw_stats* st) {
+  g_last_error.clear();
+  if (!ctxs || n_ctx < 1 || n_ctx > 8 || n_pdep < 1 || !eig)
+    return fail(WGW_ERR_ARG, "need 1..8 contexts, n_pdep >= 1 and eig");
+  for (int k = 0; k < n_ctx; ++k) {
+    if (!ctxs[k]) return fail(WGW_ERR_ARG, "null context");
+    for (int j = 0; j < k; ++j)
+      if (ctxs[j] == ctxs[k]) return fail(WGW_ERR_ARG, "a context is listed twice");
+    if (ctxs[k]->N != ctxs[0]->N || ctxs[k]->L != ctxs[0]->L || ctxs[k]->ecut != ctxs[0]->ecut)
+      return fail(WGW_ERR_ARG, "the channels differ in cell, cutoff or grid");
+  }
+  wgw_ctx* c = ctxs[0];
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  if (n_pdep > c->rho.nrb() / 2) return fail(WGW_ERR_ARG, "n_pdep too large for the density sphere");
+  const std::vector<wgw_ctx*> chans(ctxs + 1, ctxs + n_ctx);
+  return davidson_impl(c, n_pdep, x0, eig, basis, st, chans);
 }
 
 int wgw_dyson(int n, int n_omega, const double* chi0bar, double* chibar) {

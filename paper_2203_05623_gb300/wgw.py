@@ -103,6 +103,8 @@ def lib(path: str | None = None):
     L.wgw_poll.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Result)]
     L.wgw_wait.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(Result)]
     L.wgw_dyson.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp]
+    L.wgw_pdep_davidson_channels.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, _dp, _dp,
+                                             _dp, ctypes.POINTER(Stats)]
     L.wgw_apply_channels.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int,
                                      _dp, ctypes.c_int, _dp, ctypes.POINTER(Stats)]
     L.wgw_g0_lanczos.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
@@ -317,6 +319,22 @@ def wgw_pdep_davidson(ctx: Context, n_pdep: int, x0=None, want_basis=True, allow
                                 basis.view(np.float64).ctypes.data_as(_dp) if want_basis else None,
                                 ctypes.byref(st))
     _check(s, "wgw_pdep_davidson", (WGW_OK, WGW_ERR_NOCONV) if allow_noconv else (WGW_OK,))
+    return eig, (basis.T if want_basis else None), st.as_dict(), s
+
+
+def wgw_pdep_davidson_channels(ctxs, n_pdep: int, x0=None, want_basis=True, allow_noconv=False):
+    """PDEP eigenpairs of the spin-summed chibar0 (one context per channel); as wgw_pdep_davidson."""
+    ctxs = list(ctxs)
+    eig = np.zeros(n_pdep)
+    xb = _interleave(x0) if x0 is not None else None
+    basis = np.zeros((n_pdep, ctxs[0].n_rho), np.complex128) if want_basis else None
+    st = Stats()
+    handles = (ctypes.c_void_p * len(ctxs))(*[c.handle for c in ctxs])
+    s = lib().wgw_pdep_davidson_channels(handles, len(ctxs), n_pdep, xb.ctypes.data_as(_dp) if xb is not None else None,
+                                         eig.ctypes.data_as(_dp),
+                                         basis.view(np.float64).ctypes.data_as(_dp) if want_basis else None,
+                                         ctypes.byref(st))
+    _check(s, "wgw_pdep_davidson_channels", (WGW_OK, WGW_ERR_NOCONV) if allow_noconv else (WGW_OK,))
     return eig, (basis.T if want_basis else None), st.as_dict(), s
 
 

@@ -95,3 +95,21 @@ def test_kb_with_d_channels_matches_oracle(W, precision):
     ref = chi0.sos_drho(model_of(s), dV, [0.0, 0.8])
     out, st, _ = W.wgw_apply_chi0(setup(W, s, precision, 2.0), dV, [0.0, 0.8])
     assert rel(out, ref) < (1e-10 if precision == "fp64" else 1e-8)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_spin_summed_davidson_matches_dense(W, spin24, precision):
+    """PDEP eigenvalues of the spin-summed chibar0 against a dense diagonalisation of the
+    oracle's sum of the two channels' chibar0 matrices."""
+    up, dn = spin24
+    X = sum(chi0.chibar0_matrix(model_of(c, f_s=1.0), 0.0) for c in (up, dn))
+    w_ref = np.linalg.eigvalsh(0.5 * (X + X.conj().T))[:6]
+    opt = dict(precision=W.WGW_FP64, cg_tol=1e-13, dav_tol=1e-12, f_s=1.0) if precision == "fp64" else \
+        dict(precision=W.WGW_MIXED, cg_tol=1e-11, dav_tol=1e-11, f_s=1.0)
+    ctxs = [W.wgw_setup(c.L, c.ecut, c.grid, c.vloc_G, c.psi_v, c.e_v, W.wgw_default_options(**opt))
+            for c in (up, dn)]
+    x0 = synth.perturbations(up.miller_rho, up.L, 6, 55)
+    eig, basis, st, _ = W.wgw_pdep_davidson_channels(ctxs, 6, x0)
+    assert st["n_converged"] == 6
+    assert np.max(np.abs(eig - w_ref) / np.abs(w_ref)) < (1e-10 if precision == "fp64" else 1e-8)
+    assert np.max(np.abs(basis.conj().T @ basis - np.eye(6))) < 1e-10
