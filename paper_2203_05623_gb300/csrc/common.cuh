@@ -80,11 +80,24 @@ WGW_HD ff operator+(ff a, ff b) {
 }
 WGW_HD ff operator-(ff a) { return ff(-a.hi, -a.lo); }
 WGW_HD ff operator-(ff a, ff b) { return a + (-b); }
+// The product is left unnormalised too (|lo| is within a few ulp(hi)); its error is about 2^-46
+// of |a b| plus the norm-wise error the unnormalised operands carry.
 WGW_HD ff operator*(ff a, ff b) {
   const float p = ffm(a.hi, b.hi);
   float e = fff(a.hi, b.hi, -p);            // exact low part of a.hi * b.hi
   e = fff(a.hi, b.lo, fff(a.lo, b.hi, e));
-  return fast_two_sum(p, e);
+  return ff(p, e);
+}
+// a b + c d: both leading products with their exact low parts, one TwoSum (unnormalised, as the
+// sum); 16 FP32 operations instead of the 22 of two products and a sum.
+WGW_HD ff ff_dot2(ff a, ff b, ff c, ff d) {
+  const float p = ffm(a.hi, b.hi), q = ffm(c.hi, d.hi);
+  float e = fff(a.hi, b.hi, -p);
+  float f = fff(c.hi, d.hi, -q);
+  e = fff(a.hi, b.lo, fff(a.lo, b.hi, e));
+  f = fff(c.hi, d.lo, fff(c.lo, d.hi, f));
+  const ff s = two_sum(p, q);
+  return ff(s.hi, ffa(s.lo, ffa(e, f)));
 }
 WGW_HD ff& operator+=(ff& a, ff b) { a = a + b; return a; }
 WGW_HD ff& operator*=(ff& a, ff b) { a = a * b; return a; }
@@ -121,6 +134,10 @@ WGW_HD cplx<T> operator-(cplx<T> a, cplx<T> b) { return mk<T>(a.re - b.re, a.im 
 template <typename T>
 WGW_HD cplx<T> cmul(cplx<T> a, cplx<T> b) {
   return mk<T>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <>
+WGW_HD cplx<ff> cmul<ff>(cplx<ff> a, cplx<ff> b) {
+  return mk<ff>(ff_dot2(a.re, b.re, -a.im, b.im), ff_dot2(a.re, b.im, a.im, b.re));
 }
 template <typename T>
 WGW_HD cplx<T> cscale(cplx<T> a, T s) { return mk<T>(a.re * s, a.im * s); }
