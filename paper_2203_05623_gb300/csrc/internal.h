@@ -85,22 +85,24 @@ cudaError_t launch_drho_xline(int m, FftCtx<T> f, const cplx<T>* Tbuf, const T* 
 // tc_tiles: for T = float, the tensor-core kernels (tc_kernels.cu) with Psi pre-split into these
 // tiles (launch_tc_tile_psi); null selects the CUDA-core GEMMs.
 // psi_ff: with ffc, Psi as float-float pairs in 8-byte slots (no per-load conversion), or null.
+// tc_err: device int the tensor-core kernels set when a wait times out (required with tc_tiles).
 template <typename T>
 cudaError_t launch_pc(T* Y, long ldy, int n_sys, const int* list, const T* Psi, long ldp, int n, int nv,
                       const int* active, T* work, cudaStream_t st, bool ffc = false,
-                      const unsigned char* tc_tiles = nullptr, const T* psi_ff = nullptr);
+                      const unsigned char* tc_tiles = nullptr, const T* psi_ff = nullptr, int* tc_err = nullptr);
 // P_c on the tensor cores (3xTF32 products, FP32 accumulation in tensor memory); work holds
-// tc_pc_work_elems(n, n_sys, nv) floats; tiles from launch_tc_tile_psi.
+// tc_pc_work_elems(n, n_sys, nv) floats; tiles from launch_tc_tile_psi; *err (device) is set to 1
+// when a wait on an MMA or copy barrier times out.
 cudaError_t launch_pc_tc(float* Y, long ldy, int n_sys, const int* list, const unsigned char* tiles, int n, int nv,
-                         const int* active, float* work, cudaStream_t st);
+                         const int* active, float* work, cudaStream_t st, int* err);
 size_t tc_pc_work_elems(int n, int n_sys, int nv);
 bool tc_pc_supported(int nv);
 // Psi (n x nv, column v at Psi + v ldp) split into TF32 hi/lo parts and laid out as the operand
 // tiles of both phases; tc_psi_tile_bytes(n, nv) bytes.
 size_t tc_psi_tile_bytes(int n, int nv);
 cudaError_t launch_tc_tile_psi(const float* Psi, long ldp, int n, int nv, unsigned char* tiles, cudaStream_t st);
-// Reads (and clears) the tensor-core kernels' wait-timeout flag; synchronises st.
-cudaError_t tc_error_read_and_clear(int* flag, cudaStream_t st);
+// Reads (and clears) a tensor-core wait-timeout flag (device int dev_flag); synchronises st.
+cudaError_t tc_error_read_and_clear(int* flag, int* dev_flag, cudaStream_t st);
 // C = A^T B: A is K x m (column j at A + j*lda), B is K x n (column j at B + c_j * ldb with
 // c_j = cols[j], or j when cols is null); C is written row-major with rows of length n, padded
 // to a multiple of 64 rows.  work: gemm_tn_work_elems(K, m, n) doubles.  ffc: float-float

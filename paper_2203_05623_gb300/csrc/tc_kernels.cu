@@ -11,7 +11,7 @@
 // canonical K-major layout without swizzle: 8-row x 16-byte core matrices, adjacent in K at
 // 128 bytes (leading byte offset) and adjacent in M/N at 1024 bytes (stride byte offset) for
 // K chunks of 32 elements.  One thread issues the MMAs and commits them to an mbarrier; every
-// wait on that mbarrier is bounded and reports a timeout through g_tc_error.
+// wait on that mbarrier is bounded and reports a timeout through the caller's error flag.
 #include <algorithm>
 #include <cstdint>
 
@@ -19,7 +19,6 @@
 
 namespace wgw {
 
-__device__ int g_tc_error = 0;
 
 namespace tc {
 
@@ -86,13 +85,13 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Bounded wait (about one second of wall time) for the completion of phase `parity`; false,
-// with g_tc_error set, on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+// with *err set, on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, int* err) {
   if (mbar_test(mbar, parity)) return true;
   const unsigned long long t0 = global_ns();
   while (!mbar_test(mbar, parity))
     if (global_ns() - t0 > kWaitNs) {
-      atomicExch(&g_tc_error, 1);
+      atomicExch(err, 1);
       return false;
     }
   return true;
@@ -235,7 +234,7 @@ __global__ void k_tc_tile_psi(const float* __restrict__ Psi, long ldp, int n, in
 __global__ void __launch_bounds__(kThreads) k_tc_pc1(const unsigned char* __restrict__ t1, const float* __restrict__ Y,
                                                      long ldy, int n, int nv, int n_list,
                                                      const int* __restrict__ list, int kcpb, int Nn, int ldc,
-                                                     float* __restrict__ Cpart) {
+                                                     float* __restrict__ Cpart, int* err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int j0 = blockIdx.x * kRowsA, kb = blockIdx.y;
@@ -292,7 +291,7 @@ __global__ void __launch_bounds__(kThreads) k_tc_pc1(const unsigned char* __rest
   for (int c = 0; c < nc; ++c) {
     const int st = c & 1;
     if (tid == 0) {
-      ok = ok && mbar_wait(smem_u32(bars + st), (c >> 1) & 1);   // B of chunk c landed
+      ok = ok && mbar_wait(smem_u32(bars + st), (c >> 1) & 1, err);   // B of chunk c landed
       if (ok) {
         fence_after();
         unsigned char* base = smem + st * stage_bytes;
@@ -305,7 +304,7 @@ __global__ void __launch_bounds__(kThreads) k_tc_pc1(const unsigned char* __rest
       load_a(kc_lo + c + 1);                 // global loads in flight while the MMAs run
       const int s1 = (c + 1) & 1;
       if (c >= 1) {                          // stage s1 was read by the MMAs of chunk c - 1
-        const bool w = mbar_wait(smem_u32(bars + 2 + s1), ((c - 1) >> 1) & 1);
+        const bool w = mbar_wait(smem_u32(bars + 2 + s1), ((c - 1) >> 1) & 1, err);
         ok = ok && w;
       }
       ok = __syncthreads_and(ok) != 0;
@@ -316,7 +315,7 @@ __global__ void __launch_bounds__(kThreads) k_tc_pc1(const unsigned char* __rest
     }
   }
   if (nc > 0) {
-    const bool w = ok && mbar_wait(smem_u32(bars + 2 + ((nc - 1) & 1)), ((nc - 1) >> 1) & 1);
+    const bool w = ok && mbar_wait(smem_u32(bars + 2 + ((nc - 1) & 1)), ((nc - 1) >> 1) & 1, err);
     ok = __syncthreads_and(w) != 0;
   }
   fence_after();
@@ -386,7 +385,7 @@ __global__ void __launch_bounds__(kThreads2, 2) k_tc_pc2(const unsigned char* __
                                                       const unsigned char* __restrict__ ct, float* __restrict__ Y,
                                                       long ldy, int n, int nvc, int n_list,
                                                       const int* __restrict__ list, float alpha, float beta,
-                                                      const int* __restrict__ active) {
+                                                      const int* __restrict__ active, int* err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int rt = blockIdx.x, jt = blockIdx.y;
@@ -422,13 +421,13 @@ __global__ void __launch_bounds__(kThreads2, 2) k_tc_pc2(const unsigned char* __
   bool ok = true;
   if (tid == 0) {
     for (int vc = 0; vc < nvc && ok; ++vc) {
-      if (vc > 0) ok = mbar_wait(smem_u32(bars + 1), (vc - 1) & 1);   // previous MMAs read the stage
+      if (vc > 0) ok = mbar_wait(smem_u32(bars + 1), (vc - 1) & 1, err);   // previous MMAs read the stage
       if (!ok) break;
       const uint32_t fb = smem_u32(bars);
       mbar_expect_tx(fb, 4 * kTile);
       bulk_g2s(smem_u32(smem), t2 + (static_cast<size_t>(rt) * nvc + vc) * 2 * kTile, 2 * kTile, fb);
       bulk_g2s(smem_u32(smem + 2 * kTile), ct + (static_cast<size_t>(jt) * nvc + vc) * 2 * kTile, 2 * kTile, fb);
-      ok = mbar_wait(fb, vc & 1);
+      ok = mbar_wait(fb, vc & 1, err);
       if (!ok) break;
       fence_after();
       issue_chunk(tmem, smem_u32(smem), smem_u32(smem + kTile), smem_u32(smem + 2 * kTile),
@@ -438,7 +437,7 @@ __global__ void __launch_bounds__(kThreads2, 2) k_tc_pc2(const unsigned char* __
   }
   ok = __syncthreads_and(ok) != 0;
   if (ok && nvc > 0) {
-    const bool w = mbar_wait(smem_u32(bars + 1), (nvc - 1) & 1);
+    const bool w = mbar_wait(smem_u32(bars + 1), (nvc - 1) & 1, err);
     ok = __syncthreads_and(w) != 0;
   }
   fence_after();
@@ -522,9 +521,9 @@ size_t tc_pc_work_elems(int n, int n_sys, int nv) {
 bool tc_pc_supported(int nv) { return nv >= 1 && nv <= 256; }
 
 cudaError_t launch_pc_tc(float* Y, long ldy, int n_sys, const int* list, const unsigned char* tiles, int n, int nv,
-                         const int* active, float* work, cudaStream_t st) {
+                         const int* active, float* work, cudaStream_t st, int* err) {
   if (n_sys == 0 || nv == 0) return cudaSuccess;
-  if (!tc_pc_supported(nv)) return cudaErrorInvalidValue;
+  if (!tc_pc_supported(nv) || !err) return cudaErrorInvalidValue;
   const TcGeom g = tc_geom(n, n_sys, nv);
   const unsigned char* t1 = tiles;
   const unsigned char* t2 = tiles + static_cast<size_t>(g.nkc) * 2 * g.Nn * 128;
@@ -535,7 +534,7 @@ cudaError_t launch_pc_tc(float* Y, long ldy, int n_sys, const int* list, const u
                                        static_cast<int>(smem1));
   if (e != cudaSuccess) return e;
   tc::k_tc_pc1<<<dim3(g.njt, g.n_kb), tc::kThreads, smem1, st>>>(t1, Y, ldy, n, nv, n_sys, list, g.kcpb, g.Nn,
-                                                                 g.ldc, Cpart);
+                                                                 g.ldc, Cpart, err);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long total = static_cast<long>(g.njt) * tc::kRowsA * g.nvc * tc::kKC;
@@ -547,19 +546,16 @@ cudaError_t launch_pc_tc(float* Y, long ldy, int n_sys, const int* list, const u
   e = cudaFuncSetAttribute(tc::k_tc_pc2, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem2));
   if (e != cudaSuccess) return e;
   tc::k_tc_pc2<<<dim3(g.nrt, g.njt), tc::kThreads2, smem2, st>>>(t2, ct, Y, ldy, n, g.nvc, n_sys, list, -1.f, 1.f,
-                                                                active);
+                                                                active, err);
   return cudaGetLastError();
 }
 
-cudaError_t tc_error_read_and_clear(int* flag, cudaStream_t st) {
-  cudaError_t e = cudaMemcpyFromSymbolAsync(flag, g_tc_error, sizeof(int), 0, cudaMemcpyDeviceToHost, st);
+cudaError_t tc_error_read_and_clear(int* flag, int* dev_flag, cudaStream_t st) {
+  cudaError_t e = cudaMemcpyAsync(flag, dev_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return e;
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return e;
-  if (*flag) {
-    const int zero = 0;
-    e = cudaMemcpyToSymbolAsync(g_tc_error, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st);
-  }
+  if (*flag) e = cudaMemsetAsync(dev_flag, 0, sizeof(int), st);
   return e;
 }
 

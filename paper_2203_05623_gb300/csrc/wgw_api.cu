@@ -212,7 +212,7 @@ struct wgw_ctx {
   // apply work space (double unless noted)
   DevBuf dvin, dv_rb, dv_r, Trho, Dr, drho_rb, eps, a_idx, b_idx, brow, cg_rz, cg_bb, cg_rr,
       cg_act, cg_it, cnt, rr64, act64, norms, pc_work, sys_list, list64, cg_rzi, omg, row_list, rowact,
-      drho_all, psi_tc, cg_best, cg_itbest, lz_q, lz_qf;
+      drho_all, psi_tc, cg_best, cg_itbest, lz_q, lz_qf, tc_err;
   cudaStream_t stream = nullptr;
   Prof prof;
   std::vector<int> last_iters;      // per system of the last apply: CG iterations (all refinements)
@@ -251,7 +251,7 @@ struct wgw_ctx {
     d.release(); f.release(); wfc.release(); rho.release();
     DevBuf* all[] = {&e_v_d, &dvin, &dv_rb, &dv_r, &Trho, &Dr, &drho_rb, &eps, &a_idx, &b_idx, &brow,
                      &cg_rz, &cg_bb, &cg_rr, &cg_act, &cg_it, &cnt, &rr64, &act64, &norms, &pc_work, &sys_list, &list64, &cg_rzi, &omg,
-                     &row_list, &rowact, &drho_all, &psi_tc, &cg_best, &cg_itbest, &lz_q, &lz_qf};
+                     &row_list, &rowact, &drho_all, &psi_tc, &cg_best, &cg_itbest, &lz_q, &lz_qf, &tc_err};
     for (DevBuf* b : all) b->release();
     if (stream) cudaStreamDestroy(stream);
   }
@@ -294,9 +294,11 @@ int run_pc(wgw_ctx* c, T* Y, int n_list, const int* list, const T* Psi, const in
   WGW_TRY(c->pc_work.ensure(sizeof(T) * std::max(pc_work_elems((int)n, n_list, std::max(c->n_v, c->n_proj)),
                                                  tc_pc_work_elems((int)n, n_list, c->n_v))));
   T* work = c->pc_work.as<T>();
-  if (tcores && !c->psi_tc.p) {   // operand tiles of the occupied block, once per context
+  if (tcores && !c->psi_tc.p) {   // operand tiles of the occupied block and the wait flag, once per context
     WGW_TRY(c->psi_tc.ensure(tc_psi_tile_bytes((int)n, c->n_v)));
     WGW_CK(launch_tc_tile_psi(c->f.psi.as<float>(), c->ld_w, (int)n, c->n_v, c->psi_tc.as<unsigned char>(), st));
+    WGW_TRY(c->tc_err.ensure(sizeof(int)));
+    WGW_CK(cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), st));
   }
   const unsigned char* tiles = tcores ? c->psi_tc.as<unsigned char>() : nullptr;
   WGW_CK(c->prof.run(PK_PC, 2.0 * n_list * n * sizeof(T) + n * nv * sizeof(T), 4.0 * n * nv * n_list, st, [&] {
@@ -304,7 +306,7 @@ int run_pc(wgw_ctx* c, T* Y, int n_list, const int* list, const T* Psi, const in
     const T* psi_ff = (ffc && Psi == reinterpret_cast<const T*>(c->d.psi.p)) ? reinterpret_cast<const T*>(c->d.psi_ff.p)
                                                                              : nullptr;
     return launch_pc<T>(Y, c->ld_w, n_list, list, Psi, c->ld_w, (int)n, c->n_v, active, work, st, ffc, tiles,
-                        psi_ff); }));
+                        psi_ff, tcores ? c->tc_err.as<int>() : nullptr); }));
   return WGW_OK;
 }
 
@@ -411,9 +413,9 @@ int cg_solve(wgw_ctx* c, Prec<T>& pr, int n_sys, double tol, int max_iter, cudaS
       WGW_TRY(build_list(c, act, n_sys, lbuf, st, &n_list));
     }
   }
-  if (sizeof(T) == sizeof(float) && c->opt.tensor_cores) {
+  if (sizeof(T) == sizeof(float) && c->tc_err.p) {
     int flag = 0;
-    WGW_CK(tc_error_read_and_clear(&flag, st));
+    WGW_CK(tc_error_read_and_clear(&flag, c->tc_err.as<int>(), st));
     if (flag) return fail(WGW_ERR_TIMEOUT, "tensor-core P_c: a wait on the MMA completion barrier timed out");
   }
   return WGW_OK;
