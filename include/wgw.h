@@ -302,6 +302,16 @@ int wgw_g0_lanczos(wgw_ctx* ctx, const double* phi, int n_pdep, const int* state
                    double* g0, wgw_stats* st);
 
 /*
+ * Failure-detection self-test (no counterpart in the paper).  Every wait of the library's
+ * kernels on a device barrier is bounded to about one second of wall time, after which the
+ * kernel sets an error flag, releases what it holds and returns; the host turns the flag into
+ * WGW_ERR_TIMEOUT.  This call runs one such wait on a barrier that nothing completes, on the
+ * current device, and stores the flag the kernel left (1: the wait gave up as designed) in
+ * *timed_out.  Takes about one second; the device stays usable.
+ */
+int wgw_selftest_wait_timeout(int* timed_out);
+
+/*
  * Dyson equation in a basis (Sec. 2: the screened response from the independent-particle one,
  * epsilon^-1 - 1 = (1 - chibar0)^-1 chibar0 for the symmetrised responses), for every frequency
  * of a batch, in FP64 on the GPU (Gaussian elimination with partial pivoting, one CTA per

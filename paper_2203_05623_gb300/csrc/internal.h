@@ -101,6 +101,8 @@ bool tc_pc_supported(int nv);
 // tiles of both phases; tc_psi_tile_bytes(n, nv) bytes.
 size_t tc_psi_tile_bytes(int n, int nv);
 cudaError_t launch_tc_tile_psi(const float* Psi, long ldp, int n, int nv, unsigned char* tiles, cudaStream_t st);
+// One bounded mbarrier wait that nothing completes: sets *dev_flag after about one second.
+cudaError_t tc_wait_selftest(int* dev_flag, cudaStream_t st);
 // Reads (and clears) a tensor-core wait-timeout flag (device int dev_flag); synchronises st.
 cudaError_t tc_error_read_and_clear(int* flag, int* dev_flag, cudaStream_t st);
 // C = A^T B: A is K x m (column j at A + j*lda), B is K x n (column j at B + c_j * ldb with

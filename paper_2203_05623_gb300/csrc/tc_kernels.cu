@@ -472,6 +472,16 @@ __global__ void __launch_bounds__(kThreads2, 2) k_tc_pc2(const unsigned char* __
   if (warp == 0) tmem_dealloc(tmem, ncols);
 }
 
+// Self-test of the bounded wait: one thread waits on a fresh mbarrier that nothing arrives on;
+// after about one second the wait gives up, sets *err and the kernel returns normally.
+__global__ void k_tc_wait_selftest(int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(smem_u32(&bar), 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  mbar_wait(smem_u32(&bar), 0, err);
+}
+
 }  // namespace tc
 
 namespace {
@@ -547,6 +557,11 @@ cudaError_t launch_pc_tc(float* Y, long ldy, int n_sys, const int* list, const u
   if (e != cudaSuccess) return e;
   tc::k_tc_pc2<<<dim3(g.nrt, g.njt), tc::kThreads2, smem2, st>>>(t2, ct, Y, ldy, n, g.nvc, n_sys, list, -1.f, 1.f,
                                                                 active, err);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_wait_selftest(int* dev_flag, cudaStream_t st) {
+  tc::k_tc_wait_selftest<<<1, 32, 0, st>>>(dev_flag);
   return cudaGetLastError();
 }
 

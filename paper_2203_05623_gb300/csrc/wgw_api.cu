@@ -1782,6 +1782,17 @@ int wgw_pdep_davidson_channels(wgw_ctx* const* ctxs, int n_ctx, int n_pdep, cons
   return davidson_impl(c, n_pdep, x0, eig, basis, st, chans);
 }
 
+int wgw_selftest_wait_timeout(int* timed_out) {
+  g_last_error.clear();
+  if (!timed_out) return fail(WGW_ERR_ARG, "null argument");
+  DevBuf flag;
+  WGW_TRY(flag.ensure(sizeof(int)));
+  WGW_CK(cudaMemset(flag.p, 0, sizeof(int)));
+  WGW_CK(tc_wait_selftest(flag.as<int>(), nullptr));
+  WGW_CK(cudaMemcpy(timed_out, flag.p, sizeof(int), cudaMemcpyDeviceToHost));
+  return WGW_OK;
+}
+
 int wgw_dyson(int n, int n_omega, const double* chi0bar, double* chibar) {
   g_last_error.clear();
   if (n < 1 || n > 4096 || n_omega < 0) return fail(WGW_ERR_ARG, "need 1 <= n <= 4096 and n_omega >= 0");

@@ -105,6 +105,7 @@ def lib(path: str | None = None):
     L.wgw_dyson.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp]
     L.wgw_pdep_davidson_channels.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, _dp, _dp,
                                              _dp, ctypes.POINTER(Stats)]
+    L.wgw_selftest_wait_timeout.argtypes = [ctypes.POINTER(ctypes.c_int)]
     L.wgw_apply_channels.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int,
                                      _dp, ctypes.c_int, _dp, ctypes.POINTER(Stats)]
     L.wgw_g0_lanczos.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
@@ -233,6 +234,13 @@ def wgw_apply_channels(ctxs, dV, omega=(0.0,), symmetrized=False, allow_noconv=F
                                  ctypes.byref(st))
     _check(s, "wgw_apply_channels", (WGW_OK, WGW_ERR_NOCONV) if allow_noconv else (WGW_OK,))
     return out.transpose(2, 1, 0), st.as_dict(), s
+
+
+def wgw_selftest_wait_timeout() -> int:
+    """Runs one bounded device wait that nothing completes; returns the flag it left (1 = gave up)."""
+    t = ctypes.c_int(0)
+    _check(lib().wgw_selftest_wait_timeout(ctypes.byref(t)), "wgw_selftest_wait_timeout")
+    return t.value
 
 
 class Ticket:
