@@ -376,6 +376,89 @@ def run_serve(args, wl):
     W.wgw_destroy(ctx)
 
 
+def library_baselines(W, ctx, s, prof_all):
+    """The library's FP32 kernels against cuFFT and cuBLAS on the same shapes (untimed by the
+    bench line; CUDA events around each variant, after warm-up).
+
+    H psi for 1024 real-in-r wavefunctions (512 packed pairs) of the 48^3 model: the library's
+    pruned FFT pipeline (wgw_apply_h_dev, FP32, including its sphere <-> real-basis conversions)
+    against scatter + torch.fft.ifftn + V(r) + torch.fft.fftn + gather + kinetic term on the full
+    complex64 grid (cuFFT).  P_c of 4096 FP32 systems against the 64 occupied states: the
+    library's per-system time from the untimed profiled step against torch.matmul (cuBLAS) for
+    C = Psi^T X, X -= Psi C in FP32 and in TF32."""
+    import numpy as np
+    import torch
+    import synth
+
+    def timed(fn, reps=5):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+
+    n_psi, N = 1024, s.grid
+    x = synth.perturbations(s.miller_wfc, s.L, n_psi, 73)
+    xd = torch.from_numpy(np.ascontiguousarray(x.T)).cuda()
+    outd = torch.empty_like(xd)
+    ours_h = timed(lambda: W.wgw_apply_h_dev(ctx, xd, outd, fp32=True))
+    mw = np.asarray(s.miller_wfc) % N
+    idx = torch.from_numpy((mw[:, 0] * N + mw[:, 1]) * N + mw[:, 2]).cuda()
+    b = 2.0 * np.pi / s.L
+    kin = torch.from_numpy(0.5 * b * b * np.sum(np.asarray(s.miller_wfc, np.float64) ** 2, axis=1)).float().cuda()
+    Xp = (xd[0::2] + 1j * xd[1::2]).to(torch.complex64)          # packed pairs: psi_a + i psi_b
+    grid = torch.zeros((n_psi // 2, N ** 3), dtype=torch.complex64, device="cuda")
+    vr = torch.rand((N, N, N), device="cuda")
+
+    def cufft_h():
+        grid.zero_()
+        grid[:, idx] = Xp
+        r = torch.fft.ifftn(grid.view(-1, N, N, N), dim=(1, 2, 3))
+        r.mul_(vr)
+        f = torch.fft.fftn(r, dim=(1, 2, 3)).view(n_psi // 2, -1)
+        return f[:, idx] + kin * Xp
+
+    def cufft_only():
+        r = torch.fft.ifftn(grid.view(-1, N, N, N), dim=(1, 2, 3))
+        return torch.fft.fftn(r, dim=(1, 2, 3))
+
+    cu_h = timed(cufft_h)
+    cu_fft = timed(cufft_only)
+    del grid
+    # P_c GEMMs.
+    n, nv, n_sys = 2 * (s.miller_wfc.shape[0] // 2) + 1, s.psi_v.shape[1], 4096
+    psi = torch.randn((n, nv), device="cuda")
+    X = torch.randn((n, n_sys), device="cuda")
+
+    def pc():
+        C = psi.t() @ X
+        return X - psi @ C
+
+    old = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    cu_pc32 = timed(pc)
+    torch.backends.cuda.matmul.allow_tf32 = True
+    cu_pc_tf32 = timed(pc)
+    torch.backends.cuda.matmul.allow_tf32 = old
+    d = prof_all.get("pc_project", {"ms": 0.0, "launches": 0, "bytes": 0.0})
+    # Algorithmic bytes per pc_project launch: 2 n_list n 4 + n nv 4.
+    sys_done = (d["bytes"] - d["launches"] * n * nv * 4.0) / (8.0 * n)
+    ours_pc = d["ms"] / sys_done * n_sys if sys_done > 0 else None
+    return {"h_psi_1024_wavefunctions_ms": {"library_fp32": ours_h, "cufft_complex64": cu_h,
+                                            "cufft_fft_pair_only": cu_fft},
+            "pc_4096_systems_ms": {"library_tcgen05_3xtf32": ours_pc, "cublas_fp32": cu_pc32,
+                                   "cublas_tf32": cu_pc_tf32},
+            "what": "same shapes on the same GPU; library P_c per 4096 systems from the profiled step's "
+                    "pc_project class (lists of varying length), cuBLAS as one call on 4096 systems"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -384,6 +467,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="pdep_L16_48", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-library-baselines", action="store_true",
+                    help="skip the cuFFT / cuBLAS comparison on the same shapes")
     ap.add_argument("--n-pert", type=int, default=0,
                     help="perturbations per rank (default: the workload's); smaller values serve profiling")
     ap.add_argument("--fp64-emulation", type=int, default=1, choices=[0, 1],
@@ -564,6 +649,8 @@ def main():
     }
     if cpu:
         line["cpu_baseline"] = cpu
+    if world == 1 and args.precision == "mixed" and not args.no_library_baselines:
+        line["library_baseline"] = library_baselines(W, ctx, s, prof_all)
     if rank == 0:
         print(json.dumps(line), flush=True)
     W.wgw_destroy(ctx)

@@ -302,6 +302,17 @@ int wgw_g0_lanczos(wgw_ctx* ctx, const double* phi, int n_pdep, const int* state
                    double* g0, wgw_stats* st);
 
 /*
+ * Kohn-Sham Hamiltonian on wavefunctions (Sec. 4.1: kinetic term on the sphere, V_loc by FFT to
+ * the real-space grid and back, KB projectors): out = H psi for n_psi wavefunctions that are
+ * real in r, on device memory, work enqueued on `stream` (as for wgw_apply_chi0_dev).
+ *   psi_dev, out_dev  N_pw x n_psi complex, wavefunction-sphere canonical order (psi_v layout of
+ *                     wgw_setup); only the real-in-r part of psi is used.
+ *   fp32     1: the FP32 kernels of the inner CG (mixed-precision context only); 0: FP64
+ *            accuracy (float-float on a mixed context with fp64_emulation, else native FP64).
+ */
+int wgw_apply_h_dev(wgw_ctx* ctx, const double* psi_dev, int n_psi, double* out_dev, int fp32, void* stream);
+
+/*
  * Failure-detection self-test (no counterpart in the paper).  Every wait of the library's
  * kernels on a device barrier is bounded to about one second of wall time, after which the
  * kernel sets an error flag, releases what it holds and returns; the host turns the flag into

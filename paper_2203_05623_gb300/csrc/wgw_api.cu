@@ -1782,6 +1782,35 @@ int wgw_pdep_davidson_channels(wgw_ctx* const* ctxs, int n_ctx, int n_pdep, cons
   return davidson_impl(c, n_pdep, x0, eig, basis, st, chans);
 }
 
+int wgw_apply_h_dev(wgw_ctx* c, const double* psi_dev, int n_psi, double* out_dev, int fp32, void* stream) {
+  g_last_error.clear();
+  if (!c || n_psi < 0 || (n_psi > 0 && (!psi_dev || !out_dev))) return fail(WGW_ERR_ARG, "bad argument");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  if (n_psi == 0) return WGW_OK;
+  if (fp32 && c->opt.precision != WGW_MIXED)
+    return fail(WGW_ERR_ARG, "the FP32 H needs a mixed-precision context (it holds the FP32 copies)");
+  cudaStream_t st = (cudaStream_t)stream;
+  set_ff(c);
+  WGW_TRY(ensure_work(c, n_psi, 1));
+  const int n = c->wfc.nrb();
+  const long ld = c->ld_w;
+  double* P = c->d.P.as<double>();
+  double* Q = c->d.Q.as<double>();
+  WGW_CK(cudaMemsetAsync(P, 0, sizeof(double) * (size_t)n_psi * ld, st));
+  WGW_CK(launch_sphere_to_rb(n_psi, psi_dev, 2L * c->wfc.n, nullptr, c->wfc.map(), 0, P, ld, st));
+  if (fp32) {
+    WGW_CK(cudaMemsetAsync(c->f.shift.p, 0, sizeof(float) * n_psi, st));
+    WGW_CK((launch_copy_cast<double, float>(n_psi, n, P, ld, c->f.P.as<float>(), ld, nullptr, st)));
+    WGW_TRY(apply_A<float>(c, c->f, c->f.P.as<float>(), c->f.Q.as<float>(), n_psi, nullptr, nullptr, st, false));
+    WGW_CK((launch_copy_cast<float, double>(n_psi, n, c->f.Q.as<float>(), ld, Q, ld, nullptr, st)));
+  } else {
+    WGW_CK(cudaMemsetAsync(c->d.shift.p, 0, sizeof(double) * n_psi, st));
+    WGW_TRY(apply_A<double>(c, c->d, P, Q, n_psi, nullptr, nullptr, st, false));
+  }
+  WGW_CK(launch_rb_to_sphere(n_psi, Q, ld, nullptr, nullptr, c->wfc.map(), out_dev, 2L * c->wfc.n, st));
+  return WGW_OK;
+}
+
 int wgw_selftest_wait_timeout(int* timed_out) {
   g_last_error.clear();
   if (!timed_out) return fail(WGW_ERR_ARG, "null argument");

@@ -105,6 +105,8 @@ def lib(path: str | None = None):
     L.wgw_dyson.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp]
     L.wgw_pdep_davidson_channels.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, _dp, _dp,
                                              _dp, ctypes.POINTER(Stats)]
+    L.wgw_apply_h_dev.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                  ctypes.c_void_p]
     L.wgw_selftest_wait_timeout.argtypes = [ctypes.POINTER(ctypes.c_int)]
     L.wgw_apply_channels.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int,
                                      _dp, ctypes.c_int, _dp, ctypes.POINTER(Stats)]
@@ -234,6 +236,22 @@ def wgw_apply_channels(ctxs, dV, omega=(0.0,), symmetrized=False, allow_noconv=F
                                  ctypes.byref(st))
     _check(s, "wgw_apply_channels", (WGW_OK, WGW_ERR_NOCONV) if allow_noconv else (WGW_OK,))
     return out.transpose(2, 1, 0), st.as_dict(), s
+
+
+def wgw_apply_h_dev(ctx: Context, psi_dev, out_dev=None, fp32=False, stream=None):
+    """H psi on device: psi_dev a torch complex128 tensor (n_psi, N_pw) (row = one wavefunction,
+    canonical order); returns out_dev of the same shape."""
+    import torch
+    assert psi_dev.is_cuda and psi_dev.dtype == torch.complex128 and psi_dev.is_contiguous()
+    n_psi = psi_dev.shape[0]
+    if out_dev is None:
+        out_dev = torch.empty_like(psi_dev)
+    if stream is None:
+        stream = torch.cuda.current_stream(psi_dev.device).cuda_stream
+    _check(lib().wgw_apply_h_dev(ctx.handle, ctypes.c_void_p(psi_dev.data_ptr()), n_psi,
+                                 ctypes.c_void_p(out_dev.data_ptr()), 1 if fp32 else 0,
+                                 ctypes.c_void_p(stream)), "wgw_apply_h_dev")
+    return out_dev
 
 
 def wgw_selftest_wait_timeout() -> int:
