@@ -55,6 +55,19 @@ WORKLOADS = {
 }
 
 
+METRIC = "Sternheimer solves/s at 1e-8 rel err vs FP64 oracle; p50/p99 request latency"
+
+
+def line_config(args, wl, tensor_cores, world):
+    """The config object of the block-apply line (both arms)."""
+    mixed = args.precision == "mixed"
+    return {"workload": args.workload, "desc": wl["desc"], "cg_tol": wl["cg_tol"], "precision": args.precision,
+            "fp64_passes": ("float-float" if args.fp64_emulation else "native FP64") if mixed else "n/a",
+            "pc_fp32": "tcgen05 3xTF32" if tensor_cores else "CUDA-core FP32",
+            "l2": "256 MB buffer written between steps, outside the timed interval",
+            "parallelism": f"perturbation shards x{world}" if world > 1 else "1 GPU"}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -112,29 +125,72 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def cpu_baseline(wl, sys_, budget_s=20.0):
-    """The FP64 oracle's Sternheimer CG (plain numpy) on a bounded sample of the same systems."""
-    import numpy as np
+_CPU_STATE = {}
+
+
+def _cpu_init(L, ecut, grid, vloc_G, psi_v, e_v, miller_rho, n_pert, pert_seed, cg_tol):
+    """Worker set-up: the model and perturbations of the workload (host only)."""
     import synth
-    from oracle import chi0
     from oracle.model import Model
-    m = Model(sys_.L, sys_.ecut, sys_.grid, sys_.vloc_G, sys_.psi_v, sys_.e_v)
-    phi = synth.perturbations(sys_.miller_rho, sys_.L, wl["n_pert"], wl["pert_seed"])
-    dV = m.vsqrt[:, None] * phi
+    m = Model(L, ecut, grid, vloc_G, psi_v, e_v)
+    phi = synth.perturbations(miller_rho, L, n_pert, pert_seed)
+    _CPU_STATE.update(m=m, dV=m.vsqrt[:, None] * phi, tol=cg_tol)
+
+
+def _cpu_solve(job):
+    """Solves the (v, p) systems of one job until its deadline; returns how many it finished."""
+    from oracle import chi0
+    systems, deadline = job
+    done = 0
+    for v, p in systems:
+        if time.time() > deadline:
+            break
+        chi0.sternheimer_cg_drho(_CPU_STATE["m"], _CPU_STATE["dV"], tol=_CPU_STATE["tol"], systems=[(v, p)])
+        done += 1
+    return done
+
+
+def cpu_baseline(wl, sys_, budget_s=20.0, one_core=True):
+    """The FP64 oracle's Sternheimer CG (plain numpy, one thread per process) on a bounded random
+    sample of the same systems, one process per host core, each solving its own systems; with
+    one_core also a single process.  Processes are spawned (never forked) before any GPU call."""
+    import multiprocessing as mp
+    import numpy as np
     nv = sys_.n_v
     order = [(v, p) for p in range(wl["n_pert"]) for v in range(nv)]
-    rng = np.random.default_rng(0)
-    pick = [order[i] for i in rng.permutation(len(order))]
-    done, t0 = 0, time.perf_counter()
-    for v, p in pick:
-        chi0.sternheimer_cg_drho(m, dV, tol=wl["cg_tol"], systems=[(v, p)])
-        done += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": done / dt, "unit": "Sternheimer solves/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{done} of {len(order)} (v, p) systems of the same workload, FP64 numpy CG with "
-                      f"FFT-applied H to the same cg_tol, {dt:.1f} s"}
+    pick = [order[i] for i in np.random.default_rng(0).permutation(len(order))]
+    cores = os.cpu_count() or 1
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = "1"
+    init = (sys_.L, sys_.ecut, sys_.grid, sys_.vloc_G, sys_.psi_v, sys_.e_v, sys_.miller_rho,
+            wl["n_pert"], wl["pert_seed"], wl["cg_tol"])
+    desc = "FP64 numpy CG with FFT-applied H to the same cg_tol"
+    try:
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(cores, initializer=_cpu_init, initargs=init) as pool:
+            pool.map(_cpu_solve, [([], 0.0)] * cores)                # set-up outside the timing
+            t0 = time.time()
+            done = sum(pool.map(_cpu_solve, [(pick[k::cores], t0 + budget_s) for k in range(cores)]))
+            dt = time.time() - t0
+        res = {"value": done / dt, "unit": "Sternheimer solves/s", "cores": cores, "kind": "oracle",
+               "sample": f"{done} of {len(order)} (v, p) systems of the same workload, {desc}, "
+                         f"{cores} single-threaded processes, {dt:.1f} s"}
+        if one_core:
+            with ctx.Pool(1, initializer=_cpu_init, initargs=init) as pool:
+                pool.apply(_cpu_solve, (([], 0.0),))
+                t0 = time.time()
+                one = pool.apply(_cpu_solve, ((pick, t0 + budget_s),))
+                dt1 = time.time() - t0
+            res["one_core"] = {"value": one / dt1, "sample": f"{one} systems, one process, {dt1:.1f} s"}
+        return res
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
 
 
 def run_reference(args, wl):
@@ -145,19 +201,19 @@ def run_reference(args, wl):
     s = synth.make_system(wl["config"])
     lat = []
     for _ in range(args.warmup):
-        cpu_baseline(wl, s, budget_s=2.0)
+        cpu_baseline(wl, s, budget_s=2.0, one_core=False)
     vals = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        cb = cpu_baseline(wl, s, budget_s=8.0)
+        cb = cpu_baseline(wl, s, budget_s=8.0, one_core=False)
         lat.append(time.perf_counter() - t0)
         vals.append(cb["value"])
     v = statistics.mean(vals)
-    line = {"impl": "reference", "metric": "Sternheimer solves/s at 1e-8 rel err vs FP64 oracle",
+    line = {"impl": "reference", "metric": METRIC,
             "value": v, "unit": "Sternheimer solves/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(lat), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "desc": wl["desc"]},
+            "config": line_config(args, wl, 1, 1),
             "cpu_baseline": {"value": v, "unit": "Sternheimer solves/s", "cores": os.cpu_count(),
                              "kind": "oracle", "sample": cb["sample"]},
             "e2e": {"value": v, "unit": "Sternheimer solves/s", "h2d_bytes_per_step": 0,
@@ -613,17 +669,12 @@ def main():
     except Exception:
         traffic = None
     line = {
-        "metric": "Sternheimer solves/s at 1e-8 rel err vs FP64 oracle; p50/p99 request latency",
+        "metric": METRIC,
         "value": value, "unit": "Sternheimer solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64" if args.precision == "mixed" else "f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "desc": wl["desc"], "cg_tol": wl["cg_tol"],
-                   "precision": args.precision,
-                   "fp64_passes": ("float-float" if args.fp64_emulation else "native FP64") if args.precision == "mixed" else "n/a",
-                   "pc_fp32": "tcgen05 3xTF32" if opt.tensor_cores else "CUDA-core FP32",
-                   "l2": "256 MB buffer written between steps, outside the timed interval",
-                   "parallelism": f"perturbation shards x{world}" if world > 1 else "1 GPU"},
+        "config": line_config(args, wl, opt.tensor_cores, world),
         "latency_ms": {"p50": 1e3 * statistics.median(times),
                        "p99": 1e3 * sorted(times)[min(len(times) - 1, int(0.99 * len(times)))],
                        "what": "one block-apply request, device time"},
