@@ -80,6 +80,10 @@ typedef struct wgw_options {
   int tensor_cores;    /* MIXED: 1 = the projector P_c of the FP32 inner solves runs on the tcgen05
                           tensor cores (TF32 products split three ways, hi*hi + hi*lo + lo*hi, FP32
                           accumulation: FP32 accuracy); 0 = FP32 CUDA-core GEMMs. */
+  int cuda_graphs;     /* 1 = the CG iterations between two convergence polls (check_every of them)
+                          are captured as one CUDA graph and replayed (the launches and results are
+                          the same as without; the first window of a solve runs directly); 0 = direct
+                          launches.  Not used while profiling is on. */
 } wgw_options;
 
 typedef struct wgw_stats {
@@ -92,7 +96,7 @@ typedef struct wgw_stats {
 
 /* Fills *opt with defaults: WGW_FP64, cg_tol 1e-12, max_cg_iter 2000, max_refine 8,
  * inner_tol 5e-6, f_s 2, check_every 8, dav_tol 1e-8, dav_max_iter 100, dav_factor 4, seed 12345,
- * fp64_emulation 1, tensor_cores 1. */
+ * fp64_emulation 1, tensor_cores 1, cuda_graphs 1. */
 int wgw_default_options(wgw_options* opt);
 
 /*

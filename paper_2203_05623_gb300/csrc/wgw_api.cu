@@ -396,23 +396,87 @@ int cg_solve(wgw_ctx* c, Prec<T>& pr, int n_sys, double tol, int max_iter, cudaS
   int n_list = 0;
   WGW_TRY(build_list(c, act, n_sys, lbuf, st, &n_list));
   const int every = std::max(1, c->opt.check_every);
-  for (int it = 0; it < max_iter && n_list > 0; ++it) {
+  const bool proj_q = sizeof(T) == sizeof(double) || kProjectInnerOutput;
+  // The iterations between two list rebuilds (a window): the launches depend on the window only
+  // through n_list, so every window but the first (which also sizes the work buffers) is
+  // captured as a CUDA graph and replayed, updating the previous executable graph in place.
+  auto window = [&](int it0, int w, cudaStream_t st) -> int {
     const double lb = (double)n_list * n * sizeof(T);
-    const bool proj_q = sizeof(T) == sizeof(double) || kProjectInnerOutput;
-    WGW_TRY(apply_A<T>(c, pr, P, Q, n_list, lbuf, act, st, proj_q));
-    WGW_CK(c->prof.run(PK_CG, 7 * lb, 0, st, [&] {
-      return launch_cg_step_a<T>(c->wfc.tab(), n, n_list, lbuf, X, R, Z, P, Q, ld, eps, cs, tol * tol,
-                                 max_iter, st); }));
-    WGW_TRY(run_pc<T>(c, Z, n_list, lbuf, Psi, act, st));
-    WGW_CK(c->prof.run(PK_CG, 4 * lb, 0, st, [&] {
-      return launch_cg_step_b<T>(n, n_list, lbuf, R, Z, P, ld, cs, st); }));
-    if ((it + 1) % every == 0) {
-      // Without the projection of q, rounding noise collects in the occupied part of r, where
-      // the iteration cannot remove it; clear it before the convergence test settles on it.
-      if (!proj_q) WGW_TRY(run_pc<T>(c, R, n_list, lbuf, Psi, act, st));
-      WGW_TRY(build_list(c, act, n_sys, lbuf, st, &n_list));
+    for (int k = 0; k < w; ++k) {
+      WGW_TRY(apply_A<T>(c, pr, P, Q, n_list, lbuf, act, st, proj_q));
+      WGW_CK(c->prof.run(PK_CG, 7 * lb, 0, st, [&] {
+        return launch_cg_step_a<T>(c->wfc.tab(), n, n_list, lbuf, X, R, Z, P, Q, ld, eps, cs, tol * tol,
+                                   max_iter, st); }));
+      WGW_TRY(run_pc<T>(c, Z, n_list, lbuf, Psi, act, st));
+      WGW_CK(c->prof.run(PK_CG, 4 * lb, 0, st, [&] {
+        return launch_cg_step_b<T>(n, n_list, lbuf, R, Z, P, ld, cs, st); }));
+    }
+    // Without the projection of q, rounding noise collects in the occupied part of r, where the
+    // iteration cannot remove it; clear it before the convergence test settles on it.
+    if (!proj_q && (it0 + w) % every == 0) WGW_TRY(run_pc<T>(c, R, n_list, lbuf, Psi, act, st));
+    return WGW_OK;
+  };
+  const bool graphs = c->opt.cuda_graphs != 0 && !c->prof.on;
+  // A default stream cannot be captured: the graph then runs on the context's stream, ordered
+  // after and before the caller's stream by events.
+  const bool side = st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread;
+  const cudaStream_t gst = side ? c->stream : st;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  if (graphs && side) {
+    WGW_CK(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
+    WGW_CK(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
+  }
+  cudaGraphExec_t exec = nullptr;
+  int status = WGW_OK;
+  for (int it = 0; it < max_iter && n_list > 0;) {
+    const int w = std::min(every - it % every, max_iter - it);
+    if (graphs && it > 0) {
+      if (side) {
+        WGW_CK(cudaEventRecord(ev_in, st));
+        WGW_CK(cudaStreamWaitEvent(gst, ev_in, 0));
+      }
+      WGW_CK(cudaStreamBeginCapture(gst, cudaStreamCaptureModeRelaxed));
+      const int rc = window(it, w, gst);
+      cudaGraph_t g = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(gst, &g);
+      if (rc != WGW_OK || ce != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        status = rc != WGW_OK ? rc : fail(WGW_ERR_CUDA, cudaGetErrorString(ce));
+        break;
+      }
+      cudaGraphExecUpdateResultInfo info;
+      if (!exec || cudaGraphExecUpdate(exec, g, &info) != cudaSuccess) {
+        (void)cudaGetLastError();
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        const cudaError_t ie = cudaGraphInstantiate(&exec, g, 0);
+        if (ie != cudaSuccess) {
+          cudaGraphDestroy(g);
+          status = fail(WGW_ERR_CUDA, cudaGetErrorString(ie));
+          break;
+        }
+      }
+      cudaGraphDestroy(g);
+      const cudaError_t le = cudaGraphLaunch(exec, gst);
+      if (le != cudaSuccess) { status = fail(WGW_ERR_CUDA, cudaGetErrorString(le)); break; }
+      if (side) {
+        WGW_CK(cudaEventRecord(ev_out, gst));
+        WGW_CK(cudaStreamWaitEvent(st, ev_out, 0));
+      }
+    } else {
+      status = window(it, w, st);
+      if (status != WGW_OK) break;
+    }
+    it += w;
+    if (it % every == 0) {
+      status = build_list(c, act, n_sys, lbuf, st, &n_list);
+      if (status != WGW_OK) break;
     }
   }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (ev_in) cudaEventDestroy(ev_in);
+  if (ev_out) cudaEventDestroy(ev_out);
+  if (status != WGW_OK) return status;
   if (sizeof(T) == sizeof(float) && c->tc_err.p) {
     int flag = 0;
     WGW_CK(tc_error_read_and_clear(&flag, c->tc_err.as<int>(), st));
@@ -1431,6 +1495,7 @@ int wgw_default_options(wgw_options* opt) {
   opt->precision = WGW_FP64;
   opt->fp64_emulation = 1;
   opt->tensor_cores = 1;
+  opt->cuda_graphs = 1;
   opt->cg_tol = 1e-12;
   opt->max_cg_iter = 2000;
   opt->max_refine = 8;

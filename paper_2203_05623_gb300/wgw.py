@@ -36,7 +36,7 @@ class Options(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("f_s", ctypes.c_double),
                 ("check_every", ctypes.c_int), ("dav_tol", ctypes.c_double),
                 ("dav_max_iter", ctypes.c_int), ("dav_factor", ctypes.c_int), ("seed", ctypes.c_int),
-                ("fp64_emulation", ctypes.c_int), ("tensor_cores", ctypes.c_int)]
+                ("fp64_emulation", ctypes.c_int), ("tensor_cores", ctypes.c_int), ("cuda_graphs", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -264,3 +264,19 @@ def test_apply_h_matches_oracle_and_eigenpairs(W, cfg24, kb):
     pv = torch.from_numpy(np.ascontiguousarray(s.psi_v.T)).cuda()
     hv = W.wgw_apply_h_dev(ctx, pv).cpu().numpy().T
     assert np.max(np.abs(hv - s.psi_v * s.e_v[None, :])) < 1e-11 * np.max(np.abs(s.e_v))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_cuda_graph_windows_give_identical_results(W, cfg24, ref24, prec):
+    """The CG windows replayed as CUDA graphs launch the same kernels with the same arguments:
+    bit-identical results with and without graphs, and both within tolerance of the oracle."""
+    dV, ref = ref24
+    p = W.WGW_MIXED if prec == "mixed" else W.WGW_FP64
+    outs = []
+    for graphs in (0, 1):
+        ctx = setup(W, cfg24, precision=p, cg_tol=1e-11, check_every=3, cuda_graphs=graphs)
+        drho, st, _ = W.wgw_apply_chi0(ctx, dV, [0.0, 0.7])
+        outs.append(drho)
+        assert st["n_converged"] == st["n_systems"]
+    assert np.array_equal(outs[0], outs[1])
+    assert rel_err(outs[1][:, :, 0], ref[:, :, 0]) < (1e-8 if prec == "mixed" else 1e-10)
