@@ -700,6 +700,7 @@ def main():
     }
     if cpu:
         line["cpu_baseline"] = cpu
+    line["autotune"] = W.wgw_autotune_info(ctx)
     if world == 1 and args.precision == "mixed" and not args.no_library_baselines:
         line["library_baseline"] = library_baselines(W, ctx, s, prof_all)
     if rank == 0:

@@ -317,6 +317,16 @@ int wgw_g0_lanczos(wgw_ctx* ctx, const double* phi, int n_pdep, const int* state
 int wgw_apply_h_dev(wgw_ctx* ctx, const double* psi_dev, int n_psi, double* out_dev, int fp32, void* stream);
 
 /*
+ * Autotuner record of a context.  The K split of the tensor-core projector (how many phase-1
+ * CTAs per SM the contraction over plane waves is cut into) is picked on the context's own
+ * shapes: at the first projection of at least 256 systems every candidate runs on a scratch
+ * copy of the vectors and the fastest median time wins.  *tc_split = the choice (0: not tuned
+ * yet); splits[k], ms[k] = each candidate and its median time for up to n_max candidates.
+ * Returns the number of candidates written, or -WGW_ERR_ARG for a null context or negative n_max.
+ */
+int wgw_autotune_info(const wgw_ctx* ctx, int* tc_split, int* splits, double* ms, int n_max);
+
+/*
  * Failure-detection self-test (no counterpart in the paper).  Every wait of the library's
  * kernels on a device barrier is bounded to about one second of wall time, after which the
  * kernel sets an error flag, releases what it holds and returns; the host turns the flag into

@@ -89,12 +89,15 @@ cudaError_t launch_drho_xline(int m, FftCtx<T> f, const cplx<T>* Tbuf, const T* 
 template <typename T>
 cudaError_t launch_pc(T* Y, long ldy, int n_sys, const int* list, const T* Psi, long ldp, int n, int nv,
                       const int* active, T* work, cudaStream_t st, bool ffc = false,
-                      const unsigned char* tc_tiles = nullptr, const T* psi_ff = nullptr, int* tc_err = nullptr);
+                      const unsigned char* tc_tiles = nullptr, const T* psi_ff = nullptr, int* tc_err = nullptr,
+                      int tc_split = 8);
 // P_c on the tensor cores (3xTF32 products, FP32 accumulation in tensor memory); work holds
 // tc_pc_work_elems(n, n_sys, nv) floats; tiles from launch_tc_tile_psi; *err (device) is set to 1
 // when a wait on an MMA or copy barrier times out.
+// split: phase-1 CTAs per SM the K dimension is cut for (1..kTcSplitMax; picked by the autotuner).
+constexpr int kTcSplitDefault = 8, kTcSplitMax = 16;
 cudaError_t launch_pc_tc(float* Y, long ldy, int n_sys, const int* list, const unsigned char* tiles, int n, int nv,
-                         const int* active, float* work, cudaStream_t st, int* err);
+                         const int* active, float* work, cudaStream_t st, int* err, int split = kTcSplitDefault);
 size_t tc_pc_work_elems(int n, int n_sys, int nv);
 bool tc_pc_supported(int nv);
 // Psi (n x nv, column v at Psi + v ldp) split into TF32 hi/lo parts and laid out as the operand

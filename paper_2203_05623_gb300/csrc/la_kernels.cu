@@ -600,12 +600,12 @@ inline dim3 grid_el(int n, int n_sys) {
 template <typename T>
 cudaError_t launch_pc(T* Y, long ldy, int n_sys, const int* list, const T* Psi, long ldp, int n, int nv,
                       const int* active, T* work, cudaStream_t st, bool ffc, const unsigned char* tc_tiles,
-                      const T* psi_ff, int* tc_err) {
+                      const T* psi_ff, int* tc_err, int tc_split) {
   if (n_sys == 0 || nv == 0) return cudaSuccess;
   if constexpr (sizeof(T) == sizeof(float)) {
     if (tc_tiles && tc_pc_supported(nv))
       return launch_pc_tc(reinterpret_cast<float*>(Y), ldy, n_sys, list, tc_tiles, n, nv, active,
-                          reinterpret_cast<float*>(work), st, tc_err);
+                          reinterpret_cast<float*>(work), st, tc_err, tc_split);
   }
   const int n_kb = pc_kblocks(n, n_sys);
   const int kblk = ((n + n_kb - 1) / n_kb + kGK - 1) / kGK * kGK;
@@ -922,7 +922,7 @@ template cudaError_t launch_kb<double>(double*, const double*, long, int, const 
 #define WGW_INST_LA(T)                                                                             \
   template cudaError_t launch_pc<T>(T*, long, int, const int*, const T*, long, int, int,           \
                                     const int*, T*, cudaStream_t, bool, const unsigned char*,      \
-                                    const T*, int*);                                               \
+                                    const T*, int*, int);                                          \
   template cudaError_t launch_cg_init_a<T>(const SphereTab&, int, int, const T*, T*, T*, T*, long, \
                                            const double*, CgState, cudaStream_t);                 \
   template cudaError_t launch_cg_init_b<T>(int, int, const T*, const T*, T*, long, CgState,       \

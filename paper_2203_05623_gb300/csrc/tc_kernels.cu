@@ -488,7 +488,7 @@ namespace {
 struct TcGeom {
   int Nn, ldc, nkc, nrt, nvc, njt, n_kb, kcpb;
 };
-TcGeom tc_geom(int n, int n_sys, int nv) {
+TcGeom tc_geom(int n, int n_sys, int nv, int split = kTcSplitDefault) {
   TcGeom g;
   g.Nn = (nv + 15) / 16 * 16;
   g.ldc = (nv + 31) / 32 * 32;
@@ -496,8 +496,8 @@ TcGeom tc_geom(int n, int n_sys, int nv) {
   g.nrt = (n + tc::kRowsA - 1) / tc::kRowsA;
   g.nvc = g.ldc / tc::kKC;
   g.njt = (n_sys + tc::kRowsA - 1) / tc::kRowsA;
-  // About 8 phase-1 CTAs per SM (two resident at a time), each with at least 4 chunks of K.
-  int kb = (8 * 152 + g.njt - 1) / g.njt;
+  // About `split` phase-1 CTAs per SM (two resident at a time), each with at least 4 chunks of K.
+  int kb = (split * 152 + g.njt - 1) / g.njt;
   kb = std::max(1, std::min(kb, std::max(1, g.nkc / 4)));
   g.kcpb = (g.nkc + kb - 1) / kb;
   g.n_kb = (g.nkc + g.kcpb - 1) / g.kcpb;
@@ -523,18 +523,23 @@ cudaError_t launch_tc_tile_psi(const float* Psi, long ldp, int n, int nv, unsign
 }
 
 size_t tc_pc_work_elems(int n, int n_sys, int nv) {
-  const TcGeom g = tc_geom(n, n_sys, nv);
-  // Cpart floats, then the split C^T tiles (bytes / 4).
-  return static_cast<size_t>(g.n_kb) * n_sys * g.ldc + static_cast<size_t>(g.njt) * g.nvc * 2 * tc::kTile / 4;
+  // Cpart floats, then the split C^T tiles (bytes / 4); room for every split the tuner tries.
+  size_t most = 0;
+  for (int split = 1; split <= kTcSplitMax; ++split) {
+    const TcGeom g = tc_geom(n, n_sys, nv, split);
+    most = std::max(most, static_cast<size_t>(g.n_kb) * n_sys * g.ldc +
+                              static_cast<size_t>(g.njt) * g.nvc * 2 * tc::kTile / 4);
+  }
+  return most;
 }
 
 bool tc_pc_supported(int nv) { return nv >= 1 && nv <= 256; }
 
 cudaError_t launch_pc_tc(float* Y, long ldy, int n_sys, const int* list, const unsigned char* tiles, int n, int nv,
-                         const int* active, float* work, cudaStream_t st, int* err) {
+                         const int* active, float* work, cudaStream_t st, int* err, int split) {
   if (n_sys == 0 || nv == 0) return cudaSuccess;
-  if (!tc_pc_supported(nv) || !err) return cudaErrorInvalidValue;
-  const TcGeom g = tc_geom(n, n_sys, nv);
+  if (!tc_pc_supported(nv) || !err || split < 1 || split > kTcSplitMax) return cudaErrorInvalidValue;
+  const TcGeom g = tc_geom(n, n_sys, nv, split);
   const unsigned char* t1 = tiles;
   const unsigned char* t2 = tiles + static_cast<size_t>(g.nkc) * 2 * g.Nn * 128;
   float* Cpart = work;

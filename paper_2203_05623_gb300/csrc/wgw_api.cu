@@ -215,6 +215,10 @@ struct wgw_ctx {
       drho_all, psi_tc, cg_best, cg_itbest, lz_q, lz_qf, tc_err;
   cudaStream_t stream = nullptr;
   Prof prof;
+  // Autotuner results: the K split of the tensor-core P_c (phase-1 CTAs per SM; 0 = not tuned
+  // yet) and the median time of each candidate on this context's shapes.
+  int tc_split = 0;
+  std::vector<std::pair<int, double>> tc_tune;
   std::vector<int> last_iters;      // per system of the last apply: CG iterations (all refinements)
   std::vector<double> last_relres;  // per system of the last apply: final FP64 ||b - A x|| / ||b||
   // Serialises every entry point that uses the context's device state (callers and the
@@ -284,6 +288,45 @@ int to_real(wgw_ctx* c, Prec<T>& pr, const HostSphere& sp, const T* X, long ldx,
   return WGW_OK;
 }
 
+// Autotuner of the tensor-core P_c: at the first projection of at least 256 systems (never
+// inside a graph capture) every candidate K split runs three times on a scratch copy of the
+// vectors and the fastest median wins for the life of the context.
+constexpr int kTcSplitCandidates[] = {2, 4, 8, 16};
+
+int tune_tc_split(wgw_ctx* c, const float* Y, int n_list, float* work, cudaStream_t st) {
+  const int n = c->wfc.nrb();
+  DevBuf scratch;
+  WGW_TRY(scratch.ensure(sizeof(float) * (size_t)n_list * c->ld_w));
+  WGW_CK(cudaMemcpyAsync(scratch.p, Y, sizeof(float) * (size_t)n_list * c->ld_w, cudaMemcpyDeviceToDevice, st));
+  cudaEvent_t a = nullptr, b = nullptr;
+  WGW_CK(cudaEventCreate(&a));
+  WGW_CK(cudaEventCreate(&b));
+  int best = kTcSplitDefault;
+  double best_ms = 1e300;
+  c->tc_tune.clear();
+  for (int split : kTcSplitCandidates) {
+    std::vector<float> ts;
+    for (int r = 0; r < 4; ++r) {
+      WGW_CK(cudaEventRecord(a, st));
+      WGW_CK(launch_pc_tc(scratch.as<float>(), c->ld_w, n_list, nullptr, c->psi_tc.as<unsigned char>(), n, c->n_v,
+                          nullptr, work, st, c->tc_err.as<int>(), split));
+      WGW_CK(cudaEventRecord(b, st));
+      WGW_CK(cudaEventSynchronize(b));
+      float ms = 0.f;
+      WGW_CK(cudaEventElapsedTime(&ms, a, b));
+      if (r > 0) ts.push_back(ms);   // the first run warms up
+    }
+    std::sort(ts.begin(), ts.end());
+    const double med = ts[ts.size() / 2];
+    c->tc_tune.emplace_back(split, med);
+    if (med < best_ms) { best_ms = med; best = split; }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  c->tc_split = best;
+  return WGW_OK;
+}
+
 // P_c applied to the systems of a list (null = 0..n_list-1), timed as pc_project.
 template <typename T>
 int run_pc(wgw_ctx* c, T* Y, int n_list, const int* list, const T* Psi, const int* active, cudaStream_t st) {
@@ -301,12 +344,19 @@ int run_pc(wgw_ctx* c, T* Y, int n_list, const int* list, const T* Psi, const in
     WGW_CK(cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), st));
   }
   const unsigned char* tiles = tcores ? c->psi_tc.as<unsigned char>() : nullptr;
+  if (tcores && c->tc_split == 0 && n_list >= 256) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    WGW_CK(cudaStreamIsCapturing(st, &cap));
+    if (cap == cudaStreamCaptureStatusNone)
+      WGW_TRY(tune_tc_split(c, reinterpret_cast<const float*>(Y), n_list, reinterpret_cast<float*>(work), st));
+  }
+  const int split = c->tc_split > 0 ? c->tc_split : kTcSplitDefault;
   WGW_CK(c->prof.run(PK_PC, 2.0 * n_list * n * sizeof(T) + n * nv * sizeof(T), 4.0 * n * nv * n_list, st, [&] {
     const bool ffc = sizeof(T) == 8 && c->d.use_ff;
     const T* psi_ff = (ffc && Psi == reinterpret_cast<const T*>(c->d.psi.p)) ? reinterpret_cast<const T*>(c->d.psi_ff.p)
                                                                              : nullptr;
     return launch_pc<T>(Y, c->ld_w, n_list, list, Psi, c->ld_w, (int)n, c->n_v, active, work, st, ffc, tiles,
-                        psi_ff, tcores ? c->tc_err.as<int>() : nullptr); }));
+                        psi_ff, tcores ? c->tc_err.as<int>() : nullptr, split); }));
   return WGW_OK;
 }
 
@@ -1874,6 +1924,20 @@ int wgw_apply_h_dev(wgw_ctx* c, const double* psi_dev, int n_psi, double* out_de
   }
   WGW_CK(launch_rb_to_sphere(n_psi, Q, ld, nullptr, nullptr, c->wfc.map(), out_dev, 2L * c->wfc.n, st));
   return WGW_OK;
+}
+
+int wgw_autotune_info(const wgw_ctx* c, int* tc_split, int* splits, double* ms, int n_max) {
+  if (!c || n_max < 0) {
+    fail(WGW_ERR_ARG, "bad argument");
+    return -WGW_ERR_ARG;
+  }
+  if (tc_split) *tc_split = c->tc_split;
+  const int m = std::min<int>(n_max, (int)c->tc_tune.size());
+  for (int k = 0; k < m; ++k) {
+    if (splits) splits[k] = c->tc_tune[k].first;
+    if (ms) ms[k] = c->tc_tune[k].second;
+  }
+  return m;
 }
 
 int wgw_selftest_wait_timeout(int* timed_out) {

@@ -107,6 +107,8 @@ def lib(path: str | None = None):
                                              _dp, ctypes.POINTER(Stats)]
     L.wgw_apply_h_dev.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                   ctypes.c_void_p]
+    L.wgw_autotune_info.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                    _dp, ctypes.c_int]
     L.wgw_selftest_wait_timeout.argtypes = [ctypes.POINTER(ctypes.c_int)]
     L.wgw_apply_channels.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int,
                                      _dp, ctypes.c_int, _dp, ctypes.POINTER(Stats)]
@@ -252,6 +254,17 @@ def wgw_apply_h_dev(ctx: Context, psi_dev, out_dev=None, fp32=False, stream=None
                                  ctypes.c_void_p(out_dev.data_ptr()), 1 if fp32 else 0,
                                  ctypes.c_void_p(stream)), "wgw_apply_h_dev")
     return out_dev
+
+
+def wgw_autotune_info(ctx: Context) -> dict:
+    """The autotuner's choice of the tensor-core P_c K split and each candidate's median time."""
+    choice = ctypes.c_int(0)
+    splits = (ctypes.c_int * 16)()
+    ms = np.zeros(16)
+    k = lib().wgw_autotune_info(ctx.handle, ctypes.byref(choice), splits, ms.ctypes.data_as(_dp), 16)
+    if k < 0:
+        _check(-k, "wgw_autotune_info")
+    return {"tc_split": choice.value, "candidates_ms": {int(splits[i]): float(ms[i]) for i in range(k)}}
 
 
 def wgw_selftest_wait_timeout() -> int:

@@ -280,3 +280,19 @@ def test_cuda_graph_windows_give_identical_results(W, cfg24, ref24, prec):
         assert st["n_converged"] == st["n_systems"]
     assert np.array_equal(outs[0], outs[1])
     assert rel_err(outs[1][:, :, 0], ref[:, :, 0]) < (1e-8 if prec == "mixed" else 1e-10)
+
+
+def test_autotuner_picks_a_candidate_and_results_stay_correct(W):
+    """The tensor-core P_c K split is tuned at the first projection of >= 256 systems; the result
+    of the apply is within tolerance whatever the choice."""
+    s = synth.make_system(synth.Config("nv70", L=10.0, ecut=5.0, grid=24, n_wells=16, well_seed=1, n_v=70))
+    dV = synth.perturbations(s.miller_rho, s.L, 4, 62)          # 280 systems
+    ctx = setup(W, s, precision=W.WGW_MIXED, cg_tol=1e-11)
+    assert W.wgw_autotune_info(ctx)["tc_split"] == 0
+    drho, st, _ = W.wgw_apply_chi0(ctx, dV)
+    info = W.wgw_autotune_info(ctx)
+    assert info["tc_split"] in (2, 4, 8, 16)
+    assert sorted(info["candidates_ms"]) == [2, 4, 8, 16]
+    assert all(t > 0 for t in info["candidates_ms"].values())
+    ref = chi0.sos_drho(model_of(s), dV, [0.0])
+    assert rel_err(drho, ref) < 1e-8
