@@ -23,6 +23,7 @@ the paper by eye:
   dyson.py    the Dyson step chibar = (1 - chi0bar)^-1 chi0bar in a basis (Sec. 2)
   g0.py       G0 Lanczos chains of the unprojected h for the short-range
               correlation integral (Eq. ISR, Eq. lanczos, Sec. 3)
+  sigma.py    exchange self-energy <psi_i|Sigma_X|psi_i> (Eq. sigmacIR, Sec. 2)
 
 Parity status of each function is stated in its module header.
 """

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import chi0, dyson, g0, lanczos, pdep
+from oracle import chi0, dyson, g0, lanczos, pdep, sigma
 from oracle.model import Model, sphere
 
 
@@ -430,3 +430,57 @@ def test_static_response_derivative_with_d_channels():
     dV = synth.perturbations(s.miller_rho, s.L, 1, 43)[:, 0]
     fd = chi0.finite_difference_drho(m, dV, 1e-3)
     assert rel(chi0.sos_drho(m, dV, [0.0])[:, 0, 0], fd) < 1e-9
+
+
+# ---------------------------------------------------------------- exchange self-energy (Eq. sigmacIR)
+def _convolution_pair_density(m, ci, cj):
+    """sum_G1 c_i(G1)^* c_j(G1 + G) on the density sphere (direct G-space route)."""
+    where = {tuple(g): k for k, g in enumerate(m.mw.tolist())}
+    out = np.zeros(m.mr.shape[0], np.complex128)
+    for a, G in enumerate(m.mr.tolist()):
+        acc = 0.0
+        for k1, G1 in enumerate(m.mw.tolist()):
+            k2 = where.get((G1[0] + G[0], G1[1] + G[1], G1[2] + G[2]))
+            if k2 is not None:
+                acc += np.conj(ci[k1]) * cj[k2]
+        out[a] = acc
+    return out
+
+
+def test_pair_density_equals_convolution(tiny):
+    m = model_of(tiny)
+    for i, j in ((0, 0), (0, 1), (1, 0)):
+        got = sigma.pair_density(m, m.psi_v[:, i], m.psi_v[:, j])
+        ref = _convolution_pair_density(m, m.psi_v[:, i], m.psi_v[:, j])
+        assert rel(got, ref) < 1e-13
+
+
+def test_sigma_x_plane_waves_closed_form():
+    """Plane-wave states e^{ik.r}: <i|Sigma_X|i> = -(1/Omega) sum_{j != i} 4 pi / |k_j - k_i|^2."""
+    m = free_model(n_occ=7)
+    got = sigma.sigma_x(m)
+    k = m.b * m.mw[:7].astype(np.float64)
+    ref = []
+    for i in range(7):
+        d2 = np.sum((k - k[i]) ** 2, axis=1)
+        ref.append(-np.sum(4 * np.pi / d2[np.arange(7) != i]) / m.omega)
+    assert np.max(np.abs(got - np.asarray(ref))) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_sigma_x_total_invariant_under_rotation(tiny):
+    m = model_of(tiny)
+    rng = np.random.default_rng(81)
+    Q, _ = np.linalg.qr(rng.standard_normal((2, 2)) + 1j * rng.standard_normal((2, 2)))
+    rot = Model(tiny.L, tiny.ecut, tiny.grid, tiny.vloc_G, tiny.psi_v @ Q, tiny.e_v)
+    a, b = sigma.sigma_x(m), sigma.sigma_x(rot)
+    assert abs(np.sum(a) - np.sum(b)) < 1e-13 * abs(np.sum(a))
+    assert np.all(a < 0)
+
+
+def test_planted_missing_conjugate_fails_pair_density_pin(tiny, monkeypatch):
+    m = model_of(tiny)
+    ci = m.psi_v[:, 0] * np.exp(0.7j)        # a phase makes the conjugate matter
+    monkeypatch.setattr(sigma.np, "conj", lambda x: x)
+    got = sigma.pair_density(m, ci, m.psi_v[:, 1])
+    monkeypatch.undo()
+    assert rel(got, _convolution_pair_density(m, ci, m.psi_v[:, 1])) > 1e-3
