@@ -317,6 +317,19 @@ int wgw_g0_lanczos(wgw_ctx* ctx, const double* phi, int n_pdep, const int* state
 int wgw_apply_h_dev(wgw_ctx* ctx, const double* psi_dev, int n_psi, double* out_dev, int fp32, void* stream);
 
 /*
+ * Exchange self-energy of occupied states (Sec. 2, Eq. sigmacIR: Sigma_X is Eq. self_energy_gw
+ * with the bare Coulomb potential v in place of W_0):
+ *   sigma_x[k] = <psi_i|Sigma_X|psi_i> = -(1/Omega) sum_{j occ} sum_{G != 0} (4 pi/|G|^2) |FT[psi_i psi_j](G)|^2
+ * for i = states[k], psi(r) = sum_G c(G) e^{iG.r} as given to wgw_setup (Omega^{-1/2} normalisation),
+ * FT the density-sphere coefficients (1/N_grid) sum_r; one spin channel (no factor 2); the
+ * G = 0 head is left out (it belongs to the long-range part).  Pair densities are formed in real
+ * space and transformed with the library's FFT kernels at FP64 accuracy (float-float on a
+ * mixed context with fp64_emulation).  Result in Ha.
+ * Returns WGW_ERR_ARG for a state index outside 0..n_v-1.
+ */
+int wgw_sigma_x(wgw_ctx* ctx, const int* states, int n_states, double* sigma_x);
+
+/*
  * Autotuner record of a context.  The K split of the tensor-core projector (how many phase-1
  * CTAs per SM the contraction over plane waves is cut into) is picked on the context's own
  * shapes: at the first projection of at least 256 systems every candidate runs on a scratch

@@ -1926,6 +1926,63 @@ int wgw_apply_h_dev(wgw_ctx* c, const double* psi_dev, int n_psi, double* out_de
   return WGW_OK;
 }
 
+int wgw_sigma_x(wgw_ctx* c, const int* states, int n_states, double* sigma_x) {
+  g_last_error.clear();
+  if (!c || !states || n_states < 1 || !sigma_x) return fail(WGW_ERR_ARG, "need a context, states and output");
+  for (int k = 0; k < n_states; ++k)
+    if (states[k] < 0 || states[k] >= c->n_v) return fail(WGW_ERR_ARG, "state index outside 0..n_v-1");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  cudaStream_t st = c->stream;
+  set_ff(c);
+  const int N = c->N, n_v = c->n_v;
+  const HostSphere& rs = c->rho;
+  const long ldr = c->ld_r;
+  const int nr = rs.nrb();
+  // v^1/2 per real-basis element of the density sphere (0 at G = 0).
+  std::vector<double> vsh(nr, 0.0);
+  for (int j = 1; j <= rs.n_pairs; ++j) vsh[2 * j - 1] = vsh[2 * j] = rs.vsqrt[rs.pos[j]];
+  DevBuf vs, out, nrm;
+  WGW_TRY(vs.ensure(sizeof(double) * nr));
+  WGW_CK(cudaMemcpyAsync(vs.p, vsh.data(), sizeof(double) * nr, cudaMemcpyHostToDevice, st));
+  // Pair densities u_i u_j of every listed i with every occupied j (real in r at Gamma), in
+  // batches of about 512: products in real space and the x transform in the x-line kernel,
+  // then the plane transforms onto the density sphere; |v^1/2 n_ij|^2 summed over G.
+  const int per = std::max(1, std::min(n_states, 512 / std::max(1, n_v)));
+  std::vector<double> acc(n_states, 0.0);
+  for (int q0 = 0; q0 < n_states; q0 += per) {
+    const int nq = std::min(per, n_states - q0), n_sys = nq * n_v;
+    WGW_TRY(ensure_work(c, n_sys, 1));
+    std::vector<int> ai(n_sys), bi(n_sys);
+    for (int q = 0; q < nq; ++q)
+      for (int j = 0; j < n_v; ++j) { ai[q * n_v + j] = states[q0 + q]; bi[q * n_v + j] = j; }
+    WGW_CK(cudaMemcpyAsync(c->a_idx.p, ai.data(), sizeof(int) * n_sys, cudaMemcpyHostToDevice, st));
+    WGW_CK(cudaMemcpyAsync(c->b_idx.p, bi.data(), sizeof(int) * n_sys, cudaMemcpyHostToDevice, st));
+    const int NPr = 2 * rs.m + 1, pairs = (n_sys + 1) / 2;
+    WGW_TRY(c->Trho.ensure(sizeof(cplx<double>) * (size_t)pairs * NPr * N * N));
+    WGW_TRY(out.ensure(sizeof(double) * (size_t)n_sys * ldr));
+    WGW_TRY(nrm.ensure(sizeof(double) * n_sys));
+    FftCtx<double> f = c->d.fft(c->plan);
+    XArgs<double> a{};
+    a.mode = XM_FROM_REAL; a.A = c->d.psi_r_fft(); a.lda = c->grid3; a.a_index = c->a_idx.as<int>();
+    a.Bm = c->d.psi_r_fft(); a.ldb = c->grid3; a.b_index = c->b_idx.as<int>(); a.n_sys = n_sys;
+    WGW_CK(launch_xline<double>(rs.m, f, c->Trho.as<cplx<double>>(), a, nullptr, st));
+    Epi<double> e{};
+    e.out = out.as<double>(); e.ldo = ldr; e.vcoef = 1.0; e.n_sys = n_sys;
+    WGW_CK(launch_plane_r2g<double>(rs.tab(), rs.npt_max, f, c->Trho.as<cplx<double>>(), e, st));
+    dim3 g(std::max(1, std::min(64, (nr + 255) / 256)), std::min(n_sys, 65535));
+    k_scale_rows<<<g, 256, 0, st>>>(nr, n_sys, out.as<double>(), ldr, vs.as<double>(), out.as<double>(), ldr);
+    WGW_CK(cudaGetLastError());
+    WGW_CK(launch_norm2<double>(n_sys, nr, out.as<double>(), ldr, nrm.as<double>(), st));
+    std::vector<double> h(n_sys);
+    WGW_CK(cudaMemcpyAsync(h.data(), nrm.p, sizeof(double) * n_sys, cudaMemcpyDeviceToHost, st));
+    WGW_CK(cudaStreamSynchronize(st));
+    for (int q = 0; q < nq; ++q)
+      for (int j = 0; j < n_v; ++j) acc[q0 + q] += h[q * n_v + j];
+  }
+  for (int k = 0; k < n_states; ++k) sigma_x[k] = -acc[k] / c->omega_cell;
+  return WGW_OK;
+}
+
 int wgw_autotune_info(const wgw_ctx* c, int* tc_split, int* splits, double* ms, int n_max) {
   if (!c || n_max < 0) {
     fail(WGW_ERR_ARG, "bad argument");

@@ -107,6 +107,7 @@ def lib(path: str | None = None):
                                              _dp, ctypes.POINTER(Stats)]
     L.wgw_apply_h_dev.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                   ctypes.c_void_p]
+    L.wgw_sigma_x.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int, _dp]
     L.wgw_autotune_info.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                     _dp, ctypes.c_int]
     L.wgw_selftest_wait_timeout.argtypes = [ctypes.POINTER(ctypes.c_int)]
@@ -254,6 +255,15 @@ def wgw_apply_h_dev(ctx: Context, psi_dev, out_dev=None, fp32=False, stream=None
                                  ctypes.c_void_p(out_dev.data_ptr()), 1 if fp32 else 0,
                                  ctypes.c_void_p(stream)), "wgw_apply_h_dev")
     return out_dev
+
+
+def wgw_sigma_x(ctx: Context, states) -> np.ndarray:
+    """<psi_i|Sigma_X|psi_i> [Ha] for the listed occupied states."""
+    sts = np.ascontiguousarray(states, np.int32)
+    out = np.zeros(sts.size)
+    _check(lib().wgw_sigma_x(ctx.handle, sts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), sts.size,
+                             out.ctypes.data_as(_dp)), "wgw_sigma_x")
+    return out
 
 
 def wgw_autotune_info(ctx: Context) -> dict:
