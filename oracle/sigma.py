@@ -21,11 +21,22 @@ Readings (the paper leaves these open):
     pair densities are formed on the grid and taken to the density sphere,
     which holds every product of two wavefunction-sphere functions.
 
+The short-range correlation integral of Eq. ISR,
+  I^SR_i(w) = (1/Omega) sum_nm int dw'/(2 pi) Lambda_nm(i w') <psi_i phi~_n|(h - w - i w')^-1|psi_i phi~_m>,
+is evaluated with the G0 Lanczos resolvent of oracle/g0.py (Eq. lanczos).
+Readings: Lambda_nm(i w') is even in w' (it is built from chi0bar(i w'), which is), so the
+integral over the whole imaginary axis is folded onto [0, inf):
+  I^SR_i(w) = (1/Omega) int_0^inf dw'/(2 pi) sum_nm Lambda_nm(i w') [g0_nm(w + i w') + g0_nm(w - i w')],
+and is taken by the quadrature (nodes, weights) the caller passes (e.g. Gauss-Legendre
+on [0, w_max]); Lambda is supplied at the nodes (e.g. the Dyson step in the PDEP basis).
+
 Pins (tests/test_oracle_pins.py): the pair densities equal the direct
 G-space convolution sum_G1 c_i(G1)^* c_j(G1 + G); for plane-wave states the
 result is the closed form -(1/Omega) sum_{j != i} 4 pi / |k_j - k_i|^2; the
 total sum_i <psi_i|Sigma_X|psi_i> is invariant under a unitary rotation of the
-occupied states.
+occupied states.  For I^SR: with Lambda = c * identity at every node and exhausted chains, the
+quadrature of the folded integrand over [0, W] converges to the closed form
+(c/Omega) sum_n <b_n| (1/pi) arctan(W / (h - w)) |b_n> evaluated through the eigenpairs of h.
 """
 from __future__ import annotations
 
@@ -54,3 +65,25 @@ def sigma_x(model: Model, states=None) -> np.ndarray:
             acc += np.sum(v * np.abs(n_ij) ** 2)
         out.append(-acc / model.omega)
     return np.asarray(out)
+
+
+def isr(model: Model, phi: np.ndarray, states, n_steps: int, omegas, lam: np.ndarray, nodes, weights):
+    """I^SR_i(w) for the listed states and real frequencies w: shape (n_states, n_omega), complex.
+
+    lam: Lambda_nm(i w'_k) at the quadrature nodes, shape (n_nodes, n_pdep, n_pdep).
+    nodes, weights: quadrature of [0, inf) (w'_k >= 0).
+    """
+    from . import g0
+    omegas = np.asarray(omegas, np.float64).ravel()
+    nodes = np.asarray(nodes, np.float64).ravel()
+    weights = np.asarray(weights, np.float64).ravel()
+    lam = np.asarray(lam, np.float64)
+    z = np.array([[w + 1j * wp, w - 1j * wp] for w in omegas for wp in nodes]).ravel()
+    G = g0.g0_lanczos(model, phi, states, n_steps, z)["g0"]          # (ns, nz, npd, npd)
+    nw, nk = omegas.size, nodes.size
+    G = G.reshape(len(states), nw, nk, 2, *G.shape[2:])
+    out = np.zeros((len(states), nw), np.complex128)
+    for k in range(nk):
+        s = np.einsum("nm,iwnm->iw", lam[k], G[:, :, k, 0] + G[:, :, k, 1])
+        out += weights[k] / (2.0 * np.pi) * s
+    return out / model.omega

@@ -484,3 +484,25 @@ def test_planted_missing_conjugate_fails_pair_density_pin(tiny, monkeypatch):
     got = sigma.pair_density(m, ci, m.psi_v[:, 1])
     monkeypatch.undo()
     assert rel(got, _convolution_pair_density(m, ci, m.psi_v[:, 1])) > 1e-3
+
+
+def test_isr_quadrature_converges_to_arctan_closed_form(tiny):
+    """Lambda = c * identity at every node, exhausted chains: the folded quadrature over [0, W]
+    of Eq. ISR approaches (c/Omega) sum_n <b_n|(1/pi) arctan(W/(h - w))|b_n>."""
+    m = model_of(tiny)
+    phi = synth.perturbations(tiny.miller_rho, tiny.L, 2, 82)
+    W, c = 30.0, 0.37
+    x, wts = np.polynomial.legendre.leggauss(400)
+    # Composite Gauss-Legendre: [0, 2] resolves the peak of 2x/(x^2 + w'^2) near the spectrum.
+    nodes = np.concatenate([(x + 1.0), 2.0 + 0.5 * (W - 2.0) * (x + 1.0)])
+    weights = np.concatenate([wts, 0.5 * (W - 2.0) * wts])
+    lam = np.broadcast_to(c * np.eye(2), (nodes.size, 2, 2))
+    omegas = [0.23, -1.7]                       # away from the spectrum of h
+    got = sigma.isr(m, phi, [1], m.mw.shape[0], omegas, lam, nodes, weights)
+    e, U = np.linalg.eigh(m.h_dense())
+    S = g0.start_vectors(m, phi, 1)
+    Y = U.conj().T @ S
+    ref = np.array([c / m.omega * np.sum(np.abs(Y) ** 2 * (np.arctan(W / (e - w)) / np.pi)[:, None])
+                    for w in omegas])
+    assert np.max(np.abs(got[0] - ref)) < 1e-9 * np.max(np.abs(ref))
+    assert np.max(np.abs(got.imag)) < 1e-12 * np.max(np.abs(ref))
