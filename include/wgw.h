@@ -350,6 +350,22 @@ int wgw_autotune_info(const wgw_ctx* ctx, int* tc_split, int* splits, double* ms
 int wgw_selftest_wait_timeout(int* timed_out);
 
 /*
+ * Short-range correlation integral of Eq. ISR on the imaginary axis, for listed occupied states
+ * i and real frequencies w:
+ *   isr[i][j] = (1/Omega) int_0^inf dw'/(2 pi) sum_nm Lambda_nm(i w') [g0_nm(w_j + i w') + g0_nm(w_j - i w')]
+ * (the integral over the whole axis folded with Lambda even in w'), taken by the caller's
+ * quadrature (nodes w'_k >= 0, weights), with g0 the G0 Lanczos resolvent of wgw_g0_lanczos
+ * (same phi, states and n_steps) and Lambda_nm(i w'_k) given at the nodes (e.g. wgw_dyson of the
+ * PDEP-basis chibar0 from wgw_lanczos).  The contraction runs on the GPU.
+ *   lam      host, n_nodes x n_pdep x n_pdep (row-major per node).
+ *   isr      host output, n_states x n_omega complex, interleaved.
+ * Returns WGW_ERR_ARG for a state outside 0..n_v-1, a negative node or missing arrays.
+ */
+int wgw_isr(wgw_ctx* ctx, const double* phi, int n_pdep, const int* states, int n_states, int n_steps,
+            const double* omega, int n_omega, const double* lam, const double* nodes, const double* weights,
+            int n_nodes, double* isr, wgw_stats* st);
+
+/*
  * Dyson equation in a basis (Sec. 2: the screened response from the independent-particle one,
  * epsilon^-1 - 1 = (1 - chibar0)^-1 chibar0 for the symmetrised responses), for every frequency
  * of a batch, in FP64 on the GPU (Gaussian elimination with partial pivoting, one CTA per

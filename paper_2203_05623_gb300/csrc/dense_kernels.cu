@@ -540,6 +540,34 @@ __global__ void k_lz_g0_eval(int n_pdep, int n_v, int n_steps, int n_z, const do
     g[2 * e + 1] = im;
   }
 }
+// Eq. ISR by quadrature: out[i][j] = coef sum_k (w_k / 2 pi) sum_nm lam[k][n][m]
+// (g[i][(j nk + k) 2][n][m] + g[i][(j nk + k) 2 + 1][n][m]), complex.  One block per (i, j).
+__global__ void __launch_bounds__(256) k_lz_isr(int n_pdep, int n_states, int n_omega, int n_nodes,
+                                                const double* __restrict__ g, const double* __restrict__ lam,
+                                                const double* __restrict__ w, double coef, double* __restrict__ out) {
+  __shared__ double red[33];
+  const int i = blockIdx.x / n_omega, j = blockIdx.x % n_omega;
+  const int nz = 2 * n_omega * n_nodes;
+  const size_t mm = (size_t)n_pdep * n_pdep;
+  Thr th{(int)threadIdx.x, (int)blockDim.x};
+  double re = 0.0, im = 0.0;
+  for (size_t e = threadIdx.x; e < (size_t)n_nodes * mm; e += blockDim.x) {
+    const int k = (int)(e / mm);
+    const size_t nm = e % mm;
+    const double f = lam[e] * w[k] * (0.5 / 3.14159265358979323846);
+    const size_t zp = (size_t)(j * n_nodes + k) * 2;
+    const double* gp = g + 2 * (((size_t)i * nz + zp) * mm + nm);
+    const double* gm = g + 2 * (((size_t)i * nz + zp + 1) * mm + nm);
+    re += f * (gp[0] + gm[0]);
+    im += f * (gp[1] + gm[1]);
+  }
+  re = block_sum(re, red, th);
+  im = block_sum(im, red, th);
+  if (threadIdx.x == 0) {
+    out[2 * ((size_t)i * n_omega + j)] = coef * re;
+    out[2 * ((size_t)i * n_omega + j) + 1] = coef * im;
+  }
+}
 }  // namespace
 
 cudaError_t launch_syev(int n, double* A, int lda, double* w, double* Z, int ldz, double* work, int* info,
@@ -643,6 +671,12 @@ cudaError_t launch_lz_residues(int n_pdep, int n_v, int n_steps, const double* o
                                double* C, cudaStream_t st) {
   k_lz_residues<<<WGW_G1D((size_t)n_v * n_pdep * n_steps * n_pdep), 256, 0, st>>>(n_pdep, n_v, n_steps, ov, U, beta,
                                                                                    C);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lz_isr(int n_pdep, int n_states, int n_omega, int n_nodes, const double* g, const double* lam,
+                          const double* w, double coef, double* out, cudaStream_t st) {
+  k_lz_isr<<<n_states * n_omega, 256, 0, st>>>(n_pdep, n_states, n_omega, n_nodes, g, lam, w, coef, out);
   return cudaGetLastError();
 }
 

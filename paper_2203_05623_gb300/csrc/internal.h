@@ -175,6 +175,8 @@ cudaError_t launch_lz_normalise(int n, int l, int n_ch, const double* R, double*
                                 double* beta, int n_steps, const double* npart, int nb, cudaStream_t st);
 cudaError_t launch_lz_residues(int n_pdep, int n_v, int n_steps, const double* ov, const double* U, const double* beta,
                                double* C, cudaStream_t st);
+cudaError_t launch_lz_isr(int n_pdep, int n_states, int n_omega, int n_nodes, const double* g, const double* lam,
+                          const double* w, double coef, double* out, cudaStream_t st);
 cudaError_t launch_lz_g0_eval(int n_pdep, int n_v, int n_steps, int n_z, const double* C, const double* d,
                               const double* z, double* g, cudaStream_t st);
 // Q[:, s] += B diag(D) B^T P[:, s] for the systems of a list (Kleinman-Bylander term); B is n x n_proj.

@@ -1333,6 +1333,11 @@ struct LzG0 {
   double* d;         // host outputs, or null
   double* C;
   double* g0;
+  // Eq. ISR by quadrature (optional): z holds w_j +- i w'_k in the order (j, k, +/-).
+  const double* lam = nullptr;      // host, n_nodes x n_pdep x n_pdep
+  const double* weights = nullptr;  // host, n_nodes
+  int n_omega = 0, n_nodes = 0;
+  double* isr = nullptr;            // host output, n_states x n_omega complex
 };
 
 // Lanczos chains of every (state, basis vector) pair.  Without g0: chains of P_c H P_c from
@@ -1476,14 +1481,28 @@ int lanczos_impl(wgw_ctx* c, const double* phi, int npd, int n_steps, const doub
     WGW_CK(launch_lz_residues(npd, n_v, n_steps, ov.as<double>(), U.as<double>(), be.as<double>(), Cd.as<double>(),
                               st));
     if (g0->C) WGW_CK(cudaMemcpyAsync(g0->C, Cd.p, sizeof(double) * nC, cudaMemcpyDeviceToHost, st));
-    if (g0->g0 && g0->n_z > 0) {
+    if ((g0->g0 || g0->isr) && g0->n_z > 0) {
       const size_t ng = (size_t)n_v * g0->n_z * npd * npd;
       WGW_TRY(zd.ensure(sizeof(double) * 2 * g0->n_z));
       WGW_TRY(gd.ensure(sizeof(double) * 2 * ng));
       WGW_CK(cudaMemcpyAsync(zd.p, g0->z, sizeof(double) * 2 * g0->n_z, cudaMemcpyHostToDevice, st));
       WGW_CK(launch_lz_g0_eval(npd, n_v, n_steps, g0->n_z, Cd.as<double>(), dd.as<double>(), zd.as<double>(),
                                gd.as<double>(), st));
-      WGW_CK(cudaMemcpyAsync(g0->g0, gd.p, sizeof(double) * 2 * ng, cudaMemcpyDeviceToHost, st));
+      if (g0->g0) WGW_CK(cudaMemcpyAsync(g0->g0, gd.p, sizeof(double) * 2 * ng, cudaMemcpyDeviceToHost, st));
+      if (g0->isr) {
+        DevBuf lamd, wd, od;
+        const size_t nl = (size_t)g0->n_nodes * npd * npd;
+        WGW_TRY(lamd.ensure(sizeof(double) * nl));
+        WGW_TRY(wd.ensure(sizeof(double) * g0->n_nodes));
+        WGW_TRY(od.ensure(sizeof(double) * 2 * (size_t)n_v * g0->n_omega));
+        WGW_CK(cudaMemcpyAsync(lamd.p, g0->lam, sizeof(double) * nl, cudaMemcpyHostToDevice, st));
+        WGW_CK(cudaMemcpyAsync(wd.p, g0->weights, sizeof(double) * g0->n_nodes, cudaMemcpyHostToDevice, st));
+        WGW_CK(launch_lz_isr(npd, n_v, g0->n_omega, g0->n_nodes, gd.as<double>(), lamd.as<double>(),
+                             wd.as<double>(), 1.0 / c->omega_cell, od.as<double>(), st));
+        WGW_CK(cudaMemcpyAsync(g0->isr, od.p, sizeof(double) * 2 * (size_t)n_v * g0->n_omega,
+                               cudaMemcpyDeviceToHost, st));
+        WGW_CK(cudaStreamSynchronize(st));   // lamd, wd, od leave scope
+      }
     }
     if (g0->d) {
       std::vector<double> dh((size_t)n_ch * n_steps);
@@ -2054,6 +2073,30 @@ int wgw_g0_lanczos(wgw_ctx* c, const double* phi, int n_pdep, const int* states,
   std::lock_guard<std::recursive_mutex> lk(c->mu);
   const LzG0 g{states, n_states, z, n_z, d, residues, g0};
   return lanczos_impl(c, phi, n_pdep, n_steps, nullptr, 0, alpha, beta, nullptr, st, &g);
+}
+
+int wgw_isr(wgw_ctx* c, const double* phi, int n_pdep, const int* states, int n_states, int n_steps,
+            const double* omega, int n_omega, const double* lam, const double* nodes, const double* weights,
+            int n_nodes, double* isr, wgw_stats* st) {
+  g_last_error.clear();
+  if (!c || !phi || n_pdep < 1 || !states || n_states < 1 || n_steps < 1 || n_steps > 255 || n_omega < 1 ||
+      !omega || n_nodes < 1 || !lam || !nodes || !weights || !isr)
+    return fail(WGW_ERR_ARG, "need a context, phi, states, 1 <= n_steps <= 255, frequencies, Lambda and nodes");
+  for (int i = 0; i < n_states; ++i)
+    if (states[i] < 0 || states[i] >= c->n_v) return fail(WGW_ERR_ARG, "state index outside 0..n_v-1");
+  for (int k = 0; k < n_nodes; ++k)
+    if (!(nodes[k] >= 0.0)) return fail(WGW_ERR_ARG, "quadrature nodes must be >= 0");
+  std::vector<double> z;
+  z.reserve(4 * (size_t)n_omega * n_nodes);
+  for (int j = 0; j < n_omega; ++j)
+    for (int k = 0; k < n_nodes; ++k) {
+      z.push_back(omega[j]); z.push_back(nodes[k]);
+      z.push_back(omega[j]); z.push_back(-nodes[k]);
+    }
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  LzG0 g{states, n_states, z.data(), 2 * n_omega * n_nodes, nullptr, nullptr, nullptr};
+  g.lam = lam; g.weights = weights; g.n_omega = n_omega; g.n_nodes = n_nodes; g.isr = isr;
+  return lanczos_impl(c, phi, n_pdep, n_steps, nullptr, 0, nullptr, nullptr, nullptr, st, &g);
 }
 
 int wgw_symm_eig_dev(int n, double* A_dev, double* w_dev, double* Z_dev, void* stream) {

@@ -107,6 +107,8 @@ def lib(path: str | None = None):
                                              _dp, ctypes.POINTER(Stats)]
     L.wgw_apply_h_dev.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                   ctypes.c_void_p]
+    L.wgw_isr.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
+                          _dp, ctypes.c_int, _dp, _dp, _dp, ctypes.c_int, _dp, ctypes.POINTER(Stats)]
     L.wgw_sigma_x.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int, _dp]
     L.wgw_autotune_info.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                     _dp, ctypes.c_int]
@@ -255,6 +257,26 @@ def wgw_apply_h_dev(ctx: Context, psi_dev, out_dev=None, fp32=False, stream=None
                                  ctypes.c_void_p(out_dev.data_ptr()), 1 if fp32 else 0,
                                  ctypes.c_void_p(stream)), "wgw_apply_h_dev")
     return out_dev
+
+
+def wgw_isr(ctx: Context, phi, states, n_steps: int, omega, lam, nodes, weights) -> np.ndarray:
+    """I^SR_i(w) of Eq. ISR by quadrature; returns (n_states, n_omega) complex."""
+    phi = np.asarray(phi, np.complex128)
+    npd = phi.shape[1]
+    sts = np.ascontiguousarray(states, np.int32)
+    om = np.ascontiguousarray(omega, np.float64)
+    lm = np.ascontiguousarray(lam, np.float64)
+    nd = np.ascontiguousarray(nodes, np.float64)
+    wt = np.ascontiguousarray(weights, np.float64)
+    assert lm.shape == (nd.size, npd, npd) and wt.size == nd.size
+    out = np.zeros((sts.size, om.size), np.complex128)
+    st = Stats()
+    pb = _interleave(phi)
+    _check(lib().wgw_isr(ctx.handle, pb.ctypes.data_as(_dp), npd, sts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                         sts.size, n_steps, om.ctypes.data_as(_dp), om.size, lm.ctypes.data_as(_dp),
+                         nd.ctypes.data_as(_dp), wt.ctypes.data_as(_dp), nd.size,
+                         out.view(np.float64).ctypes.data_as(_dp), ctypes.byref(st)), "wgw_isr")
+    return out
 
 
 def wgw_sigma_x(ctx: Context, states) -> np.ndarray:

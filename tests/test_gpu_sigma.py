@@ -52,3 +52,25 @@ def test_sigma_x_rejects_bad_state(W, tiny):
     ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, W.wgw_default_options())
     with pytest.raises(W.WgwError):
         W.wgw_sigma_x(ctx, [s.n_v])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_isr_matches_oracle(W, cfg24, precision):
+    """I^SR of Eq. ISR: the GPU chains, resolvent and quadrature contraction against the oracle's
+    (1e-10 of the largest value), with a Lambda that varies with the node and is not diagonal."""
+    from oracle import sigma as osig
+    s = cfg24
+    m = Model(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v)
+    npd, n_steps = 4, 12
+    phi = synth.perturbations(s.miller_rho, s.L, npd, 91)
+    x, wts = np.polynomial.legendre.leggauss(8)
+    nodes, weights = 5.0 * (x + 1.0), 5.0 * wts
+    rng = np.random.default_rng(92)
+    A = rng.standard_normal((npd, npd))
+    lam = np.array([(A + A.T) / (1.0 + wp) for wp in nodes])
+    states, omegas = [0, 3], [-0.4, 0.35]
+    ref = osig.isr(m, phi, states, n_steps, omegas, lam, nodes, weights)
+    opt = W.wgw_default_options(precision=W.WGW_MIXED if precision == "mixed" else W.WGW_FP64)
+    ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, opt)
+    got = W.wgw_isr(ctx, phi, states, n_steps, omegas, lam, nodes, weights)
+    assert np.max(np.abs(got - ref)) < 1e-10 * np.max(np.abs(ref))
