@@ -36,7 +36,17 @@ result is the closed form -(1/Omega) sum_{j != i} 4 pi / |k_j - k_i|^2; the
 total sum_i <psi_i|Sigma_X|psi_i> is invariant under a unitary rotation of the
 occupied states.  For I^SR: with Lambda = c * identity at every node and exhausted chains, the
 quadrature of the folded integrand over [0, W] converges to the closed form
-(c/Omega) sum_n <b_n| (1/pi) arctan(W / (h - w)) |b_n> evaluated through the eigenpairs of h.
+(c/Omega) sum_n <b_n| (1/pi) arctan(W / (h - w)) |b_n> evaluated through the eigenpairs of h;
+with exhausted chains it equals isr_dense (the exact resolvent of the dense h).
+
+The residue term of Eq. Rfac in the same basis,
+  R_i(w) = (1/Omega) sum_j f_ij(w) sum_nm Lambda_nm(e_j - w) <b_n|j><j|b_m>,
+  f_ij(w) = theta(e_j - e_F) theta(w - e_j) - theta(e_F - e_j) theta(e_j - w),
+runs over the eigenstates j of h with Lambda (the Dyson step on chi0bar projected on the basis)
+at the real frequency e_j - w (reading: the KS energies stand in for the QP energies in f).
+Pin: I^SR jumps by -(1/Omega) sum_nm Lambda_nm(0) <b_n|j><j|b_m> where w crosses e_j, and R jumps
+back, so I^SR + R is continuous there (an occupied and an empty j are tested); a sign error in R
+breaks it.
 """
 from __future__ import annotations
 
@@ -87,3 +97,67 @@ def isr(model: Model, phi: np.ndarray, states, n_steps: int, omegas, lam: np.nda
         s = np.einsum("nm,iwnm->iw", lam[k], G[:, :, k, 0] + G[:, :, k, 1])
         out += weights[k] / (2.0 * np.pi) * s
     return out / model.omega
+
+
+# ---------------------------------------------------------------- residues and dense references
+def chi0_z(model: Model, z: complex) -> np.ndarray:
+    """Dense chi0_GG'(z) on the density sphere at a complex frequency z (the sum over states of
+    oracle/chi0.py with i w replaced by z): (f_s/Omega)[B diag(1/(d - z)) B^H + conj(B-) diag(1/(d + z)) B-^T],
+    d_vc = e_v - e_c."""
+    from .chi0 import _states, pair_densities
+    w, U = _states(model)
+    nv = model.psi_v.shape[1]
+    B = pair_densities(model, U[:, :nv], U[:, nv:])
+    d = (w[:nv, None] - w[None, nv:]).ravel()
+    where = {tuple(m): i for i, m in enumerate(model.mr.tolist())}
+    neg = np.array([where[(-h, -k, -l)] for h, k, l in model.mr.tolist()])
+    Bm = B[neg]
+    chi = (B / (d - z)) @ B.conj().T + (Bm.conj() / (d + z)) @ Bm.T
+    return chi * (model.f_s / model.omega)
+
+
+def lam_basis(model: Model, phi: np.ndarray, z: complex) -> np.ndarray:
+    """Lambda(z) = (1 - chi0bar(z))^-1 chi0bar(z) with chi0bar projected on the basis phi
+    (orthonormal columns on the density sphere): the Dyson step of Sec. 2 in that basis."""
+    phi = np.asarray(phi, np.complex128)
+    pt = model.vsqrt[:, None] * phi
+    X = pt.conj().T @ chi0_z(model, z) @ pt
+    return np.linalg.solve(np.eye(X.shape[0]) - X, X)
+
+
+def _spectral_overlaps(model: Model, phi: np.ndarray, i: int):
+    """Eigenpairs (e, U) of h and the overlaps Y[j, n] = <j | psi_i phi~_n> (b_n of oracle/g0.py)."""
+    from . import g0
+    e, U = np.linalg.eigh(model.h_dense())
+    return e, U.conj().T @ g0.start_vectors(model, phi, i)
+
+
+def isr_dense(model: Model, phi: np.ndarray, i: int, omegas, lam: np.ndarray, nodes, weights) -> np.ndarray:
+    """I^SR_i(w) as sigma.isr, with the exact resolvent sum_j <b_n|j><j|b_m>/(e_j - z) of the
+    dense h in place of the Lanczos chains."""
+    e, Y = _spectral_overlaps(model, phi, i)
+    out = []
+    for w in np.asarray(omegas, np.float64).ravel():
+        acc = 0.0 + 0.0j
+        for k, (wp, wt) in enumerate(zip(np.asarray(nodes).ravel(), np.asarray(weights).ravel())):
+            g = (Y.conj() / (e - w - 1j * wp)[:, None]).T @ Y + (Y.conj() / (e - w + 1j * wp)[:, None]).T @ Y
+            acc += wt / (2.0 * np.pi) * np.sum(lam[k] * g)
+        out.append(acc / model.omega)
+    return np.asarray(out)
+
+
+def residue_term(model: Model, phi: np.ndarray, i: int, omegas, e_fermi: float, eta: float = 0.0) -> np.ndarray:
+    """R_i(w) of Eq. Rfac in the basis: (1/Omega) sum_j f_ij(w) sum_nm Lambda_nm(e_j - w) <b_n|j><j|b_m>,
+    f_ij(w) = theta(e_j - e_F) theta(w - e_j) - theta(e_F - e_j) theta(e_j - w), over every
+    eigenstate j of h (Lambda at the real frequency e_j - w, plus i eta)."""
+    e, Y = _spectral_overlaps(model, phi, i)
+    out = []
+    for w in np.asarray(omegas, np.float64).ravel():
+        acc = 0.0 + 0.0j
+        for j in range(e.size):
+            f = (1.0 if (e[j] > e_fermi and w > e[j]) else 0.0) - (1.0 if (e[j] <= e_fermi and e[j] > w) else 0.0)
+            if f != 0.0:
+                A = np.outer(Y[j].conj(), Y[j])                 # <b_n|j><j|b_m>
+                acc += f * np.sum(lam_basis(model, phi, e[j] - w + 1j * eta) * A)
+        out.append(acc / model.omega)
+    return np.asarray(out)

@@ -506,3 +506,70 @@ def test_isr_quadrature_converges_to_arctan_closed_form(tiny):
                     for w in omegas])
     assert np.max(np.abs(got[0] - ref)) < 1e-9 * np.max(np.abs(ref))
     assert np.max(np.abs(got.imag)) < 1e-12 * np.max(np.abs(ref))
+
+
+def _real_orthonormal_basis(s, n, seed):
+    Q, _ = np.linalg.qr(synth.perturbations(s.miller_rho, s.L, n, seed))
+    return Q
+
+
+def test_isr_lanczos_equals_dense_resolvent(tiny):
+    """I^SR with exhausted G0 chains equals I^SR with the exact resolvent of the dense h."""
+    m = model_of(tiny)
+    phi = _real_orthonormal_basis(tiny, 2, 83)
+    x, wts = np.polynomial.legendre.leggauss(24)
+    nodes, weights = 4.0 * (x + 1.0), 4.0 * wts
+    lam = np.array([sigma.lam_basis(m, phi, 1j * wp).real for wp in nodes])
+    omegas = [-0.9, 0.05, 0.6]
+    a = sigma.isr(m, phi, [0], m.mw.shape[0], omegas, lam, nodes, weights)[0]
+    b = sigma.isr_dense(m, phi, 0, omegas, lam, nodes, weights)
+    assert np.max(np.abs(a - b)) < 1e-11 * np.max(np.abs(b))
+
+
+@pytest.mark.parametrize("j_of", ["lumo", "homo"])
+def test_contour_deformation_terms_continuous_across_a_pole(tiny, j_of):
+    """Eq. sigmacIR: I(w) jumps by -(1/Omega) sum_nm Lambda_nm(0) <b_n|j><j|b_m> where w crosses an
+    eigenvalue e_j of h, and the residue term R(w) (Eq. Rfac) jumps back: I + R is continuous."""
+    m = model_of(tiny)
+    phi = _real_orthonormal_basis(tiny, 2, 84)
+    e = np.linalg.eigvalsh(m.h_dense())
+    nv = tiny.n_v
+    ej = e[nv] if j_of == "lumo" else e[nv - 1]
+    e_fermi = 0.5 * (e[nv - 1] + e[nv])
+    edges = [0.0, 1e-7, 1e-6, 1e-5, 1e-4, 1e-3, 1e-2, 0.1, 1.0, 10.0, 60.0]
+    x, wts = np.polynomial.legendre.leggauss(60)
+    nodes = np.concatenate([a + 0.5 * (b - a) * (x + 1.0) for a, b in zip(edges[:-1], edges[1:])])
+    weights = np.concatenate([0.5 * (b - a) * wts for a, b in zip(edges[:-1], edges[1:])])
+    lam = np.array([sigma.lam_basis(m, phi, 1j * wp) for wp in nodes])
+    d = 1e-6
+    om = [ej - d, ej + d]
+    i_ = sigma.isr_dense(m, phi, 0, om, lam, nodes, weights)
+    r_ = sigma.residue_term(m, phi, 0, om, e_fermi)
+    _, Y = sigma._spectral_overlaps(m, phi, 0)
+    jj = np.where(np.abs(e - ej) < 1e-9)[0]
+    A = sum(np.outer(Y[j].conj(), Y[j]) for j in jj)
+    jump = -np.sum(sigma.lam_basis(m, phi, 0.0) * A) / m.omega
+    assert abs(jump) > 1e-8
+    assert abs((i_[1] - i_[0]) - jump) < 1e-3 * abs(jump)
+    assert abs((i_[1] + r_[1]) - (i_[0] + r_[0])) < 1e-3 * abs(jump)
+
+
+def test_planted_residue_sign_error_breaks_continuity(tiny, monkeypatch):
+    m = model_of(tiny)
+    phi = _real_orthonormal_basis(tiny, 2, 84)
+    e = np.linalg.eigvalsh(m.h_dense())
+    nv = tiny.n_v
+    ej, e_fermi = e[nv], 0.5 * (e[nv - 1] + e[nv])
+    edges = [0.0, 1e-7, 1e-6, 1e-5, 1e-4, 1e-3, 1e-2, 0.1, 1.0, 10.0, 60.0]
+    x, wts = np.polynomial.legendre.leggauss(60)
+    nodes = np.concatenate([a + 0.5 * (b - a) * (x + 1.0) for a, b in zip(edges[:-1], edges[1:])])
+    weights = np.concatenate([0.5 * (b - a) * wts for a, b in zip(edges[:-1], edges[1:])])
+    lam = np.array([sigma.lam_basis(m, phi, 1j * wp) for wp in nodes])
+    om = [ej - 1e-6, ej + 1e-6]
+    real = sigma.residue_term
+    monkeypatch.setattr(sigma, "residue_term", lambda *a, **k: -real(*a, **k))
+    i_ = sigma.isr_dense(m, phi, 0, om, lam, nodes, weights)
+    r_ = sigma.residue_term(m, phi, 0, om, e_fermi)
+    monkeypatch.undo()
+    jump = i_[1] - i_[0]
+    assert abs((i_[1] + r_[1]) - (i_[0] + r_[0])) > 0.5 * abs(jump)
