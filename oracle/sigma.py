@@ -47,6 +47,10 @@ at the real frequency e_j - w (reading: the KS energies stand in for the QP ener
 Pin: I^SR jumps by -(1/Omega) sum_nm Lambda_nm(0) <b_n|j><j|b_m> where w crosses e_j, and R jumps
 back, so I^SR + R is continuous there (an occupied and an empty j are tested); a sign error in R
 breaks it.
+
+The QP equation (Eq. e_qp) is solved by secant root finding (qp_energy); reading: the model
+Hamiltonian has no exchange-correlation potential, so <v_xc> = 0 unless given.  Pin: a one-pole
+self-energy whose QP equation is a quadratic with a closed-form root.
 """
 from __future__ import annotations
 
@@ -161,3 +165,25 @@ def residue_term(model: Model, phi: np.ndarray, i: int, omegas, e_fermi: float, 
                 acc += f * np.sum(lam_basis(model, phi, e[j] - w + 1j * eta) * A)
         out.append(acc / model.omega)
     return np.asarray(out)
+
+
+# ---------------------------------------------------------------- quasiparticle equation (Eq. e_qp)
+def secant(f, x0: float, x1: float, tol: float = 1e-10, max_iter: int = 100) -> float:
+    """Root of f by the secant method from x0, x1 (Sec. 3: the QP equation is solved with a
+    root-finding algorithm such as the secant method)."""
+    f0, f1 = f(x0), f(x1)
+    for _ in range(max_iter):
+        if f1 == f0:
+            break
+        x2 = x1 - f1 * (x1 - x0) / (f1 - f0)
+        x0, f0 = x1, f1
+        x1, f1 = x2, f(x2)
+        if abs(x1 - x0) <= tol * max(1.0, abs(x1)):
+            return x1
+    raise RuntimeError("secant did not converge")
+
+
+def qp_energy(e_i: float, sigma_of_e, v_xc: float = 0.0, tol: float = 1e-10) -> float:
+    """e^QP = e_i + Re <psi_i|Sigma(e^QP)|psi_i> - <psi_i|v_xc|psi_i> (Eq. e_qp), by secant from e_i.
+    sigma_of_e(E) returns <psi_i|Sigma(E)|psi_i>."""
+    return secant(lambda E: e_i + np.real(sigma_of_e(E)) - v_xc - E, e_i, e_i + 0.01, tol)

@@ -573,3 +573,16 @@ def test_planted_residue_sign_error_breaks_continuity(tiny, monkeypatch):
     monkeypatch.undo()
     jump = i_[1] - i_[0]
     assert abs((i_[1] + r_[1]) - (i_[0] + r_[0])) > 0.5 * abs(jump)
+
+
+def test_qp_secant_solves_a_pole_model_exactly():
+    """Sigma(E) = a + b / (E - c) (one pole): e_i + Re Sigma(E) - E = 0 is a quadratic whose root
+    near e_i is known in closed form; the secant solve reaches it."""
+    e_i, a, b, c = -0.3, -0.05, 0.02, 0.4
+    E = sigma.qp_energy(e_i, lambda E: a + b / (E - c))
+    # (e_i + a - E)(E - c) + b = 0  ->  E^2 - (e_i + a + c) E + c (e_i + a) - b = 0
+    p, q = e_i + a + c, c * (e_i + a) - b
+    roots = np.array([(p - np.sqrt(p * p - 4 * q)) / 2, (p + np.sqrt(p * p - 4 * q)) / 2])
+    ref = roots[np.argmin(np.abs(roots - e_i))]
+    assert abs(E - ref) < 1e-10
+    assert abs(e_i + a + b / (E - c) - E) < 1e-10
