@@ -20,9 +20,13 @@ Readings:
                      [1/(e_v - d_l' - i w) + 1/(e_v - d_l' + i w)].
   * Full reorthogonalisation: two classical Gram-Schmidt passes per step.
 
+chi0_pdep_z evaluates the same chains at complex frequencies z (z = w + i eta: a real
+frequency with a broadening, as the residue term of Eq. Rfac needs).
+
 Pins: the moment identity <q1|A^k|q1> = (T^k)_11 for k < 2 n_steps,
 orthonormality of Q, eig(T) = eig of P_c h P_c on range(P_c) when the chain
-spans it, and chi0_nm(Lanczos) = chi0_nm(sum over states) in that limit.
+spans it, and chi0_nm(Lanczos) = chi0_nm(sum over states) in that limit, at imaginary and
+at complex frequencies inside and beyond the gap.
 """
 from __future__ import annotations
 
@@ -98,3 +102,27 @@ def chi0_pdep_sos(model: Model, phi: np.ndarray, omegas):
     phi = np.asarray(phi, np.complex128)
     drho = sos_drho(model, model.vsqrt[:, None] * phi, omegas)   # (N_rho, npd, n_omega)
     return np.einsum("gn,gmk->nmk", (model.vsqrt[:, None] * phi).conj(), drho)
+
+
+def chi0_pdep_z(model: Model, phi: np.ndarray, zs, n_steps: int) -> np.ndarray:
+    """chi0_nm(z) in the basis phi at complex frequencies z from the same chains as chi0_pdep:
+    the i w of Eq. lanczos replaced by z, g = 1/(e_v - d - z) + 1/(e_v - d + z) (z = i w gives
+    chi0_pdep; z = w + i eta gives the response at a real frequency w with a broadening eta).
+    Returns shape (n_pdep, n_pdep, n_z)."""
+    phi = np.asarray(phi, np.complex128)
+    zs = np.asarray(zs, np.complex128).ravel()
+    nv = model.psi_v.shape[1]
+    npd = phi.shape[1]
+    out = np.zeros((npd, npd, zs.size), np.complex128)
+    for v in range(nv):
+        pv = model.to_r(model.psi_v[:, v], model.mw)
+        S = np.stack([_pc(model, model.to_G(model.to_r(model.vsqrt * phi[:, n], model.mr) * pv, model.mw))
+                      for n in range(npd)], axis=1)
+        for m in range(npd):
+            alpha, beta, Q = chain(model, S[:, m], n_steps)
+            d, U = tridiag_eig(alpha, beta)
+            ov = S.conj().T @ Q
+            for k, z in enumerate(zs):
+                g = 1.0 / (model.e_v[v] - d - z) + 1.0 / (model.e_v[v] - d + z)
+                out[:, m, k] += beta[0] * (ov @ (U @ (g * U[0, :])))
+    return out * (model.f_s / model.omega)

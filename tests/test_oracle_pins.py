@@ -586,3 +586,19 @@ def test_qp_secant_solves_a_pole_model_exactly():
     ref = roots[np.argmin(np.abs(roots - e_i))]
     assert abs(E - ref) < 1e-10
     assert abs(e_i + a + b / (E - c) - E) < 1e-10
+
+
+def test_lanczos_chi0_at_complex_frequency(tiny):
+    """chi0_pdep_z: z = i w reproduces chi0_pdep; with chains spanning range(P_c), z = w + i eta at a
+    real w (inside and beyond the gap) equals the dense sum over states at that z."""
+    m = model_of(tiny)
+    phi = synth.perturbations(tiny.miller_rho, tiny.L, 2, 85)
+    n_full = m.mw.shape[0] - m.psi_v.shape[1]
+    a = lanczos.chi0_pdep_z(m, phi, [0.7j], 6)[:, :, 0]
+    b = lanczos.chi0_pdep(m, phi, [0.7], 6)[0][:, :, 0]
+    assert rel(a, b) < 1e-13
+    pt = m.vsqrt[:, None] * phi
+    for z in (0.1 + 0.01j, 1.3 + 0.05j):
+        got = lanczos.chi0_pdep_z(m, phi, [z], n_full)[:, :, 0]
+        ref = pt.conj().T @ sigma.chi0_z(m, z) @ pt
+        assert rel(got, ref) < 1e-10, z
