@@ -271,10 +271,15 @@ int wgw_symm_eig_dev(int n, double* A_dev, double* w_dev, double* Z_dev, void* s
  * memory is all reserved up front by another allocator, or code that must not pay for the
  * device-wide synchronisation a cudaMalloc/cudaFree implies).  Same arguments, result and
  * error codes as wgw_symm_eig_dev, for 1 <= n <= 512; larger n returns WGW_ERR_ARG.
- * Its work space is one fixed array in device memory (about 2.1 MB) that every GPU loading
- * the library keeps until the process exits.  The first call on a device looks up that
- * array's device address (with the device current), so make that first call before any
- * stream capture.  All calls share the array: calls whose work overlaps on a GPU (different
+ * Its work space is one fixed array in device memory (about 2.1 MB), part of the library's
+ * device code: it comes into existence on a GPU when that code is loaded there, which wgw_setup
+ * does for the device it runs on and the first call of this function does otherwise, and it
+ * stays until the process exits.  Loading takes device memory, so a caller that reserves all
+ * device memory up front should create a context with wgw_setup, or make one call (n = 1 will
+ * do), on that device first.  The first call on a device (in a CUDA context) also looks up the
+ * array's device address with the device current, so make that first call before any stream
+ * capture.  The call returns once its stream has finished the work (it reads the solver's
+ * status back).  All calls share the array: calls whose work overlaps on a GPU (different
  * streams or host threads at the same time) race and must be serialised by the caller.
  */
 int wgw_symm_eig_noalloc_dev(int n, double* A_dev, double* w_dev, double* Z_dev, void* stream);

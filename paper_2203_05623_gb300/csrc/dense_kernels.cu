@@ -5,6 +5,8 @@
 #include <cmath>
 #include <mutex>
 
+#include <cuda.h>   // CUcontext / CUresult types only
+
 #include "../../include/wgw.h"
 #include "internal.h"
 
@@ -794,8 +796,9 @@ cudaError_t launch_dyson(int n, int n_omega, const double* A, double* X, double*
 
 // ---------------------------------------------------------------- scratch-free variant
 // Work space of wgw_symm_eig_noalloc_dev: a file-scope device array sized for the largest
-// accepted n.  Every GPU that loads the library holds it (about 2.1 MB) until the process
-// exits, and every call shares it.
+// accepted n (about 2.1 MB).  It exists on a GPU once this file's device code is loaded there
+// (wgw_setup on that device loads it, and so does the first call of the entry point), stays
+// until the process exits, and is shared by every call.
 namespace {
 
 constexpr int kNoAllocMaxN = 512;
@@ -804,29 +807,68 @@ static __device__ __align__(256) double g_syev_scratch[kNoAllocElems];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
-double* g_scratch_ptr[kMaxDevices] = {};
+// Per device: the array's device address and the CUDA context it was looked up in.  A context
+// created after a cudaDeviceReset (or another context made current through the driver API)
+// holds its own copy of the array, so a different current context means a fresh lookup.
+struct ScratchSlot {
+  CUcontext ctx = nullptr;
+  double* ptr = nullptr;
+};
+ScratchSlot g_scratch[kMaxDevices];
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+
+// The context current on the calling thread (null if none), through the driver entry point the
+// runtime hands out, so the library needs no link against the driver library.
+CUcontext current_context() {
+  static CtxGetCurrentFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGetCurrentFn>(p);
+  });
+  CUcontext c = nullptr;
+  if (fn && fn(&c) != CUDA_SUCCESS) c = nullptr;
+  return c;
+}
 
 // Device address of g_syev_scratch on the current device.  The host-side symbol is only a
-// stand-in and must never reach a kernel; the address is looked up once per device (with
-// that device current) and cached.
+// stand-in and must never reach a kernel; the address is looked up with the device current
+// (which also loads this file's device code there if nothing has yet) and cached per device
+// and context.
 int scratch_address(double** out) {
   int dev = -1;
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return wgw::report_error(WGW_ERR_CUDA, cudaGetErrorString(err));
   if (dev < 0 || dev >= kMaxDevices) return wgw::report_error(WGW_ERR_STATE, "device index out of range");
+  const CUcontext cur = current_context();
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
+  ScratchSlot& slot = g_scratch[dev];
+  if (!slot.ptr || !cur || cur != slot.ctx) {
     void* p = nullptr;
     err = cudaGetSymbolAddress(&p, g_syev_scratch);
     if (err != cudaSuccess || !p)
       return wgw::report_error(WGW_ERR_CUDA, "cudaGetSymbolAddress of the eigensolver scratch failed");
-    g_scratch_ptr[dev] = static_cast<double*>(p);
+    slot.ptr = static_cast<double*>(p);
+    slot.ctx = current_context();
   }
-  *out = g_scratch_ptr[dev];
+  *out = slot.ptr;
   return WGW_OK;
 }
 
 }  // namespace
+
+namespace wgw {
+// Loads the scratch-free eigensolver's work array on the current device and caches its address
+// (called by wgw_setup, so that a context's device is prepared before its memory fills up).
+int noalloc_prepare() {
+  double* p = nullptr;
+  return scratch_address(&p);
+}
+}  // namespace wgw
 
 extern "C" int wgw_symm_eig_noalloc_dev(int n, double* A_dev, double* w_dev, double* Z_dev, void* stream) {
   wgw::clear_error();

@@ -222,6 +222,9 @@ cudaError_t launch_norm2(int n_sys, int n, const T* x, long ld, double* out, cud
 cudaError_t launch_to_ff(size_t n, const double* in, double* out, cudaStream_t st);
 // X = (1 - A)^-1 A per n x n row-major matrix of a batch (dense_kernels.cu); M: work of the same size.
 cudaError_t launch_dyson(int n, int n_omega, const double* A, double* X, double* M, int* info, cudaStream_t st);
+// Loads the work array of wgw_symm_eig_noalloc_dev on the current device and caches its device
+// address (dense_kernels.cu); returns a WGW status.
+int noalloc_prepare();
 // Count of nonzero entries of flags[0..n) into *out (one block).
 cudaError_t launch_count(const int* flags, int n, int* out, cudaStream_t st);
 

@@ -473,19 +473,27 @@ int cg_solve(wgw_ctx* c, Prec<T>& pr, int n_sys, double tol, int max_iter, cudaS
   const cudaStream_t gst = side ? c->stream : st;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   if (graphs && side) {
-    WGW_CK(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
-    WGW_CK(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
+    cudaError_t ee = cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming);
+    if (ee == cudaSuccess) ee = cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming);
+    if (ee != cudaSuccess) {
+      if (ev_in) cudaEventDestroy(ev_in);
+      return fail(WGW_ERR_CUDA, cudaGetErrorString(ee));
+    }
   }
   cudaGraphExec_t exec = nullptr;
   int status = WGW_OK;
   for (int it = 0; it < max_iter && n_list > 0;) {
     const int w = std::min(every - it % every, max_iter - it);
     if (graphs && it > 0) {
+      // Failures set status and leave the loop, so that the executable graph and the events
+      // are destroyed below on every path.
+      cudaError_t pe = cudaSuccess;
       if (side) {
-        WGW_CK(cudaEventRecord(ev_in, st));
-        WGW_CK(cudaStreamWaitEvent(gst, ev_in, 0));
+        pe = cudaEventRecord(ev_in, st);
+        if (pe == cudaSuccess) pe = cudaStreamWaitEvent(gst, ev_in, 0);
       }
-      WGW_CK(cudaStreamBeginCapture(gst, cudaStreamCaptureModeRelaxed));
+      if (pe == cudaSuccess) pe = cudaStreamBeginCapture(gst, cudaStreamCaptureModeRelaxed);
+      if (pe != cudaSuccess) { status = fail(WGW_ERR_CUDA, cudaGetErrorString(pe)); break; }
       const int rc = window(it, w, gst);
       cudaGraph_t g = nullptr;
       const cudaError_t ce = cudaStreamEndCapture(gst, &g);
@@ -507,12 +515,12 @@ int cg_solve(wgw_ctx* c, Prec<T>& pr, int n_sys, double tol, int max_iter, cudaS
         }
       }
       cudaGraphDestroy(g);
-      const cudaError_t le = cudaGraphLaunch(exec, gst);
-      if (le != cudaSuccess) { status = fail(WGW_ERR_CUDA, cudaGetErrorString(le)); break; }
-      if (side) {
-        WGW_CK(cudaEventRecord(ev_out, gst));
-        WGW_CK(cudaStreamWaitEvent(st, ev_out, 0));
+      cudaError_t le = cudaGraphLaunch(exec, gst);
+      if (le == cudaSuccess && side) {
+        le = cudaEventRecord(ev_out, gst);
+        if (le == cudaSuccess) le = cudaStreamWaitEvent(st, ev_out, 0);
       }
+      if (le != cudaSuccess) { status = fail(WGW_ERR_CUDA, cudaGetErrorString(le)); break; }
     } else {
       status = window(it, w, st);
       if (status != WGW_OK) break;
@@ -1610,6 +1618,7 @@ static int setup_impl(wgw_ctx* c, const double* vloc_G, const double* psi_v, con
   WGW_TRY(upload_sphere(c->rho));
   WGW_CK(cudaGetDevice(&c->device));
   WGW_CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+  WGW_TRY(noalloc_prepare());
   cudaStream_t st = c->stream;
   // Twiddles exp(+2 pi i k / N).
   std::vector<cplx<double>> twd(N);
