@@ -46,7 +46,13 @@ runs over the eigenstates j of h with Lambda (the Dyson step on chi0bar projecte
 at the real frequency e_j - w (reading: the KS energies stand in for the QP energies in f).
 Pin: I^SR jumps by -(1/Omega) sum_nm Lambda_nm(0) <b_n|j><j|b_m> where w crosses e_j, and R jumps
 back, so I^SR + R is continuous there (an occupied and an empty j are tested); a sign error in R
-breaks it.
+breaks it.  Reading of the overall sign: Eq. Ifac carries a leading minus in front of G0 W_p, and
+with G0(z) = (z - h)^-1 that minus makes -G0(z) = (h - z)^-1, the operator Eq. ISR writes without a
+minus; the two equations agree and I^SR is evaluated with (h - z)^-1.  Pin of that sign: with a
+frequency-independent W_p (Lambda = c * identity at every frequency) I + R is the static COHSEX
+closed form (c/Omega) sum_j sum_n |<j|b_n>|^2 (1/2 - theta(e_F - e_j)), a Coulomb hole of +1/2 over
+every state and a screened exchange of -1 over the occupied ones, the same sign as the exchange
+sum -sum_{j occ} of Sigma_X; a sign error in I or in R breaks it.
 
 The QP equation (Eq. e_qp) is solved by secant root finding (qp_energy); reading: the model
 Hamiltonian has no exchange-correlation potential, so <v_xc> = 0 unless given.  Pin: a one-pole
@@ -150,10 +156,15 @@ def isr_dense(model: Model, phi: np.ndarray, i: int, omegas, lam: np.ndarray, no
     return np.asarray(out)
 
 
-def residue_term(model: Model, phi: np.ndarray, i: int, omegas, e_fermi: float, eta: float = 0.0) -> np.ndarray:
+def residue_term(model: Model, phi: np.ndarray, i: int, omegas, e_fermi: float, eta: float = 0.0,
+                 lam_fn=None) -> np.ndarray:
     """R_i(w) of Eq. Rfac in the basis: (1/Omega) sum_j f_ij(w) sum_nm Lambda_nm(e_j - w) <b_n|j><j|b_m>,
     f_ij(w) = theta(e_j - e_F) theta(w - e_j) - theta(e_F - e_j) theta(e_j - w), over every
-    eigenstate j of h (Lambda at the real frequency e_j - w, plus i eta)."""
+    eigenstate j of h (Lambda at the real frequency e_j - w, plus i eta).  lam_fn(z) gives
+    Lambda(z) in the basis; by default the Dyson step on the basis (lam_basis)."""
+    if lam_fn is None:
+        def lam_fn(z):
+            return lam_basis(model, phi, z)
     e, Y = _spectral_overlaps(model, phi, i)
     out = []
     for w in np.asarray(omegas, np.float64).ravel():
@@ -162,7 +173,7 @@ def residue_term(model: Model, phi: np.ndarray, i: int, omegas, e_fermi: float, 
             f = (1.0 if (e[j] > e_fermi and w > e[j]) else 0.0) - (1.0 if (e[j] <= e_fermi and e[j] > w) else 0.0)
             if f != 0.0:
                 A = np.outer(Y[j].conj(), Y[j])                 # <b_n|j><j|b_m>
-                acc += f * np.sum(lam_basis(model, phi, e[j] - w + 1j * eta) * A)
+                acc += f * np.sum(lam_fn(e[j] - w + 1j * eta) * A)
         out.append(acc / model.omega)
     return np.asarray(out)
 

@@ -53,6 +53,26 @@ def test_lanczos_coefficients_and_chi0_match_oracle(W, cfg24, precision):
     assert np.max(np.abs(ref_chi.imag)) < 1e-14 * np.max(np.abs(ref_chi))
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_lanczos_full_frequency_config_sizes(W, cfg24, precision):
+    """The full-frequency configuration at its stated sizes: 32 basis vectors x 4 occupied states
+    = 128 chains of 64 steps, chi0 in the basis at the 32 Gauss-Legendre frequencies on
+    [0, 50 Ha].  alpha, beta element-wise and chi0_nm(i w_k) at every frequency against the
+    oracle's chains (1e-10; both paths keep the chains at FP64 accuracy)."""
+    s = cfg24
+    phi = synth.perturbations(s.miller_rho, s.L, 32, 24)
+    oms, _ = synth.gauss_legendre_omega(32, 50.0)
+    n_steps = 64
+    ref_chi, ref_a, ref_b = lanczos.chi0_pdep(model_of(s), phi, oms, n_steps)
+    chi, a, b, st = W.wgw_lanczos(_setup_full(W, s, precision), phi, n_steps, oms)
+    assert st["n_systems"] == 128 and a.shape == (s.n_v, 32, n_steps)
+    assert np.max(np.abs(a - ref_a)) < 1e-10 * np.max(np.abs(ref_a))
+    assert np.max(np.abs(b - ref_b) / np.maximum(np.abs(ref_b), 1e-30)) < 1e-10
+    for k in range(len(oms)):
+        assert np.max(np.abs(chi[:, :, k] - ref_chi[:, :, k].real)) < 1e-10 * np.max(np.abs(ref_chi[:, :, k])), k
+
+
 def test_lanczos_exact_limit_equals_sum_over_states(W, tiny):
     s = tiny
     phi = synth.perturbations(s.miller_rho, s.L, 3, 22)

@@ -75,6 +75,29 @@ def test_queued_requests_match_oracle_and_sync(W, cfg24):
     assert merged >= 1
 
 
+def test_queued_requests_mixed_path_alone_and_in_the_mix(W, cfg24):
+    """Mixed path (FP32 inner CG on the tensor-core projector, float-float refinement): each
+    request's result in a merged batch equals the oracle and its own result alone within the
+    path's tolerance 1e-8, although the batch composition changes the list compaction and the
+    projector's K split."""
+    s = cfg24
+    ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v,
+                      W.wgw_default_options(precision=W.WGW_MIXED, cg_tol=1e-11))
+    m = model_of(s)
+    reqs = [(synth.perturbations(s.miller_rho, s.L, 2 + k % 3, 200 + k), [0.0] if k % 2 else [0.0, 0.6])
+            for k in range(8)]
+    alone = [W.wgw_apply_chi0(ctx, dV, om)[0] for dV, om in reqs]
+    tickets = [W.wgw_submit(ctx, dV, om) for dV, om in reqs]
+    merged = 0
+    for (dV, om), t, a in zip(reqs, tickets, alone):
+        got, res = W.wgw_wait(t)
+        assert res["status"] == W.WGW_OK
+        merged = max(merged, res["batch_requests"])
+        assert rel_err(got, chi0.sos_drho(m, dV, om)) < 1e-8
+        assert rel_err(got, a) < 1e-8
+    assert merged >= 2
+
+
 def test_two_contexts_overlap_and_poll(W, cfg24, tiny):
     c1, c2 = ctx_of(W, cfg24), ctx_of(W, tiny)
     d1 = synth.perturbations(cfg24.miller_rho, cfg24.L, 3, 7)

@@ -554,6 +554,69 @@ def test_contour_deformation_terms_continuous_across_a_pole(tiny, j_of):
     assert abs((i_[1] + r_[1]) - (i_[0] + r_[0])) < 1e-3 * abs(jump)
 
 
+def _half_line_quadrature(n=60):
+    """Nodes and weights for int_0^inf: composite Gauss-Legendre panels on [0, 100] refined
+    towards 0, and the tail [100, inf) mapped onto (0, 1] by w' = 100 / u."""
+    edges = [0.0, 1e-4, 1e-3, 1e-2, 0.1, 1.0, 10.0, 100.0]
+    x, wts = np.polynomial.legendre.leggauss(n)
+    nodes = [a + 0.5 * (b - a) * (x + 1.0) for a, b in zip(edges[:-1], edges[1:])]
+    weights = [0.5 * (b - a) * wts for a, b in zip(edges[:-1], edges[1:])]
+    u = 0.5 * (x + 1.0)
+    nodes.append(100.0 / u)
+    weights.append(0.5 * wts * 100.0 / u ** 2)
+    return np.concatenate(nodes), np.concatenate(weights)
+
+
+@pytest.mark.parametrize("where", ["gap", "below", "inside_occupied", "above_lumo"])
+def test_static_screening_gives_cohsex_closed_form(tiny, where):
+    """Frequency-independent W_p (Lambda = c * identity at every frequency): I + R of Eq. sigmacIR
+    is the static COHSEX self-energy (c/Omega) sum_j sum_n |<j|b_n>|^2 (1/2 - theta(e_F - e_j)),
+    whatever w: a Coulomb hole of +1/2 over every eigenstate j of h and a screened exchange of -1
+    over the occupied ones (the sign of the exchange sum of Sigma_X).  Pins the overall sign of the
+    imaginary-axis integral of Eq. Ifac / Eq. ISR and of the residue term of Eq. Rfac."""
+    m = model_of(tiny)
+    phi = _real_orthonormal_basis(tiny, 2, 86)
+    e = np.linalg.eigvalsh(m.h_dense())
+    nv = tiny.n_v
+    e_fermi = 0.5 * (e[nv - 1] + e[nv])
+    w = {"gap": e_fermi, "below": e[0] - 0.5, "inside_occupied": 0.5 * (e[0] + e[1]),
+         "above_lumo": 0.5 * (e[nv] + e[nv + 1])}[where]
+    assert np.min(np.abs(e - w)) > 1e-3
+    c = 0.3
+    nodes, weights = _half_line_quadrature()
+    lam = np.broadcast_to(c * np.eye(2), (nodes.size, 2, 2))
+    i_ = sigma.isr_dense(m, phi, 0, [w], lam, nodes, weights)[0]
+    r_ = sigma.residue_term(m, phi, 0, [w], e_fermi, lam_fn=lambda z: c * np.eye(2))[0]
+    _, Y = sigma._spectral_overlaps(m, phi, 0)
+    weight = np.where(e <= e_fermi, -0.5, 0.5)
+    ref = c / m.omega * np.sum(np.abs(Y) ** 2 * weight[:, None])
+    assert abs(ref) > 1e-6
+    assert abs((i_ + r_) - ref) < 1e-8 * abs(ref), (i_, r_, ref)
+    # The screened-exchange part alone carries the sign of Sigma_X: -(c/Omega) sum_occ |<j|b>|^2.
+    sex = -c / m.omega * np.sum(np.abs(Y[:nv]) ** 2)
+    coh = 0.5 * c / m.omega * np.sum(np.abs(Y) ** 2)
+    assert abs((sex + coh) - ref) < 1e-12 * abs(ref) and sex < 0
+
+
+def test_planted_integral_sign_error_fails_cohsex_pin(tiny, monkeypatch):
+    m = model_of(tiny)
+    phi = _real_orthonormal_basis(tiny, 2, 86)
+    e = np.linalg.eigvalsh(m.h_dense())
+    nv = tiny.n_v
+    e_fermi = 0.5 * (e[nv - 1] + e[nv])
+    c = 0.3
+    nodes, weights = _half_line_quadrature()
+    lam = np.broadcast_to(c * np.eye(2), (nodes.size, 2, 2))
+    real = sigma.isr_dense
+    monkeypatch.setattr(sigma, "isr_dense", lambda *a, **k: -real(*a, **k))
+    i_ = sigma.isr_dense(m, phi, 0, [e_fermi], lam, nodes, weights)[0]
+    monkeypatch.undo()
+    r_ = sigma.residue_term(m, phi, 0, [e_fermi], e_fermi, lam_fn=lambda z: c * np.eye(2))[0]
+    _, Y = sigma._spectral_overlaps(m, phi, 0)
+    ref = c / m.omega * np.sum(np.abs(Y) ** 2 * np.where(e <= e_fermi, -0.5, 0.5)[:, None])
+    assert abs((i_ + r_) - ref) > 0.1 * abs(ref)
+
+
 def test_planted_residue_sign_error_breaks_continuity(tiny, monkeypatch):
     m = model_of(tiny)
     phi = _real_orthonormal_basis(tiny, 2, 84)
