@@ -50,6 +50,11 @@ WORKLOADS = {
                              "split by +-0.2 Ha, 64 up + 62 down occupied states x 64 perturbations = "
                              "8064 Sternheimer systems, one context per channel (f_s = 1) run "
                              "concurrently, mixed FP32/FP64"),
+    "kb_L24_96": dict(config="kb_L24_96", n_pert=256, pert_seed=5, cg_tol=1e-10,
+                      desc="chibar0 block apply on the 96^3 model with Kleinman-Bylander projectors: "
+                           "256 perturbations x 256 occupied states = 65536 Sternheimer systems, "
+                           "N_pw=30095, N_rho=240417, 64 atoms x (well + s,p projectors) = 256 "
+                           "projectors, mixed FP32/FP64, device-memory chunks of whole perturbations"),
     "chi0_L10_24": dict(config="chi0_L10_24", n_pert=8, pert_seed=2, cg_tol=1e-10,
                         desc="chi0 apply, 8 perturbations x 4 occupied states = 32 Sternheimer systems, "
                              "24^3 grid, N_pw=515, N_rho=4337, mixed FP32/FP64"),
@@ -132,12 +137,14 @@ class Clocks:
 _CPU_STATE = {}
 
 
-def _cpu_init(L, ecut, grid, vloc_G, psi_v, e_v, miller_rho, n_pert, pert_seed, cg_tol):
-    """Worker set-up: the model and perturbations of the workload (host only)."""
+def _cpu_init(config, n_pert, pert_seed, cg_tol):
+    """Worker set-up: the model and perturbations of the workload (host only; the ground state
+    comes from the generator's cache when it has one)."""
     import synth
     from oracle.model import Model
-    m = Model(L, ecut, grid, vloc_G, psi_v, e_v)
-    phi = synth.perturbations(miller_rho, L, n_pert, pert_seed)
+    s = synth.make_system(config)
+    m = Model(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, s.beta_G, s.d_proj)
+    phi = synth.perturbations(s.miller_rho, s.L, n_pert, pert_seed)
     _CPU_STATE.update(m=m, dV=m.vsqrt[:, None] * phi, tol=cg_tol)
 
 
@@ -149,7 +156,8 @@ def _cpu_solve(job):
     for v, p in systems:
         if time.time() > deadline:
             break
-        chi0.sternheimer_cg_drho(_CPU_STATE["m"], _CPU_STATE["dV"], tol=_CPU_STATE["tol"], systems=[(v, p)])
+        chi0.sternheimer_cg_drho(_CPU_STATE["m"], _CPU_STATE["dV"][:, [p]], tol=_CPU_STATE["tol"],
+                                 systems=[(v, 0)])
         done += 1
     return done
 
@@ -168,8 +176,7 @@ def cpu_baseline(wl, sys_, budget_s=20.0, one_core=True):
     saved = {k: os.environ.get(k) for k in keys}
     for k in keys:
         os.environ[k] = "1"
-    init = (sys_.L, sys_.ecut, sys_.grid, sys_.vloc_G, sys_.psi_v, sys_.e_v, sys_.miller_rho,
-            wl["n_pert"], wl["pert_seed"], wl["cg_tol"])
+    init = (wl["config"], wl["n_pert"], wl["pert_seed"], wl["cg_tol"])
     desc = "FP64 numpy CG with FFT-applied H to the same cg_tol"
     try:
         ctx = mp.get_context("spawn")
@@ -585,7 +592,9 @@ def main():
                                     fp64_emulation=args.fp64_emulation)
     if args.tensor_cores is not None:
         opt.tensor_cores = args.tensor_cores
-    ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, opt)
+    kb = s.beta_G.shape[1] > 0
+    ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, opt,
+                      beta_G=s.beta_G if kb else None, d_proj=s.d_proj if kb else None)
     stream = torch.cuda.current_stream()
     x = torch.from_numpy(np.ascontiguousarray(phi.T)).cuda()
     out = torch.zeros((1, wl["n_pert"], s.n_rho), dtype=torch.complex128, device="cuda")

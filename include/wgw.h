@@ -51,6 +51,7 @@ extern "C" {
 #define WGW_ERR_CUDA 4     /* a CUDA call failed */
 #define WGW_ERR_TIMEOUT 5  /* a bounded device wait gave up */
 #define WGW_ERR_STATE 6    /* call not valid in the context's state */
+#define WGW_ERR_CANCELLED 7  /* the request was cancelled (wgw_cancel) */
 
 #define WGW_FP64 0   /* every step in FP64 */
 #define WGW_MIXED 1  /* FP32 inner CG + FP64 residual refinement (Sec. 5.1, mixed precision) */
@@ -84,6 +85,12 @@ typedef struct wgw_options {
                           are captured as one CUDA graph and replayed (the launches and results are
                           the same as without; the first window of a solve runs directly); 0 = direct
                           launches.  Not used while profiling is on. */
+  int max_batch_systems;  /* most Sternheimer systems (complex-shifted: twice their count) solved as one
+                             batch; larger applies run in chunks of whole perturbations.  0 = as many as
+                             fit 85 % of the free device memory (the default). */
+  int fused_h;            /* MIXED: 1 = the FP32 H application runs as one kernel per pair with the FFT
+                             intermediate in (distributed) shared memory, on the grids it supports (24, 32,
+                             48); 0 = three kernels with the intermediate in device memory.  Same results. */
 } wgw_options;
 
 typedef struct wgw_stats {
@@ -96,7 +103,7 @@ typedef struct wgw_stats {
 
 /* Fills *opt with defaults: WGW_FP64, cg_tol 1e-12, max_cg_iter 2000, max_refine 8,
  * inner_tol 5e-6, f_s 2, check_every 8, dav_tol 1e-8, dav_max_iter 100, dav_factor 4, seed 12345,
- * fp64_emulation 1, tensor_cores 1, cuda_graphs 1. */
+ * fp64_emulation 1, tensor_cores 1, cuda_graphs 1, max_batch_systems 0, fused_h 1. */
 int wgw_default_options(wgw_options* opt);
 
 /*
@@ -182,13 +189,13 @@ int wgw_apply_chibar0_dev(wgw_ctx* ctx, const double* phi_dev, int n_pert, const
  * Kernel timing (no counterpart in the paper; used to report roofline fractions).
  * When enabled, every kernel launch of the context is bracketed by CUDA events on
  * its stream and accumulated per kernel class; enabling resets the counters.
- * Classes 0..7: plane_g2r, xline, plane_r2g, drho_xline, pc_project, cg_update, convert,
- * other, for the kernels on FP32 arrays; classes 8..15: the same names with "_f64", for the
- * kernels on FP64 arrays (native FP64 or float-float compute).  wgw_profile_read returns, for one class, the summed
+ * Classes 0..8: plane_g2r, xline, plane_r2g, drho_xline, pc_project, cg_update, convert,
+ * other, hpsi_fused, for the kernels on FP32 arrays; classes 9..17: the same names with "_f64",
+ * for the kernels on FP64 arrays (native FP64 or float-float compute).  wgw_profile_read returns, for one class, the summed
  * device milliseconds, the launch count and the summed algorithmic bytes and flops
  * (each launch's own compulsory inputs and outputs); any output pointer may be NULL.
  */
-#define WGW_PROF_KINDS 16
+#define WGW_PROF_KINDS 18
 int wgw_profile_enable(wgw_ctx* ctx, int on);
 /* Restricts recording to the classes whose bit is set in mask (bit k = class k; default all),
  * so that a timed run can bracket only the launches of one class. */
@@ -197,15 +204,30 @@ int wgw_profile_read(wgw_ctx* ctx, int kind, double* ms, long* launches, double*
 const char* wgw_profile_kind_name(int kind);
 
 /*
- * Per-system diagnostics of the last apply call on this context.  Systems are
- * ordered s = r * n_v + v, where r runs over the real-in-r parts of the batch
- * (the perturbations' real parts, then their non-zero imaginary parts).
- * Writes min(n, n_systems) entries: CG iterations summed over refinement steps,
- * and the final FP64 relative residual; either pointer may be NULL.  Returns the
- * number of entries written, or WGW_ERR_ARG (with nothing written) on a NULL context
- * or negative n.
+ * Per-system diagnostics of the last batched solve of this context (the last apply call, or
+ * the last block application of a Davidson run).  Static systems (omega = 0) are ordered
+ * s = r * n_v + v, where r runs over the real-in-r parts of the batch (the perturbations' real
+ * parts, then their non-zero imaginary parts); when the call had frequencies omega > 0 the
+ * records are those of its complex-shifted systems, q = (k * n_real + r) * n_v + v over those
+ * frequencies k.  Writes min(n, n_systems) entries: CG iterations summed over refinement
+ * steps, the final FP64 relative residual, and converged[s] = 1 if the system met cg_tol, else
+ * 0 (the systems behind a WGW_ERR_NOCONV); any output pointer may be NULL.  Returns the number
+ * of entries written, or WGW_ERR_ARG (with nothing written) on a NULL context or negative n.
  */
-int wgw_system_info(const wgw_ctx* ctx, int n, int* iters, double* rel_residual);
+int wgw_system_info(const wgw_ctx* ctx, int n, int* iters, double* rel_residual, int* converged);
+
+/*
+ * Sampled solutions (no counterpart in the paper; they let a caller check single Sternheimer
+ * systems of a large batch, Eq. sternheimer, one by one).  wgw_sample_solutions selects static
+ * systems, numbered as in wgw_system_info (s = r * n_v + v), whose solutions dpsi_s the following
+ * static applies (omega = 0) of the context keep; n = 0 clears the selection.  Indices beyond a
+ * batch's systems are ignored for that batch.  wgw_read_samples copies the kept solutions of the
+ * last static apply, in the selection's order, to dpsi: N_pw x n complex, wavefunction-sphere
+ * canonical order (the psi_v layout of wgw_setup), each in range(P_c); a system not in the last
+ * batch reads as zeros.  Returns WGW_ERR_ARG for n above the selection.
+ */
+int wgw_sample_solutions(wgw_ctx* ctx, int n, const int* systems);
+int wgw_read_samples(wgw_ctx* ctx, int n, double* dpsi);
 
 /*
  * PDEP basis (Sec. 3): the n_pdep leading (most negative) eigenpairs of chi0bar(omega = 0) by a
@@ -415,7 +437,17 @@ typedef struct wgw_result {
   int batch_systems;      /* Sternheimer systems of that batch */
 } wgw_result;
 
+/* Checks and copies the request, queues it and returns its ticket at once.  Returns WGW_ERR_ARG
+ * (nothing queued) for an unknown kind, n_pert < 1, n_omega outside 1..4096, a frequency that is
+ * negative or not finite, a null buffer, or perturbation coefficients that are not finite.  A
+ * request whose least memory need (one perturbation at a time, plus its inputs and outputs)
+ * exceeds 80 % of the free device memory waits; on an idle context it completes with
+ * WGW_ERR_NOMEM. */
 int wgw_submit(wgw_ctx* ctx, const wgw_request* req, uint64_t* ticket);
+/* Cancels a request: a queued one completes at once, a running one when its batch ends, with
+ * status WGW_ERR_CANCELLED and its output left unwritten.  WGW_ERR_ARG for an unknown or
+ * already finished ticket.  The ticket is still released by wgw_poll / wgw_wait. */
+int wgw_cancel(wgw_ctx* ctx, uint64_t ticket);
 /* *done = 1 (and *res filled, ticket released) when the request has finished, else 0. */
 int wgw_poll(wgw_ctx* ctx, uint64_t ticket, int* done, wgw_result* res);
 /* Blocks until the request has finished; fills *res (may be NULL) and releases the ticket. */

@@ -198,35 +198,46 @@ def sternheimer_cg_drho(model: Model, dV: np.ndarray, tol: float = 1e-12, max_it
             psi_r[v] = model.to_r(model.psi_v[:, v], model.mw)
         if p not in dV_r:
             dV_r[p] = model.to_r(dV[:, p], model.mr)
-        ev = model.e_v[v]
-        minv = 1.0 / np.maximum(0.5 * model.g2w - ev, 1.0)
-
-        def A(x):
-            return _pc(model, model.apply_h(x) - ev * x)
-
-        b = -_pc(model, model.to_G(dV_r[p] * psi_r[v], model.mw))
-        bnorm = np.linalg.norm(b)
-        x = np.zeros_like(b)
-        r = b.copy()
-        z = _pc(model, minv * r)
-        d = z.copy()
-        rz = np.vdot(r, z).real
-        it = 0
-        while np.linalg.norm(r) > tol * bnorm and it < max_iter:
-            q = A(d)
-            alpha = rz / np.vdot(d, q).real
-            x += alpha * d
-            r -= alpha * q
-            z = _pc(model, minv * r)
-            rz_new = np.vdot(r, z).real
-            d = z + (rz_new / rz) * d
-            rz = rz_new
-            it += 1
+        x, it = sternheimer_cg_solve(model, dV_r[p], v, tol, max_iter, psi_r[v])
         iters.append(it)
         rho_r = 2.0 * (psi_r[v].conj() * model.to_r(x, model.mw)).real
         out[:, p] += model.to_G(rho_r, model.mr)
     out *= model.f_s / model.omega
     return (out, iters) if return_iters else out
+
+
+def sternheimer_cg_solve(model: Model, dV_r: np.ndarray, v: int, tol: float = 1e-12, max_iter: int = 2000,
+                         psi_r=None):
+    """One static system of Eq. sternheimer by preconditioned CG: P_c (H - e_v) P_c x = -P_c [dV psi_v]
+    on range(P_c), dV given in real space (dV_r, real in r), the diagonal preconditioner
+    1 / max(0.5|G|^2 - e_v, 1), stop when ||b - A x|| <= tol ||b||.  Returns (x, iterations), x on
+    the wavefunction sphere."""
+    pv = model.to_r(model.psi_v[:, v], model.mw) if psi_r is None else psi_r
+    ev = model.e_v[v]
+    minv = 1.0 / np.maximum(0.5 * model.g2w - ev, 1.0)
+
+    def A(x):
+        return _pc(model, model.apply_h(x) - ev * x)
+
+    b = -_pc(model, model.to_G(dV_r * pv, model.mw))
+    bnorm = np.linalg.norm(b)
+    x = np.zeros_like(b)
+    r = b.copy()
+    z = _pc(model, minv * r)
+    d = z.copy()
+    rz = np.vdot(r, z).real
+    it = 0
+    while np.linalg.norm(r) > tol * bnorm and it < max_iter:
+        q = A(d)
+        alpha = rz / np.vdot(d, q).real
+        x += alpha * d
+        r -= alpha * q
+        z = _pc(model, minv * r)
+        rz_new = np.vdot(r, z).real
+        d = z + (rz_new / rz) * d
+        rz = rz_new
+        it += 1
+    return x, it
 
 
 def pair_densities(model: Model, occ: np.ndarray, emp: np.ndarray) -> np.ndarray:

@@ -78,6 +78,14 @@ cudaError_t launch_drho_xline(int m, FftCtx<T> f, const cplx<T>* Tbuf, const T* 
   return launch_drho_xline_c<T, T>(m, f.plan, f.tw, Tbuf, psi_r, ldpsi, n_v, n_sys, n_pert, coef, D, ldd, st);
 }
 
+// Fused FP32 H application (hpsi_fused.cu): plane g2r, x-line with V(r) and plane r2g of the
+// systems of a list in one kernel, the pair intermediate in (distributed) shared memory.  Same
+// arguments and results as the three separate launches with XM_APPLY_V; supported for the grid
+// sizes and sphere radii hpsi_fused_supported accepts.
+bool hpsi_fused_supported(int N, int m);
+cudaError_t launch_hpsi_fused(const SphereTab& sp, int N, const float* P, long ldp, int n_list, const int* list,
+                              const int* active, const float* V, const Epi<float>& e, cudaStream_t st);
+
 // Linear algebra (la_kernels.cu).
 // Y <- Y - Psi Psi^T Y for the active systems of a list (null = systems 0..n_sys-1);
 // work holds pc_work_elems(n, n_sys, nv) elements of T.

@@ -12,10 +12,12 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/wgw.h"
 #include "internal.h"
+#include "serve_sched.h"
 #include "tables.h"
 
 using namespace wgw;
@@ -134,16 +136,17 @@ struct Prec {
 // (enabled by wgw_profile_enable).  Each record brackets one launch.
 // Classes 0..7 time the FP32 kernels, 8..15 the same kernels on FP64 arrays (native FP64 or
 // float-float compute).
-constexpr int kProfKinds = 16;
+constexpr int kProfHalf = 9, kProfKinds = 2 * kProfHalf;
 const char* const kProfNames[kProfKinds] = {"plane_g2r", "xline", "plane_r2g", "drho_xline",
-                                            "pc_project", "cg_update", "convert", "other",
+                                            "pc_project", "cg_update", "convert", "other", "hpsi_fused",
                                             "plane_g2r_f64", "xline_f64", "plane_r2g_f64", "drho_xline_f64",
-                                            "pc_project_f64", "cg_update_f64", "convert_f64", "other_f64"};
-enum ProfKind { PK_G2R = 0, PK_XLINE, PK_R2G, PK_DRHO, PK_PC, PK_CG, PK_CONV, PK_OTHER };
+                                            "pc_project_f64", "cg_update_f64", "convert_f64", "other_f64",
+                                            "hpsi_fused_f64"};
+enum ProfKind { PK_G2R = 0, PK_XLINE, PK_R2G, PK_DRHO, PK_PC, PK_CG, PK_CONV, PK_OTHER, PK_HPSI };
 
 struct Prof {
   bool on = false;
-  unsigned mask = 0xffffu;   // classes recorded while on
+  unsigned mask = (1u << kProfKinds) - 1;   // classes recorded while on
   bool f64 = true;    // storage precision of the launches being recorded
   struct Rec { int kind; cudaEvent_t a, b; double bytes, flops; };
   std::vector<Rec> recs;
@@ -158,7 +161,7 @@ struct Prof {
   }
   template <typename F>
   cudaError_t run(int kind, double by, double fl, cudaStream_t st, F&& f) {
-    const int k = kind + (f64 ? 8 : 0);
+    const int k = kind + (f64 ? kProfHalf : 0);
     if (!on || !((mask >> k) & 1u)) return f();
     Rec r{k, get(), get(), by, fl};
     cudaEventRecord(r.a, st);
@@ -221,26 +224,22 @@ struct wgw_ctx {
   std::vector<std::pair<int, double>> tc_tune;
   std::vector<int> last_iters;      // per system of the last apply: CG iterations (all refinements)
   std::vector<double> last_relres;  // per system of the last apply: final FP64 ||b - A x|| / ||b||
+  std::vector<int> last_conv;       // per system of the last apply: 1 if it met cg_tol
+  // Sampled solutions (wgw_sample_solutions): static systems whose dpsi the applies keep, and
+  // their values from the last static apply (N_pw complex each, canonical order).
+  std::vector<int> sample_sys;
+  std::vector<double> sample_out;
+  DevBuf sample_buf;
+  std::vector<int> blk_iters;       // the same for the batched solve that just ran (one chunk)
+  std::vector<double> blk_relres;
+  std::vector<int> blk_conv;
   // Serialises every entry point that uses the context's device state (callers and the
   // request worker).
   std::recursive_mutex mu;
-  // Request queue of wgw_submit (see the serving section below).
-  struct Req {
-    uint64_t ticket;
-    int kind;
-    int n_pert;
-    std::vector<double> dV;        // copied at submission
-    std::vector<double> omega;
-    double* out;
-    std::chrono::steady_clock::time_point t_submit;
-  };
-  struct Done { int status; double latency_s, queue_s; int batch_requests, batch_systems; };
+  // Request queue of wgw_submit (see the serving section below), guarded by qmu.
   std::mutex qmu;
   std::condition_variable qcv;
-  std::deque<Req> queue;
-  std::map<uint64_t, Done> done;
-  std::set<uint64_t> running;
-  uint64_t next_ticket = 1;
+  serve::Queue sq;
   bool stop = false;
   std::thread worker;
   int device = 0;
@@ -367,22 +366,37 @@ int apply_A(wgw_ctx* c, Prec<T>& pr, const T* P, T* Q, int n_list, const int* li
   ProfPrec pp(c->prof, sizeof(T) == 8);
   const int N = c->N, NP = 2 * c->wfc.m + 1, pairs = (n_list + 1) / 2;
   if (pairs == 0) return WGW_OK;
-  WGW_TRY(pr.Tw.ensure(sizeof(cplx<T>) * (size_t)pairs * NP * N * N));
+  const bool need_t = !(sizeof(T) == sizeof(float) && c->opt.fused_h != 0 && hpsi_fused_supported(N, c->wfc.m));
+  if (need_t) WGW_TRY(pr.Tw.ensure(sizeof(cplx<T>) * (size_t)pairs * NP * N * N));
   FftCtx<T> f = pr.fft(c->plan);
   cplx<T>* Tb = pr.Tw.template as<cplx<T>>();
   const int nrb = c->wfc.nrb();
   const double tb = t_bytes<T>(c, c->wfc.m, pairs);
-  WGW_CK(c->prof.run(PK_G2R, tb + (double)n_list * nrb * sizeof(T), 0, st, [&] {
-    return launch_plane_g2r<T>(c->wfc.tab(), f, P, c->ld_w, n_list, list, active, Tb, st); }));
-  XArgs<T> a{};
-  a.mode = XM_APPLY_V; a.V = pr.v_r_fft(); a.n_sys = n_list; a.list = list;
-  WGW_CK(c->prof.run(PK_XLINE, 2 * tb + (double)c->grid3 * sizeof(T), 0, st, [&] {
-    return launch_xline<T>(c->wfc.m, f, Tb, a, active, st); }));
   Epi<T> e{};
   e.out = Q; e.ldo = c->ld_w; e.pin = P; e.ldp = c->ld_w; e.vcoef = T(1); e.kin = T(1);
   e.shift = pr.shift.template as<T>(); e.n_sys = n_list; e.active = active; e.list = list;
-  WGW_CK(c->prof.run(PK_R2G, tb + 2.0 * n_list * nrb * sizeof(T), 0, st, [&] {
-    return launch_plane_r2g<T>(c->wfc.tab(), c->wfc.npt_max, f, Tb, e, st); }));
+  bool fused = false;
+  if constexpr (std::is_same<T, float>::value) {
+    if (c->opt.fused_h != 0 && hpsi_fused_supported(N, c->wfc.m)) {
+      // Algorithmic work: p in, q out and V(r); flops 5 n log2 n per line transform (rows and
+      // columns of the 2m+1 planes both ways, N^2 x-lines both ways) and the V(r) product.
+      const double nl = 5.0 * N * std::log2((double)N);
+      const double fl = (double)pairs * (2.0 * NP * NP * nl + 2.0 * NP * N * nl + 2.0 * N * N * nl + 2.0 * c->grid3);
+      WGW_CK(c->prof.run(PK_HPSI, 2.0 * n_list * nrb * sizeof(T) + (double)c->grid3 * sizeof(T), fl, st, [&] {
+        return launch_hpsi_fused(c->wfc.tab(), N, P, c->ld_w, n_list, list, active, pr.v_r_fft(), e, st); }));
+      fused = true;
+    }
+  }
+  if (!fused) {
+    WGW_CK(c->prof.run(PK_G2R, tb + (double)n_list * nrb * sizeof(T), 0, st, [&] {
+      return launch_plane_g2r<T>(c->wfc.tab(), f, P, c->ld_w, n_list, list, active, Tb, st); }));
+    XArgs<T> a{};
+    a.mode = XM_APPLY_V; a.V = pr.v_r_fft(); a.n_sys = n_list; a.list = list;
+    WGW_CK(c->prof.run(PK_XLINE, 2 * tb + (double)c->grid3 * sizeof(T), 0, st, [&] {
+      return launch_xline<T>(c->wfc.m, f, Tb, a, active, st); }));
+    WGW_CK(c->prof.run(PK_R2G, tb + 2.0 * n_list * nrb * sizeof(T), 0, st, [&] {
+      return launch_plane_r2g<T>(c->wfc.tab(), c->wfc.npt_max, f, Tb, e, st); }));
+  }
   if (c->n_proj > 0) {
     WGW_TRY(c->pc_work.ensure(sizeof(T) * pc_work_elems(nrb, n_list, std::max(c->n_v, c->n_proj))));
     WGW_CK(c->prof.run(PK_PC, 3.0 * n_list * nrb * sizeof(T), 4.0 * nrb * c->n_proj * n_list, st, [&] {
@@ -573,7 +587,6 @@ int ensure_work(wgw_ctx* c, int n_sys, int n_real) {
   WGW_TRY(c->cnt.ensure(sizeof(int) * 4));
   WGW_TRY(c->dv_r.ensure(sizeof(double) * (size_t)n_real * c->grid3));
   WGW_TRY(c->Dr.ensure(sizeof(double) * (size_t)n_real * c->grid3));
-  WGW_TRY(c->drho_rb.ensure(sizeof(double) * (size_t)n_real * c->ld_r));
   return WGW_OK;
 }
 
@@ -657,21 +670,22 @@ int solve_all(wgw_ctx* c, int n_sys, cudaStream_t st, wgw_stats* stats) {
   WGW_CK(cudaStreamSynchronize(st));
   int conv = 0, maxit = 0;
   double maxrel = 0.0;
-  c->last_iters = iters_total;
-  c->last_relres.assign(n_sys, 0.0);
+  c->blk_iters = iters_total;
+  c->blk_relres.assign(n_sys, 0.0);
+  c->blk_conv.assign(n_sys, 0);
   for (int s = 0; s < n_sys; ++s) {
     const double rel = bb[s] > 0 ? std::sqrt(rr[s] / bb[s]) : 0.0;
-    c->last_relres[s] = rel;
+    c->blk_relres[s] = rel;
     maxrel = std::max(maxrel, rel);
-    if (rel <= tol * (1.0 + 1e-6) || bb[s] == 0.0) ++conv;
+    if (rel <= tol * (1.0 + 1e-6) || bb[s] == 0.0) { ++conv; c->blk_conv[s] = 1; }
     maxit = std::max(maxit, iters_total[s]);
   }
   if (stats) {
-    stats->n_systems = n_sys;
-    stats->n_converged = conv;
-    stats->max_iters = maxit;
-    stats->refinements = refinements;
-    stats->max_rel_residual = maxrel;
+    stats->n_systems += n_sys;
+    stats->n_converged += conv;
+    stats->max_iters = std::max(stats->max_iters, maxit);
+    stats->refinements = std::max(stats->refinements, refinements);
+    stats->max_rel_residual = std::max(stats->max_rel_residual, maxrel);
   }
   return conv == n_sys ? WGW_OK : fail(WGW_ERR_NOCONV, "some Sternheimer systems missed cg_tol");
 }
@@ -799,13 +813,14 @@ int solve_shifted(wgw_ctx* c, int n_cs, cudaStream_t st, wgw_stats* stats) {
   WGW_CK(cudaStreamSynchronize(st));
   int conv = 0, maxit = 0;
   double maxrel = 0.0;
-  c->last_iters = iters_total;
-  c->last_relres.assign(n_cs, 0.0);
+  c->blk_iters = iters_total;
+  c->blk_relres.assign(n_cs, 0.0);
+  c->blk_conv.assign(n_cs, 0);
   for (int q = 0; q < n_cs; ++q) {
     const double rel = bb[q] > 0 ? std::sqrt(rr[q] / bb[q]) : 0.0;
-    c->last_relres[q] = rel;
+    c->blk_relres[q] = rel;
     maxrel = std::max(maxrel, rel);
-    if (rel <= tol * (1.0 + 1e-6) || bb[q] == 0.0) ++conv;
+    if (rel <= tol * (1.0 + 1e-6) || bb[q] == 0.0) { ++conv; c->blk_conv[q] = 1; }
     maxit = std::max(maxit, iters_total[q]);
   }
   if (stats) {
@@ -818,10 +833,52 @@ int solve_shifted(wgw_ctx* c, int n_cs, cudaStream_t st, wgw_stats* stats) {
   return conv == n_cs ? WGW_OK : fail(WGW_ERR_NOCONV, "some complex-shifted Sternheimer systems missed cg_tol");
 }
 
+// Device bytes one batched solve needs per system and per perturbation (vectors, the FFT pair
+// intermediates of both precisions, projector work, real-space perturbation and drho).
+void solve_bytes(const wgw_ctx* c, double* per_sys, double* per_pert) {
+  const double N2 = (double)c->N * c->N;
+  const bool mixed = c->opt.precision == WGW_MIXED;
+  const int nv = std::max(c->n_v, c->n_proj), nvp = (nv + 63) / 64 * 64;
+  *per_sys = (6.0 * 8 + (mixed ? 6.0 * 4 : 0.0)) * c->ld_w + 0.5 * (2 * c->wfc.m + 1) * N2 * (16.0 + (mixed ? 8.0 : 0.0)) +
+             8.0 * nvp * 2 + 128.0;
+  *per_pert = 2.0 * 8.0 * c->grid3 + 8.0 * c->ld_r + 0.5 * (2 * c->rho.m + 1) * N2 * 16.0;
+}
+
+// Bytes held by the grow-only work buffers of the batched solves (reused or regrown by the next one).
+double held_work_bytes(const wgw_ctx* c) {
+  const DevBuf* bufs[] = {&c->d.X, &c->d.R, &c->d.Z, &c->d.P, &c->d.Q, &c->d.Bv, &c->d.Tw,
+                          &c->f.X, &c->f.R, &c->f.Z, &c->f.P, &c->f.Q, &c->f.Bv, &c->f.Tw,
+                          &c->pc_work, &c->dv_r, &c->Dr, &c->Trho};
+  double b = 0.0;
+  for (const DevBuf* d : bufs) b += (double)d->bytes;
+  return b;
+}
+
+// Perturbations per batched solve: all of them when they fit, else as many as fit 85 % of the
+// free device memory (plus the work buffers the context already holds), or the option's cap.
+int chunk_perts(wgw_ctx* c, int n_real, int sys_per_pert) {
+  double per_sys = 0, per_pert = 0;
+  solve_bytes(c, &per_sys, &per_pert);
+  const double per = per_sys * sys_per_pert + per_pert;
+  int by_mem = n_real;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+    const double budget = 0.85 * ((double)free_b + held_work_bytes(c));
+    by_mem = (int)std::max(1.0, std::floor(budget / per));
+  } else {
+    cudaGetLastError();
+  }
+  int cap = n_real;
+  if (c->opt.max_batch_systems > 0) cap = std::max(1, c->opt.max_batch_systems / std::max(1, sys_per_pert));
+  return std::max(1, std::min(n_real, std::min(by_mem, cap)));
+}
+
 // drho = chi0 dV for n_real perturbations that are real in r, given and returned in
-// real-basis form (rows of length ld_r): dV in dvrb, drho into c->drho_rb.  Steps 2-6
-// of the apply: system tables, dV(r), right-hand sides, Sternheimer solves, drho.
-int chi0_rb(wgw_ctx* c, const double* dvrb, int n_real, cudaStream_t st, wgw_stats* stats) {
+// real-basis form (rows of length ld_r): dV in dvrb, drho into drho_out.  Steps 2-6
+// of the apply for one batched solve: system tables, dV(r), right-hand sides, Sternheimer
+// solves, drho.
+int chi0_rb_block(wgw_ctx* c, const double* dvrb, int n_real, double* drho_out, cudaStream_t st,
+                  wgw_stats* stats) {
   const int N = c->N, n_v = c->n_v;
   const long ldr = c->ld_r, ldw = c->ld_w;
   const HostSphere& rs = c->rho;
@@ -890,18 +947,60 @@ int chi0_rb(wgw_ctx* c, const double* dvrb, int n_real, cudaStream_t st, wgw_sta
     WGW_CK(c->prof.run(PK_XLINE, tr + (double)n_real * c->grid3 * sizeof(double), 0, st, [&] {
       return launch_xline<double>(rs.m, f, c->Trho.as<cplx<double>>(), a, nullptr, st); }));
     Epi<double> e{};
-    e.out = c->drho_rb.as<double>(); e.ldo = ldr; e.vcoef = 1.0; e.n_sys = n_real;
+    e.out = drho_out; e.ldo = ldr; e.vcoef = 1.0; e.n_sys = n_real;
     WGW_CK(c->prof.run(PK_R2G, tr + (double)n_real * rs.nrb() * sizeof(double), 0, st, [&] {
       return launch_plane_r2g<double>(rs.tab(), rs.npt_max, f, c->Trho.as<cplx<double>>(), e, st); }));
   }
   return solve_status;
 }
 
+// Copies the solutions of the sampled systems among [s0, s0 + n) (rows s - s0 of d.X, real basis)
+// to the host as wavefunction-sphere coefficients.
+int keep_samples(wgw_ctx* c, int s0, int n, cudaStream_t st) {
+  const int n_pw = c->wfc.n;
+  if (c->sample_out.size() != c->sample_sys.size() * 2 * (size_t)n_pw)
+    c->sample_out.assign(c->sample_sys.size() * 2 * (size_t)n_pw, 0.0);
+  for (size_t k = 0; k < c->sample_sys.size(); ++k) {
+    const int sys = c->sample_sys[k];
+    if (sys < s0 || sys >= s0 + n) continue;
+    WGW_TRY(c->sample_buf.ensure(sizeof(double) * 2 * (size_t)n_pw));
+    WGW_CK(launch_rb_to_sphere(1, c->d.X.as<double>() + (size_t)(sys - s0) * c->ld_w, c->ld_w, nullptr, nullptr,
+                               c->wfc.map(), c->sample_buf.as<double>(), 2L * n_pw, st));
+    WGW_CK(cudaMemcpyAsync(c->sample_out.data() + k * 2 * (size_t)n_pw, c->sample_buf.p,
+                           sizeof(double) * 2 * (size_t)n_pw, cudaMemcpyDeviceToHost, st));
+    WGW_CK(cudaStreamSynchronize(st));
+  }
+  return WGW_OK;
+}
+
+// chi0_rb_block over chunks of perturbations that fit the device (drho into c->drho_rb); the
+// per-system records of wgw_system_info follow the batch order s = r n_v + v.
+int chi0_rb(wgw_ctx* c, const double* dvrb, int n_real, cudaStream_t st, wgw_stats* stats) {
+  WGW_TRY(c->drho_rb.ensure(sizeof(double) * (size_t)std::max(n_real, 1) * c->ld_r));
+  const int per = chunk_perts(c, n_real, c->n_v);
+  c->last_iters.assign((size_t)n_real * c->n_v, 0);
+  c->last_relres.assign((size_t)n_real * c->n_v, 0.0);
+  c->last_conv.assign((size_t)n_real * c->n_v, 0);
+  int status = WGW_OK;
+  for (int r0 = 0; r0 < n_real; r0 += per) {
+    const int nr = std::min(per, n_real - r0);
+    const int s1 = chi0_rb_block(c, dvrb + (size_t)r0 * c->ld_r, nr, c->drho_rb.as<double>() + (size_t)r0 * c->ld_r,
+                                 st, stats);
+    if (s1 != WGW_OK && s1 != WGW_ERR_NOCONV) return s1;
+    if (s1 == WGW_ERR_NOCONV) status = s1;
+    std::copy(c->blk_iters.begin(), c->blk_iters.end(), c->last_iters.begin() + (size_t)r0 * c->n_v);
+    std::copy(c->blk_relres.begin(), c->blk_relres.end(), c->last_relres.begin() + (size_t)r0 * c->n_v);
+    std::copy(c->blk_conv.begin(), c->blk_conv.end(), c->last_conv.begin() + (size_t)r0 * c->n_v);
+    WGW_TRY(keep_samples(c, r0 * c->n_v, nr * c->n_v, st));
+  }
+  return status == WGW_OK ? WGW_OK : fail(status, "some Sternheimer systems missed cg_tol");
+}
+
 // drho(i w_k) = chi0(i w_k) dV for n_real real-in-r perturbations (real-basis rows of dvrb) and
 // every w_k > 0, batched over frequencies: complex system (k, r, v) -> rows 2s, 2s+1 with
-// s = (k n_real + r) n_v + v.  Results into c->drho_all, row k * n_real + r.
-int chi0_rb_shifted(wgw_ctx* c, const double* dvrb, int n_real, const std::vector<double>& oms, cudaStream_t st,
-                    wgw_stats* stats) {
+// s = (k n_real + r) n_v + v.  Results for frequency k at out + k * kstride (rows r, length ld_r).
+int chi0_rb_shifted_block(wgw_ctx* c, const double* dvrb, int n_real, const std::vector<double>& oms,
+                          double* out, size_t kstride, cudaStream_t st, wgw_stats* stats) {
   const int N = c->N, n_v = c->n_v, n_om = (int)oms.size();
   const long ldr = c->ld_r, ldw = c->ld_w;
   const HostSphere& rs = c->rho;
@@ -954,7 +1053,6 @@ int chi0_rb_shifted(wgw_ctx* c, const double* dvrb, int n_real, const std::vecto
   }
   const int solve_status = solve_shifted(c, n_cs, st, stats);
   if (solve_status != WGW_OK && solve_status != WGW_ERR_NOCONV) return solve_status;
-  WGW_TRY(c->drho_all.ensure(sizeof(double) * (size_t)n_om * n_real * ldr));
   const int pairs = (n_rs + 1) / 2;
   const int NPr = 2 * rs.m + 1, rpairs = (n_real + 1) / 2;
   WGW_TRY(c->Trho.ensure(sizeof(cplx<double>) * (size_t)rpairs * NPr * N * N));
@@ -975,11 +1073,42 @@ int chi0_rb_shifted(wgw_ctx* c, const double* dvrb, int n_real, const std::vecto
     WGW_CK(c->prof.run(PK_XLINE, tr + (double)n_real * c->grid3 * sizeof(double), 0, st, [&] {
       return launch_xline<double>(rs.m, f, c->Trho.as<cplx<double>>(), a, nullptr, st); }));
     Epi<double> e{};
-    e.out = c->drho_all.as<double>() + (size_t)k * n_real * ldr; e.ldo = ldr; e.vcoef = 1.0; e.n_sys = n_real;
+    e.out = out + (size_t)k * kstride; e.ldo = ldr; e.vcoef = 1.0; e.n_sys = n_real;
     WGW_CK(c->prof.run(PK_R2G, tr + (double)n_real * rs.nrb() * sizeof(double), 0, st, [&] {
       return launch_plane_r2g<double>(rs.tab(), rs.npt_max, f, c->Trho.as<cplx<double>>(), e, st); }));
   }
   return solve_status;
+}
+
+// chi0_rb_shifted_block over chunks of perturbations that fit the device; results into
+// c->drho_all (row k n_real + r), per-system records in the order q = (k n_real + r) n_v + v.
+int chi0_rb_shifted(wgw_ctx* c, const double* dvrb, int n_real, const std::vector<double>& oms, cudaStream_t st,
+                    wgw_stats* stats) {
+  const int n_om = (int)oms.size(), n_v = c->n_v;
+  const long ldr = c->ld_r;
+  WGW_TRY(c->drho_all.ensure(sizeof(double) * (size_t)std::max(1, n_om * n_real) * ldr));
+  const int per = chunk_perts(c, n_real, 2 * n_v * n_om);
+  const size_t n_cs = (size_t)n_om * n_real * n_v;
+  c->last_iters.assign(n_cs, 0);
+  c->last_relres.assign(n_cs, 0.0);
+  c->last_conv.assign(n_cs, 0);
+  int status = WGW_OK;
+  for (int r0 = 0; r0 < n_real; r0 += per) {
+    const int nr = std::min(per, n_real - r0);
+    const int s1 = chi0_rb_shifted_block(c, dvrb + (size_t)r0 * ldr, nr, oms, c->drho_all.as<double>() + (size_t)r0 * ldr,
+                                         (size_t)n_real * ldr, st, stats);
+    if (s1 != WGW_OK && s1 != WGW_ERR_NOCONV) return s1;
+    if (s1 == WGW_ERR_NOCONV) status = s1;
+    for (int k = 0; k < n_om; ++k)
+      for (int r = 0; r < nr; ++r)
+        for (int v = 0; v < n_v; ++v) {
+          const size_t q = ((size_t)k * nr + r) * n_v + v, g = ((size_t)k * n_real + r0 + r) * n_v + v;
+          c->last_iters[g] = c->blk_iters[q];
+          c->last_relres[g] = c->blk_relres[q];
+          c->last_conv[g] = c->blk_conv[q];
+        }
+  }
+  return status == WGW_OK ? WGW_OK : fail(status, "some complex-shifted Sternheimer systems missed cg_tol");
 }
 
 // Float-float FP64-accuracy passes: the mixed path on the compiled grids.
@@ -1583,6 +1712,8 @@ int wgw_default_options(wgw_options* opt) {
   opt->dav_max_iter = 100;
   opt->dav_factor = 4;
   opt->seed = 12345;
+  opt->max_batch_systems = 0;
+  opt->fused_h = 1;
   return WGW_OK;
 }
 
@@ -1592,6 +1723,7 @@ static int check_options(const wgw_options& o) {
     return fail(WGW_ERR_ARG, "bad tolerances or iteration limits");
   if (!(o.dav_tol > 0) || o.dav_max_iter < 1 || o.dav_factor < 2)
     return fail(WGW_ERR_ARG, "bad Davidson options");
+  if (o.max_batch_systems < 0) return fail(WGW_ERR_ARG, "max_batch_systems < 0");
   return WGW_OK;
 }
 
@@ -1888,14 +2020,35 @@ const char* wgw_profile_kind_name(int kind) {
   return (kind >= 0 && kind < kProfKinds) ? kProfNames[kind] : "";
 }
 
-int wgw_system_info(const wgw_ctx* c, int n, int* iters, double* rel_residual) {
+int wgw_system_info(const wgw_ctx* c, int n, int* iters, double* rel_residual, int* converged) {
   if (!c || n < 0) return fail(WGW_ERR_ARG, "bad argument");
   const int m = std::min<int>(n, (int)c->last_iters.size());
   for (int s = 0; s < m; ++s) {
     if (iters) iters[s] = c->last_iters[s];
     if (rel_residual) rel_residual[s] = c->last_relres[s];
+    if (converged) converged[s] = c->last_conv[s];
   }
   return m;
+}
+
+int wgw_sample_solutions(wgw_ctx* c, int n, const int* systems) {
+  g_last_error.clear();
+  if (!c || n < 0 || (n > 0 && !systems)) return fail(WGW_ERR_ARG, "bad argument");
+  for (int k = 0; k < n; ++k)
+    if (systems[k] < 0) return fail(WGW_ERR_ARG, "negative system index");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  c->sample_sys.assign(systems, systems + n);
+  c->sample_out.assign((size_t)n * 2 * c->wfc.n, 0.0);
+  return WGW_OK;
+}
+
+int wgw_read_samples(wgw_ctx* c, int n, double* dpsi) {
+  g_last_error.clear();
+  if (!c || n < 0 || (n > 0 && !dpsi)) return fail(WGW_ERR_ARG, "bad argument");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  if ((size_t)n > c->sample_sys.size()) return fail(WGW_ERR_ARG, "more samples requested than selected");
+  std::copy(c->sample_out.begin(), c->sample_out.begin() + (size_t)n * 2 * c->wfc.n, dpsi);
+  return WGW_OK;
 }
 
 int wgw_pdep_davidson(wgw_ctx* c, int n_pdep, const double* x0, double* eig, double* basis, wgw_stats* st) {
@@ -2124,43 +2277,40 @@ int wgw_symm_eig_dev(int n, double* A_dev, double* w_dev, double* Z_dev, void* s
 
 
 // ---------------------------------------------------------------- serving: request queue
-// Requests are copied in by wgw_submit and executed by one worker thread per context on the
-// context's stream.  The worker merges every queued request with the same kind and frequency
-// set into one batched apply (as many as the free device memory admits), then scatters the
-// results back; requests to different contexts run on different streams and overlap on the GPU.
-static double batch_bytes(const wgw_ctx* c, int n_real) {
-  const double per_sys = 72.0 * c->ld_w + 12.0 * (2 * c->wfc.m + 1) * (double)c->N * c->N;
-  const double per_pert = 3.0 * 8.0 * c->grid3 + 64.0 * c->ld_r + 12.0 * (2 * c->rho.m + 1) * (double)c->N * c->N;
-  return n_real * (per_sys * c->n_v + per_pert);
+// Requests are checked and copied in by wgw_submit and executed by one worker thread per
+// context on the context's stream.  The worker takes the head request when the least memory it
+// can run in fits 80 % of the free device memory (plus the work buffers the context holds), and
+// merges every queued request of the same kind and frequency set that keeps the whole batch
+// resident in that budget into one batched apply, then scatters the results back; requests to
+// different contexts run on different streams and overlap on the GPU.
+static double batch_bytes(const wgw_ctx* c, int n_real, bool whole) {
+  double per_sys = 0, per_pert = 0;
+  solve_bytes(c, &per_sys, &per_pert);
+  const int n_pert = (n_real + 1) / 2;
+  const double io = 8.0 * (2.0 * c->rho.n * n_pert * 2 + (double)n_real * c->ld_r * 3);
+  const int resident = whole ? n_real : 1;
+  return resident * (per_sys * c->n_v + per_pert) + io;
 }
 
 static void serve_loop(wgw_ctx* c) {
   cudaSetDevice(c->device);
   for (;;) {
-    std::vector<wgw_ctx::Req> batch;
+    std::vector<serve::Request> batch;
     {
       std::unique_lock<std::mutex> lk(c->qmu);
-      c->qcv.wait(lk, [&] { return c->stop || !c->queue.empty(); });
-      if (c->queue.empty()) return;
+      c->qcv.wait(lk, [&] { return c->stop || !c->sq.empty(); });
+      if (c->sq.empty()) return;
       size_t free_b = 0, total_b = 0;
-      cudaMemGetInfo(&free_b, &total_b);
-      const double budget = 0.8 * (double)free_b;
-      const wgw_ctx::Req& head = c->queue.front();
-      const int kind = head.kind;
-      const std::vector<double> om = head.omega;
-      int n_tot = 0;
-      for (auto it = c->queue.begin(); it != c->queue.end();) {
-        const bool same = it->kind == kind && it->omega == om;
-        // Real perturbation count is at most 2 n_pert (non-Hermitian parts).
-        if (same && (batch.empty() || batch_bytes(c, 2 * (n_tot + it->n_pert)) <= budget)) {
-          n_tot += it->n_pert;
-          c->running.insert(it->ticket);
-          batch.push_back(std::move(*it));
-          it = c->queue.erase(it);
-        } else {
-          ++it;
-        }
+      if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        free_b = 0;
       }
+      const double budget = 0.8 * ((double)free_b + held_work_bytes(c));
+      std::vector<std::pair<uint64_t, serve::Done>> rejected;
+      batch = c->sq.take_batch(budget, [&](int n_real, bool whole) { return batch_bytes(c, n_real, whole); },
+                               false, &rejected);
+      if (!rejected.empty()) c->qcv.notify_all();
+      if (batch.empty()) continue;
     }
     const auto t_start = std::chrono::steady_clock::now();
     const int n_rho = c->rho.n, n_om = (int)batch[0].omega.size();
@@ -2175,28 +2325,18 @@ static void serve_loop(wgw_ctx* c) {
     wgw_stats stt{};
     const int status = apply_host(c, dv.data(), n_tot, batch[0].omega.data(), n_om, out.data(),
                                   batch[0].kind == WGW_REQ_CHIBAR0, &stt);
-    off = 0;
-    for (auto& r : batch) {
-      if (status == WGW_OK || status == WGW_ERR_NOCONV)
-        for (int k = 0; k < n_om; ++k)
-          std::copy(out.begin() + (size_t)2 * n_rho * ((size_t)k * n_tot + off),
-                    out.begin() + (size_t)2 * n_rho * ((size_t)k * n_tot + off + r.n_pert),
-                    r.out + (size_t)2 * n_rho * ((size_t)k * r.n_pert));
-      off += r.n_pert;
-    }
-    const auto t_end = std::chrono::steady_clock::now();
     {
       std::lock_guard<std::mutex> lk(c->qmu);
+      off = 0;
       for (auto& r : batch) {
-        wgw_ctx::Done d;
-        d.status = status;
-        d.latency_s = std::chrono::duration<double>(t_end - r.t_submit).count();
-        d.queue_s = std::chrono::duration<double>(t_start - r.t_submit).count();
-        d.batch_requests = (int)batch.size();
-        d.batch_systems = stt.n_systems;
-        c->done[r.ticket] = d;
-        c->running.erase(r.ticket);
+        if ((status == WGW_OK || status == WGW_ERR_NOCONV) && !c->sq.cancelled(r.ticket))
+          for (int k = 0; k < n_om; ++k)
+            std::copy(out.begin() + (size_t)2 * n_rho * ((size_t)k * n_tot + off),
+                      out.begin() + (size_t)2 * n_rho * ((size_t)k * n_tot + off + r.n_pert),
+                      r.out + (size_t)2 * n_rho * ((size_t)k * r.n_pert));
+        off += r.n_pert;
       }
+      c->sq.finish(batch, status, t_start, std::chrono::steady_clock::now(), stt.n_systems);
     }
     c->qcv.notify_all();
   }
@@ -2205,12 +2345,11 @@ static void serve_loop(wgw_ctx* c) {
 int wgw_submit(wgw_ctx* c, const wgw_request* req, uint64_t* ticket) {
   g_last_error.clear();
   if (!c || !req || !ticket) return fail(WGW_ERR_ARG, "null argument");
-  if (req->kind != WGW_REQ_CHI0 && req->kind != WGW_REQ_CHIBAR0) return fail(WGW_ERR_ARG, "unknown request kind");
-  if (req->n_pert < 1 || !req->dV || !req->out || req->n_omega < 1 || !req->omega)
-    return fail(WGW_ERR_ARG, "need n_pert >= 1, dV, out and n_omega >= 1 frequencies");
-  for (int k = 0; k < req->n_omega; ++k)
-    if (!(req->omega[k] >= 0.0)) return fail(WGW_ERR_ARG, "imaginary frequencies must be >= 0");
-  wgw_ctx::Req r;
+  std::string why;
+  if (serve::validate(req->kind, req->dV, req->n_pert, req->omega, req->n_omega, req->out, c->rho.n, &why) !=
+      serve::kOk)
+    return fail(WGW_ERR_ARG, why);
+  serve::Request r;
   r.kind = req->kind;
   r.n_pert = req->n_pert;
   r.dV.assign(req->dV, req->dV + (size_t)2 * c->rho.n * req->n_pert);
@@ -2220,16 +2359,14 @@ int wgw_submit(wgw_ctx* c, const wgw_request* req, uint64_t* ticket) {
   {
     std::lock_guard<std::mutex> lk(c->qmu);
     if (c->stop) return fail(WGW_ERR_STATE, "context is shutting down");
-    r.ticket = c->next_ticket++;
-    *ticket = r.ticket;
-    c->queue.push_back(std::move(r));
+    *ticket = c->sq.push(std::move(r));
     if (!c->worker.joinable()) c->worker = std::thread(serve_loop, c);
   }
   c->qcv.notify_all();
   return WGW_OK;
 }
 
-static void fill_result(const wgw_ctx::Done& d, wgw_result* res) {
+static void fill_result(const serve::Done& d, wgw_result* res) {
   if (!res) return;
   res->status = d.status;
   res->latency_s = d.latency_s;
@@ -2242,16 +2379,16 @@ int wgw_poll(wgw_ctx* c, uint64_t ticket, int* done, wgw_result* res) {
   g_last_error.clear();
   if (!c || !done) return fail(WGW_ERR_ARG, "null argument");
   std::lock_guard<std::mutex> lk(c->qmu);
-  auto it = c->done.find(ticket);
-  if (it != c->done.end()) {
+  serve::Done d;
+  if (c->sq.take_done(ticket, &d)) {
     *done = 1;
-    fill_result(it->second, res);
-    c->done.erase(it);
+    fill_result(d, res);
     return WGW_OK;
   }
-  if (c->running.count(ticket)) { *done = 0; return WGW_OK; }
-  for (const auto& r : c->queue)
-    if (r.ticket == ticket) { *done = 0; return WGW_OK; }
+  if (c->sq.state(ticket) != serve::Queue::kUnknown) {
+    *done = 0;
+    return WGW_OK;
+  }
   return fail(WGW_ERR_ARG, "unknown or already released ticket");
 }
 
@@ -2259,13 +2396,24 @@ int wgw_wait(wgw_ctx* c, uint64_t ticket, wgw_result* res) {
   g_last_error.clear();
   if (!c) return fail(WGW_ERR_ARG, "null argument");
   std::unique_lock<std::mutex> lk(c->qmu);
-  bool known = c->done.count(ticket) || c->running.count(ticket);
-  for (const auto& r : c->queue) known = known || r.ticket == ticket;
-  if (!known) return fail(WGW_ERR_ARG, "unknown or already released ticket");
-  c->qcv.wait(lk, [&] { return c->done.count(ticket) > 0; });
-  fill_result(c->done[ticket], res);
-  c->done.erase(ticket);
+  if (c->sq.state(ticket) == serve::Queue::kUnknown) return fail(WGW_ERR_ARG, "unknown or already released ticket");
+  c->qcv.wait(lk, [&] { return c->sq.state(ticket) == serve::Queue::kDone; });
+  serve::Done d;
+  c->sq.take_done(ticket, &d);
+  fill_result(d, res);
   return WGW_OK;
+}
+
+int wgw_cancel(wgw_ctx* c, uint64_t ticket) {
+  g_last_error.clear();
+  if (!c) return fail(WGW_ERR_ARG, "null argument");
+  int rc;
+  {
+    std::lock_guard<std::mutex> lk(c->qmu);
+    rc = c->sq.cancel(ticket);
+  }
+  c->qcv.notify_all();
+  return rc == serve::kOk ? WGW_OK : fail(WGW_ERR_ARG, "unknown or already finished ticket");
 }
 
 void wgw_destroy(wgw_ctx* c) { delete c; }
@@ -2279,6 +2427,7 @@ const char* wgw_status_string(int s) {
     case WGW_ERR_CUDA: return "CUDA error";
     case WGW_ERR_TIMEOUT: return "bounded device wait timed out";
     case WGW_ERR_STATE: return "invalid state";
+    case WGW_ERR_CANCELLED: return "request cancelled";
     default: return "unknown status";
   }
 }

@@ -15,11 +15,11 @@ import numpy as np
 from . import build as _build
 
 WGW_OK, WGW_ERR_ARG, WGW_ERR_NOMEM, WGW_ERR_NOCONV = 0, 1, 2, 3
-WGW_ERR_CUDA, WGW_ERR_TIMEOUT, WGW_ERR_STATE = 4, 5, 6
+WGW_ERR_CUDA, WGW_ERR_TIMEOUT, WGW_ERR_STATE, WGW_ERR_CANCELLED = 4, 5, 6, 7
 WGW_FP64, WGW_MIXED = 0, 1
 WGW_SPHERE_WFC, WGW_SPHERE_RHO = 0, 1
 WGW_REQ_CHI0, WGW_REQ_CHIBAR0 = 0, 1
-WGW_PROF_KINDS = 16
+WGW_PROF_KINDS = 18
 
 _dp = ctypes.POINTER(ctypes.c_double)
 
@@ -36,7 +36,8 @@ class Options(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("f_s", ctypes.c_double),
                 ("check_every", ctypes.c_int), ("dav_tol", ctypes.c_double),
                 ("dav_max_iter", ctypes.c_int), ("dav_factor", ctypes.c_int), ("seed", ctypes.c_int),
-                ("fp64_emulation", ctypes.c_int), ("tensor_cores", ctypes.c_int), ("cuda_graphs", ctypes.c_int)]
+                ("fp64_emulation", ctypes.c_int), ("tensor_cores", ctypes.c_int), ("cuda_graphs", ctypes.c_int),
+                ("max_batch_systems", ctypes.c_int), ("fused_h", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -98,7 +99,11 @@ def lib(path: str | None = None):
     L.wgw_symm_eig_noalloc_dev.argtypes = L.wgw_symm_eig_dev.argtypes
     L.wgw_lanczos.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp,
                               ctypes.POINTER(Stats)]
-    L.wgw_system_info.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp]
+    L.wgw_system_info.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp,
+                                  ctypes.POINTER(ctypes.c_int)]
+    L.wgw_cancel.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
+    L.wgw_sample_solutions.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    L.wgw_read_samples.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp]
     L.wgw_submit.argtypes = [ctypes.c_void_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
     L.wgw_poll.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Result)]
     L.wgw_wait.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(Result)]
@@ -328,6 +333,11 @@ def wgw_submit(ctx: Context, dV, omega=(0.0,), kind: int = WGW_REQ_CHI0) -> Tick
     return Ticket(ctx, t.value, out)
 
 
+def wgw_cancel(t: Ticket) -> None:
+    """Cancels a queued or running request (it then completes with WGW_ERR_CANCELLED)."""
+    _check(lib().wgw_cancel(t.ctx.handle, t.ticket), "wgw_cancel")
+
+
 def wgw_poll(t: Ticket):
     """(done, result dict or None); a finished ticket is released by the call that reports it."""
     done, res = ctypes.c_int(), Result()
@@ -479,13 +489,29 @@ def wgw_symm_eig_dev(A_dev, stream=None, w=None, Z=None, noalloc=False):
     return w, Z
 
 
-def wgw_system_info(ctx: Context, n_sys: int):
-    """Per system of the last apply: (CG iterations, final FP64 relative residual)."""
+def wgw_system_info(ctx: Context, n_sys: int, with_flags: bool = False):
+    """Per system of the last batched solve: (CG iterations, final FP64 relative residual) and,
+    with with_flags, the converged flags (1 = met cg_tol)."""
     it = np.zeros(n_sys, np.int32)
     rr = np.zeros(n_sys, np.float64)
+    cv = np.zeros(n_sys, np.int32)
     k = lib().wgw_system_info(ctx.handle, n_sys, it.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
-                              rr.ctypes.data_as(_dp))
-    return it[:k], rr[:k]
+                              rr.ctypes.data_as(_dp), cv.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    return (it[:k], rr[:k], cv[:k]) if with_flags else (it[:k], rr[:k])
+
+
+def wgw_sample_solutions(ctx: Context, systems) -> None:
+    """Select static systems (s = r n_v + v) whose solutions the next applies keep."""
+    sy = np.ascontiguousarray(np.asarray(systems, np.int32))
+    _check(lib().wgw_sample_solutions(ctx.handle, sy.size, sy.ctypes.data_as(ctypes.POINTER(ctypes.c_int))),
+           "wgw_sample_solutions")
+
+
+def wgw_read_samples(ctx: Context, n: int) -> np.ndarray:
+    """The kept solutions of the last static apply: (N_pw, n) complex, canonical order."""
+    out = np.zeros((n, ctx.n_pw), np.complex128)
+    _check(lib().wgw_read_samples(ctx.handle, n, out.ctypes.data_as(_dp)), "wgw_read_samples")
+    return out.T.copy()
 
 
 def _dev_call(fn, name, ctx, x, omega, out, stream, allow_noconv):

@@ -241,11 +241,20 @@ def _real_to_complex(y: np.ndarray, n: int, basis) -> np.ndarray:
     return c
 
 
-def make_system(cfg: Config | str) -> System:
-    """Build the model ground state of a configuration (dense host diagonalisation)."""
+# Above this many plane waves the ground state comes from the iterative block solver below
+# (a dense real-symmetric diagonalisation of 30095^2 would take tens of minutes).
+DENSE_MAX_PW = 9000
+
+
+def make_system(cfg: Config | str, iterative: bool | None = None) -> System:
+    """Build the model ground state of a configuration: dense host diagonalisation, or, for
+    spheres above DENSE_MAX_PW plane waves (or iterative=True), the block solver of
+    _iterative_ground_state started from a dense solve at a lower cutoff (cached on disk)."""
     if isinstance(cfg, str):
         cfg = CONFIGS[cfg]
     miller_wfc = miller_sphere(cfg.L, cfg.ecut)
+    if iterative or (iterative is None and miller_wfc.shape[0] > DENSE_MAX_PW):
+        return _make_system_iterative(cfg)
     miller_rho = miller_sphere(cfg.L, 4.0 * cfg.ecut)
     m_rho = int(np.max(np.abs(miller_rho)))
     if cfg.grid <= 2 * m_rho:
@@ -330,3 +339,246 @@ def gauss_legendre_omega(n: int = 32, omega_max: float = 50.0):
     x, w = np.polynomial.legendre.leggauss(n)
     half = 0.5 * omega_max
     return half * (x + 1.0), half * w
+
+
+# ---------------------------------------------------------------- iterative ground state
+# For the large configuration (96^3 grid, 30095 plane waves, 256 occupied states) the lowest
+# eigenpairs of the model Hamiltonian come from a block LOBPCG iteration (Knyazev 2001) in the
+# real basis {1, sqrt2 cos(G.r), sqrt2 sin(G.r)}, with H applied through real-to-complex FFTs
+# (exact on these alias-free grids: grid > 4 x max Miller index of the wavefunction sphere), a
+# Teter-Payne-Allan kinetic preconditioner, and a start block from a dense diagonalisation at a
+# lower cutoff.  Ground-state diagonalisation only: no response arithmetic.
+
+def _cache_dir() -> str:
+    import os
+    d = os.environ.get("WGW_SYNTH_CACHE") or os.path.join(os.path.dirname(os.path.dirname(
+        os.path.abspath(__file__))), "_cache")
+    os.makedirs(d, exist_ok=True)
+    return d
+
+
+def _to_real_basis(c: np.ndarray, basis) -> np.ndarray:
+    """Complex coefficient columns of functions real in r -> real-basis columns (inverse of
+    _real_to_complex)."""
+    i0, pos, _neg = basis
+    y = np.empty((c.shape[0], c.shape[1]))
+    y[0] = c[i0].real
+    y[1::2] = math.sqrt(2.0) * c[pos].real
+    y[2::2] = -math.sqrt(2.0) * c[pos].imag
+    return y
+
+
+class _RealH:
+    """The model Hamiltonian on real-basis columns: 0.5 G^2 y + FFT[V(r) FFT^-1 y] + B D B^T y."""
+
+    def __init__(self, cfg, miller_wfc, miller_rho, vloc_G, beta_G, d_proj, workers=None):
+        import os
+        import scipy.fft
+        self.fft = scipy.fft
+        self.workers = workers or os.cpu_count()
+        self.N = cfg.grid
+        self.n = miller_wfc.shape[0]
+        self.basis = real_basis_map(miller_wfc)
+        b = 2.0 * math.pi / cfg.L
+        g2 = (b * b) * np.sum(miller_wfc.astype(np.float64) ** 2, axis=1)
+        i0, pos, _ = self.basis
+        self.kin = np.empty(self.n)
+        self.kin[0] = 0.5 * g2[i0]
+        self.kin[1::2] = 0.5 * g2[pos]
+        self.kin[2::2] = 0.5 * g2[pos]
+        N = self.N
+        # Half-spectrum positions (l >= 0) of the sphere members and of the positive members.
+        mw = miller_wfc.astype(np.int64)
+        self.half = np.where(mw[:, 2] >= 0)[0]
+        self.h_idx = tuple(np.mod(mw[self.half].T, N))
+        # Positive members with l >= 0 are read directly, those with l < 0 through their mirror
+        # -G (l > 0) and a conjugation.
+        self.pos_direct = np.where(mw[pos, 2] >= 0)[0]
+        self.pos_mirror = np.where(mw[pos, 2] < 0)[0]
+        self.pos_direct_idx = tuple(np.mod(mw[pos][self.pos_direct].T, N))
+        self.pos_mirror_idx = tuple(np.mod(-mw[pos][self.pos_mirror].T, N))
+        self.i0_idx = (0, 0, 0)
+        mr = miller_rho.astype(np.int64)
+        keep = mr[:, 2] >= 0
+        grid = np.zeros((N, N, N // 2 + 1), np.complex128)
+        grid[tuple(np.mod(mr[keep].T, N))] = vloc_G[keep]
+        self.v_r = scipy.fft.irfftn(grid, s=(N, N, N), axes=(0, 1, 2), workers=self.workers) * N ** 3
+        self.B = _to_real_basis(beta_G, self.basis) if beta_G.shape[1] else None
+        self.D = np.asarray(d_proj, np.float64)
+
+    def __call__(self, y: np.ndarray, chunk: int = 64) -> np.ndarray:
+        out = self.kin[:, None] * y
+        N = self.N
+        s2 = 1.0 / math.sqrt(2.0)
+        for j0 in range(0, y.shape[1], chunk):
+            yb = y[:, j0:j0 + chunk]
+            c = _real_to_complex(yb, self.n, self.basis)
+            grid = np.zeros((yb.shape[1], N, N, N // 2 + 1), np.complex128)
+            grid[(slice(None),) + self.h_idx] = c[self.half].T
+            r = self.fft.irfftn(grid, s=(N, N, N), axes=(1, 2, 3), workers=self.workers) * N ** 3
+            r *= self.v_r[None]
+            g = self.fft.rfftn(r, axes=(1, 2, 3), workers=self.workers) / N ** 3
+            vp = np.empty((yb.shape[1], self.pos_direct.size + self.pos_mirror.size), np.complex128)
+            vp[:, self.pos_direct] = g[(slice(None),) + self.pos_direct_idx]   # value at +G
+            vp[:, self.pos_mirror] = np.conj(g[(slice(None),) + self.pos_mirror_idx])
+            out[0, j0:j0 + chunk] += g[(slice(None),) + self.i0_idx].real
+            out[1::2, j0:j0 + chunk] += (2.0 * s2) * vp.real.T
+            out[2::2, j0:j0 + chunk] += -(2.0 * s2) * vp.imag.T
+        if self.B is not None:
+            out += self.B @ (self.D[:, None] * (self.B.T @ y))
+        return out
+
+    def precondition(self, r: np.ndarray, x: np.ndarray) -> np.ndarray:
+        """Teter-Payne-Allan preconditioner per column, scaled by the column's kinetic energy."""
+        ek = np.sum(self.kin[:, None] * x * x, axis=0) / np.maximum(np.sum(x * x, axis=0), 1e-300)
+        t = self.kin[:, None] / np.maximum(ek[None, :], 1e-3)
+        num = 27.0 + t * (18.0 + t * (12.0 + 8.0 * t))
+        return r * (num / (num + 16.0 * t ** 4))
+
+
+def _orthonormalize(S: np.ndarray) -> np.ndarray:
+    """Orthonormal columns spanning S (Cholesky QR twice, eigen-decomposition of the Gram matrix
+    when it is too ill-conditioned), dropping directions below 1e-13 of the largest."""
+    for _ in range(2):
+        G = S.T @ S
+        try:
+            Lc = np.linalg.cholesky(G)
+            if np.min(np.abs(np.diag(Lc))) < 1e-7 * np.max(np.abs(np.diag(Lc))):
+                raise np.linalg.LinAlgError
+            S = scipy.linalg.solve_triangular(Lc, S.T, lower=True).T
+        except np.linalg.LinAlgError:
+            w, U = np.linalg.eigh(0.5 * (G + G.T))
+            keep = w > 1e-26 * w[-1]
+            S = S @ (U[:, keep] / np.sqrt(w[keep]))
+    return S
+
+
+def _lobpcg(H: _RealH, X: np.ndarray, n_conv: int, tol: float, max_iter: int = 300, log=None):
+    """Lowest eigenpairs of H by block LOBPCG from the columns of X.  Each step: residuals
+    R = HX - X theta, preconditioned W = T R (converged columns left out), Rayleigh-Ritz on
+    span[X, W, P] made orthonormal by whitening its Gram matrix (dropping near-dependent
+    directions), P = the W, P part of the new X.  Converged when the first n_conv residual
+    norms ||H x - theta x|| are <= tol.  Returns (theta, X, iterations), ascending."""
+    X = _orthonormalize(X)
+    m = X.shape[1]
+    HX = H(X)
+    theta, C = np.linalg.eigh(0.5 * (X.T @ HX + HX.T @ X))
+    X, HX = X @ C, HX @ C
+    P = HP = None
+    for it in range(max_iter):
+        R = HX - X * theta[None, :]
+        rn = np.linalg.norm(R, axis=0)
+        if log:
+            log(it, theta, rn)
+        if np.all(rn[:n_conv] <= tol):
+            return theta, X, it
+        act = np.where(rn > 0.1 * tol)[0]
+        Wb = H.precondition(R[:, act], X[:, act])
+        Wb -= X @ (X.T @ Wb)
+        Wb /= np.maximum(np.linalg.norm(Wb, axis=0), 1e-300)[None, :]
+        HW = H(Wb)
+        S = [X, Wb] + ([P] if P is not None else [])
+        HS = [HX, HW] + ([HP] if P is not None else [])
+        S = np.concatenate(S, axis=1)
+        HS = np.concatenate(HS, axis=1)
+        G = S.T @ S
+        A = S.T @ HS
+        g, U = np.linalg.eigh(0.5 * (G + G.T))
+        keep = g > 1e-13 * g[-1]
+        T = U[:, keep] / np.sqrt(g[keep])
+        th, V = np.linalg.eigh(T.T @ (0.5 * (A + A.T)) @ T)
+        Cm = (T @ V)[:, :m]
+        theta = th[:m]
+        P = S[:, m:] @ Cm[m:]
+        HP = HS[:, m:] @ Cm[m:]
+        X = X @ Cm[:m] + P
+        HX = HX @ Cm[:m] + HP
+        # Keep X orthonormal against rounding (a triangular change of basis, applied to HX too).
+        Lc = np.linalg.cholesky(X.T @ X)
+        X = scipy.linalg.solve_triangular(Lc, X.T, lower=True).T
+        HX = scipy.linalg.solve_triangular(Lc, HX.T, lower=True).T
+        nP = np.maximum(np.linalg.norm(P, axis=0), 1e-300)
+        P, HP = P / nP[None, :], HP / nP[None, :]
+        if it % 20 == 19:
+            HX = H(X)                     # drop the rounding drift of the updated images
+            theta, C = np.linalg.eigh(0.5 * (X.T @ HX + HX.T @ X))
+            X, HX = X @ C, HX @ C
+            P = HP = None
+    raise RuntimeError("LOBPCG did not converge")
+
+
+def _cache_key(cfg: Config) -> str:
+    import hashlib
+    return hashlib.sha256(repr(dataclasses.astuple(cfg)).encode() + b"lobpcg-v1").hexdigest()[:20]
+
+
+def _make_system_iterative(cfg: Config, tol: float = 1e-10) -> System:
+    import os
+    miller_wfc = miller_sphere(cfg.L, cfg.ecut)
+    miller_rho = miller_sphere(cfg.L, 4.0 * cfg.ecut)
+    m_wfc = int(np.max(np.abs(miller_wfc)))
+    if cfg.grid <= 4 * m_wfc:
+        raise ValueError("the iterative ground state needs an alias-free grid (> 4 x max Miller)")
+    path = os.path.join(_cache_dir(), f"gs_{cfg.name}_{_cache_key(cfg)}.npz")
+    if os.path.exists(path):
+        z = np.load(path)
+        seed = int(z["seed"])
+        rng = np.random.Generator(np.random.PCG64(seed))
+        positions = rng.uniform(0.0, cfg.L, size=(cfg.n_wells, 3))
+        vloc_G = _gaussian_wells(cfg, miller_rho, positions)
+        beta_G, d_proj, proj_atom = _kb_projectors(cfg, miller_wfc, positions)
+        return System(cfg=cfg, L=cfg.L, omega_cell=cfg.L ** 3, ecut=cfg.ecut, grid=cfg.grid,
+                      miller_wfc=miller_wfc, miller_rho=miller_rho, vloc_G=vloc_G, beta_G=beta_G,
+                      d_proj=d_proj, proj_atom=proj_atom, psi_v=z["psi_v"], e_v=z["e_v"],
+                      e_lumo=float(z["e_lumo"]), positions=positions, well_seed_used=seed)
+    n_want = cfg.n_v + 1                               # the occupied states and the LUMO
+    m = n_want + max(16, cfg.n_v // 16)                # guard vectors
+    seed = cfg.well_seed
+    for _attempt in range(16):
+        rng = np.random.Generator(np.random.PCG64(seed))
+        positions = rng.uniform(0.0, cfg.L, size=(cfg.n_wells, 3))
+        vloc_G = _gaussian_wells(cfg, miller_rho, positions)
+        beta_G, d_proj, proj_atom = _kb_projectors(cfg, miller_wfc, positions)
+        H = _RealH(cfg, miller_wfc, miller_rho, vloc_G, beta_G, d_proj)
+        X0 = _low_cutoff_start(cfg, miller_wfc, positions, m, H.basis)
+        theta, X, _ = _lobpcg(H, X0, n_want, tol)
+        if theta[cfg.n_v] - theta[cfg.n_v - 1] >= cfg.min_gap:
+            break
+        seed += 1
+    else:
+        raise RuntimeError("no gapped model found")
+    y = X[:, : cfg.n_v].copy()
+    piv = np.argmax(np.abs(y), axis=0)
+    y *= np.sign(y[piv, np.arange(y.shape[1])])[None, :]
+    psi_v = _real_to_complex(y, miller_wfc.shape[0], H.basis)
+    e_v = theta[: cfg.n_v].copy()
+    np.savez(path + ".tmp.npz", psi_v=psi_v, e_v=e_v, e_lumo=theta[cfg.n_v], seed=seed)
+    os.replace(path + ".tmp.npz", path)
+    return System(cfg=cfg, L=cfg.L, omega_cell=cfg.L ** 3, ecut=cfg.ecut, grid=cfg.grid,
+                  miller_wfc=miller_wfc, miller_rho=miller_rho, vloc_G=vloc_G, beta_G=beta_G,
+                  d_proj=d_proj, proj_atom=proj_atom, psi_v=psi_v, e_v=e_v,
+                  e_lumo=float(theta[cfg.n_v]), positions=positions, well_seed_used=seed)
+
+
+def _low_cutoff_start(cfg: Config, miller_wfc, positions, m: int, basis) -> np.ndarray:
+    """Start block: the m lowest eigenvectors of the same model at a cutoff with about 5000 plane
+    waves (dense diagonalisation), placed in the full sphere's real basis."""
+    n = miller_wfc.shape[0]
+    ecut0 = min(cfg.ecut, cfg.ecut * (5000.0 / n) ** (2.0 / 3.0))
+    lo = dataclasses.replace(cfg, ecut=ecut0)
+    mw0 = miller_sphere(cfg.L, ecut0)
+    mr0 = miller_sphere(cfg.L, 4.0 * ecut0)
+    v0 = _gaussian_wells(lo, mr0, positions)
+    b0, d0, _ = _kb_projectors(lo, mw0, positions)
+    Hr, basis0 = _dense_h_real(lo, mw0, mr0, v0, b0, d0)
+    _, vecs = scipy.linalg.eigh(Hr, subset_by_index=[0, min(m, Hr.shape[0]) - 1], driver="evr")
+    c0 = _real_to_complex(vecs, mw0.shape[0], basis0)
+    where = {tuple(g): i for i, g in enumerate(miller_wfc.tolist())}
+    idx = np.array([where[tuple(g)] for g in mw0.tolist()])
+    c = np.zeros((n, vecs.shape[1]), np.complex128)
+    c[idx] = c0
+    X = _to_real_basis(c, basis)
+    if X.shape[1] < m:
+        rng = np.random.default_rng(0)
+        X = np.concatenate([X, rng.standard_normal((n, m - X.shape[1]))], axis=1)
+    return X

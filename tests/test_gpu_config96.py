@@ -1,0 +1,108 @@
+"""The 96^3 Kleinman-Bylander configuration at full size on the GPU, against the oracle.
+
+Model: L = 24 bohr, ecut 12.75 Ha, 96^3 grid (30095 plane waves, 240417 density-sphere
+G-vectors), 64 atoms each with a Gaussian well and s + p projectors (256 projectors), 256
+occupied states from the iterative ground state of synth.  The apply is the benchmarked one:
+chibar0 on 256 perturbations = 65536 Sternheimer systems, mixed path, cg_tol 1e-10, in
+device-memory chunks of whole perturbations.
+
+Checks (the oracle cannot apply chi0 to a whole perturbation at this size in test time, so it
+solves sampled systems one by one, and properties that hold at any size cover the rest):
+  * 16 sampled systems spread over (state, perturbation): the library's solution dpsi of each
+    equals the oracle's FP64 CG solution of the same Eq. sternheimer system within 1e-8
+    (relative 2-norm), and every system converged;
+  * the 256 x 256 matrix <phi_a|chibar0 phi_b> of the batch is symmetric to 1e-8 of its norm and
+    negative definite (chibar0 is Hermitian and negative semidefinite, Sec. 2.1).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+N_SAMPLES = 16
+
+
+@pytest.fixture(scope="module")
+def W():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_05623_gb300 import build
+    build.build()
+    import paper_2203_05623_gb300 as W
+    return W
+
+
+def _oracle_solution(job):
+    """Worker: FP64 CG solution of one static system (state v, perturbation column phi) of the
+    96^3 model."""
+    v, phi = job
+    from oracle import chi0
+    from oracle.model import Model
+    s = synth.make_system("kb_L24_96")
+    m = Model(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, s.beta_G, s.d_proj)
+    dV_r = m.to_r(m.vsqrt * phi, m.mr)
+    x, it = chi0.sternheimer_cg_solve(m, dV_r, v, tol=1e-12, max_iter=4000)
+    return x, it
+
+
+@pytest.fixture(scope="module")
+def sys96():
+    return synth.make_system("kb_L24_96")
+
+
+@pytest.fixture(scope="module")
+def samples(sys96):
+    """(v, p) of the sampled systems and the oracle's solutions, computed in spawned processes
+    before the first GPU call of this module."""
+    import multiprocessing as mp
+    rng = np.random.default_rng(96)
+    picks = [(int(v), int(p)) for v, p in zip(rng.choice(256, N_SAMPLES, replace=False),
+                                               rng.choice(256, N_SAMPLES, replace=False))]
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = "1"
+    phi = synth.perturbations(sys96.miller_rho, sys96.L, 256, 5)
+    jobs = [(v, phi[:, p].copy()) for v, p in picks]
+    del phi
+    try:
+        with mp.get_context("spawn").Pool(min(N_SAMPLES, os.cpu_count() or 1)) as pool:
+            ref = pool.map(_oracle_solution, jobs)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return picks, ref
+
+
+def test_config96_full_batch(W, sys96, samples):
+    import torch
+    s = sys96
+    assert s.n_pw == 30095 and s.n_rho == 240417 and s.beta_G.shape[1] == 256 and s.n_v == 256
+    picks, ref = samples
+    phi = synth.perturbations(s.miller_rho, s.L, 256, 5)
+    ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v,
+                      W.wgw_default_options(precision=W.WGW_MIXED, cg_tol=1e-10, max_cg_iter=300),
+                      beta_G=s.beta_G, d_proj=s.d_proj)
+    W.wgw_sample_solutions(ctx, [p * 256 + v for v, p in picks])
+    x = torch.from_numpy(np.ascontiguousarray(phi.T)).cuda()
+    out = torch.zeros((1, 256, s.n_rho), dtype=torch.complex128, device="cuda")
+    st, _ = W.wgw_apply_chibar0_dev(ctx, x, [0.0], out)
+    torch.cuda.synchronize()
+    assert st["n_systems"] == 65536 and st["n_converged"] == 65536
+    got = W.wgw_read_samples(ctx, len(picks))
+    for k, ((v, p), (xr, it)) in enumerate(zip(picks, ref)):
+        err = np.linalg.norm(got[:, k] - xr) / np.linalg.norm(xr)
+        assert err < 1e-8, (v, p, err, it)
+    M = phi.conj().T @ out[0].cpu().numpy().T          # <phi_a | chibar0 phi_b>
+    assert np.max(np.abs(M.imag)) < 1e-8 * np.max(np.abs(M))
+    Mr = M.real
+    assert np.linalg.norm(Mr - Mr.T) < 1e-8 * np.linalg.norm(Mr)
+    assert np.max(np.linalg.eigvalsh(0.5 * (Mr + Mr.T))) < 0
