@@ -526,6 +526,45 @@ def library_baselines(W, ctx, s, prof_all):
                     "pc_project class (lists of varying length), cuBLAS as one call on 4096 systems"}
 
 
+def fp64_path(W, s, wl, x, out_mixed, stream, ph, oh, steps):
+    """The same workload on the all-FP64 GPU path (FP64 CG to the same cg_tol, native FP64 FFT
+    passes), measured in the same process: device time, end to end through the host-pointer
+    entry point, and the relative difference of the mixed path's result from it."""
+    import numpy as np
+    import torch
+    kb = s.beta_G.shape[1] > 0
+    opt = W.wgw_default_options(precision=W.WGW_FP64, cg_tol=wl["cg_tol"], max_cg_iter=2000)
+    ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, opt,
+                      beta_G=s.beta_G if kb else None, d_proj=s.d_proj if kb else None)
+    out = torch.zeros_like(out_mixed)
+    st, _ = W.wgw_apply_chibar0_dev(ctx, x, [0.0], out, stream=stream.cuda_stream)   # warm-up
+    times = []
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st, _ = W.wgw_apply_chibar0_dev(ctx, x, [0.0], out, stream=stream.cuda_stream)
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b) / 1e3)
+    e2e = []
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        W.wgw_apply_chibar0(ctx, ph.T, [0.0], out=oh)
+        e2e.append(time.perf_counter() - t0)
+    ref = out[0].cpu().numpy()
+    mix = out_mixed[0].cpu().numpy()
+    diff = float(np.max(np.linalg.norm(mix - ref, axis=1) / np.linalg.norm(ref, axis=1)))
+    W.wgw_destroy(ctx)
+    n = st["n_systems"]
+    return {"value": n * steps / sum(times), "unit": "Sternheimer solves/s", "ms_per_step": 1e3 * sum(times) / steps,
+            "e2e": {"value": n * steps / sum(e2e), "unit": "Sternheimer solves/s"},
+            "max_rel_residual": st["max_rel_residual"], "max_iters": st["max_iters"],
+            "mixed_vs_fp64_rel_diff": diff,
+            "what": "same workload, all-FP64 GPU path (FP64 CG and FFT passes), same process; "
+                    "mixed_vs_fp64_rel_diff = max over perturbations of ||mixed - fp64|| / ||fp64||"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -534,6 +573,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="pdep_L16_48", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-path", action="store_true",
+                    help="skip the all-FP64 GPU path measured beside the mixed one")
     ap.add_argument("--no-library-baselines", action="store_true",
                     help="skip the cuFFT / cuBLAS comparison on the same shapes")
     ap.add_argument("--n-pert", type=int, default=0,
@@ -666,8 +707,10 @@ def main():
     hbm, peak_kind = peaks()
     d = prof[dom]
     per_launch = d["bytes"] / max(d["launches"], 1)
-    if dom == "pc_project":
-        # CUDA-core FP32 GEMMs: bound by the FP32 FMA rate (152 SMs x 128 lanes x 2 flop x 2.07 GHz).
+    if dom in ("pc_project", "hpsi_fused"):
+        # CUDA-core FP32 GEMMs, or the fused H kernel whose FFT intermediate never leaves the SMs:
+        # bound by the FP32 FMA rate (152 SMs x 128 lanes x 2 flop x 2.07 GHz).  The fused kernel's
+        # flops are counted as 5 n log2 n per length-n line transform.
         bound, unit, peak, peak_src = "alu", "TFLOP/s", 152 * 128 * 2 * 2.07e9 / 1e12, "FP32 FMA unit count x max SM clock"
         achieved = d["flops"] / (d["ms"] / 1e3) / 1e12 if d["ms"] > 0 else 0.0
     else:
@@ -714,6 +757,8 @@ def main():
     if cpu:
         line["cpu_baseline"] = cpu
     line["autotune"] = W.wgw_autotune_info(ctx)
+    if world == 1 and args.precision == "mixed" and not args.no_fp64_path and args.workload == "pdep_L16_48":
+        line["fp64_path"] = fp64_path(W, s, wl, x, out, stream, ph, oh, min(args.steps, 3))
     if world == 1 and args.precision == "mixed" and not args.no_library_baselines:
         line["library_baseline"] = library_baselines(W, ctx, s, prof_all)
     if rank == 0:

@@ -55,6 +55,7 @@ class Config:
     kb_dch: bool = False      # five more (d-type) KB projectors per atom
     kb_d_d: float = 0.3       # D_d [Ha]
     min_gap: float = 0.01     # reseed (seed + 1) while HOMO-LUMO gap < this [Ha]
+    min_dist: float = 0.0     # hard core: redraw a centre closer than this to an earlier one [bohr]
 
 
 CONFIGS = {
@@ -65,9 +66,13 @@ CONFIGS = {
     # Seeds 3-8 give HOMO-LUMO gaps below 0.01 Ha; the reseeding rule lands on 9.
     "pdep_L16_48": Config("pdep_L16_48", L=16.0, ecut=7.75, grid=48, n_wells=32,
                           well_seed=9, n_v=64, n_pert=64, pert_seed=5),
-    # 96^3 grid, ~30k plane waves, 64 atoms with wells + KB projectors, N_v = 256.
+    # 96^3 grid, ~30k plane waves, 64 atoms with wells + KB projectors, N_v = 256 = 4 per atom.
+    # The wells are 6 Ha deep and 0.9 bohr wide and the atoms at least 4 bohr apart, so that each
+    # atom binds an s and three p states below a gap (the 2 Ha, 1 bohr well of the smaller models
+    # binds one state per atom, and 256 states would then fill a continuum with gaps of ~1e-3 Ha).
     "kb_L24_96": Config("kb_L24_96", L=24.0, ecut=12.75, grid=96, n_wells=64,
-                        well_seed=4, n_v=256, n_pert=256, pert_seed=5, kb=True),
+                        well_seed=4, n_v=256, n_pert=256, pert_seed=5, kb=True,
+                        well_depth=6.0, well_width=0.9, min_dist=4.0),
     # Tiny case (12^3) for quick host checks.
     "tiny_L6_12": Config("tiny_L6_12", L=6.0, ecut=2.5, grid=12, n_wells=2,
                          well_seed=7, n_v=2, n_pert=3, pert_seed=8),
@@ -148,6 +153,27 @@ def _structure_factor(miller: np.ndarray, positions: np.ndarray, L: float) -> np
     """S_a(G) = exp(-i G . R_a) for every G (rows) and atom (columns)."""
     G = (2.0 * math.pi / L) * miller.astype(np.float64)
     return np.exp(-1j * (G @ positions.T))
+
+
+def _positions(cfg: Config, seed: int) -> np.ndarray:
+    """Centres uniform in the cell from a seeded PCG64; with cfg.min_dist > 0 a centre closer than
+    min_dist (minimum image) to an earlier one is redrawn from the same stream."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if cfg.min_dist <= 0:
+        return rng.uniform(0.0, cfg.L, size=(cfg.n_wells, 3))
+    pts = []
+    while len(pts) < cfg.n_wells:
+        p = rng.uniform(0.0, cfg.L, size=3)
+        ok = True
+        for q in pts:
+            d = p - q
+            d -= cfg.L * np.round(d / cfg.L)
+            if np.dot(d, d) < cfg.min_dist ** 2:
+                ok = False
+                break
+        if ok:
+            pts.append(p)
+    return np.asarray(pts)
 
 
 def _gaussian_wells(cfg: Config, miller_rho: np.ndarray, positions: np.ndarray) -> np.ndarray:
@@ -261,8 +287,7 @@ def make_system(cfg: Config | str, iterative: bool | None = None) -> System:
         raise ValueError(f"grid {cfg.grid} too small for density sphere (max Miller {m_rho})")
     seed = cfg.well_seed
     for _attempt in range(64):
-        rng = np.random.Generator(np.random.PCG64(seed))
-        positions = rng.uniform(0.0, cfg.L, size=(cfg.n_wells, 3))
+        positions = _positions(cfg, seed)
         vloc_G = _gaussian_wells(cfg, miller_rho, positions)
         beta_G, d_proj, proj_atom = _kb_projectors(cfg, miller_wfc, positions)
         Hr, basis = _dense_h_real(cfg, miller_wfc, miller_rho, vloc_G, beta_G, d_proj)
@@ -453,12 +478,13 @@ def _orthonormalize(S: np.ndarray) -> np.ndarray:
     return S
 
 
-def _lobpcg(H: _RealH, X: np.ndarray, n_conv: int, tol: float, max_iter: int = 300, log=None):
+def _lobpcg(H: _RealH, X: np.ndarray, n_conv: int, tol: float, max_iter: int = 300, log=None, give_up=None):
     """Lowest eigenpairs of H by block LOBPCG from the columns of X.  Each step: residuals
     R = HX - X theta, preconditioned W = T R (converged columns left out), Rayleigh-Ritz on
     span[X, W, P] made orthonormal by whitening its Gram matrix (dropping near-dependent
     directions), P = the W, P part of the new X.  Converged when the first n_conv residual
-    norms ||H x - theta x|| are <= tol.  Returns (theta, X, iterations), ascending."""
+    norms ||H x - theta x|| are <= tol.  Returns (theta, X, iterations), ascending, or None when
+    give_up(theta, residual norms) says so first."""
     X = _orthonormalize(X)
     m = X.shape[1]
     HX = H(X)
@@ -472,6 +498,8 @@ def _lobpcg(H: _RealH, X: np.ndarray, n_conv: int, tol: float, max_iter: int = 3
             log(it, theta, rn)
         if np.all(rn[:n_conv] <= tol):
             return theta, X, it
+        if give_up is not None and give_up(theta, rn):
+            return None
         act = np.where(rn > 0.1 * tol)[0]
         Wb = H.precondition(R[:, act], X[:, act])
         Wb -= X @ (X.T @ Wb)
@@ -523,8 +551,7 @@ def _make_system_iterative(cfg: Config, tol: float = 1e-10) -> System:
     if os.path.exists(path):
         z = np.load(path)
         seed = int(z["seed"])
-        rng = np.random.Generator(np.random.PCG64(seed))
-        positions = rng.uniform(0.0, cfg.L, size=(cfg.n_wells, 3))
+        positions = _positions(cfg, seed)
         vloc_G = _gaussian_wells(cfg, miller_rho, positions)
         beta_G, d_proj, proj_atom = _kb_projectors(cfg, miller_wfc, positions)
         return System(cfg=cfg, L=cfg.L, omega_cell=cfg.L ** 3, ecut=cfg.ecut, grid=cfg.grid,
@@ -535,15 +562,22 @@ def _make_system_iterative(cfg: Config, tol: float = 1e-10) -> System:
     m = n_want + max(16, cfg.n_v // 16)                # guard vectors
     seed = cfg.well_seed
     for _attempt in range(16):
-        rng = np.random.Generator(np.random.PCG64(seed))
-        positions = rng.uniform(0.0, cfg.L, size=(cfg.n_wells, 3))
+        positions = _positions(cfg, seed)
         vloc_G = _gaussian_wells(cfg, miller_rho, positions)
         beta_G, d_proj, proj_atom = _kb_projectors(cfg, miller_wfc, positions)
         H = _RealH(cfg, miller_wfc, miller_rho, vloc_G, beta_G, d_proj)
         X0 = _low_cutoff_start(cfg, miller_wfc, positions, m, H.basis)
-        theta, X, _ = _lobpcg(H, X0, n_want, tol)
-        if theta[cfg.n_v] - theta[cfg.n_v - 1] >= cfg.min_gap:
-            break
+
+        def gap_too_small(theta, rn, nv=cfg.n_v):
+            # Residuals below 1e-5 put the eigenvalues within ~1e-9 of their limits: a gap
+            # clearly below min_gap by then will not open up, so the seed is dropped early.
+            return np.max(rn[: nv + 1]) < 1e-5 and theta[nv] - theta[nv - 1] < cfg.min_gap - 1e-6
+
+        res = _lobpcg(H, X0, n_want, tol, give_up=gap_too_small)
+        if res is not None:
+            theta, X, _ = res
+            if theta[cfg.n_v] - theta[cfg.n_v - 1] >= cfg.min_gap:
+                break
         seed += 1
     else:
         raise RuntimeError("no gapped model found")

@@ -1,8 +1,9 @@
 """The 96^3 Kleinman-Bylander configuration at full size on the GPU, against the oracle.
 
 Model: L = 24 bohr, ecut 12.75 Ha, 96^3 grid (30095 plane waves, 240417 density-sphere
-G-vectors), 64 atoms each with a Gaussian well and s + p projectors (256 projectors), 256
-occupied states from the iterative ground state of synth.  The apply is the benchmarked one:
+G-vectors), 64 atoms (centres at least 4 bohr apart) each with a Gaussian well (6 Ha deep,
+0.9 bohr wide) and s + p projectors (256 projectors), 256 occupied states (s + 3p per atom,
+HOMO-LUMO gap ~0.48 Ha) from the iterative ground state of synth.  The apply is the benchmarked one:
 chibar0 on 256 perturbations = 65536 Sternheimer systems, mixed path, cg_tol 1e-10, in
 device-memory chunks of whole perturbations.
 

@@ -117,8 +117,8 @@ def test_davidson_config48_sampled_against_oracle(W):
     eigenvalues to 1e-8 (relative), and the oracle residual of each returned vector is
     within the Davidson stopping rule (sqrt(dav_tol)).  Every returned eigenvalue is negative
     and they ascend; the basis is orthonormal.  "Leading" is pinned independently of the
-    Davidson: the six most negative eigenvalues of the oracle's static chi0bar, from a block
-    LOBPCG iteration (scipy, seeded random start, no information from the GPU) on the oracle's
+    Davidson: the six most negative eigenvalues of the oracle's static chi0bar, from ARPACK
+    (implicitly restarted Lanczos, seeded start, no information from the GPU) on the oracle's
     operator in the real basis, equal the six lowest returned eigenvalues, so a Davidson run
     that missed a lower eigenvalue fails.
     """
@@ -154,11 +154,9 @@ def test_davidson_config48_sampled_against_oracle(W):
 
 def _oracle_lowest_chibar0(m, states, k):
     """The k most negative eigenvalues of the static chi0bar of the oracle (sum over states),
-    by block LOBPCG on the real basis {G = 0, sqrt2 Re, sqrt2 Im of each +-G pair}: a vector y of
+    by ARPACK on the real basis {G = 0, sqrt2 Re, sqrt2 Im of each +-G pair}: a vector y of
     that basis is the real-in-r function with coefficients c(G) = (y_re - i y_im)/sqrt2 at G and
-    the conjugate at -G, on which chi0bar is real symmetric.  The operator is applied to whole
-    blocks (the oracle's static sum over states takes a block of perturbations at once); residual
-    norms below 1e-6 put the eigenvalues within ~1e-12 (the error is quadratic in the residual)."""
+    the conjugate at -G, on which chi0bar is real symmetric."""
     import scipy.sparse.linalg as sla
     from oracle import chi0
     i0, pos, neg = synth.real_basis_map(m.mr)
@@ -186,6 +184,6 @@ def _oracle_lowest_chibar0(m, states, k):
         return to_y(out)
 
     op = sla.LinearOperator((n_rho, n_rho), matvec=mv, matmat=mv, dtype=np.float64)
-    X0 = np.random.default_rng(7).standard_normal((n_rho, k + 4))
-    w, _ = sla.lobpcg(op, X0, tol=1e-6, maxiter=80, largest=False)
-    return np.sort(w)[:k]
+    v0 = np.random.default_rng(7).standard_normal(n_rho)
+    w = sla.eigsh(op, k=k, which="SA", tol=1e-12, ncv=4 * k, v0=v0, return_eigenvectors=False)
+    return np.sort(w)
