@@ -90,7 +90,8 @@ typedef struct wgw_options {
                              fit 85 % of the free device memory (the default). */
   int fused_h;            /* MIXED: 1 = the FP32 H application runs as one kernel per pair with the FFT
                              intermediate in (distributed) shared memory, on the grids it supports (24, 32,
-                             48); 0 = three kernels with the intermediate in device memory.  Same results. */
+                             48); 0 = three kernels with the intermediate in device memory.  The same
+                             operations: results agree to FP32 rounding. */
 } wgw_options;
 
 typedef struct wgw_stats {

@@ -10,9 +10,10 @@
 // writing the 2m+1 values of each line in the planes of every CTA of the cluster through
 // distributed shared memory; stage 3 transforms its planes back along y then z in place,
 // gathers the sphere, unpacks the pair and applies the epilogue.  Cluster barriers separate the
-// stages.  The arithmetic is that of the three separate kernels (same bodies, same order), so
-// the results are bit-identical to them; per pair the HBM traffic drops from four passes over
-// (2m+1) N^2 complex values to the two sphere vectors in and the one out.
+// stages.  The butterflies are those of the three separate kernels (same radix plans, same
+// order; the compiler's FMA contraction differs, so results agree to FP32 rounding); per pair
+// the HBM traffic drops from four passes over (2m+1) N^2 complex values to the two sphere
+// vectors in and the one out.
 #include <cooperative_groups.h>
 
 #include "internal.h"

@@ -107,6 +107,12 @@ constexpr int kTcSplitDefault = 8, kTcSplitMax = 16;
 cudaError_t launch_pc_tc(float* Y, long ldy, int n_sys, const int* list, const unsigned char* tiles, int n, int nv,
                          const int* active, float* work, cudaStream_t st, int* err, int split = kTcSplitDefault);
 size_t tc_pc_work_elems(int n, int n_sys, int nv);
+// Kleinman-Bylander term on the tensor cores: Q[s] += B diag(D) B^T P[s] for the systems of a list
+// (active only), B (n x n_proj, n_proj <= 256) as operand tiles from launch_tc_tile_psi, D on the
+// device; 3xTF32 products with FP32 accumulation, work and err as for launch_pc_tc.
+cudaError_t launch_kb_tc(float* Q, const float* P, long ld, int n_sys, const int* list, const unsigned char* tiles,
+                         int n, int n_proj, const float* D, const int* active, float* work, cudaStream_t st, int* err,
+                         int split = kTcSplitDefault);
 bool tc_pc_supported(int nv);
 // Psi (n x nv, column v at Psi + v ldp) split into TF32 hi/lo parts and laid out as the operand
 // tiles of both phases; tc_psi_tile_bytes(n, nv) bytes.

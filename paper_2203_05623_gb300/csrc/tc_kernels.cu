@@ -343,10 +343,11 @@ __global__ void __launch_bounds__(kThreads) k_tc_pc1(const unsigned char* __rest
   if (warp == 0) tmem_dealloc(tmem, ncols);
 }
 
-// C^T[j][v] = sum_kb Cpart[kb][j][v] (fixed order), written split and tiled for phase 2:
-// ((jt * nvc + vc) * 2 + part) * kTile + tile_off(j % 128, v % 32); zero outside n_list x nv.
+// C^T[j][v] = scale[v] sum_kb Cpart[kb][j][v] (fixed order; scale null = 1), written split and
+// tiled for phase 2: ((jt * nvc + vc) * 2 + part) * kTile + tile_off(j % 128, v % 32); zero outside
+// n_list x nv.
 __global__ void k_tc_reduce(const float* __restrict__ Cpart, int n_list, int ldc, int n_kb, int nv, int njt,
-                            int nvc, unsigned char* __restrict__ ct) {
+                            int nvc, const float* __restrict__ scale, unsigned char* __restrict__ ct) {
   const long total = static_cast<long>(njt) * kRowsA * nvc * kKC;
   const size_t slice = static_cast<size_t>(n_list) * ldc;
   for (long e = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; e < total;
@@ -366,6 +367,7 @@ __global__ void k_tc_reduce(const float* __restrict__ Cpart, int n_list, int ldc
       }
       for (; kb < n_kb; ++kb) s1 += Cpart[static_cast<size_t>(kb) * slice + o];
       sum = (s0 + s1) + (s2 + s3);
+      if (scale) sum *= scale[v];
     }
     float hi, lo;
     split_tf32(sum, hi, lo);
@@ -535,8 +537,11 @@ size_t tc_pc_work_elems(int n, int n_sys, int nv) {
 
 bool tc_pc_supported(int nv) { return nv >= 1 && nv <= 256; }
 
-cudaError_t launch_pc_tc(float* Y, long ldy, int n_sys, const int* list, const unsigned char* tiles, int n, int nv,
-                         const int* active, float* work, cudaStream_t st, int* err, int split) {
+// Yout[s] = beta Yout[s] + alpha M diag(scale) M^T Yin[s] for the systems of a list, M (n x nv) given
+// as operand tiles (launch_tc_tile_psi): phase 1 reads Yin, phase 2 updates Yout (which may be Yin).
+static cudaError_t launch_tc_pair(const float* Yin, float* Yout, long ldy, int n_sys, const int* list,
+                                  const unsigned char* tiles, int n, int nv, const float* scale, float alpha, float beta,
+                                  const int* active, float* work, cudaStream_t st, int* err, int split) {
   if (n_sys == 0 || nv == 0) return cudaSuccess;
   if (!tc_pc_supported(nv) || !err || split < 1 || split > kTcSplitMax) return cudaErrorInvalidValue;
   const TcGeom g = tc_geom(n, n_sys, nv, split);
@@ -548,21 +553,32 @@ cudaError_t launch_pc_tc(float* Y, long ldy, int n_sys, const int* list, const u
   cudaError_t e = cudaFuncSetAttribute(tc::k_tc_pc1, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem1));
   if (e != cudaSuccess) return e;
-  tc::k_tc_pc1<<<dim3(g.njt, g.n_kb), tc::kThreads, smem1, st>>>(t1, Y, ldy, n, nv, n_sys, list, g.kcpb, g.Nn,
+  tc::k_tc_pc1<<<dim3(g.njt, g.n_kb), tc::kThreads, smem1, st>>>(t1, Yin, ldy, n, nv, n_sys, list, g.kcpb, g.Nn,
                                                                  g.ldc, Cpart, err);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long total = static_cast<long>(g.njt) * tc::kRowsA * g.nvc * tc::kKC;
   tc::k_tc_reduce<<<static_cast<int>(std::min<long>((total + 255) / 256, 8192)), 256, 0, st>>>(
-      Cpart, n_sys, g.ldc, g.n_kb, nv, g.njt, g.nvc, ct);
+      Cpart, n_sys, g.ldc, g.n_kb, nv, g.njt, g.nvc, scale, ct);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t smem2 = 4u * tc::kTile + 64 + tc::kRowsA * sizeof(int);
   e = cudaFuncSetAttribute(tc::k_tc_pc2, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem2));
   if (e != cudaSuccess) return e;
-  tc::k_tc_pc2<<<dim3(g.nrt, g.njt), tc::kThreads2, smem2, st>>>(t2, ct, Y, ldy, n, g.nvc, n_sys, list, -1.f, 1.f,
-                                                                active, err);
+  tc::k_tc_pc2<<<dim3(g.nrt, g.njt), tc::kThreads2, smem2, st>>>(t2, ct, Yout, ldy, n, g.nvc, n_sys, list, alpha,
+                                                                beta, active, err);
   return cudaGetLastError();
+}
+
+cudaError_t launch_pc_tc(float* Y, long ldy, int n_sys, const int* list, const unsigned char* tiles, int n, int nv,
+                         const int* active, float* work, cudaStream_t st, int* err, int split) {
+  return launch_tc_pair(Y, Y, ldy, n_sys, list, tiles, n, nv, nullptr, -1.f, 1.f, active, work, st, err, split);
+}
+
+cudaError_t launch_kb_tc(float* Q, const float* P, long ld, int n_sys, const int* list, const unsigned char* tiles,
+                         int n, int n_proj, const float* D, const int* active, float* work, cudaStream_t st, int* err,
+                         int split) {
+  return launch_tc_pair(P, Q, ld, n_sys, list, tiles, n, n_proj, D, 1.f, 1.f, active, work, st, err, split);
 }
 
 cudaError_t tc_wait_selftest(int* dev_flag, cudaStream_t st) {

@@ -215,7 +215,7 @@ struct wgw_ctx {
   // apply work space (double unless noted)
   DevBuf dvin, dv_rb, dv_r, Trho, Dr, drho_rb, eps, a_idx, b_idx, brow, cg_rz, cg_bb, cg_rr,
       cg_act, cg_it, cnt, rr64, act64, norms, pc_work, sys_list, list64, cg_rzi, omg, row_list, rowact,
-      drho_all, psi_tc, cg_best, cg_itbest, lz_q, lz_qf, tc_err;
+      drho_all, psi_tc, kb_tc, cg_best, cg_itbest, lz_q, lz_qf, tc_err;
   cudaStream_t stream = nullptr;
   Prof prof;
   // Autotuner results: the K split of the tensor-core P_c (phase-1 CTAs per SM; 0 = not tuned
@@ -254,7 +254,7 @@ struct wgw_ctx {
     d.release(); f.release(); wfc.release(); rho.release();
     DevBuf* all[] = {&e_v_d, &dvin, &dv_rb, &dv_r, &Trho, &Dr, &drho_rb, &eps, &a_idx, &b_idx, &brow,
                      &cg_rz, &cg_bb, &cg_rr, &cg_act, &cg_it, &cnt, &rr64, &act64, &norms, &pc_work, &sys_list, &list64, &cg_rzi, &omg,
-                     &row_list, &rowact, &drho_all, &psi_tc, &cg_best, &cg_itbest, &lz_q, &lz_qf, &tc_err};
+                     &row_list, &rowact, &drho_all, &psi_tc, &kb_tc, &cg_best, &cg_itbest, &lz_q, &lz_qf, &tc_err};
     for (DevBuf* b : all) b->release();
     if (stream) cudaStreamDestroy(stream);
   }
@@ -339,8 +339,10 @@ int run_pc(wgw_ctx* c, T* Y, int n_list, const int* list, const T* Psi, const in
   if (tcores && !c->psi_tc.p) {   // operand tiles of the occupied block and the wait flag, once per context
     WGW_TRY(c->psi_tc.ensure(tc_psi_tile_bytes((int)n, c->n_v)));
     WGW_CK(launch_tc_tile_psi(c->f.psi.as<float>(), c->ld_w, (int)n, c->n_v, c->psi_tc.as<unsigned char>(), st));
-    WGW_TRY(c->tc_err.ensure(sizeof(int)));
-    WGW_CK(cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), st));
+    if (!c->tc_err.p) {
+      WGW_TRY(c->tc_err.ensure(sizeof(int)));
+      WGW_CK(cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), st));
+    }
   }
   const unsigned char* tiles = tcores ? c->psi_tc.as<unsigned char>() : nullptr;
   if (tcores && c->tc_split == 0 && n_list >= 256) {
@@ -398,8 +400,24 @@ int apply_A(wgw_ctx* c, Prec<T>& pr, const T* P, T* Q, int n_list, const int* li
       return launch_plane_r2g<T>(c->wfc.tab(), c->wfc.npt_max, f, Tb, e, st); }));
   }
   if (c->n_proj > 0) {
-    WGW_TRY(c->pc_work.ensure(sizeof(T) * pc_work_elems(nrb, n_list, std::max(c->n_v, c->n_proj))));
+    WGW_TRY(c->pc_work.ensure(sizeof(T) * std::max(pc_work_elems(nrb, n_list, std::max(c->n_v, c->n_proj)),
+                                                   tc_pc_work_elems(nrb, n_list, std::max(c->n_v, c->n_proj)))));
+    const bool kb_tc = sizeof(T) == sizeof(float) && c->opt.tensor_cores != 0 && tc_pc_supported(c->n_proj);
+    if (kb_tc && !c->kb_tc.p) {   // operand tiles of the projectors, once per context
+      WGW_TRY(c->kb_tc.ensure(tc_psi_tile_bytes(nrb, c->n_proj)));
+      WGW_CK(launch_tc_tile_psi(c->f.kbB.as<float>(), c->ld_w, nrb, c->n_proj, c->kb_tc.as<unsigned char>(), st));
+      if (!c->tc_err.p) {
+        WGW_TRY(c->tc_err.ensure(sizeof(int)));
+        WGW_CK(cudaMemsetAsync(c->tc_err.p, 0, sizeof(int), st));
+      }
+    }
     WGW_CK(c->prof.run(PK_PC, 3.0 * n_list * nrb * sizeof(T), 4.0 * nrb * c->n_proj * n_list, st, [&] {
+      if constexpr (std::is_same<T, float>::value) {
+        if (kb_tc)
+          return launch_kb_tc(Q, P, c->ld_w, n_list, list, c->kb_tc.as<unsigned char>(), nrb, c->n_proj,
+                              c->f.kbD.as<float>(), active, c->pc_work.as<float>(), st, c->tc_err.as<int>(),
+                              c->tc_split > 0 ? c->tc_split : kTcSplitDefault);
+      }
       return launch_kb<T>(Q, P, c->ld_w, n_list, list, pr.kbB.template as<T>(), c->ld_w, nrb, c->n_proj,
                           pr.kbD.template as<T>(), c->pc_work.template as<T>(), st,
                           sizeof(T) == 8 && c->d.use_ff); }));

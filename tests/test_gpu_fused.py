@@ -1,10 +1,12 @@
 """The fused FP32 H application (one kernel per pair, the FFT intermediate in distributed shared
-memory) against the three-kernel pipeline it replaces.
+memory) against the three-kernel pipeline it replaces and the oracle.
 
-Both run the same transforms in the same order on the same data, so H psi and whole chi0
-applies must be bit-identical with fused_h = 1 and fused_h = 0, on every grid the fused kernel
-takes (24^3 in one CTA per pair, 32^3 in one CTA, 48^3 in a cluster of two CTAs), and on the
-active-list launches of the CG (odd system counts, ragged pairs).
+Both run the same butterflies on the same data; the compiler contracts multiplies and adds into
+FMAs differently in the two codes, so the results agree to FP32 rounding rather than bit for
+bit.  Checked on every grid the fused kernel takes (24^3 in one CTA per pair, 32^3 in one CTA,
+48^3 in a cluster of two CTAs), on the active-list launches of the CG (odd system counts, ragged
+pairs): H psi within 1e-5 of the largest element of the three-kernel result and of the oracle's
+H, and whole mixed-path chi0 applies within the path's 1e-8 of each other and of the oracle.
 """
 import numpy as np
 import pytest
@@ -44,21 +46,37 @@ def _ctx(W, s, fused):
                        beta_G=s.beta_G if kb else None, d_proj=s.d_proj if kb else None)
 
 
-def test_fused_h_is_bit_identical(W, model):
+def _model(s):
+    from oracle.model import Model
+    return Model(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, s.beta_G, s.d_proj)
+
+
+def test_fused_h_matches_three_kernels_and_oracle(W, model):
     import torch
     s = model
     x = synth.perturbations(s.miller_wfc, s.L, 7, 91)      # 7 vectors: the last pair is half empty
     xd = torch.from_numpy(np.ascontiguousarray(x.T)).cuda()
     outs = [W.wgw_apply_h_dev(_ctx(W, s, f), xd, fp32=True).cpu().numpy() for f in (0, 1)]
-    assert np.array_equal(outs[0], outs[1])
+    scale = np.max(np.abs(outs[0]))
+    assert np.max(np.abs(outs[1] - outs[0])) < 1e-5 * scale
+    ref = _model(s).apply_h(x).T
+    assert np.max(np.abs(outs[1] - ref)) < 1e-5 * np.max(np.abs(ref))
 
 
-def test_fused_chi0_apply_is_bit_identical(W, model):
+def test_fused_chi0_apply_matches_three_kernels_and_oracle(W, model):
+    from oracle import chi0
     s = model
     dV = synth.perturbations(s.miller_rho, s.L, 3, 92)
     outs = []
     for f in (0, 1):
         drho, st, _ = W.wgw_apply_chi0(_ctx(W, s, f), dV, [0.0, 0.5])
         assert st["n_converged"] == st["n_systems"]
-        outs.append(drho)
-    assert np.array_equal(outs[0], outs[1])
+        outs.append(drho.reshape(drho.shape[0], -1))
+
+    def rel(a, b):
+        return float(np.max(np.linalg.norm(a - b, axis=0) / np.linalg.norm(b, axis=0)))
+
+    assert rel(outs[1], outs[0]) < 1e-8
+    if s.n_pw < 5000:
+        ref = chi0.sos_drho(_model(s), dV, [0.0, 0.5])
+        assert rel(outs[1], ref.reshape(ref.shape[0], -1)) < 1e-8

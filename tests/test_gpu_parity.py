@@ -176,15 +176,18 @@ def kbsys(request):
     return synth.make_system(cfg)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_cuda_cores"])
 def test_kb_projectors_match_sum_over_states(W, kbsys, prec):
-    """H = T + V_loc + sum_p |beta_p> D_p <beta_p| (Kleinman-Bylander), static and at i w."""
+    """H = T + V_loc + sum_p |beta_p> D_p <beta_p| (Kleinman-Bylander), static and at i w.  On the
+    mixed path the KB products of the FP32 solves run on the tcgen05 tensor cores (default) or as
+    CUDA-core GEMMs."""
     s = kbsys
     assert s.beta_G.shape[1] == 4 * s.cfg.n_wells
     dV = synth.perturbations(s.miller_rho, s.L, 3, 19)
     oms = [0.0, 0.6]
     ref = chi0.sos_drho(model_of(s), dV, oms)
-    opt = dict(precision=W.WGW_FP64, cg_tol=1e-13) if prec == "fp64" else dict(precision=W.WGW_MIXED, cg_tol=1e-11)
+    opt = dict(precision=W.WGW_FP64, cg_tol=1e-13) if prec == "fp64" else \
+        dict(precision=W.WGW_MIXED, cg_tol=1e-11, tensor_cores=0 if prec == "mixed_cuda_cores" else 1)
     ctx = setup(W, s, **opt)
     drho, st, _ = W.wgw_apply_chi0(ctx, dV, omega=oms)
     assert rel_err(drho.reshape(drho.shape[0], -1), ref.reshape(ref.shape[0], -1)) < (1e-10 if prec == "fp64" else 1e-8)
