@@ -70,6 +70,7 @@ def line_config(args, wl, tensor_cores, world):
     return {"workload": args.workload, "desc": wl["desc"], "cg_tol": wl["cg_tol"], "precision": args.precision,
             "fp64_passes": ("float-float" if args.fp64_emulation else "native FP64") if mixed else "n/a",
             "pc_fp32": "tcgen05 3xTF32" if tensor_cores else "CUDA-core FP32",
+            "h_fp32": "fused kernel" if getattr(args, "fused_h", None) else "three kernels",
             "l2": "256 MB buffer written between steps, outside the timed interval",
             "parallelism": f"perturbation shards x{world}" if world > 1 else "1 GPU"}
 
@@ -583,6 +584,8 @@ def main():
                     help="1: FP64-accuracy FFT passes in float-float (default); 0: native FP64")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="mixed (FP32 CG + FP64-accuracy refinement, default) or the all-FP64 path")
+    ap.add_argument("--fused-h", type=int, default=None, choices=[0, 1],
+                    help="FP32 H application as one fused kernel per pair (default: the library's)")
     ap.add_argument("--tensor-cores", type=int, default=None, choices=[0, 1],
                     help="P_c of the FP32 solves on the tcgen05 tensor cores (default: the library's)")
     args = ap.parse_args()
@@ -633,6 +636,8 @@ def main():
                                     fp64_emulation=args.fp64_emulation)
     if args.tensor_cores is not None:
         opt.tensor_cores = args.tensor_cores
+    if args.fused_h is not None:
+        opt.fused_h = args.fused_h
     kb = s.beta_G.shape[1] > 0
     ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, opt,
                       beta_G=s.beta_G if kb else None, d_proj=s.d_proj if kb else None)

@@ -90,8 +90,9 @@ typedef struct wgw_options {
                              fit 85 % of the free device memory (the default). */
   int fused_h;            /* MIXED: 1 = the FP32 H application runs as one kernel per pair with the FFT
                              intermediate in (distributed) shared memory, on the grids it supports (24, 32,
-                             48); 0 = three kernels with the intermediate in device memory.  The same
-                             operations: results agree to FP32 rounding. */
+                             48); 0 = three kernels with the intermediate in device memory (the default:
+                             faster on GB300 as the fused kernel stands).  The same operations: results
+                             agree to FP32 rounding. */
 } wgw_options;
 
 typedef struct wgw_stats {
@@ -104,7 +105,7 @@ typedef struct wgw_stats {
 
 /* Fills *opt with defaults: WGW_FP64, cg_tol 1e-12, max_cg_iter 2000, max_refine 8,
  * inner_tol 5e-6, f_s 2, check_every 8, dav_tol 1e-8, dav_max_iter 100, dav_factor 4, seed 12345,
- * fp64_emulation 1, tensor_cores 1, cuda_graphs 1, max_batch_systems 0, fused_h 1. */
+ * fp64_emulation 1, tensor_cores 1, cuda_graphs 1, max_batch_systems 0, fused_h 0. */
 int wgw_default_options(wgw_options* opt);
 
 /*

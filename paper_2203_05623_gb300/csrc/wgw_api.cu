@@ -1731,7 +1731,7 @@ int wgw_default_options(wgw_options* opt) {
   opt->dav_factor = 4;
   opt->seed = 12345;
   opt->max_batch_systems = 0;
-  opt->fused_h = 1;
+  opt->fused_h = 0;
   return WGW_OK;
 }
 
