@@ -1,5 +1,6 @@
 // __global__ wrappers of the linear-algebra kernels (bodies in la_bodies.cuh).
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -182,11 +183,19 @@ __global__ void __launch_bounds__(256) k_pc_gemm1(const T* __restrict__ Psi, lon
   const int j0 = blockIdx.x * kGT, v0 = blockIdx.z * kGT, kb = blockIdx.y;
   const int k_lo = kb * kblk, k_hi = min(n, k_lo + kblk);
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;   // tx: systems, ty: states
+  // Float-float sums are flushed into FP64 every kFlushK terms: the rounding of the float-float
+  // accumulator grows with the number of terms it has taken (about n 2^-48 of the largest
+  // partial sum), so over the 30k-term rows of large spheres it would cap the FP64 residuals of
+  // the refinement near 1e-10; blocks of 512 keep it near 1e-13.
+  constexpr bool kFf = std::is_same<C, ff>::value;
+  constexpr int kFlushK = 512;
   C acc[4][4];
+  double acc64[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = C(0);
+    for (int j = 0; j < 4; ++j) { acc[i][j] = C(0); acc64[i][j] = 0.0; }
+  int since = 0;
   for (int k0 = k_lo; k0 < k_hi; k0 += kGK) {
     load_kchunk<T, C, PsiRaw>(As, Psi, ldp, nullptr, v0, nv, k0, k_hi);
     load_kchunk<T, C>(Bs, Y, ldy, list, j0, n_list, k0, k_hi);
@@ -202,6 +211,16 @@ __global__ void __launch_bounds__(256) k_pc_gemm1(const T* __restrict__ Psi, lon
         for (int j = 0; j < 4; ++j) mac(acc[i][j], a[i], b[j]);
     }
     __syncthreads();
+    if constexpr (kFf) {
+      since += kGK;
+      if (since >= kFlushK) {
+        since = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) { acc64[i][j] += static_cast<double>(acc[i][j]); acc[i][j] = C(0); }
+      }
+    }
   }
   const int nvp = gridDim.z * kGT;
   T* out = Cpart + (size_t)kb * nvp * n_list;
@@ -211,7 +230,10 @@ __global__ void __launch_bounds__(256) k_pc_gemm1(const T* __restrict__ Psi, lon
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int jx = j0 + tx * 4 + j;
-      if (jx < n_list) out[(size_t)v * n_list + jx] = T(acc[i][j]);
+      if (jx < n_list) {
+        if constexpr (kFf) out[(size_t)v * n_list + jx] = T(acc64[i][j] + static_cast<double>(acc[i][j]));
+        else out[(size_t)v * n_list + jx] = T(acc[i][j]);
+      }
     }
   }
 }
