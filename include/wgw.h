@@ -93,6 +93,10 @@ typedef struct wgw_options {
                              48); 0 = three kernels with the intermediate in device memory (the default:
                              faster on GB300 as the fused kernel stands).  The same operations: results
                              agree to FP32 rounding. */
+  int tc_split;           /* MIXED, tensor_cores: phase-1 CTAs per SM the K dimension of the tensor-core
+                             projector and KB products is cut for, 1..16; 0 = picked by the autotuner on
+                             the context's first large projection (the default).  A fixed split gives
+                             bit-identical results from run to run. */
 } wgw_options;
 
 typedef struct wgw_stats {
@@ -105,7 +109,7 @@ typedef struct wgw_stats {
 
 /* Fills *opt with defaults: WGW_FP64, cg_tol 1e-12, max_cg_iter 2000, max_refine 8,
  * inner_tol 5e-6, f_s 2, check_every 8, dav_tol 1e-8, dav_max_iter 100, dav_factor 4, seed 12345,
- * fp64_emulation 1, tensor_cores 1, cuda_graphs 1, max_batch_systems 0, fused_h 0. */
+ * fp64_emulation 1, tensor_cores 1, cuda_graphs 1, max_batch_systems 0, fused_h 0, tc_split 0. */
 int wgw_default_options(wgw_options* opt);
 
 /*

@@ -498,9 +498,16 @@ TcGeom tc_geom(int n, int n_sys, int nv, int split = kTcSplitDefault) {
   g.nrt = (n + tc::kRowsA - 1) / tc::kRowsA;
   g.nvc = g.ldc / tc::kKC;
   g.njt = (n_sys + tc::kRowsA - 1) / tc::kRowsA;
-  // About `split` phase-1 CTAs per SM (two resident at a time), each with at least 4 chunks of K.
+  // About `split` phase-1 CTAs per SM (two resident at a time), each with at least 4 chunks of K
+  // and at most kMaxChunksPerBlock: the MMAs accumulate in FP32 inside tensor memory, and over
+  // long K runs (15k terms on 30k-element vectors) that sum lost enough accuracy to stall the
+  // FP32 inner solves near 1e-5 (three refinements and up to 6x the iterations on the 96^3
+  // model); blocks of at most 2048 terms, summed in a fixed order by the reduce, keep the
+  // projection FP32-accurate.
+  constexpr int kMaxChunksPerBlock = 64;
   int kb = (split * 152 + g.njt - 1) / g.njt;
   kb = std::max(1, std::min(kb, std::max(1, g.nkc / 4)));
+  kb = std::max(kb, (g.nkc + kMaxChunksPerBlock - 1) / kMaxChunksPerBlock);
   g.kcpb = (g.nkc + kb - 1) / kb;
   g.n_kb = (g.nkc + g.kcpb - 1) / g.kcpb;
   return g;

@@ -345,6 +345,7 @@ int run_pc(wgw_ctx* c, T* Y, int n_list, const int* list, const T* Psi, const in
     }
   }
   const unsigned char* tiles = tcores ? c->psi_tc.as<unsigned char>() : nullptr;
+  if (tcores && c->opt.tc_split > 0) c->tc_split = c->opt.tc_split;
   if (tcores && c->tc_split == 0 && n_list >= 256) {
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     WGW_CK(cudaStreamIsCapturing(st, &cap));
@@ -416,7 +417,8 @@ int apply_A(wgw_ctx* c, Prec<T>& pr, const T* P, T* Q, int n_list, const int* li
         if (kb_tc)
           return launch_kb_tc(Q, P, c->ld_w, n_list, list, c->kb_tc.as<unsigned char>(), nrb, c->n_proj,
                               c->f.kbD.as<float>(), active, c->pc_work.as<float>(), st, c->tc_err.as<int>(),
-                              c->tc_split > 0 ? c->tc_split : kTcSplitDefault);
+                              c->opt.tc_split > 0 ? c->opt.tc_split
+                                                  : (c->tc_split > 0 ? c->tc_split : kTcSplitDefault));
       }
       return launch_kb<T>(Q, P, c->ld_w, n_list, list, pr.kbB.template as<T>(), c->ld_w, nrb, c->n_proj,
                           pr.kbD.template as<T>(), c->pc_work.template as<T>(), st,
@@ -1732,6 +1734,7 @@ int wgw_default_options(wgw_options* opt) {
   opt->seed = 12345;
   opt->max_batch_systems = 0;
   opt->fused_h = 0;
+  opt->tc_split = 0;
   return WGW_OK;
 }
 
@@ -1742,6 +1745,7 @@ static int check_options(const wgw_options& o) {
   if (!(o.dav_tol > 0) || o.dav_max_iter < 1 || o.dav_factor < 2)
     return fail(WGW_ERR_ARG, "bad Davidson options");
   if (o.max_batch_systems < 0) return fail(WGW_ERR_ARG, "max_batch_systems < 0");
+  if (o.tc_split < 0 || o.tc_split > kTcSplitMax) return fail(WGW_ERR_ARG, "tc_split outside 0..16");
   return WGW_OK;
 }
 

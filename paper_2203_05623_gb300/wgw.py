@@ -37,7 +37,8 @@ class Options(ctypes.Structure):
                 ("check_every", ctypes.c_int), ("dav_tol", ctypes.c_double),
                 ("dav_max_iter", ctypes.c_int), ("dav_factor", ctypes.c_int), ("seed", ctypes.c_int),
                 ("fp64_emulation", ctypes.c_int), ("tensor_cores", ctypes.c_int), ("cuda_graphs", ctypes.c_int),
-                ("max_batch_systems", ctypes.c_int), ("fused_h", ctypes.c_int)]
+                ("max_batch_systems", ctypes.c_int), ("fused_h", ctypes.c_int),
+                ("tc_split", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
