@@ -70,7 +70,8 @@ def line_config(args, wl, tensor_cores, world):
     return {"workload": args.workload, "desc": wl["desc"], "cg_tol": wl["cg_tol"], "precision": args.precision,
             "fp64_passes": ("float-float" if args.fp64_emulation else "native FP64") if mixed else "n/a",
             "pc_fp32": "tcgen05 3xTF32" if tensor_cores else "CUDA-core FP32",
-            "h_fp32": "fused kernel" if getattr(args, "fused_h", None) else "three kernels",
+            "h_fp32": {None: "autotuned (autotune.h_kernel)", 0: "three kernels", 1: "fused kernel"}[
+                getattr(args, "fused_h", None)],
             "l2": "256 MB buffer written between steps, outside the timed interval",
             "parallelism": f"perturbation shards x{world}" if world > 1 else "1 GPU"}
 
@@ -527,6 +528,66 @@ def library_baselines(W, ctx, s, prof_all):
                     "pc_project class (lists of varying length), cuBLAS as one call on 4096 systems"}
 
 
+def largest_config(W, stream, hbm, peak_kind, steps=2):
+    """The largest single-GPU configuration (96^3 grid, 256 KB projectors, 256 occupied states,
+    256 perturbations = 65536 Sternheimer systems, mixed path) measured beside the main line: one
+    warm-up apply, `steps` timed applies (CUDA events), one end-to-end apply through the host
+    entry point, and the per-class kernel shares of one profiled apply."""
+    import numpy as np
+    import torch
+    import synth
+    wl = WORKLOADS["kb_L24_96"]
+    t0 = time.perf_counter()
+    s = synth.make_system(wl["config"])             # iterative ground state (cached on disk)
+    t_gs = time.perf_counter() - t0
+    phi = synth.perturbations(s.miller_rho, s.L, wl["n_pert"], wl["pert_seed"])
+    opt = W.wgw_default_options(precision=W.WGW_MIXED, cg_tol=wl["cg_tol"], max_cg_iter=200)
+    ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, opt, beta_G=s.beta_G, d_proj=s.d_proj)
+    x = torch.from_numpy(np.ascontiguousarray(phi.T)).cuda()
+    out = torch.zeros((1, wl["n_pert"], s.n_rho), dtype=torch.complex128, device="cuda")
+    st, _ = W.wgw_apply_chibar0_dev(ctx, x, [0.0], out, stream=stream.cuda_stream)     # warm-up
+    times = []
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st, _ = W.wgw_apply_chibar0_dev(ctx, x, [0.0], out, stream=stream.cuda_stream)
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b) / 1e3)
+    W.wgw_profile_enable(ctx, True)
+    W.wgw_apply_chibar0_dev(ctx, x, [0.0], out, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    prof = W.wgw_profile_read(ctx)
+    W.wgw_profile_enable(ctx, False)
+    del x
+    ph = np.ascontiguousarray(phi.T)
+    oh = np.zeros((1, wl["n_pert"], s.n_rho), np.complex128)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    W.wgw_apply_chibar0(ctx, ph.T, [0.0], out=oh)
+    e2e = time.perf_counter() - t1
+    W.wgw_destroy(ctx)
+    n = st["n_systems"]
+    tot = max(sum(v["ms"] for v in prof.values()), 1e-9)
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    ach = d["bytes"] / (d["ms"] / 1e3) / 1e9 if d["ms"] > 0 else 0.0
+    return {"workload": "kb_L24_96", "desc": wl["desc"], "value": n * steps / sum(times),
+            "unit": "Sternheimer solves/s", "ms_per_step": 1e3 * sum(times) / steps, "steps": steps, "warmup": 1,
+            "solve": {"n_systems": n, "max_iters": st["max_iters"], "refinements": st["refinements"],
+                      "max_rel_residual": st["max_rel_residual"]},
+            "e2e": {"value": n / e2e, "unit": "Sternheimer solves/s", "h2d_bytes_per_step": int(ph.nbytes),
+                    "d2h_bytes_per_step": int(oh.nbytes)},
+            "kernel_share": {k: round(v["ms"] / tot, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])
+                             if v["launches"]},
+            "kernel_gbs": {k: round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1)
+                           for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"]) if v["ms"] > 0},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
+                         "frac": ach / hbm, "peak_source": peak_kind,
+                         "timed_from": "one profiled apply, every launch bracketed by CUDA events"},
+            "ground_state_s": t_gs}
+
+
 def fp64_path(W, s, wl, x, out_mixed, stream, ph, oh, steps):
     """The same workload on the all-FP64 GPU path (FP64 CG to the same cg_tol, native FP64 FFT
     passes), measured in the same process: device time, end to end through the host-pointer
@@ -574,6 +635,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="pdep_L16_48", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-largest", action="store_true",
+                    help="skip the 96^3 / 65536-system configuration measured beside the default line")
     ap.add_argument("--no-fp64-path", action="store_true",
                     help="skip the all-FP64 GPU path measured beside the mixed one")
     ap.add_argument("--no-library-baselines", action="store_true",
@@ -766,9 +829,11 @@ def main():
         line["fp64_path"] = fp64_path(W, s, wl, x, out, stream, ph, oh, min(args.steps, 3))
     if world == 1 and args.precision == "mixed" and not args.no_library_baselines:
         line["library_baseline"] = library_baselines(W, ctx, s, prof_all)
+    W.wgw_destroy(ctx)
+    if world == 1 and args.precision == "mixed" and args.workload == "pdep_L16_48" and not args.no_largest:
+        line["largest_config"] = largest_config(W, stream, hbm, peak_kind)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    W.wgw_destroy(ctx)
     if dist:
         dist.destroy_process_group()
 

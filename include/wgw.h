@@ -88,11 +88,12 @@ typedef struct wgw_options {
   int max_batch_systems;  /* most Sternheimer systems (complex-shifted: twice their count) solved as one
                              batch; larger applies run in chunks of whole perturbations.  0 = as many as
                              fit 85 % of the free device memory (the default). */
-  int fused_h;            /* MIXED: 1 = the FP32 H application runs as one kernel per pair with the FFT
+  int fused_h;            /* MIXED: the FP32 H application.  1 = one kernel per pair with the FFT
                              intermediate in (distributed) shared memory, on the grids it supports (24, 32,
-                             48); 0 = three kernels with the intermediate in device memory (the default:
-                             faster on GB300 as the fused kernel stands).  The same operations: results
-                             agree to FP32 rounding. */
+                             48); 0 = three kernels with the intermediate in device memory; 2 = the faster of
+                             the two on the context's first list of >= 256 systems (autotuned, the default;
+                             wgw_autotune_info reports the choice).  The same operations: results agree to
+                             FP32 rounding. */
   int tc_split;           /* MIXED, tensor_cores: phase-1 CTAs per SM the K dimension of the tensor-core
                              projector and KB products is cut for, 1..16; 0 = picked by the autotuner on
                              the context's first large projection (the default).  A fixed split gives
@@ -109,7 +110,7 @@ typedef struct wgw_stats {
 
 /* Fills *opt with defaults: WGW_FP64, cg_tol 1e-12, max_cg_iter 2000, max_refine 8,
  * inner_tol 5e-6, f_s 2, check_every 8, dav_tol 1e-8, dav_max_iter 100, dav_factor 4, seed 12345,
- * fp64_emulation 1, tensor_cores 1, cuda_graphs 1, max_batch_systems 0, fused_h 0, tc_split 0. */
+ * fp64_emulation 1, tensor_cores 1, cuda_graphs 1, max_batch_systems 0, fused_h 2, tc_split 0. */
 int wgw_default_options(wgw_options* opt);
 
 /*
@@ -363,14 +364,19 @@ int wgw_apply_h_dev(wgw_ctx* ctx, const double* psi_dev, int n_psi, double* out_
 int wgw_sigma_x(wgw_ctx* ctx, const int* states, int n_states, double* sigma_x);
 
 /*
- * Autotuner record of a context.  The K split of the tensor-core projector (how many phase-1
- * CTAs per SM the contraction over plane waves is cut into) is picked on the context's own
- * shapes: at the first projection of at least 256 systems every candidate runs on a scratch
- * copy of the vectors and the fastest median time wins.  *tc_split = the choice (0: not tuned
- * yet); splits[k], ms[k] = each candidate and its median time for up to n_max candidates.
- * Returns the number of candidates written, or -WGW_ERR_ARG for a null context or negative n_max.
+ * Autotuner record of a context.  Two choices are made on the context's own shapes.  The K
+ * split of the tensor-core projector (how many phase-1 CTAs per SM the contraction over plane
+ * waves is cut into): at the first projection of at least 256 systems every candidate runs on a
+ * scratch copy of the vectors and the fastest median time wins; *tc_split = the choice (0: not
+ * tuned yet); splits[k], ms[k] = each candidate and its median time for up to n_max candidates.
+ * The FP32 H kernel (options.fused_h = 2): at the first application to at least 256 systems the
+ * three-kernel pipeline and the fused kernel both run on scratch output; *fused_h = the choice
+ * (-1: not tuned, 0: three kernels, 1: fused), h_ms[0], h_ms[1] = their median times [ms].  Any
+ * output may be NULL.  Returns the number of split candidates written, or -WGW_ERR_ARG for a
+ * null context or negative n_max.
  */
-int wgw_autotune_info(const wgw_ctx* ctx, int* tc_split, int* splits, double* ms, int n_max);
+int wgw_autotune_info(const wgw_ctx* ctx, int* tc_split, int* splits, double* ms, int n_max, int* fused_h,
+                      double* h_ms);
 
 /*
  * Failure-detection self-test (no counterpart in the paper).  Every wait of the library's

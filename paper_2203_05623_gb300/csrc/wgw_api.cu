@@ -222,6 +222,10 @@ struct wgw_ctx {
   // yet) and the median time of each candidate on this context's shapes.
   int tc_split = 0;
   std::vector<std::pair<int, double>> tc_tune;
+  // The FP32 H kernel choice (-1: not tuned yet; 0: three kernels; 1: fused) and the median time
+  // of each variant on this context's first large list.
+  int h_choice = -1;
+  double h_ms[2] = {0.0, 0.0};
   std::vector<int> last_iters;      // per system of the last apply: CG iterations (all refinements)
   std::vector<double> last_relres;  // per system of the last apply: final FP64 ||b - A x|| / ||b||
   std::vector<int> last_conv;       // per system of the last apply: 1 if it met cg_tol
@@ -326,6 +330,60 @@ int tune_tc_split(wgw_ctx* c, const float* Y, int n_list, float* work, cudaStrea
   return WGW_OK;
 }
 
+// Autotuner of the FP32 H application: the three-kernel pipeline and the fused kernel each run
+// four times (the first warms up) on the context's first list of at least 256 systems, writing a
+// scratch output, and the faster median wins for the life of the context (wgw_autotune_info).
+int tune_h(wgw_ctx* c, Prec<float>& pr, const float* P, int n_list, const int* list, const int* active,
+           cudaStream_t st) {
+  const int N = c->N, NP = 2 * c->wfc.m + 1, pairs = (n_list + 1) / 2;
+  DevBuf out;
+  WGW_TRY(out.ensure(sizeof(float) * (size_t)n_list * c->ld_w));
+  WGW_TRY(pr.Tw.ensure(sizeof(cplx<float>) * (size_t)pairs * NP * N * N));
+  Epi<float> e{};
+  e.out = out.as<float>(); e.ldo = c->ld_w; e.pin = P; e.ldp = c->ld_w; e.vcoef = 1.f; e.kin = 1.f;
+  e.shift = pr.shift.as<float>(); e.n_sys = n_list; e.active = nullptr; e.list = nullptr;
+  // The same amount of work on the first n_list rows of P (valid rows of the batch), every
+  // system active, so that the scratch output needs n_list rows whatever the list holds.
+  (void)list;
+  (void)active;
+  list = nullptr;
+  active = nullptr;
+  FftCtx<float> f = pr.fft(c->plan);
+  cplx<float>* Tb = pr.Tw.as<cplx<float>>();
+  cudaEvent_t a = nullptr, b = nullptr;
+  WGW_CK(cudaEventCreate(&a));
+  WGW_CK(cudaEventCreate(&b));
+  double med[2] = {0, 0};
+  for (int variant = 0; variant < 2; ++variant) {
+    std::vector<float> ts;
+    for (int r = 0; r < 4; ++r) {
+      WGW_CK(cudaEventRecord(a, st));
+      if (variant == 1) {
+        WGW_CK(launch_hpsi_fused(c->wfc.tab(), N, P, c->ld_w, n_list, list, active, pr.v_r_fft(), e, st));
+      } else {
+        WGW_CK(launch_plane_g2r<float>(c->wfc.tab(), f, P, c->ld_w, n_list, list, active, Tb, st));
+        XArgs<float> xa{};
+        xa.mode = XM_APPLY_V; xa.V = pr.v_r_fft(); xa.n_sys = n_list; xa.list = list;
+        WGW_CK(launch_xline<float>(c->wfc.m, f, Tb, xa, active, st));
+        WGW_CK(launch_plane_r2g<float>(c->wfc.tab(), c->wfc.npt_max, f, Tb, e, st));
+      }
+      WGW_CK(cudaEventRecord(b, st));
+      WGW_CK(cudaEventSynchronize(b));
+      float ms = 0.f;
+      WGW_CK(cudaEventElapsedTime(&ms, a, b));
+      if (r > 0) ts.push_back(ms);
+    }
+    std::sort(ts.begin(), ts.end());
+    med[variant] = ts[ts.size() / 2];
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  c->h_ms[0] = med[0];
+  c->h_ms[1] = med[1];
+  c->h_choice = med[1] < med[0] ? 1 : 0;
+  return WGW_OK;
+}
+
 // P_c applied to the systems of a list (null = 0..n_list-1), timed as pc_project.
 template <typename T>
 int run_pc(wgw_ctx* c, T* Y, int n_list, const int* list, const T* Psi, const int* active, cudaStream_t st) {
@@ -369,8 +427,22 @@ int apply_A(wgw_ctx* c, Prec<T>& pr, const T* P, T* Q, int n_list, const int* li
   ProfPrec pp(c->prof, sizeof(T) == 8);
   const int N = c->N, NP = 2 * c->wfc.m + 1, pairs = (n_list + 1) / 2;
   if (pairs == 0) return WGW_OK;
-  const bool need_t = !(sizeof(T) == sizeof(float) && c->opt.fused_h != 0 && hpsi_fused_supported(N, c->wfc.m));
-  if (need_t) WGW_TRY(pr.Tw.ensure(sizeof(cplx<T>) * (size_t)pairs * NP * N * N));
+  bool fused = false;
+  if constexpr (std::is_same<T, float>::value) {
+    if (c->opt.fused_h != 0 && hpsi_fused_supported(N, c->wfc.m)) {
+      if (c->opt.fused_h == 1) {
+        fused = true;
+      } else {   // 2: the autotuner's choice, made once per context on its first large list
+        if (c->h_choice < 0 && n_list >= 256) {
+          cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+          WGW_CK(cudaStreamIsCapturing(st, &cap));
+          if (cap == cudaStreamCaptureStatusNone) WGW_TRY(tune_h(c, pr, P, n_list, list, active, st));
+        }
+        fused = c->h_choice == 1;
+      }
+    }
+  }
+  if (!fused) WGW_TRY(pr.Tw.ensure(sizeof(cplx<T>) * (size_t)pairs * NP * N * N));
   FftCtx<T> f = pr.fft(c->plan);
   cplx<T>* Tb = pr.Tw.template as<cplx<T>>();
   const int nrb = c->wfc.nrb();
@@ -378,16 +450,14 @@ int apply_A(wgw_ctx* c, Prec<T>& pr, const T* P, T* Q, int n_list, const int* li
   Epi<T> e{};
   e.out = Q; e.ldo = c->ld_w; e.pin = P; e.ldp = c->ld_w; e.vcoef = T(1); e.kin = T(1);
   e.shift = pr.shift.template as<T>(); e.n_sys = n_list; e.active = active; e.list = list;
-  bool fused = false;
   if constexpr (std::is_same<T, float>::value) {
-    if (c->opt.fused_h != 0 && hpsi_fused_supported(N, c->wfc.m)) {
+    if (fused) {
       // Algorithmic work: p in, q out and V(r); flops 5 n log2 n per line transform (rows and
       // columns of the 2m+1 planes both ways, N^2 x-lines both ways) and the V(r) product.
       const double nl = 5.0 * N * std::log2((double)N);
       const double fl = (double)pairs * (2.0 * NP * NP * nl + 2.0 * NP * N * nl + 2.0 * N * N * nl + 2.0 * c->grid3);
       WGW_CK(c->prof.run(PK_HPSI, 2.0 * n_list * nrb * sizeof(T) + (double)c->grid3 * sizeof(T), fl, st, [&] {
         return launch_hpsi_fused(c->wfc.tab(), N, P, c->ld_w, n_list, list, active, pr.v_r_fft(), e, st); }));
-      fused = true;
     }
   }
   if (!fused) {
@@ -1733,7 +1803,7 @@ int wgw_default_options(wgw_options* opt) {
   opt->dav_factor = 4;
   opt->seed = 12345;
   opt->max_batch_systems = 0;
-  opt->fused_h = 0;
+  opt->fused_h = 2;
   opt->tc_split = 0;
   return WGW_OK;
 }
@@ -2186,11 +2256,14 @@ int wgw_sigma_x(wgw_ctx* c, const int* states, int n_states, double* sigma_x) {
   return WGW_OK;
 }
 
-int wgw_autotune_info(const wgw_ctx* c, int* tc_split, int* splits, double* ms, int n_max) {
+int wgw_autotune_info(const wgw_ctx* c, int* tc_split, int* splits, double* ms, int n_max, int* fused_h,
+                      double* h_ms) {
   if (!c || n_max < 0) {
     fail(WGW_ERR_ARG, "bad argument");
     return -WGW_ERR_ARG;
   }
+  if (fused_h) *fused_h = c->h_choice;
+  if (h_ms) { h_ms[0] = c->h_ms[0]; h_ms[1] = c->h_ms[1]; }
   if (tc_split) *tc_split = c->tc_split;
   const int m = std::min<int>(n_max, (int)c->tc_tune.size());
   for (int k = 0; k < m; ++k) {

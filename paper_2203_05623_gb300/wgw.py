@@ -117,7 +117,7 @@ def lib(path: str | None = None):
                           _dp, ctypes.c_int, _dp, _dp, _dp, ctypes.c_int, _dp, ctypes.POINTER(Stats)]
     L.wgw_sigma_x.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int, _dp]
     L.wgw_autotune_info.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
-                                    _dp, ctypes.c_int]
+                                    _dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp]
     L.wgw_selftest_wait_timeout.argtypes = [ctypes.POINTER(ctypes.c_int)]
     L.wgw_apply_channels.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int,
                                      _dp, ctypes.c_int, _dp, ctypes.POINTER(Stats)]
@@ -295,14 +295,20 @@ def wgw_sigma_x(ctx: Context, states) -> np.ndarray:
 
 
 def wgw_autotune_info(ctx: Context) -> dict:
-    """The autotuner's choice of the tensor-core P_c K split and each candidate's median time."""
+    """The autotuner's choices: the tensor-core P_c K split with each candidate's median time, and
+    the FP32 H kernel (-1 untuned, 0 three kernels, 1 fused) with both variants' median times."""
     choice = ctypes.c_int(0)
     splits = (ctypes.c_int * 16)()
     ms = np.zeros(16)
-    k = lib().wgw_autotune_info(ctx.handle, ctypes.byref(choice), splits, ms.ctypes.data_as(_dp), 16)
+    fused = ctypes.c_int(-1)
+    hms = np.zeros(2)
+    k = lib().wgw_autotune_info(ctx.handle, ctypes.byref(choice), splits, ms.ctypes.data_as(_dp), 16,
+                                ctypes.byref(fused), hms.ctypes.data_as(_dp))
     if k < 0:
         _check(-k, "wgw_autotune_info")
-    return {"tc_split": choice.value, "candidates_ms": {int(splits[i]): float(ms[i]) for i in range(k)}}
+    return {"tc_split": choice.value, "candidates_ms": {int(splits[i]): float(ms[i]) for i in range(k)},
+            "h_kernel": {-1: "untuned", 0: "three kernels", 1: "fused"}[fused.value],
+            "h_ms": {"three_kernels": float(hms[0]), "fused": float(hms[1])}}
 
 
 def wgw_selftest_wait_timeout() -> int:

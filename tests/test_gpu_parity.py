@@ -299,5 +299,24 @@ def test_autotuner_picks_a_candidate_and_results_stay_correct(W):
     assert info["tc_split"] in (2, 4, 8, 16)
     assert sorted(info["candidates_ms"]) == [2, 4, 8, 16]
     assert all(t > 0 for t in info["candidates_ms"].values())
+    # The FP32 H kernel is tuned on the same first large list: both variants timed, one chosen.
+    assert info["h_kernel"] in ("three kernels", "fused")
+    assert info["h_ms"]["three_kernels"] > 0 and info["h_ms"]["fused"] > 0
     ref = chi0.sos_drho(model_of(s), dV, [0.0])
     assert rel_err(drho, ref) < 1e-8
+
+
+@pytest.mark.parametrize("fused", [0, 1])
+def test_fixed_tuning_choices_are_bit_identical_across_contexts(W, fused):
+    """With the autotuned choices fixed (H kernel, tensor-core K split) two contexts give
+    bit-identical results for the same batch."""
+    s = synth.make_system(synth.Config("nv70", L=10.0, ecut=5.0, grid=24, n_wells=16, well_seed=1, n_v=70))
+    dV = synth.perturbations(s.miller_rho, s.L, 4, 63)
+    outs = []
+    for _ in range(2):
+        ctx = setup(W, s, precision=W.WGW_MIXED, cg_tol=1e-11, fused_h=fused, tc_split=4)
+        drho, st, _ = W.wgw_apply_chi0(ctx, dV, [0.0, 0.4])
+        outs.append(drho)
+        info = W.wgw_autotune_info(ctx)
+        assert info["tc_split"] == 4 and info["h_kernel"] == "untuned"
+    assert np.array_equal(outs[0], outs[1])
