@@ -420,13 +420,21 @@ int wgw_dyson(int n, int n_omega, const double* chi0bar, double* chibar);
 /*
  * Serving (no counterpart in the paper, which runs one calculation per job): non-blocking
  * requests on a context.  wgw_submit copies the request's inputs and returns a ticket at once;
- * one worker thread per context runs queued requests on the context's stream, merging all
- * queued requests with the same kind and frequency set into one batched apply (as many as 80 %
- * of the free device memory admits), so requests that arrive while a batch runs are taken into
- * the next one.  Requests on different contexts (different systems or grids) run on different
- * streams and overlap on the GPU.  The result of a request equals its result alone up to the
- * rounding of the batched reductions (tests bound it by the path's tolerance).
- * While a context has requests in flight, its other entry points wait for the running batch.
+ * one worker thread per context runs queued requests on the context's stream.
+ *   - On a mixed-precision context, static requests (one frequency, omega = 0) are batched
+ *     continuously: every Sternheimer system of an admitted request takes a slot of a device
+ *     pool (up to 16384 slots, 60 % of the free memory), the FP32 inner CG of all slots runs in
+ *     windows of check_every iterations, and between two windows finished systems are retired
+ *     (FP64-accurate residual, next refinement or done), finished requests return their results,
+ *     and queued requests are admitted into the free slots.  A request that arrives while others
+ *     are on the GPU joins at the next window and its systems iterate in the same launches.
+ *   - Other requests (frequencies other than the single 0, or an FP64 context) run as batched
+ *     applies: queued requests with the same kind and frequency set are merged (as many as 80 %
+ *     of the free device memory admits); such a request waits until the continuous engine is idle.
+ * Requests on different contexts (different systems or grids) run on different streams and
+ * overlap on the GPU.  The result of a request equals its result alone up to the rounding of the
+ * batched reductions (tests bound it by the path's tolerance).  While a context has requests in
+ * flight, its other entry points wait until they are done.
  */
 #define WGW_REQ_CHI0 0     /* out = chi0(i omega) dV, as wgw_apply_chi0 */
 #define WGW_REQ_CHIBAR0 1  /* out = chi0bar(i omega) phi, as wgw_apply_chibar0 */
@@ -445,8 +453,9 @@ typedef struct wgw_result {
   int status;             /* status of the batched apply that served the request */
   double latency_s;       /* submission -> results written */
   double queue_s;         /* submission -> start of its batch */
-  int batch_requests;     /* requests merged into that batch */
-  int batch_systems;      /* Sternheimer systems of that batch */
+  int batch_requests;     /* requests merged into that batch; continuous batching: most requests it
+                             shared the slot pool with */
+  int batch_systems;      /* Sternheimer systems of that batch (continuous batching: its own) */
 } wgw_result;
 
 /* Checks and copies the request, queues it and returns its ticket at once.  Returns WGW_ERR_ARG

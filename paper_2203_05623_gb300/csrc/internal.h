@@ -203,12 +203,16 @@ cudaError_t launch_build_list(const int* active, int n_sys, int* list, int* coun
 int pc_kblocks(int n, int n_sys);
 int pcf_kblocks(int n, int n_sys);
 size_t pc_work_elems(int n, int n_sys, int nv);
+// Systems 0..n_sys-1, or list[0..n_sys) when a list is given.
 template <typename T>
 cudaError_t launch_cg_init_a(const SphereTab& sp, int n, int n_sys, const T* Bv, T* X, T* R, T* Z,
-                             long ld, const double* eps, CgState cs, cudaStream_t st);
+                             long ld, const double* eps, CgState cs, cudaStream_t st, const int* list = nullptr);
 template <typename T>
 cudaError_t launch_cg_init_b(int n, int n_sys, const T* R, const T* Z, T* P, long ld, CgState cs,
-                             cudaStream_t st);
+                             cudaStream_t st, const int* list = nullptr);
+// out[j] = in[rows[j]] for j < n_rows, rows of n doubles.
+cudaError_t launch_gather_rows(int n_rows, int n, const int* rows, const double* in, long ldi, double* out, long ldo,
+                               cudaStream_t st);
 template <typename T>
 cudaError_t launch_cg_step_a(const SphereTab& sp, int n, int n_sys, const int* list, T* X, T* R, T* Z,
                              const T* P, const T* Q, long ld, const double* eps, CgState cs, double tol2,

@@ -30,15 +30,25 @@ __global__ void k_pc(T* Y, long ldy, int n_sys, const T* Psi, long ldp, int n, i
 
 template <typename T>
 __global__ void k_cg_init_a(SphereTab sp, int n, const T* Bv, T* X, T* R, T* Z, long ld,
-                            const double* eps, CgState cs) {
+                            const double* eps, CgState cs, const int* list) {
   __shared__ double red[33];
-  cg_init_a_body<T>(blockIdx.x, sp, n, Bv, X, R, Z, ld, eps, cs, red, thr());
+  cg_init_a_body<T>(list ? list[blockIdx.x] : blockIdx.x, sp, n, Bv, X, R, Z, ld, eps, cs, red, thr());
 }
 
 template <typename T>
-__global__ void k_cg_init_b(int n, const T* R, const T* Z, T* P, long ld, CgState cs) {
+__global__ void k_cg_init_b(int n, const T* R, const T* Z, T* P, long ld, CgState cs, const int* list) {
   __shared__ double red[33];
-  cg_init_b_body<T>(blockIdx.x, n, R, Z, P, ld, cs, red, thr());
+  cg_init_b_body<T>(list ? list[blockIdx.x] : blockIdx.x, n, R, Z, P, ld, cs, red, thr());
+}
+
+// out[j] = in[rows[j]] for j < n_rows (rows of length n).
+__global__ void k_gather_rows(int n_rows, int n, const int* __restrict__ rows, const double* __restrict__ in,
+                              long ldi, double* __restrict__ out, long ldo) {
+  for (int j = blockIdx.y; j < n_rows; j += gridDim.y) {
+    const double* src = in + (size_t)rows[j] * ldi;
+    double* dst = out + (size_t)j * ldo;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i];
+  }
 }
 
 template <typename T>
@@ -757,17 +767,17 @@ size_t pc_work_elems(int n, int n_sys, int nv) {
 
 template <typename T>
 cudaError_t launch_cg_init_a(const SphereTab& sp, int n, int n_sys, const T* Bv, T* X, T* R, T* Z,
-                             long ld, const double* eps, CgState cs, cudaStream_t st) {
+                             long ld, const double* eps, CgState cs, cudaStream_t st, const int* list) {
   if (n_sys == 0) return cudaSuccess;
-  k_cg_init_a<T><<<n_sys, kCgThreads, 0, st>>>(sp, n, Bv, X, R, Z, ld, eps, cs);
+  k_cg_init_a<T><<<n_sys, kCgThreads, 0, st>>>(sp, n, Bv, X, R, Z, ld, eps, cs, list);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_cg_init_b(int n, int n_sys, const T* R, const T* Z, T* P, long ld, CgState cs,
-                             cudaStream_t st) {
+                             cudaStream_t st, const int* list) {
   if (n_sys == 0) return cudaSuccess;
-  k_cg_init_b<T><<<n_sys, kCgThreads, 0, st>>>(n, R, Z, P, ld, cs);
+  k_cg_init_b<T><<<n_sys, kCgThreads, 0, st>>>(n, R, Z, P, ld, cs, list);
   return cudaGetLastError();
 }
 
@@ -800,6 +810,13 @@ cudaError_t launch_rb_to_sphere(int n_sys, const double* in, long ldi, const int
                                 const double* scale, RbMap mp, double* c, long ldc, cudaStream_t st) {
   if (n_sys == 0) return cudaSuccess;
   k_rb_to_sphere<<<grid_el(mp.n_pairs + 1, n_sys), 256, 0, st>>>(n_sys, mp.n_pairs, in, ldi, b_row, scale, mp, c, ldc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows(int n_rows, int n, const int* rows, const double* in, long ldi, double* out, long ldo,
+                               cudaStream_t st) {
+  if (n_rows == 0) return cudaSuccess;
+  k_gather_rows<<<grid_el(n, n_rows), 256, 0, st>>>(n_rows, n, rows, in, ldi, out, ldo);
   return cudaGetLastError();
 }
 
@@ -946,9 +963,9 @@ template cudaError_t launch_kb<double>(double*, const double*, long, int, const 
                                     const int*, T*, cudaStream_t, bool, const unsigned char*,      \
                                     const T*, int*, int);                                          \
   template cudaError_t launch_cg_init_a<T>(const SphereTab&, int, int, const T*, T*, T*, T*, long, \
-                                           const double*, CgState, cudaStream_t);                 \
+                                           const double*, CgState, cudaStream_t, const int*);     \
   template cudaError_t launch_cg_init_b<T>(int, int, const T*, const T*, T*, long, CgState,       \
-                                           cudaStream_t);                                         \
+                                           cudaStream_t, const int*);                             \
   template cudaError_t launch_cg_step_a<T>(const SphereTab&, int, int, const int*, T*, T*, T*,     \
                                            const T*, const T*, long, const double*, CgState,      \
                                            double, int, cudaStream_t);                            \

@@ -112,6 +112,17 @@ class Queue {
     return batch;
   }
 
+  // The head request, moved out and marked running, if it satisfies `take`; false otherwise.
+  template <typename F>
+  bool take_head_if(F&& take, Request* out) {
+    if (queue_.empty() || !take(queue_.front())) return false;
+    *out = std::move(queue_.front());
+    queue_.pop_front();
+    running_.insert(out->ticket);
+    return true;
+  }
+  const Request* head() const { return queue_.empty() ? nullptr : &queue_.front(); }
+
   // Cancels a request: a queued one is removed and completed with kErrCancelled at once; a
   // running one completes with kErrCancelled when its batch ends (its output is not written).
   // Returns kErrArg for an unknown or already finished ticket.
@@ -148,6 +159,20 @@ class Queue {
       running_.erase(r.ticket);
       cancelled_.erase(r.ticket);
     }
+  }
+
+  // Completes one running request (kErrCancelled if it was cancelled) with its own batch figures.
+  void finish_one(const Request& r, int status, Clock::time_point t_start, Clock::time_point t_end, int batch_requests,
+                  int batch_systems) {
+    Done d;
+    d.status = cancelled_.count(r.ticket) ? kErrCancelled : status;
+    d.latency_s = std::chrono::duration<double>(t_end - r.t_submit).count();
+    d.queue_s = std::chrono::duration<double>(t_start - r.t_submit).count();
+    d.batch_requests = batch_requests;
+    d.batch_systems = batch_systems;
+    done_[r.ticket] = d;
+    running_.erase(r.ticket);
+    cancelled_.erase(r.ticket);
   }
 
   enum State { kUnknown = 0, kQueued, kRunning, kDone };

@@ -245,6 +245,9 @@ struct wgw_ctx {
   std::condition_variable qcv;
   serve::Queue sq;
   bool stop = false;
+  // Continuous-batching engine of the served static requests (worker thread only).
+  DevBuf eng_in, eng_out, eng_xc, eng_list, eng_mask, eng_pool;
+  long eng_requests = 0, eng_windows = 0;
   std::thread worker;
   int device = 0;
   ~wgw_ctx() {
@@ -256,6 +259,8 @@ struct wgw_ctx {
     if (worker.joinable()) worker.join();
     prof.release();
     d.release(); f.release(); wfc.release(); rho.release();
+    DevBuf* eng[] = {&eng_in, &eng_out, &eng_xc, &eng_list, &eng_mask, &eng_pool};
+    for (DevBuf* b : eng) b->release();
     DevBuf* all[] = {&e_v_d, &dvin, &dv_rb, &dv_r, &Trho, &Dr, &drho_rb, &eps, &a_idx, &b_idx, &brow,
                      &cg_rz, &cg_bb, &cg_rr, &cg_act, &cg_it, &cnt, &rr64, &act64, &norms, &pc_work, &sys_list, &list64, &cg_rzi, &omg,
                      &row_list, &rowact, &drho_all, &psi_tc, &kb_tc, &cg_best, &cg_itbest, &lz_q, &lz_qf, &tc_err};
@@ -963,6 +968,38 @@ int chunk_perts(wgw_ctx* c, int n_real, int sys_per_pert) {
   return std::max(1, std::min(n_real, std::min(by_mem, cap)));
 }
 
+// drho_r(r) = (2 f_s / Omega) sum_v psi_v(r) x_{r v}(r) for the solutions X (systems s = r n_v + v,
+// rows of length ldx), then to the density sphere: real-basis rows of drho_out (length ld_r).
+int drho_pass(wgw_ctx* c, const double* X, long ldx, int n_real, double* drho_out, cudaStream_t st) {
+  ProfPrec pp(c->prof, true);
+  const int N = c->N, n_v = c->n_v, n_sys = n_real * n_v;
+  const HostSphere& rs = c->rho;
+  const int NP = 2 * c->wfc.m + 1, pairs = (n_sys + 1) / 2;
+  WGW_TRY(c->d.Tw.ensure(sizeof(cplx<double>) * (size_t)pairs * NP * N * N));
+  WGW_TRY(c->Dr.ensure(sizeof(double) * (size_t)n_real * c->grid3));
+  FftCtx<double> f = c->d.fft(c->plan);
+  const double tb = t_bytes<double>(c, c->wfc.m, pairs);
+  WGW_CK(c->prof.run(PK_G2R, tb + (double)n_sys * c->wfc.nrb() * sizeof(double), 0, st, [&] {
+    return launch_plane_g2r<double>(c->wfc.tab(), f, X, ldx, n_sys, nullptr, nullptr, c->d.Tw.as<cplx<double>>(),
+                                    st); }));
+  const double coef = 2.0 * c->opt.f_s / c->omega_cell;
+  WGW_CK(c->prof.run(PK_DRHO, tb + (double)(n_v + n_real) * c->grid3 * sizeof(double), 0, st, [&] {
+    return launch_drho_xline<double>(c->wfc.m, f, c->d.Tw.as<cplx<double>>(), c->d.psi_r_fft(), c->grid3, n_v,
+                                     n_sys, n_real, coef, c->Dr.as<double>(), c->grid3, st); }));
+  const int NPr = 2 * rs.m + 1, rpairs = (n_real + 1) / 2;
+  WGW_TRY(c->Trho.ensure(sizeof(cplx<double>) * (size_t)rpairs * NPr * N * N));
+  XArgs<double> a{};
+  a.mode = XM_FROM_REAL; a.A = c->Dr.as<double>(); a.lda = c->grid3; a.n_sys = n_real;
+  const double tr = t_bytes<double>(c, rs.m, rpairs);
+  WGW_CK(c->prof.run(PK_XLINE, tr + (double)n_real * c->grid3 * sizeof(double), 0, st, [&] {
+    return launch_xline<double>(rs.m, f, c->Trho.as<cplx<double>>(), a, nullptr, st); }));
+  Epi<double> e{};
+  e.out = drho_out; e.ldo = c->ld_r; e.vcoef = 1.0; e.n_sys = n_real;
+  WGW_CK(c->prof.run(PK_R2G, tr + (double)n_real * rs.nrb() * sizeof(double), 0, st, [&] {
+    return launch_plane_r2g<double>(rs.tab(), rs.npt_max, f, c->Trho.as<cplx<double>>(), e, st); }));
+  return WGW_OK;
+}
+
 // drho = chi0 dV for n_real perturbations that are real in r, given and returned in
 // real-basis form (rows of length ld_r): dV in dvrb, drho into drho_out.  Steps 2-6
 // of the apply for one batched solve: system tables, dV(r), right-hand sides, Sternheimer
@@ -1017,30 +1054,7 @@ int chi0_rb_block(wgw_ctx* c, const double* dvrb, int n_real, double* drho_out, 
   const int solve_status = solve_all(c, n_sys, st, stats);
   if (solve_status != WGW_OK && solve_status != WGW_ERR_NOCONV) return solve_status;
   // 6. drho_r(r) = (2 f_s / Omega) sum_v psi_v(r) x_{v r}(r), then to the density sphere.
-  {
-    const int NP = 2 * c->wfc.m + 1, pairs = (n_sys + 1) / 2;
-    WGW_TRY(c->d.Tw.ensure(sizeof(cplx<double>) * (size_t)pairs * NP * N * N));
-    FftCtx<double> f = c->d.fft(c->plan);
-    const double tb = t_bytes<double>(c, c->wfc.m, pairs);
-    WGW_CK(c->prof.run(PK_G2R, tb + (double)n_sys * c->wfc.nrb() * sizeof(double), 0, st, [&] {
-      return launch_plane_g2r<double>(c->wfc.tab(), f, c->d.X.as<double>(), ldw, n_sys, nullptr, nullptr,
-                                      c->d.Tw.as<cplx<double>>(), st); }));
-    const double coef = 2.0 * c->opt.f_s / c->omega_cell;
-    WGW_CK(c->prof.run(PK_DRHO, tb + (double)(n_v + n_real) * c->grid3 * sizeof(double), 0, st, [&] {
-      return launch_drho_xline<double>(c->wfc.m, f, c->d.Tw.as<cplx<double>>(), c->d.psi_r_fft(),
-                                       c->grid3, n_v, n_sys, n_real, coef, c->Dr.as<double>(), c->grid3, st); }));
-    const int NPr = 2 * rs.m + 1, rpairs = (n_real + 1) / 2;
-    WGW_TRY(c->Trho.ensure(sizeof(cplx<double>) * (size_t)rpairs * NPr * N * N));
-    XArgs<double> a{};
-    a.mode = XM_FROM_REAL; a.A = c->Dr.as<double>(); a.lda = c->grid3; a.n_sys = n_real;
-    const double tr = t_bytes<double>(c, rs.m, rpairs);
-    WGW_CK(c->prof.run(PK_XLINE, tr + (double)n_real * c->grid3 * sizeof(double), 0, st, [&] {
-      return launch_xline<double>(rs.m, f, c->Trho.as<cplx<double>>(), a, nullptr, st); }));
-    Epi<double> e{};
-    e.out = drho_out; e.ldo = ldr; e.vcoef = 1.0; e.n_sys = n_real;
-    WGW_CK(c->prof.run(PK_R2G, tr + (double)n_real * rs.nrb() * sizeof(double), 0, st, [&] {
-      return launch_plane_r2g<double>(rs.tab(), rs.npt_max, f, c->Trho.as<cplx<double>>(), e, st); }));
-  }
+  WGW_TRY(drho_pass(c, c->d.X.as<double>(), ldw, n_real, drho_out, st));
   return solve_status;
 }
 
@@ -1777,6 +1791,298 @@ int lanczos_impl(wgw_ctx* c, const double* phi, int npd, int n_steps, const doub
   return WGW_OK;
 }
 
+// ---------------------------------------------------------------- continuous batching
+// Served requests whose frequencies are all zero run through a slot engine.  Every Sternheimer
+// system of an admitted request takes a slot (a row of the context's CG work arrays); the worker
+// runs the FP32 inner CG of all slots together in windows of check_every iterations, and between
+// two windows it (1) retires the systems whose inner solve ended: the FP32 correction is added,
+// the FP64-accurate residual computed, and the system is done or starts its next refinement;
+// (2) finishes the requests whose systems are all done (final P_c, drho, results to the host);
+// (3) admits queued requests into the free slots (perturbations to real space, right-hand sides,
+// inner CG set-up).  A request that arrives while others are on the GPU therefore joins at the
+// next window, and its systems iterate in the same launches as theirs.  The arithmetic of a
+// system is that of the batched solve (same kernels, refinement and stopping rule), so a request's
+// result equals its result alone up to the rounding of the batched reductions.
+struct EngReq {
+  serve::Request rq;
+  int n_real = 0;
+  std::vector<int> brow;      // per perturbation: part row of its imaginary part, -1 if none
+  int pbase = -1;             // first perturbation-pool row of its parts
+  std::vector<int> slots;     // slot of system (r, v) at r n_v + v
+  int n_done = 0, n_conv = 0, max_iters = 0, refinements = 0, peers = 1;
+  double max_rel = 0.0;
+  std::chrono::steady_clock::time_point t_admit;
+};
+
+struct Engine {
+  enum { kFree = 0, kStart = 1, kInner = 2, kDone = 3 };
+  wgw_ctx* c = nullptr;
+  cudaStream_t st = nullptr;
+  int cap = 0, pcap = 0;
+  std::vector<int> phase, refine, iters, sys_r, sys_v;
+  std::vector<uint64_t> owner;
+  std::vector<int> free_slots;
+  std::vector<char> pool_used;
+  std::vector<int> a_idx, b_idx;
+  std::vector<double> eps, shift;
+  std::vector<float> shiftf;
+  std::map<uint64_t, EngReq> live;
+
+  int init(int n_cap, int n_pcap) {
+    cap = n_cap;
+    pcap = n_pcap;
+    WGW_TRY(ensure_work(c, cap, pcap));
+    WGW_TRY(c->norms.ensure(sizeof(double) * cap));
+    WGW_TRY(c->eng_mask.ensure(sizeof(int) * cap));
+    WGW_TRY(c->eng_list.ensure(sizeof(int) * cap));
+    WGW_TRY(c->eng_pool.ensure(sizeof(double) * (size_t)pcap * c->grid3));
+    phase.assign(cap, kFree); refine.assign(cap, 0); iters.assign(cap, 0); sys_r.assign(cap, 0);
+    sys_v.assign(cap, 0); owner.assign(cap, 0); a_idx.assign(cap, 0); b_idx.assign(cap, 0);
+    eps.assign(cap, 0.0); shift.assign(cap, 0.0); shiftf.assign(cap, 0.f);
+    free_slots.clear();
+    for (int s = cap - 1; s >= 0; --s) free_slots.push_back(s);
+    pool_used.assign(pcap, 0);
+    WGW_CK(cudaMemsetAsync(c->d.X.p, 0, sizeof(double) * (size_t)cap * c->ld_w, st));
+    WGW_CK(cudaMemsetAsync(c->cg_act.p, 0, sizeof(int) * cap, st));
+    return WGW_OK;
+  }
+  int pool_alloc(int n) {
+    for (int b = 0; b + n <= pcap; ++b) {
+      bool ok = true;
+      for (int k = 0; k < n && ok; ++k) ok = !pool_used[b + k];
+      if (ok) {
+        for (int k = 0; k < n; ++k) pool_used[b + k] = 1;
+        return b;
+      }
+    }
+    return -1;
+  }
+  // Uploads a host list and a matching mask over all slots; returns the device list.
+  int upload_list(const std::vector<int>& l, int** dev_list, const int** dev_mask) {
+    std::vector<int> mask(cap, 0);
+    for (int s : l) mask[s] = 1;
+    WGW_CK(cudaMemcpyAsync(c->eng_list.p, l.data(), sizeof(int) * l.size(), cudaMemcpyHostToDevice, st));
+    WGW_CK(cudaMemcpyAsync(c->eng_mask.p, mask.data(), sizeof(int) * cap, cudaMemcpyHostToDevice, st));
+    WGW_CK(cudaStreamSynchronize(st));   // the host vectors leave scope
+    *dev_list = c->eng_list.as<int>();
+    if (dev_mask) *dev_mask = c->eng_mask.as<int>();
+    return WGW_OK;
+  }
+  int upload_tables() {
+    WGW_CK(cudaMemcpyAsync(c->a_idx.p, a_idx.data(), sizeof(int) * cap, cudaMemcpyHostToDevice, st));
+    WGW_CK(cudaMemcpyAsync(c->b_idx.p, b_idx.data(), sizeof(int) * cap, cudaMemcpyHostToDevice, st));
+    WGW_CK(cudaMemcpyAsync(c->eps.p, eps.data(), sizeof(double) * cap, cudaMemcpyHostToDevice, st));
+    WGW_CK(cudaMemcpyAsync(c->d.shift.p, shift.data(), sizeof(double) * cap, cudaMemcpyHostToDevice, st));
+    WGW_CK(cudaMemcpyAsync(c->f.shift.p, shiftf.data(), sizeof(float) * cap, cudaMemcpyHostToDevice, st));
+    WGW_CK(cudaStreamSynchronize(st));
+    return WGW_OK;
+  }
+
+  // Admits one request (slots and pool rows are available): perturbation parts, dV(r), the
+  // right-hand sides of its systems, x = 0, r = b, |b|^2.
+  int admit(serve::Request&& rq) {
+    const int n_pert = rq.n_pert, n_v = c->n_v;
+    const long ldr = c->ld_r;
+    const HostSphere& rs = c->rho;
+    const bool sym = rq.kind == WGW_REQ_CHIBAR0;
+    const double* scale = sym ? rs.d_vsqrt.as<double>() : nullptr;
+    WGW_TRY(c->eng_in.ensure(sizeof(double) * 2 * (size_t)rs.n * n_pert));
+    WGW_CK(cudaMemcpyAsync(c->eng_in.p, rq.dV.data(), sizeof(double) * rq.dV.size(), cudaMemcpyHostToDevice, st));
+    WGW_TRY(c->dv_rb.ensure(sizeof(double) * (size_t)2 * n_pert * ldr));
+    double* dvrb = c->dv_rb.as<double>();
+    WGW_CK(cudaMemsetAsync(dvrb, 0, sizeof(double) * (size_t)2 * n_pert * ldr, st));
+    WGW_CK(launch_sphere_to_rb(n_pert, c->eng_in.as<double>(), 2L * rs.n, scale, rs.map(), 0, dvrb, ldr, st));
+    WGW_CK(launch_sphere_to_rb(n_pert, c->eng_in.as<double>(), 2L * rs.n, scale, rs.map(), 1,
+                               dvrb + (size_t)n_pert * ldr, ldr, st));
+    WGW_TRY(c->rr64.ensure(sizeof(double) * std::max(cap, 2 * n_pert)));
+    WGW_CK(launch_norm2<double>(2 * n_pert, rs.nrb(), dvrb, ldr, c->rr64.as<double>(), st));
+    std::vector<double> nrm(2 * n_pert);
+    WGW_CK(cudaMemcpyAsync(nrm.data(), c->rr64.p, sizeof(double) * 2 * n_pert, cudaMemcpyDeviceToHost, st));
+    WGW_CK(cudaStreamSynchronize(st));
+    EngReq er;
+    er.brow.assign(n_pert, -1);
+    int n_real = n_pert;
+    for (int p = 0; p < n_pert; ++p)
+      if (nrm[n_pert + p] > 0.0) {
+        if (n_real != n_pert + p)
+          WGW_CK(cudaMemcpyAsync(dvrb + (size_t)n_real * ldr, dvrb + (size_t)(n_pert + p) * ldr, sizeof(double) * ldr,
+                                 cudaMemcpyDeviceToDevice, st));
+        er.brow[p] = n_real++;
+      }
+    er.n_real = n_real;
+    er.pbase = pool_alloc(n_real);
+    if (er.pbase < 0 || (int)free_slots.size() < n_real * n_v) return fail(WGW_ERR_STATE, "engine admission without room");
+    double* pool = c->eng_pool.as<double>() + (size_t)er.pbase * c->grid3;
+    WGW_TRY(to_real<double>(c, c->d, rs, dvrb, ldr, n_real, pool, c->Trho, st));
+    std::vector<int> slots;
+    for (int r = 0; r < n_real; ++r)
+      for (int v = 0; v < n_v; ++v) {
+        const int sl = free_slots.back();
+        free_slots.pop_back();
+        slots.push_back(sl);
+        owner[sl] = rq.ticket; sys_r[sl] = r; sys_v[sl] = v; phase[sl] = kStart; refine[sl] = 0; iters[sl] = 0;
+        a_idx[sl] = v; b_idx[sl] = er.pbase + r;
+        eps[sl] = c->e_v[v]; shift[sl] = -c->e_v[v]; shiftf[sl] = (float)-c->e_v[v];
+      }
+    er.slots = slots;
+    WGW_TRY(upload_tables());
+    int* dl = nullptr;
+    const int* dm = nullptr;
+    WGW_TRY(upload_list(slots, &dl, &dm));
+    // Right-hand sides b_s = -P_c [psi_v(r) dV_r(r)] of the new slots.
+    const int n_new = (int)slots.size(), NP = 2 * c->wfc.m + 1, N = c->N, pairs = (n_new + 1) / 2;
+    WGW_TRY(c->d.Tw.ensure(sizeof(cplx<double>) * (size_t)pairs * NP * N * N));
+    FftCtx<double> f = c->d.fft(c->plan);
+    XArgs<double> a{};
+    a.mode = XM_FROM_REAL; a.A = c->d.psi_r_fft(); a.lda = c->grid3; a.a_index = c->a_idx.as<int>();
+    a.Bm = c->eng_pool.as<double>(); a.ldb = c->grid3; a.b_index = c->b_idx.as<int>(); a.n_sys = n_new; a.list = dl;
+    WGW_CK(launch_xline<double>(c->wfc.m, f, c->d.Tw.as<cplx<double>>(), a, nullptr, st));
+    Epi<double> e{};
+    e.out = c->d.Bv.as<double>(); e.ldo = c->ld_w; e.vcoef = -1.0; e.n_sys = n_new; e.list = dl;
+    WGW_CK(launch_plane_r2g<double>(c->wfc.tab(), c->wfc.npt_max, f, c->d.Tw.as<cplx<double>>(), e, st));
+    WGW_TRY(run_pc<double>(c, c->d.Bv.as<double>(), n_new, dl, c->d.psi.as<double>(), nullptr, st));
+    const int n = c->wfc.nrb();
+    const long ld = c->ld_w;
+    WGW_CK(launch_axpby(cap, n, 0.0, c->d.Bv.as<double>(), 0.0, c->d.Bv.as<double>(), c->d.X.as<double>(), ld, dm, st));
+    WGW_CK((launch_copy_cast<double, double>(cap, n, c->d.Bv.as<double>(), ld, c->d.R.as<double>(), ld, dm, st)));
+    WGW_CK(launch_norm2<double>(cap, n, c->d.Bv.as<double>(), ld, c->norms.as<double>(), st));
+    er.t_admit = std::chrono::steady_clock::now();
+    er.rq = std::move(rq);
+    er.peers = (int)live.size() + 1;
+    for (auto& kv : live) kv.second.peers = std::max(kv.second.peers, (int)live.size() + 1);
+    live.emplace(er.rq.ticket, std::move(er));
+    c->eng_requests++;
+    return WGW_OK;
+  }
+
+  // Starts the inner FP32 solves of the slots in phase kStart (right-hand side = FP64 residual).
+  int start_inner() {
+    std::vector<int> l;
+    for (int s = 0; s < cap; ++s)
+      if (phase[s] == kStart) l.push_back(s);
+    if (l.empty()) return WGW_OK;
+    int* dl = nullptr;
+    const int* dm = nullptr;
+    WGW_TRY(upload_list(l, &dl, &dm));
+    const int n = c->wfc.nrb();
+    const long ld = c->ld_w;
+    CgState cs = cg_state(c, true);
+    WGW_CK((launch_copy_cast<double, float>(cap, n, c->d.R.as<double>(), ld, c->f.Bv.as<float>(), ld, dm, st)));
+    WGW_CK(launch_cg_init_a<float>(c->wfc.tab(), n, (int)l.size(), c->f.Bv.as<float>(), c->f.X.as<float>(),
+                                   c->f.R.as<float>(), c->f.Z.as<float>(), ld, c->eps.as<double>(), cs, st, dl));
+    WGW_TRY(run_pc<float>(c, c->f.Z.as<float>(), (int)l.size(), dl, c->f.psi.as<float>(), cs.active, st));
+    WGW_CK(launch_cg_init_b<float>(n, (int)l.size(), c->f.R.as<float>(), c->f.Z.as<float>(), c->f.P.as<float>(), ld,
+                                   cs, st, dl));
+    for (int s : l) phase[s] = kInner;
+    return WGW_OK;
+  }
+
+  // One window of check_every FP32 CG iterations over every slot in its inner solve; then the
+  // systems whose inner solve ended are retired.
+  int window() {
+    std::vector<int> l;
+    for (int s = 0; s < cap; ++s)
+      if (phase[s] == kInner) l.push_back(s);
+    if (l.empty()) return WGW_OK;
+    int* dl = nullptr;
+    WGW_TRY(upload_list(l, &dl, nullptr));
+    const int n = c->wfc.nrb(), nl = (int)l.size();
+    const long ld = c->ld_w;
+    CgState cs = cg_state(c, true);
+    const int* act = cs.active;
+    float* P = c->f.P.as<float>();
+    float* Q = c->f.Q.as<float>();
+    for (int k = 0; k < std::max(1, c->opt.check_every); ++k) {
+      WGW_TRY(apply_A<float>(c, c->f, P, Q, nl, dl, act, st, false));
+      WGW_CK(launch_cg_step_a<float>(c->wfc.tab(), n, nl, dl, c->f.X.as<float>(), c->f.R.as<float>(),
+                                     c->f.Z.as<float>(), P, Q, ld, c->eps.as<double>(), cs,
+                                     c->opt.inner_tol * c->opt.inner_tol, c->opt.max_cg_iter, st));
+      WGW_TRY(run_pc<float>(c, c->f.Z.as<float>(), nl, dl, c->f.psi.as<float>(), act, st));
+      WGW_CK(launch_cg_step_b<float>(n, nl, dl, c->f.R.as<float>(), c->f.Z.as<float>(), P, ld, cs, st));
+    }
+    WGW_TRY(run_pc<float>(c, c->f.R.as<float>(), nl, dl, c->f.psi.as<float>(), act, st));
+    c->eng_windows++;
+    std::vector<int> ah(cap), ih(cap);
+    WGW_CK(cudaMemcpyAsync(ah.data(), cs.active, sizeof(int) * cap, cudaMemcpyDeviceToHost, st));
+    WGW_CK(cudaMemcpyAsync(ih.data(), cs.iters, sizeof(int) * cap, cudaMemcpyDeviceToHost, st));
+    WGW_CK(cudaStreamSynchronize(st));
+    std::vector<int> ret;
+    for (int s : l)
+      if (!ah[s]) ret.push_back(s);
+    if (ret.empty()) return WGW_OK;
+    // Retire: x += e, r = b - A x at FP64 accuracy, then done or the next refinement.
+    const int* dm = nullptr;
+    WGW_TRY(upload_list(ret, &dl, &dm));
+    double* X = c->d.X.as<double>();
+    WGW_CK(launch_add_to<float>(cap, n, c->f.X.as<float>(), ld, X, ld, dm, st));
+    WGW_TRY(apply_A<double>(c, c->d, X, c->d.Q.as<double>(), (int)ret.size(), dl, nullptr, st));
+    WGW_CK(launch_axpby(cap, n, 1.0, c->d.Bv.as<double>(), -1.0, c->d.Q.as<double>(), c->d.R.as<double>(), ld, dm, st));
+    WGW_CK(launch_norm2<double>(cap, n, c->d.R.as<double>(), ld, c->rr64.as<double>(), st));
+    std::vector<double> rr(cap), bb(cap);
+    WGW_CK(cudaMemcpyAsync(rr.data(), c->rr64.p, sizeof(double) * cap, cudaMemcpyDeviceToHost, st));
+    WGW_CK(cudaMemcpyAsync(bb.data(), c->norms.p, sizeof(double) * cap, cudaMemcpyDeviceToHost, st));
+    WGW_CK(cudaStreamSynchronize(st));
+    const double tol = c->opt.cg_tol;
+    for (int s : ret) {
+      iters[s] += ih[s];
+      const double rel = bb[s] > 0 ? std::sqrt(rr[s] / bb[s]) : 0.0;
+      const bool conv = rel <= tol * (1.0 + 1e-6) || bb[s] == 0.0;
+      EngReq& er = live.at(owner[s]);
+      if (conv || refine[s] + 1 >= c->opt.max_refine) {
+        phase[s] = kDone;
+        er.n_done++;
+        if (conv) er.n_conv++;
+        er.max_rel = std::max(er.max_rel, rel);
+        er.max_iters = std::max(er.max_iters, iters[s]);
+        er.refinements = std::max(er.refinements, refine[s] + 1);
+      } else {
+        refine[s]++;
+        phase[s] = kStart;
+      }
+    }
+    return WGW_OK;
+  }
+
+  // Releases a request's slots and pool rows.
+  void release(EngReq& er) {
+    for (int sl : er.slots) {
+      phase[sl] = kFree;
+      free_slots.push_back(sl);
+    }
+    for (int k = 0; k < er.n_real; ++k) pool_used[er.pbase + k] = 0;
+  }
+
+  // Final projection, drho and the results of a request whose systems are all done.
+  int finish(EngReq& er) {
+    const int n_pert = er.rq.n_pert, n_real = er.n_real, n_v = c->n_v;
+    const HostSphere& rs = c->rho;
+    int* dl = nullptr;
+    WGW_TRY(upload_list(er.slots, &dl, nullptr));
+    const int ns = (int)er.slots.size();
+    WGW_TRY(run_pc<double>(c, c->d.X.as<double>(), ns, dl, c->d.psi.as<double>(), nullptr, st));
+    WGW_TRY(c->eng_xc.ensure(sizeof(double) * (size_t)ns * c->ld_w));
+    WGW_CK(launch_gather_rows(ns, (int)c->ld_w, dl, c->d.X.as<double>(), c->ld_w, c->eng_xc.as<double>(), c->ld_w, st));
+    WGW_TRY(c->drho_rb.ensure(sizeof(double) * (size_t)n_real * c->ld_r));
+    WGW_TRY(drho_pass(c, c->eng_xc.as<double>(), c->ld_w, n_real, c->drho_rb.as<double>(), st));
+    const bool sym = er.rq.kind == WGW_REQ_CHIBAR0;
+    WGW_TRY(c->brow.ensure(sizeof(int) * n_pert));
+    WGW_CK(cudaMemcpyAsync(c->brow.p, er.brow.data(), sizeof(int) * n_pert, cudaMemcpyHostToDevice, st));
+    WGW_TRY(c->eng_out.ensure(sizeof(double) * 2 * (size_t)rs.n * n_pert));
+    WGW_CK(launch_rb_to_sphere(n_pert, c->drho_rb.as<double>(), c->ld_r, c->brow.as<int>(),
+                               sym ? rs.d_vsqrt.as<double>() : nullptr, rs.map(), c->eng_out.as<double>(), 2L * rs.n, st));
+    WGW_CK(cudaMemcpyAsync(er.rq.out, c->eng_out.p, sizeof(double) * 2 * (size_t)rs.n * n_pert,
+                           cudaMemcpyDeviceToHost, st));
+    WGW_CK(cudaStreamSynchronize(st));
+    (void)n_v;
+    return WGW_OK;
+  }
+};
+
+// A request the engine takes: chi0 or chibar0 at the single frequency 0.
+bool engine_eligible(const serve::Request& r) {
+  return (r.kind == WGW_REQ_CHI0 || r.kind == WGW_REQ_CHIBAR0) && r.omega.size() == 1 && r.omega[0] == 0.0;
+}
+
 }  // namespace
 
 namespace wgw {
@@ -2387,14 +2693,133 @@ static double batch_bytes(const wgw_ctx* c, int n_real, bool whole) {
   return resident * (per_sys * c->n_v + per_pert) + io;
 }
 
+// Slots of the engine: 60 % of the free device memory (plus the context's work buffers) at the
+// bytes one batched-solve system needs, at most 16384 (the option max_batch_systems caps it too).
+static int engine_capacity(wgw_ctx* c) {
+  double per_sys = 0, per_pert = 0;
+  solve_bytes(c, &per_sys, &per_pert);
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    free_b = 0;
+  }
+  const double budget = 0.6 * ((double)free_b + held_work_bytes(c));
+  int cap = (int)std::min(16384.0, budget / (per_sys + 2.0 * per_pert / std::max(1, c->n_v)));
+  if (c->opt.max_batch_systems > 0) cap = std::min(cap, c->opt.max_batch_systems);
+  return cap;
+}
+
+// Runs the engine until no live request is left and the queue's head is not one it takes.
+// Returns false (nothing taken) when the engine's buffers cannot be set up.
+static bool run_engine(wgw_ctx* c, int cap) {
+  std::lock_guard<std::recursive_mutex> ctx_lock(c->mu);
+  set_ff(c);
+  Engine E;
+  E.c = c;
+  E.st = c->stream;
+  const int n_v = c->n_v;
+  int rc = E.init(cap, 2 * (cap / n_v) + 2);
+  auto fail_all = [&](int status) {
+    std::lock_guard<std::mutex> lk(c->qmu);
+    const auto now = std::chrono::steady_clock::now();
+    for (auto& kv : E.live) c->sq.finish_one(kv.second.rq, status, kv.second.t_admit, now, kv.second.peers, 0);
+    E.live.clear();
+  };
+  if (rc != WGW_OK) return false;   // nothing admitted yet: the head is left to the batched path
+  for (;;) {
+    // Admission into the free slots, in queue order.
+    for (;;) {
+      serve::Request rq;
+      bool got;
+      {
+        std::lock_guard<std::mutex> lk(c->qmu);
+        got = c->sq.take_head_if([&](const serve::Request& h) {
+          const int worst = 2 * h.n_pert;
+          if (!engine_eligible(h) || worst * n_v > (int)E.free_slots.size()) return false;
+          int room = 0, best = 0;
+          for (int k = 0; k < E.pcap; ++k) { room = E.pool_used[k] ? 0 : room + 1; best = std::max(best, room); }
+          return best >= worst;
+        }, &rq);
+      }
+      if (!got) break;
+      const uint64_t t = rq.ticket;
+      const auto t0 = std::chrono::steady_clock::now();
+      serve::Request keep = rq;
+      rc = E.admit(std::move(rq));
+      if (rc != WGW_OK) {
+        std::lock_guard<std::mutex> lk(c->qmu);
+        c->sq.finish_one(keep, rc, t0, std::chrono::steady_clock::now(), 1, 0);
+        (void)t;
+        break;
+      }
+    }
+    if (rc != WGW_OK && rc != WGW_ERR_STATE) { fail_all(rc); break; }
+    rc = WGW_OK;
+    // Cancelled live requests leave at once.
+    std::vector<uint64_t> gone;
+    {
+      std::lock_guard<std::mutex> lk(c->qmu);
+      for (auto& kv : E.live)
+        if (c->sq.cancelled(kv.first)) gone.push_back(kv.first);
+    }
+    for (uint64_t t : gone) {
+      EngReq& er = E.live.at(t);
+      E.release(er);
+      std::lock_guard<std::mutex> lk(c->qmu);
+      c->sq.finish_one(er.rq, WGW_ERR_CANCELLED, er.t_admit, std::chrono::steady_clock::now(), er.peers,
+                       (int)er.slots.size());
+      E.live.erase(t);
+    }
+    if (!gone.empty()) c->qcv.notify_all();
+    if (E.live.empty()) break;
+    rc = E.start_inner();
+    if (rc == WGW_OK) rc = E.window();
+    if (rc != WGW_OK) { fail_all(rc); break; }
+    // Requests whose systems are all done.
+    std::vector<uint64_t> ready;
+    for (auto& kv : E.live)
+      if (kv.second.n_done == (int)kv.second.slots.size()) ready.push_back(kv.first);
+    for (uint64_t t : ready) {
+      EngReq& er = E.live.at(t);
+      rc = E.finish(er);
+      E.release(er);
+      const int status = rc != WGW_OK ? rc : (er.n_conv == (int)er.slots.size() ? WGW_OK : WGW_ERR_NOCONV);
+      {
+        std::lock_guard<std::mutex> lk(c->qmu);
+        c->sq.finish_one(er.rq, status, er.t_admit, std::chrono::steady_clock::now(), er.peers, (int)er.slots.size());
+      }
+      E.live.erase(t);
+      if (rc != WGW_OK) break;
+    }
+    if (!ready.empty()) c->qcv.notify_all();
+    if (rc != WGW_OK) { fail_all(rc); break; }
+  }
+  c->qcv.notify_all();
+  return true;
+}
+
 static void serve_loop(wgw_ctx* c) {
   cudaSetDevice(c->device);
   for (;;) {
     std::vector<serve::Request> batch;
+    int eng_cap = 0;
     {
       std::unique_lock<std::mutex> lk(c->qmu);
       c->qcv.wait(lk, [&] { return c->stop || !c->sq.empty(); });
       if (c->sq.empty()) return;
+      const serve::Request* h = c->sq.head();
+      if (c->opt.precision == WGW_MIXED && engine_eligible(*h)) {
+        lk.unlock();
+        eng_cap = engine_capacity(c);
+        lk.lock();
+        h = c->sq.head();
+        if (!h || !engine_eligible(*h) || 2 * h->n_pert * c->n_v > eng_cap) eng_cap = 0;
+      }
+    }
+    if (eng_cap > 0 && run_engine(c, eng_cap)) continue;
+    {
+      std::unique_lock<std::mutex> lk(c->qmu);
+      if (c->sq.empty()) continue;
       size_t free_b = 0, total_b = 0;
       if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
         cudaGetLastError();

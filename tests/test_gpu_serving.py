@@ -129,3 +129,51 @@ def test_submit_rejects_bad_requests(W, tiny):
         W.wgw_submit(ctx, d, [-0.1])
     with pytest.raises(W.WgwError):
         W.wgw_submit(ctx, d, [0.0], kind=7)
+
+
+def test_continuous_batching_admits_requests_into_running_cg(W):
+    """Mixed path, static requests: a request submitted while a long one is on the GPU is admitted
+    at the next CG window (its queueing time is a fraction of the long request's run), the two share
+    the slot pool, and each result equals the oracle and its own result alone within 1e-8."""
+    import time
+    s = synth.make_system("pdep_L16_48")
+    ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v,
+                      W.wgw_default_options(precision=W.WGW_MIXED, cg_tol=1e-10))
+    m = model_of(s)
+    big = synth.perturbations(s.miller_rho, s.L, 16, 301)
+    small = synth.perturbations(s.miller_rho, s.L, 2, 302)
+    alone_small, _, _ = W.wgw_apply_chi0(ctx, small)
+    t_big = W.wgw_submit(ctx, big, [0.0])
+    time.sleep(0.02)                              # the big request is on the GPU
+    t_small = W.wgw_submit(ctx, small, [0.0])
+    got_small, r_small = W.wgw_wait(t_small)
+    got_big, r_big = W.wgw_wait(t_big)
+    assert r_small["status"] == W.WGW_OK and r_big["status"] == W.WGW_OK
+    assert r_small["batch_requests"] >= 2 and r_big["batch_requests"] >= 2
+    assert r_small["queue_s"] < 0.5 * r_big["latency_s"], (r_small, r_big)
+    assert r_small["batch_systems"] == 2 * s.n_v and r_big["batch_systems"] == 16 * s.n_v
+    assert rel_err(got_small, alone_small) < 1e-8
+    states = chi0._states(m)
+    ref_small = chi0.sos_static_block(m, small, states)
+    assert rel_err(got_small[:, :, 0], ref_small) < 1e-8
+    ref_big = chi0.sos_static_block(m, big[:, :4], states)
+    assert rel_err(got_big[:, :4, 0], ref_big) < 1e-8
+
+
+def test_continuous_batching_cancel_running_request(W, cfg24):
+    """A running request of the continuous engine is dropped at the next window when cancelled;
+    the requests around it are served normally."""
+    s = cfg24
+    ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v,
+                      W.wgw_default_options(precision=W.WGW_MIXED, cg_tol=1e-11))
+    a = synth.perturbations(s.miller_rho, s.L, 4, 311)
+    b = synth.perturbations(s.miller_rho, s.L, 4, 312)
+    ta = W.wgw_submit(ctx, a, [0.0])
+    tb = W.wgw_submit(ctx, b, [0.0])
+    W.wgw_cancel(ta)
+    got_a, ra = W.wgw_wait(ta)
+    got_b, rb = W.wgw_wait(tb)
+    assert ra["status"] == W.WGW_ERR_CANCELLED and np.all(got_a == 0)
+    assert rb["status"] == W.WGW_OK
+    alone_b, _, _ = W.wgw_apply_chi0(ctx, b)
+    assert rel_err(got_b, alone_b) < 1e-8
