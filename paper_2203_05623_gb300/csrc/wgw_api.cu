@@ -1831,7 +1831,7 @@ struct Engine {
   int init(int n_cap, int n_pcap) {
     cap = n_cap;
     pcap = n_pcap;
-    WGW_TRY(ensure_work(c, cap, pcap));
+    WGW_TRY(ensure_work(c, cap, 1));
     WGW_TRY(c->norms.ensure(sizeof(double) * cap));
     WGW_TRY(c->eng_mask.ensure(sizeof(int) * cap));
     WGW_TRY(c->eng_list.ensure(sizeof(int) * cap));
