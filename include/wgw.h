@@ -438,9 +438,16 @@ int wgw_dyson(int n, int n_omega, const double* chi0bar, double* chibar);
  */
 #define WGW_REQ_CHI0 0     /* out = chi0(i omega) dV, as wgw_apply_chi0 */
 #define WGW_REQ_CHIBAR0 1  /* out = chi0bar(i omega) phi, as wgw_apply_chibar0 */
+#define WGW_REQ_PDEP 2     /* PDEP basis, as wgw_pdep_davidson: n_pert = n_pdep eigenpairs, dV = start block
+                              (N_rho x n_pdep complex) or NULL, no frequencies (omega may be NULL,
+                              n_omega 0); out = n_pdep eigenvalues followed by the basis (N_rho x n_pdep
+                              complex).  The Davidson runs on its own host thread and stream, and each of
+                              its chi0bar block applications is served like a WGW_REQ_CHIBAR0 request of
+                              the queue (batched with the other requests); result.batch_requests = block
+                              applications, result.batch_systems = Sternheimer systems solved. */
 
 typedef struct wgw_request {
-  int kind;               /* WGW_REQ_CHI0 or WGW_REQ_CHIBAR0 */
+  int kind;               /* WGW_REQ_CHI0, WGW_REQ_CHIBAR0 or WGW_REQ_PDEP */
   const double* dV;       /* host, N_rho x n_pert complex; copied during wgw_submit */
   int n_pert;
   const double* omega;    /* host, n_omega >= 1 frequencies >= 0; copied */

@@ -19,7 +19,7 @@ namespace wgw {
 namespace serve {
 
 constexpr int kOk = 0, kErrArg = 1, kErrNomem = 2, kErrCancelled = 7;
-constexpr int kKindChi0 = 0, kKindChibar0 = 1;
+constexpr int kKindChi0 = 0, kKindChibar0 = 1, kKindPdep = 2;
 constexpr int kMaxFrequencies = 4096;
 
 using Clock = std::chrono::steady_clock;
@@ -42,12 +42,20 @@ struct Done {
 
 // Checks a request descriptor before anything is copied: a known kind, at least one
 // perturbation, 1..kMaxFrequencies finite frequencies >= 0, non-null buffers, and finite
-// perturbation coefficients.  Returns kOk or kErrArg with the reason in *why.
+// perturbation coefficients.  A PDEP request (n_pert = number of eigenpairs) takes no
+// frequencies, and its start block dV may be null.  Returns kOk or kErrArg with the reason in *why.
 inline int validate(int kind, const double* dV, int n_pert, const double* omega, int n_omega, const double* out,
                     long n_rho, std::string* why) {
   auto bad = [&](const char* m) { if (why) *why = m; return kErrArg; };
-  if (kind != kKindChi0 && kind != kKindChibar0) return bad("unknown request kind");
+  if (kind != kKindChi0 && kind != kKindChibar0 && kind != kKindPdep) return bad("unknown request kind");
   if (n_pert < 1) return bad("need n_pert >= 1");
+  if (kind == kKindPdep) {
+    if (!out) return bad("null out");
+    if (dV)
+      for (size_t i = 0; i < 2 * (size_t)n_rho * n_pert; ++i)
+        if (!std::isfinite(dV[i])) return bad("start block coefficients must be finite");
+    return kOk;
+  }
   if (n_omega < 1 || n_omega > kMaxFrequencies) return bad("need 1 <= n_omega <= 4096 frequencies");
   if (!dV || !omega || !out) return bad("null dV, omega or out");
   for (int k = 0; k < n_omega; ++k)

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <deque>
+#include <functional>
 #include <map>
 #include <set>
 #include <mutex>
@@ -245,6 +246,10 @@ struct wgw_ctx {
   std::condition_variable qcv;
   serve::Queue sq;
   bool stop = false;
+  // Served Davidson requests: one host thread each while it runs (its block applications are
+  // requests of the queue); the worker stays up while any is running.
+  int pdep_active = 0;
+  std::vector<std::thread> pdep_threads;
   // Continuous-batching engine of the served static requests (worker thread only).
   DevBuf eng_in, eng_out, eng_xc, eng_list, eng_mask, eng_pool;
   long eng_requests = 0, eng_windows = 0;
@@ -257,6 +262,8 @@ struct wgw_ctx {
     }
     qcv.notify_all();
     if (worker.joinable()) worker.join();
+    for (std::thread& t : pdep_threads)
+      if (t.joinable()) t.join();
     prof.release();
     d.release(); f.release(); wfc.release(); rho.release();
     DevBuf* eng[] = {&eng_in, &eng_out, &eng_xc, &eng_list, &eng_mask, &eng_pool};
@@ -1321,22 +1328,23 @@ struct Davidson {
   int nr;           // real-basis length of the density sphere
   long ld;
   DevBuf vs_rb, gwork, Cbuf, Gbuf, Ubuf, sbuf, syw, info, cols, scl, Ysel;
+  Prof* pf = nullptr;   // the context's profiler, or an idle one off the context's thread
 
   int gemm_tn(const double* A, int m, const double* B, int n, double* C) {
     WGW_TRY(gwork.ensure(sizeof(double) * gemm_tn_work_elems(nr, m, n)));
-    WGW_CK(c->prof.run(PK_OTHER, 8.0 * (double)nr * (m + n), 2.0 * nr * m * n, st, [&] {
+    WGW_CK(pf->run(PK_OTHER, 8.0 * (double)nr * (m + n), 2.0 * nr * m * n, st, [&] {
       return launch_gemm_tn(A, ld, B, ld, nr, m, n, C, gwork.as<double>(), st); }));
     return WGW_OK;
   }
   int gemm_nn(const double* A, int k, const double* C, int ldc, int ncols, double* Y, double alpha, double beta) {
-    WGW_CK(c->prof.run(PK_OTHER, 8.0 * (double)nr * (k + 2 * ncols), 2.0 * nr * k * ncols, st, [&] {
+    WGW_CK(pf->run(PK_OTHER, 8.0 * (double)nr * (k + 2 * ncols), 2.0 * nr * k * ncols, st, [&] {
       return launch_gemm_nn(A, ld, nr, k, C, ldc, ncols, Y, ld, alpha, beta, st); }));
     return WGW_OK;
   }
   int syev(int n, double* A, double* w, double* Z) {
     WGW_TRY(syw.ensure(sizeof(double) * syev_work_elems(n)));
     WGW_TRY(info.ensure(sizeof(int)));
-    WGW_CK(c->prof.run(PK_OTHER, 16.0 * n * n, 3.0 * n * n * n, st, [&] {
+    WGW_CK(pf->run(PK_OTHER, 16.0 * n * n, 3.0 * n * n * n, st, [&] {
       return launch_syev(n, A, n, w, Z, n, syw.as<double>(), info.as<int>(), st); }));
     int h = 0;
     WGW_CK(cudaMemcpyAsync(&h, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1388,7 +1396,12 @@ struct Davidson {
     return WGW_OK;
   }
   // out = chibar0 in for nb vectors (real basis): v^1/2 chi0 v^1/2.
+  // Block application supplied from outside (the served Davidson routes it through the request
+  // queue); null = the context's own batched solve below.
+  std::function<int(const double* in, int nb, double* out, wgw_stats* acc)> ext;
+
   int chibar0(const double* in, int nb, double* out, wgw_stats* acc) {
+    if (ext) return ext(in, nb, out, acc);
     WGW_TRY(c->dv_rb.ensure(sizeof(double) * (size_t)nb * ld));
     double* dv = c->dv_rb.as<double>();
     dim3 g(std::max(1, std::min(64, (nr + 255) / 256)), std::min(nb, 65535));
@@ -1433,15 +1446,20 @@ struct Davidson {
 };
 
 int davidson_impl(wgw_ctx* c, int npd, const double* x0, double* eig, double* basis, wgw_stats* out_st,
-                  const std::vector<wgw_ctx*>& chans = {}) {
+                  const std::vector<wgw_ctx*>& chans = {},
+                  std::function<int(const double*, int, double*, wgw_stats*)> ext = nullptr,
+                  cudaStream_t own_stream = nullptr) {
   Davidson D;
   D.c = c;
   D.chans = chans;
-  set_ff(c);
-  D.st = c->stream;
+  D.ext = ext;
+  Prof idle;
+  D.pf = ext ? &idle : &c->prof;
+  if (!ext) set_ff(c);
+  D.st = own_stream ? own_stream : c->stream;
   D.nr = c->rho.nrb();
   D.ld = c->ld_r;
-  cudaStream_t st = c->stream;
+  cudaStream_t st = D.st;
   const long ld = D.ld;
   const int nr = D.nr;
   const int kmax = c->opt.dav_factor * npd;
@@ -1549,7 +1567,7 @@ int davidson_impl(wgw_ctx* c, int npd, const double* x0, double* eig, double* ba
     WGW_CK(cudaMemcpyAsync(basis, bout.p, sizeof(double) * 2 * (size_t)c->rho.n * npd, cudaMemcpyDeviceToHost, st));
     WGW_CK(cudaStreamSynchronize(st));
   }
-  c->prof.flush();
+  if (!ext) c->prof.flush();
   if (out_st) {
     out_st->n_systems = acc.n_systems;
     out_st->n_converged = converged;
@@ -2798,6 +2816,71 @@ static bool run_engine(wgw_ctx* c, int cap) {
   return true;
 }
 
+// A served Davidson request (Sec. 3, Sec. 4.2) on its own host thread and stream: the Davidson
+// iteration of davidson_impl, whose chibar0 block applications are submitted to the queue as
+// chibar0 requests (so that they are batched with everything else the context serves) and waited
+// for; the Rayleigh-Ritz work runs on the helper's stream.  Outputs: eigenvalues then the basis.
+static void pdep_helper(wgw_ctx* c, serve::Request rq) {
+  cudaSetDevice(c->device);
+  const auto t_start = std::chrono::steady_clock::now();
+  cudaStream_t hs = nullptr;
+  int rc = cudaStreamCreateWithFlags(&hs, cudaStreamNonBlocking) == cudaSuccess ? WGW_OK : WGW_ERR_CUDA;
+  const int n_rho = c->rho.n, npd = rq.n_pert;
+  int n_apply = 0;
+  wgw_stats st{};
+  DevBuf cin, cout;
+  auto ext = [&](const double* in, int nb, double* out, wgw_stats* acc) -> int {
+    {
+      std::lock_guard<std::mutex> lk(c->qmu);
+      if (c->sq.cancelled(rq.ticket)) return fail(WGW_ERR_CANCELLED, "request cancelled");
+    }
+    WGW_TRY(cin.ensure(sizeof(double) * 2 * (size_t)n_rho * nb));
+    WGW_TRY(cout.ensure(sizeof(double) * 2 * (size_t)n_rho * nb));
+    WGW_CK(launch_rb_to_sphere(nb, in, c->ld_r, nullptr, nullptr, c->rho.map(), cin.as<double>(), 2L * n_rho, hs));
+    serve::Request r;
+    r.kind = WGW_REQ_CHIBAR0;
+    r.n_pert = nb;
+    r.dV.resize(2 * (size_t)n_rho * nb);
+    r.omega = {0.0};
+    std::vector<double> o(2 * (size_t)n_rho * nb, 0.0);
+    r.out = o.data();
+    WGW_CK(cudaMemcpyAsync(r.dV.data(), cin.p, sizeof(double) * r.dV.size(), cudaMemcpyDeviceToHost, hs));
+    WGW_CK(cudaStreamSynchronize(hs));
+    r.t_submit = std::chrono::steady_clock::now();
+    uint64_t t;
+    {
+      std::lock_guard<std::mutex> lk(c->qmu);
+      t = c->sq.push(std::move(r));
+    }
+    c->qcv.notify_all();
+    serve::Done d;
+    {
+      std::unique_lock<std::mutex> lk(c->qmu);
+      c->qcv.wait(lk, [&] { return c->sq.state(t) == serve::Queue::kDone; });
+      c->sq.take_done(t, &d);
+    }
+    if (d.status != WGW_OK && d.status != WGW_ERR_NOCONV) return fail(d.status, "served chibar0 block failed");
+    WGW_CK(cudaMemcpyAsync(cout.p, o.data(), sizeof(double) * o.size(), cudaMemcpyHostToDevice, hs));
+    WGW_CK(cudaMemsetAsync(out, 0, sizeof(double) * (size_t)nb * c->ld_r, hs));
+    WGW_CK(launch_sphere_to_rb(nb, cout.as<double>(), 2L * n_rho, nullptr, c->rho.map(), 0, out, c->ld_r, hs));
+    WGW_CK(cudaStreamSynchronize(hs));   // o leaves scope
+    acc->n_systems += d.batch_systems;
+    ++n_apply;
+    return WGW_OK;
+  };
+  if (rc == WGW_OK)
+    rc = davidson_impl(c, npd, rq.dV.empty() ? nullptr : rq.dV.data(), rq.out, rq.out + npd, &st, {}, ext, hs);
+  cin.release();
+  cout.release();
+  if (hs) cudaStreamDestroy(hs);
+  {
+    std::lock_guard<std::mutex> lk(c->qmu);
+    c->sq.finish_one(rq, rc, t_start, std::chrono::steady_clock::now(), n_apply, st.n_systems);
+    c->pdep_active--;
+  }
+  c->qcv.notify_all();
+}
+
 static void serve_loop(wgw_ctx* c) {
   cudaSetDevice(c->device);
   for (;;) {
@@ -2805,9 +2888,16 @@ static void serve_loop(wgw_ctx* c) {
     int eng_cap = 0;
     {
       std::unique_lock<std::mutex> lk(c->qmu);
-      c->qcv.wait(lk, [&] { return c->stop || !c->sq.empty(); });
+      c->qcv.wait(lk, [&] { return (c->stop && c->pdep_active == 0) || !c->sq.empty(); });
       if (c->sq.empty()) return;
       const serve::Request* h = c->sq.head();
+      if (h->kind == WGW_REQ_PDEP) {
+        serve::Request rq;
+        c->sq.take_head_if([](const serve::Request&) { return true; }, &rq);
+        c->pdep_active++;
+        c->pdep_threads.emplace_back(pdep_helper, c, std::move(rq));
+        continue;
+      }
       if (c->opt.precision == WGW_MIXED && engine_eligible(*h)) {
         lk.unlock();
         eng_cap = engine_capacity(c);
@@ -2872,8 +2962,14 @@ int wgw_submit(wgw_ctx* c, const wgw_request* req, uint64_t* ticket) {
   serve::Request r;
   r.kind = req->kind;
   r.n_pert = req->n_pert;
-  r.dV.assign(req->dV, req->dV + (size_t)2 * c->rho.n * req->n_pert);
-  r.omega.assign(req->omega, req->omega + req->n_omega);
+  if (req->kind == WGW_REQ_PDEP) {
+    if (req->n_pert > c->rho.nrb() / 2 || c->opt.dav_factor * req->n_pert > 2048)
+      return fail(WGW_ERR_ARG, "n_pdep too large for the density sphere or the Davidson subspace");
+    if (req->dV) r.dV.assign(req->dV, req->dV + (size_t)2 * c->rho.n * req->n_pert);
+  } else {
+    r.dV.assign(req->dV, req->dV + (size_t)2 * c->rho.n * req->n_pert);
+    r.omega.assign(req->omega, req->omega + req->n_omega);
+  }
   r.out = req->out;
   r.t_submit = std::chrono::steady_clock::now();
   {

@@ -18,7 +18,7 @@ WGW_OK, WGW_ERR_ARG, WGW_ERR_NOMEM, WGW_ERR_NOCONV = 0, 1, 2, 3
 WGW_ERR_CUDA, WGW_ERR_TIMEOUT, WGW_ERR_STATE, WGW_ERR_CANCELLED = 4, 5, 6, 7
 WGW_FP64, WGW_MIXED = 0, 1
 WGW_SPHERE_WFC, WGW_SPHERE_RHO = 0, 1
-WGW_REQ_CHI0, WGW_REQ_CHIBAR0 = 0, 1
+WGW_REQ_CHI0, WGW_REQ_CHIBAR0, WGW_REQ_PDEP = 0, 1, 2
 WGW_PROF_KINDS = 18
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -321,8 +321,8 @@ def wgw_selftest_wait_timeout() -> int:
 class Ticket:
     """A submitted request; holds the output buffer until the library reports it done."""
 
-    def __init__(self, ctx, ticket, out):
-        self.ctx, self.ticket, self.out = ctx, ticket, out
+    def __init__(self, ctx, ticket, out, n_pdep=0):
+        self.ctx, self.ticket, self.out, self.n_pdep = ctx, ticket, out, n_pdep
 
 
 def wgw_submit(ctx: Context, dV, omega=(0.0,), kind: int = WGW_REQ_CHI0) -> Ticket:
@@ -338,6 +338,26 @@ def wgw_submit(ctx: Context, dV, omega=(0.0,), kind: int = WGW_REQ_CHI0) -> Tick
     t = ctypes.c_uint64()
     _check(lib().wgw_submit(ctx.handle, ctypes.byref(req), ctypes.byref(t)), "wgw_submit")
     return Ticket(ctx, t.value, out)
+
+
+def wgw_submit_pdep(ctx: Context, n_pdep: int, x0=None) -> Ticket:
+    """Queues a PDEP Davidson (n_pdep eigenpairs of chibar0, start block x0 (N_rho, n_pdep) or
+    None); its chibar0 block applications are served through the same queue.  wgw_wait returns
+    ((eigenvalues, basis (N_rho, n_pdep)), result dict)."""
+    xb = _interleave(x0) if x0 is not None else None
+    out = np.zeros(n_pdep + 2 * n_pdep * ctx.n_rho)
+    req = Request(WGW_REQ_PDEP, xb.ctypes.data_as(_dp) if xb is not None else None, n_pdep, None, 0,
+                  out.ctypes.data_as(_dp))
+    t = ctypes.c_uint64()
+    _check(lib().wgw_submit(ctx.handle, ctypes.byref(req), ctypes.byref(t)), "wgw_submit")
+    return Ticket(ctx, t.value, out, n_pdep)
+
+
+def _ticket_output(t: Ticket):
+    if t.n_pdep:
+        n = t.n_pdep
+        return t.out[:n].copy(), t.out[n:].view(np.complex128).reshape(n, t.ctx.n_rho).T
+    return t.out.transpose(2, 1, 0)
 
 
 def wgw_cancel(t: Ticket) -> None:
@@ -356,7 +376,7 @@ def wgw_wait(t: Ticket):
     """Blocks until done -> (result (N_rho, n_pert, n_omega), result dict)."""
     res = Result()
     _check(lib().wgw_wait(t.ctx.handle, t.ticket, ctypes.byref(res)), "wgw_wait")
-    return t.out.transpose(2, 1, 0), res.as_dict()
+    return _ticket_output(t), res.as_dict()
 
 
 def wgw_dyson(chi0bar):

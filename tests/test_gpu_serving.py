@@ -177,3 +177,53 @@ def test_continuous_batching_cancel_running_request(W, cfg24):
     assert rb["status"] == W.WGW_OK
     alone_b, _, _ = W.wgw_apply_chi0(ctx, b)
     assert rel_err(got_b, alone_b) < 1e-8
+
+
+def test_served_pdep_request_with_chibar0_requests(W, cfg24):
+    """A PDEP Davidson submitted to the queue (its chibar0 block applications are queued requests,
+    batched with whatever else is served) beside chibar0 requests: the eigenpairs equal the dense
+    PDEP oracle's and the synchronous Davidson's within the mixed path's 1e-8, and every chibar0
+    request equals its result alone."""
+    from oracle import pdep
+    s = cfg24
+    ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v,
+                      W.wgw_default_options(precision=W.WGW_MIXED, cg_tol=1e-11, dav_tol=1e-11))
+    n_pdep = 8
+    x0 = synth.perturbations(s.miller_rho, s.L, n_pdep, 11)
+    reqs = [synth.perturbations(s.miller_rho, s.L, 1 + k % 3, 320 + k) for k in range(6)]
+    t_pdep = W.wgw_submit_pdep(ctx, n_pdep, x0)
+    tickets = [W.wgw_submit(ctx, dV, [0.0], kind=W.WGW_REQ_CHIBAR0) for dV in reqs]
+    (eig, basis), r = W.wgw_wait(t_pdep)
+    assert r["status"] == W.WGW_OK, r
+    assert r["batch_requests"] >= 2 and r["batch_systems"] >= n_pdep * s.n_v
+    w_ref, U_ref = pdep.pdep_dense(model_of(s), 16)
+    assert np.max(np.abs(eig - w_ref[:n_pdep]) / np.abs(w_ref[:n_pdep])) < 1e-8
+    assert np.max(np.abs(basis.conj().T @ basis - np.eye(n_pdep))) < 1e-10
+    if abs(w_ref[n_pdep] - w_ref[n_pdep - 1]) > 1e-6:
+        sv = np.linalg.svd(U_ref[:, :n_pdep].conj().T @ basis, compute_uv=False)
+        assert np.min(sv) > 1 - 1e-7
+    eig_sync, _, _, _ = W.wgw_pdep_davidson(ctx, n_pdep, x0, want_basis=False)
+    assert np.max(np.abs(eig - eig_sync) / np.abs(eig_sync)) < 1e-8
+    for dV, t in zip(reqs, tickets):
+        got, rr = W.wgw_wait(t)
+        assert rr["status"] == W.WGW_OK
+        alone, _, _ = W.wgw_apply_chibar0(ctx, dV)
+        assert rel_err(got, alone) < 1e-8
+
+
+def test_served_pdep_cancel_and_bad_request(W, cfg24):
+    """A running PDEP request stops at its next block application when cancelled; one asking for
+    more eigenpairs than the Davidson subspace holds is refused at submission."""
+    s = cfg24
+    ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v,
+                      W.wgw_default_options(precision=W.WGW_MIXED, cg_tol=1e-11, dav_tol=1e-11))
+    t = W.wgw_submit_pdep(ctx, 8)
+    W.wgw_cancel(t)
+    _, r = W.wgw_wait(t)
+    assert r["status"] == W.WGW_ERR_CANCELLED
+    with pytest.raises(RuntimeError):
+        W.wgw_submit_pdep(ctx, 4096)
+    dV = synth.perturbations(s.miller_rho, s.L, 2, 330)
+    got, rr = W.wgw_wait(W.wgw_submit(ctx, dV, [0.0]))
+    alone, _, _ = W.wgw_apply_chi0(ctx, dV)
+    assert rr["status"] == W.WGW_OK and rel_err(got, alone) < 1e-8

@@ -151,3 +151,21 @@ def test_corrupted_descriptors_are_rejected(H):
     bad[7] = np.nan
     assert v(d=bad) == ERR_ARG
     assert v(d=None) == ERR_ARG and v(ob=None) == ERR_ARG and v(o=None) == ERR_ARG
+
+
+def test_pdep_descriptors(H):
+    """A PDEP request (kind 2) takes no frequencies and an optional start block; its output buffer
+    and a finite start block are still required."""
+    n_rho = 5
+    x0 = np.zeros(2 * n_rho * 2)
+    out = np.zeros(2 + 2 * n_rho * 2)
+
+    def v(d=x0, n_pert=2, ob=out):
+        ptr = (lambda a: a.ctypes.data_as(dp) if a is not None else None)
+        return H.sh_validate(2, ptr(d), n_pert, None, 0, ptr(ob), n_rho)
+
+    assert v() == OK and v(d=None) == OK
+    assert v(n_pert=0) == ERR_ARG and v(ob=None) == ERR_ARG
+    bad = x0.copy()
+    bad[3] = np.inf
+    assert v(d=bad) == ERR_ARG
