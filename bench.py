@@ -37,6 +37,13 @@ WORKLOADS = {
                          desc="served stream on the 48^3 model: chibar0 requests of 4-16 perturbations "
                               "(256-1024 Sternheimer systems), Poisson arrivals (seed 6) at 0.3/0.6/0.9 of "
                               "the measured closed-loop capacity, merged into batched applies"),
+    "serve_mixed": dict(config=None, n_pert=128, pert_seed=0, cg_tol=1e-10,
+                        desc="served mixed stream: one seeded system per grid of {32,48,64}^3 (cell "
+                             "N/3 bohr, ecut 9 Ha, N_v = 4 x wells drawn up to what the cell holds, "
+                             "0-8 KB atoms) and the 96^3 KB model (N_v 256), one context each; Poisson arrivals (seed 7) at 0.7 of the "
+                             "measured capacity of chibar0 requests (80 %, 16-128 perturbations) and "
+                             "PDEP Davidson requests (20 %, 16-64 eigenpairs, dav_tol 1e-8) on a system "
+                             "drawn uniformly; mixed FP32/FP64, continuously batched"),
     "dyson_P64_W32": dict(config=None, n_pert=64, pert_seed=32, cg_tol=0.0,
                           desc="Dyson step (1 - chibar0)^-1 chibar0 for 32 imaginary frequencies of a "
                                "64 x 64 PDEP-basis chibar0 (negative semidefinite, spectrum in [-8, 0])"),
@@ -72,6 +79,8 @@ def line_config(args, wl, tensor_cores, world):
             "pc_fp32": "tcgen05 3xTF32" if tensor_cores else "CUDA-core FP32",
             "h_fp32": {None: "autotuned (autotune.h_kernel)", 0: "three kernels", 1: "fused kernel"}[
                 getattr(args, "fused_h", None)],
+            "cg_launch": {None: "device-driven loop (conditional graph node)", 2: "device-driven loop (conditional graph node)",
+                          1: "one graph per window", 0: "direct launches"}[getattr(args, "cuda_graphs", None)],
             "l2": "256 MB buffer written between steps, outside the timed interval",
             "parallelism": f"perturbation shards x{world}" if world > 1 else "1 GPU"}
 
@@ -445,6 +454,105 @@ def run_serve(args, wl):
     W.wgw_destroy(ctx)
 
 
+def run_serve_mixed(args, wl):
+    """Served mixed stream over contexts of different grids: chibar0 and PDEP requests submitted at
+    Poisson arrival times through wgw_submit / wgw_submit_pdep, collected with wgw_wait."""
+    import numpy as np
+    import synth
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2203_05623_gb300 import build
+    build.build()
+    import paper_2203_05623_gb300 as W
+    t_gs = time.perf_counter()
+    systems = [synth.make_system(c) for c in synth.serve_stream_configs()]
+    t_gs = time.perf_counter() - t_gs
+    ctxs, pools, caps = [], [], []
+    for s in systems:
+        kb = s.beta_G.shape[1] > 0
+        opt = W.wgw_default_options(precision=W.WGW_MIXED, cg_tol=wl["cg_tol"], max_cg_iter=300, dav_tol=1e-8)
+        ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, opt,
+                          beta_G=s.beta_G if kb else None, d_proj=s.d_proj if kb else None)
+        pool = synth.perturbations(s.miller_rho, s.L, wl["n_pert"], s.cfg.pert_seed)
+        for _ in range(max(args.warmup, 1)):
+            W.wgw_apply_chibar0(ctx, pool[:, :16])
+        t0 = time.perf_counter()
+        _, st, _ = W.wgw_apply_chibar0(ctx, pool[:, :32])
+        caps.append(st["n_systems"] / (time.perf_counter() - t0))     # closed-loop systems/s
+        ctxs.append(ctx)
+        pools.append(pool)
+    rng = np.random.default_rng(7)
+    n_sys = len(systems)
+    # Mean GPU time of a request (a PDEP request costs about 6 block applications of its size).
+    mean_t = np.mean([(0.8 * 72 + 0.2 * 6 * 40) * s.n_v / caps[k] for k, s in enumerate(systems)])
+    load = 0.7
+    rate = load / mean_t
+    duration = float(max(20.0, 12.0 * args.steps))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=100000))
+    n_req = max(1, int(np.searchsorted(arrivals, duration)))
+    plan = []
+    for k in range(n_req):
+        sys_k = int(rng.integers(n_sys))
+        if rng.random() < 0.2:
+            plan.append(("pdep", sys_k, int(rng.integers(16, 65)), None))
+        else:
+            n = int(rng.integers(16, 129))
+            plan.append(("chibar0", sys_k, n, np.sort(rng.choice(wl["n_pert"], size=n, replace=False))))
+    tickets = []
+    with Clocks(local) as clk:
+        t_start = time.perf_counter()
+        for k, (kind, sys_k, n, cols) in enumerate(plan):
+            dt = arrivals[k] - (time.perf_counter() - t_start)
+            if dt > 0:
+                time.sleep(dt)
+            if kind == "pdep":
+                tickets.append(W.wgw_submit_pdep(ctxs[sys_k], n))
+            else:
+                tickets.append(W.wgw_submit(ctxs[sys_k], pools[sys_k][:, cols], [0.0], kind=W.WGW_REQ_CHIBAR0))
+        lat, solved, per_kind = [], 0, {"chibar0": [], "pdep": []}
+        outs = []
+        for (kind, sys_k, n, cols), t in zip(plan, tickets):
+            out, res = W.wgw_wait(t)
+            if res["status"] != W.WGW_OK:
+                raise RuntimeError(f"{kind} request on system {sys_k} failed with status {res['status']}")
+            lat.append(res["latency_s"])
+            per_kind[kind].append(res["latency_s"])
+            solved += res["batch_systems"] if kind == "pdep" else n * systems[sys_k].n_v
+            outs.append(out)
+        span = time.perf_counter() - t_start
+    # Served results against the same request alone (first chibar0 request of every system).
+    diff = 0.0
+    for sys_k in range(n_sys):
+        for (kind, sk, n, cols), out in zip(plan, outs):
+            if kind == "chibar0" and sk == sys_k:
+                alone, _, _ = W.wgw_apply_chibar0(ctxs[sys_k], pools[sys_k][:, cols])
+                num = np.linalg.norm((out - alone).reshape(out.shape[0], -1), axis=0)
+                den = np.linalg.norm(alone.reshape(alone.shape[0], -1), axis=0)
+                diff = max(diff, float(np.max(num / den)))
+                break
+
+    def pct(v, q):
+        return 1e3 * float(np.percentile(np.asarray(v), q)) if len(v) else None
+
+    print(json.dumps({
+        "metric": "served Sternheimer solves/s and request latency (arrival -> result on the host)",
+        "value": solved / span, "unit": "Sternheimer solves/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32/f64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": wl["desc"], "cg_tol": wl["cg_tol"],
+                   "systems": [{"grid": s.grid, "n_pw": s.n_pw, "n_v": s.n_v, "kb_atoms": int(len(np.unique(s.proj_atom))),
+                                "closed_loop_systems_per_s": caps[k]} for k, s in enumerate(systems)],
+                   "offered_load": load, "arrival_window_s": duration, "ground_states_s": t_gs},
+        "requests": n_req, "span_s": span,
+        "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99)},
+        "latency_ms_chibar0": {"p50": pct(per_kind["chibar0"], 50), "p99": pct(per_kind["chibar0"], 99)},
+        "latency_ms_pdep": {"p50": pct(per_kind["pdep"], 50), "p99": pct(per_kind["pdep"], 99)},
+        "served_vs_alone_rel_diff": diff, "clocks": clk.summary()}), flush=True)
+    for c in ctxs:
+        W.wgw_destroy(c)
+
+
 def library_baselines(W, ctx, s, prof_all):
     """The library's FP32 kernels against cuFFT and cuBLAS on the same shapes (untimed by the
     bench line; CUDA events around each variant, after warm-up).
@@ -651,6 +759,8 @@ def main():
                     help="FP32 H application as one fused kernel per pair (default: the library's)")
     ap.add_argument("--tensor-cores", type=int, default=None, choices=[0, 1],
                     help="P_c of the FP32 solves on the tcgen05 tensor cores (default: the library's)")
+    ap.add_argument("--cuda-graphs", type=int, default=None, choices=[0, 1, 2],
+                    help="CG launch mode: 2 device-driven loop, 1 a graph per window, 0 direct (default: 2)")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.n_pert > 0:
@@ -658,6 +768,8 @@ def main():
         wl["desc"] += f" (reduced to {args.n_pert} perturbations)"
     if args.impl == "reference":
         return run_reference(args, wl)
+    if args.workload == "serve_mixed":
+        return run_serve_mixed(args, wl)
     if args.workload.startswith("serve"):
         return run_serve(args, wl)
     if args.workload.startswith("dyson"):
@@ -701,6 +813,8 @@ def main():
         opt.tensor_cores = args.tensor_cores
     if args.fused_h is not None:
         opt.fused_h = args.fused_h
+    if args.cuda_graphs is not None:
+        opt.cuda_graphs = args.cuda_graphs
     kb = s.beta_G.shape[1] > 0
     ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, opt,
                       beta_G=s.beta_G if kb else None, d_proj=s.d_proj if kb else None)

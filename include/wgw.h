@@ -68,7 +68,7 @@ typedef struct wgw_options {
   int max_refine;      /* MIXED: FP64 refinement steps */
   double inner_tol;    /* MIXED: relative residual reduction of each inner FP32 solve */
   double f_s;          /* occupation of each state (2 = spin-unpolarised, the sum over sigma of Eq. dfpt) */
-  int check_every;     /* CG iterations between convergence polls by the host */
+  int check_every;     /* CG iterations between two compactions of the list of iterating systems */
   double dav_tol;      /* Davidson: max |lambda_i(k) - lambda_i(k-1)| <= dav_tol and every Ritz residual
                           norm <= sqrt(dav_tol) */
   int dav_max_iter;    /* Davidson iterations */
@@ -81,10 +81,15 @@ typedef struct wgw_options {
   int tensor_cores;    /* MIXED: 1 = the projector P_c of the FP32 inner solves runs on the tcgen05
                           tensor cores (TF32 products split three ways, hi*hi + hi*lo + lo*hi, FP32
                           accumulation: FP32 accuracy); 0 = FP32 CUDA-core GEMMs. */
-  int cuda_graphs;     /* 1 = the CG iterations between two convergence polls (check_every of them)
-                          are captured as one CUDA graph and replayed (the launches and results are
-                          the same as without; the first window of a solve runs directly); 0 = direct
-                          launches.  Not used while profiling is on. */
+  int cuda_graphs;     /* 2 = device-driven loop: after the first window of check_every iterations (run
+                          directly), each graph launch holds a conditional WHILE node that repeats a
+                          window and a device-side compaction of the list of systems still iterating
+                          (finished systems drop out of the launches without a host poll); the host
+                          waits only when half of the list has finished, to launch smaller grids.
+                          The same kernels as 1, with FP32 K splits sized for the captured list, so
+                          results agree with 1 to rounding.  1 = each window between two host polls
+                          is captured as one CUDA graph and replayed (bit-identical to 0); 0 = direct
+                          launches.  Graphs are not used while profiling is on. */
   int max_batch_systems;  /* most Sternheimer systems (complex-shifted: twice their count) solved as one
                              batch; larger applies run in chunks of whole perturbations.  0 = as many as
                              fit 85 % of the free device memory (the default). */
@@ -110,7 +115,7 @@ typedef struct wgw_stats {
 
 /* Fills *opt with defaults: WGW_FP64, cg_tol 1e-12, max_cg_iter 2000, max_refine 8,
  * inner_tol 5e-6, f_s 2, check_every 8, dav_tol 1e-8, dav_max_iter 100, dav_factor 4, seed 12345,
- * fp64_emulation 1, tensor_cores 1, cuda_graphs 1, max_batch_systems 0, fused_h 2, tc_split 0. */
+ * fp64_emulation 1, tensor_cores 1, cuda_graphs 2, max_batch_systems 0, fused_h 2, tc_split 0. */
 int wgw_default_options(wgw_options* opt);
 
 /*
@@ -476,7 +481,9 @@ int wgw_submit(wgw_ctx* ctx, const wgw_request* req, uint64_t* ticket);
  * status WGW_ERR_CANCELLED and its output left unwritten.  WGW_ERR_ARG for an unknown or
  * already finished ticket.  The ticket is still released by wgw_poll / wgw_wait. */
 int wgw_cancel(wgw_ctx* ctx, uint64_t ticket);
-/* *done = 1 (and *res filled, ticket released) when the request has finished, else 0. */
+/* *done = 1 (and *res filled, ticket released) when the request has finished, else 0.  For a
+ * request that finished with res->status != WGW_OK, wgw_last_error on the calling thread then
+ * says what failed (as wgw_wait). */
 int wgw_poll(wgw_ctx* ctx, uint64_t ticket, int* done, wgw_result* res);
 /* Blocks until the request has finished; fills *res (may be NULL) and releases the ticket. */
 int wgw_wait(wgw_ctx* ctx, uint64_t ticket, wgw_result* res);

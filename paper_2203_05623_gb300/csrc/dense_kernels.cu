@@ -577,8 +577,8 @@ cudaError_t launch_syev(int n, double* A, int lda, double* w, double* Z, int ldz
   if (n <= 0) return cudaSuccess;
   if (n > kSyevMax) return cudaErrorInvalidValue;
   const size_t smem = sizeof(double) * 2 * (size_t)n;
-  if (smem > 48 * 1024) {
-    cudaError_t err = cudaFuncSetAttribute(k_syev, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    cudaError_t err = ensure_smem_limit((const void*)k_syev, smem);
     if (err != cudaSuccess) return err;
   }
   k_syev<<<1, 1024, smem, st>>>(n, A, lda, w, Z, ldz, work, info, 0);
@@ -590,8 +590,8 @@ cudaError_t launch_syev_batched(int n, int batch, double* A, double* w, double* 
   if (n <= 0 || batch <= 0) return cudaSuccess;
   if (n > kSyevMax) return cudaErrorInvalidValue;
   const size_t smem = sizeof(double) * 2 * (size_t)n;
-  if (smem > 48 * 1024) {
-    cudaError_t err = cudaFuncSetAttribute(k_syev, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    cudaError_t err = ensure_smem_limit((const void*)k_syev, smem);
     if (err != cudaSuccess) return err;
   }
   k_syev<<<batch, n <= 128 ? 128 : 1024, smem, st>>>(n, A, n, w, Z, n, work, info, tridiagonal ? 1 : 0);

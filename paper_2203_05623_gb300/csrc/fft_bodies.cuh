@@ -54,7 +54,8 @@ struct VecBatch {
 WGW_HD bool is_active(const int* active, int s) { return active == nullptr || active[s] != 0; }
 
 // Members of pair q: entries 2q and 2q+1 of a system list (null = identity) of n_list
-// entries; the second member is -1 when 2q+1 >= n_list.
+// entries; the second member is -1 when 2q+1 >= n_list.  A list compacted on the device holds
+// -1 past its count: s0 = -1 marks a pair the kernels skip.
 WGW_HD void pair_members(const int* list, int n_list, int q, int& s0, int& s1) {
   s0 = list ? list[2 * q] : 2 * q;
   s1 = 2 * q + 1 < n_list ? (list ? list[2 * q + 1] : 2 * q + 1) : -1;

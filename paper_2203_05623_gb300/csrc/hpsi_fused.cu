@@ -44,9 +44,10 @@ constexpr int threads_for() { return N == 48 ? 288 : (N == 32 ? 256 : 192); }
 
 // Pair q is idle when none of its systems is active (the same rule as the separate kernels).
 __device__ __forceinline__ bool pair_idle(const int* active, const int* list, int pair, int n_list) {
-  if (active == nullptr) return false;
   int s0, s1;
   pair_members(list, n_list, pair, s0, s1);
+  if (s0 < 0) return true;   // past the count of a device-compacted list
+  if (active == nullptr) return false;
   return !active[s0] && (s1 < 0 || !active[s1]);
 }
 
@@ -267,7 +268,7 @@ cudaError_t launch_n(const SphereTab& sp, const float* P, long ldp, int n_list, 
   int R = 1;
   size_t smem = 0;
   if (!plan_map(N, sp.m, pm, R, smem)) return cudaErrorNotSupported;
-  cudaError_t err = cudaFuncSetAttribute(k_hpsi_fused<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t err = ensure_smem_limit((const void*)k_hpsi_fused<N>, smem);
   if (err != cudaSuccess) return err;
   if (R > 1) {
     err = cudaFuncSetAttribute(k_hpsi_fused<N>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);

@@ -211,6 +211,14 @@ template <typename T>
 cudaError_t launch_cg_init_b(int n, int n_sys, const T* R, const T* Z, T* P, long ld, CgState cs,
                              cudaStream_t st, const int* list = nullptr);
 // out[j] = in[rows[j]] for j < n_rows, rows of n doubles.
+// Raises the dynamic shared-memory limit of a kernel on the current device to at least `bytes`
+// and never lowers it: contexts of different sizes launch the same kernels from several host
+// threads, and a lower setting made by one between another's setting and its launch would make
+// that launch fail.
+cudaError_t ensure_smem_limit(const void* kernel, size_t bytes);
+// Control step of the device-driven CG loop (see k_loop_ctl in la_kernels.cu).
+cudaError_t launch_loop_ctl(const int* flags, int* list, int n_cap, int* rows, int* count, int* windows,
+                            int max_windows, int min_keep, cudaGraphConditionalHandle cond, cudaStream_t st);
 cudaError_t launch_gather_rows(int n_rows, int n, const int* rows, const double* in, long ldi, double* out, long ldo,
                                cudaStream_t st);
 template <typename T>

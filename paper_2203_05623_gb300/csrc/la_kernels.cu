@@ -1,6 +1,9 @@
 // __global__ wrappers of the linear-algebra kernels (bodies in la_bodies.cuh).
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <type_traits>
+#include <utility>
 
 #include "internal.h"
 
@@ -32,13 +35,17 @@ template <typename T>
 __global__ void k_cg_init_a(SphereTab sp, int n, const T* Bv, T* X, T* R, T* Z, long ld,
                             const double* eps, CgState cs, const int* list) {
   __shared__ double red[33];
-  cg_init_a_body<T>(list ? list[blockIdx.x] : blockIdx.x, sp, n, Bv, X, R, Z, ld, eps, cs, red, thr());
+  const int s = list ? list[blockIdx.x] : blockIdx.x;
+  if (s < 0) return;   // past the count of a device-compacted list
+  cg_init_a_body<T>(s, sp, n, Bv, X, R, Z, ld, eps, cs, red, thr());
 }
 
 template <typename T>
 __global__ void k_cg_init_b(int n, const T* R, const T* Z, T* P, long ld, CgState cs, const int* list) {
   __shared__ double red[33];
-  cg_init_b_body<T>(list ? list[blockIdx.x] : blockIdx.x, n, R, Z, P, ld, cs, red, thr());
+  const int s = list ? list[blockIdx.x] : blockIdx.x;
+  if (s < 0) return;
+  cg_init_b_body<T>(s, n, R, Z, P, ld, cs, red, thr());
 }
 
 // out[j] = in[rows[j]] for j < n_rows (rows of length n).
@@ -56,6 +63,7 @@ __global__ void k_cg_step_a(SphereTab sp, int n, T* X, T* R, T* Z, const T* P, c
                             const double* eps, CgState cs, double tol2, int max_iter, const int* list) {
   __shared__ double red[33];
   const int s = list ? list[blockIdx.x] : blockIdx.x;
+  if (s < 0) return;
   cg_step_a_body<T>(s, sp, n, X, R, Z, P, Q, ld, eps, cs, tol2, max_iter, red, thr());
 }
 
@@ -63,6 +71,7 @@ template <typename T>
 __global__ void k_cg_step_b(int n, const T* R, const T* Z, T* P, long ld, CgState cs, const int* list) {
   __shared__ double red[33];
   const int s = list ? list[blockIdx.x] : blockIdx.x;
+  if (s < 0) return;
   cg_step_b_body<T>(s, n, R, Z, P, ld, cs, red, thr());
 }
 
@@ -157,8 +166,8 @@ __device__ __forceinline__ void load_kchunk(C (*dst)[kGT + 4], const T* __restri
     const int c = e / (kGK / V), kq = (e % (kGK / V)) * V, k = k0 + kq;
     const int cc = col0 + c;
     T vals[V];
-    if (cc < n_cols) {
-      const int col = cols ? cols[cc] : cc;
+    const int col = cc < n_cols ? (cols ? cols[cc] : cc) : -1;
+    if (col >= 0) {
       const T* src = base + (size_t)col * ld + k;
       if (k + V <= k_hi) {
         const VT w = *reinterpret_cast<const VT*>(src);
@@ -281,7 +290,8 @@ __global__ void __launch_bounds__(256) k_pcf_gemm1(const float* __restrict__ Psi
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     const int j = j0 + lr + 32 * r;
-    brow[r] = j < n_list ? Y + (size_t)(list ? list[j] : j) * ldy : nullptr;
+    const int sj = j < n_list ? (list ? list[j] : j) : -1;
+    brow[r] = sj >= 0 ? Y + (size_t)sj * ldy : nullptr;
   }
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
@@ -376,7 +386,10 @@ __global__ void __launch_bounds__(256) k_pcf_gemm2(const float* __restrict__ Psi
   const int i0 = blockIdx.x * kF2R, j0 = blockIdx.y * kFS;
   if (active) {
     int any = 0;
-    for (int t = tid; t < kFS && j0 + t < n_list; t += 256) any |= active[list ? list[j0 + t] : j0 + t];
+    for (int t = tid; t < kFS && j0 + t < n_list; t += 256) {
+      const int st = list ? list[j0 + t] : j0 + t;
+      any |= st >= 0 && active[st];
+    }
     if (!__syncthreads_or(any)) return;
   }
   float acc[4][8];
@@ -415,7 +428,7 @@ __global__ void __launch_bounds__(256) k_pcf_gemm2(const float* __restrict__ Psi
     const int jx = j0 + ty * 8 + j;
     if (jx >= n_list) continue;
     const int sx = list ? list[jx] : jx;
-    if (active && !active[sx]) continue;
+    if (sx < 0 || (active && !active[sx])) continue;
     float* y = Y + (size_t)sx * ldy + r0;
     if (r0 + 4 <= n) {
       float4 w = beta != 0.f ? *reinterpret_cast<float4*>(y) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -468,7 +481,10 @@ __global__ void __launch_bounds__(256) k_pc_gemm2(const T* __restrict__ Psi, lon
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
   if (active) {
     bool any = false;
-    for (int t = 0; t < kGT && j0 + t < n_list; ++t) any |= active[list ? list[j0 + t] : j0 + t] != 0;
+    for (int t = 0; t < kGT && j0 + t < n_list; ++t) {
+      const int st = list ? list[j0 + t] : j0 + t;
+      any |= st >= 0 && active[st] != 0;
+    }
     if (!any) return;
   }
   CT acc[4][4];   // [row][system]
@@ -507,7 +523,7 @@ __global__ void __launch_bounds__(256) k_pc_gemm2(const T* __restrict__ Psi, lon
     const int jx = j0 + ty * 4 + j;
     if (jx >= n_list) continue;
     const int sx = list ? list[jx] : jx;
-    if (active && !active[sx]) continue;
+    if (sx < 0 || (active && !active[sx])) continue;
     T* y = Y + (size_t)sx * ldy + r0;
     if (r0 + 4 <= n) {
 #pragma unroll
@@ -560,6 +576,59 @@ __global__ void __launch_bounds__(1024) k_build_list(const int* __restrict__ act
   if (threadIdx.x == 0) *count = base;
 }
 
+// The control step of a device-driven CG loop (one block of 1024 threads), run after every
+// window of iterations inside a conditional WHILE graph node: compacts the n_cap entries of
+// `list` in place to the systems still flagged (keeping their order; entries past the new count
+// become -1, and with rows != null the row list 2s, 2s+1 of each complex system is rebuilt the
+// same way), stores the count, and sets the node's condition to keep looping while more than
+// min_keep systems remain and fewer than max_windows windows have run.
+__global__ void __launch_bounds__(1024) k_loop_ctl(const int* __restrict__ flags, int* __restrict__ list, int n_cap,
+                                                   int* __restrict__ rows, int* __restrict__ count,
+                                                   int* __restrict__ windows, int max_windows, int min_keep,
+                                                   cudaGraphConditionalHandle cond) {
+  __shared__ int warp_sums[32];
+  __shared__ int base;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  for (int c0 = 0; c0 < n_cap; c0 += blockDim.x) {
+    const int j = c0 + threadIdx.x;
+    const int s = j < n_cap ? list[j] : -1;
+    const int f = (s >= 0 && flags[s]) ? 1 : 0;
+    const unsigned mask = __ballot_sync(0xffffffffu, f);
+    const int before = __popc(mask & ((1u << lane) - 1u));
+    if (lane == 0) warp_sums[w] = __popc(mask);
+    __syncthreads();   // every entry of this chunk is read before any is overwritten
+    if (w == 0) {
+      int v = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+      }
+      warp_sums[lane] = v;
+    }
+    __syncthreads();
+    const int pos = base + (w ? warp_sums[w - 1] : 0) + before;   // pos <= j: writes stay behind the reads
+    if (f) {
+      list[pos] = s;
+      if (rows) { rows[2 * pos] = 2 * s; rows[2 * pos + 1] = 2 * s + 1; }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) base += warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+  }
+  const int n_left = base;
+  for (int j = n_left + threadIdx.x; j < n_cap; j += blockDim.x) {
+    list[j] = -1;
+    if (rows) { rows[2 * j] = -1; rows[2 * j + 1] = -1; }
+  }
+  if (threadIdx.x == 0) {
+    *count = n_left;
+    const int done = ++*windows;
+    cudaGraphSetConditional(cond, (n_left > min_keep && done < max_windows) ? 1u : 0u);
+  }
+}
+
 template <typename T>
 __global__ void k_cocg_init_a(SphereTab sp, int n, const T* Bv, T* X, T* R, T* Z, long ld, const double* eps,
                               CocgState cs) {
@@ -578,6 +647,7 @@ __global__ void k_cocg_step_a(SphereTab sp, int n, T* X, T* R, T* Z, const T* P,
                               const double* eps, CocgState cs, double tol2, int max_iter, const int* list) {
   __shared__ double red[33];
   const int s = list ? list[blockIdx.x] : blockIdx.x;
+  if (s < 0) return;
   cocg_step_a_body<T>(s, sp, n, X, R, Z, P, Q, ld, eps, cs, tol2, max_iter, red, thr());
 }
 
@@ -585,6 +655,7 @@ template <typename T>
 __global__ void k_cocg_step_b(int n, const T* R, const T* Z, T* P, long ld, CocgState cs, const int* list) {
   __shared__ double red[33];
   const int s = list ? list[blockIdx.x] : blockIdx.x;
+  if (s < 0) return;
   cocg_step_b_body<T>(s, n, R, Z, P, ld, cs, red, thr());
 }
 
@@ -629,6 +700,27 @@ inline dim3 grid_el(int n, int n_sys) {
 
 }  // namespace
 
+cudaError_t ensure_smem_limit(const void* kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> set_to;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = set_to[std::make_pair(kernel, dev)];
+  if (cur >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
+
+cudaError_t launch_loop_ctl(const int* flags, int* list, int n_cap, int* rows, int* count, int* windows,
+                            int max_windows, int min_keep, cudaGraphConditionalHandle cond, cudaStream_t st) {
+  k_loop_ctl<<<1, 1024, 0, st>>>(flags, list, n_cap, rows, count, windows, max_windows, min_keep, cond);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_pc(T* Y, long ldy, int n_sys, const int* list, const T* Psi, long ldp, int n, int nv,
                       const int* active, T* work, cudaStream_t st, bool ffc, const unsigned char* tc_tiles,
@@ -649,9 +741,9 @@ cudaError_t launch_pc(T* Y, long ldy, int n_sys, const int* list, const T* Psi, 
     // GPU (kblk a multiple of the 32-element K chunk).
     const int nkb_f = pcf_kblocks(n, n_sys);
     const int kblk32 = ((n + nkb_f - 1) / nkb_f + kFK - 1) / kFK * kFK;
-    cudaError_t e = cudaFuncSetAttribute(k_pcf_gemm1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kF1Smem);
+    cudaError_t e = ensure_smem_limit((const void*)k_pcf_gemm1, kF1Smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_pcf_gemm2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kF2Smem);
+    e = ensure_smem_limit((const void*)k_pcf_gemm2, kF2Smem);
     if (e != cudaSuccess) return e;
     dim3 gf1((n_sys + kFS - 1) / kFS, (n + kblk32 - 1) / kblk32, nvp / kGT);
     const int n_kb32 = (int)gf1.y;

@@ -38,6 +38,7 @@ struct Done {
   int status = kOk;
   double latency_s = 0, queue_s = 0;
   int batch_requests = 0, batch_systems = 0;
+  std::string msg;   // what failed, for a status other than kOk
 };
 
 // Checks a request descriptor before anything is copied: a known kind, at least one
@@ -155,10 +156,11 @@ class Queue {
 
   // Completes the requests of a batch with `status` (kErrCancelled for the cancelled ones).
   void finish(const std::vector<Request>& batch, int status, Clock::time_point t_start, Clock::time_point t_end,
-              int batch_systems) {
+              int batch_systems, const std::string& msg = std::string()) {
     for (const Request& r : batch) {
       Done d;
       d.status = cancelled_.count(r.ticket) ? kErrCancelled : status;
+      if (d.status != kOk) d.msg = d.status == kErrCancelled ? "request cancelled" : msg;
       d.latency_s = std::chrono::duration<double>(t_end - r.t_submit).count();
       d.queue_s = std::chrono::duration<double>(t_start - r.t_submit).count();
       d.batch_requests = (int)batch.size();
@@ -171,9 +173,10 @@ class Queue {
 
   // Completes one running request (kErrCancelled if it was cancelled) with its own batch figures.
   void finish_one(const Request& r, int status, Clock::time_point t_start, Clock::time_point t_end, int batch_requests,
-                  int batch_systems) {
+                  int batch_systems, const std::string& msg = std::string()) {
     Done d;
     d.status = cancelled_.count(r.ticket) ? kErrCancelled : status;
+    if (d.status != kOk) d.msg = d.status == kErrCancelled ? "request cancelled" : msg;
     d.latency_s = std::chrono::duration<double>(t_end - r.t_submit).count();
     d.queue_s = std::chrono::duration<double>(t_start - r.t_submit).count();
     d.batch_requests = batch_requests;

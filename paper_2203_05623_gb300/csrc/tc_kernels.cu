@@ -262,7 +262,8 @@ __global__ void __launch_bounds__(kThreads) k_tc_pc1(const unsigned char* __rest
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int j = j0 + (mg0 + 2 * i) * 8 + rr;
-    rowp[i] = j < n_list ? Y + static_cast<size_t>(list ? list[j] : j) * ldy : nullptr;
+    const int sj = j < n_list ? (list ? list[j] : j) : -1;
+    rowp[i] = sj >= 0 ? Y + static_cast<size_t>(sj) * ldy : nullptr;
   }
   float4 pre[8];
   auto load_a = [&](int kc) {
@@ -402,7 +403,7 @@ __global__ void __launch_bounds__(kThreads2, 2) k_tc_pc2(const unsigned char* __
     int sx = -1;
     if (j < n_list) {
       sx = list ? list[j] : j;
-      if (active && !active[sx]) sx = -1;
+      if (sx >= 0 && active && !active[sx]) sx = -1;
     }
     sys[t] = sx;
     any |= sx >= 0;
@@ -557,8 +558,7 @@ static cudaError_t launch_tc_pair(const float* Yin, float* Yout, long ldy, int n
   float* Cpart = work;
   unsigned char* ct = reinterpret_cast<unsigned char*>(work + static_cast<size_t>(g.n_kb) * n_sys * g.ldc);
   const size_t smem1 = 2u * (2u * tc::kTile + 2u * g.Nn * 128) + 64;
-  cudaError_t e = cudaFuncSetAttribute(tc::k_tc_pc1, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem1));
+  cudaError_t e = ensure_smem_limit((const void*)tc::k_tc_pc1, smem1);
   if (e != cudaSuccess) return e;
   tc::k_tc_pc1<<<dim3(g.njt, g.n_kb), tc::kThreads, smem1, st>>>(t1, Yin, ldy, n, nv, n_sys, list, g.kcpb, g.Nn,
                                                                  g.ldc, Cpart, err);
@@ -570,7 +570,7 @@ static cudaError_t launch_tc_pair(const float* Yin, float* Yout, long ldy, int n
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t smem2 = 4u * tc::kTile + 64 + tc::kRowsA * sizeof(int);
-  e = cudaFuncSetAttribute(tc::k_tc_pc2, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem2));
+  e = ensure_smem_limit((const void*)tc::k_tc_pc2, smem2);
   if (e != cudaSuccess) return e;
   tc::k_tc_pc2<<<dim3(g.nrt, g.njt), tc::kThreads2, smem2, st>>>(t2, ct, Yout, ldy, n, g.nvc, n_sys, list, alpha,
                                                                 beta, active, err);

@@ -216,7 +216,7 @@ struct wgw_ctx {
   // apply work space (double unless noted)
   DevBuf dvin, dv_rb, dv_r, Trho, Dr, drho_rb, eps, a_idx, b_idx, brow, cg_rz, cg_bb, cg_rr,
       cg_act, cg_it, cnt, rr64, act64, norms, pc_work, sys_list, list64, cg_rzi, omg, row_list, rowact,
-      drho_all, psi_tc, kb_tc, cg_best, cg_itbest, lz_q, lz_qf, tc_err;
+      drho_all, psi_tc, kb_tc, cg_best, cg_itbest, lz_q, lz_qf, tc_err, loop_ctr;
   cudaStream_t stream = nullptr;
   Prof prof;
   // Autotuner results: the K split of the tensor-core P_c (phase-1 CTAs per SM; 0 = not tuned
@@ -535,6 +535,76 @@ int build_list(wgw_ctx* c, const int* flags, int n, int* list, cudaStream_t st, 
   return WGW_OK;
 }
 
+// The device-driven CG loop (cuda_graphs = 2): one graph launch whose conditional WHILE node runs
+// `window` (check_every iterations over the list of n_cap entries it was captured with) and then
+// the control step k_loop_ctl, which compacts the list on the device (entries past the count
+// become -1, which every list kernel skips) and repeats the body while more than min_keep systems
+// are still iterating and fewer than max_windows windows have run.  The host waits once at the
+// end, for the count and the windows run, and captures the next launch with the shorter list:
+// no host poll between windows.  rows: the row list of the complex-shifted solve (null for CG).
+int device_loop(wgw_ctx* c, cudaStream_t st, const int* flags, int* list, int* rows, int n_cap, int max_windows,
+                int min_keep, const std::function<int(cudaStream_t)>& window, int* n_left, int* n_windows) {
+  WGW_TRY(c->loop_ctr.ensure(2 * sizeof(int)));
+  int* ctr = c->loop_ctr.as<int>();
+  // A default stream cannot be captured: the loop then runs on the context's stream, ordered
+  // after and before the caller's stream by events.
+  const bool side = st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread;
+  const cudaStream_t gst = side ? c->stream : st;
+  cudaError_t e = cudaSuccess;
+  auto ck = [&](cudaError_t x) { if (e == cudaSuccess) e = x; return e == cudaSuccess; };
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  if (side) {
+    ck(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
+    ck(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
+    ck(cudaEventRecord(ev_in, st));
+    ck(cudaStreamWaitEvent(gst, ev_in, 0));
+  }
+  ck(cudaMemsetAsync(ctr, 0, 2 * sizeof(int), gst));
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int status = WGW_OK;
+  ck(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h{};
+  ck(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  if (e == cudaSuccess) ck(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+  if (e == cudaSuccess && ck(cudaStreamBeginCaptureToGraph(gst, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                            cudaStreamCaptureModeRelaxed))) {
+    status = window(gst);
+    const cudaError_t le = status == WGW_OK
+        ? launch_loop_ctl(flags, list, n_cap, rows, ctr, ctr + 1, max_windows, min_keep, h, gst) : cudaSuccess;
+    cudaGraph_t body = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(gst, &body);
+    ck(le);
+    ck(ce);
+  }
+  int hc[2] = {0, 0};
+  if (status == WGW_OK && e == cudaSuccess) {
+    ck(cudaGraphInstantiate(&exec, g, 0));
+    ck(cudaGraphLaunch(exec, gst));
+    ck(cudaMemcpyAsync(hc, ctr, sizeof hc, cudaMemcpyDeviceToHost, gst));
+    ck(cudaStreamSynchronize(gst));
+    if (side) {
+      ck(cudaEventRecord(ev_out, gst));
+      ck(cudaStreamWaitEvent(st, ev_out, 0));
+    }
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (g) cudaGraphDestroy(g);
+  if (ev_in) cudaEventDestroy(ev_in);
+  if (ev_out) cudaEventDestroy(ev_out);
+  if (status != WGW_OK) return status;
+  if (e != cudaSuccess) return fail(WGW_ERR_CUDA, cudaGetErrorString(e));
+  *n_left = hc[0];
+  *n_windows = hc[1];
+  return WGW_OK;
+}
+
 // Preconditioned CG on A x = b for all systems (b in pr.Bv, x into pr.X), to relative residual tol.
 // Every check_every iterations the host rebuilds the list of systems still iterating, and the
 // following iterations launch over that list only.
@@ -598,8 +668,20 @@ int cg_solve(wgw_ctx* c, Prec<T>& pr, int n_sys, double tol, int max_iter, cudaS
   }
   cudaGraphExec_t exec = nullptr;
   int status = WGW_OK;
+  const bool dev_loop = graphs && c->opt.cuda_graphs == 2;
   for (int it = 0; it < max_iter && n_list > 0;) {
     const int w = std::min(every - it % every, max_iter - it);
+    if (dev_loop && it > 0 && it % every == 0) {
+      // Halve the grids: return to the host when half of the captured list has finished.
+      int left = 0, ran = 0;
+      status = device_loop(c, st, act, lbuf, nullptr, n_list, (max_iter - it + every - 1) / every,
+                           n_list > 64 ? n_list / 2 : 0, [&](cudaStream_t s) { return window(it, every, s); },
+                           &left, &ran);
+      if (status != WGW_OK) break;
+      it += ran * every;
+      n_list = left;
+      continue;
+    }
     if (graphs && it > 0) {
       // Failures set status and leave the loop, so that the executable graph and the events
       // are destroyed below on every path.
@@ -837,17 +919,37 @@ int cocg_solve(wgw_ctx* c, Prec<T>& pr, int n_cs, double tol, int max_iter, cuda
   const int* lbuf = c->sys_list.as<int>();
   const int* rbuf = c->row_list.as<int>();
   const int every = std::max(1, c->opt.check_every);
-  for (int it = 0; it < max_iter && n_list > 0; ++it) {
+  const bool proj_q = sizeof(T) == sizeof(double) || kProjectInnerOutput;
+  auto iteration = [&](cudaStream_t s) -> int {
     const double lb = 2.0 * n_list * n * sizeof(T);
-    const bool proj_q = sizeof(T) == sizeof(double) || kProjectInnerOutput;
-    WGW_TRY(apply_A<T>(c, pr, P, Q, 2 * n_list, rbuf, nullptr, st, proj_q));
-    WGW_CK(c->prof.run(PK_CG, 9 * lb, 0, st, [&] {
+    WGW_TRY(apply_A<T>(c, pr, P, Q, 2 * n_list, rbuf, nullptr, s, proj_q));
+    WGW_CK(c->prof.run(PK_CG, 9 * lb, 0, s, [&] {
       return launch_cocg_step_a<T>(c->wfc.tab(), n, n_list, lbuf, X, R, Z, P, Q, ld, eps, cs, tol * tol,
-                                   max_iter, st); }));
-    WGW_TRY(run_pc<T>(c, Z, 2 * n_list, rbuf, Psi, nullptr, st));
-    WGW_CK(c->prof.run(PK_CG, 4 * lb, 0, st, [&] {
-      return launch_cocg_step_b<T>(n, n_list, lbuf, R, Z, P, ld, cs, st); }));
-    if ((it + 1) % every == 0) {
+                                   max_iter, s); }));
+    WGW_TRY(run_pc<T>(c, Z, 2 * n_list, rbuf, Psi, nullptr, s));
+    WGW_CK(c->prof.run(PK_CG, 4 * lb, 0, s, [&] {
+      return launch_cocg_step_b<T>(n, n_list, lbuf, R, Z, P, ld, cs, s); }));
+    return WGW_OK;
+  };
+  const bool dev_loop = c->opt.cuda_graphs == 2 && !c->prof.on;
+  for (int it = 0; it < max_iter && n_list > 0;) {
+    if (dev_loop && it > 0 && it % every == 0) {   // as in cg_solve, after a first direct window
+      int left = 0, ran = 0;
+      WGW_TRY(device_loop(c, st, cs.active, c->sys_list.as<int>(), c->row_list.as<int>(), n_list,
+                          (max_iter - it + every - 1) / every, n_list > 64 ? n_list / 2 : 0,
+                          [&](cudaStream_t s) -> int {
+                            for (int k = 0; k < every; ++k) WGW_TRY(iteration(s));
+                            if (!proj_q) WGW_TRY(run_pc<T>(c, R, 2 * n_list, rbuf, Psi, nullptr, s));
+                            return WGW_OK;
+                          },
+                          &left, &ran));
+      it += ran * every;
+      n_list = left;
+      continue;
+    }
+    WGW_TRY(iteration(st));
+    ++it;
+    if (it % every == 0) {
       if (!proj_q) WGW_TRY(run_pc<T>(c, R, 2 * n_list, rbuf, Psi, nullptr, st));   // as in cg_solve
       WGW_TRY(build_cs_lists(c, cs.active, n_cs, st, &n_list));
     }
@@ -2115,7 +2217,7 @@ int wgw_default_options(wgw_options* opt) {
   opt->precision = WGW_FP64;
   opt->fp64_emulation = 1;
   opt->tensor_cores = 1;
-  opt->cuda_graphs = 1;
+  opt->cuda_graphs = 2;
   opt->cg_tol = 1e-12;
   opt->max_cg_iter = 2000;
   opt->max_refine = 8;
@@ -2736,11 +2838,20 @@ static bool run_engine(wgw_ctx* c, int cap) {
   E.c = c;
   E.st = c->stream;
   const int n_v = c->n_v;
-  int rc = E.init(cap, 2 * (cap / n_v) + 2);
+  int rc;
+  {
+    // Contexts of one process share the device memory: sizing the engine from the free memory
+    // and allocating it is one step, so that two contexts never size from the same reading.
+    static std::mutex hbm_mu;
+    std::lock_guard<std::mutex> adm(hbm_mu);
+    cap = std::min(cap, engine_capacity(c));
+    if (cap < 2 * n_v) return false;
+    rc = E.init(cap, 2 * (cap / n_v) + 2);
+  }
   auto fail_all = [&](int status) {
     std::lock_guard<std::mutex> lk(c->qmu);
     const auto now = std::chrono::steady_clock::now();
-    for (auto& kv : E.live) c->sq.finish_one(kv.second.rq, status, kv.second.t_admit, now, kv.second.peers, 0);
+    for (auto& kv : E.live) c->sq.finish_one(kv.second.rq, status, kv.second.t_admit, now, kv.second.peers, 0, g_last_error);
     E.live.clear();
   };
   if (rc != WGW_OK) return false;   // nothing admitted yet: the head is left to the batched path
@@ -2766,7 +2877,7 @@ static bool run_engine(wgw_ctx* c, int cap) {
       rc = E.admit(std::move(rq));
       if (rc != WGW_OK) {
         std::lock_guard<std::mutex> lk(c->qmu);
-        c->sq.finish_one(keep, rc, t0, std::chrono::steady_clock::now(), 1, 0);
+        c->sq.finish_one(keep, rc, t0, std::chrono::steady_clock::now(), 1, 0, g_last_error);
         (void)t;
         break;
       }
@@ -2804,7 +2915,8 @@ static bool run_engine(wgw_ctx* c, int cap) {
       const int status = rc != WGW_OK ? rc : (er.n_conv == (int)er.slots.size() ? WGW_OK : WGW_ERR_NOCONV);
       {
         std::lock_guard<std::mutex> lk(c->qmu);
-        c->sq.finish_one(er.rq, status, er.t_admit, std::chrono::steady_clock::now(), er.peers, (int)er.slots.size());
+        c->sq.finish_one(er.rq, status, er.t_admit, std::chrono::steady_clock::now(), er.peers, (int)er.slots.size(),
+                         g_last_error);
       }
       E.live.erase(t);
       if (rc != WGW_OK) break;
@@ -2859,7 +2971,7 @@ static void pdep_helper(wgw_ctx* c, serve::Request rq) {
       c->qcv.wait(lk, [&] { return c->sq.state(t) == serve::Queue::kDone; });
       c->sq.take_done(t, &d);
     }
-    if (d.status != WGW_OK && d.status != WGW_ERR_NOCONV) return fail(d.status, "served chibar0 block failed");
+    if (d.status != WGW_OK && d.status != WGW_ERR_NOCONV) return fail(d.status, "served chibar0 block: " + d.msg);
     WGW_CK(cudaMemcpyAsync(cout.p, o.data(), sizeof(double) * o.size(), cudaMemcpyHostToDevice, hs));
     WGW_CK(cudaMemsetAsync(out, 0, sizeof(double) * (size_t)nb * c->ld_r, hs));
     WGW_CK(launch_sphere_to_rb(nb, cout.as<double>(), 2L * n_rho, nullptr, c->rho.map(), 0, out, c->ld_r, hs));
@@ -2875,7 +2987,7 @@ static void pdep_helper(wgw_ctx* c, serve::Request rq) {
   if (hs) cudaStreamDestroy(hs);
   {
     std::lock_guard<std::mutex> lk(c->qmu);
-    c->sq.finish_one(rq, rc, t_start, std::chrono::steady_clock::now(), n_apply, st.n_systems);
+    c->sq.finish_one(rq, rc, t_start, std::chrono::steady_clock::now(), n_apply, st.n_systems, g_last_error);
     c->pdep_active--;
   }
   c->qcv.notify_all();
@@ -2946,7 +3058,7 @@ static void serve_loop(wgw_ctx* c) {
                       r.out + (size_t)2 * n_rho * ((size_t)k * r.n_pert));
         off += r.n_pert;
       }
-      c->sq.finish(batch, status, t_start, std::chrono::steady_clock::now(), stt.n_systems);
+      c->sq.finish(batch, status, t_start, std::chrono::steady_clock::now(), stt.n_systems, g_last_error);
     }
     c->qcv.notify_all();
   }
@@ -2983,6 +3095,8 @@ int wgw_submit(wgw_ctx* c, const wgw_request* req, uint64_t* ticket) {
 }
 
 static void fill_result(const serve::Done& d, wgw_result* res) {
+  // The failure of a served request is reported by wgw_last_error on the thread that collects it.
+  if (d.status != WGW_OK) g_last_error = d.msg;
   if (!res) return;
   res->status = d.status;
   res->latency_s = d.latency_s;

@@ -369,14 +369,22 @@ def wgw_poll(t: Ticket):
     """(done, result dict or None); a finished ticket is released by the call that reports it."""
     done, res = ctypes.c_int(), Result()
     _check(lib().wgw_poll(t.ctx.handle, t.ticket, ctypes.byref(done), ctypes.byref(res)), "wgw_poll")
-    return bool(done.value), (res.as_dict() if done.value else None)
+    if not done.value:
+        return False, None
+    d = res.as_dict()
+    if d["status"] != WGW_OK:
+        d["error"] = lib().wgw_last_error().decode()
+    return True, d
 
 
 def wgw_wait(t: Ticket):
     """Blocks until done -> (result (N_rho, n_pert, n_omega), result dict)."""
     res = Result()
     _check(lib().wgw_wait(t.ctx.handle, t.ticket, ctypes.byref(res)), "wgw_wait")
-    return _ticket_output(t), res.as_dict()
+    d = res.as_dict()
+    if d["status"] != WGW_OK:
+        d["error"] = lib().wgw_last_error().decode()
+    return _ticket_output(t), d
 
 
 def wgw_dyson(chi0bar):

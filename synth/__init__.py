@@ -56,6 +56,7 @@ class Config:
     kb_d_d: float = 0.3       # D_d [Ha]
     min_gap: float = 0.01     # reseed (seed + 1) while HOMO-LUMO gap < this [Ha]
     min_dist: float = 0.0     # hard core: redraw a centre closer than this to an earlier one [bohr]
+    n_kb: int = -1            # with kb: only the first n_kb atoms carry projectors (-1: every atom)
 
 
 CONFIGS = {
@@ -77,6 +78,34 @@ CONFIGS = {
     "tiny_L6_12": Config("tiny_L6_12", L=6.0, ecut=2.5, grid=12, n_wells=2,
                          well_seed=7, n_v=2, n_pert=3, pert_seed=8),
 }
+
+
+# The served mixed stream: one system per grid of SERVE_GRIDS.  On 32^3, 48^3 and 64^3: cell
+# L = N/3 bohr at ecut 9 Ha (max Miller index 0.675 L, so each grid is alias-free for the
+# iterative solver), wells 6 Ha deep and 0.9 bohr wide at least 4 bohr apart so that every well
+# binds an s and three p states below a gap, N_v = 4 x wells drawn uniformly up to what the cell
+# holds (SERVE_NV_CAP), and 0-8 of the atoms carrying s + p KB projectors.  On 96^3 the 96^3 KB
+# model (kb_L24_96: N_v = 256, 64 KB atoms): the block solver of the ground state does not reach
+# 1e-10 within its iteration limit on the L = 32 bohr cell of the same family.
+SERVE_GRIDS = (32, 48, 64, 96)
+SERVE_NV_CAP = {32: 32, 48: 96, 64: 160, 96: 256}
+
+
+def serve_stream_configs(seed: int = 55) -> list:
+    """The seeded systems of the served mixed stream, one Config per grid of SERVE_GRIDS."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for g in SERVE_GRIDS:
+        if g == 96:
+            out.append(CONFIGS["kb_L24_96"])
+            continue
+        n_wells = int(rng.integers(4, SERVE_NV_CAP[g] // 4 + 1))
+        n_kb = int(min(rng.integers(0, 9), n_wells))
+        out.append(Config(f"serve{g}", L=g / 3.0, ecut=9.0, grid=g, n_wells=n_wells,
+                          well_seed=int(rng.integers(1, 1 << 30)), n_v=4 * n_wells, n_pert=128,
+                          pert_seed=int(rng.integers(1, 1 << 30)), well_depth=6.0, well_width=0.9,
+                          min_dist=4.0, kb=n_kb > 0, n_kb=n_kb if n_kb > 0 else -1))
+    return out
 
 
 def miller_sphere(L: float, ecut: float) -> np.ndarray:
@@ -193,7 +222,7 @@ def _kb_projectors(cfg: Config, miller_wfc: np.ndarray, positions: np.ndarray):
     and with kb_dch five d-type beta_d,k = -wp^2 Q_k(G) beta_s, Q = (GxGy, GyGz, GzGx, (Gx^2 - Gy^2)/2,
     (3Gz^2 - G^2)/(2 sqrt 3)) (the transforms of the l = 2 real harmonics times a Gaussian)."""
     n_pw = miller_wfc.shape[0]
-    if not cfg.kb:
+    if not cfg.kb or cfg.n_kb == 0:
         return (np.zeros((n_pw, 0), np.complex128), np.zeros(0), np.zeros(0, np.int32))
     b = 2.0 * math.pi / cfg.L
     G = b * miller_wfc.astype(np.float64)
@@ -202,7 +231,8 @@ def _kb_projectors(cfg: Config, miller_wfc: np.ndarray, positions: np.ndarray):
     radial = np.exp(-0.5 * wp * wp * G2) / math.sqrt(cfg.L ** 3)
     S = _structure_factor(miller_wfc, positions, cfg.L)
     cols, d, atom = [], [], []
-    for a in range(positions.shape[0]):
+    n_atoms = positions.shape[0] if cfg.n_kb < 0 else min(cfg.n_kb, positions.shape[0])
+    for a in range(n_atoms):
         s = radial * S[:, a]
         cols.append(s); d.append(cfg.kb_d_s); atom.append(a)
         for alpha in range(3):
@@ -537,7 +567,10 @@ def _lobpcg(H: _RealH, X: np.ndarray, n_conv: int, tol: float, max_iter: int = 3
 
 def _cache_key(cfg: Config) -> str:
     import hashlib
-    return hashlib.sha256(repr(dataclasses.astuple(cfg)).encode() + b"lobpcg-v1").hexdigest()[:20]
+    fields = dataclasses.astuple(cfg)
+    if cfg.n_kb < 0:             # the field came later: keys of configurations without it stay put
+        fields = fields[:-1]
+    return hashlib.sha256(repr(fields).encode() + b"lobpcg-v1").hexdigest()[:20]
 
 
 def _make_system_iterative(cfg: Config, tol: float = 1e-10) -> System:

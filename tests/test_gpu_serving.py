@@ -227,3 +227,56 @@ def test_served_pdep_cancel_and_bad_request(W, cfg24):
     got, rr = W.wgw_wait(W.wgw_submit(ctx, dV, [0.0]))
     alone, _, _ = W.wgw_apply_chi0(ctx, dV)
     assert rr["status"] == W.WGW_OK and rel_err(got, alone) < 1e-8
+
+
+def test_mixed_grid_stream_of_chibar0_and_pdep_requests(W, cfg24):
+    """The served mixed stream at test size: contexts on a 24^3 and a 32^3 system (the 32^3 one of
+    the served-stream recipe: 8 deep wells, 32 states, 7 KB atoms), chibar0 and PDEP requests
+    submitted from several threads and interleaved across the two.  Each chibar0 result equals its
+    result alone and the oracle's sum over states within 1e-8; each PDEP request's eigenvalues
+    equal the synchronous Davidson's within 1e-8 (and the dense PDEP oracle's on 24^3)."""
+    from oracle import pdep
+    s32 = synth.make_system(synth.serve_stream_configs()[0])
+    assert s32.grid == 32 and s32.beta_G.shape[1] == 28
+    opt = W.wgw_default_options(precision=W.WGW_MIXED, cg_tol=1e-11, dav_tol=1e-11)
+    sy = {24: cfg24, 32: s32}
+    ctx = {g: W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, opt,
+                          beta_G=s.beta_G if s.beta_G.shape[1] else None,
+                          d_proj=s.d_proj if s.beta_G.shape[1] else None) for g, s in sy.items()}
+    plan = []
+    for k in range(8):
+        g = (24, 32)[k % 2]
+        if k in (2, 5):
+            plan.append(("pdep", g, 4, synth.perturbations(sy[g].miller_rho, sy[g].L, 4, 340 + k)))
+        else:
+            plan.append(("chibar0", g, 0, synth.perturbations(sy[g].miller_rho, sy[g].L, 1 + k % 3, 340 + k)))
+    tickets = [None] * len(plan)
+
+    def submit(i):
+        kind, g, n, x = plan[i]
+        tickets[i] = W.wgw_submit_pdep(ctx[g], n, x) if kind == "pdep" else \
+            W.wgw_submit(ctx[g], x, [0.0], kind=W.WGW_REQ_CHIBAR0)
+
+    th = [threading.Thread(target=submit, args=(i,)) for i in range(len(plan))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    results = [W.wgw_wait(t) for t in tickets]
+    dense24 = pdep.pdep_dense(model_of(cfg24), 8)[0]
+    states = {g: chi0._states(model_of(s)) for g, s in sy.items()}
+    for (kind, g, n, x), (out, r) in zip(plan, results):
+        assert r["status"] == W.WGW_OK, (kind, g, r.get("error"))
+        if kind == "pdep":
+            eig, basis = out
+            eig_sync, _, _, _ = W.wgw_pdep_davidson(ctx[g], n, x, want_basis=False)
+            assert np.max(np.abs(eig - eig_sync) / np.abs(eig_sync)) < 1e-8
+            assert np.max(np.abs(basis.conj().T @ basis - np.eye(n))) < 1e-10
+            if g == 24:
+                assert np.max(np.abs(eig - dense24[:n]) / np.abs(dense24[:n])) < 1e-8
+        else:
+            alone, _, _ = W.wgw_apply_chibar0(ctx[g], x)
+            assert rel_err(out, alone) < 1e-8
+            m = model_of(sy[g])
+            ref = m.vsqrt[:, None] * chi0.sos_static_block(m, m.vsqrt[:, None] * x, states[g])
+            assert rel_err(out[:, :, 0], ref) < 1e-8
