@@ -45,10 +45,19 @@ int fail(int status, const std::string& msg) {
     if (s_ != WGW_OK) return s_;      \
   } while (0)
 
-// Device buffer that only grows.
+// Device buffer that only grows; freed when it goes out of scope (move-only).
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+    return *this;
+  }
+  ~DevBuf() { release(); }
   int ensure(size_t need) {
     if (need <= bytes) return WGW_OK;
     if (p) cudaFree(p);
