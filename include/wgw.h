@@ -423,6 +423,85 @@ int wgw_isr(wgw_ctx* ctx, const double* phi, int n_pdep, const int* states, int 
 int wgw_dyson(int n, int n_omega, const double* chi0bar, double* chibar);
 
 /*
+ * Response and screened response in a basis at complex frequencies (Sec. 2, the Dyson step;
+ * Sec. 3, Eq. lanczos with the i w of the resolvent replaced by a complex z): from the chains of
+ * wgw_lanczos (same phi and n_steps, run inside this call),
+ *   chi0_z[k][m][n] = (f_s/Omega) sum_v sum_l' W[v][n][l'][m] [1/(e_v - d_l' - z_k) + 1/(e_v - d_l' + z_k)],
+ *   W[v][n][l'][m] = beta_1 U_{1 l'} sum_l <P_c phi~_n psi_v|q^l> U_{l l'}   (chain of (v, m)),
+ * and lam_z[k] = (1 - chi0_z[k])^-1 chi0_z[k] (complex Gaussian elimination with partial
+ * pivoting, one CTA per frequency), all in FP64 on the GPU.  z = w + i eta is a real frequency
+ * w with a broadening eta (the frequencies the residue term of Eq. Rfac needs); z = i w gives
+ * wgw_lanczos's chi0_pdep.
+ *   z          host, n_z complex frequencies, interleaved (re, im).
+ *   chi0_z, lam_z  host outputs (either may be NULL), n_z x n_pdep x n_pdep complex, interleaved,
+ *              element (m, n) of frequency k at 2 ((k n_pdep + m) n_pdep + n).
+ * Returns WGW_ERR_ARG for bad sizes or when 1 - chi0_z is singular at one of the frequencies.
+ */
+int wgw_lanczos_z(wgw_ctx* ctx, const double* phi, int n_pdep, int n_steps, const double* z, int n_z,
+                  double* chi0_z, double* lam_z, wgw_stats* st);
+
+/*
+ * Parameters of the correlation self-energy (wgw_sigma, wgw_qp).
+ *   n_steps_chi  length of the chi0 Lanczos chains in the basis (Eq. lanczos), 1..255.
+ *   n_steps_g0   length of the G0 chains (Eq. ISR), 1..255.
+ *   nodes, weights, n_nodes  quadrature of the imaginary-axis integral over [0, inf) (host).
+ *   e_fermi      Fermi energy [Ha]: at least the highest occupied e_v.
+ *   eta          broadening of Lambda at the real frequencies of the residue term [Ha], >= 0.
+ */
+typedef struct wgw_sigma_params {
+  int n_steps_chi;
+  int n_steps_g0;
+  const double* nodes;
+  const double* weights;
+  int n_nodes;
+  double e_fermi;
+  double eta;
+} wgw_sigma_params;
+
+/*
+ * Diagonal self-energy of occupied states at real frequencies by contour deformation (Sec. 2,
+ * Eq. sigmacIR: Sigma(w) = Sigma_X + I(w) + R(w)), every part on the GPU from chains run once
+ * inside the call:
+ *   sigma_x[i]   as wgw_sigma_x.
+ *   isr[i][j]    I^SR_i(w_j) of Eq. ISR as wgw_isr (real), with Lambda(i w'_k) at the quadrature
+ *                nodes from the chi0 chains of the basis (wgw_lanczos_z at z = i w'_k).
+ *   res[i][j]    R_i(w_j) of Eq. Rfac in the basis (complex, interleaved):
+ *                  (1/Omega) sum_j' f_ij'(w) sum_nm Lambda_nm(e_j' - w + i eta) <b_n|j'><j'|b_m>,
+ *                  f_ij'(w) = theta(e_j' - e_F) theta(w - e_j') - theta(e_F - e_j') theta(e_j' - w),
+ *                b_n = psi_i phi~_n, Lambda from the chi0 chains (wgw_lanczos_z at e_j' - w + i eta).
+ * The context holds the occupied states only, so every w_j must be <= e_fermi: there f vanishes
+ * for every empty state and the sum runs over the occupied j' with e_j' > w (the Kohn-Sham
+ * energies stand in for the quasiparticle energies in f).
+ *   states     host, n_states indices of occupied states.
+ *   omega      host, n_omega real frequencies [Ha], each <= e_fermi.
+ *   sigma_x    host output (or NULL), n_states.
+ *   isr        host output (or NULL), n_states x n_omega.
+ *   res        host output (or NULL), n_states x n_omega complex, interleaved.
+ * Returns WGW_ERR_ARG for bad sizes, a state outside 0..n_v-1, e_fermi below an occupied energy,
+ * a frequency above e_fermi, or when 1 - chi0 is singular at a frequency it needs.
+ */
+int wgw_sigma(wgw_ctx* ctx, const double* phi, int n_pdep, const int* states, int n_states,
+              const wgw_sigma_params* prm, const double* omega, int n_omega, double* sigma_x, double* isr,
+              double* res, wgw_stats* st);
+
+/*
+ * Quasiparticle energies of occupied states (Sec. 2, Eq. e_qp):
+ *   e_qp = e_i + Re <psi_i|Sigma(e_qp)|psi_i> - <psi_i|v_xc|psi_i>,
+ * solved by the secant method from e_i and e_i + 0.01 Ha (Sec. 3: a root-finding algorithm such
+ * as the secant method), stopping when two iterates differ by at most tol * max(1, |e|); Sigma as
+ * wgw_sigma, its chains run once for all iterations and the states of a call iterate together.
+ *   v_xc       host, n_states expectation values of the exchange-correlation potential (NULL = 0).
+ *   e_qp       host output, n_states.
+ *   sigma_qp   host output (or NULL), n_states complex (interleaved): Sigma_i(e_qp).
+ *   iters      host output (or NULL), n_states: secant steps taken.
+ * Returns WGW_ERR_NOCONV when a state has not converged in max_iter steps (or its secant
+ * stalls), WGW_ERR_ARG as wgw_sigma, also when an iterate rises above e_fermi.
+ */
+int wgw_qp(wgw_ctx* ctx, const double* phi, int n_pdep, const int* states, int n_states,
+           const wgw_sigma_params* prm, const double* v_xc, double tol, int max_iter, double* e_qp,
+           double* sigma_qp, int* iters, wgw_stats* st);
+
+/*
  * Serving (no counterpart in the paper, which runs one calculation per job): non-blocking
  * requests on a context.  wgw_submit copies the request's inputs and returns a ticket at once;
  * one worker thread per context runs queued requests on the context's stream.

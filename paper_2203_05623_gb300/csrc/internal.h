@@ -248,6 +248,20 @@ cudaError_t launch_norm2(int n_sys, int n, const T* x, long ld, double* out, cud
 cudaError_t launch_to_ff(size_t n, const double* in, double* out, cudaStream_t st);
 // X = (1 - A)^-1 A per n x n row-major matrix of a batch (dense_kernels.cu); M: work of the same size.
 cudaError_t launch_dyson(int n, int n_omega, const double* A, double* X, double* M, int* info, cudaStream_t st);
+// Self-energy at real frequencies (sigma_kernels.cu).
+// chi[e][m][n] = coef sum_v sum_l' W[v][n][l'][m] [1/(e_v - d - z_e) + 1/(e_v - d + z_e)], complex.
+cudaError_t launch_chi_z(int n_pdep, int n_v, int n_steps, int n_e, const double* W, const double* d,
+                         const double* e_v, const double* z, double coef, double* chi, cudaStream_t st);
+// X = (1 - A)^-1 A per complex n x n row-major matrix of a batch; M: work of the same size.
+cudaError_t launch_dyson_z(int n, int batch, const double* A, double* X, double* M, int* info, cudaStream_t st);
+// I^SR at one real frequency per point from the G0 residues C, Ritz values d and Lambda at the nodes.
+cudaError_t launch_isr_points(int n_pdep, int n_states, int n_steps, int n_nodes, int n_pts, const double* C,
+                              const double* d, const int* pt_state, const double* pt_w, const double* lam,
+                              const double* nodes, const double* wts, double coef, double* out, cudaStream_t st);
+// Residue-term contraction per entry: f_e sum_nm Lambda_e[m][n] Y_n Y_m (complex).
+cudaError_t launch_residue_entries(int n_pdep, int n_e, const double* lam, const double* Y, long ys,
+                                   const int* e_state, const int* e_j, const double* e_f, double* out,
+                                   cudaStream_t st);
 // Loads the work array of wgw_symm_eig_noalloc_dev on the current device and caches its device
 // address (dense_kernels.cu); returns a WGW status.
 int noalloc_prepare();

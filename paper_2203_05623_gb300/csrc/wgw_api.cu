@@ -1710,11 +1710,22 @@ struct LzG0 {
   double* isr = nullptr;            // host output, n_states x n_omega complex
 };
 
+// Spectral data of a set of chains kept on the device for later evaluation at any frequency:
+// the residues W[v][n][l'][m] = beta_1 U_{1 l'} sum_l <b_(n,v)|q^l_(m,v)> U_{l l'} and the Ritz
+// values d of chain s = m n_v + v (v over the occupied states for the chi0 chains, over the
+// listed states for the G0 chains); for the G0 chains also the overlaps
+// Y[i][j][m] = <psi_j | psi_(states i) phi~_m> with every occupied j (rows of length n_pdep,
+// ys doubles per listed state).
+struct LzKeep {
+  DevBuf W, d, Y;
+  long ys = 0;
+};
+
 // Lanczos chains of every (state, basis vector) pair.  Without g0: chains of P_c H P_c from
 // P_c [phi~_m psi_v], every occupied v, and chi0 in the basis.  With g0: chains of H.
 int lanczos_impl(wgw_ctx* c, const double* phi, int npd, int n_steps, const double* omega, int n_om,
                  double* alpha_out, double* beta_out, double* chi_out, wgw_stats* st_out,
-                 const LzG0* g0 = nullptr) {
+                 const LzG0* g0 = nullptr, LzKeep* keep = nullptr) {
   cudaStream_t st = c->stream;
   // FP64-accurate chains: float-float FFT passes on the mixed path (compiled grids), native FP64
   // otherwise.
@@ -1828,6 +1839,21 @@ int lanczos_impl(wgw_ctx* c, const double* phi, int npd, int n_steps, const doub
                           ov.as<double>() + (size_t)v * ovs, gw.as<double>(), st, lists.as<int>(), Qf != nullptr));
     WGW_CK(cudaStreamSynchronize(st));   // cols is reused for the next state
   }
+  if (keep && !proj) {
+    // Overlaps of every occupied state with the chain starts b_(m,i) = psi_i phi~_m (unnormalised).
+    const int nv_all = c->n_v;
+    keep->ys = (long)((nv_all + 63) / 64 * 64) * npd;
+    WGW_TRY(keep->Y.ensure(sizeof(double) * (size_t)keep->ys * n_v));
+    WGW_TRY(gw.ensure(sizeof(double) * gemm_tn_work_elems(n, nv_all, npd)));
+    for (int v = 0; v < n_v; ++v) {
+      for (int m = 0; m < npd; ++m) cols[m] = m * n_v + v;
+      WGW_CK(cudaMemcpyAsync(lists.p, cols.data(), sizeof(int) * npd, cudaMemcpyHostToDevice, st));
+      WGW_CK(launch_gemm_tn(c->d.psi.as<double>(), ldw, S, ldw, n, nv_all, npd,
+                            keep->Y.as<double>() + (size_t)v * keep->ys, gw.as<double>(), st, lists.as<int>(),
+                            c->d.use_ff));
+      WGW_CK(cudaStreamSynchronize(st));
+    }
+  }
   // Tridiagonal spectra d, U of every chain.
   WGW_TRY(T.ensure(sizeof(double) * (size_t)n_ch * n_steps * n_steps));
   WGW_TRY(U.ensure(sizeof(double) * (size_t)n_ch * n_steps * n_steps));
@@ -1842,6 +1868,15 @@ int lanczos_impl(wgw_ctx* c, const double* phi, int npd, int n_steps, const doub
   WGW_CK(cudaStreamSynchronize(st));
   for (int q = 0; q < n_ch; ++q)
     if (infh[q] != 0) return fail(WGW_ERR_NOCONV, "tridiagonal eigensolver did not converge");
+  if (keep) {
+    const size_t nW = (size_t)n_v * npd * n_steps * npd;
+    WGW_TRY(keep->W.ensure(sizeof(double) * nW));
+    WGW_TRY(keep->d.ensure(sizeof(double) * (size_t)n_ch * n_steps));
+    WGW_CK(launch_lz_residues(npd, n_v, n_steps, ov.as<double>(), U.as<double>(), be.as<double>(),
+                              keep->W.as<double>(), st));
+    WGW_CK(cudaMemcpyAsync(keep->d.p, dd.p, sizeof(double) * (size_t)n_ch * n_steps, cudaMemcpyDeviceToDevice, st));
+    WGW_CK(cudaStreamSynchronize(st));
+  }
   if (!proj) {
     // Residues C[i][n][l'][m] = beta_1 U_{1 l'} sum_l <b_n|q^l_m> U_{l l'}, then the resolvent
     // matrices g0[i][k][n][m] = sum_l' C[i][n][l'][m] / (d_l' - z_k).
@@ -2634,12 +2669,7 @@ int wgw_apply_h_dev(wgw_ctx* c, const double* psi_dev, int n_psi, double* out_de
   return WGW_OK;
 }
 
-int wgw_sigma_x(wgw_ctx* c, const int* states, int n_states, double* sigma_x) {
-  g_last_error.clear();
-  if (!c || !states || n_states < 1 || !sigma_x) return fail(WGW_ERR_ARG, "need a context, states and output");
-  for (int k = 0; k < n_states; ++k)
-    if (states[k] < 0 || states[k] >= c->n_v) return fail(WGW_ERR_ARG, "state index outside 0..n_v-1");
-  std::lock_guard<std::recursive_mutex> lk(c->mu);
+static int sigma_x_impl(wgw_ctx* c, const int* states, int n_states, double* sigma_x) {
   cudaStream_t st = c->stream;
   set_ff(c);
   const int N = c->N, n_v = c->n_v;
@@ -2689,6 +2719,15 @@ int wgw_sigma_x(wgw_ctx* c, const int* states, int n_states, double* sigma_x) {
   }
   for (int k = 0; k < n_states; ++k) sigma_x[k] = -acc[k] / c->omega_cell;
   return WGW_OK;
+}
+
+int wgw_sigma_x(wgw_ctx* c, const int* states, int n_states, double* sigma_x) {
+  g_last_error.clear();
+  if (!c || !states || n_states < 1 || !sigma_x) return fail(WGW_ERR_ARG, "need a context, states and output");
+  for (int k = 0; k < n_states; ++k)
+    if (states[k] < 0 || states[k] >= c->n_v) return fail(WGW_ERR_ARG, "state index outside 0..n_v-1");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  return sigma_x_impl(c, states, n_states, sigma_x);
 }
 
 int wgw_autotune_info(const wgw_ctx* c, int* tc_split, int* splits, double* ms, int n_max, int* fused_h,
@@ -2789,6 +2828,270 @@ int wgw_isr(wgw_ctx* c, const double* phi, int n_pdep, const int* states, int n_
   LzG0 g{states, n_states, z.data(), 2 * n_omega * n_nodes, nullptr, nullptr, nullptr};
   g.lam = lam; g.weights = weights; g.n_omega = n_omega; g.n_nodes = n_nodes; g.isr = isr;
   return lanczos_impl(c, phi, n_pdep, n_steps, nullptr, 0, nullptr, nullptr, nullptr, st, &g);
+}
+
+// ---------------------------------------------------------------- self-energy at real frequencies
+// chi0bar(z) and Lambda(z) = (1 - chi0bar(z))^-1 chi0bar(z) in the basis at the n_z complex
+// frequencies z_host (interleaved) from kept chi0 chains; device outputs chi and lam, n_z x
+// n_pdep^2 complex each.
+static int lambda_z(wgw_ctx* c, const LzKeep& kc, int npd, int n_steps, const double* z_host, int n_z, DevBuf& chi,
+                    DevBuf& lam) {
+  cudaStream_t st = c->stream;
+  const size_t mat = 2 * (size_t)npd * npd;
+  DevBuf zd, M, info;
+  WGW_TRY(zd.ensure(sizeof(double) * 2 * n_z));
+  WGW_TRY(chi.ensure(sizeof(double) * mat * n_z));
+  WGW_TRY(lam.ensure(sizeof(double) * mat * n_z));
+  WGW_TRY(M.ensure(sizeof(double) * mat * n_z));
+  WGW_TRY(info.ensure(sizeof(int) * n_z));
+  WGW_CK(cudaMemcpyAsync(zd.p, z_host, sizeof(double) * 2 * n_z, cudaMemcpyHostToDevice, st));
+  WGW_CK(launch_chi_z(npd, c->n_v, n_steps, n_z, kc.W.as<double>(), kc.d.as<double>(), c->e_v_d.as<double>(),
+                      zd.as<double>(), c->opt.f_s / c->omega_cell, chi.as<double>(), st));
+  WGW_CK(launch_dyson_z(npd, n_z, chi.as<double>(), lam.as<double>(), M.as<double>(), info.as<int>(), st));
+  std::vector<int> flags(n_z);
+  WGW_CK(cudaMemcpyAsync(flags.data(), info.p, sizeof(int) * n_z, cudaMemcpyDeviceToHost, st));
+  WGW_CK(cudaStreamSynchronize(st));
+  for (int k = 0; k < n_z; ++k)
+    if (flags[k]) return fail(WGW_ERR_ARG, "1 - chi0bar is singular at one of the frequencies");
+  return WGW_OK;
+}
+
+// What the self-energy of a set of states needs, computed once: the chi0 chains of the basis
+// (for Lambda at any frequency), the G0 chains of the states with the overlaps <psi_j|psi_i phi~_m>,
+// Lambda at the quadrature nodes, and Sigma_X.
+struct SigmaCtx {
+  int npd = 0, ns = 0;
+  wgw_sigma_params prm{};
+  LzKeep chi, g0;
+  DevBuf lam_nodes, nodes, wts;
+  std::vector<double> sx;
+};
+
+static int sigma_check(const wgw_ctx* c, const double* phi, int npd, const int* states, int ns,
+                       const wgw_sigma_params* p) {
+  if (!c || !phi || npd < 1 || !states || ns < 1 || !p)
+    return fail(WGW_ERR_ARG, "need a context, phi, n_pdep >= 1, states and parameters");
+  if (p->n_steps_chi < 1 || p->n_steps_chi > 255 || p->n_steps_g0 < 1 || p->n_steps_g0 > 255)
+    return fail(WGW_ERR_ARG, "chain lengths must be within 1..255");
+  if (p->n_nodes < 1 || !p->nodes || !p->weights) return fail(WGW_ERR_ARG, "need quadrature nodes and weights");
+  for (int k = 0; k < p->n_nodes; ++k)
+    if (!(p->nodes[k] >= 0.0) || !std::isfinite(p->nodes[k]) || !std::isfinite(p->weights[k]))
+      return fail(WGW_ERR_ARG, "quadrature nodes must be finite and >= 0, weights finite");
+  if (!(p->eta >= 0.0) || !std::isfinite(p->eta)) return fail(WGW_ERR_ARG, "eta must be finite and >= 0");
+  for (int k = 0; k < ns; ++k)
+    if (states[k] < 0 || states[k] >= c->n_v) return fail(WGW_ERR_ARG, "state index outside 0..n_v-1");
+  for (int v = 0; v < c->n_v; ++v)
+    if (!(c->e_v[v] <= p->e_fermi)) return fail(WGW_ERR_ARG, "e_fermi lies below an occupied energy");
+  return WGW_OK;
+}
+
+static int sigma_prepare(wgw_ctx* c, const double* phi, int npd, const int* states, int ns, const wgw_sigma_params& p,
+                         SigmaCtx& S) {
+  S.npd = npd;
+  S.ns = ns;
+  S.prm = p;
+  WGW_TRY(lanczos_impl(c, phi, npd, p.n_steps_chi, nullptr, 0, nullptr, nullptr, nullptr, nullptr, nullptr, &S.chi));
+  const LzG0 g{states, ns, nullptr, 0, nullptr, nullptr, nullptr};
+  WGW_TRY(lanczos_impl(c, phi, npd, p.n_steps_g0, nullptr, 0, nullptr, nullptr, nullptr, nullptr, &g, &S.g0));
+  std::vector<double> zn(2 * (size_t)p.n_nodes);
+  for (int k = 0; k < p.n_nodes; ++k) zn[2 * k + 1] = p.nodes[k];
+  DevBuf chi;
+  WGW_TRY(lambda_z(c, S.chi, npd, p.n_steps_chi, zn.data(), p.n_nodes, chi, S.lam_nodes));
+  WGW_TRY(S.nodes.ensure(sizeof(double) * p.n_nodes));
+  WGW_TRY(S.wts.ensure(sizeof(double) * p.n_nodes));
+  WGW_CK(cudaMemcpyAsync(S.nodes.p, p.nodes, sizeof(double) * p.n_nodes, cudaMemcpyHostToDevice, c->stream));
+  WGW_CK(cudaMemcpyAsync(S.wts.p, p.weights, sizeof(double) * p.n_nodes, cudaMemcpyHostToDevice, c->stream));
+  S.sx.assign(ns, 0.0);
+  WGW_TRY(sigma_x_impl(c, states, ns, S.sx.data()));
+  WGW_CK(cudaStreamSynchronize(c->stream));
+  return WGW_OK;
+}
+
+// I^SR (real) and R (complex, interleaved) at evaluation points p = (listed state pi[p], real
+// frequency pw[p] <= e_fermi).  R sums, in the order of j, the occupied states above w.
+static int sigma_eval(wgw_ctx* c, SigmaCtx& S, const std::vector<int>& pi, const std::vector<double>& pw,
+                      std::vector<double>& isr, std::vector<double>& res) {
+  cudaStream_t st = c->stream;
+  const int np = (int)pi.size(), npd = S.npd;
+  isr.assign(np, 0.0);
+  res.assign(2 * (size_t)np, 0.0);
+  if (np == 0) return WGW_OK;
+  {
+    DevBuf dpi, dpw, dout;
+    WGW_TRY(dpi.ensure(sizeof(int) * np));
+    WGW_TRY(dpw.ensure(sizeof(double) * np));
+    WGW_TRY(dout.ensure(sizeof(double) * np));
+    WGW_CK(cudaMemcpyAsync(dpi.p, pi.data(), sizeof(int) * np, cudaMemcpyHostToDevice, st));
+    WGW_CK(cudaMemcpyAsync(dpw.p, pw.data(), sizeof(double) * np, cudaMemcpyHostToDevice, st));
+    WGW_CK(launch_isr_points(npd, S.ns, S.prm.n_steps_g0, S.prm.n_nodes, np, S.g0.W.as<double>(), S.g0.d.as<double>(),
+                             dpi.as<int>(), dpw.as<double>(), S.lam_nodes.as<double>(), S.nodes.as<double>(),
+                             S.wts.as<double>(), 1.0 / c->omega_cell, dout.as<double>(), st));
+    WGW_CK(cudaMemcpyAsync(isr.data(), dout.p, sizeof(double) * np, cudaMemcpyDeviceToHost, st));
+    WGW_CK(cudaStreamSynchronize(st));
+  }
+  // Residue term: f = -1 for every occupied j with e_j > w (w <= e_fermi: no empty state enters).
+  std::vector<int> es, ej, ep;
+  std::vector<double> ef, ez;
+  for (int p = 0; p < np; ++p)
+    for (int j = 0; j < c->n_v; ++j)
+      if (c->e_v[j] > pw[p]) {
+        es.push_back(pi[p]); ej.push_back(j); ep.push_back(p); ef.push_back(-1.0);
+        ez.push_back(c->e_v[j] - pw[p]); ez.push_back(S.prm.eta);
+      }
+  const int n_e = (int)es.size(), chunk = 512;
+  DevBuf chi, lam, des, dej, def, dout;
+  for (int e0 = 0; e0 < n_e; e0 += chunk) {
+    const int ne = std::min(chunk, n_e - e0);
+    WGW_TRY(lambda_z(c, S.chi, npd, S.prm.n_steps_chi, ez.data() + 2 * (size_t)e0, ne, chi, lam));
+    WGW_TRY(des.ensure(sizeof(int) * ne));
+    WGW_TRY(dej.ensure(sizeof(int) * ne));
+    WGW_TRY(def.ensure(sizeof(double) * ne));
+    WGW_TRY(dout.ensure(sizeof(double) * 2 * ne));
+    WGW_CK(cudaMemcpyAsync(des.p, es.data() + e0, sizeof(int) * ne, cudaMemcpyHostToDevice, st));
+    WGW_CK(cudaMemcpyAsync(dej.p, ej.data() + e0, sizeof(int) * ne, cudaMemcpyHostToDevice, st));
+    WGW_CK(cudaMemcpyAsync(def.p, ef.data() + e0, sizeof(double) * ne, cudaMemcpyHostToDevice, st));
+    WGW_CK(launch_residue_entries(npd, ne, lam.as<double>(), S.g0.Y.as<double>(), S.g0.ys, des.as<int>(),
+                                  dej.as<int>(), def.as<double>(), dout.as<double>(), st));
+    std::vector<double> h(2 * (size_t)ne);
+    WGW_CK(cudaMemcpyAsync(h.data(), dout.p, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st));
+    WGW_CK(cudaStreamSynchronize(st));
+    for (int e = 0; e < ne; ++e) {
+      res[2 * (size_t)ep[e0 + e]] += h[2 * e] / c->omega_cell;
+      res[2 * (size_t)ep[e0 + e] + 1] += h[2 * e + 1] / c->omega_cell;
+    }
+  }
+  return WGW_OK;
+}
+
+static void sigma_stats(const wgw_ctx* c, const SigmaCtx& S, wgw_stats* st) {
+  if (!st) return;
+  *st = wgw_stats{};
+  st->n_systems = S.npd * (c->n_v + S.ns);   // chains
+  st->n_converged = st->n_systems;
+  st->max_iters = std::max(S.prm.n_steps_chi, S.prm.n_steps_g0);
+}
+
+int wgw_lanczos_z(wgw_ctx* c, const double* phi, int n_pdep, int n_steps, const double* z, int n_z, double* chi0_z,
+                  double* lam_z, wgw_stats* st) {
+  g_last_error.clear();
+  if (!c || !phi || n_pdep < 1 || n_steps < 1 || n_steps > 255 || n_z < 1 || !z)
+    return fail(WGW_ERR_ARG, "need a context, phi, n_pdep >= 1, 1 <= n_steps <= 255 and n_z >= 1 frequencies");
+  for (int k = 0; k < 2 * n_z; ++k)
+    if (!std::isfinite(z[k])) return fail(WGW_ERR_ARG, "frequencies must be finite");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  LzKeep kc;
+  WGW_TRY(lanczos_impl(c, phi, n_pdep, n_steps, nullptr, 0, nullptr, nullptr, nullptr, st, nullptr, &kc));
+  DevBuf chi, lam;
+  const int rc = lambda_z(c, kc, n_pdep, n_steps, z, n_z, chi, lam);
+  if (rc != WGW_OK && rc != WGW_ERR_ARG) return rc;
+  const size_t bytes = sizeof(double) * 2 * (size_t)n_pdep * n_pdep * n_z;
+  if (chi0_z) WGW_CK(cudaMemcpyAsync(chi0_z, chi.p, bytes, cudaMemcpyDeviceToHost, c->stream));
+  if (lam_z && rc == WGW_OK) WGW_CK(cudaMemcpyAsync(lam_z, lam.p, bytes, cudaMemcpyDeviceToHost, c->stream));
+  WGW_CK(cudaStreamSynchronize(c->stream));
+  return rc;
+}
+
+int wgw_sigma(wgw_ctx* c, const double* phi, int n_pdep, const int* states, int n_states,
+              const wgw_sigma_params* prm, const double* omega, int n_omega, double* sigma_x, double* isr,
+              double* res, wgw_stats* st) {
+  g_last_error.clear();
+  WGW_TRY(sigma_check(c, phi, n_pdep, states, n_states, prm));
+  if (n_omega < 0 || (n_omega > 0 && !omega)) return fail(WGW_ERR_ARG, "need n_omega >= 0 frequencies");
+  for (int j = 0; j < n_omega; ++j)
+    if (!std::isfinite(omega[j]) || !(omega[j] <= prm->e_fermi))
+      return fail(WGW_ERR_ARG, "frequencies must be finite and <= e_fermi (the context holds no empty states)");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  SigmaCtx S;
+  WGW_TRY(sigma_prepare(c, phi, n_pdep, states, n_states, *prm, S));
+  if (sigma_x) std::copy(S.sx.begin(), S.sx.end(), sigma_x);
+  std::vector<int> pi;
+  std::vector<double> pw, hi, hr;
+  for (int i = 0; i < n_states; ++i)
+    for (int j = 0; j < n_omega; ++j) { pi.push_back(i); pw.push_back(omega[j]); }
+  WGW_TRY(sigma_eval(c, S, pi, pw, hi, hr));
+  if (isr) std::copy(hi.begin(), hi.end(), isr);
+  if (res) std::copy(hr.begin(), hr.end(), res);
+  sigma_stats(c, S, st);
+  return WGW_OK;
+}
+
+int wgw_qp(wgw_ctx* c, const double* phi, int n_pdep, const int* states, int n_states,
+           const wgw_sigma_params* prm, const double* v_xc, double tol, int max_iter, double* e_qp,
+           double* sigma_qp, int* iters, wgw_stats* st) {
+  g_last_error.clear();
+  WGW_TRY(sigma_check(c, phi, n_pdep, states, n_states, prm));
+  if (!e_qp || !(tol > 0.0) || max_iter < 1) return fail(WGW_ERR_ARG, "need e_qp, tol > 0 and max_iter >= 1");
+  for (int i = 0; i < n_states; ++i)
+    if (!(c->e_v[states[i]] + 0.01 <= prm->e_fermi))
+      return fail(WGW_ERR_ARG, "the secant's second start point e_i + 0.01 lies above e_fermi");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  SigmaCtx S;
+  WGW_TRY(sigma_prepare(c, phi, n_pdep, states, n_states, *prm, S));
+  const int ns = n_states;
+  // Secant per state on F(E) = e_i + Re Sigma_i(E) - v_xc - E from e_i and e_i + 0.01; the
+  // states still iterating are evaluated together.
+  std::vector<double> x0(ns), x1(ns), f0(ns), f1(ns), sig(2 * (size_t)ns, 0.0);
+  std::vector<int> done(ns, 0), it(ns, 0);
+  auto F = [&](const std::vector<int>& who, const std::vector<double>& E, std::vector<double>& out,
+               std::vector<double>& sg) -> int {
+    std::vector<double> hi, hr;
+    WGW_TRY(sigma_eval(c, S, who, E, hi, hr));
+    out.resize(who.size());
+    sg.resize(2 * who.size());
+    for (size_t q = 0; q < who.size(); ++q) {
+      const int i = who[q];
+      const double re = S.sx[i] + hi[q] + hr[2 * q];
+      sg[2 * q] = re;
+      sg[2 * q + 1] = hr[2 * q + 1];
+      out[q] = c->e_v[states[i]] + re - (v_xc ? v_xc[i] : 0.0) - E[q];
+    }
+    return WGW_OK;
+  };
+  {
+    std::vector<int> who;
+    std::vector<double> E, out, sg;
+    for (int i = 0; i < ns; ++i) {
+      x0[i] = c->e_v[states[i]];
+      x1[i] = x0[i] + 0.01;
+      who.push_back(i); E.push_back(x0[i]);
+      who.push_back(i); E.push_back(x1[i]);
+    }
+    WGW_TRY(F(who, E, out, sg));
+    for (int i = 0; i < ns; ++i) { f0[i] = out[2 * i]; f1[i] = out[2 * i + 1]; }
+  }
+  int status = WGW_OK;
+  for (int step = 0; step < max_iter; ++step) {
+    std::vector<int> who;
+    std::vector<double> E, out, sg;
+    for (int i = 0; i < ns; ++i) {
+      if (done[i]) continue;
+      if (f1[i] == f0[i]) { done[i] = -1; continue; }   // stalled
+      const double x2 = x1[i] - f1[i] * (x1[i] - x0[i]) / (f1[i] - f0[i]);
+      if (!std::isfinite(x2) || !(x2 <= prm->e_fermi))
+        return fail(WGW_ERR_ARG, "a secant iterate rose above e_fermi (the context holds no empty states)");
+      who.push_back(i);
+      E.push_back(x2);
+    }
+    if (who.empty()) break;
+    WGW_TRY(F(who, E, out, sg));
+    for (size_t q = 0; q < who.size(); ++q) {
+      const int i = who[q];
+      x0[i] = x1[i]; f0[i] = f1[i];
+      x1[i] = E[q]; f1[i] = out[q];
+      sig[2 * i] = sg[2 * q];
+      sig[2 * i + 1] = sg[2 * q + 1];
+      ++it[i];
+      if (std::fabs(x1[i] - x0[i]) <= tol * std::max(1.0, std::fabs(x1[i]))) done[i] = 1;
+    }
+  }
+  for (int i = 0; i < ns; ++i) {
+    e_qp[i] = x1[i];
+    if (sigma_qp) { sigma_qp[2 * i] = sig[2 * i]; sigma_qp[2 * i + 1] = sig[2 * i + 1]; }
+    if (iters) iters[i] = it[i];
+    if (done[i] != 1) status = WGW_ERR_NOCONV;
+  }
+  sigma_stats(c, S, st);
+  return status == WGW_OK ? WGW_OK : fail(status, "the secant did not converge for some states");
 }
 
 int wgw_symm_eig_dev(int n, double* A_dev, double* w_dev, double* Z_dev, void* stream) {

@@ -41,6 +41,11 @@ class Options(ctypes.Structure):
                 ("tc_split", ctypes.c_int)]
 
 
+class SigmaParams(ctypes.Structure):
+    _fields_ = [("n_steps_chi", ctypes.c_int), ("n_steps_g0", ctypes.c_int), ("nodes", _dp), ("weights", _dp),
+                ("n_nodes", ctypes.c_int), ("e_fermi", ctypes.c_double), ("eta", ctypes.c_double)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("n_systems", ctypes.c_int), ("n_converged", ctypes.c_int),
                 ("max_iters", ctypes.c_int), ("refinements", ctypes.c_int),
@@ -116,6 +121,13 @@ def lib(path: str | None = None):
     L.wgw_isr.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
                           _dp, ctypes.c_int, _dp, _dp, _dp, ctypes.c_int, _dp, ctypes.POINTER(Stats)]
     L.wgw_sigma_x.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int, _dp]
+    L.wgw_lanczos_z.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _dp, _dp,
+                                ctypes.POINTER(Stats)]
+    L.wgw_sigma.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                            ctypes.POINTER(SigmaParams), _dp, ctypes.c_int, _dp, _dp, _dp, ctypes.POINTER(Stats)]
+    L.wgw_qp.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                         ctypes.POINTER(SigmaParams), _dp, ctypes.c_double, ctypes.c_int, _dp, _dp,
+                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Stats)]
     L.wgw_autotune_info.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                     _dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp]
     L.wgw_selftest_wait_timeout.argtypes = [ctypes.POINTER(ctypes.c_int)]
@@ -283,6 +295,75 @@ def wgw_isr(ctx: Context, phi, states, n_steps: int, omega, lam, nodes, weights)
                          nd.ctypes.data_as(_dp), wt.ctypes.data_as(_dp), nd.size,
                          out.view(np.float64).ctypes.data_as(_dp), ctypes.byref(st)), "wgw_isr")
     return out
+
+
+def wgw_lanczos_z(ctx: Context, phi, n_steps: int, z):
+    """chi0bar and Lambda = (1 - chi0bar)^-1 chi0bar in the basis phi at complex frequencies z, from
+    Lanczos chains of n_steps; returns (chi0 (n_z, n_pdep, n_pdep), lam (same)), element [k, m, n]."""
+    phi = np.asarray(phi, np.complex128)
+    npd = phi.shape[1]
+    zz = np.ascontiguousarray(np.asarray(z, np.complex128).ravel())
+    chi = np.zeros((zz.size, npd, npd), np.complex128)
+    lam = np.zeros((zz.size, npd, npd), np.complex128)
+    pb = _interleave(phi)
+    st = Stats()
+    _check(lib().wgw_lanczos_z(ctx.handle, pb.ctypes.data_as(_dp), npd, n_steps, zz.view(np.float64).ctypes.data_as(_dp),
+                               zz.size, chi.view(np.float64).ctypes.data_as(_dp),
+                               lam.view(np.float64).ctypes.data_as(_dp), ctypes.byref(st)), "wgw_lanczos_z")
+    return chi, lam
+
+
+def _sigma_params(n_steps_chi, n_steps_g0, nodes, weights, e_fermi, eta):
+    nd = np.ascontiguousarray(nodes, np.float64)
+    wt = np.ascontiguousarray(weights, np.float64)
+    assert wt.size == nd.size
+    p = SigmaParams(int(n_steps_chi), int(n_steps_g0), nd.ctypes.data_as(_dp), wt.ctypes.data_as(_dp), nd.size,
+                    float(e_fermi), float(eta))
+    return p, (nd, wt)
+
+
+def wgw_sigma(ctx: Context, phi, states, omega, *, n_steps_chi: int, n_steps_g0: int, nodes, weights,
+              e_fermi: float, eta: float):
+    """Sigma_X, I^SR(w) and R(w) of the listed occupied states at real frequencies w <= e_fermi;
+    returns (sigma_x (n_states), isr (n_states, n_omega) real, res (n_states, n_omega) complex)."""
+    phi = np.asarray(phi, np.complex128)
+    npd = phi.shape[1]
+    sts = np.ascontiguousarray(states, np.int32)
+    om = np.ascontiguousarray(omega, np.float64)
+    p, keep = _sigma_params(n_steps_chi, n_steps_g0, nodes, weights, e_fermi, eta)
+    sx = np.zeros(sts.size)
+    isr = np.zeros((sts.size, om.size))
+    res = np.zeros((sts.size, om.size), np.complex128)
+    pb = _interleave(phi)
+    st = Stats()
+    _check(lib().wgw_sigma(ctx.handle, pb.ctypes.data_as(_dp), npd, sts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                           sts.size, ctypes.byref(p), om.ctypes.data_as(_dp), om.size, sx.ctypes.data_as(_dp),
+                           isr.ctypes.data_as(_dp), res.view(np.float64).ctypes.data_as(_dp), ctypes.byref(st)),
+           "wgw_sigma")
+    del keep
+    return sx, isr, res
+
+
+def wgw_qp(ctx: Context, phi, states, *, n_steps_chi: int, n_steps_g0: int, nodes, weights, e_fermi: float,
+           eta: float, v_xc=None, tol: float = 1e-10, max_iter: int = 100):
+    """Quasiparticle energies of the listed occupied states (Eq. e_qp) by the secant method;
+    returns (e_qp (n_states), sigma at e_qp (n_states) complex, secant steps (n_states))."""
+    phi = np.asarray(phi, np.complex128)
+    npd = phi.shape[1]
+    sts = np.ascontiguousarray(states, np.int32)
+    p, keep = _sigma_params(n_steps_chi, n_steps_g0, nodes, weights, e_fermi, eta)
+    vx = None if v_xc is None else np.ascontiguousarray(v_xc, np.float64)
+    eq = np.zeros(sts.size)
+    sg = np.zeros(sts.size, np.complex128)
+    it = np.zeros(sts.size, np.int32)
+    pb = _interleave(phi)
+    st = Stats()
+    _check(lib().wgw_qp(ctx.handle, pb.ctypes.data_as(_dp), npd, sts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                        sts.size, ctypes.byref(p), vx.ctypes.data_as(_dp) if vx is not None else None, tol, max_iter,
+                        eq.ctypes.data_as(_dp), sg.view(np.float64).ctypes.data_as(_dp),
+                        it.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ctypes.byref(st)), "wgw_qp")
+    del keep
+    return eq, sg, it
 
 
 def wgw_sigma_x(ctx: Context, states) -> np.ndarray:
