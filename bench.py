@@ -553,6 +553,51 @@ def run_serve_mixed(args, wl):
         W.wgw_destroy(c)
 
 
+def served_stream(W, ctx, s, phi, capacity, window_s=8.0, load=0.7, seed=11):
+    """Served chibar0 requests on the context of the main line: Poisson arrivals (seed) at `load`
+    of the closed-loop capacity (systems/s) for window_s seconds, each request 4-64 perturbations
+    drawn from phi's columns, submitted through wgw_submit and collected with wgw_wait; latency =
+    submission -> result in host memory (measured by the library).  The first request is solved
+    again alone and compared with its served result."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    n_pool = phi.shape[1]
+    sizes = rng.integers(4, min(64, n_pool) + 1, size=100000)
+    rate = load * capacity / (float(np.mean(sizes)) * s.n_v)          # requests/s
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=100000))
+    n_req = max(2, int(np.searchsorted(arrivals, window_s)))
+    cols = [np.sort(rng.choice(n_pool, size=int(sizes[k]), replace=False)) for k in range(n_req)]
+    tickets, t_start = [], time.perf_counter()
+    for k in range(n_req):
+        dt = arrivals[k] - (time.perf_counter() - t_start)
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(W.wgw_submit(ctx, phi[:, cols[k]], [0.0], kind=W.WGW_REQ_CHIBAR0))
+    lat, solved, merged, first = [], 0, [], None
+    for k, t in enumerate(tickets):
+        out, res = W.wgw_wait(t)
+        if res["status"] != W.WGW_OK:
+            raise RuntimeError(f"served request failed with status {res['status']}: {res.get('error')}")
+        lat.append(res["latency_s"])
+        merged.append(res["batch_requests"])
+        solved += len(cols[k]) * s.n_v
+        if k == 0:
+            first = out
+    span = time.perf_counter() - t_start
+    alone, _, _ = W.wgw_apply_chibar0(ctx, phi[:, cols[0]])
+    num = np.linalg.norm((first - alone).reshape(first.shape[0], -1), axis=0)
+    den = np.linalg.norm(alone.reshape(alone.shape[0], -1), axis=0)
+    lat = np.asarray(lat)
+    return {"requests": n_req, "offered_load": load, "offered_systems_per_s": load * capacity,
+            "served_systems_per_s": solved / span, "arrival_window_s": window_s, "span_s": span,
+            "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99))},
+            "mean_requests_per_batch": float(np.mean(merged)),
+            "served_vs_alone_rel_diff": float(np.max(num / den)),
+            "what": "chibar0 requests of 4-64 perturbations of the same model, Poisson arrivals at the offered "
+                    "load through wgw_submit / wgw_wait, continuously batched; latency = submission -> result "
+                    "in host memory"}
+
+
 def library_baselines(W, ctx, s, prof_all):
     """The library's FP32 kernels against cuFFT and cuBLAS on the same shapes (untimed by the
     bench line; CUDA events around each variant, after warm-up).
@@ -749,6 +794,8 @@ def main():
                     help="skip the all-FP64 GPU path measured beside the mixed one")
     ap.add_argument("--no-library-baselines", action="store_true",
                     help="skip the cuFFT / cuBLAS comparison on the same shapes")
+    ap.add_argument("--no-served", action="store_true",
+                    help="skip the served-request stream on the main line's model")
     ap.add_argument("--n-pert", type=int, default=0,
                     help="perturbations per rank (default: the workload's); smaller values serve profiling")
     ap.add_argument("--fp64-emulation", type=int, default=1, choices=[0, 1],
@@ -943,6 +990,12 @@ def main():
         line["fp64_path"] = fp64_path(W, s, wl, x, out, stream, ph, oh, min(args.steps, 3))
     if world == 1 and args.precision == "mixed" and not args.no_library_baselines:
         line["library_baseline"] = library_baselines(W, ctx, s, prof_all)
+    if world == 1 and args.precision == "mixed" and args.workload == "pdep_L16_48" and not args.no_served:
+        served = served_stream(W, ctx, s, phi, value)
+        line["served"] = served
+        line["latency_ms"] = dict(served["latency_ms"], what="served chibar0 requests (the served object)")
+        line["block_apply_ms"] = {"p50": 1e3 * statistics.median(times),
+                                  "what": "one 64-perturbation block apply, device time"}
     W.wgw_destroy(ctx)
     if world == 1 and args.precision == "mixed" and args.workload == "pdep_L16_48" and not args.no_largest:
         line["largest_config"] = largest_config(W, stream, hbm, peak_kind)
