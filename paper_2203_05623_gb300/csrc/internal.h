@@ -241,6 +241,9 @@ cudaError_t launch_copy_cast(int n_sys, int n, const Ti* in, long ldi, To* out, 
 template <typename T>
 cudaError_t launch_add_to(int n_sys, int n, const T* x, long ldx, double* y, long ldy,
                           const int* active, cudaStream_t st);
+// y[s] += p[s] - t[s] for active systems (FP32 inputs, FP64 difference and sum).
+cudaError_t launch_add_diff(int n_sys, int n, const float* p, const float* t, long ldx, double* y, long ldy,
+                            const int* active, cudaStream_t st);
 // Per-system norms ||x_s||^2 into out[s].
 template <typename T>
 cudaError_t launch_norm2(int n_sys, int n, const T* x, long ld, double* out, cudaStream_t st);

@@ -118,6 +118,18 @@ __global__ void k_add_to(int n_sys, int n, const T* x, long ldx, double* y, long
   }
 }
 
+// y[s] += p[s] - t[s] (FP32 inputs, difference and sum in FP64), active systems only.
+__global__ void k_add_diff(int n_sys, int n, const float* p, const float* t, long ldx, double* y, long ldy,
+                           const int* active) {
+  for (int s = blockIdx.y; s < n_sys; s += gridDim.y) {
+    if (active && !active[s]) continue;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      const size_t q = (size_t)s * ldx + i;
+      y[(size_t)s * ldy + i] += double(p[q]) - double(t[q]);
+    }
+  }
+}
+
 template <typename T>
 __global__ void k_norm2(int n, const T* x, long ld, double* out) {
   __shared__ double red[33];
@@ -932,6 +944,13 @@ cudaError_t launch_add_to(int n_sys, int n, const T* x, long ldx, double* y, lon
                           const int* active, cudaStream_t st) {
   if (n_sys == 0) return cudaSuccess;
   k_add_to<T><<<grid_el(n, n_sys), 256, 0, st>>>(n_sys, n, x, ldx, y, ldy, active);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_diff(int n_sys, int n, const float* p, const float* t, long ldx, double* y, long ldy,
+                            const int* active, cudaStream_t st) {
+  if (n_sys == 0) return cudaSuccess;
+  k_add_diff<<<grid_el(n, n_sys), 256, 0, st>>>(n_sys, n, p, t, ldx, y, ldy, active);
   return cudaGetLastError();
 }
 

@@ -788,6 +788,9 @@ __global__ void k_residual_flags(int n_sys, const double* rr, const double* bb, 
   if (s < n_sys) act[s] = (bb[s] > 0.0 && rr[s] > tol2 * bb[s]) ? 1 : 0;
 }
 
+// The residual of each refinement is projected with the FP32 tensor-core P_c (see solve_all).
+constexpr bool kRefineResidualFp32Pc = true;
+
 // Solve all systems to cg_tol.  Right-hand sides in d.Bv; solutions into d.X.
 int solve_all(wgw_ctx* c, int n_sys, cudaStream_t st, wgw_stats* stats) {
   const int n = c->wfc.nrb();
@@ -835,8 +838,30 @@ int solve_all(wgw_ctx* c, int n_sys, cudaStream_t st, wgw_stats* stats) {
       // O(eps_32) component along the occupied states; P_c (H - e_v) maps it to zero (the
       // occupied states are eigenvectors of H), so the residual does not see it and it is
       // projected out once, after the last refinement.
-      WGW_TRY(apply_A<double>(c, c->d, X, Q, na, l64, act64, st));
+      //
+      // P_c of the residual: (H - e_v) x is formed at FP64 accuracy and left unprojected;
+      // r = b - (H - e_v) x then differs from P_c r only by o = P_v (H - e_v) x, small with
+      // the occupied component of x (FP32 rounding of the corrections).  That component is
+      // removed with the FP32 tensor-core projector applied twice to the FP32 image t of r:
+      //   r += P_c(P_c(t)) - t.
+      // One FP32 pass leaves an occupied error of about eps |t| ~ eps |o| (the overlaps are
+      // formed from all of t), which the inner solves cannot reduce and which stalled the
+      // refinement above cg_tol = 1e-11 with 256 occupied states; the second pass takes it to
+      // eps^2 |o|.  What remains is the FP32 rounding of the subtraction, eps_32 |o|, far below
+      // cg_tol |b|.  The FP64-accuracy projector stays on the right-hand sides and the final x.
+      WGW_TRY(apply_A<double>(c, c->d, X, Q, na, l64, act64, st, !kRefineResidualFp32Pc));
       WGW_CK(c->prof.run(PK_CONV, 24.0 * n_sys * n, 0, st, [&] { return launch_axpby(n_sys, n, 1.0, Bv, -1.0, Q, R, ld, act64, st); }));
+      if (kRefineResidualFp32Pc) {
+        float* t32 = c->f.Bv.as<float>();
+        float* p32 = c->f.X.as<float>();
+        WGW_CK(c->prof.run(PK_CONV, 24.0 * na * n, 0, st, [&] {
+          cudaError_t e = launch_copy_cast<double, float>(n_sys, n, R, ld, t32, ld, act64, st);
+          if (e == cudaSuccess) e = launch_copy_cast<double, float>(n_sys, n, R, ld, p32, ld, act64, st);
+          return e; }));
+        for (int pass = 0; pass < 2; ++pass) WGW_TRY(run_pc<float>(c, p32, na, l64, c->f.psi.as<float>(), act64, st));
+        WGW_CK(c->prof.run(PK_CONV, 24.0 * na * n, 0, st, [&] {
+          return launch_add_diff(n_sys, n, p32, t32, ld, R, ld, act64, st); }));
+      }
     }
     // The solution lies in range(P_c): remove the occupied component in FP64.
     WGW_TRY(run_pc<double>(c, X, n_sys, nullptr, c->d.psi.as<double>(), nullptr, st));
