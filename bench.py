@@ -18,6 +18,7 @@ times the FP64 CPU oracle on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -808,6 +809,12 @@ def main():
                     help="P_c of the FP32 solves on the tcgen05 tensor cores (default: the library's)")
     ap.add_argument("--cuda-graphs", type=int, default=None, choices=[0, 1, 2],
                     help="CG launch mode: 2 device-driven loop, 1 a graph per window, 0 direct (default: 2)")
+    ap.add_argument("--fft-kernels", default=None,
+                    help="FP32 FFT stage kernels G->r,x-line,r->G as three of 0 register, 1 register packed, "
+                         "2 shared memory (default: autotuned); fixed choices keep a profiler's replays from "
+                         "steering the autotuner")
+    ap.add_argument("--tc-split", type=int, default=None,
+                    help="tensor-core projector K split (default: autotuned)")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.n_pert > 0:
@@ -862,6 +869,10 @@ def main():
         opt.fused_h = args.fused_h
     if args.cuda_graphs is not None:
         opt.cuda_graphs = args.cuda_graphs
+    if args.fft_kernels is not None:
+        opt.fft_kernels = (ctypes.c_int * 3)(*[int(v) for v in args.fft_kernels.split(",")])
+    if args.tc_split is not None:
+        opt.tc_split = args.tc_split
     kb = s.beta_G.shape[1] > 0
     ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, opt,
                       beta_G=s.beta_G if kb else None, d_proj=s.d_proj if kb else None)
@@ -986,6 +997,7 @@ def main():
     if cpu:
         line["cpu_baseline"] = cpu
     line["autotune"] = W.wgw_autotune_info(ctx)
+    line["autotune"]["fft"] = W.wgw_autotune_fft(ctx)
     if world == 1 and args.precision == "mixed" and not args.no_fp64_path and args.workload == "pdep_L16_48":
         line["fp64_path"] = fp64_path(W, s, wl, x, out, stream, ph, oh, min(args.steps, 3))
     if world == 1 and args.precision == "mixed" and not args.no_library_baselines:

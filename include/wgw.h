@@ -103,7 +103,20 @@ typedef struct wgw_options {
                              projector and KB products is cut for, 1..16; 0 = picked by the autotuner on
                              the context's first large projection (the default).  A fixed split gives
                              bit-identical results from run to run. */
+  int fft_kernels[3];     /* MIXED: the kernel of each FP32 FFT stage of the H application (G -> r planes,
+                             x-lines with V(r), r -> G planes) on the grids with register-resident kernels
+                             (24, 32, 48, 64): WGW_FFT_REG (one line per thread in registers), WGW_FFT_REG_PACKED
+                             (the same with packed FP32 butterflies), WGW_FFT_SHARED (lines in shared
+                             memory), or WGW_FFT_AUTO (the default: every candidate of the stage is timed on
+                             the context's first application to >= 256 systems and the fastest kept;
+                             wgw_autotune_fft reports the choice).  The same transforms: results agree to
+                             FP32 rounding, and a fixed choice is bit-identical from run to run. */
 } wgw_options;
+
+#define WGW_FFT_AUTO (-1)
+#define WGW_FFT_REG 0
+#define WGW_FFT_REG_PACKED 1
+#define WGW_FFT_SHARED 2
 
 typedef struct wgw_stats {
   int n_systems;            /* real Sternheimer systems solved (states x real perturbation parts) */
@@ -115,7 +128,8 @@ typedef struct wgw_stats {
 
 /* Fills *opt with defaults: WGW_FP64, cg_tol 1e-12, max_cg_iter 2000, max_refine 8,
  * inner_tol 5e-6, f_s 2, check_every 8, dav_tol 1e-8, dav_max_iter 100, dav_factor 4, seed 12345,
- * fp64_emulation 1, tensor_cores 1, cuda_graphs 2, max_batch_systems 0, fused_h 2, tc_split 0. */
+ * fp64_emulation 1, tensor_cores 1, cuda_graphs 2, max_batch_systems 0, fused_h 2, tc_split 0,
+ * fft_kernels WGW_FFT_AUTO x 3. */
 int wgw_default_options(wgw_options* opt);
 
 /*
@@ -382,6 +396,16 @@ int wgw_sigma_x(wgw_ctx* ctx, const int* states, int n_states, double* sigma_x);
  */
 int wgw_autotune_info(const wgw_ctx* ctx, int* tc_split, int* splits, double* ms, int n_max, int* fused_h,
                       double* h_ms);
+
+/*
+ * FFT autotuner record of a context (the choice of fft_kernels, Sec. 4.1's FFTs): choice[s] = the
+ * kernel of stage s (0: G -> r planes, 1: x-lines, 2: r -> G planes) in effect for the FP32 H
+ * application, WGW_FFT_REG / WGW_FFT_REG_PACKED / WGW_FFT_SHARED, or WGW_FFT_AUTO while it has not
+ * been tuned yet; ms[3 s + k] = the median time [ms] of candidate k of stage s on the context's first
+ * large list (0 when not timed: a fixed option, a grid without register-resident kernels, or not
+ * tuned yet).  Either output may be NULL.  Returns WGW_ERR_ARG for a null context.
+ */
+int wgw_autotune_fft(const wgw_ctx* ctx, int* choice, double* ms);
 
 /*
  * Failure-detection self-test (no counterpart in the paper).  Every wait of the library's

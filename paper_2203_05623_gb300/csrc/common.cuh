@@ -147,6 +147,50 @@ WGW_HD cplx<T> mul_i(cplx<T> a, int sign) {
   return sign > 0 ? mk<T>(-a.im, a.re) : mk<T>(a.im, -a.re);
 }
 
+// Complex sum, difference and real scaling with a packing choice P: P = false is the scalar
+// form; P = true on FP32 values computes each as one f32x2 instruction (sm_100 and later) instead
+// of two scalar ones, with the same round-to-nearest result per component.  The FFT butterflies
+// are mostly such operations; kernels pick P where it measured faster.
+#ifndef WGW_F32X2
+#define WGW_F32X2 1
+#endif
+template <bool P, typename T>
+WGW_HD cplx<T> cadd(cplx<T> a, cplx<T> b) { return a + b; }
+template <bool P, typename T>
+WGW_HD cplx<T> csub(cplx<T> a, cplx<T> b) { return a - b; }
+template <bool P, typename T>
+WGW_HD cplx<T> cscl(cplx<T> a, T s) { return cscale(a, s); }
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000) && WGW_F32X2
+__device__ __forceinline__ unsigned long long pk_f32x2(float x, float y) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+  return r;
+}
+__device__ __forceinline__ cplx<float> upk_f32x2(unsigned long long r) {
+  cplx<float> c;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(c.re), "=f"(c.im) : "l"(r));
+  return c;
+}
+template <>
+__device__ __forceinline__ cplx<float> cadd<true, float>(cplx<float> a, cplx<float> b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk_f32x2(a.re, a.im)), "l"(pk_f32x2(b.re, b.im)));
+  return upk_f32x2(r);
+}
+template <>
+__device__ __forceinline__ cplx<float> csub<true, float>(cplx<float> a, cplx<float> b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk_f32x2(a.re, a.im)), "l"(pk_f32x2(b.re, b.im)));
+  return upk_f32x2(r);
+}
+template <>
+__device__ __forceinline__ cplx<float> cscl<true, float>(cplx<float> a, float s) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk_f32x2(a.re, a.im)), "l"(pk_f32x2(s, s)));
+  return upk_f32x2(r);
+}
+#endif
+
 // Thread context of a kernel body.
 struct Thr {
   int tid;       // thread index within the block

@@ -14,63 +14,66 @@
 // line-fastest so that neighbouring threads touch neighbouring lines.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace wgw {
 
 // Radix-R DFT of v[0..R-1] in registers, X_k = sum_j v_j exp(sign 2 pi i j k / R), natural order.
-template <typename T>
+// P: packed FP32 sums (cadd / csub / cscl of common.cuh).
+template <typename T, bool P = false>
 WGW_HD void dft2(cplx<T>* v) {
-  cplx<T> a = v[0] + v[1], b = v[0] - v[1];
+  cplx<T> a = cadd<P>(v[0], v[1]), b = csub<P>(v[0], v[1]);
   v[0] = a; v[1] = b;
 }
 
-template <typename T>
+template <typename T, bool P = false>
 WGW_HD void dft3(cplx<T>* v, int sign) {
   const T h = T(0.86602540378443864676);  // sin(2 pi / 3)
-  cplx<T> t = v[1] + v[2];
-  cplx<T> u = v[0] - cscale(t, T(0.5));
-  cplx<T> w = mul_i(cscale(v[1] - v[2], h), sign);
-  v[0] = v[0] + t;
-  v[1] = u + w;
-  v[2] = u - w;
+  cplx<T> t = cadd<P>(v[1], v[2]);
+  cplx<T> u = csub<P>(v[0], cscl<P>(t, T(0.5)));
+  cplx<T> w = mul_i(cscl<P>(csub<P>(v[1], v[2]), h), sign);
+  v[0] = cadd<P>(v[0], t);
+  v[1] = cadd<P>(u, w);
+  v[2] = csub<P>(u, w);
 }
 
-template <typename T>
+template <typename T, bool P = false>
 WGW_HD void dft4(cplx<T>* v, int sign) {
-  cplx<T> a = v[0] + v[2], b = v[0] - v[2];
-  cplx<T> c = v[1] + v[3], d = mul_i(v[1] - v[3], sign);
-  v[0] = a + c; v[2] = a - c;
-  v[1] = b + d; v[3] = b - d;
+  cplx<T> a = cadd<P>(v[0], v[2]), b = csub<P>(v[0], v[2]);
+  cplx<T> c = cadd<P>(v[1], v[3]), d = mul_i(csub<P>(v[1], v[3]), sign);
+  v[0] = cadd<P>(a, c); v[2] = csub<P>(a, c);
+  v[1] = cadd<P>(b, d); v[3] = csub<P>(b, d);
 }
 
-template <typename T>
+template <typename T, bool P = false>
 WGW_HD void dft5(cplx<T>* v, int sign) {
   const T c1 = T(0.30901699437494742410), c2 = T(-0.80901699437494742410);  // cos(2pi/5), cos(4pi/5)
   const T s1 = T(0.95105651629515357212), s2 = T(0.58778525229247312917);   // sin(2pi/5), sin(4pi/5)
-  cplx<T> a1 = v[1] + v[4], b1 = v[1] - v[4];
-  cplx<T> a2 = v[2] + v[3], b2 = v[2] - v[3];
-  cplx<T> u1 = v[0] + cscale(a1, c1) + cscale(a2, c2);
-  cplx<T> u2 = v[0] + cscale(a1, c2) + cscale(a2, c1);
-  cplx<T> w1 = mul_i(cscale(b1, s1) + cscale(b2, s2), sign);
-  cplx<T> w2 = mul_i(cscale(b1, s2) - cscale(b2, s1), sign);
-  v[0] = v[0] + a1 + a2;
-  v[1] = u1 + w1; v[4] = u1 - w1;
-  v[2] = u2 + w2; v[3] = u2 - w2;
+  cplx<T> a1 = cadd<P>(v[1], v[4]), b1 = csub<P>(v[1], v[4]);
+  cplx<T> a2 = cadd<P>(v[2], v[3]), b2 = csub<P>(v[2], v[3]);
+  cplx<T> u1 = cadd<P>(cadd<P>(v[0], cscl<P>(a1, c1)), cscl<P>(a2, c2));
+  cplx<T> u2 = cadd<P>(cadd<P>(v[0], cscl<P>(a1, c2)), cscl<P>(a2, c1));
+  cplx<T> w1 = mul_i(cadd<P>(cscl<P>(b1, s1), cscl<P>(b2, s2)), sign);
+  cplx<T> w2 = mul_i(csub<P>(cscl<P>(b1, s2), cscl<P>(b2, s1)), sign);
+  v[0] = cadd<P>(cadd<P>(v[0], a1), a2);
+  v[1] = cadd<P>(u1, w1); v[4] = csub<P>(u1, w1);
+  v[2] = cadd<P>(u2, w2); v[3] = csub<P>(u2, w2);
 }
 
-template <typename T>
+template <typename T, bool P = false>
 WGW_HD void dft8(cplx<T>* v, int sign) {
   const T r = T(0.70710678118654752440);  // 1/sqrt(2)
   cplx<T> a[4], b[4];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) { a[j] = v[j] + v[j + 4]; b[j] = v[j] - v[j + 4]; }
+  for (int j = 0; j < 4; ++j) { a[j] = cadd<P>(v[j], v[j + 4]); b[j] = csub<P>(v[j], v[j + 4]); }
   // b_j *= exp(sign i pi j / 4):  exp(sign i pi / 4) = (1 + sign i) r,  exp(sign 3 i pi / 4) = (-1 + sign i) r
-  b[1] = cscale(b[1] + mul_i(b[1], sign), r);
+  b[1] = cscl<P>(cadd<P>(b[1], mul_i(b[1], sign)), r);
   b[2] = mul_i(b[2], sign);
-  b[3] = cscale(mul_i(b[3], sign) - b[3], r);
-  dft4(a, sign);
-  dft4(b, sign);
+  b[3] = cscl<P>(csub<P>(mul_i(b[3], sign), b[3]), r);
+  dft4<T, P>(a, sign);
+  dft4<T, P>(b, sign);
 #pragma unroll
   for (int k = 0; k < 4; ++k) { v[2 * k] = a[k]; v[2 * k + 1] = b[k]; }
 }
@@ -98,13 +101,13 @@ WGW_HD cplx<T> twiddle(const cplx<T>* tw, int k, int sign) {
 // N-hi..N-1 of a block (the footprint of a sphere of radius lo = hi = m).
 WGW_HD int split_line(int li, int m, int n) { return li <= m ? li : li + n - 2 * m - 1; }
 
-template <typename T, int R>
+template <typename T, int R, bool P = false>
 WGW_HD void dft_fixed(cplx<T>* v, int sign) {
-  if constexpr (R == 2) dft2(v);
-  else if constexpr (R == 3) dft3(v, sign);
-  else if constexpr (R == 4) dft4(v, sign);
-  else if constexpr (R == 5) dft5(v, sign);
-  else dft8(v, sign);
+  if constexpr (R == 2) dft2<T, P>(v);
+  else if constexpr (R == 3) dft3<T, P>(v, sign);
+  else if constexpr (R == 4) dft4<T, P>(v, sign);
+  else if constexpr (R == 5) dft5<T, P>(v, sign);
+  else dft8<T, P>(v, sign);
 }
 
 // One DIF stage of radix R over all lines (block size S, butterfly span M = S/R).
@@ -314,7 +317,7 @@ WGW_HD void fft_dit_n(cplx<T>* buf, const FftPlan& p, const cplx<T>* tw, int sig
 // One line of compile-time length N held by one thread (v[0..N-1], kept in registers once the
 // loops are unrolled): the same stages as dif_stages_c / dit_stages_c, so the same
 // digit-reversed positions, with every index and twiddle index a compile-time constant.
-template <typename T, int N, int ST, int SIGN>
+template <typename T, int N, int ST, int SIGN, bool PK = false>
 WGW_HD void reg_dif(cplx<T>* v, const cplx<T>* tw) {
   constexpr CPlan P = cplan(N);
   if constexpr (ST < P.nst) {
@@ -326,7 +329,7 @@ WGW_HD void reg_dif(cplx<T>* v, const cplx<T>* tw) {
         cplx<T> u[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) u[r] = v[blk * S + j2 + r * M];
-        dft_fixed<T, R>(u, SIGN);
+        dft_fixed<T, R, PK>(u, SIGN);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           cplx<T> x = u[r];
@@ -335,11 +338,11 @@ WGW_HD void reg_dif(cplx<T>* v, const cplx<T>* tw) {
         }
       }
     }
-    reg_dif<T, N, ST + 1, SIGN>(v, tw);
+    reg_dif<T, N, ST + 1, SIGN, PK>(v, tw);
   }
 }
 
-template <typename T, int N, int ST, int SIGN>
+template <typename T, int N, int ST, int SIGN, bool PK = false>
 WGW_HD void reg_dit(cplx<T>* v, const cplx<T>* tw) {
   constexpr CPlan P = cplan(N);
   if constexpr (ST >= 0) {
@@ -355,12 +358,12 @@ WGW_HD void reg_dit(cplx<T>* v, const cplx<T>* tw) {
           if (r > 0 && j2 > 0) x = cmul(x, twiddle(tw, step * j2 * r, SIGN));
           u[r] = x;
         }
-        dft_fixed<T, R>(u, SIGN);
+        dft_fixed<T, R, PK>(u, SIGN);
 #pragma unroll
         for (int r = 0; r < R; ++r) v[blk * S + j2 + r * M] = u[r];
       }
     }
-    reg_dit<T, N, ST - 1, SIGN>(v, tw);
+    reg_dit<T, N, ST - 1, SIGN, PK>(v, tw);
   }
 }
 

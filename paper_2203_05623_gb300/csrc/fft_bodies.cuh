@@ -25,6 +25,8 @@
 // only where global T arrays are read or written.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "fft.cuh"
 
@@ -106,7 +108,9 @@ WGW_HD void plane_g2r_body(int pair, int hi, const SphereTab& sp, const FftPlan&
 // column per thread, written straight to T[hi][y][z].  Several planes per block keep the
 // threads busy in both phases (2m+1 rows, N columns per plane).
 // smem B: np x (2m+1) x (N+1) complex, row kr = k + m of plane p at (p (2m+1) + kr) (N+1).
-template <typename T, int N, typename C>
+
+// PK: packed FP32 butterflies (cadd / csub / cscl of common.cuh) in the line transforms.
+template <typename T, int N, typename C, bool PK = false>
 WGW_HD void plane_g2r_reg_body(int pair, int hi0, int np, const SphereTab& sp, const cplx<C>* tw, const T* X,
                                long ldx, int n_list, const int* list, cplx<C>* Tout, cplx<C>* B, Thr th) {
   const int m = sp.m, NR = 2 * m + 1, LS = N + 1;
@@ -142,7 +146,7 @@ WGW_HD void plane_g2r_reg_body(int pair, int hi0, int np, const SphereTab& sp, c
     cplx<C> v[N];
 #pragma unroll
     for (int x = 0; x < N; ++x) v[x] = row[x];
-    reg_dif<C, N, 0, +1>(v, tw);
+    reg_dif<C, N, 0, +1, PK>(v, tw);
 #pragma unroll
     for (int x = 0; x < N; ++x) row[x] = v[x];
   }
@@ -156,7 +160,7 @@ WGW_HD void plane_g2r_reg_body(int pair, int hi0, int np, const SphereTab& sp, c
       const int kr = y <= m ? y + m : (y >= N - m ? y - N + m : -1);
       v[y] = kr >= 0 ? Bp[kr * LS + zc] : mk<C>(C(0), C(0));
     }
-    reg_dif<C, N, 0, +1>(v, tw);
+    reg_dif<C, N, 0, +1, PK>(v, tw);
     cplx<C>* out = Tout + ((size_t)pair * NR + hi0 + p) * N * N;
 #pragma unroll
     for (int y = 0; y < N; ++y) out[(size_t)y * N + zc] = v[y];
@@ -248,7 +252,7 @@ WGW_HD void xline_body(int pair, int y, int m, const FftPlan& pl, const cplx<C>*
 // The x-line pass with one line per thread held in registers (compile-time N): line l = y N + z
 // of pair `pair`, same modes, layouts and positions as xline_body.  The pair intermediate is
 // read and written at T[hi][l], so consecutive threads touch consecutive addresses.
-template <typename T, int N, typename C>
+template <typename T, int N, typename C, bool PK = false>
 WGW_HD void xline_reg_body(int pair, int l, int m, const cplx<C>* tw, cplx<C>* Tbuf, const XArgs<T>& a) {
   const int NP = 2 * m + 1;
   int s0, s1;
@@ -277,7 +281,7 @@ WGW_HD void xline_reg_body(int pair, int l, int m, const cplx<C>* tw, cplx<C>* T
       const int hi = x <= m ? x + m : x - N + m;
       v[x] = in ? tp[(size_t)hi * N * N] : mk<C>(C(0), C(0));
     }
-    reg_dif<C, N, 0, +1>(v, tw);
+    reg_dif<C, N, 0, +1, PK>(v, tw);
   }
   if (a.mode == XM_TO_REAL) {
     T* r0 = a.R0 + (size_t)s0 * a.ldr + line;
@@ -294,7 +298,7 @@ WGW_HD void xline_reg_body(int pair, int l, int m, const cplx<C>* tw, cplx<C>* T
 #pragma unroll
     for (int x = 0; x < N; ++x) v[x] = cscale(v[x], rs_ld<C>(vr, (size_t)x * N));
   }
-  reg_dit<C, N, cplan(N).nst - 1, -1>(v, tw);
+  reg_dit<C, N, cplan(N).nst - 1, -1, PK>(v, tw);
 #pragma unroll
   for (int x = 0; x < N; ++x) {
     const bool in = x <= m || x >= N - m;
@@ -413,7 +417,7 @@ WGW_HD void plane_r2g_body(int pair, int hp, const SphereTab& sp, const FftPlan&
 // every plane along y -> k one per thread straight from T[hi][y][z] (rows |k| <= m kept), one
 // exchange through shared memory, then the rows along z -> l one per thread.  Leaves plane q in
 // B + q (2m+1)(N+1) as B[k + m][l] (natural l).
-template <typename C, int N>
+template <typename C, int N, bool PK = false>
 WGW_HD void plane_r2g_reg_load(int pair, const int* his, int np, int m, const cplx<C>* tw, const cplx<C>* Tin,
                                cplx<C>* B, Thr th) {
   const int NR = 2 * m + 1, LS = N + 1;
@@ -424,7 +428,7 @@ WGW_HD void plane_r2g_reg_load(int pair, const int* his, int np, int m, const cp
     cplx<C> v[N];
 #pragma unroll
     for (int y = 0; y < N; ++y) v[y] = in[(size_t)y * N + zc];
-    reg_dit<C, N, cplan(N).nst - 1, -1>(v, tw);
+    reg_dit<C, N, cplan(N).nst - 1, -1, PK>(v, tw);
 #pragma unroll
     for (int k = 0; k < N; ++k) {
       if (k <= m) Bq[(k + m) * LS + zc] = v[k];
@@ -437,7 +441,7 @@ WGW_HD void plane_r2g_reg_load(int pair, const int* his, int np, int m, const cp
     cplx<C> v[N];
 #pragma unroll
     for (int x = 0; x < N; ++x) v[x] = row[x];
-    reg_dit<C, N, cplan(N).nst - 1, -1>(v, tw);
+    reg_dit<C, N, cplan(N).nst - 1, -1, PK>(v, tw);
 #pragma unroll
     for (int x = 0; x < N; ++x) row[x] = v[x];
   }
@@ -453,7 +457,7 @@ WGW_HD int ent_pos_rows(int2 en, int m) {
 // plane_r2g_body with the register-resident load: planes +hp and -hp of one pair transformed
 // together, then gathered, unpacked and passed through the epilogue.
 // smem: 2 (2m+1)(N+1) complex.
-template <typename T, int N, typename C>
+template <typename T, int N, typename C, bool PK = false>
 WGW_HD void plane_r2g_reg_body(int pair, int hp, const SphereTab& sp, const cplx<C>* tw, const cplx<C>* Tin,
                                const Epi<T>& ep, cplx<C>* B, Thr th) {
   const int m = sp.m, plane = (2 * m + 1) * (N + 1);
@@ -465,7 +469,7 @@ WGW_HD void plane_r2g_reg_body(int pair, int hp, const SphereTab& sp, const cplx
   const int off_p = sp.plane_off[m + hp];
   const int cnt = sp.plane_off[m + hp + 1] - off_p;
   const int his[2] = {m + hp, m - hp};
-  plane_r2g_reg_load<C, N>(pair, his, hp == 0 ? 1 : 2, m, tw, Tin, B, th);
+  plane_r2g_reg_load<C, N, PK>(pair, his, hp == 0 ? 1 : 2, m, tw, Tin, B, th);
   if (hp == 0) {
     const int K = (cnt - 1) / 2;
     for (int t = th.tid; t < K; t += th.nth) {

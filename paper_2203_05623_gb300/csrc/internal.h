@@ -9,12 +9,25 @@
 
 namespace wgw {
 
+// Kernel choice per stage of the FFT pipeline (G -> r planes, x-lines, r -> G planes) on the
+// lengths with register-resident kernels: kFftRegScalar, kFftRegPacked (packed FP32 butterflies;
+// FP32 compute only) or kFftShared (the shared-memory kernel); -1 = the built-in default
+// kFftDefault.  Other lengths always run the shared-memory kernels.
+constexpr int kFftRegScalar = 0, kFftRegPacked = 1, kFftShared = 2, kFftChoices = 3;
+struct FftKern {
+  int g2r = -1, xline = -1, r2g = -1;
+};
+// Built-in choice, from GB300 measurements on the 48^3 block: packed FP32 butterflies speed the
+// x-line and r -> G kernels up (+13 %, +5 %) and slow the G -> r kernel down (-17 %).
+constexpr FftKern kFftDefault{kFftRegScalar, kFftRegPacked, kFftRegPacked};
+
 template <typename T>
 struct FftCtx {
   FftPlan plan;
   const cplx<T>* tw;              // exp(+2 pi i k / N), k < N
   const cplx<ff>* twe = nullptr;  // the same in float-float; non-null selects float-float
                                   // compute for T = double (pair buffers then hold cplx<ff>)
+  FftKern kern{};                 // kernel choice per stage
 };
 
 int fft_threads(int n);
@@ -26,13 +39,14 @@ void clear_error();
 // Pruned 3D FFT pipeline (fft_kernels_*.cu), storage type T and compute type C.
 template <typename T, typename C>
 cudaError_t launch_plane_g2r_c(const SphereTab& sp, const FftPlan& plan, const cplx<C>* tw, const T* X, long ldx,
-                               int n_sys, const int* list, const int* active, cplx<C>* Tbuf, cudaStream_t st);
+                               int n_sys, const int* list, const int* active, cplx<C>* Tbuf, cudaStream_t st,
+                               int kern);
 template <typename T, typename C>
 cudaError_t launch_xline_c(int m, const FftPlan& plan, const cplx<C>* tw, cplx<C>* Tbuf, const XArgs<T>& a,
-                           const int* active, cudaStream_t st);
+                           const int* active, cudaStream_t st, int kern);
 template <typename T, typename C>
 cudaError_t launch_plane_r2g_c(const SphereTab& sp, int npt_max, const FftPlan& plan, const cplx<C>* tw,
-                               const cplx<C>* Tbuf, const Epi<T>& e, cudaStream_t st);
+                               const cplx<C>* Tbuf, const Epi<T>& e, cudaStream_t st, int kern);
 template <typename T, typename C>
 cudaError_t launch_drho_xline_c(int m, const FftPlan& plan, const cplx<C>* tw, const cplx<C>* Tbuf,
                                 const T* psi_r, long ldpsi, int n_v, int n_sys, int n_pert, T coef, T* D,
@@ -52,22 +66,23 @@ cudaError_t launch_plane_g2r(const SphereTab& sp, FftCtx<T> f, const T* X, long 
                              const int* list, const int* active, cplx<T>* Tbuf, cudaStream_t st) {
   if (use_ff(f))
     return launch_plane_g2r_c<T, ff>(sp, f.plan, f.twe, X, ldx, n_sys, list, active,
-                                     reinterpret_cast<cplx<ff>*>(Tbuf), st);
-  return launch_plane_g2r_c<T, T>(sp, f.plan, f.tw, X, ldx, n_sys, list, active, Tbuf, st);
+                                     reinterpret_cast<cplx<ff>*>(Tbuf), st, f.kern.g2r);
+  return launch_plane_g2r_c<T, T>(sp, f.plan, f.tw, X, ldx, n_sys, list, active, Tbuf, st, f.kern.g2r);
 }
 template <typename T>
 cudaError_t launch_xline(int m, FftCtx<T> f, cplx<T>* Tbuf, const XArgs<T>& a, const int* active,
                          cudaStream_t st) {
   if (use_ff(f))
-    return launch_xline_c<T, ff>(m, f.plan, f.twe, reinterpret_cast<cplx<ff>*>(Tbuf), a, active, st);
-  return launch_xline_c<T, T>(m, f.plan, f.tw, Tbuf, a, active, st);
+    return launch_xline_c<T, ff>(m, f.plan, f.twe, reinterpret_cast<cplx<ff>*>(Tbuf), a, active, st, f.kern.xline);
+  return launch_xline_c<T, T>(m, f.plan, f.tw, Tbuf, a, active, st, f.kern.xline);
 }
 template <typename T>
 cudaError_t launch_plane_r2g(const SphereTab& sp, int npt_max, FftCtx<T> f, const cplx<T>* Tbuf,
                              const Epi<T>& e, cudaStream_t st) {
   if (use_ff(f))
-    return launch_plane_r2g_c<T, ff>(sp, npt_max, f.plan, f.twe, reinterpret_cast<const cplx<ff>*>(Tbuf), e, st);
-  return launch_plane_r2g_c<T, T>(sp, npt_max, f.plan, f.tw, Tbuf, e, st);
+    return launch_plane_r2g_c<T, ff>(sp, npt_max, f.plan, f.twe, reinterpret_cast<const cplx<ff>*>(Tbuf), e, st,
+                                     f.kern.r2g);
+  return launch_plane_r2g_c<T, T>(sp, npt_max, f.plan, f.tw, Tbuf, e, st, f.kern.r2g);
 }
 template <typename T>
 cudaError_t launch_drho_xline(int m, FftCtx<T> f, const cplx<T>* Tbuf, const T* psi_r, long ldpsi,

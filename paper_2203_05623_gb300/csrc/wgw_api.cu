@@ -236,6 +236,11 @@ struct wgw_ctx {
   // of each variant on this context's first large list.
   int h_choice = -1;
   double h_ms[2] = {0.0, 0.0};
+  // The FFT stage kernels of the FP32 H application (G -> r, x-line, r -> G; -1 entries: the
+  // built-in default until tuned) and each candidate's median time (0: not timed).
+  FftKern fft_kern{};
+  bool fft_tuned = false;
+  double fft_ms[3][kFftChoices] = {};
   std::vector<int> last_iters;      // per system of the last apply: CG iterations (all refinements)
   std::vector<double> last_relres;  // per system of the last apply: final FP64 ||b - A x|| / ||b||
   std::vector<int> last_conv;       // per system of the last apply: 1 if it met cg_tol
@@ -312,6 +317,16 @@ int to_real(wgw_ctx* c, Prec<T>& pr, const HostSphere& sp, const T* X, long ldx,
   return WGW_OK;
 }
 
+// FFT stage kernels of the FP32 H application: the option where fixed, else the autotuner's
+// choice (the built-in default until it has run).
+FftKern fft_choice(const wgw_ctx* c) {
+  FftKern k = c->fft_kern;
+  if (c->opt.fft_kernels[0] != WGW_FFT_AUTO) k.g2r = c->opt.fft_kernels[0];
+  if (c->opt.fft_kernels[1] != WGW_FFT_AUTO) k.xline = c->opt.fft_kernels[1];
+  if (c->opt.fft_kernels[2] != WGW_FFT_AUTO) k.r2g = c->opt.fft_kernels[2];
+  return k;
+}
+
 // Autotuner of the tensor-core P_c: at the first projection of at least 256 systems (never
 // inside a graph capture) every candidate K split runs three times on a scratch copy of the
 // vectors and the fastest median wins for the life of the context.
@@ -351,6 +366,75 @@ int tune_tc_split(wgw_ctx* c, const float* Y, int n_list, float* work, cudaStrea
   return WGW_OK;
 }
 
+// Autotuner of the FFT stage kernels of the FP32 H application (grids with register-resident
+// kernels; stages the options leave to it), at the context's first application to at least 256
+// systems: each candidate of a stage is timed (median of three after a warm-up) on the first
+// n_list rows of P, with the other stages at their current choice; the G -> r (and x-line) stages
+// run untimed before each x-line (r -> G) timing, so every timed launch sees a freshly written
+// intermediate.  Output goes to scratch.
+int tune_fft(wgw_ctx* c, Prec<float>& pr, const float* P, int n_list, cudaStream_t st) {
+  c->fft_tuned = true;
+  const int N = c->N, NP = 2 * c->wfc.m + 1, pairs = (n_list + 1) / 2;
+  if (!(N == 24 || N == 32 || N == 48 || N == 64)) return WGW_OK;
+  DevBuf out;
+  WGW_TRY(out.ensure(sizeof(float) * (size_t)n_list * c->ld_w));
+  WGW_TRY(pr.Tw.ensure(sizeof(cplx<float>) * (size_t)pairs * NP * N * N));
+  Epi<float> e{};
+  e.out = out.as<float>(); e.ldo = c->ld_w; e.pin = P; e.ldp = c->ld_w; e.vcoef = 1.f; e.kin = 1.f;
+  e.shift = pr.shift.as<float>(); e.n_sys = n_list; e.active = nullptr; e.list = nullptr;
+  const int* list = nullptr;
+  const int* active = nullptr;
+  FftCtx<float> f = pr.fft(c->plan);
+  cplx<float>* Tb = pr.Tw.as<cplx<float>>();
+  XArgs<float> xa{};
+  xa.mode = XM_APPLY_V; xa.V = pr.v_r_fft(); xa.n_sys = n_list; xa.list = list;
+  cudaEvent_t a = nullptr, b = nullptr;
+  WGW_CK(cudaEventCreate(&a));
+  WGW_CK(cudaEventCreate(&b));
+  FftKern k = fft_choice(c);
+  int* sel[3] = {&k.g2r, &k.xline, &k.r2g};
+  int rc = WGW_OK;
+  for (int stage = 0; stage < 3 && rc == WGW_OK; ++stage) {
+    if (c->opt.fft_kernels[stage] != WGW_FFT_AUTO) continue;
+    double best = 1e300;
+    int pick = *sel[stage];
+    for (int cand = 0; cand < kFftChoices && rc == WGW_OK; ++cand) {
+      *sel[stage] = cand;
+      f.kern = k;
+      std::vector<float> ts;
+      for (int r = 0; r < 4; ++r) {
+        cudaError_t err = cudaSuccess;
+        if (stage >= 1) err = launch_plane_g2r<float>(c->wfc.tab(), f, P, c->ld_w, n_list, list, active, Tb, st);
+        if (err == cudaSuccess && stage == 2) err = launch_xline<float>(c->wfc.m, f, Tb, xa, active, st);
+        if (err == cudaSuccess) err = cudaEventRecord(a, st);
+        if (err == cudaSuccess && stage == 0)
+          err = launch_plane_g2r<float>(c->wfc.tab(), f, P, c->ld_w, n_list, list, active, Tb, st);
+        if (err == cudaSuccess && stage == 1) err = launch_xline<float>(c->wfc.m, f, Tb, xa, active, st);
+        if (err == cudaSuccess && stage == 2)
+          err = launch_plane_r2g<float>(c->wfc.tab(), c->wfc.npt_max, f, Tb, e, st);
+        if (err == cudaSuccess) err = cudaEventRecord(b, st);
+        if (err == cudaSuccess) err = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, a, b);
+        if (err != cudaSuccess) {
+          rc = fail(WGW_ERR_CUDA, std::string("FFT autotuner: ") + cudaGetErrorString(err));
+          break;
+        }
+        if (r > 0) ts.push_back(ms);
+      }
+      if (rc != WGW_OK) break;
+      std::sort(ts.begin(), ts.end());
+      c->fft_ms[stage][cand] = ts[ts.size() / 2];
+      if (c->fft_ms[stage][cand] < best) { best = c->fft_ms[stage][cand]; pick = cand; }
+    }
+    *sel[stage] = pick;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc == WGW_OK) c->fft_kern = k;
+  return rc;
+}
+
 // Autotuner of the FP32 H application: the three-kernel pipeline and the fused kernel each run
 // four times (the first warms up) on the context's first list of at least 256 systems, writing a
 // scratch output, and the faster median wins for the life of the context (wgw_autotune_info).
@@ -374,6 +458,9 @@ int tune_h(wgw_ctx* c, Prec<float>& pr, const float* P, int n_list, const int* l
   cudaEvent_t a = nullptr, b = nullptr;
   WGW_CK(cudaEventCreate(&a));
   WGW_CK(cudaEventCreate(&b));
+  XArgs<float> xa{};
+  xa.mode = XM_APPLY_V; xa.V = pr.v_r_fft(); xa.n_sys = n_list; xa.list = list;
+  f.kern = fft_choice(c);
   double med[2] = {0, 0};
   for (int variant = 0; variant < 2; ++variant) {
     std::vector<float> ts;
@@ -383,8 +470,6 @@ int tune_h(wgw_ctx* c, Prec<float>& pr, const float* P, int n_list, const int* l
         WGW_CK(launch_hpsi_fused(c->wfc.tab(), N, P, c->ld_w, n_list, list, active, pr.v_r_fft(), e, st));
       } else {
         WGW_CK(launch_plane_g2r<float>(c->wfc.tab(), f, P, c->ld_w, n_list, list, active, Tb, st));
-        XArgs<float> xa{};
-        xa.mode = XM_APPLY_V; xa.V = pr.v_r_fft(); xa.n_sys = n_list; xa.list = list;
         WGW_CK(launch_xline<float>(c->wfc.m, f, Tb, xa, active, st));
         WGW_CK(launch_plane_r2g<float>(c->wfc.tab(), c->wfc.npt_max, f, Tb, e, st));
       }
@@ -450,6 +535,11 @@ int apply_A(wgw_ctx* c, Prec<T>& pr, const T* P, T* Q, int n_list, const int* li
   if (pairs == 0) return WGW_OK;
   bool fused = false;
   if constexpr (std::is_same<T, float>::value) {
+    if (!c->fft_tuned && n_list >= 256) {   // FFT stage kernels, once per context on its first large list
+      cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+      WGW_CK(cudaStreamIsCapturing(st, &cap));
+      if (cap == cudaStreamCaptureStatusNone) WGW_TRY(tune_fft(c, pr, P, n_list, st));
+    }
     if (c->opt.fused_h != 0 && hpsi_fused_supported(N, c->wfc.m)) {
       if (c->opt.fused_h == 1) {
         fused = true;
@@ -465,6 +555,7 @@ int apply_A(wgw_ctx* c, Prec<T>& pr, const T* P, T* Q, int n_list, const int* li
   }
   if (!fused) WGW_TRY(pr.Tw.ensure(sizeof(cplx<T>) * (size_t)pairs * NP * N * N));
   FftCtx<T> f = pr.fft(c->plan);
+  if constexpr (std::is_same<T, float>::value) f.kern = fft_choice(c);
   cplx<T>* Tb = pr.Tw.template as<cplx<T>>();
   const int nrb = c->wfc.nrb();
   const double tb = t_bytes<T>(c, c->wfc.m, pairs);
@@ -2300,6 +2391,7 @@ int wgw_default_options(wgw_options* opt) {
   opt->max_batch_systems = 0;
   opt->fused_h = 2;
   opt->tc_split = 0;
+  for (int k = 0; k < 3; ++k) opt->fft_kernels[k] = WGW_FFT_AUTO;
   return WGW_OK;
 }
 
@@ -2311,6 +2403,9 @@ static int check_options(const wgw_options& o) {
     return fail(WGW_ERR_ARG, "bad Davidson options");
   if (o.max_batch_systems < 0) return fail(WGW_ERR_ARG, "max_batch_systems < 0");
   if (o.tc_split < 0 || o.tc_split > kTcSplitMax) return fail(WGW_ERR_ARG, "tc_split outside 0..16");
+  for (int k = 0; k < 3; ++k)
+    if (o.fft_kernels[k] < WGW_FFT_AUTO || o.fft_kernels[k] > WGW_FFT_SHARED)
+      return fail(WGW_ERR_ARG, "fft_kernels entries must be WGW_FFT_AUTO, _REG, _REG_PACKED or _SHARED");
   return WGW_OK;
 }
 
@@ -2770,6 +2865,18 @@ int wgw_autotune_info(const wgw_ctx* c, int* tc_split, int* splits, double* ms, 
     if (ms) ms[k] = c->tc_tune[k].second;
   }
   return m;
+}
+
+int wgw_autotune_fft(const wgw_ctx* c, int* choice, double* ms) {
+  if (!c) return fail(WGW_ERR_ARG, "null context");
+  const FftKern k = fft_choice(c);
+  const int ch[3] = {k.g2r, k.xline, k.r2g};
+  for (int s = 0; s < 3; ++s) {
+    if (choice) choice[s] = ch[s];
+    for (int q = 0; q < kFftChoices; ++q)
+      if (ms) ms[3 * s + q] = c->fft_ms[s][q];
+  }
+  return WGW_OK;
 }
 
 int wgw_selftest_wait_timeout(int* timed_out) {

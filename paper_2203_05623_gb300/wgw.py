@@ -38,7 +38,7 @@ class Options(ctypes.Structure):
                 ("dav_max_iter", ctypes.c_int), ("dav_factor", ctypes.c_int), ("seed", ctypes.c_int),
                 ("fp64_emulation", ctypes.c_int), ("tensor_cores", ctypes.c_int), ("cuda_graphs", ctypes.c_int),
                 ("max_batch_systems", ctypes.c_int), ("fused_h", ctypes.c_int),
-                ("tc_split", ctypes.c_int)]
+                ("tc_split", ctypes.c_int), ("fft_kernels", ctypes.c_int * 3)]
 
 
 class SigmaParams(ctypes.Structure):
@@ -131,6 +131,7 @@ def lib(path: str | None = None):
     L.wgw_autotune_info.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                     _dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp]
     L.wgw_selftest_wait_timeout.argtypes = [ctypes.POINTER(ctypes.c_int)]
+    L.wgw_autotune_fft.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), _dp]
     L.wgw_apply_channels.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int,
                                      _dp, ctypes.c_int, _dp, ctypes.POINTER(Stats)]
     L.wgw_g0_lanczos.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
@@ -159,6 +160,8 @@ def wgw_default_options(**overrides) -> Options:
     o = Options()
     _check(lib().wgw_default_options(ctypes.byref(o)), "wgw_default_options")
     for k, v in overrides.items():
+        if k == "fft_kernels":
+            v = (ctypes.c_int * 3)(*[int(x) for x in v])
         setattr(o, k, v)
     return o
 
@@ -390,6 +393,20 @@ def wgw_autotune_info(ctx: Context) -> dict:
     return {"tc_split": choice.value, "candidates_ms": {int(splits[i]): float(ms[i]) for i in range(k)},
             "h_kernel": {-1: "untuned", 0: "three kernels", 1: "fused"}[fused.value],
             "h_ms": {"three_kernels": float(hms[0]), "fused": float(hms[1])}}
+
+
+FFT_KERNEL_NAMES = {-1: "untuned", 0: "register", 1: "register, packed FP32", 2: "shared memory"}
+
+
+def wgw_autotune_fft(ctx: Context) -> dict:
+    """The FFT stage kernels in effect for the FP32 H application (G -> r, x-line, r -> G) and each
+    candidate's median time [ms] from the autotuner (0 = not timed)."""
+    ch = (ctypes.c_int * 3)()
+    ms = np.zeros(9)
+    _check(lib().wgw_autotune_fft(ctx.handle, ch, ms.ctypes.data_as(_dp)), "wgw_autotune_fft")
+    stages = ("g2r", "xline", "r2g")
+    return {st: {"choice": FFT_KERNEL_NAMES[ch[i]],
+                 "ms": {FFT_KERNEL_NAMES[k]: float(ms[3 * i + k]) for k in range(3)}} for i, st in enumerate(stages)}
 
 
 def wgw_selftest_wait_timeout() -> int:

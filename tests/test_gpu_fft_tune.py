@@ -1,0 +1,98 @@
+"""Kernel choices of the FP32 FFT stages (G -> r planes, x-lines with V(r), r -> G planes; the
+transforms of Sec. 4.1's H application) against the oracle.
+
+Each stage runs the register-resident kernel (one line per thread), the same with packed FP32
+butterflies, or the shared-memory kernel; all compute the same transforms, so a mixed-path apply
+matches the oracle's sum over states within the path's 1e-8 whatever the choice, on every grid
+with register-resident kernels.  The autotuner times every candidate of every stage on the first
+application to >= 256 systems and keeps the fastest; a fixed choice is bit-identical from one
+context to the next.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import chi0
+from oracle.model import Model
+
+pytestmark = pytest.mark.gpu
+
+MODELS = {
+    24: "chi0_L10_24",
+    32: synth.Config("g32", L=32.0 / 3.0, ecut=9.0, grid=32, n_wells=8, well_seed=3, n_v=16, kb=True),
+    64: synth.Config("g64", L=16.0, ecut=7.75, grid=64, n_wells=32, well_seed=3, n_v=16),
+}
+CHOICES = [(0, 0, 0), (1, 1, 1), (2, 2, 2), (2, 0, 1)]
+
+
+@pytest.fixture(scope="module")
+def W():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_05623_gb300 import build
+    build.build()
+    import paper_2203_05623_gb300 as W
+    return W
+
+
+def rel_err(got, ref):
+    num = np.linalg.norm(got - ref, axis=0)
+    den = np.linalg.norm(ref, axis=0)
+    return float(np.max(num / np.where(den > 0, den, 1.0)))
+
+
+def _model(s):
+    return Model(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, s.beta_G, s.d_proj)
+
+
+def _ctx(W, s, cg_tol=1e-10, **opt):
+    kb = s.beta_G.shape[1] > 0
+    return W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v,
+                       W.wgw_default_options(precision=W.WGW_MIXED, cg_tol=cg_tol, **opt),
+                       beta_G=s.beta_G if kb else None, d_proj=s.d_proj if kb else None)
+
+
+@pytest.fixture(scope="module", params=sorted(MODELS))
+def case(request):
+    s = synth.make_system(MODELS[request.param])
+    dV = synth.perturbations(s.miller_rho, s.L, 2, 70 + request.param)
+    return s, dV, chi0.sos_drho(_model(s), dV, [0.0])
+
+
+@pytest.mark.parametrize("choice", CHOICES)
+def test_every_fft_kernel_choice_matches_oracle(W, case, choice):
+    s, dV, ref = case
+    ctx = _ctx(W, s, fft_kernels=choice)
+    drho, st, _ = W.wgw_apply_chi0(ctx, dV)
+    assert st["n_converged"] == st["n_systems"]
+    assert rel_err(drho, ref) < 1e-8
+    rep = W.wgw_autotune_fft(ctx)
+    names = [W.FFT_KERNEL_NAMES[k] for k in choice]
+    assert [rep[st_]["choice"] for st_ in ("g2r", "xline", "r2g")] == names
+
+
+def test_fft_autotuner_times_every_candidate(W):
+    """280 systems: the first FP32 H application times the three candidates of each stage."""
+    s = synth.make_system(synth.Config("nv70", L=10.0, ecut=5.0, grid=24, n_wells=16, well_seed=1, n_v=70))
+    dV = synth.perturbations(s.miller_rho, s.L, 4, 64)
+    ctx = _ctx(W, s, cg_tol=1e-11)
+    assert all(v["choice"] == "untuned" for v in W.wgw_autotune_fft(ctx).values())
+    drho, st, _ = W.wgw_apply_chi0(ctx, dV)
+    rep = W.wgw_autotune_fft(ctx)
+    for stage in ("g2r", "xline", "r2g"):
+        assert rep[stage]["choice"] in ("register", "register, packed FP32", "shared memory")
+        assert all(t > 0 for t in rep[stage]["ms"].values())
+        # The kept candidate is the fastest one timed.
+        assert rep[stage]["ms"][rep[stage]["choice"]] == min(rep[stage]["ms"].values())
+    assert rel_err(drho, chi0.sos_drho(_model(s), dV, [0.0])) < 1e-8
+
+
+def test_fixed_fft_choice_is_bit_identical_across_contexts(W):
+    s = synth.make_system(synth.Config("nv70", L=10.0, ecut=5.0, grid=24, n_wells=16, well_seed=1, n_v=70))
+    dV = synth.perturbations(s.miller_rho, s.L, 4, 65)
+    outs = []
+    for _ in range(2):
+        ctx = _ctx(W, s, cg_tol=1e-11, fft_kernels=(2, 1, 0), fused_h=0, tc_split=4)
+        outs.append(W.wgw_apply_chi0(ctx, dV)[0])
+    assert np.array_equal(outs[0], outs[1])

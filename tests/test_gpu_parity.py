@@ -313,13 +313,13 @@ def test_autotuner_picks_a_candidate_and_results_stay_correct(W):
 
 @pytest.mark.parametrize("fused", [0, 1])
 def test_fixed_tuning_choices_are_bit_identical_across_contexts(W, fused):
-    """With the autotuned choices fixed (H kernel, tensor-core K split) two contexts give
-    bit-identical results for the same batch."""
+    """With the autotuned choices fixed (H kernel, tensor-core K split, FFT stage kernels) two
+    contexts give bit-identical results for the same batch."""
     s = synth.make_system(synth.Config("nv70", L=10.0, ecut=5.0, grid=24, n_wells=16, well_seed=1, n_v=70))
     dV = synth.perturbations(s.miller_rho, s.L, 4, 63)
     outs = []
     for _ in range(2):
-        ctx = setup(W, s, precision=W.WGW_MIXED, cg_tol=1e-11, fused_h=fused, tc_split=4)
+        ctx = setup(W, s, precision=W.WGW_MIXED, cg_tol=1e-11, fused_h=fused, tc_split=4, fft_kernels=(0, 1, 1))
         drho, st, _ = W.wgw_apply_chi0(ctx, dV, [0.0, 0.4])
         outs.append(drho)
         info = W.wgw_autotune_info(ctx)
