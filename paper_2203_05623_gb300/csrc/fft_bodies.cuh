@@ -63,6 +63,52 @@ WGW_HD void pair_members(const int* list, int n_list, int q, int& s0, int& s1) {
   s1 = 2 * q + 1 < n_list ? (list ? list[2 * q + 1] : 2 * q + 1) : -1;
 }
 
+// Sphere points of a pair into shared memory, entries [e0, e1) of the plane tables: each thread
+// takes kScatterBatch entries per round and issues all their global loads (table entry, then the
+// four coefficients) before its first shared-memory store, so that the loads of a round are in
+// flight together; a one-entry loop serialises a dependent load pair per entry, and that latency
+// bounded the G -> r plane kernels.  Every entry lands in its own slot, so the result does not
+// depend on the order.  put(e, en.x, z) stores value z of entry e.
+constexpr int kScatterBatch = 4;
+template <typename T, typename C, typename PUT>
+WGW_HD void scatter_pair(const SphereTab& sp, int e0, int e1, const T* x0, const T* x1, bool has1, PUT put,
+                         Thr th) {
+  const C s = C(kInvSqrt2);
+  for (int base = e0 + th.tid; base < e1; base += kScatterBatch * th.nth) {
+    int2 en[kScatterBatch];
+    C ar[kScatterBatch], ai[kScatterBatch], br[kScatterBatch], bi[kScatterBatch];
+#pragma unroll
+    for (int q = 0; q < kScatterBatch; ++q) {
+      const int e = base + q * th.nth;
+      en[q] = e < e1 ? sp.ent[e] : int2{0, -1};
+    }
+#pragma unroll
+    for (int q = 0; q < kScatterBatch; ++q) {
+      const int j = en[q].y;
+      const int i0 = j > 0 ? 2 * j - 1 : 0, i1 = j > 0 ? 2 * j : 0;
+      ar[q] = ai[q] = br[q] = bi[q] = C(0);
+      if (j >= 0) {
+        ar[q] = C(x0[i0]);
+        if (j > 0) ai[q] = C(x0[i1]);
+        if (has1) {
+          br[q] = C(x1[i0]);
+          if (j > 0) bi[q] = C(x1[i1]);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kScatterBatch; ++q) {
+      const int j = en[q].y;
+      if (j < 0) continue;
+      const int neg = (en[q].x >> 16) & 1;
+      cplx<C> z;
+      if (j == 0) z = mk<C>(ar[q], br[q]);
+      else z = neg ? mk<C>((ar[q] + bi[q]) * s, (br[q] - ai[q]) * s) : mk<C>((ar[q] - bi[q]) * s, (ai[q] + br[q]) * s);
+      put(base + q * th.nth, en[q].x, z);
+    }
+  }
+}
+
 // G -> r along z then y for plane hi of one pair; writes T[hi] of that pair.
 // smem: N * (N + 1) complex.
 template <typename T, int NC = 0, typename C = T>
@@ -77,21 +123,8 @@ WGW_HD void plane_g2r_body(int pair, int hi, const SphereTab& sp, const FftPlan&
   WGW_SYNC();
   const T* x0 = X + (size_t)s0 * ldx;
   const T* x1 = X + (size_t)(has1 ? s1 : s0) * ldx;
-  const C s = C(kInvSqrt2);
-  for (int e = sp.plane_off[hi] + th.tid; e < sp.plane_off[hi + 1]; e += th.nth) {
-    const int2 en = sp.ent[e];
-    const int kk = en.x & 0xff, ll = (en.x >> 8) & 0xff, neg = (en.x >> 16) & 1;
-    const int j = en.y;
-    cplx<C> z;
-    if (j == 0) {
-      z = mk<C>(C(x0[0]), has1 ? C(x1[0]) : C(0));
-    } else {
-      const C ar = C(x0[2 * j - 1]), ai = C(x0[2 * j]);
-      const C br = has1 ? C(x1[2 * j - 1]) : C(0), bi = has1 ? C(x1[2 * j]) : C(0);
-      z = neg ? mk<C>((ar + bi) * s, (br - ai) * s) : mk<C>((ar - bi) * s, (ai + br) * s);
-    }
-    B[kk * LS + ll] = z;
-  }
+  scatter_pair<T, C>(sp, sp.plane_off[hi], sp.plane_off[hi + 1], x0, x1, has1,
+                     [&](int, int ex, cplx<C> z) { B[(ex & 0xff) * LS + ((ex >> 8) & 0xff)] = z; }, th);
   WGW_SYNC();
   fft_dif_n<C, NC>(B, pl, tw, +1, 2 * m + 1, LS, 1, m, th);   // rows |k| <= m, along l -> z
   fft_dif_n<C, NC>(B, pl, tw, +1, N, 1, LS, -1, th);          // columns z, along k -> y
@@ -121,25 +154,16 @@ WGW_HD void plane_g2r_reg_body(int pair, int hi0, int np, const SphereTab& sp, c
   WGW_SYNC();
   const T* x0 = X + (size_t)s0 * ldx;
   const T* x1 = X + (size_t)(has1 ? s1 : s0) * ldx;
-  const C s = C(kInvSqrt2);
-  for (int p = 0; p < np; ++p) {
-    cplx<C>* Bp = B + (size_t)p * NR * LS;
-    for (int e = sp.plane_off[hi0 + p] + th.tid; e < sp.plane_off[hi0 + p + 1]; e += th.nth) {
-      const int2 en = sp.ent[e];
-      const int kk = en.x & 0xff, ll = (en.x >> 8) & 0xff, neg = (en.x >> 16) & 1;
-      const int kr = kk <= m ? kk + m : kk - N + m;
-      const int j = en.y;
-      cplx<C> z;
-      if (j == 0) {
-        z = mk<C>(C(x0[0]), has1 ? C(x1[0]) : C(0));
-      } else {
-        const C ar = C(x0[2 * j - 1]), ai = C(x0[2 * j]);
-        const C br = has1 ? C(x1[2 * j - 1]) : C(0), bi = has1 ? C(x1[2 * j]) : C(0);
-        z = neg ? mk<C>((ar + bi) * s, (br - ai) * s) : mk<C>((ar - bi) * s, (ai + br) * s);
-      }
-      Bp[kr * LS + ll] = z;
-    }
-  }
+  // The np planes' entries are contiguous in the tables: one scatter over all of them, the plane
+  // of an entry found from the plane offsets.
+  const int e_lo = sp.plane_off[hi0], e_hi = sp.plane_off[hi0 + np];
+  scatter_pair<T, C>(sp, e_lo, e_hi, x0, x1, has1, [&](int e, int ex, cplx<C> z) {
+    int p = 0;
+    while (p + 1 < np && e >= sp.plane_off[hi0 + p + 1]) ++p;
+    const int kk = ex & 0xff, ll = (ex >> 8) & 0xff;
+    const int kr = kk <= m ? kk + m : kk - N + m;
+    B[((size_t)p * NR + kr) * LS + ll] = z;
+  }, th);
   WGW_SYNC();
   for (int t = th.tid; t < np * NR; t += th.nth) {   // rows: l -> z
     cplx<C>* row = B + (size_t)t * LS;

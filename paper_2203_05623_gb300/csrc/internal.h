@@ -17,9 +17,10 @@ constexpr int kFftRegScalar = 0, kFftRegPacked = 1, kFftShared = 2, kFftChoices 
 struct FftKern {
   int g2r = -1, xline = -1, r2g = -1;
 };
-// Built-in choice, from GB300 measurements on the 48^3 block: packed FP32 butterflies speed the
-// x-line and r -> G kernels up (+13 %, +5 %) and slow the G -> r kernel down (-17 %).
-constexpr FftKern kFftDefault{kFftRegScalar, kFftRegPacked, kFftRegPacked};
+// Built-in choice until tuned, from GB300 measurements on the 48^3 block (register-resident kernels,
+// median of three): G -> r 0.199 ms packed against 0.248 scalar, x-line 0.362 against 0.418,
+// r -> G 0.252 against 0.264; the shared-memory kernels 2-4x slower.
+constexpr FftKern kFftDefault{kFftRegPacked, kFftRegPacked, kFftRegPacked};
 
 template <typename T>
 struct FftCtx {
