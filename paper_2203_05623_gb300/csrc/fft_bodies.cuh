@@ -69,6 +69,10 @@ WGW_HD void pair_members(const int* list, int n_list, int q, int& s0, int& s1) {
 // flight together; a one-entry loop serialises a dependent load pair per entry, and that latency
 // bounded the G -> r plane kernels.  Every entry lands in its own slot, so the result does not
 // depend on the order.  put(e, en.x, z) stores value z of entry e.
+// The float-float shared-memory kernels keep the one-entry loops: batching measured slower there
+// (r -> G -12 %, G -> r -3 % on the 48^3 block; their time goes to float-float arithmetic).
+template <typename C>
+constexpr bool kBatchLoads = !std::is_same<C, ff>::value;
 constexpr int kScatterBatch = 4;
 template <typename T, typename C, typename PUT>
 WGW_HD void scatter_pair(const SphereTab& sp, int e0, int e1, const T* x0, const T* x1, bool has1, PUT put,
@@ -123,8 +127,26 @@ WGW_HD void plane_g2r_body(int pair, int hi, const SphereTab& sp, const FftPlan&
   WGW_SYNC();
   const T* x0 = X + (size_t)s0 * ldx;
   const T* x1 = X + (size_t)(has1 ? s1 : s0) * ldx;
-  scatter_pair<T, C>(sp, sp.plane_off[hi], sp.plane_off[hi + 1], x0, x1, has1,
-                     [&](int, int ex, cplx<C> z) { B[(ex & 0xff) * LS + ((ex >> 8) & 0xff)] = z; }, th);
+  if constexpr (kBatchLoads<C>) {
+    scatter_pair<T, C>(sp, sp.plane_off[hi], sp.plane_off[hi + 1], x0, x1, has1,
+                       [&](int, int ex, cplx<C> z) { B[(ex & 0xff) * LS + ((ex >> 8) & 0xff)] = z; }, th);
+  } else {
+    const C s = C(kInvSqrt2);
+    for (int e = sp.plane_off[hi] + th.tid; e < sp.plane_off[hi + 1]; e += th.nth) {
+      const int2 en = sp.ent[e];
+      const int kk = en.x & 0xff, ll = (en.x >> 8) & 0xff, neg = (en.x >> 16) & 1;
+      const int j = en.y;
+      cplx<C> z;
+      if (j == 0) {
+        z = mk<C>(C(x0[0]), has1 ? C(x1[0]) : C(0));
+      } else {
+        const C ar = C(x0[2 * j - 1]), ai = C(x0[2 * j]);
+        const C br = has1 ? C(x1[2 * j - 1]) : C(0), bi = has1 ? C(x1[2 * j]) : C(0);
+        z = neg ? mk<C>((ar + bi) * s, (br - ai) * s) : mk<C>((ar - bi) * s, (ai + br) * s);
+      }
+      B[kk * LS + ll] = z;
+    }
+  }
   WGW_SYNC();
   fft_dif_n<C, NC>(B, pl, tw, +1, 2 * m + 1, LS, 1, m, th);   // rows |k| <= m, along l -> z
   fft_dif_n<C, NC>(B, pl, tw, +1, N, 1, LS, -1, th);          // columns z, along k -> y
@@ -380,6 +402,90 @@ WGW_HD void unpack_store(const Epi<T>& ep, const SphereTab& sp, int s0, int s1, 
   }
 }
 
+// The epilogue inputs of one pair j (elements 2j-1, 2j of both systems): kin g2 + shift and pin,
+// read before any output of the pair is written (the compiler cannot move a load of pin above a
+// store to out, which may alias it, so epi_store's load-store sequence waits on every load).
+template <typename C>
+struct EpiIn {
+  C c0[2], c1[2], p0[2], p1[2];
+};
+
+template <typename T, typename C>
+WGW_HD EpiIn<C> epi_load(const Epi<T>& e, const SphereTab& sp, int s0, int s1, bool act0, bool act1, int j) {
+  EpiIn<C> r;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) r.c0[q] = r.c1[q] = r.p0[q] = r.p1[q] = C(0);
+  if (!e.pin) return r;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int i = 2 * j - 1 + q;
+    const C g = C(e.kin) * g2_as<C>(sp, i);
+    r.c0[q] = r.c1[q] = g;
+    if (act0) {
+      if (e.shift) r.c0[q] += C(e.shift[s0]);
+      r.p0[q] = C(e.pin[(size_t)s0 * e.ldp + i]);
+    }
+    if (act1) {
+      if (e.shift) r.c1[q] += C(e.shift[s1]);
+      r.p1[q] = C(e.pin[(size_t)s1 * e.ldp + i]);
+    }
+  }
+  return r;
+}
+
+// epi_store with its inputs already loaded: the same arithmetic.
+template <typename T, typename C>
+WGW_HD void epi_store_in(const Epi<T>& e, int s, int i, C f, C c, C p) {
+  C v = C(e.vcoef) * f;
+  if (e.pin) v += c * p;
+  e.out[(size_t)s * e.ldo + i] = T(v);
+}
+
+// unpack_store with loaded epilogue inputs.
+template <typename T, typename C>
+WGW_HD void unpack_store_in(const Epi<T>& ep, int s0, int s1, bool act0, bool act1, int j, cplx<C> zp,
+                            cplx<C> zm, C scale, const EpiIn<C>& in) {
+  const C a = zp.re, b = zp.im, c = zm.re, d = zm.im;
+  const C hs = C(0.5) * scale * C(kSqrt2);
+  if (act0) {
+    epi_store_in(ep, s0, 2 * j - 1, (a + c) * hs, in.c0[0], in.p0[0]);
+    epi_store_in(ep, s0, 2 * j, (b - d) * hs, in.c0[1], in.p0[1]);
+  }
+  if (act1) {
+    epi_store_in(ep, s1, 2 * j - 1, (b + d) * hs, in.c1[0], in.p1[0]);
+    epi_store_in(ep, s1, 2 * j, (c - a) * hs, in.c1[1], in.p1[1]);
+  }
+}
+
+// Gather, unpack and epilogue of cnt sphere pairs: pair t has table entries ea(t) (the member G_j)
+// and eb(t) (its mirror), values zp(t, ea), zm(t, eb).  Each thread takes kGatherBatch pairs per
+// round: their table entries first, then their epilogue inputs, then the stores, so that the
+// loads of a round are in flight together.
+constexpr int kGatherBatch = 2;
+template <typename T, typename C, typename EA, typename EB, typename ZP, typename ZM>
+WGW_HD void gather_pairs(const Epi<T>& ep, const SphereTab& sp, int s0, int s1, bool act0, bool act1, int cnt,
+                         C scale, EA ea, EB eb, ZP zp, ZM zm, Thr th) {
+  for (int t0 = th.tid; t0 < cnt; t0 += kGatherBatch * th.nth) {
+    int2 a[kGatherBatch], b[kGatherBatch];
+#pragma unroll
+    for (int q = 0; q < kGatherBatch; ++q) {
+      const int t = t0 + q * th.nth;
+      a[q] = b[q] = int2{0, -1};
+      if (t < cnt) { a[q] = ea(t); b[q] = eb(t); }
+    }
+    EpiIn<C> in[kGatherBatch];
+#pragma unroll
+    for (int q = 0; q < kGatherBatch; ++q)
+      if (a[q].y >= 0) in[q] = epi_load<T, C>(ep, sp, s0, s1, act0, act1, a[q].y);
+#pragma unroll
+    for (int q = 0; q < kGatherBatch; ++q) {
+      const int t = t0 + q * th.nth;
+      if (a[q].y >= 0)
+        unpack_store_in(ep, s0, s1, act0, act1, a[q].y, zp(t, a[q]), zm(t, b[q]), scale, in[q]);
+    }
+  }
+}
+
 // r -> G along y then z for plane hi of one pair (in B), natural k, l afterwards.
 template <typename C, int NC = 0>
 WGW_HD void plane_r2g_load(int pair, int hi, const SphereTab& sp, const FftPlan& pl,
@@ -415,10 +521,16 @@ WGW_HD void plane_r2g_body(int pair, int hp, const SphereTab& sp, const FftPlan&
   if (hp == 0) {
     // Plane 0 lists [G = 0, K positives, K mirrors].
     const int K = (cnt - 1) / 2;
-    for (int t = th.tid; t < K; t += th.nth) {
-      const int2 ep_ = sp.ent[off_p + 1 + t];
-      unpack_store(ep, sp, s0, s1, act0, act1, ep_.y, B[ent_pos(ep_, LS)],
-                   B[ent_pos(sp.ent[off_p + 1 + K + t], LS)], scale);
+    if constexpr (kBatchLoads<C>) {
+      gather_pairs(ep, sp, s0, s1, act0, act1, K, scale, [&](int t) { return sp.ent[off_p + 1 + t]; },
+                   [&](int t) { return sp.ent[off_p + 1 + K + t]; },
+                   [&](int, int2 e) { return B[ent_pos(e, LS)]; }, [&](int, int2 e) { return B[ent_pos(e, LS)]; }, th);
+    } else {
+      for (int t = th.tid; t < K; t += th.nth) {
+        const int2 ep_ = sp.ent[off_p + 1 + t];
+        unpack_store(ep, sp, s0, s1, act0, act1, ep_.y, B[ent_pos(ep_, LS)],
+                     B[ent_pos(sp.ent[off_p + 1 + K + t], LS)], scale);
+      }
     }
     if (th.tid == 0) {
       const cplx<C> z0 = B[ent_pos(sp.ent[off_p], LS)];
@@ -431,9 +543,15 @@ WGW_HD void plane_r2g_body(int pair, int hp, const SphereTab& sp, const FftPlan&
   WGW_SYNC();
   const int off_m = sp.plane_off[m - hp];
   plane_r2g_load<C, NC>(pair, m - hp, sp, pl, tw, Tin, B, th);
-  for (int t = th.tid; t < cnt; t += th.nth) {
-    unpack_store(ep, sp, s0, s1, act0, act1, sp.ent[off_p + t].y, Zp[t],
-                 B[ent_pos(sp.ent[off_m + t], LS)], scale);
+  if constexpr (kBatchLoads<C>) {
+    gather_pairs(ep, sp, s0, s1, act0, act1, cnt, scale, [&](int t) { return sp.ent[off_p + t]; },
+                 [&](int t) { return sp.ent[off_m + t]; }, [&](int t, int2) { return Zp[t]; },
+                 [&](int, int2 e) { return B[ent_pos(e, LS)]; }, th);
+  } else {
+    for (int t = th.tid; t < cnt; t += th.nth) {
+      unpack_store(ep, sp, s0, s1, act0, act1, sp.ent[off_p + t].y, Zp[t],
+                   B[ent_pos(sp.ent[off_m + t], LS)], scale);
+    }
   }
 }
 
@@ -496,11 +614,10 @@ WGW_HD void plane_r2g_reg_body(int pair, int hp, const SphereTab& sp, const cplx
   plane_r2g_reg_load<C, N, PK>(pair, his, hp == 0 ? 1 : 2, m, tw, Tin, B, th);
   if (hp == 0) {
     const int K = (cnt - 1) / 2;
-    for (int t = th.tid; t < K; t += th.nth) {
-      const int2 ep_ = sp.ent[off_p + 1 + t];
-      unpack_store(ep, sp, s0, s1, act0, act1, ep_.y, B[ent_pos_rows<N>(ep_, m)],
-                   B[ent_pos_rows<N>(sp.ent[off_p + 1 + K + t], m)], scale);
-    }
+    gather_pairs(ep, sp, s0, s1, act0, act1, K, scale, [&](int t) { return sp.ent[off_p + 1 + t]; },
+                 [&](int t) { return sp.ent[off_p + 1 + K + t]; },
+                 [&](int, int2 e) { return B[ent_pos_rows<N>(e, m)]; },
+                 [&](int, int2 e) { return B[ent_pos_rows<N>(e, m)]; }, th);
     if (th.tid == 0) {
       const cplx<C> z0 = B[ent_pos_rows<N>(sp.ent[off_p], m)];
       if (act0) epi_store(ep, sp, s0, 0, z0.re * scale);
@@ -509,10 +626,9 @@ WGW_HD void plane_r2g_reg_body(int pair, int hp, const SphereTab& sp, const cplx
     return;
   }
   const int off_m = sp.plane_off[m - hp];
-  for (int t = th.tid; t < cnt; t += th.nth) {
-    unpack_store(ep, sp, s0, s1, act0, act1, sp.ent[off_p + t].y, B[ent_pos_rows<N>(sp.ent[off_p + t], m)],
-                 B[plane + ent_pos_rows<N>(sp.ent[off_m + t], m)], scale);
-  }
+  gather_pairs(ep, sp, s0, s1, act0, act1, cnt, scale, [&](int t) { return sp.ent[off_p + t]; },
+               [&](int t) { return sp.ent[off_m + t]; }, [&](int, int2 e) { return B[ent_pos_rows<N>(e, m)]; },
+               [&](int, int2 e) { return B[plane + ent_pos_rows<N>(e, m)]; }, th);
 }
 
 // Density response of perturbation p on slab y (Eq. dfpt, one spin channel
