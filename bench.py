@@ -815,6 +815,8 @@ def main():
                          "steering the autotuner")
     ap.add_argument("--tc-split", type=int, default=None,
                     help="tensor-core projector K split (default: autotuned)")
+    ap.add_argument("--h-chunk", type=int, default=None,
+                    help="pairs per L2-resident chunk of the FP32 H pipeline, 0 = none (default: autotuned)")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.n_pert > 0:
@@ -873,6 +875,8 @@ def main():
         opt.fft_kernels = (ctypes.c_int * 3)(*[int(v) for v in args.fft_kernels.split(",")])
     if args.tc_split is not None:
         opt.tc_split = args.tc_split
+    if args.h_chunk is not None:
+        opt.h_chunk_pairs = args.h_chunk
     kb = s.beta_G.shape[1] > 0
     ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, opt,
                       beta_G=s.beta_G if kb else None, d_proj=s.d_proj if kb else None)
@@ -998,6 +1002,7 @@ def main():
         line["cpu_baseline"] = cpu
     line["autotune"] = W.wgw_autotune_info(ctx)
     line["autotune"]["fft"] = W.wgw_autotune_fft(ctx)
+    line["autotune"]["h_chunk"] = W.wgw_autotune_chunk(ctx)
     if world == 1 and args.precision == "mixed" and not args.no_fp64_path and args.workload == "pdep_L16_48":
         line["fp64_path"] = fp64_path(W, s, wl, x, out, stream, ph, oh, min(args.steps, 3))
     if world == 1 and args.precision == "mixed" and not args.no_library_baselines:

@@ -111,6 +111,13 @@ typedef struct wgw_options {
                              the context's first application to >= 256 systems and the fastest kept;
                              wgw_autotune_fft reports the choice).  The same transforms: results agree to
                              FP32 rounding, and a fixed choice is bit-identical from run to run. */
+  int h_chunk_pairs;      /* MIXED: the FP32 three-kernel H application runs its pairs in groups of this
+                             many through a pair intermediate of that size, so that what one kernel
+                             writes is still in L2 when the next reads it; 0 = all pairs at once; -1 =
+                             autotuned (the default: no chunking and chunks of 32 MB and 64 MB of
+                             intermediate are timed on the context's first application to >= 256 systems;
+                             wgw_autotune_chunk reports the choice).  Results are bit-identical for any
+                             value. */
 } wgw_options;
 
 #define WGW_FFT_AUTO (-1)
@@ -129,7 +136,7 @@ typedef struct wgw_stats {
 /* Fills *opt with defaults: WGW_FP64, cg_tol 1e-12, max_cg_iter 2000, max_refine 8,
  * inner_tol 5e-6, f_s 2, check_every 8, dav_tol 1e-8, dav_max_iter 100, dav_factor 4, seed 12345,
  * fp64_emulation 1, tensor_cores 1, cuda_graphs 2, max_batch_systems 0, fused_h 2, tc_split 0,
- * fft_kernels WGW_FFT_AUTO x 3. */
+ * fft_kernels WGW_FFT_AUTO x 3, h_chunk_pairs -1. */
 int wgw_default_options(wgw_options* opt);
 
 /*
@@ -406,6 +413,15 @@ int wgw_autotune_info(const wgw_ctx* ctx, int* tc_split, int* splits, double* ms
  * tuned yet).  Either output may be NULL.  Returns WGW_ERR_ARG for a null context.
  */
 int wgw_autotune_fft(const wgw_ctx* ctx, int* choice, double* ms);
+
+/*
+ * Chunk autotuner record of a context (h_chunk_pairs): *chunk_pairs = the chunk in effect (0: no
+ * chunking; -1: not tuned yet); candidates[k], ms[k] = each timed chunk size and the median time
+ * [ms] of the FP32 three-kernel H application on the context's first large list, for up to n_max
+ * candidates.  Any output may be NULL.  Returns the number of candidates written, or -WGW_ERR_ARG
+ * for a null context or negative n_max.
+ */
+int wgw_autotune_chunk(const wgw_ctx* ctx, int* chunk_pairs, int* candidates, double* ms, int n_max);
 
 /*
  * Failure-detection self-test (no counterpart in the paper).  Every wait of the library's

@@ -240,6 +240,11 @@ struct wgw_ctx {
   // built-in default until tuned) and each candidate's median time (0: not timed).
   FftKern fft_kern{};
   bool fft_tuned = false;
+  // Pairs per L2-resident chunk of the FP32 three-kernel H pipeline (0: all pairs at once) and the
+  // tuned candidates' median times.
+  int h_chunk = 0;
+  bool chunk_tuned = false;
+  std::vector<std::pair<int, double>> chunk_ms;
   double fft_ms[3][kFftChoices] = {};
   std::vector<int> last_iters;      // per system of the last apply: CG iterations (all refinements)
   std::vector<double> last_relres;  // per system of the last apply: final FP64 ||b - A x|| / ||b||
@@ -526,6 +531,94 @@ int run_pc(wgw_ctx* c, T* Y, int n_list, const int* list, const T* Psi, const in
   return WGW_OK;
 }
 
+// The three FFT kernels of the local part of H on a list (g2r, x-line with V(r), r2g with the
+// kinetic and shift epilogue), Q = (T + V - e_v) P.  chunk > 0: the pairs run in consecutive groups
+// of `chunk` pairs through a pair intermediate of that size, so that an intermediate written by
+// g2r is still in L2 when the x-line and r2g kernels read it (a 48^3 pair holds 387 KB; 128 pairs
+// hold 50 MB of the 129 MB L2).  The same kernels on the same pairs: results are bit-identical to
+// chunk = 0.
+template <typename T>
+int h_pipeline(wgw_ctx* c, Prec<T>& pr, const FftCtx<T>& f, const T* P, T* Q, int n_list, const int* list,
+               const int* active, cplx<T>* Tb, int chunk, cudaStream_t st) {
+  const int pairs = (n_list + 1) / 2, nrb = c->wfc.nrb();
+  if (chunk <= 0 || chunk >= pairs) chunk = pairs;
+  for (int p0 = 0; p0 < pairs; p0 += chunk) {
+    const int nc = std::min(n_list - 2 * p0, 2 * chunk), pc = (nc + 1) / 2;
+    // A chunk of an explicit list is a sub-list; without a list its systems are 2 p0.. of the
+    // batch, so the per-system arrays move with it.
+    const long so = list ? 0 : 2L * p0;
+    const int* lc = list ? list + 2 * p0 : nullptr;
+    const int* ac = (active && !list) ? active + so : active;
+    const T* Pc = P + so * c->ld_w;
+    const double tb = t_bytes<T>(c, c->wfc.m, pc);
+    Epi<T> e{};
+    e.out = Q + so * c->ld_w; e.ldo = c->ld_w; e.pin = Pc; e.ldp = c->ld_w; e.vcoef = T(1); e.kin = T(1);
+    e.shift = pr.shift.template as<T>() + so; e.n_sys = nc; e.active = ac; e.list = lc;
+    WGW_CK(c->prof.run(PK_G2R, tb + (double)nc * nrb * sizeof(T), 0, st, [&] {
+      return launch_plane_g2r<T>(c->wfc.tab(), f, Pc, c->ld_w, nc, lc, ac, Tb, st); }));
+    XArgs<T> a{};
+    a.mode = XM_APPLY_V; a.V = pr.v_r_fft(); a.n_sys = nc; a.list = lc;
+    WGW_CK(c->prof.run(PK_XLINE, 2 * tb + (double)c->grid3 * sizeof(T), 0, st, [&] {
+      return launch_xline<T>(c->wfc.m, f, Tb, a, ac, st); }));
+    WGW_CK(c->prof.run(PK_R2G, tb + 2.0 * nc * nrb * sizeof(T), 0, st, [&] {
+      return launch_plane_r2g<T>(c->wfc.tab(), c->wfc.npt_max, f, Tb, e, st); }));
+  }
+  return WGW_OK;
+}
+
+// Autotuner of the chunk size of the FP32 H pipeline (options.h_chunk_pairs = -1), at the context's
+// first application to >= 256 systems, after the FFT stage kernels: no chunking and chunks whose
+// pair intermediate holds 32 MB and 64 MB each run the pipeline four times on the first n_list
+// rows of P (scratch output, the first run a warm-up), and the fastest median wins.
+int tune_chunk(wgw_ctx* c, Prec<float>& pr, const float* P, int n_list, cudaStream_t st) {
+  c->chunk_tuned = true;
+  const int pairs = (n_list + 1) / 2;
+  const double per_pair = t_bytes<float>(c, c->wfc.m, 1);   // one pair's intermediate
+  std::vector<int> cands = {0};
+  for (double mb : {32.0, 64.0}) {
+    const int k = std::max(1, (int)(mb * 1048576.0 / per_pair));
+    if (k < pairs && (cands.size() == 1 || k != cands.back())) cands.push_back(k);
+  }
+  if (cands.size() == 1) return WGW_OK;
+  DevBuf out;
+  WGW_TRY(out.ensure(sizeof(float) * (size_t)n_list * c->ld_w));
+  const int NP = 2 * c->wfc.m + 1, N = c->N;
+  WGW_TRY(pr.Tw.ensure(sizeof(cplx<float>) * (size_t)pairs * NP * N * N));
+  FftCtx<float> f = pr.fft(c->plan);
+  f.kern = fft_choice(c);
+  cudaEvent_t a = nullptr, b = nullptr;
+  WGW_CK(cudaEventCreate(&a));
+  WGW_CK(cudaEventCreate(&b));
+  int rc = WGW_OK, best = 0;
+  double best_ms = 1e300;
+  c->chunk_ms.clear();
+  for (int k : cands) {
+    std::vector<float> ts;
+    for (int r = 0; r < 4 && rc == WGW_OK; ++r) {
+      cudaError_t err = cudaEventRecord(a, st);
+      if (err == cudaSuccess) {
+        rc = h_pipeline<float>(c, pr, f, P, out.as<float>(), n_list, nullptr, nullptr, pr.Tw.as<cplx<float>>(), k, st);
+        if (rc != WGW_OK) break;
+        err = cudaEventRecord(b, st);
+      }
+      if (err == cudaSuccess) err = cudaEventSynchronize(b);
+      float ms = 0.f;
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, a, b);
+      if (err != cudaSuccess) rc = fail(WGW_ERR_CUDA, std::string("chunk autotuner: ") + cudaGetErrorString(err));
+      if (r > 0) ts.push_back(ms);
+    }
+    if (rc != WGW_OK) break;
+    std::sort(ts.begin(), ts.end());
+    const double med = ts[ts.size() / 2];
+    c->chunk_ms.push_back({k, med});
+    if (med < best_ms) { best_ms = med; best = k; }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc == WGW_OK) c->h_chunk = best;
+  return rc;
+}
+
 // Q = P_c (H - e_v) P for the active systems of a list (P already in range(P_c)).
 template <typename T>
 int apply_A(wgw_ctx* c, Prec<T>& pr, const T* P, T* Q, int n_list, const int* list, const int* active,
@@ -573,14 +666,21 @@ int apply_A(wgw_ctx* c, Prec<T>& pr, const T* P, T* Q, int n_list, const int* li
     }
   }
   if (!fused) {
-    WGW_CK(c->prof.run(PK_G2R, tb + (double)n_list * nrb * sizeof(T), 0, st, [&] {
-      return launch_plane_g2r<T>(c->wfc.tab(), f, P, c->ld_w, n_list, list, active, Tb, st); }));
-    XArgs<T> a{};
-    a.mode = XM_APPLY_V; a.V = pr.v_r_fft(); a.n_sys = n_list; a.list = list;
-    WGW_CK(c->prof.run(PK_XLINE, 2 * tb + (double)c->grid3 * sizeof(T), 0, st, [&] {
-      return launch_xline<T>(c->wfc.m, f, Tb, a, active, st); }));
-    WGW_CK(c->prof.run(PK_R2G, tb + 2.0 * n_list * nrb * sizeof(T), 0, st, [&] {
-      return launch_plane_r2g<T>(c->wfc.tab(), c->wfc.npt_max, f, Tb, e, st); }));
+    (void)tb;
+    int chunk = 0;
+    if constexpr (std::is_same<T, float>::value) {
+      if (c->opt.h_chunk_pairs >= 0) {
+        chunk = c->opt.h_chunk_pairs;
+      } else {
+        if (!c->chunk_tuned && n_list >= 256) {
+          cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+          WGW_CK(cudaStreamIsCapturing(st, &cap));
+          if (cap == cudaStreamCaptureStatusNone) WGW_TRY(tune_chunk(c, pr, P, n_list, st));
+        }
+        chunk = c->h_chunk;
+      }
+    }
+    WGW_TRY(h_pipeline<T>(c, pr, f, P, Q, n_list, list, active, Tb, chunk, st));
   }
   if (c->n_proj > 0) {
     WGW_TRY(c->pc_work.ensure(sizeof(T) * std::max(pc_work_elems(nrb, n_list, std::max(c->n_v, c->n_proj)),
@@ -2392,6 +2492,7 @@ int wgw_default_options(wgw_options* opt) {
   opt->fused_h = 2;
   opt->tc_split = 0;
   for (int k = 0; k < 3; ++k) opt->fft_kernels[k] = WGW_FFT_AUTO;
+  opt->h_chunk_pairs = -1;
   return WGW_OK;
 }
 
@@ -2406,6 +2507,7 @@ static int check_options(const wgw_options& o) {
   for (int k = 0; k < 3; ++k)
     if (o.fft_kernels[k] < WGW_FFT_AUTO || o.fft_kernels[k] > WGW_FFT_SHARED)
       return fail(WGW_ERR_ARG, "fft_kernels entries must be WGW_FFT_AUTO, _REG, _REG_PACKED or _SHARED");
+  if (o.h_chunk_pairs < -1) return fail(WGW_ERR_ARG, "h_chunk_pairs must be -1 (autotuned), 0 or a pair count");
   return WGW_OK;
 }
 
@@ -2877,6 +2979,20 @@ int wgw_autotune_fft(const wgw_ctx* c, int* choice, double* ms) {
       if (ms) ms[3 * s + q] = c->fft_ms[s][q];
   }
   return WGW_OK;
+}
+
+int wgw_autotune_chunk(const wgw_ctx* c, int* chunk_pairs, int* candidates, double* ms, int n_max) {
+  if (!c || n_max < 0) {
+    fail(WGW_ERR_ARG, "bad argument");
+    return -WGW_ERR_ARG;
+  }
+  if (chunk_pairs) *chunk_pairs = c->opt.h_chunk_pairs >= 0 ? c->opt.h_chunk_pairs : (c->chunk_tuned ? c->h_chunk : -1);
+  const int m = std::min<int>(n_max, (int)c->chunk_ms.size());
+  for (int k = 0; k < m; ++k) {
+    if (candidates) candidates[k] = c->chunk_ms[k].first;
+    if (ms) ms[k] = c->chunk_ms[k].second;
+  }
+  return m;
 }
 
 int wgw_selftest_wait_timeout(int* timed_out) {

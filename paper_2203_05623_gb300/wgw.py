@@ -38,7 +38,7 @@ class Options(ctypes.Structure):
                 ("dav_max_iter", ctypes.c_int), ("dav_factor", ctypes.c_int), ("seed", ctypes.c_int),
                 ("fp64_emulation", ctypes.c_int), ("tensor_cores", ctypes.c_int), ("cuda_graphs", ctypes.c_int),
                 ("max_batch_systems", ctypes.c_int), ("fused_h", ctypes.c_int),
-                ("tc_split", ctypes.c_int), ("fft_kernels", ctypes.c_int * 3)]
+                ("tc_split", ctypes.c_int), ("fft_kernels", ctypes.c_int * 3), ("h_chunk_pairs", ctypes.c_int)]
 
 
 class SigmaParams(ctypes.Structure):
@@ -132,6 +132,8 @@ def lib(path: str | None = None):
                                     _dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp]
     L.wgw_selftest_wait_timeout.argtypes = [ctypes.POINTER(ctypes.c_int)]
     L.wgw_autotune_fft.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), _dp]
+    L.wgw_autotune_chunk.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     _dp, ctypes.c_int]
     L.wgw_apply_channels.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int,
                                      _dp, ctypes.c_int, _dp, ctypes.POINTER(Stats)]
     L.wgw_g0_lanczos.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
@@ -407,6 +409,18 @@ def wgw_autotune_fft(ctx: Context) -> dict:
     stages = ("g2r", "xline", "r2g")
     return {st: {"choice": FFT_KERNEL_NAMES[ch[i]],
                  "ms": {FFT_KERNEL_NAMES[k]: float(ms[3 * i + k]) for k in range(3)}} for i, st in enumerate(stages)}
+
+
+def wgw_autotune_chunk(ctx: Context) -> dict:
+    """Pairs per chunk of the FP32 H pipeline in effect (0 none, -1 untuned) and each timed
+    candidate's median time [ms]."""
+    ch = ctypes.c_int(-1)
+    cands = (ctypes.c_int * 8)()
+    ms = np.zeros(8)
+    k = lib().wgw_autotune_chunk(ctx.handle, ctypes.byref(ch), cands, ms.ctypes.data_as(_dp), 8)
+    if k < 0:
+        _check(-k, "wgw_autotune_chunk")
+    return {"chunk_pairs": ch.value, "candidates_ms": {int(cands[i]): float(ms[i]) for i in range(k)}}
 
 
 def wgw_selftest_wait_timeout() -> int:

@@ -96,3 +96,33 @@ def test_fixed_fft_choice_is_bit_identical_across_contexts(W):
         ctx = _ctx(W, s, cg_tol=1e-11, fft_kernels=(2, 1, 0), fused_h=0, tc_split=4)
         outs.append(W.wgw_apply_chi0(ctx, dV)[0])
     assert np.array_equal(outs[0], outs[1])
+
+
+def test_h_chunks_are_bit_identical(W):
+    """The FP32 H pipeline run in chunks of pairs (ragged last chunk included) computes every pair
+    exactly as the unchunked run: bit-identical results, and the oracle's within 1e-8."""
+    s = synth.make_system(synth.Config("nv70", L=10.0, ecut=5.0, grid=24, n_wells=16, well_seed=1, n_v=70))
+    dV = synth.perturbations(s.miller_rho, s.L, 4, 66)          # 280 systems = 140 pairs
+    outs = []
+    for chunk in (0, 16, 45):
+        ctx = _ctx(W, s, cg_tol=1e-11, fft_kernels=(1, 1, 1), fused_h=0, tc_split=4, h_chunk_pairs=chunk)
+        outs.append(W.wgw_apply_chi0(ctx, dV)[0])
+        assert W.wgw_autotune_chunk(ctx)["chunk_pairs"] == chunk
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    assert rel_err(outs[0], chi0.sos_drho(_model(s), dV, [0.0])) < 1e-8
+
+
+def test_chunk_autotuner_times_its_candidates(W):
+    """256 systems of the 48^3 model (128 pairs, 21 x 48^2 complex FP32 = 387,072 B each): no chunking
+    and 32 MB chunks (86 pairs; 64 MB would exceed the list) are timed at the first FP32 H
+    application and one is kept."""
+    s = synth.make_system("pdep_L16_48")
+    phi = synth.perturbations(s.miller_rho, s.L, 4, 67)
+    ctx = _ctx(W, s, fused_h=0)
+    assert W.wgw_autotune_chunk(ctx)["chunk_pairs"] == -1
+    _, st, _ = W.wgw_apply_chibar0(ctx, phi)
+    assert st["n_converged"] == st["n_systems"] == 256
+    rep = W.wgw_autotune_chunk(ctx)
+    assert sorted(rep["candidates_ms"]) == [0, 32 * 1048576 // (21 * 48 * 48 * 8)]
+    assert all(t > 0 for t in rep["candidates_ms"].values())
+    assert rep["chunk_pairs"] == min(rep["candidates_ms"], key=rep["candidates_ms"].get)
