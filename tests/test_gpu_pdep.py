@@ -89,6 +89,30 @@ def test_davidson_without_start_block(W, cfg24, dense24):
     assert np.max(np.abs(eig - w_ref[:4]) / np.abs(w_ref[:4])) < 1e-10
 
 
+def test_davidson_checkpoint_and_resume(W, cfg24, dense24, tmp_path):
+    """Checkpoint and resume through the C ABI: a Davidson stopped after three iterations returns
+    its current Ritz values and basis (status NOCONV); the basis, written to disk and read back,
+    is the start block of a fresh context's solve, which converges to the dense PDEP eigenvalues in
+    fewer iterations than the cold start from the original block."""
+    s = cfg24
+    w_ref, _ = dense24
+    n_pdep = 8
+    opt = dict(precision=W.WGW_FP64, cg_tol=1e-13, dav_tol=1e-12)
+    x0 = synth.perturbations(s.miller_rho, s.L, n_pdep, 11)
+    ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, W.wgw_default_options(dav_max_iter=3, **opt))
+    eig1, basis1, st1, status = W.wgw_pdep_davidson(ctx, n_pdep, x0, allow_noconv=True)
+    assert status == W.WGW_ERR_NOCONV and st1["max_iters"] == 3
+    np.save(tmp_path / "pdep_basis.npy", basis1)
+    np.save(tmp_path / "pdep_eig.npy", eig1)
+    del ctx
+    ctx2 = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, W.wgw_default_options(**opt))
+    eig2, basis2, st2, _ = W.wgw_pdep_davidson(ctx2, n_pdep, np.load(tmp_path / "pdep_basis.npy"))
+    _, _, cold, _ = W.wgw_pdep_davidson(ctx2, n_pdep, x0, want_basis=False)
+    assert st2["n_converged"] == n_pdep
+    assert np.max(np.abs(eig2 - w_ref[:n_pdep]) / np.abs(w_ref[:n_pdep])) < 1e-10
+    assert st2["max_iters"] < cold["max_iters"]
+
+
 def _neg_index(miller):
     """Index of -G for every G of a sphere in canonical order."""
     where = {tuple(g): i for i, g in enumerate(np.asarray(miller))}
