@@ -10,9 +10,10 @@
 namespace wgw {
 
 // Kernel choice per stage of the FFT pipeline (G -> r planes, x-lines, r -> G planes) on the
-// lengths with register-resident kernels: kFftRegScalar, kFftRegPacked (packed FP32 butterflies;
-// FP32 compute only) or kFftShared (the shared-memory kernel); -1 = the built-in default
-// kFftDefault.  Other lengths always run the shared-memory kernels.
+// lengths with register-resident kernels (24, 32, 48, 64, and 96 in FP32): kFftRegScalar,
+// kFftRegPacked (packed FP32 butterflies; FP32 compute only) or kFftShared (the shared-memory
+// kernel); -1 = the built-in default kFftDefault (kFftDefault96 at 96).  Other lengths always run
+// the shared-memory kernels.
 constexpr int kFftRegScalar = 0, kFftRegPacked = 1, kFftShared = 2, kFftChoices = 3;
 struct FftKern {
   int g2r = -1, xline = -1, r2g = -1;
@@ -21,6 +22,9 @@ struct FftKern {
 // median of three): G -> r 0.199 ms packed against 0.248 scalar, x-line 0.362 against 0.418,
 // r -> G 0.252 against 0.264; the shared-memory kernels 2-4x slower.
 constexpr FftKern kFftDefault{kFftRegPacked, kFftRegPacked, kFftRegPacked};
+// N = 96 (FP32; 65536 systems of the 96^3 model): G -> r 30.4 ms packed, 36.2 scalar, 31.0 shared;
+// x-line 39.0 scalar, 40.2 packed, 106.5 shared; r -> G 23.1 packed, 24.2 scalar, 40.6 shared.
+constexpr FftKern kFftDefault96{kFftRegPacked, kFftRegScalar, kFftRegPacked};
 
 template <typename T>
 struct FftCtx {

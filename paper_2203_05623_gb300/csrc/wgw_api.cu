@@ -380,7 +380,7 @@ int tune_tc_split(wgw_ctx* c, const float* Y, int n_list, float* work, cudaStrea
 int tune_fft(wgw_ctx* c, Prec<float>& pr, const float* P, int n_list, cudaStream_t st) {
   c->fft_tuned = true;
   const int N = c->N, NP = 2 * c->wfc.m + 1, pairs = (n_list + 1) / 2;
-  if (!(N == 24 || N == 32 || N == 48 || N == 64)) return WGW_OK;
+  if (!(N == 24 || N == 32 || N == 48 || N == 64 || N == 96)) return WGW_OK;
   DevBuf out;
   WGW_TRY(out.ensure(sizeof(float) * (size_t)n_list * c->ld_w));
   WGW_TRY(pr.Tw.ensure(sizeof(cplx<float>) * (size_t)pairs * NP * N * N));
@@ -3186,7 +3186,10 @@ static int sigma_eval(wgw_ctx* c, SigmaCtx& S, const std::vector<int>& pi, const
         es.push_back(pi[p]); ej.push_back(j); ep.push_back(p); ef.push_back(-1.0);
         ez.push_back(c->e_v[j] - pw[p]); ez.push_back(S.prm.eta);
       }
-  const int n_e = (int)es.size(), chunk = 512;
+  // Entries per round: chi0bar, Lambda and the elimination work of one entry take 3 x 16 n_pdep^2
+  // bytes; at most 512 entries and about 256 MB per round.
+  const int n_e = (int)es.size();
+  const int chunk = (int)std::max<size_t>(1, std::min<size_t>(512, ((size_t)256 << 20) / (48 * (size_t)npd * npd)));
   DevBuf chi, lam, des, dej, def, dout;
   for (int e0 = 0; e0 < n_e; e0 += chunk) {
     const int ne = std::min(chunk, n_e - e0);

@@ -4,9 +4,9 @@ transforms of Sec. 4.1's H application) against the oracle.
 Each stage runs the register-resident kernel (one line per thread), the same with packed FP32
 butterflies, or the shared-memory kernel; all compute the same transforms, so a mixed-path apply
 matches the oracle's sum over states within the path's 1e-8 whatever the choice, on every grid
-with register-resident kernels.  The autotuner times every candidate of every stage on the first
-application to >= 256 systems and keeps the fastest; a fixed choice is bit-identical from one
-context to the next.
+with register-resident kernels (24, 32, 64, and 96 in FP32; 48 is the 48^3 model of the other
+files).  The autotuner times every candidate of every stage on the first application to >= 256
+systems and keeps the fastest; a fixed choice is bit-identical from one context to the next.
 """
 import numpy as np
 import pytest
@@ -21,6 +21,7 @@ MODELS = {
     24: "chi0_L10_24",
     32: synth.Config("g32", L=32.0 / 3.0, ecut=9.0, grid=32, n_wells=8, well_seed=3, n_v=16, kb=True),
     64: synth.Config("g64", L=16.0, ecut=7.75, grid=64, n_wells=32, well_seed=3, n_v=16),
+    96: synth.Config("g96", L=24.0, ecut=3.3, grid=96, n_wells=64, well_seed=3, n_v=16, kb=True),
 }
 CHOICES = [(0, 0, 0), (1, 1, 1), (2, 2, 2), (2, 0, 1)]
 
