@@ -105,7 +105,7 @@ typedef struct wgw_options {
                              bit-identical results from run to run. */
   int fft_kernels[3];     /* MIXED: the kernel of each FP32 FFT stage of the H application (G -> r planes,
                              x-lines with V(r), r -> G planes) on the grids with register-resident kernels
-                             (24, 32, 48, 64): WGW_FFT_REG (one line per thread in registers), WGW_FFT_REG_PACKED
+                             (24, 32, 48, 64, 96): WGW_FFT_REG (one line per thread in registers), WGW_FFT_REG_PACKED
                              (the same with packed FP32 butterflies), WGW_FFT_SHARED (lines in shared
                              memory), or WGW_FFT_AUTO (the default: every candidate of the stage is timed on
                              the context's first application to >= 256 systems and the fastest kept;
