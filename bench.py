@@ -69,6 +69,10 @@ WORKLOADS = {
                               "Sternheimer systems (COCG batched over frequencies, mixed FP32/FP64), and Lanczos "
                               "chains of 64 steps for every (v, pdep) pair (128 chains) with chi0 in the basis at "
                               "the same frequencies"),
+    "qp_L10_24": dict(config="chi0_L10_24", n_pert=32, pert_seed=94, cg_tol=0.0,
+                      desc="quasiparticle energies of the 4 occupied states of the 24^3 model (Eq. e_qp by secant "
+                           "on Sigma_X + I^SR + R): 32 basis vectors (seeded, scaled by 2), chi0 and G0 chains of 16 steps, 16 "
+                           "Gauss-Legendre nodes on [0, 20 Ha], eta 0.1 Ha, e_F at mid-gap, FP64 path"),
     "chi0_L10_24": dict(config="chi0_L10_24", n_pert=8, pert_seed=2, cg_tol=1e-10,
                         desc="chi0 apply, 8 perturbations x 4 occupied states = 32 Sternheimer systems, "
                              "24^3 grid, N_pw=515, N_rho=4337, mixed FP32/FP64"),
@@ -418,6 +422,71 @@ def run_freq(args, wl):
             "clocks": clk.summary()}
     if cpu:
         line["lanczos"]["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+
+
+def run_qp(args, wl):
+    """Quasiparticle energies through wgw_qp (chains, Sigma_X, I^SR, the residue term and the secant
+    iterations all inside one call; host buffers, copies included)."""
+    import numpy as np
+    import synth
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    s = synth.make_system(wl["config"])
+    phi = 2.0 * synth.perturbations(s.miller_rho, s.L, wl["n_pert"], wl["pert_seed"])
+    x, wts = np.polynomial.legendre.leggauss(16)
+    nodes, weights = 10.0 * (x + 1.0), 10.0 * wts
+    n_steps = 16
+    cpu = None
+    from oracle.model import Model
+    m = Model(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v)
+    e = np.linalg.eigvalsh(m.h_dense())
+    e_fermi = 0.5 * (e[s.n_v - 1] + e[s.n_v])
+    states = list(range(s.n_v))
+    prm = dict(n_steps_chi=n_steps, n_steps_g0=n_steps, nodes=nodes, weights=weights, e_fermi=e_fermi, eta=0.1)
+    if not args.no_cpu_baseline:
+        # The oracle's Sigma(w) of the highest state at one frequency (its chains, Lambda at the nodes
+        # and at the residue frequencies), host cores only, before the first GPU call.
+        from oracle import lanczos as lz_oracle, sigma as sg_oracle
+        t0 = time.perf_counter()
+        chi = lz_oracle.chi0_pdep(m, phi, nodes, n_steps)[0]
+        lam = np.array([np.linalg.solve(np.eye(phi.shape[1]) - chi[:, :, k], chi[:, :, k]).real
+                        for k in range(nodes.size)])
+        i, w = s.n_v - 1, s.e_v[s.n_v - 1] - 0.05
+
+        def lam_fn(z):
+            c = lz_oracle.chi0_pdep_z(m, phi, [z], n_steps)[:, :, 0]
+            return np.linalg.solve(np.eye(c.shape[0]) - c, c)
+        sg_oracle.sigma_x(m, [i])
+        sg_oracle.isr(m, phi, [i], n_steps, [w], lam, nodes, weights)
+        sg_oracle.residue_term(m, phi, i, [w], e_fermi, 0.1, lam_fn)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 1.0 / dt, "unit": "Sigma evaluations/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"Sigma_X + I^SR + R of one state at one frequency with the same basis, chains and "
+                         f"nodes (oracle.sigma, oracle.lanczos), {dt:.1f} s"}
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2203_05623_gb300 import build
+    build.build()
+    import paper_2203_05623_gb300 as W
+    ctx = W.wgw_setup(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v, W.wgw_default_options(precision=W.WGW_FP64))
+    for _ in range(max(args.warmup, 1)):
+        W.wgw_qp(ctx, phi, states, **prm)
+    ts, eq, it = [], None, None
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            eq, sg, it = W.wgw_qp(ctx, phi, states, **prm)
+            ts.append(time.perf_counter() - t0)
+    line = {"metric": "quasiparticle energies per second (Eq. e_qp, secant on the GPU-evaluated Sigma)",
+            "value": len(states) * args.steps / sum(ts), "unit": "QP energies/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(ts) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"],
+                       "timed": "host call including the host <-> device copies"},
+            "e_qp": [float(v) for v in eq], "e_ks": [float(v) for v in s.e_v], "secant_steps": [int(v) for v in it],
+            "clocks": clk.summary()}
+    if cpu:
+        line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
 
 
@@ -917,6 +986,8 @@ def main():
         return run_spin(args, wl)
     if args.workload == "chi0w_L10_24":
         return run_freq(args, wl)
+    if args.workload == "qp_L10_24":
+        return run_qp(args, wl)
 
     import numpy as np
     import torch
