@@ -241,7 +241,12 @@ int emu_fft_position(int N, int n) {
 // float-float compute (compile-time N = 24 only).
 int emu_apply_h(double L, double ecut, int N, const double* vloc_c, int n_sys, const double* X,
                 const double* shift, double* out, int flags) {
-  const bool fp32 = flags & 1, ct = flags & 2, ffc = flags & 4, reg = flags & 8;
+  const bool fp32 = flags & 1, ct = flags & 2, ffc = flags & 4, reg = flags & 8, reg96 = flags & 16;
+  if (reg96) {   // the 96-point register-resident FP32 bodies
+    if (N != 96) return 1;
+    apply_h_impl<float, 96>(L, ecut, N, vloc_c, n_sys, X, shift, out, true);
+    return 0;
+  }
   if ((ct || ffc || reg) && N != 24) return 1;
   if (ffc) {
     apply_h_impl<double, 24, ff>(L, ecut, N, vloc_c, n_sys, X, shift, out, reg);

@@ -212,6 +212,27 @@ def test_apply_h_bodies_equal_dense_h(emu, cfg24, fp32):
     assert np.max(np.abs(got - ref)) < tol * np.max(np.abs(ref))
 
 
+def test_apply_h_bodies_96_register_resident(emu):
+    """The 96-point register-resident FP32 bodies (one line per thread; batched sphere scatter and
+    gather) apply the local H of a 96^3 model as the dense H does, to FP32 accuracy."""
+    s = synth.make_system(synth.Config("g96", L=24.0, ecut=3.3, grid=96, n_wells=64, well_seed=3, n_v=16, kb=True))
+    m = Model(s.L, s.ecut, s.grid, s.vloc_G, s.psi_v, s.e_v)          # local part only, as the bodies
+    mp = Maps(emu, s.L, s.ecut, s.grid)
+    rng = np.random.default_rng(3)
+    n_sys = 3
+    X = rng.standard_normal((n_sys, mp.nrb))
+    shift = np.array([0.2, -0.5, 0.9])
+    v_in, vp = P(np.stack([s.vloc_G.real, s.vloc_G.imag], 1).ravel())
+    xin, xp = P(X.ravel())
+    sh, shp = P(shift)
+    out = np.zeros(n_sys * mp.nrb)
+    assert emu.emu_apply_h(ctypes.c_double(s.L), ctypes.c_double(s.ecut), s.grid, vp, n_sys, xp, shp,
+                           out.ctypes.data_as(dp), 16 | 1) == 0
+    ref = m.h_dense() @ mp.to_c(X) + shift[None, :] * mp.to_c(X)
+    got = mp.to_c(out.reshape(n_sys, mp.nrb))
+    assert np.max(np.abs(got - ref)) < 2e-6 * np.max(np.abs(ref))
+
+
 @pytest.mark.parametrize("reg", [0, 1])
 def test_products_bodies_equal_oracle(emu, cfg24, reg):
     """Right-hand-side products (FROM_REAL and TO_REAL x-line passes), shared-memory or
